@@ -1,0 +1,190 @@
+"""Seeded synthetic workloads: parameter dictionaries and initial fields.
+
+This module holds no step of the method. It only states the problems (lattice,
+boundaries, material constants) and draws the seeded initial fields (density
+profile with noise, initial charge, geometry mask, inlet profile). Both the
+CUDA binding and the CPU oracle read these dictionaries; neither side's
+arithmetic lives here.
+
+Problems follow the setups of Lauricella et al. (arXiv:1612.05404), Sec. III:
+liquid / vapour densities 2.0 / 0.16 at Shan-Chen coupling G = -5, psi scale
+rho0 = 1, Newtonian viscosity 1/6, charged drop and electrified jet geometry.
+The 3-D cases use the D3Q19 set.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+RHO_L = 2.0  # liquid density of the paper's runs (Sec. III A)
+RHO_V = 0.16  # vapour density (Sec. III A)
+FLUID, SOLID, INLET, OUTLET = 0, 1, 2, 3
+SEED_BASE = 20161205
+
+E0_SWEEP = (1e-4, 4e-4, 7e-4, 1e-3)
+
+
+def base_params(**kw) -> dict:
+    """Every parameter both sides read, with neutral defaults."""
+    p = dict(
+        dim=3, shape=(16, 16, 16),
+        face_bc=["periodic"] * 6, phi_bc=["periodic"] * 6, phi_axis=2,
+        charge_model="none", force_el="qe", neutralize=True,
+        poisson_maxit=20000, poisson_fixed_sweeps=0, alpha_mode="entropic",
+        phi_lo=0.0, phi_hi=0.0, phi_solid=0.0,
+        nu0=1.0 / 6.0, nu_inf=1.0 / 6.0, n_carreau=1.0,
+        G=-5.0, Gw=-5.0, rho0=1.0, eps_kappa=1.0,
+        sigma_liq=0.0, sigma_gas=0.0, Dq=1e-3, E_ext=(0.0, 0.0, 0.0),
+        Q_b=0.0, Q_s=0.0, K_d=1.0, xi_b=0.0, xi_s=0.0, theta_width=0.1,
+        sor_omega=None, poisson_tol=1e-13, alpha_eq_tol=1e-8,
+        rho_in=RHO_L, rho_out=RHO_V,
+        # CUDA-side choices (the oracle ignores them)
+        precision="fp64", poisson_check_every=8,
+    )
+    p["lambda"] = 0.0
+    for k, v in kw.items():
+        p[k] = v
+    if p["sor_omega"] is None:
+        nmax = max(p["shape"])
+        p["sor_omega"] = 2.0 / (1.0 + math.sin(math.pi / nmax))
+    return p
+
+
+def kappa_for_ratio(ratio: float, rho_l: float = RHO_L, rho_v: float = RHO_V) -> float:
+    """kappa in eps = 1 + kappa rho such that eps(rho_l)/eps(rho_v) = ratio."""
+    return (ratio - 1.0) / (rho_l - ratio * rho_v)
+
+
+def _grid(shape):
+    nx, ny, nz = shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    return x.astype(np.float64), y.astype(np.float64), z.astype(np.float64)
+
+
+def drop_profile(shape, radius, center=None, width=5.0, dim=3):
+    """tanh drop profile between RHO_L inside and RHO_V outside (x fastest)."""
+    x, y, z = _grid(shape)
+    nx, ny, nz = shape
+    if center is None:
+        center = ((nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0)
+    r2 = (x - center[0]) ** 2 + (y - center[1]) ** 2
+    if dim == 3:
+        r2 = r2 + (z - center[2]) ** 2
+    r = np.sqrt(r2)
+    rho = 0.5 * (RHO_L + RHO_V) - 0.5 * (RHO_L - RHO_V) * np.tanh(2.0 * (r - radius) / width)
+    return rho.reshape(-1)
+
+
+def uniform_noise(n, amp, seed):
+    return np.random.default_rng(seed).uniform(-amp, amp, size=n)
+
+
+def charged_drop_at_rest(n=32, radius=8.0, precision="fp64", steps=500, seed=SEED_BASE + 1,
+                         eps_ratio=2.0, sigma_ratio=10.0, Q=1e-3, noise=1e-4):
+    """Charged drop at rest on an n^3 periodic D3Q19 lattice; the free charge is
+    transported (advection-diffusion plus Ohmic relaxation)."""
+    shape = (n, n, n)
+    kappa = kappa_for_ratio(eps_ratio)
+    eps_l = 1.0 + kappa * RHO_L
+    sig_l = eps_l / 50.0
+    cfg = base_params(shape=shape, charge_model="transport", eps_kappa=kappa,
+                      sigma_liq=sig_l, sigma_gas=sig_l / sigma_ratio, Dq=1e-3,
+                      precision=precision, poisson_tol=1e-13 if precision == "fp64" else 1e-6)
+    cfg["steps"] = steps
+    N = n ** 3
+    rho = drop_profile(shape, radius) + uniform_noise(N, noise, seed)
+    inside = rho > 1.0
+    q = np.where(inside, Q / max(int(inside.sum()), 1), 0.0)
+    fields = dict(mask=np.zeros(N, np.uint8), rho=rho, q=q)
+    return cfg, fields
+
+
+def drop_in_field(E0=1e-3, n=64, radius=12.0, precision="fp32", steps=5000,
+                  seed=SEED_BASE + 2, eps_ratio=2.0, sigma_ratio=10.0, noise=1e-4,
+                  n_carreau=0.6, lam=10.0):
+    """Leaky-dielectric drop between electrodes: periodic in x, y; bounce-back
+    walls carrying Dirichlet potentials on the z faces (E = E0 along z)."""
+    shape = (n, n, n)
+    kappa = kappa_for_ratio(eps_ratio)
+    eps_l = 1.0 + kappa * RHO_L
+    sig_l = eps_l / 50.0
+    nu0 = 1.0 / 6.0
+    cfg = base_params(
+        shape=shape, charge_model="transport", eps_kappa=kappa,
+        face_bc=["periodic", "periodic", "periodic", "periodic", "wall", "wall"],
+        phi_bc=["periodic", "periodic", "periodic", "periodic", "dirichlet", "dirichlet"],
+        phi_axis=2, phi_lo=0.0, phi_hi=-E0 * (n + 1),
+        sigma_liq=sig_l, sigma_gas=sig_l / sigma_ratio, Dq=1e-3,
+        nu0=nu0, nu_inf=nu0 / 10.0, n_carreau=n_carreau,
+        precision=precision, poisson_tol=1e-13 if precision == "fp64" else 1e-6)
+    cfg["lambda"] = lam
+    cfg["steps"] = steps
+    cfg["E0"] = E0
+    N = n ** 3
+    rho = drop_profile(shape, radius) + uniform_noise(N, noise, seed)
+    fields = dict(mask=np.zeros(N, np.uint8), rho=rho, q=np.zeros(N))
+    return cfg, fields
+
+
+def jet(shape=(128, 128, 512), nozzle_r=8, wall=2, nozzle_len=16, u_mean=0.02, E0=5e-4,
+        precision="bf16", steps=20000, seed=SEED_BASE + 3, perturb=1e-3):
+    """Electrified jet (Sec. III B, extended to 3-D): a nozzle of inner radius
+    nozzle_r along z injects liquid with a Poiseuille profile; outlet nodes at
+    the far z plane are a vapour reservoir; lateral faces are walls; the
+    potential drops linearly from 0 (nozzle side, nozzle conductor at 0) to
+    -E0 (nz+1) (collector side). Charge is the non-conserved xi form."""
+    nx, ny, nz = shape
+    nu0 = 1.0 / 6.0
+    cfg = base_params(
+        shape=shape, charge_model="xi", xi_b=1e-4, xi_s=6e-2, K_d=1.0,
+        face_bc=["wall"] * 6, phi_bc=["dirichlet"] * 6, phi_axis=2,
+        phi_lo=0.0, phi_hi=-E0 * (nz + 1), phi_solid=0.0,
+        nu0=nu0, nu_inf=nu0 / 10.0, n_carreau=0.5, eps_kappa=1.0,
+        precision=precision, poisson_tol=1e-13 if precision == "fp64" else 1e-6)
+    cfg["lambda"] = 20.0
+    cfg["steps"] = steps
+    x, y, z = _grid(shape)
+    cx, cy = (nx - 1) / 2.0, (ny - 1) / 2.0
+    r = np.sqrt((x - cx) ** 2 + (y - cy) ** 2).reshape(-1)
+    zf = z.reshape(-1)
+    mask = np.zeros(nx * ny * nz, np.uint8)
+    mask[(r >= nozzle_r) & (r < nozzle_r + wall) & (zf < nozzle_len)] = SOLID
+    inlet = (r < nozzle_r) & (zf == 0)
+    mask[inlet] = INLET
+    mask[zf == nz - 1] = OUTLET
+    rho = np.full(nx * ny * nz, RHO_V)
+    rho[(r < nozzle_r) & (zf < nozzle_len)] = RHO_L
+    # a drop just outside the nozzle, as in the paper's initial state
+    d = np.sqrt((x.reshape(-1) - cx) ** 2 + (y.reshape(-1) - cy) ** 2 + (zf - nozzle_len) ** 2)
+    rho = np.maximum(rho, 0.5 * (RHO_L + RHO_V) - 0.5 * (RHO_L - RHO_V) * np.tanh(2.0 * (d - nozzle_r) / 5.0))
+    rho[mask == SOLID] = 0.0
+    u_in = np.zeros((nx * ny * nz, 3))
+    prof = 2.0 * u_mean * (1.0 - (r / nozzle_r) ** 2)
+    pert = uniform_noise(nx * ny * nz, perturb, seed)
+    u_in[inlet, 2] = prof[inlet] + pert[inlet]
+    fields = dict(mask=mask, rho=rho, q=np.zeros(nx * ny * nz), u_in=u_in)
+    return cfg, fields
+
+
+def paper_drop_2d(n=320, radius=40.0, Q=2.13, qs_over_qb=10.0, steps=1000,
+                  seed=SEED_BASE + 6, noise=0.0):
+    """The paper's 2-D charged drop at rest (Sec. III A): D2Q9, periodic n x n,
+    R = 40, G = -5, Q = 2.13 with Q_s/Q_b = 10, K_d = 1, nu = 1/6, eps = 1 + rho."""
+    shape = (n, n, 1)
+    Q_b = Q / (1.0 + qs_over_qb)
+    cfg = base_params(dim=2, shape=shape, charge_model="conserved", Q_b=Q_b,
+                      Q_s=Q - Q_b, K_d=1.0, eps_kappa=1.0, phi_axis=0)
+    cfg["steps"] = steps
+    rho = drop_profile(shape, radius, dim=2)
+    if noise:
+        rho = rho + uniform_noise(n * n, noise, seed)
+    fields = dict(mask=np.zeros(n * n, np.uint8), rho=rho)
+    return cfg, fields
+
+
+def as_float64_fields(fields: dict) -> dict:
+    out = {}
+    for k, v in fields.items():
+        out[k] = np.ascontiguousarray(v, dtype=np.uint8 if k == "mask" else np.float64)
+    return out

@@ -1,0 +1,220 @@
+"""Pins of the oracle's electrostatics: the Poisson solve (Sec. II) against a
+direct solve and a manufactured solution, Gauss's law and the paper's |E| on
+the 2-D charged drop, the charge models Eqs. (surface-q2)/(surface-q3) with
+the curvature K, and the transported charge relaxing with time constant
+eps/sigma."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1612_05404_gb300 import workloads as W
+
+
+def _dense_vs_sor(cfg, mask, rho, qn):
+    A, b, index = oracle.poisson_system(cfg, mask, rho, qn)
+    x = np.linalg.solve(A, b)
+    ref = np.zeros(mask.size)
+    ref[index >= 0] = x[index[index >= 0]]
+    phi, it, res = oracle.poisson_solve(cfg, mask, rho, qn)
+    return phi, ref, it, res
+
+
+def test_poisson_periodic_matches_direct_solve():
+    shape = (6, 4, 6)
+    N = 144
+    cfg = W.base_params(shape=shape, charge_model="xi", poisson_tol=1e-14, eps_kappa=0.7)
+    rng = np.random.default_rng(80)
+    rho = rng.uniform(0.16, 2.0, N)
+    q = rng.standard_normal(N)
+    qn = q - q.mean()
+    phi, ref, it, res = _dense_vs_sor(cfg, np.zeros(N, np.uint8), rho, qn)
+    assert res <= 1e-14 and it > 0
+    assert np.allclose(phi, ref - ref.mean(), rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+def test_poisson_dirichlet_and_conductors_match_direct_solve():
+    shape = (6, 4, 5)
+    N = 120
+    cfg = W.base_params(shape=shape, charge_model="xi", poisson_tol=1e-14,
+                        face_bc=["periodic", "periodic", "wall", "wall", "wall", "wall"],
+                        phi_bc=["periodic", "periodic", "neumann", "neumann", "dirichlet", "dirichlet"],
+                        phi_lo=0.2, phi_hi=-0.5, phi_solid=0.1)
+    rng = np.random.default_rng(81)
+    mask = np.zeros(N, np.uint8)
+    mask[[13, 50, 77]] = oracle.SOLID
+    rho = rng.uniform(0.16, 2.0, N)
+    qn = rng.standard_normal(N) * (mask == 0)
+    phi, ref, it, res = _dense_vs_sor(cfg, mask, rho, qn)
+    fl = mask == 0
+    assert np.allclose(phi[fl], ref[fl], rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+def test_poisson_manufactured_second_order():
+    """phi = sin(2pi x/n) sin(2pi y/n) sin(pi (z+1)/(n+1)) + linear(z) with
+    eps = 1 + kappa rho(x, y) smooth: the discrete solution converges to it at
+    second order (error ratio ~4 per halving of the spacing)."""
+    errs = []
+    for n in (8, 16):
+        shape = (n, n, n)
+        x, y, z = [a.reshape(-1) for a in np.meshgrid(np.arange(n), np.arange(n), np.arange(n),
+                                                       indexing="xy")]
+        x, y, z = (np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")[::-1])
+        x, y, z = x.reshape(-1).astype(float), y.reshape(-1).astype(float), z.reshape(-1).astype(float)
+        kx = ky = 2 * np.pi / n
+        kz = np.pi / (n + 1)
+        lo, hi = 0.3, -0.7
+        kap = 0.5
+        rho = 1.0 + 0.5 * np.cos(kx * x) * np.cos(ky * y)
+        eps = 1.0 + kap * rho
+        ex = -kap * 0.5 * kx * np.sin(kx * x) * np.cos(ky * y)
+        ey = -kap * 0.5 * ky * np.cos(kx * x) * np.sin(ky * y)
+        S = np.sin(kx * x) * np.sin(ky * y) * np.sin(kz * (z + 1))
+        phi_ex = S + lo + (z + 1) * (hi - lo) / (n + 1)
+        px = kx * np.cos(kx * x) * np.sin(ky * y) * np.sin(kz * (z + 1))
+        py = ky * np.sin(kx * x) * np.cos(ky * y) * np.sin(kz * (z + 1))
+        lap = -(kx ** 2 + ky ** 2 + kz ** 2) * S
+        q = -(eps * lap + ex * px + ey * py)
+        cfg = W.base_params(shape=shape, charge_model="xi", poisson_tol=1e-13, eps_kappa=kap,
+                            face_bc=["periodic"] * 4 + ["wall", "wall"],
+                            phi_bc=["periodic"] * 4 + ["dirichlet", "dirichlet"],
+                            phi_lo=lo, phi_hi=hi)
+        phi, it, res = oracle.poisson_solve(cfg, np.zeros(n ** 3, np.uint8), rho, q)
+        errs.append(np.abs(phi - phi_ex).max())
+    assert 3.0 < errs[0] / errs[1] < 5.5
+
+
+def test_conserved_charge_totals(paper):
+    """Eq. (surface-q2): sum q = Q_b + Q_s exactly, split in the ratio
+    Q_s/Q_b = 10, on the paper's 2-D drop."""
+    cfg, fl = W.paper_drop_2d(n=96, radius=20.0)
+    q, K, sums = oracle.charge_field(cfg, fl["mask"], fl["rho"])
+    assert q.sum() == pytest.approx(paper["Q_total"]["value"], rel=1e-13)
+    cfg_b = dict(cfg, Q_s=0.0)
+    qb, _, _ = oracle.charge_field(cfg_b, fl["mask"], fl["rho"])
+    assert (q.sum() - qb.sum()) / qb.sum() == pytest.approx(paper["Qs_over_Qb"]["value"], rel=1e-12)
+
+
+def test_xi_form_is_linear_in_coefficients():
+    cfg, fl = W.paper_drop_2d(n=64, radius=15.0)
+    c1 = dict(cfg, charge_model="xi", xi_b=1e-4, xi_s=0.0)
+    c2 = dict(cfg, charge_model="xi", xi_b=0.0, xi_s=6e-2)
+    c3 = dict(cfg, charge_model="xi", xi_b=1e-4, xi_s=6e-2)
+    q1 = oracle.charge_field(c1, fl["mask"], fl["rho"])[0]
+    q2 = oracle.charge_field(c2, fl["mask"], fl["rho"])[0]
+    q3 = oracle.charge_field(c3, fl["mask"], fl["rho"])[0]
+    assert np.allclose(q3, q1 + q2, rtol=1e-14, atol=0)
+    rho = fl["rho"]
+    th = 0.5 * (1 + np.tanh((rho - 1.0) / 0.1))
+    assert np.allclose(q1, 1e-4 * rho * th, rtol=1e-13)
+
+
+def test_mean_curvature_circle_and_sphere():
+    """K = -div(grad rho/|grad rho|) equals 1/R on a circle and 2/R on a
+    sphere at the interface (positive on convex drops)."""
+    cfg, fl = W.paper_drop_2d(n=128, radius=30.0)
+    _, K, _ = oracle.charge_field(cfg, fl["mask"], fl["rho"])
+    n = 128
+    x = np.arange(n) - 63.5
+    d = np.sqrt(x[None, :] ** 2 + x[:, None] ** 2).reshape(-1)
+    sel = np.abs(d - 30.0) < 0.5
+    assert K[sel].mean() == pytest.approx(1 / 30.0, rel=0.02)
+    n3 = 40
+    cfg3 = W.base_params(shape=(n3, n3, n3), charge_model="conserved", Q_s=1.0)
+    rho3 = W.drop_profile((n3, n3, n3), 12.0)
+    _, K3, _ = oracle.charge_field(cfg3, np.zeros(n3 ** 3, np.uint8), rho3)
+    g = np.arange(n3) - (n3 - 1) / 2
+    d3 = np.sqrt(g[None, None, :] ** 2 + g[None, :, None] ** 2 + g[:, None, None] ** 2).reshape(-1)
+    sel3 = np.abs(d3 - 12.0) < 0.5
+    assert K3[sel3].mean() == pytest.approx(2 / 12.0, rel=0.03)
+
+
+@pytest.mark.slow
+def test_paper_drop_field_gauss_law_and_boundary_value(paper):
+    """The paper's 2-D charged drop (320^2, R = 40, Q = 2.13, Q_s/Q_b = 10,
+    eps = 1 + rho, neutralised): outside the drop |E| follows Gauss's law,
+    |E| = Q_enc/(2 pi r eps_V), and the paper's boundary value 3.5e-3 lies
+    within the range of |E| across the interface."""
+    cfg, fl = W.paper_drop_2d()
+    cfg["poisson_tol"] = 1e-8
+    n = 320
+    q, _, _ = oracle.charge_field(cfg, fl["mask"], fl["rho"])
+    qm = q.mean()
+    phi, it, res = oracle.poisson_solve(cfg, fl["mask"], fl["rho"], q - qm, qmean=qm)
+    E = oracle.efield(cfg, fl["mask"], phi)
+    Em = np.sqrt((E ** 2).sum(1))
+    x = np.arange(n) - 159.5
+    d = np.sqrt(x[None, :] ** 2 + x[:, None] ** 2).reshape(-1)
+    Q = paper["Q_total"]["value"]
+    eps_v = 1.0 + fl["rho"][0]
+    for r in (60.0, 80.0):
+        sel = np.abs(d - r) < 0.5
+        q_enc = Q * (1.0 - np.pi * r ** 2 / n ** 2)
+        assert Em[sel].mean() == pytest.approx(q_enc / (2 * np.pi * r * eps_v), rel=0.02)
+    band = (d > 37.0) & (d < 45.0)
+    Eb = paper["E_boundary"]["value"]
+    assert Em[band].min() < Eb < Em[band].max()
+
+
+def _decay_run(n=16, steps=30, sigma=0.06, kappa=1.0, Dq=1e-3, amp=1e-6):
+    shape = (n, 4, 4)
+    N = n * 16
+    cfg = W.base_params(shape=shape, G=0.0, Gw=0.0, charge_model="transport",
+                        sigma_liq=sigma, sigma_gas=sigma, eps_kappa=kappa, Dq=Dq,
+                        poisson_tol=1e-13)
+    x = np.tile(np.arange(n), 16).astype(float)
+    q0 = amp * np.sin(2 * np.pi * x / n)
+    sim = oracle.Sim(cfg, dict(mask=np.zeros(N, np.uint8), rho=np.full(N, 2.0), q=q0))
+    qs = []
+    for _ in range(steps):
+        qs.append(sim.g.reshape(7, N).sum(0)[:n].copy())
+        sim.step()
+    return np.array(qs), cfg
+
+
+def test_transport_mode_matches_linear_mode_dynamics():
+    """Uniform medium at rest: a single Fourier mode of the transported charge
+    evolves by the 7x7 linear map of the D3Q7 collision with the Ohmic source
+    R = sigma Lphi = -(sigma/eps) q (Poisson eps Lphi = -q) followed by
+    streaming. Computed here in Fourier space, independently of the oracle's
+    site loops."""
+    n, steps, sigma, kappa, Dq = 16, 30, 0.06, 1.0, 1e-3
+    qs, cfg = _decay_run(n, steps, sigma, kappa, Dq)
+    eps = 1.0 + kappa * 2.0
+    tau = 0.5 + Dq / 0.25
+    w = np.array([0.25] + [0.125] * 6)
+    cx = np.array([0, 1, -1, 0, 0, 0, 0])
+    k = 2 * np.pi / n
+    one = np.ones(7)
+    C = np.eye(7) - (np.eye(7) - np.outer(w, one)) / tau - (sigma / eps) * np.outer(w, one)
+    M = np.diag(np.exp(-1j * k * cx)) @ C
+    a = w * (-1j) * 1e-6
+    xs = np.arange(n)
+    for t in range(steps):
+        qt = np.real(one @ a * np.exp(1j * k * xs))
+        assert np.allclose(qs[t], qt, rtol=0, atol=1e-9 * 1e-6)
+        a = M @ a
+
+
+def test_transport_relaxation_time_constant():
+    """Charge relaxation in a uniform conductor: the amplitude decays as
+    exp(-t/tau_e) with tau_e = eps/sigma (plus the small diffusive rate
+    D k^2)."""
+    n, steps = 16, 30
+    for sigma, kappa in ((0.06, 1.0), (0.02, 0.5)):
+        qs, _ = _decay_run(n, steps, sigma, kappa, 1e-3)
+        amp = np.abs(qs).max(1)
+        rate = -np.polyfit(np.arange(steps), np.log(amp), 1)[0]
+        eps = 1.0 + 2.0 * kappa
+        expect = sigma / eps + 0.25 * (4e-3) * (2 * np.pi / n) ** 2
+        assert rate == pytest.approx(-np.log(1 - expect), rel=0.02)
+
+
+def test_uniform_field_on_neutral_fluid_exerts_no_force():
+    shape = (4, 4, 4)
+    cfg = W.base_params(shape=shape, G=0.0, Gw=0.0, charge_model="xi", xi_b=0.0, xi_s=0.0,
+                        E_ext=(0.3, -0.1, 0.2))
+    sim = oracle.Sim(cfg, dict(mask=np.zeros(64, np.uint8), rho=np.full(64, 1.5)))
+    r0, j0 = sim.moments()
+    sim.step()
+    r1, j1 = sim.moments()
+    assert np.abs(j1).max() < 1e-16

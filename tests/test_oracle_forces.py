@@ -1,0 +1,144 @@
+"""Pins of the oracle's forces: Shan-Chen Eq. (sc) with its equation of state
+(G_crit = -4 at rho = ln 2, Sec. III A), coexistence, the Laplace law with the
+paper's surface tension, and the exact-difference source Eq. (add)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1612_05404_gb300 import workloads as W
+
+
+def _eos(rho, G):
+    """Shan-Chen pressure p = rho c_s^2 + G c_s^2 psi^2 / 2, psi = 1 - exp(-rho)."""
+    return rho / 3.0 + G / 6.0 * (1.0 - np.exp(-rho)) ** 2
+
+
+def test_sc_force_continuum_limit():
+    """On a long-wave profile Eq. (sc) tends to -G c_s^2 psi grad psi (the
+    gradient of the non-ideal pressure), with an O(k^2) error that drops by
+    about 4 when the wavelength doubles."""
+    for dim in (2, 3):
+        errs = []
+        for nx in (64, 128):
+            shape = (nx, 4, 1) if dim == 2 else (nx, 4, 4)
+            cfg = W.base_params(dim=dim, shape=shape, G=-5.0, phi_axis=0)
+            x = np.arange(nx, dtype=float)
+            k = 2 * np.pi / nx
+            rho1 = 1.0 + 0.5 * np.sin(k * x)
+            rho = np.broadcast_to(rho1, shape[::-1]).reshape(-1).copy()
+            F = oracle.sc_force(cfg, np.zeros(rho.size, np.uint8), rho)
+            psi = 1 - np.exp(-rho1)
+            dpsi = np.exp(-rho1) * 0.5 * k * np.cos(k * x)
+            ref = 5.0 / 3.0 * psi * dpsi
+            Fx = F[:nx, 0]
+            assert np.abs(F[:, 1:]).max() < 1e-15
+            errs.append(np.abs(Fx - ref).max() / np.abs(ref).max())
+        assert errs[0] < 5e-3
+        assert 3.0 < errs[0] / errs[1] < 5.0
+
+
+def test_sc_force_sums_to_zero_periodic():
+    """Pairwise antisymmetry of Eq. (sc): on a periodic lattice sum_r F = 0,
+    so the total momentum of a Shan-Chen fluid is conserved."""
+    cfg = W.base_params(shape=(8, 6, 10), G=-5.0)
+    rho = np.random.default_rng(70).uniform(0.1, 2.2, 480)
+    F = oracle.sc_force(cfg, np.zeros(480, np.uint8), rho)
+    assert np.abs(F.sum(0)).max() < 1e-14 * np.abs(F).sum()
+
+
+def test_eos_critical_point(paper):
+    """The pressure implied by Eq. (sc) with psi = 1 - exp(-rho) has its
+    critical point at G = -4, rho = ln 2 (Sec. III A): dp/drho and
+    d2p/drho2 vanish there, and only there for G > G_crit it is monotone."""
+    G, r = paper["G_crit"]["value"], paper["rho_crit"]["value"]
+    h = 1e-4
+    d1 = (_eos(r + h, G) - _eos(r - h, G)) / (2 * h)
+    d2 = (_eos(r + h, G) - 2 * _eos(r, G) + _eos(r - h, G)) / h ** 2
+    assert abs(d1) < 1e-8 and abs(d2) < 1e-6
+    rr = np.linspace(0.01, 4, 4000)
+    assert np.all(np.diff(_eos(rr, -3.9)) > 0)
+    assert np.any(np.diff(_eos(rr, -4.1)) < 0)
+
+
+def test_flat_interface_coexistence(paper):
+    """A flat liquid slab at G = -5 settles at densities near the paper's
+    2.0 / 0.16 with equal bulk pressures (mechanical equilibrium of the
+    Eq. (sc) EOS)."""
+    nx, ny = 64, 2
+    cfg = W.base_params(dim=2, shape=(nx, ny, 1), phi_axis=0, alpha_mode="bgk")
+    x = np.tile(np.arange(nx), ny).astype(float)
+    rho = np.where(np.abs(x - 31.5) < 16, 2.0, 0.16)
+    sim = oracle.Sim(cfg, dict(mask=np.zeros(nx * ny, np.uint8), rho=rho))
+    sim.step(3000)
+    r = sim.rho.reshape(ny, nx)[0]
+    rl, rv = r[31], r[0]
+    assert rl == pytest.approx(paper["rho_liquid"]["value"], rel=0.05)
+    assert rv == pytest.approx(paper["rho_vapour"]["value"], rel=0.05)
+    assert _eos(rl, -5.0) == pytest.approx(_eos(rv, -5.0), rel=2e-2)
+
+
+@pytest.mark.slow
+def test_laplace_law_surface_tension(paper):
+    """2-D drops at G = -5: Delta p = sigma / R with sigma independent of R and
+    close to the paper's 5.8e-2 (Sec. III A); the same sigma reproduces the
+    paper's Ohnesorge and Deborah numbers (Eq. oh, a0 = 20, lambda = 1000)."""
+    sig = []
+    for n, R in ((40, 9.0), (48, 13.0)):
+        cfg = W.base_params(dim=2, shape=(n, n, 1), phi_axis=0, alpha_mode="bgk")
+        sim = oracle.Sim(cfg, dict(mask=np.zeros(n * n, np.uint8),
+                                   rho=W.drop_profile((n, n, 1), R, dim=2)))
+        sim.step(2500)
+        r = sim.rho.reshape(n, n)
+        rin, rout = r[n // 2, n // 2], r[0, 0]
+        Req = np.sqrt((r - rout).sum() / (rin - rout) / np.pi)
+        sig.append((_eos(rin, -5.0) - _eos(rout, -5.0)) * Req)
+    assert sig[0] == pytest.approx(sig[1], rel=0.02)
+    s = float(np.mean(sig))
+    assert s == pytest.approx(paper["sigma"]["value"], rel=0.10)
+    Oh = (1 / 6) * np.sqrt(2.0 / (s * paper["a0"]["value"]))
+    De = paper["lambda_jet"]["value"] * np.sqrt(s / (2.0 * paper["a0"]["value"] ** 3))
+    assert Oh == pytest.approx(paper["Oh"]["value"], rel=0.05)
+    assert De == pytest.approx(paper["De"]["value"], rel=0.06)
+
+
+def test_exact_difference_forcing_momentum():
+    """Eq. (add) with the polynomial equilibrium adds exactly F to the
+    momentum of each site and no mass: sum_r j(t+1) = sum_r j(t) + sum_r F,
+    and the reported velocity is the half-step one, (j + F/2)/rho."""
+    shape = (4, 4, 4)
+    N = 64
+    E = (1e-3, 2e-3, -1e-3)
+    cfg = W.base_params(shape=shape, G=0.0, Gw=0.0, charge_model="xi", xi_b=1e-2,
+                        E_ext=E, alpha_mode="entropic")
+    rng = np.random.default_rng(71)
+    u0 = rng.uniform(-0.02, 0.02, (N, 3))
+    sim = oracle.Sim(cfg, dict(mask=np.zeros(N, np.uint8), rho=np.full(N, 2.0), u=u0))
+    r0, j0 = sim.moments()
+    sim.step()
+    r1, j1 = sim.moments()
+    theta = 0.5 * (1 + np.tanh(10.0))
+    F = 1e-2 * 2.0 * theta * np.array(E)
+    assert r1.sum() == pytest.approx(r0.sum(), rel=1e-14)
+    assert np.allclose(j1.sum(0), j0.sum(0) + N * F, rtol=0, atol=1e-14)
+    assert np.allclose(sim.u.reshape(N, 3), (j0 + 0.5 * F) / r0[:, None], rtol=1e-13, atol=1e-16)
+
+
+def test_sc_wall_term():
+    """Eq. (sc) wall sum: with G_w = G a wall acts like a neighbour of the
+    site's own density, so a uniform fluid between walls feels no force; with
+    G_w = 0 a wall-adjacent site feels G psi^2 sum_{p in wall} w_p c_p."""
+    shape = (4, 6, 4)
+    N = 96
+    face = ["periodic", "periodic", "wall", "wall", "periodic", "periodic"]
+    phi = ["periodic", "periodic", "neumann", "neumann", "periodic", "periodic"]
+    rho = np.full(N, 1.3)
+    F = oracle.sc_force(W.base_params(shape=shape, G=-5.0, Gw=-5.0, face_bc=face, phi_bc=phi),
+                        np.zeros(N, np.uint8), rho)
+    assert np.abs(F).max() < 1e-16
+    F0 = oracle.sc_force(W.base_params(shape=shape, G=-5.0, Gw=0.0, face_bc=face, phi_bc=phi),
+                         np.zeros(N, np.uint8), rho).reshape(4, 6, 4, 3)
+    psi2 = (1 - np.exp(-1.3)) ** 2
+    # y = 0 row: the wall lies at y = -1 -> links with c_y = -1 (w = 1/18 + 4/36)
+    assert F0[:, 0, :, 1] == pytest.approx(np.full((4, 4), -5.0 * psi2 * -(1 / 18 + 4 / 36)), rel=1e-14)
+    assert F0[:, 5, :, 1] == pytest.approx(np.full((4, 4), -5.0 * psi2 * (1 / 18 + 4 / 36)), rel=1e-14)
+    assert np.abs(F0[:, 1:5]).max() < 1e-16
