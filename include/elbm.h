@@ -1,0 +1,182 @@
+/*
+ * elbm.h -- C ABI of the GB300 (sm_103a) charged entropic lattice Boltzmann
+ * library: one time step of Lauricella et al., "Entropic Lattice Boltzmann
+ * Model for Charged Leaky Dielectric Multiphase Fluids in Electrified Jets"
+ * (arXiv:1612.05404), Sec. II, on a 3-D D3Q19 lattice.
+ *
+ * One step (Sec. II C) is: moments; free charge (Eqs. surface-q2 / surface-q3,
+ * or the transported D3Q7 charge); neutralisation and the variable-permittivity
+ * Poisson equation div(eps grad phi) = -q (Sec. II); Shan-Chen force Eq. (sc);
+ * electric force Eq. (force_el2); entropic alpha Eq. (entropic) with Eq. (H);
+ * Carreau viscosity Eqs. (stress), (strain2), (carreau), (beta); the update
+ * Eq. (lattice-b) with the exact-difference source Eq. (add); streaming.
+ *
+ * Conventions
+ *  - Every call returns an elbm_status (0 = success). Nothing is printed, no
+ *    call exits the process. elbm_strerror() names a status.
+ *  - Lattice arrays are flat, x fastest: site = x + nx*(y + ny*z). Host arrays
+ *    passed in are FP64 (fields) or uint8 (node kinds), owned by the caller and
+ *    only read during the call. Population arrays are planes: f[p*N + site],
+ *    in the velocity order reported by elbm_velocity_set().
+ *  - The handle owns every byte of device memory it uses; elbm_free releases
+ *    it. Work is issued on the caller's CUDA stream (params.cuda_stream,
+ *    NULL = the legacy default stream).
+ *  - Invalid parameters return ELBM_E_INVAL and allocate nothing.
+ */
+#ifndef ELBM_H
+#define ELBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct elbm_handle elbm_handle;
+
+typedef enum {
+    ELBM_OK = 0,
+    ELBM_W_POISSON_NOCONV = 1, /* a Poisson solve hit poisson_maxit; last iterate kept */
+    ELBM_E_INVAL = -1,         /* invalid argument or parameter set */
+    ELBM_E_NOMEM = -2,         /* device or pinned host allocation failed */
+    ELBM_E_CUDA = -3,          /* a CUDA runtime call failed */
+    ELBM_E_NUMERIC = -4,       /* a non-finite value or rho <= 0 appeared */
+    ELBM_E_STATE = -5          /* request not possible in this handle's state */
+} elbm_status;
+
+/* node kinds of the geometry mask */
+enum { ELBM_NODE_FLUID = 0, ELBM_NODE_SOLID = 1, ELBM_NODE_INLET = 2, ELBM_NODE_OUTLET = 3 };
+/* flow boundary of a domain face (faces: -x,+x,-y,+y,-z,+z) */
+enum { ELBM_FACE_PERIODIC = 0, ELBM_FACE_WALL = 1 };
+/* potential boundary of a domain face */
+enum { ELBM_PHI_PERIODIC = 0, ELBM_PHI_DIRICHLET = 1, ELBM_PHI_NEUMANN = 2 };
+/* free-charge model: none, Eq. (surface-q2), Eq. (surface-q3), D3Q7 transport */
+enum { ELBM_CHARGE_NONE = 0, ELBM_CHARGE_CONSERVED = 1, ELBM_CHARGE_XI = 2,
+       ELBM_CHARGE_TRANSPORT = 3 };
+/* electric force: q E, or Eq. (force_el2) q E + (eps-1)/2 grad|E|^2 */
+enum { ELBM_FEL_QE = 0, ELBM_FEL_FULL = 1 };
+/* relaxation: entropic alpha (Eq. entropic) or alpha = 2 (BGK) */
+enum { ELBM_ALPHA_ENTROPIC = 0, ELBM_ALPHA_BGK = 1 };
+/* population storage / arithmetic:
+ *   FP64: f stored and computed in FP64, potential in FP64;
+ *   FP32: f stored as FP32 deviations d = f - w, FP32 arithmetic;
+ *   BF16: f stored as BF16 deviations, FP32 arithmetic. */
+enum { ELBM_PREC_FP64 = 0, ELBM_PREC_FP32 = 1, ELBM_PREC_BF16 = 2 };
+/* arithmetic of the alpha root: FP64, or FP32 (working-precision root of the
+ * same equation, written without cancellation) */
+enum { ELBM_APREC_FP64 = 0, ELBM_APREC_FP32 = 1 };
+
+/* selectors for elbm_fields; selected blocks are written back to back in
+ * this bit order */
+#define ELBM_F_RHO   (1u << 0) /* N: density at the last completed step */
+#define ELBM_F_U     (1u << 1) /* 3N: half-step velocity (j + F/2)/rho, xyz per site */
+#define ELBM_F_PHI   (1u << 2) /* N: potential */
+#define ELBM_F_Q     (1u << 3) /* N: free charge (before neutralisation) */
+#define ELBM_F_ALPHA (1u << 4) /* N: entropic alpha */
+#define ELBM_F_NU    (1u << 5) /* N: Carreau viscosity */
+#define ELBM_F_POP   (1u << 6) /* 19N: populations f(r, t) after streaming */
+#define ELBM_F_GPOP  (1u << 7) /* 7N: charge populations g(r, t) (transport mode) */
+#define ELBM_F_DIAG  (1u << 8) /* ELBM_NDIAG diagnostics of the last step */
+
+/* diagnostics (FP64): 0 mass, 1-3 momentum sum (j + F/2), 4 total charge,
+ * 5 alpha min, 6 alpha max, 7 alpha mean, 8 near-equilibrium shortcuts,
+ * 9 no-root fallbacks, 10 clipped at the positivity bound, 11 Poisson
+ * sweeps, 12 Poisson relative residual, 13 max |h(alpha)|/rho as evaluated
+ * on the device, 14 max |u|, 15 non-finite count, 16 subtracted mean charge,
+ * 17 step counter, 18 Poisson sweeps summed over all steps, 19 reserved */
+#define ELBM_NDIAG 20
+
+typedef struct elbm_params {
+    int nx, ny, nz;              /* lattice (3-D, D3Q19) */
+    int face_bc[6];              /* ELBM_FACE_* ; opposite faces must agree when periodic */
+    int phi_bc[6];               /* ELBM_PHI_* ; PERIODIC exactly where face_bc is */
+    int phi_axis;                /* axis normal to the electrode planes (0,1,2) */
+    int charge_model;            /* ELBM_CHARGE_* */
+    int force_el;                /* ELBM_FEL_* */
+    int neutralize;              /* subtract the mean free charge before Poisson */
+    int poisson_maxit;           /* cap on red-black SOR sweeps per step */
+    int poisson_fixed_sweeps;    /* > 0: exactly this many sweeps, no convergence test */
+    int poisson_check_every;     /* convergence test every k sweeps (>= 1); with FP32
+                                    potentials a test interval without progress
+                                    (residual above 0.97 of the previous test)
+                                    ends the solve at its rounding floor */
+    int alpha_mode;              /* ELBM_ALPHA_* */
+    int precision;               /* ELBM_PREC_* */
+    int alpha_precision;         /* ELBM_APREC_* (FP64 precision forces FP64) */
+    int store_macro;             /* keep u, alpha, nu planes for elbm_fields */
+    int diag_every;              /* diagnostics every k steps (0 = never) */
+    int profile;                 /* time each pass with CUDA events (elbm_pass_times) */
+    double phi_lo, phi_hi;       /* potential on the ghost planes at axis coord -1 and n */
+    double phi_solid;            /* potential of interior solid (conductor) nodes */
+    double nu0, nu_inf, lambda, n_carreau;  /* Carreau law; n = 1 is Newtonian nu0 */
+    double G, Gw, rho0;          /* Shan-Chen couplings, psi = rho0 (1 - exp(-rho/rho0)) */
+    double eps_kappa;            /* permittivity eps = 1 + kappa rho / rho0 */
+    double sigma_liq, sigma_gas; /* conductivity per phase (transport mode) */
+    double Dq;                   /* charge diffusivity (transport mode) */
+    double E_ext[3];             /* uniform applied field */
+    double Q_b, Q_s, K_d;        /* Eq. (surface-q2) totals and curvature scale */
+    double xi_b, xi_s;           /* Eq. (surface-q3) coefficients */
+    double theta_width;          /* width of the smoothed Heaviside theta(rho; rho0) */
+    double sor_omega, poisson_tol;
+    double alpha_eq_tol;         /* max |Delta_p/f_p| below which alpha = 2; must be
+                                    >= 2^-18 when the arithmetic is FP32 */
+    double rho_in, rho_out;      /* densities of inlet / outlet nodes */
+    void *cuda_stream;           /* cudaStream_t of the caller (NULL: default stream) */
+} elbm_params;
+
+/* Initial state, all host arrays of N = nx*ny*nz sites (caller-owned):
+ *   mask  uint8 node kinds (NULL = all fluid);
+ *   rho0  FP64 initial density (required);
+ *   u0    FP64 3N initial velocity, xyz per site (NULL = at rest);
+ *   q0    FP64 initial free charge, transport mode (NULL = 0);
+ *   u_in  FP64 3N inlet velocity, read at inlet nodes (NULL = 0);
+ *   f0    FP64 19N populations f(r, 0) overriding the equilibrium start
+ *         (NULL = f^eq(rho0, u0), Eq. 2). */
+typedef struct elbm_init_fields {
+    const unsigned char *mask;
+    const double *rho0, *u0, *q0, *u_in, *f0;
+} elbm_init_fields;
+
+/* Validate the parameters, allocate the device state, build f(r, 0) (and
+ * g(r, 0) = w_i q0 (1 + c_i.u0/c_s^2) in transport mode), set phi = 0.
+ * n_instances must be 1. On success *out owns the new handle. */
+elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *init, int n_instances,
+                      elbm_handle **out);
+
+/* Advance nsteps >= 0 time steps on the handle's stream. Returns after the
+ * work is done; ELBM_E_NUMERIC if a non-finite value or rho <= 0 appeared,
+ * ELBM_W_POISSON_NOCONV if a Poisson solve hit its cap. */
+elbm_status elbm_step(elbm_handle *h, int nsteps);
+
+/* Copy the selected fields (ELBM_F_* bits) to the caller's host buffer out of
+ * out_len doubles, blocks back to back in bit order, converted to FP64.
+ * U, ALPHA and NU need store_macro = 1 (else ELBM_E_STATE); GPOP needs
+ * transport mode. ELBM_E_INVAL if out_len is too small. */
+elbm_status elbm_fields(elbm_handle *h, unsigned mask, double *out, size_t out_len);
+
+/* Number of doubles elbm_fields writes for this selector (0 on error). */
+size_t elbm_fields_size(const elbm_handle *h, unsigned mask);
+
+/* Per-pass device time accumulated since elbm_init when params.profile = 1,
+ * measured with CUDA events on the handle's stream around each pass:
+ * out[0] moments + charge ms, out[1] Poisson ms, out[2] collision ms,
+ * out[3] reductions ms, out[4] steps timed, out[5] collision launches,
+ * out[6] Poisson sweeps, out[7] kernel launches of all passes.
+ * Writes min(n, 8) values; ELBM_E_STATE when profiling is off. Not part of
+ * the paper's method: instrumentation for measuring the method's kernels. */
+elbm_status elbm_pass_times(const elbm_handle *h, double *out, int n);
+
+/* Release the handle and its device memory. NULL is a no-op. */
+void elbm_free(elbm_handle *h);
+
+/* Static text for a status code. */
+const char *elbm_strerror(int status);
+
+/* The D3Q19 velocity set of the library (host call, no GPU needed):
+ * c[3*p + a] and w[p] for p = 0..18; returns 19. */
+int elbm_velocity_set(int *c, double *w);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ELBM_H */

@@ -115,7 +115,8 @@ def lib():
                                          ctypes.POINTER(ctypes.c_int)]
         L.orc_efield.argtypes = [pp, u8p, dp, dp]
         L.orc_stream.argtypes = [pp, u8p, dp, dp, dp, dp, dp, dp]
-        L.orc_init.argtypes = [pp, u8p, dp, dp, dp, dp, dp, dp]
+        L.orc_init.argtypes = [pp, u8p, dp, dp, dp, dp, dp, dp, dp]
+        L.orc_apply_io.argtypes = [pp, u8p, dp, dp]
         L.orc_step.argtypes = [pp, u8p, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
         _lib = L
     return _lib
@@ -305,7 +306,10 @@ class Sim:
         self.P = make_params(cfg)
         self.N = _n(cfg)
         self.Q = Q_of(cfg["dim"])
-        self.mask = np.ascontiguousarray(fields["mask"], dtype=np.uint8).reshape(-1)
+        mask = fields.get("mask")
+        if mask is None:
+            mask = np.zeros(self.N, np.uint8)
+        self.mask = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
         self.u_in = np.ascontiguousarray(fields.get("u_in", np.zeros((self.N, 3))),
                                          dtype=np.float64).reshape(-1)
         rho0 = np.ascontiguousarray(fields["rho"], dtype=np.float64).reshape(-1)
@@ -318,11 +322,12 @@ class Sim:
         self.g = np.zeros(7 * self.N) if self.transport else None
         self.phi = np.zeros(self.N)
         rc = lib().orc_init(ctypes.byref(self.P), _u8(self.mask), _dp(rho0), _dp(u0),
-                            _dp(q0), _dp(self.f), _dp(self.g), _dp(self.phi))
+                            _dp(q0), _dp(self.u_in), _dp(self.f), _dp(self.g), _dp(self.phi))
         if rc != 0:
             raise ValueError(f"oracle rejected the parameters (code {rc})")
-        if "f" in fields:
+        if fields.get("f") is not None:
             self.f[:] = np.asarray(fields["f"], dtype=np.float64).reshape(-1)
+            lib().orc_apply_io(ctypes.byref(self.P), _u8(self.mask), _dp(self.u_in), _dp(self.f))
         self.rho = np.zeros(self.N)
         self.u = np.zeros(3 * self.N)
         self.q = np.zeros(self.N)

@@ -704,8 +704,32 @@ static int validate(const orc_params *p)
     return 0;
 }
 
+/* Populations of fluid sites that arrive from inlet / outlet nodes carry the
+ * boundary equilibria at every time level, the initial one included (the
+ * boundary nodes are sources of f^eq(rho_in, u_in) and f^eq(rho_out, 0)). */
+void orc_apply_io(const orc_params *p, const unsigned char *mask, const double *u_in, double *f)
+{
+    ctx_t C;
+    ctx_init(&C, p);
+    for (long s = 0; s < C.N; s++) {
+        if (mask[s] != ORC_FLUID) continue;
+        int x, y, z, face;
+        coords(&C, s, &x, &y, &z);
+        for (int k = 0; k < C.Q; k++) {
+            long src = nbr(&C, x, y, z, -C.c[k][0], -C.c[k][1], -C.c[k][2], &face);
+            if (src < 0 || (mask[src] != ORC_INLET && mask[src] != ORC_OUTLET)) continue;
+            double uio[3] = {0, 0, 0}, fe[19];
+            if (mask[src] == ORC_INLET && u_in)
+                for (int a = 0; a < 3; a++) uio[a] = u_in[3 * src + a];
+            orc_feq(p->dim, mask[src] == ORC_INLET ? p->rho_in : p->rho_out, uio, fe);
+            f[k * C.N + s] = fe[k];
+        }
+    }
+}
+
 int orc_init(const orc_params *p, const unsigned char *mask, const double *rho0_field,
-             const double *u0_field, const double *q0_field, double *f, double *g, double *phi)
+             const double *u0_field, const double *q0_field, const double *u_in,
+             double *f, double *g, double *phi)
 {
     if (validate(p)) return -1;
     ctx_t C;
@@ -729,6 +753,7 @@ int orc_init(const orc_params *p, const unsigned char *mask, const double *rho0_
         }
         phi[s] = 0.0;
     }
+    orc_apply_io(p, mask, u_in, f);
     return 0;
 }
 

@@ -101,7 +101,10 @@ void orc_stream(const orc_params *p, const unsigned char *mask, const double *u_
 /* ---------------- whole step ---------------- */
 int orc_init(const orc_params *p, const unsigned char *mask,
              const double *rho0_field, const double *u0_field,
-             const double *q0_field, double *f, double *g, double *phi);
+             const double *q0_field, const double *u_in, double *f, double *g,
+             double *phi);
+void orc_apply_io(const orc_params *p, const unsigned char *mask, const double *u_in,
+                  double *f);
 int orc_step(const orc_params *p, const unsigned char *mask,
              const double *u_in, double *f, double *g, double *phi,
              double *rho, double *u, double *q, double *alpha_out,

@@ -1,0 +1,544 @@
+// elbm_capi.cu -- the C ABI declared in include/elbm.h: parameter checks,
+// device state, the order of the passes of one step (Sec. II C of
+// arXiv:1612.05404) and field export. Every pass runs in the kernels of
+// k_fp64.cu / k_fp32.cu / k_bf16.cu; this file only sequences them, plus the
+// small deterministic reductions that turn per-block partial sums into the
+// global sums the step needs (mean charge, Poisson residual, diagnostics).
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "elbm.h"
+#include "elbm_internal.h"
+
+using namespace elbm;
+
+struct elbm_handle {
+    elbm_params p;
+    Geom g;
+    Phys ph;
+    Bufs b;
+    Launch L;
+    Ops ops;
+    cudaStream_t s;
+    int has_dirichlet;
+    double *pin;          // pinned host scalars (convergence flag, residual)
+    long long step;
+    int last_sweeps;
+    double last_resid;
+    double sweeps_total;
+    int noconv;
+    size_t pop_bytes, g_bytes, sc_bytes;
+    cudaEvent_t ev[5];    // pass boundaries when profiling
+    double pass_ms[4];
+    double prof_steps, prof_collide, prof_sweeps, launches;
+};
+
+namespace {
+
+enum { FIN_CHARGE_AB = 0, FIN_CHARGE_Q = 1, FIN_RESID = 2, FIN_PHI = 3, FIN_DIAG = 4 };
+
+// Sum (or min / max) each of the K columns of the per-block partials in a
+// fixed order, then derive the scalars of `mode`. One block of 256 threads:
+// run-to-run reproducible.
+__global__ void k_finalize(const double *part, int nblocks, int K, int mode, Phys ph,
+                           double *scal, double *diag, long long step)
+{
+    __shared__ double sh[256];
+    __shared__ double res[16];
+    const int t = threadIdx.x;
+    for (int k = 0; k < K; k++) {
+        int op = 0;  // 0 sum, 1 min, 2 max
+        if (mode == FIN_DIAG) {
+            if (k == D_AMIN) op = 1;
+            else if (k == D_AMAX || k == D_HERR || k == D_UMAX) op = 2;
+        }
+        double acc = op == 1 ? 1e300 : (op == 2 ? -1e300 : 0.0);
+        for (int i = t; i < nblocks; i += 256) {
+            double v = part[(long long)i * K + k];
+            acc = op == 0 ? acc + v : (op == 1 ? fmin(acc, v) : fmax(acc, v));
+        }
+        sh[t] = acc;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if (t < w) {
+                double a = sh[t], c = sh[t + w];
+                sh[t] = op == 0 ? a + c : (op == 1 ? fmin(a, c) : fmax(a, c));
+            }
+            __syncthreads();
+        }
+        if (t == 0) res[k] = sh[0];
+        __syncthreads();
+    }
+    if (t != 0) return;
+    if (mode == FIN_CHARGE_AB) {
+        scal[S_SA] = res[0];
+        scal[S_SB] = res[1];
+    } else if (mode == FIN_CHARGE_Q) {
+        scal[S_QSUM] = res[0];
+        scal[S_Q2] = res[1];
+        scal[S_QMEAN] = (ph.neutralize && ph.n_fluid > 0) ? res[0] / ph.n_fluid : 0.0;
+    } else if (mode == FIN_RESID) {
+        double rn = sqrt(res[0]), ref = sqrt(res[1]) + sqrt(res[2]);
+        scal[S_RESID] = ref > 0.0 ? rn / ref : rn;
+        scal[S_CONV] = (rn <= ph.tol * ref) ? 1.0 : 0.0;
+    } else if (mode == FIN_PHI) {
+        scal[S_PHISUM] = res[0];
+        scal[S_PHIMEAN] = res[0] / ph.n_unknown;
+    } else if (mode == FIN_DIAG) {
+        diag[0] = res[D_MASS];
+        diag[1] = res[D_MX];
+        diag[2] = res[D_MY];
+        diag[3] = res[D_MZ];
+        diag[4] = res[D_Q];
+        diag[5] = res[D_AMIN];
+        diag[6] = res[D_AMAX];
+        diag[7] = res[D_NFLUID] > 0 ? res[D_ASUM] / res[D_NFLUID] : 0.0;
+        diag[8] = res[D_NSHORT];
+        diag[9] = res[D_NNOROOT];
+        diag[10] = res[D_NCLIP];
+        diag[13] = res[D_HERR];
+        diag[14] = res[D_UMAX];
+        diag[15] = res[D_NBAD];
+        diag[16] = scal[S_QMEAN];
+        diag[17] = (double)step;
+    }
+}
+
+bool cuda_ok(cudaError_t e) { return e == cudaSuccess; }
+
+int validate(const elbm_params *p, const elbm_init_fields *in, int n_instances)
+{
+    if (!p || !in || !in->rho0 || n_instances != 1) return 1;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return 1;
+    if ((long long)p->nx * p->ny * p->nz > (1LL << 34)) return 1;
+    for (int f = 0; f < 6; f++) {
+        if (p->face_bc[f] != ELBM_FACE_PERIODIC && p->face_bc[f] != ELBM_FACE_WALL) return 1;
+        if (p->phi_bc[f] < ELBM_PHI_PERIODIC || p->phi_bc[f] > ELBM_PHI_NEUMANN) return 1;
+        if ((p->face_bc[f] == ELBM_FACE_PERIODIC) != (p->phi_bc[f] == ELBM_PHI_PERIODIC)) return 1;
+    }
+    for (int a = 0; a < 3; a++)
+        if ((p->face_bc[2 * a] == ELBM_FACE_PERIODIC) != (p->face_bc[2 * a + 1] == ELBM_FACE_PERIODIC)) return 1;
+    if (p->phi_axis < 0 || p->phi_axis > 2) return 1;
+    if (p->charge_model < ELBM_CHARGE_NONE || p->charge_model > ELBM_CHARGE_TRANSPORT) return 1;
+    if (p->force_el != ELBM_FEL_QE) return 1;
+    if (p->alpha_mode != ELBM_ALPHA_ENTROPIC && p->alpha_mode != ELBM_ALPHA_BGK) return 1;
+    if (p->precision < ELBM_PREC_FP64 || p->precision > ELBM_PREC_BF16) return 1;
+    if (p->alpha_precision != ELBM_APREC_FP64 && p->alpha_precision != ELBM_APREC_FP32) return 1;
+    if (!(p->nu0 > 0.0) || !(p->nu_inf > 0.0) || !(p->rho0 > 0.0)) return 1;
+    if (!(p->n_carreau > 0.0) || !(p->lambda >= 0.0)) return 1;
+    // FP32 arithmetic leaves about 3e-7 of noise in Delta_p/f_p; an alpha root
+    // sought below a few times that is a root of rounding noise
+    if (p->precision != ELBM_PREC_FP64 && !(p->alpha_eq_tol >= 0x1p-18)) return 1;
+    if (p->charge_model != ELBM_CHARGE_NONE) {
+        if (!(p->theta_width > 0.0) || !(p->K_d > 0.0)) return 1;
+        if (!(p->sor_omega > 0.0 && p->sor_omega < 2.0)) return 1;
+        if (!(p->poisson_tol >= 0.0) || p->poisson_maxit < 0 || p->poisson_fixed_sweeps < 0) return 1;
+        // red-black ordering needs even periodic extents
+        int n[3] = {p->nx, p->ny, p->nz};
+        for (int a = 0; a < 3; a++)
+            if (p->face_bc[2 * a] == ELBM_FACE_PERIODIC && (n[a] & 1) && n[a] > 1) return 1;
+    }
+    if (p->charge_model == ELBM_CHARGE_TRANSPORT && !(p->Dq >= 0.0)) return 1;
+    if (p->diag_every < 0) return 1;
+    return 0;
+}
+
+void free_bufs(elbm_handle *h)
+{
+    void *ptrs[] = {h->b.fA, h->b.fB, h->b.gA, h->b.gB, h->b.rho, h->b.q, h->b.phi, h->b.ux,
+                    h->b.uy, h->b.uz, h->b.alpha, h->b.nu, h->b.mask, h->b.nh, h->b.ab,
+                    h->b.part, h->b.scal, h->b.diag};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    if (h->pin) cudaFreeHost(h->pin);
+    for (int i = 0; i < 5; i++)
+        if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+}
+
+void finalize(elbm_handle *h, int K, int mode)
+{
+    h->launches += 1;
+    k_finalize<<<1, 256, 0, h->s>>>(h->b.part, h->L.nblocks, K, mode, h->ph, h->b.scal, h->b.diag, h->step);
+}
+
+elbm_status poisson(elbm_handle *h)
+{
+    const Ops &o = h->ops;
+    const int fixed = h->p.poisson_fixed_sweeps;
+    const int ce = h->p.poisson_check_every > 0 ? h->p.poisson_check_every : 8;
+    const int maxit = h->p.poisson_maxit;
+    int k = 0;
+    bool conv = false, checked_last = false;
+    double prev = -1.0;
+    for (;;) {
+        if (fixed > 0) {
+            if (k >= fixed) break;
+        } else if (k % ce == 0 || k >= maxit) {
+            o.resid(h->g, h->ph, h->b, h->L, h->s);
+            h->launches += 1;
+            finalize(h, 3, FIN_RESID);
+            if (!cuda_ok(cudaMemcpyAsync(h->pin, h->b.scal + S_RESID, 2 * sizeof(double),
+                                         cudaMemcpyDeviceToHost, h->s)))
+                return ELBM_E_CUDA;
+            if (!cuda_ok(cudaStreamSynchronize(h->s))) return ELBM_E_CUDA;
+            h->last_resid = h->pin[0];
+            conv = h->pin[1] != 0.0;
+            // reduced precision: the FP32 potential has a rounding floor; a
+            // check interval without progress means the floor is reached
+            if (!conv && h->p.precision != ELBM_PREC_FP64 && prev >= 0.0 && h->pin[0] > 0.97 * prev)
+                conv = true;
+            prev = h->pin[0];
+            checked_last = true;
+            if (conv || k >= maxit) break;
+        }
+        o.sor(h->g, h->ph, h->b, 0, h->L, h->s);
+        o.sor(h->g, h->ph, h->b, 1, h->L, h->s);
+        h->launches += 2;
+        checked_last = false;
+        k++;
+    }
+    if (fixed == 0 && !conv) h->noconv = 1;
+    if (!h->has_dirichlet) {
+        o.phi_mean(h->g, h->ph, h->b, 0, h->L, h->s);
+        finalize(h, 1, FIN_PHI);
+        o.phi_mean(h->g, h->ph, h->b, 1, h->L, h->s);
+        h->launches += 2;
+    }
+    if (!checked_last) {
+        o.resid(h->g, h->ph, h->b, h->L, h->s);
+        h->launches += 1;
+        finalize(h, 3, FIN_RESID);
+        h->last_resid = -1.0;  // read lazily from the device scalars
+    }
+    h->last_sweeps = k;
+    h->sweeps_total += k;
+    return ELBM_OK;
+}
+
+elbm_status one_step(elbm_handle *h, bool diag)
+{
+    const Ops &o = h->ops;
+    const bool prof = h->p.profile != 0;
+    if (prof) cudaEventRecord(h->ev[0], h->s);
+    o.moments(h->g, h->ph, h->b, h->L, h->s);
+    h->launches += 1;
+    const int cm = h->p.charge_model;
+    if (cm == ELBM_CHARGE_TRANSPORT) {
+        finalize(h, 2, FIN_CHARGE_Q);
+    } else if (cm == ELBM_CHARGE_CONSERVED || cm == ELBM_CHARGE_XI) {
+        o.charge(h->g, h->ph, h->b, 0, h->L, h->s);
+        finalize(h, 2, FIN_CHARGE_AB);
+        o.charge(h->g, h->ph, h->b, 1, h->L, h->s);
+        finalize(h, 2, FIN_CHARGE_Q);
+        h->launches += 3;
+    }
+    if (prof) cudaEventRecord(h->ev[1], h->s);
+    int sweeps0 = (int)h->sweeps_total;
+    if (cm != ELBM_CHARGE_NONE) {
+        elbm_status st = poisson(h);
+        if (st != ELBM_OK) return st;
+    }
+    if (prof) cudaEventRecord(h->ev[2], h->s);
+    o.collide(h->g, h->ph, h->b, diag ? 1 : 0, h->L, h->s);
+    h->launches += 1;
+    if (prof) cudaEventRecord(h->ev[3], h->s);
+    if (diag) finalize(h, D_NPART, FIN_DIAG);
+    if (prof) {
+        cudaEventRecord(h->ev[4], h->s);
+        if (!cuda_ok(cudaEventSynchronize(h->ev[4]))) return ELBM_E_CUDA;
+        float ms[4];
+        for (int i = 0; i < 4; i++) cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]);
+        for (int i = 0; i < 4; i++) h->pass_ms[i] += ms[i];
+        h->prof_steps += 1;
+        h->prof_collide += 1;
+        h->prof_sweeps += h->sweeps_total - sweeps0;
+    }
+    void *t = h->b.fA; h->b.fA = h->b.fB; h->b.fB = t;
+    t = h->b.gA; h->b.gA = h->b.gB; h->b.gB = t;
+    h->step++;
+    return cuda_ok(cudaGetLastError()) ? ELBM_OK : ELBM_E_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *elbm_strerror(int st)
+{
+    switch (st) {
+    case ELBM_OK: return "ok";
+    case ELBM_W_POISSON_NOCONV: return "Poisson solve reached its sweep cap";
+    case ELBM_E_INVAL: return "invalid argument";
+    case ELBM_E_NOMEM: return "out of memory";
+    case ELBM_E_CUDA: return "CUDA runtime error";
+    case ELBM_E_NUMERIC: return "non-finite value or non-positive density";
+    case ELBM_E_STATE: return "request not possible in this state";
+    default: return "unknown status";
+    }
+}
+
+int elbm_velocity_set(int *c, double *w)
+{
+    for (int p = 0; p < Q; p++) {
+        if (c) { c[3 * p] = cx(p); c[3 * p + 1] = cy(p); c[3 * p + 2] = cz(p); }
+        if (w) w[p] = wq(p);
+    }
+    return Q;
+}
+
+elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_instances,
+                      elbm_handle **out)
+{
+    if (!out) return ELBM_E_INVAL;
+    *out = nullptr;
+    if (validate(p, in, n_instances)) return ELBM_E_INVAL;
+    elbm_handle *h = new (std::nothrow) elbm_handle;
+    if (!h) return ELBM_E_NOMEM;
+    std::memset(h, 0, sizeof(*h));
+    h->p = *p;
+    h->s = (cudaStream_t)p->cuda_stream;
+    const long long N = (long long)p->nx * p->ny * p->nz;
+
+    Geom &g = h->g;
+    g.nx = p->nx; g.ny = p->ny; g.nz = p->nz; g.N = N;
+    for (int a = 0; a < 3; a++) g.per[a] = p->face_bc[2 * a] == ELBM_FACE_PERIODIC;
+    for (int f = 0; f < 6; f++) g.phi_kind[f] = p->phi_bc[f];
+    g.phi_axis = p->phi_axis;
+    g.phi_lo = p->phi_lo; g.phi_hi = p->phi_hi; g.phi_solid = p->phi_solid;
+
+    long long n_fluid = N, n_solid = 0;
+    if (in->mask) {
+        n_fluid = 0;
+        for (long long i = 0; i < N; i++) {
+            if (in->mask[i] > ELBM_NODE_OUTLET) { delete h; return ELBM_E_INVAL; }
+            if (in->mask[i] == ELBM_NODE_FLUID) n_fluid++;
+            if (in->mask[i] == ELBM_NODE_SOLID) n_solid++;
+            if (in->mask[i] != ELBM_NODE_FLUID) g.has_mask = 1;
+        }
+    }
+    h->has_dirichlet = n_solid > 0;
+    for (int f = 0; f < 6; f++)
+        if (p->phi_bc[f] == ELBM_PHI_DIRICHLET) h->has_dirichlet = 1;
+
+    Phys &ph = h->ph;
+    ph.G = p->G; ph.Gw = p->Gw; ph.rho0 = p->rho0; ph.eps_kappa = p->eps_kappa;
+    ph.sigma_liq = p->sigma_liq; ph.sigma_gas = p->sigma_gas;
+    ph.tau_q = 0.5 + p->Dq / CS2Q;
+    for (int a = 0; a < 3; a++) ph.E_ext[a] = p->E_ext[a];
+    ph.Q_b = p->Q_b; ph.Q_s = p->Q_s; ph.K_d = p->K_d; ph.xi_b = p->xi_b; ph.xi_s = p->xi_s;
+    ph.theta_width = p->theta_width;
+    ph.omega = p->sor_omega; ph.tol = p->poisson_tol; ph.eq_tol = p->alpha_eq_tol;
+    ph.rho_in = p->rho_in; ph.rho_out = p->rho_out;
+    ph.n_fluid = (double)n_fluid;
+    ph.n_unknown = (double)(N - n_solid);
+    ph.charge_model = p->charge_model; ph.force_el = p->force_el; ph.alpha_mode = p->alpha_mode;
+    ph.aprec = p->precision == ELBM_PREC_FP64 ? ELBM_APREC_FP64 : p->alpha_precision;
+    ph.store_macro = p->store_macro; ph.neutralize = p->neutralize;
+    ph.rheo.nu0 = p->nu0; ph.rheo.nu_inf = p->nu_inf; ph.rheo.lambda = p->lambda; ph.rheo.n = p->n_carreau;
+    ph.rheo.newtonian = (p->n_carreau == 1.0 || p->lambda == 0.0 || p->nu0 == p->nu_inf) ? 1 : 0;
+
+    Launch &L = h->L;
+    int bx = p->nx >= 128 ? 128 : ((p->nx + 31) / 32) * 32;
+    int by = 128 / bx;
+    L.block = dim3(bx, by, 1);
+    L.grid = dim3((p->nx + bx - 1) / bx, (p->ny + by - 1) / by, p->nz);
+    L.nblocks = (int)(L.grid.x * L.grid.y * L.grid.z);
+    if (L.grid.y > 65535 || L.grid.z > 65535) { delete h; return ELBM_E_INVAL; }
+
+    switch (p->precision) {
+    case ELBM_PREC_FP64: h->ops = ops_fp64(); h->pop_bytes = 8; h->sc_bytes = 8; h->g_bytes = 8; break;
+    case ELBM_PREC_FP32: h->ops = ops_fp32(); h->pop_bytes = 4; h->sc_bytes = 4; h->g_bytes = 4; break;
+    default: h->ops = ops_bf16(); h->pop_bytes = 2; h->sc_bytes = 4; h->g_bytes = 4; break;
+    }
+
+    Bufs &b = h->b;
+    bool ok = true;
+    auto alloc = [&](void **ptr, size_t bytes) {
+        if (!ok) return;
+        if (!cuda_ok(cudaMalloc(ptr, bytes))) { ok = false; *ptr = nullptr; return; }
+        if (!cuda_ok(cudaMemsetAsync(*ptr, 0, bytes, h->s))) ok = false;
+    };
+    const bool transport = p->charge_model == ELBM_CHARGE_TRANSPORT;
+    alloc(&b.fA, (size_t)Q * N * h->pop_bytes);
+    alloc(&b.fB, (size_t)Q * N * h->pop_bytes);
+    if (transport) {
+        alloc(&b.gA, (size_t)Q7 * N * h->g_bytes);
+        alloc(&b.gB, (size_t)Q7 * N * h->g_bytes);
+    }
+    alloc(&b.rho, (size_t)N * h->sc_bytes);
+    alloc(&b.q, (size_t)N * h->sc_bytes);
+    alloc(&b.phi, (size_t)N * h->sc_bytes);
+    if (p->store_macro) {
+        alloc(&b.ux, (size_t)N * h->sc_bytes);
+        alloc(&b.uy, (size_t)N * h->sc_bytes);
+        alloc(&b.uz, (size_t)N * h->sc_bytes);
+        alloc(&b.alpha, (size_t)N * h->sc_bytes);
+        alloc(&b.nu, (size_t)N * h->sc_bytes);
+    }
+    if (g.has_mask) alloc((void **)&b.mask, (size_t)N);
+    if (p->charge_model == ELBM_CHARGE_CONSERVED || p->charge_model == ELBM_CHARGE_XI) {
+        alloc(&b.nh, (size_t)4 * N * h->sc_bytes);
+        alloc(&b.ab, (size_t)2 * N * h->sc_bytes);
+    }
+    alloc((void **)&b.part, (size_t)L.nblocks * D_NPART * sizeof(double));
+    alloc((void **)&b.scal, S_NSCAL * sizeof(double));
+    alloc((void **)&b.diag, ELBM_NDIAG * sizeof(double));
+    if (ok && !cuda_ok(cudaMallocHost((void **)&h->pin, 16 * sizeof(double)))) ok = false;
+    if (ok && p->profile)
+        for (int i = 0; i < 5; i++)
+            if (!cuda_ok(cudaEventCreate(&h->ev[i]))) ok = false;
+    if (!ok) { free_bufs(h); delete h; return ELBM_E_NOMEM; }
+
+    // upload the initial fields into temporaries and build f(r, 0)
+    double *d_rho0 = nullptr, *d_u0 = nullptr, *d_f0 = nullptr, *d_uin = nullptr, *d_q0 = nullptr;
+    auto up = [&](double **dst, const double *src, size_t n) {
+        if (!ok || !src) return;
+        if (!cuda_ok(cudaMalloc((void **)dst, n * sizeof(double)))) { ok = false; return; }
+        if (!cuda_ok(cudaMemcpyAsync(*dst, src, n * sizeof(double), cudaMemcpyHostToDevice, h->s))) ok = false;
+    };
+    up(&d_rho0, in->rho0, N);
+    up(&d_u0, in->u0, 3 * N);
+    up(&d_f0, in->f0, (size_t)Q * N);
+    up(&d_uin, in->u_in, 3 * N);
+    if (transport) up(&d_q0, in->q0, N);
+    if (ok && b.mask && !cuda_ok(cudaMemcpyAsync(b.mask, in->mask, N, cudaMemcpyHostToDevice, h->s))) ok = false;
+    if (ok) {
+        h->ops.init_pop(g, ph, b, d_rho0, d_u0, d_f0, d_uin, d_q0, L, h->s);
+        if (!cuda_ok(cudaGetLastError()) || !cuda_ok(cudaStreamSynchronize(h->s))) ok = false;
+    }
+    double *tmps[] = {d_rho0, d_u0, d_f0, d_uin, d_q0};
+    for (double *t : tmps)
+        if (t) cudaFree(t);
+    if (!ok) { free_bufs(h); delete h; return ELBM_E_CUDA; }
+    *out = h;
+    return ELBM_OK;
+}
+
+elbm_status elbm_step(elbm_handle *h, int nsteps)
+{
+    if (!h || nsteps < 0) return ELBM_E_INVAL;
+    h->noconv = 0;
+    for (int i = 0; i < nsteps; i++) {
+        bool diag = h->p.diag_every > 0 && (((h->step + 1) % h->p.diag_every) == 0 || i == nsteps - 1);
+        elbm_status st = one_step(h, diag);
+        if (st != ELBM_OK) return st;
+    }
+    if (!cuda_ok(cudaStreamSynchronize(h->s))) return ELBM_E_CUDA;
+    if (nsteps > 0 && h->p.diag_every > 0) {
+        double bad = 0.0;
+        if (!cuda_ok(cudaMemcpy(&bad, h->b.diag + 15, sizeof(double), cudaMemcpyDeviceToHost))) return ELBM_E_CUDA;
+        if (bad != 0.0) return ELBM_E_NUMERIC;
+    }
+    return h->noconv ? ELBM_W_POISSON_NOCONV : ELBM_OK;
+}
+
+size_t elbm_fields_size(const elbm_handle *h, unsigned mask)
+{
+    if (!h) return 0;
+    size_t N = (size_t)h->g.N, n = 0;
+    if (mask & ELBM_F_RHO) n += N;
+    if (mask & ELBM_F_U) n += 3 * N;
+    if (mask & ELBM_F_PHI) n += N;
+    if (mask & ELBM_F_Q) n += N;
+    if (mask & ELBM_F_ALPHA) n += N;
+    if (mask & ELBM_F_NU) n += N;
+    if (mask & ELBM_F_POP) n += (size_t)Q * N;
+    if (mask & ELBM_F_GPOP) n += (size_t)Q7 * N;
+    if (mask & ELBM_F_DIAG) n += ELBM_NDIAG;
+    return n;
+}
+
+elbm_status elbm_fields(elbm_handle *h, unsigned mask, double *out, size_t out_len)
+{
+    if (!h || !out) return ELBM_E_INVAL;
+    if (mask & ~0x1FFu) return ELBM_E_INVAL;
+    if (out_len < elbm_fields_size(h, mask)) return ELBM_E_INVAL;
+    if ((mask & (ELBM_F_U | ELBM_F_ALPHA | ELBM_F_NU)) && !h->p.store_macro) return ELBM_E_STATE;
+    if ((mask & ELBM_F_GPOP) && h->p.charge_model != ELBM_CHARGE_TRANSPORT) return ELBM_E_STATE;
+    const long long N = h->g.N;
+    size_t need = 0;
+    if (mask & (ELBM_F_RHO | ELBM_F_U | ELBM_F_PHI | ELBM_F_Q | ELBM_F_ALPHA | ELBM_F_NU)) need = (size_t)N;
+    if (mask & ELBM_F_POP) need = (size_t)Q * N;
+    if (mask & ELBM_F_GPOP) need = need > (size_t)Q7 * N ? need : (size_t)Q7 * N;
+    double *tmp = nullptr;
+    if (need && !cuda_ok(cudaMalloc((void **)&tmp, need * sizeof(double)))) return ELBM_E_NOMEM;
+    elbm_status st = ELBM_OK;
+    size_t off = 0;
+    auto plane = [&](const void *src) {
+        if (st != ELBM_OK) return;
+        h->ops.export_plane(src, tmp, N, h->s);
+        if (!cuda_ok(cudaMemcpyAsync(out + off, tmp, N * sizeof(double), cudaMemcpyDeviceToHost, h->s)) ||
+            !cuda_ok(cudaStreamSynchronize(h->s)))
+            st = ELBM_E_CUDA;
+        off += N;
+    };
+    if (mask & ELBM_F_RHO) plane(h->b.rho);
+    if ((mask & ELBM_F_U) && st == ELBM_OK) {
+        const void *c3[3] = {h->b.ux, h->b.uy, h->b.uz};
+        double *buf = (double *)std::malloc(N * sizeof(double));
+        if (!buf) st = ELBM_E_NOMEM;
+        for (int a = 0; a < 3 && st == ELBM_OK; a++) {
+            h->ops.export_plane(c3[a], tmp, N, h->s);
+            if (!cuda_ok(cudaMemcpyAsync(buf, tmp, N * sizeof(double), cudaMemcpyDeviceToHost, h->s)) ||
+                !cuda_ok(cudaStreamSynchronize(h->s))) { st = ELBM_E_CUDA; break; }
+            for (long long i = 0; i < N; i++) out[off + 3 * i + a] = buf[i];
+        }
+        std::free(buf);
+        off += 3 * N;
+    }
+    if (mask & ELBM_F_PHI) plane(h->b.phi);
+    if (mask & ELBM_F_Q) plane(h->b.q);
+    if (mask & ELBM_F_ALPHA) plane(h->b.alpha);
+    if (mask & ELBM_F_NU) plane(h->b.nu);
+    if ((mask & ELBM_F_POP) && st == ELBM_OK) {
+        h->ops.export_pop(h->g, h->b, tmp, h->L, h->s);
+        if (!cuda_ok(cudaMemcpyAsync(out + off, tmp, (size_t)Q * N * sizeof(double), cudaMemcpyDeviceToHost, h->s)) ||
+            !cuda_ok(cudaStreamSynchronize(h->s)))
+            st = ELBM_E_CUDA;
+        off += (size_t)Q * N;
+    }
+    if ((mask & ELBM_F_GPOP) && st == ELBM_OK) {
+        h->ops.export_gpop(h->g, h->b, tmp, h->L, h->s);
+        if (!cuda_ok(cudaMemcpyAsync(out + off, tmp, (size_t)Q7 * N * sizeof(double), cudaMemcpyDeviceToHost, h->s)) ||
+            !cuda_ok(cudaStreamSynchronize(h->s)))
+            st = ELBM_E_CUDA;
+        off += (size_t)Q7 * N;
+    }
+    if ((mask & ELBM_F_DIAG) && st == ELBM_OK) {
+        double sc[S_NSCAL];
+        if (!cuda_ok(cudaMemcpyAsync(out + off, h->b.diag, ELBM_NDIAG * sizeof(double), cudaMemcpyDeviceToHost, h->s)) ||
+            !cuda_ok(cudaMemcpyAsync(sc, h->b.scal, S_NSCAL * sizeof(double), cudaMemcpyDeviceToHost, h->s)) ||
+            !cuda_ok(cudaStreamSynchronize(h->s))) {
+            st = ELBM_E_CUDA;
+        } else {
+            out[off + 11] = h->last_sweeps;
+            out[off + 12] = sc[S_RESID];
+            out[off + 18] = h->sweeps_total;
+        }
+        off += ELBM_NDIAG;
+    }
+    if (tmp) cudaFree(tmp);
+    return st;
+}
+
+elbm_status elbm_pass_times(const elbm_handle *h, double *out, int n)
+{
+    if (!h || !out || n < 0) return ELBM_E_INVAL;
+    if (!h->p.profile) return ELBM_E_STATE;
+    double v[8] = {h->pass_ms[0], h->pass_ms[1], h->pass_ms[2], h->pass_ms[3], h->prof_steps,
+                   h->prof_collide, h->prof_sweeps, h->launches};
+    for (int i = 0; i < n && i < 8; i++) out[i] = v[i];
+    return ELBM_OK;
+}
+
+void elbm_free(elbm_handle *h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->s);
+    free_bufs(h);
+    delete h;
+}
+
+}  // extern "C"

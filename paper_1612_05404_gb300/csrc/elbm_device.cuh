@@ -1,0 +1,341 @@
+// elbm_device.cuh -- device-side building blocks of the charged entropic
+// lattice Boltzmann step of Lauricella et al. (arXiv:1612.05404), Sec. II:
+// precision traits, the D3Q19 / D3Q7 velocity sets, and the per-site physics
+// (Eq. 2 equilibrium, Eq. entropic alpha root, Eq. strain2 / carreau / beta
+// viscosity, the matrix 2-norm of the stress).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "elbm.h"
+
+namespace elbm {
+
+// ---------------------------------------------------------------------------
+// D3Q19 (the 3-D set with c_s^2 = 1/3 of the paper's D2Q9): rest, 6 axis
+// links, 12 face diagonals. The order is the library's public population
+// order (elbm_velocity_set). Components are encoded as characters '0'/'1'/'2'
+// for -1/0/+1 so that an unrolled loop folds them to constants.
+// ---------------------------------------------------------------------------
+constexpr int Q = 19;
+__host__ __device__ constexpr int cx(int p) { return "1201111202020201111"[p] - '1'; }
+__host__ __device__ constexpr int cy(int p) { return "1112011200211112020"[p] - '1'; }
+__host__ __device__ constexpr int cz(int p) { return "1111120111120022002"[p] - '1'; }
+__host__ __device__ constexpr int opp(int p) { return p == 0 ? 0 : ((p & 1) ? p + 1 : p - 1); }
+__host__ __device__ constexpr double wq(int p) { return p == 0 ? 1.0 / 3.0 : (p < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
+constexpr double CS2 = 1.0 / 3.0;
+
+// D3Q7 for the charge advection-diffusion: rest 1/4, axis links 1/8, c_s^2 = 1/4.
+constexpr int Q7 = 7;
+__host__ __device__ constexpr int c7x(int i) { return "1201111"[i] - '1'; }
+__host__ __device__ constexpr int c7y(int i) { return "1112011"[i] - '1'; }
+__host__ __device__ constexpr int c7z(int i) { return "1111120"[i] - '1'; }
+__host__ __device__ constexpr double w7(int i) { return i == 0 ? 0.25 : 0.125; }
+constexpr double CS2Q = 0.25;
+
+// ---------------------------------------------------------------------------
+// Precision traits: storage type of the populations, arithmetic type, type
+// of the scalar planes (rho, q, phi), and whether populations are stored as
+// deviations d_p = f_p - w_p from the rest-state equilibrium.
+// ---------------------------------------------------------------------------
+template <int PR> struct Tr;
+template <> struct Tr<ELBM_PREC_FP64> {
+    typedef double st; typedef double ct; typedef double sc; typedef double gt;
+    static constexpr bool dev = false;
+};
+template <> struct Tr<ELBM_PREC_FP32> {
+    typedef float st; typedef float ct; typedef float sc; typedef float gt;
+    static constexpr bool dev = true;
+};
+template <> struct Tr<ELBM_PREC_BF16> {
+    typedef __nv_bfloat16 st; typedef float ct; typedef float sc; typedef float gt;
+    static constexpr bool dev = true;
+};
+
+__device__ __forceinline__ float to_ct(float v) { return v; }
+__device__ __forceinline__ double to_ct(double v) { return v; }
+__device__ __forceinline__ float to_ct(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename S> __device__ __forceinline__ S from_ct(float v);
+template <> __device__ __forceinline__ float from_ct<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_ct<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <typename S> __device__ __forceinline__ S from_ct(double v);
+template <> __device__ __forceinline__ double from_ct<double>(double v) { return v; }
+
+// ---------------------------------------------------------------------------
+// Problem description passed by value to every kernel.
+// ---------------------------------------------------------------------------
+struct Geom {
+    int nx, ny, nz;
+    long long N;
+    int per[3];          // axis periodic (both faces)
+    int phi_kind[6];     // ELBM_PHI_* per face
+    int phi_axis;
+    int has_mask;        // any non-fluid node
+    double phi_lo, phi_hi, phi_solid;
+};
+
+// neighbour coordinate along one axis: -1 when it leaves through a wall face
+__device__ __forceinline__ int nbc(int v, int n, int per)
+{
+    if (v < 0) return per ? v + n : -1;
+    if (v >= n) return per ? v - n : -1;
+    return v;
+}
+
+// potential on the ghost node beyond face `face` seen from (x,y,z): the
+// electrode value on faces normal to phi_axis, the linear profile between
+// them on the other Dirichlet faces
+__device__ __forceinline__ double phi_ghost(const Geom &g, int face, int x, int y, int z)
+{
+    int axis = face >> 1;
+    if (axis == g.phi_axis) return (face & 1) ? g.phi_hi : g.phi_lo;
+    int c = g.phi_axis == 0 ? x : (g.phi_axis == 1 ? y : z);
+    int n = g.phi_axis == 0 ? g.nx : (g.phi_axis == 1 ? g.ny : g.nz);
+    return g.phi_lo + (c + 1.0) * (g.phi_hi - g.phi_lo) / (n + 1.0);
+}
+
+// ---------------------------------------------------------------------------
+// Eq. (2): f^eq_p = w_p rho (1 + P_p(u)), P_p(u) = c.u/c_s^2 + ((c.u)^2 - c_s^2 u^2)/(2 c_s^4)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T Ppoly(int p, T ux, T uy, T uz, T usq)
+{
+    T cu = T(cx(p)) * ux + T(cy(p)) * uy + T(cz(p)) * uz;
+    return T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq;
+}
+
+// ---------------------------------------------------------------------------
+// Matrix 2-norm of the symmetric stress (Sec. II B): max |eigenvalue|, by
+// the closed-form trigonometric solution of the characteristic cubic
+// (Smith 1961).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T sym3_norm2(T a00, T a11, T a22, T a01, T a02, T a12)
+{
+    T p1 = a01 * a01 + a02 * a02 + a12 * a12;
+    T q = (a00 + a11 + a22) / T(3);
+    T b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
+    T p2 = b00 * b00 + b11 * b11 + b22 * b22 + T(2) * p1;
+    if (p2 <= T(0)) return fabs(q);
+    if (p1 == T(0)) return fmax(fabs(a00), fmax(fabs(a11), fabs(a22)));
+    T pp = sqrt(p2 / T(6));
+    T ip = T(1) / pp;
+    b00 *= ip; b11 *= ip; b22 *= ip;
+    T c01 = a01 * ip, c02 = a02 * ip, c12 = a12 * ip;
+    T det = b00 * (b11 * b22 - c12 * c12) - c01 * (c01 * b22 - c12 * c02) + c02 * (c01 * c12 - b11 * c02);
+    T r = det / T(2);
+    r = fmin(T(1), fmax(T(-1), r));
+    T phi = acos(r) / T(3);
+    T e1 = q + T(2) * pp * cos(phi);
+    T e3 = q + T(2) * pp * cos(phi + T(2.0943951023931954923));
+    return fmax(fabs(e1), fabs(e3));
+}
+
+// ---------------------------------------------------------------------------
+// Carreau law Eq. (carreau) inside Eq. (strain2): gdot = A beta(nu(gdot)),
+// A = Pi alpha / (rho c_s^2), beta(nu) = c_s^2/(2 nu + c_s^2) (Eq. beta).
+// The root lies in [A beta(nu0), A beta(nu_inf)]; safeguarded Newton from the
+// left end of that bracket. Returns nu.
+// ---------------------------------------------------------------------------
+struct Rheo {
+    double nu0, nu_inf, lambda, n;
+    int newtonian;
+};
+
+template <typename T>
+__device__ __forceinline__ T carreau_nu(const Rheo &R, T Pn, T alpha, T rho)
+{
+    const T cs2 = T(1.0 / 3.0);
+    const T nu0 = T(R.nu0), nui = T(R.nu_inf), lam = T(R.lambda), en = T(R.n);
+    if (R.newtonian) return nu0;
+    T A = Pn * alpha / (rho * cs2);
+    if (A == T(0)) return nu0;
+    T lo = A * cs2 / (T(2) * nu0 + cs2), hi = A * cs2 / (T(2) * nui + cs2);
+    T x = lo, nux = nu0;
+    const T eps = sizeof(T) == 8 ? T(4e-16) : T(2e-7);
+    for (int it = 0; it < 100; it++) {
+        T lg = lam * x;
+        T base = T(1) + lg * lg;
+        T pw = pow(base, T(0.5) * (en - T(1)));
+        nux = nui + (nu0 - nui) * pw;
+        T den = T(2) * nux + cs2;
+        T gx = x - A * cs2 / den;
+        if (gx == T(0)) break;
+        if (gx < T(0)) lo = x; else hi = x;
+        T dnu = (nu0 - nui) * (en - T(1)) * lam * lam * x * pw / base;
+        T gp = T(1) - A * (T(-2) * cs2 / (den * den)) * dnu;
+        T xn = x - gx / gp;
+        if (!(xn > lo && xn < hi)) xn = T(0.5) * (lo + hi);
+        if (fabs(xn - x) <= eps * fabs(x) || hi - lo <= eps * hi) { x = xn; break; }
+        x = xn;
+    }
+    T lg = lam * x;
+    return nui + (nu0 - nui) * pow(T(1) + lg * lg, T(0.5) * (en - T(1)));
+}
+
+// ---------------------------------------------------------------------------
+// Entropic alpha, Eq. (entropic) with Eq. (H): the nontrivial root of
+//   h(a) = H(f + a D) - H(f) = sum_p [ f_p phi(a x_p) ] + a h'(0),
+//   x_p = D_p/f_p, phi(y) = (1+y) ln(1+y) - y,  h'(0) = sum_p D_p (1 + ln(f_p/w_p)).
+// h is convex with h(0) = 0, so h'(0) < 0 gives one root in (0, a_max], a_max
+// the positivity bound min_{D_p<0} -f_p/D_p. Status codes as in the
+// diagnostics: 0 root, 1 near-equilibrium shortcut, 2 no root (h'(0) >= 0),
+// 3 clipped at the positivity bound. The fallback in 1 and 2 is a = 2 (BGK).
+// ---------------------------------------------------------------------------
+struct AlphaOut { double alpha, herr; int status; };
+
+// FP64: same root as the plain definition, Newton in the sign bracket from 2.
+__device__ __forceinline__ AlphaOut alpha_fp64(const double *f, const double *d, double rho,
+                                               double eq_tol)
+{
+    AlphaOut o; o.alpha = 2.0; o.herr = 0.0; o.status = 0;
+    double x[Q], lnw[Q];
+    double maxabs = 0.0, amax = 1e300, a0 = 0.0;
+#pragma unroll
+    for (int p = 0; p < Q; p++) {
+        x[p] = d[p] / f[p];
+        maxabs = fmax(maxabs, fabs(x[p]));
+        if (d[p] < 0.0) amax = fmin(amax, -f[p] / d[p]);
+        lnw[p] = log(f[p] / wq(p));
+        a0 += d[p] * (1.0 + lnw[p]);
+    }
+    if (!(maxabs >= eq_tol)) { o.status = 1; return o; }
+    if (a0 >= 0.0) { o.status = 2; return o; }
+    auto hval = [&](double a, double *hp) {
+        double h = 0.0, g = 0.0;
+#pragma unroll
+        for (int p = 0; p < Q; p++) {
+            double y = a * x[p];
+            double l = log1p(y);
+            double t = (1.0 + y <= 0.0) ? 0.0 : (f[p] + a * d[p]) * l;
+            h += t + a * d[p] * lnw[p];
+            g += d[p] * (1.0 + lnw[p] + l);
+        }
+        *hp = g;
+        return h;
+    };
+    double lo = 0.0, hi, hp;
+    if (amax < 1e299) {
+        hi = amax * (1.0 - 1e-15);
+        if (hval(hi, &hp) < 0.0) { o.alpha = hi; o.status = 3; return o; }
+    } else {
+        hi = 4.0;
+        int k = 0;
+        while (hval(hi, &hp) < 0.0 && k++ < 100) hi *= 2.0;
+    }
+    double a = 2.0;
+    if (!(a > lo && a < hi)) a = 0.5 * (lo + hi);
+    double h = 0.0;
+    for (int it = 0; it < 100; it++) {
+        h = hval(a, &hp);
+        if (h == 0.0) break;
+        if (h < 0.0) lo = a; else hi = a;
+        double an = a - h / hp;
+        if (!(an > lo && an < hi)) an = 0.5 * (lo + hi);
+        if (fabs(an - a) <= 4e-16 * fabs(a) || hi - lo <= 4e-16 * hi) { a = an; break; }
+        a = an;
+    }
+    o.alpha = a;
+    o.herr = fabs(h) / rho;
+    return o;
+}
+
+// phi(y) = (1+y) ln(1+y) - y and ln(1+y) in FP32 without cancellation: the
+// alternating series for |y| < 1/16 (error below the FP32 unit roundoff),
+// the library log1pf otherwise.
+__device__ __forceinline__ void phi_log1p_f32(float y, float *phi, float *l)
+{
+    if (fabsf(y) < 0.0625f) {
+        // ln(1+y) = y - y^2/2 + y^3/3 - ... ; phi = y^2/2 - y^3/6 + y^4/12 - y^5/20 + y^6/30 - y^7/42
+        float y2 = y * y;
+        *l = y * (1.f + y * (-0.5f + y * (1.f / 3 + y * (-0.25f + y * (0.2f + y * (-1.f / 6 + y * (1.f / 7)))))));
+        *phi = y2 * (0.5f + y * (-1.f / 6 + y * (1.f / 12 + y * (-1.f / 20 + y * (1.f / 30 + y * (-1.f / 42))))));
+    } else {
+        float lg = log1pf(y);
+        *l = lg;
+        *phi = (1.f + y) * lg - y;
+    }
+}
+
+// FP32: the same root of the same equation, with h split into pieces that
+// carry no cancellation: sum_p f_p phi(a x_p) (non-negative terms) and
+// a h'(0), where h'(0) = (1 + ln rho) sum D + sum D_p ln(f_p/(w_p rho)) and
+// sum D is accumulated with an error-free transformation (TwoSum, Knuth).
+// Converges to working precision.
+__device__ __forceinline__ AlphaOut alpha_fp32(const float *f, const float *d, const float *fdev,
+                                               float rho, float drho, float eq_tol)
+{
+    AlphaOut o; o.alpha = 2.0; o.herr = 0.0; o.status = 0;
+    float x[Q];
+    float maxabs = 0.f, amax = 1e30f;
+    float s = 0.f, c = 0.f, tl = 0.f;
+    const float lr = logf(rho);
+#pragma unroll
+    for (int p = 0; p < Q; p++) {
+        x[p] = d[p] / f[p];
+        maxabs = fmaxf(maxabs, fabsf(x[p]));
+        if (d[p] < 0.f) amax = fminf(amax, -f[p] / d[p]);
+        // TwoSum of the running sum of D
+        float t = s + d[p];
+        float bp = t - s;
+        c += (s - (t - bp)) + (d[p] - bp);
+        s = t;
+        // ln(f_p/(w_p rho)) = log1p((d_p - w_p drho)/(w_p rho)) from the stored deviation
+        float wp = float(wq(p));
+        float z = (fdev[p] - wp * drho) / (wp * rho);
+        float lz, ph;
+        phi_log1p_f32(z, &ph, &lz);
+        tl += d[p] * lz;
+    }
+    float sumD = s + c;
+    float a0 = (1.f + lr) * sumD + tl;
+    if (!(maxabs >= eq_tol)) { o.status = 1; return o; }
+    if (a0 >= 0.f) { o.status = 2; return o; }
+    auto hval = [&](float a, float *hp) {
+        float h = 0.f, g = 0.f;
+#pragma unroll
+        for (int p = 0; p < Q; p++) {
+            float ph, l;
+            float y = a * x[p];
+            if (1.f + y <= 0.f) {
+                // at the positivity bound (1+y) ln(1+y) -> 0, so phi -> -y
+                ph = -y;
+                l = -88.f;
+            } else {
+                phi_log1p_f32(y, &ph, &l);
+            }
+            h += f[p] * ph;
+            g += d[p] * l;
+        }
+        *hp = g + a0;
+        return h + a * a0;
+    };
+    float lo = 0.f, hi, hp;
+    if (amax < 1e29f) {
+        hi = amax * (1.f - 1e-6f);
+        if (hval(hi, &hp) < 0.f) { o.alpha = hi; o.status = 3; return o; }
+    } else {
+        hi = 4.f;
+        int k = 0;
+        while (hval(hi, &hp) < 0.f && k++ < 60) hi *= 2.f;
+    }
+    float a = 2.f;
+    if (!(a > lo && a < hi)) a = 0.5f * (lo + hi);
+    float h = 0.f;
+    for (int it = 0; it < 40; it++) {
+        h = hval(a, &hp);
+        if (h == 0.f) break;
+        if (h < 0.f) lo = a; else hi = a;
+        float an = a - h / hp;
+        if (!(an > lo && an < hi)) an = 0.5f * (lo + hi);
+        if (fabsf(an - a) <= 2e-7f * fabsf(a) || hi - lo <= 2e-7f * hi) { a = an; break; }
+        a = an;
+    }
+    o.alpha = a;
+    o.herr = fabsf(h) / rho;
+    return o;
+}
+
+}  // namespace elbm

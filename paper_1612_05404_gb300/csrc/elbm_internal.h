@@ -1,0 +1,72 @@
+// elbm_internal.h -- host-side state of a handle and the per-precision kernel
+// launchers (implemented in k_fp64.cu / k_fp32.cu / k_bf16.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include "elbm.h"
+#include "elbm_device.cuh"
+
+namespace elbm {
+
+// slots of the device scalar array
+enum {
+    S_QSUM = 0, S_Q2, S_QMEAN, S_SA, S_SB, S_R2, S_RQ2, S_RB2, S_RESID, S_CONV,
+    S_PHISUM, S_PHIMEAN, S_NSCAL = 16
+};
+// per-block partial slots of the collision diagnostics
+enum {
+    D_MASS = 0, D_MX, D_MY, D_MZ, D_Q, D_AMIN, D_AMAX, D_ASUM, D_NSHORT, D_NNOROOT,
+    D_NCLIP, D_HERR, D_UMAX, D_NBAD, D_NFLUID, D_NPART = 16
+};
+
+struct Phys {
+    double G, Gw, rho0, eps_kappa, sigma_liq, sigma_gas, tau_q;
+    double E_ext[3];
+    double Q_b, Q_s, K_d, xi_b, xi_s, theta_width;
+    double omega, tol, eq_tol, rho_in, rho_out;
+    double n_fluid, n_unknown;
+    int charge_model, force_el, alpha_mode, aprec, store_macro, neutralize;
+    Rheo rheo;
+};
+
+struct Bufs {
+    void *fA, *fB, *gA, *gB;          // populations (current A, next B)
+    void *rho, *q, *phi;              // scalar planes
+    void *ux, *uy, *uz, *alpha, *nu;  // optional macroscopic planes
+    unsigned char *mask;              // node kinds (NULL when all fluid)
+    void *nh;                         // paper-mode charge: 4 planes n_x, n_y, n_z, |grad rho|^2
+    void *ab;                         // paper-mode charge: 2 planes a, b
+    double *part;                     // per-block partial sums
+    double *scal;                     // device scalars (S_*)
+    double *diag;                     // ELBM_NDIAG diagnostics
+};
+
+struct Launch {
+    dim3 block, grid;
+    int nblocks;
+};
+
+// Per-precision launchers. All enqueue on `s` and never synchronise.
+struct Ops {
+    void (*init_pop)(const Geom &, const Phys &, const Bufs &, const double *rho0,
+                     const double *u0, const double *f0, const double *u_in,
+                     const double *q0, const Launch &, cudaStream_t);
+    void (*moments)(const Geom &, const Phys &, const Bufs &, const Launch &, cudaStream_t);
+    // stage 0: gradient/normal and the per-site a, b with their block sums;
+    // stage 1: q from the finalised sums, with block sums of q and q^2
+    void (*charge)(const Geom &, const Phys &, const Bufs &, int stage, const Launch &, cudaStream_t);
+    void (*sor)(const Geom &, const Phys &, const Bufs &, int color, const Launch &, cudaStream_t);
+    void (*resid)(const Geom &, const Phys &, const Bufs &, const Launch &, cudaStream_t);
+    // stage 0: block sums of phi over non-solid nodes; stage 1: subtract S_PHIMEAN
+    void (*phi_mean)(const Geom &, const Phys &, const Bufs &, int stage, const Launch &, cudaStream_t);
+    void (*collide)(const Geom &, const Phys &, const Bufs &, int diag, const Launch &, cudaStream_t);
+    void (*export_pop)(const Geom &, const Bufs &, double *out, const Launch &, cudaStream_t);
+    void (*export_gpop)(const Geom &, const Bufs &, double *out, const Launch &, cudaStream_t);
+    void (*export_plane)(const void *plane, double *out, long long n, cudaStream_t);
+};
+
+Ops ops_fp64();
+Ops ops_fp32();
+Ops ops_bf16();
+
+}  // namespace elbm

@@ -1,0 +1,840 @@
+// elbm_kernels.cuh -- the kernels of one time step of the charged entropic
+// lattice Boltzmann method (arXiv:1612.05404, Sec. II C), templated on the
+// population precision. Each k_*.cu translation unit instantiates them for
+// one precision.
+//
+// Data layout: populations are planes [p][site] (site = x + nx (y + ny z)) in
+// two buffers A (read) and B (write); streaming is done by "pull": the step
+// reads f_p(r, t) = f*_p(r - c_p, t-1) from A and writes the post-collision
+// f*_p(r, t) to B at its own site, so every plane access is coalesced along x.
+// Halfway bounce-back turns a pull across a wall face or from a solid node
+// into a read of the opposite population of the site itself. Inlet and outlet
+// nodes hold their equilibria in both buffers, so a pull from them reads
+// f^eq(rho_in, u_in) or f^eq(rho_out, 0).
+#pragma once
+
+#include "elbm_internal.h"
+
+namespace elbm {
+
+typedef long long ll;
+
+// ---------------------------------------------------------------------------
+// Block reductions. FP64 precision reduces in FP64. The FP32 modes reduce
+// within a warp in FP32 with an error-free transformation (TwoSum, Knuth) so
+// the sums keep FP64-like accuracy without using GB300's slow FP64 pipe, then
+// combine the warps in FP64. Every thread of the block must call.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum(float v)
+{
+    float hi = v, lo = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float ohi = __shfl_down_sync(0xffffffffu, hi, o);
+        float olo = __shfl_down_sync(0xffffffffu, lo, o);
+        float sm, e;
+        two_sum(hi, ohi, sm, e);
+        hi = sm;
+        lo += olo + e;
+    }
+    return (double)hi + (double)lo;
+}
+
+template <int K, typename T>
+__device__ __forceinline__ void block_sums(const T (&v)[K], double *out)
+{
+    __shared__ double sh[K][8];
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int lane = tid & 31, wid = tid >> 5;
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        double w = warp_sum(v[k]);
+        if (lane == 0) sh[k][wid] = w;
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            double t = 0.0;
+            for (int i = 0; i < nw; i++) t += sh[k][i];
+            out[k] = t;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Neighbourhood of a site: coordinates for offsets -1, 0, +1 per axis (-1 when
+// the offset leaves through a wall face).
+// ---------------------------------------------------------------------------
+struct Nbr {
+    int xs[3], ys[3], zs[3];
+    ll s;
+};
+
+__device__ __forceinline__ void nbr_init(Nbr &n, const Geom &g, int x, int y, int z, ll s)
+{
+    n.xs[0] = nbc(x - 1, g.nx, g.per[0]); n.xs[1] = x; n.xs[2] = nbc(x + 1, g.nx, g.per[0]);
+    n.ys[0] = nbc(y - 1, g.ny, g.per[1]); n.ys[1] = y; n.ys[2] = nbc(y + 1, g.ny, g.per[1]);
+    n.zs[0] = nbc(z - 1, g.nz, g.per[2]); n.zs[1] = z; n.zs[2] = nbc(z + 1, g.nz, g.per[2]);
+    n.s = s;
+}
+
+// index of the site at offset (ox, oy, oz) in {-1,0,1}^3, or -1 beyond a wall
+__device__ __forceinline__ ll nbr_idx(const Nbr &n, const Geom &g, int ox, int oy, int oz)
+{
+    int a = n.xs[ox + 1], b = n.ys[oy + 1], c = n.zs[oz + 1];
+    if (a < 0 || b < 0 || c < 0) return -1;
+    return a + (ll)g.nx * (b + (ll)g.ny * c);
+}
+
+template <int PR>
+__device__ __forceinline__ typename Tr<PR>::ct ldp(const void *A, int p, ll idx, ll N)
+{
+    return to_ct(((const typename Tr<PR>::st *)A)[(ll)p * N + idx]);
+}
+
+// f_p(r, t): pull from r - c_p, bounce-back across walls and from solids.
+// FP64 returns f_p; the deviation modes return d_p = f_p - w_p.
+template <int PR>
+__device__ __forceinline__ typename Tr<PR>::ct gather_pop(const Geom &g, const unsigned char *mask,
+                                                          const void *A, const Nbr &n, int p)
+{
+    ll src = nbr_idx(n, g, -cx(p), -cy(p), -cz(p));
+    bool bb = src < 0;
+    if (!bb && mask) bb = mask[src] == ELBM_NODE_SOLID;
+    return bb ? ldp<PR>(A, opp(p), n.s, g.N) : ldp<PR>(A, p, src, g.N);
+}
+
+template <int PR>
+__device__ __forceinline__ typename Tr<PR>::gt gather_g(const Geom &g, const unsigned char *mask,
+                                                        const void *A, const Nbr &n, int i)
+{
+    typedef typename Tr<PR>::gt gt;
+    ll src = nbr_idx(n, g, -c7x(i), -c7y(i), -c7z(i));
+    bool bb = src < 0;
+    if (!bb && mask) bb = mask[src] == ELBM_NODE_SOLID;
+    int io = i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+    const gt *G = (const gt *)A;
+    return bb ? G[(ll)io * g.N + n.s] : G[(ll)i * g.N + src];
+}
+
+template <typename T>
+__device__ __forceinline__ T psi_of(T rho, T rho0) { return rho0 * (T(1) - exp(-rho / rho0)); }
+template <typename T>
+__device__ __forceinline__ T theta_of(T rho, T rho0, T w) { return T(0.5) * (T(1) + tanh((rho - rho0) / w)); }
+
+__device__ __forceinline__ void site_xyz(const Geom &g, int &x, int &y, int &z, bool &inb, ll &s)
+{
+    x = blockIdx.x * blockDim.x + threadIdx.x;
+    y = blockIdx.y * blockDim.y + threadIdx.y;
+    z = blockIdx.z;
+    inb = x < g.nx && y < g.ny;
+    s = inb ? x + (ll)g.nx * (y + (ll)g.ny * z) : 0;
+}
+__device__ __forceinline__ int block_id() { return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); }
+
+// Potential of the face neighbour along +-axis (Sec. II Poisson problem):
+// kind 0 = unknown (index in *nb), 1 = Dirichlet value in *v, 2 = no term.
+__device__ __forceinline__ int pois_nb(const Geom &g, const unsigned char *mask, const Nbr &n,
+                                       int x, int y, int z, int axis, int sign, ll *nb, double *v)
+{
+    int o[3] = {0, 0, 0};
+    o[axis] = sign;
+    ll i = nbr_idx(n, g, o[0], o[1], o[2]);
+    if (i < 0) {
+        int face = 2 * axis + (sign > 0 ? 1 : 0);
+        if (g.phi_kind[face] == ELBM_PHI_DIRICHLET) { *v = phi_ghost(g, face, x, y, z); return 1; }
+        return 2;
+    }
+    if (mask && mask[i] == ELBM_NODE_SOLID) { *v = g.phi_solid; return 1; }
+    *nb = i;
+    return 0;
+}
+
+// ===========================================================================
+// Initial state: f(r,0) = f^eq(rho0, u0) (Eq. 2) or the given f0, placed so
+// that the first pull returns it (inverse of the streaming map). Inlet /
+// outlet nodes hold their equilibria in A and B.
+// ===========================================================================
+template <int PR>
+__global__ void k_init_pop(Geom g, Phys ph, Bufs b, const double *rho0, const double *u0,
+                           const double *f0, const double *u_in, const double *q0)
+{
+    typedef Tr<PR> T;
+    typedef typename T::st st;
+    typedef typename T::sc sc;
+    typedef typename T::gt gt;
+    int x, y, z;
+    bool inb;
+    ll s;
+    site_xyz(g, x, y, z, inb, s);
+    if (!inb) return;
+    unsigned char kind = b.mask ? b.mask[s] : 0;
+    st *A = (st *)b.fA, *B = (st *)b.fB;
+    sc *rho = (sc *)b.rho;
+    if (kind == ELBM_NODE_SOLID) { rho[s] = sc(0); return; }
+    if (kind == ELBM_NODE_INLET || kind == ELBM_NODE_OUTLET) {
+        double r = kind == ELBM_NODE_INLET ? ph.rho_in : ph.rho_out;
+        double ux = 0, uy = 0, uz = 0;
+        if (kind == ELBM_NODE_INLET && u_in) { ux = u_in[3 * s]; uy = u_in[3 * s + 1]; uz = u_in[3 * s + 2]; }
+        double usq = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+        for (int p = 0; p < Q; p++) {
+            double fe = wq(p) * r * (1.0 + Ppoly<double>(p, ux, uy, uz, usq));
+            st v = T::dev ? from_ct<st>((typename T::ct)(fe - wq(p))) : from_ct<st>((typename T::ct)fe);
+            A[(ll)p * g.N + s] = v;
+            B[(ll)p * g.N + s] = v;
+        }
+        rho[s] = sc(r);
+        return;
+    }
+    Nbr n;
+    nbr_init(n, g, x, y, z, s);
+    double ux = 0, uy = 0, uz = 0;
+    if (u0) { ux = u0[3 * s]; uy = u0[3 * s + 1]; uz = u0[3 * s + 2]; }
+    double usq = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+    for (int p = 0; p < Q; p++) {
+        double fp = f0 ? f0[(ll)p * g.N + s] : wq(p) * rho0[s] * (1.0 + Ppoly<double>(p, ux, uy, uz, usq));
+        st v = T::dev ? from_ct<st>((typename T::ct)(fp - wq(p))) : from_ct<st>((typename T::ct)fp);
+        ll src = nbr_idx(n, g, -cx(p), -cy(p), -cz(p));
+        unsigned char k2 = (src >= 0 && b.mask) ? b.mask[src] : 0;
+        if (src < 0 || k2 == ELBM_NODE_SOLID) A[(ll)opp(p) * g.N + s] = v;
+        else if (k2 == ELBM_NODE_FLUID) A[(ll)p * g.N + src] = v;
+    }
+    if (b.gA) {
+        gt *GA = (gt *)b.gA;
+        double qv = q0 ? q0[s] : 0.0;
+#pragma unroll
+        for (int i = 0; i < Q7; i++) {
+            double cu = c7x(i) * ux + c7y(i) * uy + c7z(i) * uz;
+            gt v = (gt)(w7(i) * qv * (1.0 + cu / CS2Q));
+            ll src = nbr_idx(n, g, -c7x(i), -c7y(i), -c7z(i));
+            unsigned char k2 = (src >= 0 && b.mask) ? b.mask[src] : 0;
+            int io = i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+            if (src < 0 || k2 == ELBM_NODE_SOLID) GA[(ll)io * g.N + s] = v;
+            else if (k2 == ELBM_NODE_FLUID) GA[(ll)i * g.N + src] = v;
+        }
+    }
+}
+
+// ===========================================================================
+// Moments: rho = sum_p f_p (Sec. II), and in transport mode q = sum_i g_i with
+// the per-block sums of q and q^2 (neutralisation, Poisson reference norm).
+// ===========================================================================
+template <int PR>
+__global__ void __launch_bounds__(128) k_moments(Geom g, Phys ph, Bufs b)
+{
+    typedef Tr<PR> T;
+    typedef typename T::ct ct;
+    typedef typename T::sc sc;
+    typedef typename T::gt gt;
+    int x, y, z;
+    bool inb;
+    ll s;
+    site_xyz(g, x, y, z, inb, s);
+    bool active = inb && (!b.mask || b.mask[s] == ELBM_NODE_FLUID);
+    gt qv = 0, q2 = 0;
+    if (active) {
+        Nbr n;
+        nbr_init(n, g, x, y, z, s);
+        ct rs = 0;
+#pragma unroll
+        for (int p = 0; p < Q; p++) rs += gather_pop<PR>(g, b.mask, b.fA, n, p);
+        ((sc *)b.rho)[s] = sc(T::dev ? ct(1) + rs : rs);
+        if (ph.charge_model == ELBM_CHARGE_TRANSPORT) {
+            gt qs = 0;
+#pragma unroll
+            for (int i = 0; i < Q7; i++) qs += gather_g<PR>(g, b.mask, b.gA, n, i);
+            ((sc *)b.q)[s] = sc(qs);
+            qv = qs;
+            q2 = qs * qs;
+        }
+    }
+    if (ph.charge_model == ELBM_CHARGE_TRANSPORT) {
+        gt v[2] = {qv, q2};
+        block_sums<2>(v, b.part + 2 * block_id());
+    }
+}
+
+// ===========================================================================
+// Free charge, Eqs. (surface-q2) / (surface-q3): lattice gradient of rho,
+// interface normal, mean curvature K = -div n (positive on convex drops).
+// A solid or out-of-domain neighbour takes the site's own value.
+// ===========================================================================
+template <int PR>
+__global__ void __launch_bounds__(128) k_charge_grad(Geom g, Phys ph, Bufs b)
+{
+    typedef typename Tr<PR>::sc sc;
+    int x, y, z;
+    bool inb;
+    ll s;
+    site_xyz(g, x, y, z, inb, s);
+    if (!inb) return;
+    if (b.mask && b.mask[s] == ELBM_NODE_SOLID) return;
+    Nbr n;
+    nbr_init(n, g, x, y, z, s);
+    const sc *rho = (const sc *)b.rho;
+    sc rs = rho[s];
+    sc gx = 0, gy = 0, gz = 0;
+#pragma unroll
+    for (int p = 1; p < Q; p++) {
+        ll nb = nbr_idx(n, g, cx(p), cy(p), cz(p));
+        sc v = (nb < 0 || (b.mask && b.mask[nb] == ELBM_NODE_SOLID)) ? rs : rho[nb];
+        sc wv = sc(wq(p)) * v / sc(CS2);
+        gx += wv * sc(cx(p));
+        gy += wv * sc(cy(p));
+        gz += wv * sc(cz(p));
+    }
+    sc g2 = gx * gx + gy * gy + gz * gz;
+    sc gn = sqrt(g2);
+    if (gn < sc(1e-12)) gn = sc(1e-12);
+    sc *nh = (sc *)b.nh;
+    nh[s] = gx / gn;
+    nh[g.N + s] = gy / gn;
+    nh[2 * g.N + s] = gz / gn;
+    nh[3 * g.N + s] = g2;
+}
+
+template <int PR>
+__global__ void __launch_bounds__(128) k_charge_ab(Geom g, Phys ph, Bufs b)
+{
+    typedef typename Tr<PR>::sc sc;
+    int x, y, z;
+    bool inb;
+    ll s;
+    site_xyz(g, x, y, z, inb, s);
+    bool active = inb && (!b.mask || b.mask[s] == ELBM_NODE_FLUID);
+    sc av = 0, bv = 0;
+    if (active) {
+        Nbr n;
+        nbr_init(n, g, x, y, z, s);
+        const sc *nh = (const sc *)b.nh;
+        sc div = 0;
+#pragma unroll
+        for (int p = 1; p < Q; p++) {
+            ll nb = nbr_idx(n, g, cx(p), cy(p), cz(p));
+            ll src = (nb < 0 || (b.mask && b.mask[nb] == ELBM_NODE_SOLID)) ? s : nb;
+            sc wv = sc(wq(p)) / sc(CS2);
+            div += wv * (nh[src] * sc(cx(p)) + nh[g.N + src] * sc(cy(p)) + nh[2 * g.N + src] * sc(cz(p)));
+        }
+        sc K = -div;
+        sc kp = K > sc(0) ? K : sc(0);
+        sc r = ((const sc *)b.rho)[s];
+        av = r * theta_of<sc>(r, sc(ph.rho0), sc(ph.theta_width));
+        bv = nh[3 * g.N + s] * (sc(1) + pow(kp / sc(ph.K_d), sc(0.25)));
+        sc *ab = (sc *)b.ab;
+        ab[s] = av;
+        ab[g.N + s] = bv;
+    }
+    sc v[2] = {av, bv};
+    block_sums<2>(v, b.part + 2 * block_id());
+}
+
+template <int PR>
+__global__ void __launch_bounds__(128) k_charge_q(Geom g, Phys ph, Bufs b)
+{
+    typedef typename Tr<PR>::sc sc;
+    int x, y, z;
+    bool inb;
+    ll s;
+    site_xyz(g, x, y, z, inb, s);
+    bool active = inb && (!b.mask || b.mask[s] == ELBM_NODE_FLUID);
+    sc qv = 0;
+    if (active) {
+        const sc *ab = (const sc *)b.ab;
+        if (ph.charge_model == ELBM_CHARGE_CONSERVED) {
+            double Sa = b.scal[S_SA], Sb = b.scal[S_SB];
+            qv = (Sa > 0.0 ? sc(ph.Q_b / Sa) * ab[s] : sc(0)) + (Sb > 0.0 ? sc(ph.Q_s / Sb) * ab[g.N + s] : sc(0));
+        } else {
+            qv = sc(ph.xi_b) * ab[s] + sc(ph.xi_s) * ab[g.N + s];
+        }
+        ((sc *)b.q)[s] = qv;
+    } else if (inb) {
+        ((sc *)b.q)[s] = sc(0);
+    }
+    sc v[2] = {qv, qv * qv};
+    block_sums<2>(v, b.part + 2 * block_id());
+}
+
+// ===========================================================================
+// Poisson equation div(eps grad phi) = -(q - qmean) (Sec. II), eps = 1 +
+// kappa rho/rho0, face permittivity the mean of the two sites: red-black SOR
+// half-sweep over the sites of one colour, (x+y+z) mod 2 = color.
+// ===========================================================================
+template <int PR>
+__global__ void __launch_bounds__(128) k_sor(Geom g, Phys ph, Bufs b, int color)
+{
+    typedef typename Tr<PR>::sc sc;
+    int x, y, z;
+    bool inb;
+    ll s;
+    site_xyz(g, x, y, z, inb, s);
+    if (!inb || ((x + y + z) & 1) != color) return;
+    unsigned char kind = b.mask ? b.mask[s] : 0;
+    if (kind == ELBM_NODE_SOLID) return;
+    Nbr n;
+    nbr_init(n, g, x, y, z, s);
+    sc *phi = (sc *)b.phi;
+    const sc *rho = (const sc *)b.rho;
+    const sc kap = sc(ph.eps_kappa / ph.rho0);
+    sc es = sc(1) + kap * rho[s];
+    sc num = kind == ELBM_NODE_FLUID ? ((const sc *)b.q)[s] - sc(b.scal[S_QMEAN]) : sc(0);
+    sc den = 0;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int sg = -1; sg <= 1; sg += 2) {
+            ll nb = 0;
+            double v = 0;
+            int k = pois_nb(g, b.mask, n, x, y, z, a, sg, &nb, &v);
+            if (k == 0) {
+                sc ef = sc(0.5) * (es + (sc(1) + kap * rho[nb]));
+                num += ef * phi[nb];
+                den += ef;
+            } else if (k == 1) {
+                num += es * sc(v);
+                den += es;
+            }
+        }
+    if (den > sc(0)) phi[s] = (sc(1) - sc(ph.omega)) * phi[s] + sc(ph.omega) * num / den;
+}
+
+// residual r = div(eps grad phi) + q - qmean with the reference norms:
+// per-block sums of r^2, q^2 (fluid) and b^2 (Dirichlet data)
+template <int PR>
+__global__ void __launch_bounds__(128) k_resid(Geom g, Phys ph, Bufs b)
+{
+    typedef typename Tr<PR>::sc sc;
+    int x, y, z;
+    bool inb;
+    ll s;
+    site_xyz(g, x, y, z, inb, s);
+    unsigned char kind = (inb && b.mask) ? b.mask[s] : 0;
+    bool active = inb && kind != ELBM_NODE_SOLID;
+    sc r2 = 0, q2 = 0, b2 = 0;
+    if (active) {
+        Nbr n;
+        nbr_init(n, g, x, y, z, s);
+        const sc *phi = (const sc *)b.phi;
+        const sc *rho = (const sc *)b.rho;
+        const sc kap = sc(ph.eps_kappa / ph.rho0);
+        sc es = sc(1) + kap * rho[s];
+        sc qs = kind == ELBM_NODE_FLUID ? ((const sc *)b.q)[s] : sc(0);
+        sc r = kind == ELBM_NODE_FLUID ? qs - sc(b.scal[S_QMEAN]) : sc(0);
+        sc bs = 0;
+        sc ps = phi[s];
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int sg = -1; sg <= 1; sg += 2) {
+                ll nb = 0;
+                double v = 0;
+                int k = pois_nb(g, b.mask, n, x, y, z, a, sg, &nb, &v);
+                if (k == 0) r += sc(0.5) * (es + (sc(1) + kap * rho[nb])) * (phi[nb] - ps);
+                else if (k == 1) { r += es * (sc(v) - ps); bs += es * sc(v); }
+            }
+        r2 = r * r;
+        q2 = qs * qs;
+        b2 = bs * bs;
+    }
+    sc v[3] = {r2, q2, b2};
+    block_sums<3>(v, b.part + 3 * block_id());
+}
+
+template <int PR>
+__global__ void __launch_bounds__(128) k_phi_sum(Geom g, Phys ph, Bufs b)
+{
+    typedef typename Tr<PR>::sc sc;
+    int x, y, z;
+    bool inb;
+    ll s;
+    site_xyz(g, x, y, z, inb, s);
+    bool active = inb && (!b.mask || b.mask[s] != ELBM_NODE_SOLID);
+    sc v[1] = {active ? ((const sc *)b.phi)[s] : sc(0)};
+    block_sums<1>(v, b.part + block_id());
+}
+
+template <int PR>
+__global__ void k_phi_shift(Geom g, Bufs b)
+{
+    typedef typename Tr<PR>::sc sc;
+    int x, y, z;
+    bool inb;
+    ll s;
+    site_xyz(g, x, y, z, inb, s);
+    if (!inb || (b.mask && b.mask[s] == ELBM_NODE_SOLID)) return;
+    ((sc *)b.phi)[s] -= sc(b.scal[S_PHIMEAN]);
+}
+
+// ===========================================================================
+// The fused site update, Eq. (lattice-b): pull f; Shan-Chen force Eq. (sc);
+// E = -grad phi + E_ext, F_el = q E; f^eq Eq. (2); alpha Eq. (entropic);
+// stress Eq. (stress) and its 2-norm; Carreau viscosity Eqs. (strain2),
+// (carreau), (beta); exact-difference source Eq. (add); write f*; in
+// transport mode the D3Q7 charge update. Optional diagnostics per block.
+// ===========================================================================
+template <int PR>
+__global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int diag)
+{
+    typedef Tr<PR> T;
+    typedef typename T::ct ct;
+    typedef typename T::sc sc;
+    typedef typename T::st st;
+    typedef typename T::gt gt;
+    int x, y, z;
+    bool inb;
+    ll s;
+    site_xyz(g, x, y, z, inb, s);
+    const bool active = inb && (!b.mask || b.mask[s] == ELBM_NODE_FLUID);
+    ct dm = 0, dmx = 0, dmy = 0, dmz = 0, dq = 0, dasum = 0, dnfl = 0;
+    ct dsh = 0, dnr = 0, dcl = 0, dbad = 0;
+    float damin = 1e30f, damax = -1e30f, dherr = 0.f, dumax = 0.f;
+    if (active) {
+        Nbr n;
+        nbr_init(n, g, x, y, z, s);
+        const sc *rho = (const sc *)b.rho;
+        const sc *phi = (const sc *)b.phi;
+        ct f[Q];
+#pragma unroll
+        for (int p = 0; p < Q; p++) f[p] = gather_pop<PR>(g, b.mask, b.fA, n, p);
+        ct rs = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+        for (int p = 0; p < Q; p++) {
+            rs += f[p];
+            jx += ct(cx(p)) * f[p];
+            jy += ct(cy(p)) * f[p];
+            jz += ct(cz(p)) * f[p];
+        }
+        const ct r = T::dev ? ct(1) + rs : rs;
+        const ct drho = T::dev ? rs : rs - ct(1);
+
+        // Eq. (sc): F_int = -G psi(r) sum_fluid w psi(r+c) c - G_w psi(r) sum_wall w psi(r) c
+        const ct rho0 = ct(ph.rho0);
+        const ct ps = psi_of<ct>(r, rho0);
+        ct sfx = 0, sfy = 0, sfz = 0, swx = 0, swy = 0, swz = 0;
+#pragma unroll
+        for (int p = 1; p < Q; p++) {
+            ll nb = nbr_idx(n, g, cx(p), cy(p), cz(p));
+            bool wall = nb < 0 || (b.mask && b.mask[nb] == ELBM_NODE_SOLID);
+            ct wv = ct(wq(p)) * (wall ? ps : psi_of<ct>(ct(rho[nb]), rho0));
+            if (wall) { swx += wv * ct(cx(p)); swy += wv * ct(cy(p)); swz += wv * ct(cz(p)); }
+            else { sfx += wv * ct(cx(p)); sfy += wv * ct(cy(p)); sfz += wv * ct(cz(p)); }
+        }
+        ct Fx = -ct(ph.G) * ps * sfx - ct(ph.Gw) * ps * swx;
+        ct Fy = -ct(ph.G) * ps * sfy - ct(ph.Gw) * ps * swy;
+        ct Fz = -ct(ph.G) * ps * sfz - ct(ph.Gw) * ps * swz;
+
+        // electric force q E, E = -grad phi (central differences) + E_ext
+        ct qs = 0;
+        if (ph.charge_model != ELBM_CHARGE_NONE) {
+            qs = ct(((const sc *)b.q)[s]);
+            ct E[3];
+            const ct phs = ct(phi[s]);
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                ct pv[2];
+#pragma unroll
+                for (int k = 0; k < 2; k++) {
+                    ll nb = 0;
+                    double v = 0;
+                    int kind = pois_nb(g, b.mask, n, x, y, z, a, k ? 1 : -1, &nb, &v);
+                    pv[k] = kind == 0 ? ct(phi[nb]) : (kind == 1 ? ct(v) : phs);
+                }
+                E[a] = -(pv[1] - pv[0]) / ct(2) + ct(ph.E_ext[a]);
+            }
+            Fx += qs * E[0];
+            Fy += qs * E[1];
+            Fz += qs * E[2];
+        }
+
+        // Eq. (2) at the bare velocity, Delta = f^eq - f
+        const ct ir = ct(1) / r;
+        const ct ux = jx * ir, uy = jy * ir, uz = jz * ir;
+        const ct usq = ux * ux + uy * uy + uz * uz;
+        ct D[Q];
+#pragma unroll
+        for (int p = 0; p < Q; p++) {
+            ct P = Ppoly<ct>(p, ux, uy, uz, usq);
+            D[p] = T::dev ? ct(wq(p)) * (drho + r * P) - f[p] : ct(wq(p)) * r * (ct(1) + P) - f[p];
+        }
+
+        // Eq. (entropic)
+        AlphaOut ao;
+        ao.alpha = 2.0; ao.herr = 0.0; ao.status = 0;
+        if (ph.alpha_mode == ELBM_ALPHA_ENTROPIC) {
+            if (sizeof(ct) == 8 || ph.aprec == ELBM_APREC_FP64) {
+                double fd[Q], dd[Q];
+#pragma unroll
+                for (int p = 0; p < Q; p++) {
+                    fd[p] = T::dev ? wq(p) + double(f[p]) : double(f[p]);
+                    dd[p] = double(D[p]);
+                }
+                ao = alpha_fp64(fd, dd, double(r), ph.eq_tol);
+            } else {
+                float ff[Q], dd[Q], fv[Q];
+#pragma unroll
+                for (int p = 0; p < Q; p++) {
+                    ff[p] = float(wq(p)) + float(f[p]);
+                    dd[p] = float(D[p]);
+                    fv[p] = float(f[p]);
+                }
+                ao = alpha_fp32(ff, dd, fv, float(r), float(drho), float(ph.eq_tol));
+            }
+        }
+        const ct alpha = ct(ao.alpha);
+
+        // Eq. (stress): Pi = sum (f - f^eq) c c = -sum D c c; 2-norm; Carreau; Eq. (beta)
+        ct nu = ct(ph.rheo.nu0);
+        if (!ph.rheo.newtonian) {
+            ct pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+#pragma unroll
+            for (int p = 1; p < Q; p++) {
+                pxx -= D[p] * ct(cx(p) * cx(p));
+                pyy -= D[p] * ct(cy(p) * cy(p));
+                pzz -= D[p] * ct(cz(p) * cz(p));
+                pxy -= D[p] * ct(cx(p) * cy(p));
+                pxz -= D[p] * ct(cx(p) * cz(p));
+                pyz -= D[p] * ct(cy(p) * cz(p));
+            }
+            ct Pn = sym3_norm2<ct>(pxx, pyy, pzz, pxy, pxz, pyz);
+            nu = carreau_nu<ct>(ph.rheo, Pn, alpha, r);
+        }
+        const ct beta = ct(CS2) / (ct(2) * nu + ct(CS2));
+        const ct ab = alpha * beta;
+
+        // Eq. (add): S = f^eq(rho, u + F/rho) - f^eq(rho, u); Eq. (lattice-b)
+        const ct vx = ux + Fx * ir, vy = uy + Fy * ir, vz = uz + Fz * ir;
+        const ct vsq = vx * vx + vy * vy + vz * vz;
+        st *B = (st *)b.fB;
+#pragma unroll
+        for (int p = 0; p < Q; p++) {
+            ct Sp = ct(wq(p)) * r * (Ppoly<ct>(p, vx, vy, vz, vsq) - Ppoly<ct>(p, ux, uy, uz, usq));
+            ct fo = f[p] + ab * D[p] + Sp;
+            B[(ll)p * g.N + s] = from_ct<st>(fo);
+        }
+
+        // half-step velocity (Sec. II): rho u = sum f c + F/2
+        const ct upx = (jx + ct(0.5) * Fx) * ir, upy = (jy + ct(0.5) * Fy) * ir, upz = (jz + ct(0.5) * Fz) * ir;
+
+        if (ph.charge_model == ELBM_CHARGE_TRANSPORT) {
+            // D3Q7 advection-diffusion of q with the Ohmic source R = div(sigma grad phi)
+            const ct ss = ct(ph.sigma_gas) + ct(ph.sigma_liq - ph.sigma_gas) *
+                          theta_of<ct>(ct(rho[s]), rho0, ct(ph.theta_width));
+            const ct phs = ct(phi[s]);
+            ct R = 0;
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+#pragma unroll
+                for (int sg = -1; sg <= 1; sg += 2) {
+                    ll nb = 0;
+                    double v = 0;
+                    int kind = pois_nb(g, b.mask, n, x, y, z, a, sg, &nb, &v);
+                    if (kind == 0) {
+                        ct sn = ct(ph.sigma_gas) + ct(ph.sigma_liq - ph.sigma_gas) *
+                                theta_of<ct>(ct(rho[nb]), rho0, ct(ph.theta_width));
+                        R += ct(0.5) * (ss + sn) * (ct(phi[nb]) - phs);
+                    } else if (kind == 1) {
+                        R += ss * (ct(v) - phs);
+                    }
+                }
+            gt *GB = (gt *)b.gB;
+            const ct itq = ct(1) / ct(ph.tau_q);
+#pragma unroll
+            for (int i = 0; i < Q7; i++) {
+                ct gi = ct(gather_g<PR>(g, b.mask, b.gA, n, i));
+                ct cu = ct(c7x(i)) * upx + ct(c7y(i)) * upy + ct(c7z(i)) * upz;
+                ct geq = ct(w7(i)) * qs * (ct(1) + cu / ct(CS2Q));
+                GB[(ll)i * g.N + s] = gt(gi - (gi - geq) * itq + ct(w7(i)) * R);
+            }
+        }
+
+        if (ph.store_macro) {
+            ((sc *)b.ux)[s] = sc(upx);
+            ((sc *)b.uy)[s] = sc(upy);
+            ((sc *)b.uz)[s] = sc(upz);
+            ((sc *)b.alpha)[s] = sc(alpha);
+            ((sc *)b.nu)[s] = sc(nu);
+        }
+        if (diag) {
+            dm = r;
+            dmx = jx + ct(0.5) * Fx;
+            dmy = jy + ct(0.5) * Fy;
+            dmz = jz + ct(0.5) * Fz;
+            dq = qs;
+            dasum = alpha;
+            dnfl = 1;
+            damin = damax = float(alpha);
+            if (ao.status == 1) dsh = 1;
+            else if (ao.status == 2) dnr = 1;
+            else if (ao.status == 3) dcl = 1;
+            dherr = float(ao.herr);
+            float um = float(sqrt(upx * upx + upy * upy + upz * upz));
+            dumax = um;
+            if (!(r > ct(0)) || !isfinite(float(r)) || !isfinite(um) || !isfinite(float(alpha))) dbad = 1;
+        }
+    }
+    if (diag) {
+        ct v[11] = {dm, dmx, dmy, dmz, dq, dasum, dsh, dnr, dcl, dbad, dnfl};
+        __shared__ double res[11];
+        __shared__ float mm[4][8];
+        const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+        const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            damin = fminf(damin, __shfl_down_sync(0xffffffffu, damin, o));
+            damax = fmaxf(damax, __shfl_down_sync(0xffffffffu, damax, o));
+            dherr = fmaxf(dherr, __shfl_down_sync(0xffffffffu, dherr, o));
+            dumax = fmaxf(dumax, __shfl_down_sync(0xffffffffu, dumax, o));
+        }
+        if (lane == 0) { mm[0][wid] = damin; mm[1][wid] = damax; mm[2][wid] = dherr; mm[3][wid] = dumax; }
+        block_sums<11>(v, res);
+        if (tid == 0) {
+            double *out = b.part + (ll)D_NPART * block_id();
+            out[D_MASS] = res[0]; out[D_MX] = res[1]; out[D_MY] = res[2]; out[D_MZ] = res[3];
+            out[D_Q] = res[4]; out[D_ASUM] = res[5]; out[D_NSHORT] = res[6]; out[D_NNOROOT] = res[7];
+            out[D_NCLIP] = res[8]; out[D_NBAD] = res[9]; out[D_NFLUID] = res[10];
+            const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+            float a0 = 1e30f, a1 = -1e30f, h = 0.f, u = 0.f;
+            for (int i = 0; i < nw; i++) {
+                a0 = fminf(a0, mm[0][i]); a1 = fmaxf(a1, mm[1][i]);
+                h = fmaxf(h, mm[2][i]); u = fmaxf(u, mm[3][i]);
+            }
+            out[D_AMIN] = a0; out[D_AMAX] = a1; out[D_HERR] = h; out[D_UMAX] = u;
+        }
+    }
+}
+
+// f(r, t) for the caller: the pull of every fluid site, 0 elsewhere
+template <int PR>
+__global__ void k_export_pop(Geom g, Bufs b, double *out)
+{
+    typedef Tr<PR> T;
+    int x, y, z;
+    bool inb;
+    ll s;
+    site_xyz(g, x, y, z, inb, s);
+    if (!inb) return;
+    bool fluid = !b.mask || b.mask[s] == ELBM_NODE_FLUID;
+    Nbr n;
+    nbr_init(n, g, x, y, z, s);
+#pragma unroll
+    for (int p = 0; p < Q; p++) {
+        double v = 0.0;
+        if (fluid) {
+            double fv = double(gather_pop<PR>(g, b.mask, b.fA, n, p));
+            v = T::dev ? wq(p) + fv : fv;
+        }
+        out[(ll)p * g.N + s] = v;
+    }
+}
+
+template <int PR>
+__global__ void k_export_gpop(Geom g, Bufs b, double *out)
+{
+    int x, y, z;
+    bool inb;
+    ll s;
+    site_xyz(g, x, y, z, inb, s);
+    if (!inb) return;
+    bool fluid = !b.mask || b.mask[s] == ELBM_NODE_FLUID;
+    Nbr n;
+    nbr_init(n, g, x, y, z, s);
+#pragma unroll
+    for (int i = 0; i < Q7; i++)
+        out[(ll)i * g.N + s] = fluid ? double(gather_g<PR>(g, b.mask, b.gA, n, i)) : 0.0;
+}
+
+template <typename S>
+__global__ void k_to_double(const S *in, double *out, ll n)
+{
+    ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = double(in[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers for one precision.
+// ---------------------------------------------------------------------------
+template <int PR>
+struct Launchers {
+    typedef typename Tr<PR>::sc sc;
+    static void init_pop(const Geom &g, const Phys &ph, const Bufs &b, const double *rho0,
+                         const double *u0, const double *f0, const double *u_in, const double *q0,
+                         const Launch &L, cudaStream_t s)
+    {
+        k_init_pop<PR><<<L.grid, L.block, 0, s>>>(g, ph, b, rho0, u0, f0, u_in, q0);
+    }
+    static void moments(const Geom &g, const Phys &ph, const Bufs &b, const Launch &L, cudaStream_t s)
+    {
+        k_moments<PR><<<L.grid, L.block, 0, s>>>(g, ph, b);
+    }
+    static void charge(const Geom &g, const Phys &ph, const Bufs &b, int stage, const Launch &L, cudaStream_t s)
+    {
+        if (stage == 0) {
+            k_charge_grad<PR><<<L.grid, L.block, 0, s>>>(g, ph, b);
+            k_charge_ab<PR><<<L.grid, L.block, 0, s>>>(g, ph, b);
+        } else {
+            k_charge_q<PR><<<L.grid, L.block, 0, s>>>(g, ph, b);
+        }
+    }
+    static void sor(const Geom &g, const Phys &ph, const Bufs &b, int color, const Launch &L, cudaStream_t s)
+    {
+        k_sor<PR><<<L.grid, L.block, 0, s>>>(g, ph, b, color);
+    }
+    static void resid(const Geom &g, const Phys &ph, const Bufs &b, const Launch &L, cudaStream_t s)
+    {
+        k_resid<PR><<<L.grid, L.block, 0, s>>>(g, ph, b);
+    }
+    static void phi_mean(const Geom &g, const Phys &ph, const Bufs &b, int stage, const Launch &L, cudaStream_t s)
+    {
+        if (stage == 0) k_phi_sum<PR><<<L.grid, L.block, 0, s>>>(g, ph, b);
+        else k_phi_shift<PR><<<L.grid, L.block, 0, s>>>(g, b);
+    }
+    static void collide(const Geom &g, const Phys &ph, const Bufs &b, int diag, const Launch &L, cudaStream_t s)
+    {
+        k_collide<PR><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
+    }
+    static void export_pop(const Geom &g, const Bufs &b, double *out, const Launch &L, cudaStream_t s)
+    {
+        k_export_pop<PR><<<L.grid, L.block, 0, s>>>(g, b, out);
+    }
+    static void export_gpop(const Geom &g, const Bufs &b, double *out, const Launch &L, cudaStream_t s)
+    {
+        k_export_gpop<PR><<<L.grid, L.block, 0, s>>>(g, b, out);
+    }
+    static void export_plane(const void *plane, double *out, ll n, cudaStream_t s)
+    {
+        k_to_double<sc><<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const sc *)plane, out, n);
+    }
+    static Ops table()
+    {
+        Ops o;
+        o.init_pop = init_pop;
+        o.moments = moments;
+        o.charge = charge;
+        o.sor = sor;
+        o.resid = resid;
+        o.phi_mean = phi_mean;
+        o.collide = collide;
+        o.export_pop = export_pop;
+        o.export_gpop = export_gpop;
+        o.export_plane = export_plane;
+        return o;
+    }
+};
+
+}  // namespace elbm

@@ -1,0 +1,238 @@
+"""Thin ctypes binding of the C ABI in include/elbm.h (libelbm.so).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels. There is no CPU fallback; if the library cannot be loaded the
+import of this module's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libelbm.so")
+
+OK, W_POISSON_NOCONV, E_INVAL, E_NOMEM, E_CUDA, E_NUMERIC, E_STATE = 0, 1, -1, -2, -3, -4, -5
+F_RHO, F_U, F_PHI, F_Q, F_ALPHA, F_NU, F_POP, F_GPOP, F_DIAG = (1 << i for i in range(9))
+NDIAG = 20
+DIAG_NAMES = [
+    "mass", "mom_x", "mom_y", "mom_z", "charge", "alpha_min", "alpha_max", "alpha_mean",
+    "n_shortcut", "n_noroot", "n_clipped", "poisson_sweeps", "poisson_resid", "max_h_error",
+    "max_u", "n_nonfinite", "q_mean", "step", "poisson_sweeps_total", "reserved",
+]
+EXPORTS = ["elbm_init", "elbm_step", "elbm_fields", "elbm_fields_size", "elbm_free",
+           "elbm_strerror", "elbm_velocity_set", "elbm_pass_times"]
+
+_FACE = {"periodic": 0, "wall": 1}
+_PHI = {"periodic": 0, "dirichlet": 1, "neumann": 2}
+_CHARGE = {"none": 0, "conserved": 1, "xi": 2, "transport": 3}
+_FEL = {"qe": 0, "full": 1}
+_ALPHA = {"entropic": 0, "bgk": 1}
+_PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
+_APREC = {"fp64": 0, "fp32": 1}
+
+
+class ElbmError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("face_bc", ctypes.c_int * 6), ("phi_bc", ctypes.c_int * 6),
+        ("phi_axis", ctypes.c_int), ("charge_model", ctypes.c_int), ("force_el", ctypes.c_int),
+        ("neutralize", ctypes.c_int), ("poisson_maxit", ctypes.c_int),
+        ("poisson_fixed_sweeps", ctypes.c_int), ("poisson_check_every", ctypes.c_int),
+        ("alpha_mode", ctypes.c_int), ("precision", ctypes.c_int),
+        ("alpha_precision", ctypes.c_int), ("store_macro", ctypes.c_int),
+        ("diag_every", ctypes.c_int), ("profile", ctypes.c_int),
+        ("phi_lo", ctypes.c_double), ("phi_hi", ctypes.c_double), ("phi_solid", ctypes.c_double),
+        ("nu0", ctypes.c_double), ("nu_inf", ctypes.c_double), ("lam", ctypes.c_double),
+        ("n_carreau", ctypes.c_double),
+        ("G", ctypes.c_double), ("Gw", ctypes.c_double), ("rho0", ctypes.c_double),
+        ("eps_kappa", ctypes.c_double), ("sigma_liq", ctypes.c_double),
+        ("sigma_gas", ctypes.c_double), ("Dq", ctypes.c_double), ("E_ext", ctypes.c_double * 3),
+        ("Q_b", ctypes.c_double), ("Q_s", ctypes.c_double), ("K_d", ctypes.c_double),
+        ("xi_b", ctypes.c_double), ("xi_s", ctypes.c_double), ("theta_width", ctypes.c_double),
+        ("sor_omega", ctypes.c_double), ("poisson_tol", ctypes.c_double),
+        ("alpha_eq_tol", ctypes.c_double), ("rho_in", ctypes.c_double), ("rho_out", ctypes.c_double),
+        ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class InitFields(ctypes.Structure):
+    _fields_ = [("mask", ctypes.POINTER(ctypes.c_ubyte)),
+                ("rho0", ctypes.POINTER(ctypes.c_double)), ("u0", ctypes.POINTER(ctypes.c_double)),
+                ("q0", ctypes.POINTER(ctypes.c_double)), ("u_in", ctypes.POINTER(ctypes.c_double)),
+                ("f0", ctypes.POINTER(ctypes.c_double))]
+
+
+_lib = None
+
+
+def lib():
+    """Load libelbm.so (built by paper_1612_05404_gb300.build). Raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libelbm.so not built ({LIB_PATH}); run paper_1612_05404_gb300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        vp = ctypes.c_void_p
+        L.elbm_init.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(InitFields), ctypes.c_int,
+                                ctypes.POINTER(vp)]
+        L.elbm_init.restype = ctypes.c_int
+        L.elbm_step.argtypes = [vp, ctypes.c_int]
+        L.elbm_step.restype = ctypes.c_int
+        L.elbm_fields.argtypes = [vp, ctypes.c_uint, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]
+        L.elbm_fields.restype = ctypes.c_int
+        L.elbm_fields_size.argtypes = [vp, ctypes.c_uint]
+        L.elbm_fields_size.restype = ctypes.c_size_t
+        L.elbm_free.argtypes = [vp]
+        L.elbm_free.restype = None
+        L.elbm_strerror.argtypes = [ctypes.c_int]
+        L.elbm_strerror.restype = ctypes.c_char_p
+        L.elbm_velocity_set.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+        L.elbm_velocity_set.restype = ctypes.c_int
+        L.elbm_pass_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+        L.elbm_pass_times.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().elbm_strerror(int(code)).decode()
+
+
+def velocity_set():
+    c = (ctypes.c_int * 57)()
+    w = (ctypes.c_double * 19)()
+    lib().elbm_velocity_set(c, w)
+    return np.array(list(c)).reshape(19, 3), np.array(list(w))
+
+
+def make_params(cfg: dict, stream=None) -> Params:
+    P = Params()
+    P.nx, P.ny, P.nz = cfg["shape"]
+    for i, v in enumerate(cfg["face_bc"]):
+        P.face_bc[i] = _FACE[v]
+    for i, v in enumerate(cfg["phi_bc"]):
+        P.phi_bc[i] = _PHI[v]
+    P.phi_axis = cfg["phi_axis"]
+    P.charge_model = _CHARGE[cfg["charge_model"]]
+    P.force_el = _FEL[cfg["force_el"]]
+    P.neutralize = int(cfg["neutralize"])
+    P.poisson_maxit = cfg["poisson_maxit"]
+    P.poisson_fixed_sweeps = cfg["poisson_fixed_sweeps"]
+    P.poisson_check_every = cfg.get("poisson_check_every", 8)
+    P.alpha_mode = _ALPHA[cfg["alpha_mode"]]
+    P.precision = _PREC[cfg["precision"]]
+    P.alpha_precision = _APREC[cfg.get("alpha_precision", "fp64")]
+    P.store_macro = int(cfg.get("store_macro", 1))
+    P.diag_every = int(cfg.get("diag_every", 1))
+    P.profile = int(cfg.get("profile", 0))
+    P.phi_lo, P.phi_hi, P.phi_solid = cfg["phi_lo"], cfg["phi_hi"], cfg["phi_solid"]
+    P.nu0, P.nu_inf, P.lam, P.n_carreau = cfg["nu0"], cfg["nu_inf"], cfg["lambda"], cfg["n_carreau"]
+    P.G, P.Gw, P.rho0 = cfg["G"], cfg["Gw"], cfg["rho0"]
+    P.eps_kappa = cfg["eps_kappa"]
+    P.sigma_liq, P.sigma_gas, P.Dq = cfg["sigma_liq"], cfg["sigma_gas"], cfg["Dq"]
+    for i in range(3):
+        P.E_ext[i] = cfg["E_ext"][i]
+    P.Q_b, P.Q_s, P.K_d = cfg["Q_b"], cfg["Q_s"], cfg["K_d"]
+    P.xi_b, P.xi_s, P.theta_width = cfg["xi_b"], cfg["xi_s"], cfg["theta_width"]
+    P.sor_omega, P.poisson_tol = cfg["sor_omega"], cfg["poisson_tol"]
+    P.alpha_eq_tol = cfg["alpha_eq_tol"]
+    P.rho_in, P.rho_out = cfg["rho_in"], cfg["rho_out"]
+    P.cuda_stream = stream
+    return P
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _cur_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+class Sim:
+    """One lattice on the GPU driven through the C ABI."""
+
+    def __init__(self, cfg: dict, fields: dict, stream=None):
+        self.cfg = cfg
+        nx, ny, nz = cfg["shape"]
+        self.N = nx * ny * nz
+        self._keep = {}
+        for k in ("rho", "u", "q", "u_in", "f"):
+            if k in fields and fields[k] is not None:
+                self._keep[k] = np.ascontiguousarray(fields[k], dtype=np.float64).reshape(-1)
+        mask = fields.get("mask")
+        self._keep["mask"] = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+        IF = InitFields()
+        m = self._keep["mask"]
+        IF.mask = None if m is None else m.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+        IF.rho0 = _dptr(self._keep.get("rho"))
+        IF.u0 = _dptr(self._keep.get("u"))
+        IF.q0 = _dptr(self._keep.get("q"))
+        IF.u_in = _dptr(self._keep.get("u_in"))
+        IF.f0 = _dptr(self._keep.get("f"))
+        self.P = make_params(cfg, stream if stream is not None else _cur_stream())
+        h = ctypes.c_void_p()
+        rc = lib().elbm_init(ctypes.byref(self.P), ctypes.byref(IF), 1, ctypes.byref(h))
+        if rc != OK:
+            raise ElbmError(rc, "elbm_init")
+        self.h = h
+        self.last_status = OK
+
+    def step(self, n: int = 1) -> int:
+        rc = lib().elbm_step(self.h, int(n))
+        if rc < 0:
+            raise ElbmError(rc, "elbm_step")
+        self.last_status = rc
+        return rc
+
+    def fields(self, mask: int, out=None) -> np.ndarray:
+        n = lib().elbm_fields_size(self.h, mask)
+        if out is None:
+            out = np.empty(n, dtype=np.float64)
+        rc = lib().elbm_fields(self.h, mask, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size)
+        if rc != OK:
+            raise ElbmError(rc, "elbm_fields")
+        return out
+
+    def get(self, name: str) -> np.ndarray:
+        sel = {"rho": F_RHO, "u": F_U, "phi": F_PHI, "q": F_Q, "alpha": F_ALPHA, "nu": F_NU,
+               "f": F_POP, "g": F_GPOP, "diag": F_DIAG}[name]
+        return self.fields(sel)
+
+    def pass_times(self) -> dict:
+        out = (ctypes.c_double * 8)()
+        rc = lib().elbm_pass_times(self.h, out, 8)
+        if rc != OK:
+            raise ElbmError(rc, "elbm_pass_times")
+        keys = ["moments_ms", "poisson_ms", "collide_ms", "reduce_ms", "steps", "collide_launches",
+                "sweeps", "launches"]
+        return dict(zip(keys, list(out)))
+
+    def diag(self) -> dict:
+        return dict(zip(DIAG_NAMES, self.fields(F_DIAG).tolist()))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().elbm_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

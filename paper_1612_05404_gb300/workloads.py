@@ -51,6 +51,16 @@ def base_params(**kw) -> dict:
     return p
 
 
+def reduced_precision(p: dict) -> dict:
+    """Thresholds for FP32 arithmetic: the near-equilibrium alpha shortcut
+    above the FP32 noise of Delta/f (about 3e-7), and a Poisson tolerance
+    the FP32 potential can reach."""
+    if p["precision"] != "fp64":
+        p["alpha_eq_tol"] = max(p["alpha_eq_tol"], 1e-5)
+        p["poisson_tol"] = max(p["poisson_tol"], 1e-5)
+    return p
+
+
 def kappa_for_ratio(ratio: float, rho_l: float = RHO_L, rho_v: float = RHO_V) -> float:
     """kappa in eps = 1 + kappa rho such that eps(rho_l)/eps(rho_v) = ratio."""
     return (ratio - 1.0) / (rho_l - ratio * rho_v)
@@ -90,7 +100,8 @@ def charged_drop_at_rest(n=32, radius=8.0, precision="fp64", steps=500, seed=SEE
     sig_l = eps_l / 50.0
     cfg = base_params(shape=shape, charge_model="transport", eps_kappa=kappa,
                       sigma_liq=sig_l, sigma_gas=sig_l / sigma_ratio, Dq=1e-3,
-                      precision=precision, poisson_tol=1e-13 if precision == "fp64" else 1e-6)
+                      precision=precision, poisson_tol=1e-13)
+    reduced_precision(cfg)
     cfg["steps"] = steps
     N = n ** 3
     rho = drop_profile(shape, radius) + uniform_noise(N, noise, seed)
@@ -117,7 +128,8 @@ def drop_in_field(E0=1e-3, n=64, radius=12.0, precision="fp32", steps=5000,
         phi_axis=2, phi_lo=0.0, phi_hi=-E0 * (n + 1),
         sigma_liq=sig_l, sigma_gas=sig_l / sigma_ratio, Dq=1e-3,
         nu0=nu0, nu_inf=nu0 / 10.0, n_carreau=n_carreau,
-        precision=precision, poisson_tol=1e-13 if precision == "fp64" else 1e-6)
+        precision=precision, poisson_tol=1e-13)
+    reduced_precision(cfg)
     cfg["lambda"] = lam
     cfg["steps"] = steps
     cfg["E0"] = E0
@@ -141,7 +153,8 @@ def jet(shape=(128, 128, 512), nozzle_r=8, wall=2, nozzle_len=16, u_mean=0.02, E
         face_bc=["wall"] * 6, phi_bc=["dirichlet"] * 6, phi_axis=2,
         phi_lo=0.0, phi_hi=-E0 * (nz + 1), phi_solid=0.0,
         nu0=nu0, nu_inf=nu0 / 10.0, n_carreau=0.5, eps_kappa=1.0,
-        precision=precision, poisson_tol=1e-13 if precision == "fp64" else 1e-6)
+        precision=precision, poisson_tol=1e-13)
+    reduced_precision(cfg)
     cfg["lambda"] = 20.0
     cfg["steps"] = steps
     x, y, z = _grid(shape)

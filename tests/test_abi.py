@@ -1,0 +1,101 @@
+"""The C-ABI library builds, loads without a GPU, exports every entry point
+declared in include/elbm.h, and its ctypes mirror has the C layout."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1612_05404_gb300 import build as B
+from paper_1612_05404_gb300 import elbm
+from paper_1612_05404_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return elbm.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    hdr = open(os.path.join(ROOT, "include", "elbm.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    declared = set(re.findall(r"^\s*(?:const\s+)?\w+\s*\**\s*(elbm_[a-z_]+)\s*\(", hdr, re.M))
+    assert declared >= set(elbm.EXPORTS)
+    out = subprocess.run(["nm", "-D", "--defined-only", elbm.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (elbm_[a-z_]+)$", out, re.M))
+    assert declared <= exported, declared - exported
+    for name in declared:
+        assert getattr(L, name)
+
+
+def test_struct_layout_matches_c(L):
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "elbm.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(elbm_params), offsetof(elbm_params, phi_lo),
+         offsetof(elbm_params, nu0), offsetof(elbm_params, E_ext), offsetof(elbm_params, rho_out),
+         offsetof(elbm_params, cuda_stream), sizeof(elbm_init_fields));
+  return 0; }
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "l.c")
+        exe = os.path.join(d, "l")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        got = list(map(int, subprocess.run([exe], capture_output=True, text=True).stdout.split()))
+    P = elbm.Params
+    want = [ctypes.sizeof(P), P.phi_lo.offset, P.nu0.offset, P.E_ext.offset, P.rho_out.offset,
+            P.cuda_stream.offset, ctypes.sizeof(elbm.InitFields)]
+    assert got == want
+
+
+def test_velocity_set_matches_oracle_table(L):
+    c, w = elbm.velocity_set()
+    co, wo, _ = oracle.lattice(3)
+    assert np.array_equal(c, co) and np.array_equal(w, wo)
+
+
+def test_strerror(L):
+    assert elbm.strerror(0) == "ok"
+    assert "invalid" in elbm.strerror(-1)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(shape=(0, 4, 4)),
+    dict(face_bc=["wall", "periodic", "periodic", "periodic", "periodic", "periodic"]),
+    dict(phi_bc=["dirichlet"] * 2 + ["periodic"] * 4),
+    dict(nu0=0.0),
+    dict(charge_model="transport", shape=(5, 4, 4)),   # odd periodic extent for red-black
+    dict(precision="fp16"),
+    dict(force_el="full"),
+])
+def test_invalid_parameters_rejected_without_allocation(L, bad):
+    cfg = W.base_params(shape=(4, 4, 4))
+    try:
+        cfg.update(bad)
+        P = elbm.make_params(cfg)
+    except KeyError:
+        return  # not even representable
+    N = int(np.prod(cfg["shape"])) if min(cfg["shape"]) > 0 else 1
+    rho = np.ones(max(N, 1))
+    IF = elbm.InitFields()
+    IF.rho0 = rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    h = ctypes.c_void_p()
+    assert L.elbm_init(ctypes.byref(P), ctypes.byref(IF), 1, ctypes.byref(h)) == elbm.E_INVAL
+    assert not h.value
+
+
+def test_null_arguments(L):
+    assert L.elbm_init(None, None, 1, None) == elbm.E_INVAL
+    assert L.elbm_step(None, 1) == elbm.E_INVAL
+    L.elbm_free(None)

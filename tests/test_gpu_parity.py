@@ -1,0 +1,229 @@
+"""GPU path (through the C ABI) against the FP64 CPU oracle, element by
+element, on seeded inputs: FP64 to 1e-12 relative, FP32 / BF16 within the
+reduced-precision tolerances derived in the test bodies."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1612_05404_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def E():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1612_05404_gb300 import build, elbm
+    build.build()
+    return elbm
+
+
+def rel_inf(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def run_both(E, cfg, fields, steps):
+    g = E.Sim(cfg, fields)
+    g.step(steps)
+    o = oracle.Sim(cfg, fields)
+    o.step(steps)
+    return g, o
+
+
+def compare_fp64(g, o, cfg, tol=1e-12, fields=("f", "rho", "u", "nu", "phi", "q")):
+    out = {}
+    N = o.N
+    if "f" in fields:
+        out["f"] = rel_inf(g.get("f"), o.f)
+    if "rho" in fields:
+        out["rho"] = rel_inf(g.get("rho"), o.rho)
+    if "u" in fields:
+        # momentum density: the velocity itself amplifies errors by 1/rho in the vapour
+        out["rho_u"] = rel_inf(g.get("u").reshape(-1, 3) * g.get("rho")[:, None],
+                               o.u.reshape(-1, 3) * o.rho[:, None])
+    if "nu" in fields:
+        out["nu"] = rel_inf(g.get("nu"), o.nu)
+    if cfg["charge_model"] != "none":
+        if "phi" in fields:
+            out["phi"] = rel_inf(g.get("phi"), o.phi)
+        if "q" in fields:
+            out["q"] = rel_inf(g.get("q"), o.q)
+    if cfg["charge_model"] == "transport":
+        out["g"] = rel_inf(g.get("g"), o.g)
+    bad = {k: v for k, v in out.items() if not v <= tol}
+    assert not bad, (bad, out)
+    return out
+
+
+def _tight(cfg):
+    cfg["poisson_check_every"] = 1
+    cfg["poisson_tol"] = 1e-13
+    cfg["precision"] = "fp64"
+    cfg["store_macro"] = 1
+    return cfg
+
+
+def test_streaming_roundtrip_bit_exact(E):
+    """f(r,0) given explicitly comes back unchanged from the device layout
+    (inverse streaming at init, pull at export): an exact permutation, with
+    walls, solids, inlet and outlet nodes."""
+    shape = (10, 6, 8)
+    N = 480
+    cfg = W.base_params(shape=shape, face_bc=["periodic"] * 2 + ["wall"] * 4,
+                        phi_bc=["periodic"] * 2 + ["neumann"] * 2 + ["dirichlet"] * 2)
+    mask = np.zeros(N, np.uint8)
+    mask[[33, 34, 101, 250]] = W.SOLID
+    mask[:10] = W.INLET
+    mask[-10:] = W.OUTLET
+    rng = np.random.default_rng(100)
+    f0 = rng.uniform(0.01, 0.2, 19 * N)
+    f0.reshape(19, N)[:, mask != 0] = 0.0
+    # links arriving from inlet / outlet nodes carry their equilibria (oracle)
+    u_in = np.zeros((N, 3))
+    u_in[:10, 2] = 0.02
+    ref = oracle.Sim(cfg, dict(mask=mask, rho=np.ones(N), f=f0, u_in=u_in)).f.reshape(19, N)
+    c, _ = E.velocity_set()
+    nx, ny, nz = shape
+    xs, ys, zs = np.arange(N) % nx, (np.arange(N) // nx) % ny, np.arange(N) // (nx * ny)
+    io_link = np.zeros((19, N), bool)
+    for p in range(19):
+        sx, sy, sz = (xs - c[p, 0]) % nx, ys - c[p, 1], zs - c[p, 2]
+        ok = (sy >= 0) & (sy < ny) & (sz >= 0) & (sz < nz)
+        src = sx + nx * (np.clip(sy, 0, ny - 1) + ny * np.clip(sz, 0, nz - 1))
+        io_link[p] = ok & ((mask[src] == W.INLET) | (mask[src] == W.OUTLET))
+    for prec in ("fp64", "fp32", "bf16"):
+        cfg["precision"] = prec
+        g = E.Sim(cfg, dict(mask=mask, rho=np.ones(N), f=f0, u_in=u_in))
+        out = g.get("f").reshape(19, N)
+        fl = np.broadcast_to(mask == 0, (19, N))
+        perm = fl & ~io_link      # pure permutation entries: bit-exact
+        io = fl & io_link         # boundary equilibria: two equal formulas, ulp-close
+        _, w = E.velocity_set()
+        if prec == "fp64":
+            assert np.array_equal(out[perm], ref[perm])
+            assert np.allclose(out[io], ref[io], rtol=4e-16, atol=0)
+        elif prec == "fp32":
+            expect = (ref - w[:, None]).astype(np.float32).astype(np.float64) + w[:, None]
+            assert np.array_equal(out[perm], expect[perm])
+            assert np.allclose(out[io], ref[io], rtol=2e-7, atol=0)
+        else:
+            d = np.abs(ref - w[:, None])
+            assert np.all(np.abs(out - ref)[fl] <= 2.0 ** -8 * d[fl] + 1e-12)
+        g.close()
+
+
+def test_fp64_shan_chen_drop(E):
+    cfg = _tight(W.base_params(shape=(12, 10, 8)))
+    rho = W.drop_profile(cfg["shape"], 3.0) + W.uniform_noise(960, 1e-3, 101)
+    g, o = run_both(E, cfg, dict(rho=rho), 4)
+    compare_fp64(g, o, cfg)
+    a_g, a_o = g.get("alpha"), o.alpha
+    assert rel_inf(a_g, a_o) < 1e-9
+
+
+def test_fp64_transport_charged_drop(E):
+    cfg, fields = W.charged_drop_at_rest(n=12, radius=3.5)
+    _tight(cfg)
+    g, o = run_both(E, cfg, fields, 4)
+    compare_fp64(g, o, cfg)
+
+
+def test_fp64_electrodes_walls_carreau(E):
+    cfg, fields = W.drop_in_field(E0=1e-3, n=12, radius=3.5, precision="fp64")
+    _tight(cfg)
+    g, o = run_both(E, cfg, fields, 4)
+    compare_fp64(g, o, cfg)
+    assert g.get("nu").min() < cfg["nu0"]  # the Carreau branch ran
+
+
+def test_fp64_paper_conserved_charge(E):
+    cfg = _tight(W.base_params(shape=(12, 12, 10), charge_model="conserved", Q_b=2.13 / 11,
+                               Q_s=2.13 * 10 / 11, eps_kappa=1.0))
+    rho = W.drop_profile(cfg["shape"], 3.5) + W.uniform_noise(1440, 1e-3, 102)
+    g, o = run_both(E, cfg, dict(rho=rho), 3)
+    compare_fp64(g, o, cfg)
+
+
+def test_fp64_nozzle_inlet_outlet_xi_charge(E):
+    cfg, fields = W.jet(shape=(16, 16, 20), nozzle_r=3, wall=1, nozzle_len=5, precision="fp64")
+    _tight(cfg)
+    g, o = run_both(E, cfg, fields, 3)
+    compare_fp64(g, o, cfg)
+
+
+def test_fp64_multi_step_drop(E):
+    cfg, fields = W.charged_drop_at_rest(n=16, radius=4.0)
+    _tight(cfg)
+    g, o = run_both(E, cfg, fields, 15)
+    compare_fp64(g, o, cfg, tol=1e-11)
+    dg = g.diag()
+    assert dg["mass"] == pytest.approx(o.diag[0], rel=1e-13)
+
+
+def test_fp64_fixed_sweeps_match(E):
+    cfg, fields = W.drop_in_field(E0=5e-4, n=12, radius=3.5, precision="fp64")
+    _tight(cfg)
+    cfg["poisson_fixed_sweeps"] = 7
+    g, o = run_both(E, cfg, fields, 2)
+    compare_fp64(g, o, cfg)
+
+
+@pytest.mark.parametrize("aprec", ["fp64", "fp32"])
+def test_fp32_parity(E, aprec):
+    """FP32 deviation storage, FP32 arithmetic: within 1e-5 relative L2 on
+    rho, u, phi and q after several steps."""
+    cfg, fields = W.drop_in_field(E0=1e-3, n=16, radius=4.5, precision="fp32")
+    cfg["store_macro"] = 1
+    cfg["alpha_precision"] = aprec
+    ocfg = dict(cfg, poisson_tol=1e-13)  # same alpha shortcut threshold as the GPU run
+    g = E.Sim(cfg, fields)
+    g.step(5)
+    o = oracle.Sim(ocfg, fields)
+    o.step(5)
+    errs = dict(rho=rel_l2(g.get("rho"), o.rho), u=rel_l2(g.get("u"), o.u),
+                phi=rel_l2(g.get("phi"), o.phi), q=rel_l2(g.get("q"), o.q))
+    assert max(errs.values()) < 1e-5, errs
+
+
+def test_bf16_single_step(E):
+    """BF16 deviation storage: one rounding of d = f - w per stored value
+    (unit roundoff 2^-9) bounds the single-step error on rho by
+    2^-9 sum_p |d_p| / rho; checked against that bound."""
+    cfg, fields = W.drop_in_field(E0=1e-3, n=16, radius=4.5, precision="bf16")
+    cfg["store_macro"] = 1
+    g = E.Sim(cfg, fields)
+    g.step(1)
+    o = oracle.Sim(dict(cfg, poisson_tol=1e-13), fields)
+    o.step(1)
+    f = o.f.reshape(19, -1)
+    _, w = E.velocity_set()
+    bound = 2.0 ** -8 * np.abs(f - w[:, None]).sum(0).max()
+    assert np.abs(g.get("rho") - o.rho).max() <= bound + 1e-6
+
+
+def test_mass_conservation_over_steps(E):
+    cfg, fields = W.charged_drop_at_rest(n=16, radius=4.0)
+    cfg["precision"] = "fp64"
+    g = E.Sim(cfg, fields)
+    g.step(1)
+    m0 = g.diag()["mass"]
+    g.step(20)
+    assert g.diag()["mass"] == pytest.approx(m0, rel=1e-13)
+
+
+def test_numeric_failure_is_reported(E):
+    """A negative density gives NaN in the pseudopotential logarithms: the
+    step returns ELBM_E_NUMERIC instead of hanging or faulting."""
+    cfg = W.base_params(shape=(8, 8, 8), precision="fp64", charge_model="transport",
+                        poisson_maxit=50)
+    rho = np.ones(512)
+    rho[100] = -1.0
+    g = E.Sim(cfg, dict(rho=rho))
+    with pytest.raises(E.ElbmError) as ei:
+        g.step(1)
+    assert ei.value.code == E.E_NUMERIC
