@@ -20,6 +20,7 @@ struct elbm_handle {
     Phys ph;
     Bufs b;
     Launch L;
+    Launch Lh;            // one thread per site of one red-black colour
     Ops ops;
     cudaStream_t s;
     int has_dirichlet;
@@ -43,7 +44,7 @@ enum { FIN_CHARGE_AB = 0, FIN_CHARGE_Q = 1, FIN_RESID = 2, FIN_PHI = 3, FIN_DIAG
 // fixed order, then derive the scalars of `mode`. One block of 256 threads:
 // run-to-run reproducible.
 __global__ void k_finalize(const double *part, int nblocks, int K, int mode, Phys ph,
-                           double *scal, double *diag, long long step)
+                           double *scal, float *scalf, double *diag, long long step)
 {
     __shared__ double sh[256];
     __shared__ double res[16];
@@ -73,8 +74,9 @@ __global__ void k_finalize(const double *part, int nblocks, int K, int mode, Phy
     }
     if (t != 0) return;
     if (mode == FIN_CHARGE_AB) {
-        scal[S_SA] = res[0];
-        scal[S_SB] = res[1];
+        // the factors of Eq. (surface-q2): Q_b / sum(rho theta), Q_s / sum(|grad rho|^2 (1 + ...))
+        scal[S_SA] = res[0] > 0.0 ? ph.cd.Qb / res[0] : 0.0;
+        scal[S_SB] = res[1] > 0.0 ? ph.cd.Qs / res[1] : 0.0;
     } else if (mode == FIN_CHARGE_Q) {
         scal[S_QSUM] = res[0];
         scal[S_Q2] = res[1];
@@ -104,6 +106,7 @@ __global__ void k_finalize(const double *part, int nblocks, int K, int mode, Phy
         diag[16] = scal[S_QMEAN];
         diag[17] = (double)step;
     }
+    for (int i = 0; i < S_NSCAL; i++) scalf[i] = (float)scal[i];
 }
 
 bool cuda_ok(cudaError_t e) { return e == cudaSuccess; }
@@ -149,7 +152,7 @@ void free_bufs(elbm_handle *h)
 {
     void *ptrs[] = {h->b.fA, h->b.fB, h->b.gA, h->b.gB, h->b.rho, h->b.q, h->b.phi, h->b.ux,
                     h->b.uy, h->b.uz, h->b.alpha, h->b.nu, h->b.mask, h->b.nh, h->b.ab,
-                    h->b.part, h->b.scal, h->b.diag};
+                    h->b.part, h->b.scal, h->b.scalf, h->b.diag};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (h->pin) cudaFreeHost(h->pin);
@@ -160,7 +163,8 @@ void free_bufs(elbm_handle *h)
 void finalize(elbm_handle *h, int K, int mode)
 {
     h->launches += 1;
-    k_finalize<<<1, 256, 0, h->s>>>(h->b.part, h->L.nblocks, K, mode, h->ph, h->b.scal, h->b.diag, h->step);
+    k_finalize<<<1, 256, 0, h->s>>>(h->b.part, h->L.nblocks, K, mode, h->ph, h->b.scal, h->b.scalf,
+                                    h->b.diag, h->step);
 }
 
 elbm_status poisson(elbm_handle *h)
@@ -193,8 +197,8 @@ elbm_status poisson(elbm_handle *h)
             checked_last = true;
             if (conv || k >= maxit) break;
         }
-        o.sor(h->g, h->ph, h->b, 0, h->L, h->s);
-        o.sor(h->g, h->ph, h->b, 1, h->L, h->s);
+        o.sor(h->g, h->ph, h->b, 0, h->Lh, h->s);
+        o.sor(h->g, h->ph, h->b, 1, h->Lh, h->s);
         h->launches += 2;
         checked_last = false;
         k++;
@@ -306,7 +310,6 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     for (int a = 0; a < 3; a++) g.per[a] = p->face_bc[2 * a] == ELBM_FACE_PERIODIC;
     for (int f = 0; f < 6; f++) g.phi_kind[f] = p->phi_bc[f];
     g.phi_axis = p->phi_axis;
-    g.phi_lo = p->phi_lo; g.phi_hi = p->phi_hi; g.phi_solid = p->phi_solid;
 
     long long n_fluid = N, n_solid = 0;
     if (in->mask) {
@@ -323,21 +326,34 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
         if (p->phi_bc[f] == ELBM_PHI_DIRICHLET) h->has_dirichlet = 1;
 
     Phys &ph = h->ph;
-    ph.G = p->G; ph.Gw = p->Gw; ph.rho0 = p->rho0; ph.eps_kappa = p->eps_kappa;
-    ph.sigma_liq = p->sigma_liq; ph.sigma_gas = p->sigma_gas;
-    ph.tau_q = 0.5 + p->Dq / CS2Q;
-    for (int a = 0; a < 3; a++) ph.E_ext[a] = p->E_ext[a];
-    ph.Q_b = p->Q_b; ph.Q_s = p->Q_s; ph.K_d = p->K_d; ph.xi_b = p->xi_b; ph.xi_s = p->xi_s;
-    ph.theta_width = p->theta_width;
-    ph.omega = p->sor_omega; ph.tol = p->poisson_tol; ph.eq_tol = p->alpha_eq_tol;
+    Cst<double> &k = ph.cd;
+    k.G = p->G; k.Gw = p->Gw; k.rho0 = p->rho0; k.irho0 = 1.0 / p->rho0;
+    k.kap = p->eps_kappa / p->rho0;
+    k.sig_g = p->sigma_gas; k.dsig = p->sigma_liq - p->sigma_gas;
+    k.itw = p->theta_width > 0.0 ? 1.0 / p->theta_width : 0.0;
+    k.itau_q = 1.0 / (0.5 + p->Dq / CS2Q);
+    for (int a = 0; a < 3; a++) k.E[a] = p->E_ext[a];
+    k.Qb = p->Q_b; k.Qs = p->Q_s; k.iKd = 1.0 / p->K_d; k.xib = p->xi_b; k.xis = p->xi_s;
+    k.omega = p->sor_omega;
+    k.eq_tol = p->alpha_eq_tol;
+    const int nax[3] = {p->nx, p->ny, p->nz};
+    k.phi_lo = p->phi_lo; k.phi_hi = p->phi_hi; k.phi_solid = p->phi_solid;
+    k.phi_slope = (p->phi_hi - p->phi_lo) / (nax[p->phi_axis] + 1.0);
+    k.nu0 = p->nu0; k.nu_inf = p->nu_inf; k.lam = p->lambda; k.nexp = 0.5 * (p->n_carreau - 1.0);
+    Cst<float> &kf = ph.cf;
+    {
+        const double *src = (const double *)&k;
+        float *dst = (float *)&kf;
+        for (size_t i = 0; i < sizeof(Cst<double>) / sizeof(double); i++) dst[i] = (float)src[i];
+    }
+    ph.tol = p->poisson_tol;
     ph.rho_in = p->rho_in; ph.rho_out = p->rho_out;
     ph.n_fluid = (double)n_fluid;
     ph.n_unknown = (double)(N - n_solid);
     ph.charge_model = p->charge_model; ph.force_el = p->force_el; ph.alpha_mode = p->alpha_mode;
     ph.aprec = p->precision == ELBM_PREC_FP64 ? ELBM_APREC_FP64 : p->alpha_precision;
     ph.store_macro = p->store_macro; ph.neutralize = p->neutralize;
-    ph.rheo.nu0 = p->nu0; ph.rheo.nu_inf = p->nu_inf; ph.rheo.lambda = p->lambda; ph.rheo.n = p->n_carreau;
-    ph.rheo.newtonian = (p->n_carreau == 1.0 || p->lambda == 0.0 || p->nu0 == p->nu_inf) ? 1 : 0;
+    ph.newtonian = (p->n_carreau == 1.0 || p->lambda == 0.0 || p->nu0 == p->nu_inf) ? 1 : 0;
 
     Launch &L = h->L;
     int bx = p->nx >= 128 ? 128 : ((p->nx + 31) / 32) * 32;
@@ -346,6 +362,15 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     L.grid = dim3((p->nx + bx - 1) / bx, (p->ny + by - 1) / by, p->nz);
     L.nblocks = (int)(L.grid.x * L.grid.y * L.grid.z);
     if (L.grid.y > 65535 || L.grid.z > 65535) { delete h; return ELBM_E_INVAL; }
+    {
+        Launch &H = h->Lh;
+        const int nh = (p->nx + 1) / 2;
+        int hx = nh >= 128 ? 128 : ((nh + 31) / 32) * 32;
+        int hy = 128 / hx;
+        H.block = dim3(hx, hy, 1);
+        H.grid = dim3((nh + hx - 1) / hx, (p->ny + hy - 1) / hy, p->nz);
+        H.nblocks = (int)(H.grid.x * H.grid.y * H.grid.z);
+    }
 
     switch (p->precision) {
     case ELBM_PREC_FP64: h->ops = ops_fp64(); h->pop_bytes = 8; h->sc_bytes = 8; h->g_bytes = 8; break;
@@ -384,6 +409,7 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     }
     alloc((void **)&b.part, (size_t)L.nblocks * D_NPART * sizeof(double));
     alloc((void **)&b.scal, S_NSCAL * sizeof(double));
+    alloc((void **)&b.scalf, S_NSCAL * sizeof(float));
     alloc((void **)&b.diag, ELBM_NDIAG * sizeof(double));
     if (ok && !cuda_ok(cudaMallocHost((void **)&h->pin, 16 * sizeof(double)))) ok = false;
     if (ok && p->profile)

@@ -73,7 +73,21 @@ struct Geom {
     int phi_kind[6];     // ELBM_PHI_* per face
     int phi_axis;
     int has_mask;        // any non-fluid node
-    double phi_lo, phi_hi, phi_solid;
+};
+
+// Constants of one step in the arithmetic type T, precomputed on the host so
+// FP32 kernels never touch GB300's slow FP64 pipe.
+template <typename T>
+struct Cst {
+    T G, Gw, rho0, irho0, kap;       // Shan-Chen; eps = 1 + kap rho
+    T sig_g, dsig, itw;              // sigma = sig_g + dsig theta(rho), 1/theta_width
+    T itau_q;                        // 1/tau of the charge LB
+    T E[3];                          // applied field
+    T Qb, Qs, iKd, xib, xis;         // charge models
+    T omega;                         // SOR relaxation
+    T eq_tol;                        // alpha near-equilibrium threshold
+    T phi_lo, phi_hi, phi_solid, phi_slope;  // potential data; slope = (hi - lo)/(n_axis + 1)
+    T nu0, nu_inf, lam, nexp;        // Carreau: nexp = (n - 1)/2
 };
 
 // neighbour coordinate along one axis: -1 when it leaves through a wall face
@@ -87,13 +101,13 @@ __device__ __forceinline__ int nbc(int v, int n, int per)
 // potential on the ghost node beyond face `face` seen from (x,y,z): the
 // electrode value on faces normal to phi_axis, the linear profile between
 // them on the other Dirichlet faces
-__device__ __forceinline__ double phi_ghost(const Geom &g, int face, int x, int y, int z)
+template <typename T>
+__device__ __forceinline__ T phi_ghost(const Geom &g, const Cst<T> &k, int face, int x, int y, int z)
 {
     int axis = face >> 1;
-    if (axis == g.phi_axis) return (face & 1) ? g.phi_hi : g.phi_lo;
+    if (axis == g.phi_axis) return (face & 1) ? k.phi_hi : k.phi_lo;
     int c = g.phi_axis == 0 ? x : (g.phi_axis == 1 ? y : z);
-    int n = g.phi_axis == 0 ? g.nx : (g.phi_axis == 1 ? g.ny : g.nz);
-    return g.phi_lo + (c + 1.0) * (g.phi_hi - g.phi_lo) / (n + 1.0);
+    return k.phi_lo + T(c + 1) * k.phi_slope;
 }
 
 // ---------------------------------------------------------------------------
@@ -139,40 +153,45 @@ __device__ __forceinline__ T sym3_norm2(T a00, T a11, T a22, T a01, T a02, T a12
 // The root lies in [A beta(nu0), A beta(nu_inf)]; safeguarded Newton from the
 // left end of that bracket. Returns nu.
 // ---------------------------------------------------------------------------
-struct Rheo {
-    double nu0, nu_inf, lambda, n;
-    int newtonian;
-};
+__device__ __forceinline__ float powT(float b, float e) { return __powf(b, e); }
+__device__ __forceinline__ double powT(double b, double e) { return pow(b, e); }
 
 template <typename T>
-__device__ __forceinline__ T carreau_nu(const Rheo &R, T Pn, T alpha, T rho)
+__device__ __forceinline__ T carreau_nu(const Cst<T> &k, bool newtonian, T Pn, T alpha, T rho)
 {
     const T cs2 = T(1.0 / 3.0);
-    const T nu0 = T(R.nu0), nui = T(R.nu_inf), lam = T(R.lambda), en = T(R.n);
-    if (R.newtonian) return nu0;
+    if (newtonian) return k.nu0;
     T A = Pn * alpha / (rho * cs2);
-    if (A == T(0)) return nu0;
-    T lo = A * cs2 / (T(2) * nu0 + cs2), hi = A * cs2 / (T(2) * nui + cs2);
-    T x = lo, nux = nu0;
+    if (A == T(0)) return k.nu0;
+    T lo = A * cs2 / (T(2) * k.nu0 + cs2), hi = A * cs2 / (T(2) * k.nu_inf + cs2);
+    T x = lo;
     const T eps = sizeof(T) == 8 ? T(4e-16) : T(2e-7);
-    for (int it = 0; it < 100; it++) {
-        T lg = lam * x;
+    const int itmax = sizeof(T) == 8 ? 100 : 30;
+    for (int it = 0; it < itmax; it++) {
+        T lg = k.lam * x;
         T base = T(1) + lg * lg;
-        T pw = pow(base, T(0.5) * (en - T(1)));
-        nux = nui + (nu0 - nui) * pw;
+        T pw = powT(base, k.nexp);
+        T nux = k.nu_inf + (k.nu0 - k.nu_inf) * pw;
         T den = T(2) * nux + cs2;
         T gx = x - A * cs2 / den;
-        if (gx == T(0)) break;
-        if (gx < T(0)) lo = x; else hi = x;
-        T dnu = (nu0 - nui) * (en - T(1)) * lam * lam * x * pw / base;
-        T gp = T(1) - A * (T(-2) * cs2 / (den * den)) * dnu;
-        T xn = x - gx / gp;
-        if (!(xn > lo && xn < hi)) xn = T(0.5) * (lo + hi);
-        if (fabs(xn - x) <= eps * fabs(x) || hi - lo <= eps * hi) { x = xn; break; }
-        x = xn;
+        bool done = (gx == T(0));
+        if (!done) {
+            if (gx < T(0)) lo = x; else hi = x;
+            T dnu = (k.nu0 - k.nu_inf) * T(2) * k.nexp * k.lam * k.lam * x * pw / base;
+            T gp = T(1) - A * (T(-2) * cs2 / (den * den)) * dnu;
+            T xn = x - gx / gp;
+            if (!(xn > lo && xn < hi)) xn = T(0.5) * (lo + hi);
+            done = fabs(xn - x) <= eps * fabs(x) || hi - lo <= eps * hi;
+            x = xn;
+        }
+        if (sizeof(T) == 8) {
+            if (done) break;
+        } else if (__all_sync(__activemask(), done)) {
+            break;  // FP32: leave together, no divergent tail
+        }
     }
-    T lg = lam * x;
-    return nui + (nu0 - nui) * pow(T(1) + lg * lg, T(0.5) * (en - T(1)));
+    T lg = k.lam * x;
+    return k.nu_inf + (k.nu0 - k.nu_inf) * powT(T(1) + lg * lg, k.nexp);
 }
 
 // ---------------------------------------------------------------------------
@@ -242,99 +261,102 @@ __device__ __forceinline__ AlphaOut alpha_fp64(const double *f, const double *d,
     return o;
 }
 
-// phi(y) = (1+y) ln(1+y) - y and ln(1+y) in FP32 without cancellation: the
-// alternating series for |y| < 1/16 (error below the FP32 unit roundoff),
-// the library log1pf otherwise.
-__device__ __forceinline__ void phi_log1p_f32(float y, float *phi, float *l)
+// ln(1+y) and phi(y) = (1+y) ln(1+y) - y in FP32 without cancellation, from
+// the atanh series in s = y/(2+y): ln(1+y) = 2 s A(s^2), A(t) = sum t^k/(2k+1),
+// and phi(y) = 2 s^2 (s A1 + A)/(1 - s), A1 = (A - 1)/t = sum t^k/(2k+3).
+// For |s| <= 1/3 (y in [-1/2, 1]) eight terms leave a truncation error below
+// 1e-8 relative; outside, the library log1pf (rare: strong non-equilibrium).
+__device__ __forceinline__ void lphi_f32(float y, float *l, float *ph)
 {
-    if (fabsf(y) < 0.0625f) {
-        // ln(1+y) = y - y^2/2 + y^3/3 - ... ; phi = y^2/2 - y^3/6 + y^4/12 - y^5/20 + y^6/30 - y^7/42
-        float y2 = y * y;
-        *l = y * (1.f + y * (-0.5f + y * (1.f / 3 + y * (-0.25f + y * (0.2f + y * (-1.f / 6 + y * (1.f / 7)))))));
-        *phi = y2 * (0.5f + y * (-1.f / 6 + y * (1.f / 12 + y * (-1.f / 20 + y * (1.f / 30 + y * (-1.f / 42))))));
+    float s = __fdividef(y, 2.f + y);
+    if (fabsf(s) <= 0.3334f) {
+        float t = s * s;
+        float A1 = 1.f / 3 + t * (1.f / 5 + t * (1.f / 7 + t * (1.f / 9 + t * (1.f / 11 + t * (1.f / 13 + t * (1.f / 15 + t * (1.f / 17)))))));
+        float A = 1.f + t * A1;
+        *l = 2.f * s * A;
+        *ph = __fdividef(2.f * t * (s * A1 + A), 1.f - s);
     } else {
         float lg = log1pf(y);
         *l = lg;
-        *phi = (1.f + y) * lg - y;
+        *ph = (1.f + y) * lg - y;
     }
 }
 
-// FP32: the same root of the same equation, with h split into pieces that
-// carry no cancellation: sum_p f_p phi(a x_p) (non-negative terms) and
-// a h'(0), where h'(0) = (1 + ln rho) sum D + sum D_p ln(f_p/(w_p rho)) and
-// sum D is accumulated with an error-free transformation (TwoSum, Knuth).
-// Converges to working precision.
+// FP32: the same root of the same equation. h(a) = sum_p f_p phi(a x_p) + a h'(0)
+// with h'(0) = (1 + ln rho) sum D + sum D_p ln(f_p/(w_p rho)) (sum D by TwoSum,
+// Knuth); no term carries cancellation. Start from the root of the moment
+// expansion h(a)/a ~ h'(0) + a M2/2 - a^2 M3/6 + a^3 M4/12 (M_k = sum f x^k),
+// then safeguarded Newton steps on the exact h (at most 12; two or three near
+// equilibrium); the warp leaves the loop together once every lane has
+// converged, so only warps holding strongly non-equilibrium sites iterate on.
 __device__ __forceinline__ AlphaOut alpha_fp32(const float *f, const float *d, const float *fdev,
                                                float rho, float drho, float eq_tol)
 {
     AlphaOut o; o.alpha = 2.0; o.herr = 0.0; o.status = 0;
     float x[Q];
-    float maxabs = 0.f, amax = 1e30f;
-    float s = 0.f, c = 0.f, tl = 0.f;
-    const float lr = logf(rho);
+    float maxabs = 0.f, xneg = 0.f;
+    float s = 0.f, c = 0.f, tl = 0.f, M2 = 0.f, M3 = 0.f, M4 = 0.f;
+    const float lr = __logf(rho);
+    const float irho = 1.f / rho;
 #pragma unroll
     for (int p = 0; p < Q; p++) {
-        x[p] = d[p] / f[p];
+        x[p] = __fdividef(d[p], f[p]);
         maxabs = fmaxf(maxabs, fabsf(x[p]));
-        if (d[p] < 0.f) amax = fminf(amax, -f[p] / d[p]);
-        // TwoSum of the running sum of D
+        xneg = fminf(xneg, x[p]);
         float t = s + d[p];
         float bp = t - s;
         c += (s - (t - bp)) + (d[p] - bp);
         s = t;
-        // ln(f_p/(w_p rho)) = log1p((d_p - w_p drho)/(w_p rho)) from the stored deviation
-        float wp = float(wq(p));
-        float z = (fdev[p] - wp * drho) / (wp * rho);
+        const float iw = float(1.0 / wq(p));
+        float z = (fdev[p] - float(wq(p)) * drho) * iw * irho;
         float lz, ph;
-        phi_log1p_f32(z, &ph, &lz);
+        lphi_f32(z, &lz, &ph);
         tl += d[p] * lz;
+        float fx2 = f[p] * x[p] * x[p];
+        M2 += fx2;
+        M3 += fx2 * x[p];
+        M4 += fx2 * x[p] * x[p];
     }
-    float sumD = s + c;
-    float a0 = (1.f + lr) * sumD + tl;
+    const float a0 = (1.f + lr) * (s + c) + tl;
     if (!(maxabs >= eq_tol)) { o.status = 1; return o; }
     if (a0 >= 0.f) { o.status = 2; return o; }
-    auto hval = [&](float a, float *hp) {
-        float h = 0.f, g = 0.f;
+    const float amax = xneg < 0.f ? -1.f / xneg : 1e30f;
+    // start: root of a0 + a M2/2 - a^2 M3/6 + a^3 M4/12, Newton from -2 a0/M2
+    float a = -2.f * a0 / M2;
+    for (int it = 0; it < 3; it++) {
+        float g = a0 + a * (0.5f * M2 + a * (-M3 / 6.f + a * (M4 / 12.f)));
+        float gp = 0.5f * M2 + a * (-M3 / 3.f + a * (M4 / 4.f));
+        float an = a - g / gp;
+        if (an > 0.f && an < 8.f) a = an;
+    }
+    float lo = 0.f, hi = amax * (1.f - 1e-6f);
+    if (!(a > lo && a < hi)) a = fminf(2.f, 0.5f * hi);
+    float h = 0.f;
+    bool clipped = false;
+    for (int it = 0; it < 12; it++) {
+        float hh = 0.f, g = 0.f;
 #pragma unroll
         for (int p = 0; p < Q; p++) {
-            float ph, l;
             float y = a * x[p];
-            if (1.f + y <= 0.f) {
-                // at the positivity bound (1+y) ln(1+y) -> 0, so phi -> -y
-                ph = -y;
-                l = -88.f;
-            } else {
-                phi_log1p_f32(y, &ph, &l);
-            }
-            h += f[p] * ph;
+            float l, ph;
+            if (1.f + y <= 0.f) { ph = -y; l = -88.f; }
+            else lphi_f32(y, &l, &ph);
+            hh += f[p] * ph;
             g += d[p] * l;
         }
-        *hp = g + a0;
-        return h + a * a0;
-    };
-    float lo = 0.f, hi, hp;
-    if (amax < 1e29f) {
-        hi = amax * (1.f - 1e-6f);
-        if (hval(hi, &hp) < 0.f) { o.alpha = hi; o.status = 3; return o; }
-    } else {
-        hi = 4.f;
-        int k = 0;
-        while (hval(hi, &hp) < 0.f && k++ < 60) hi *= 2.f;
-    }
-    float a = 2.f;
-    if (!(a > lo && a < hi)) a = 0.5f * (lo + hi);
-    float h = 0.f;
-    for (int it = 0; it < 40; it++) {
-        h = hval(a, &hp);
-        if (h == 0.f) break;
+        h = hh + a * a0;
+        float hp = g + a0;
         if (h < 0.f) lo = a; else hi = a;
         float an = a - h / hp;
         if (!(an > lo && an < hi)) an = 0.5f * (lo + hi);
-        if (fabsf(an - a) <= 2e-7f * fabsf(a) || hi - lo <= 2e-7f * hi) { a = an; break; }
+        bool done = fabsf(an - a) <= 4e-7f * a || h == 0.f;
         a = an;
+        if (__all_sync(__activemask(), done)) break;
     }
+    if (a >= amax * (1.f - 2e-6f)) clipped = true;
     o.alpha = a;
     o.herr = fabsf(h) / rho;
+    o.status = clipped ? 3 : 0;
     return o;
 }
 

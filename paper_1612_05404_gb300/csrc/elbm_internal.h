@@ -20,14 +20,16 @@ enum {
 };
 
 struct Phys {
-    double G, Gw, rho0, eps_kappa, sigma_liq, sigma_gas, tau_q;
-    double E_ext[3];
-    double Q_b, Q_s, K_d, xi_b, xi_s, theta_width;
-    double omega, tol, eq_tol, rho_in, rho_out;
+    Cst<double> cd;                   // constants in FP64
+    Cst<float> cf;                    // the same constants rounded to FP32
+    double tol, rho_in, rho_out;      // host / reduction-side values
     double n_fluid, n_unknown;
-    int charge_model, force_el, alpha_mode, aprec, store_macro, neutralize;
-    Rheo rheo;
+    int charge_model, force_el, alpha_mode, aprec, store_macro, neutralize, newtonian;
 };
+
+template <typename T> __host__ __device__ __forceinline__ const Cst<T> &cst(const Phys &ph);
+template <> __host__ __device__ __forceinline__ const Cst<double> &cst<double>(const Phys &ph) { return ph.cd; }
+template <> __host__ __device__ __forceinline__ const Cst<float> &cst<float>(const Phys &ph) { return ph.cf; }
 
 struct Bufs {
     void *fA, *fB, *gA, *gB;          // populations (current A, next B)
@@ -38,6 +40,7 @@ struct Bufs {
     void *ab;                         // paper-mode charge: 2 planes a, b
     double *part;                     // per-block partial sums
     double *scal;                     // device scalars (S_*)
+    float *scalf;                     // the same scalars rounded to FP32
     double *diag;                     // ELBM_NDIAG diagnostics
 };
 

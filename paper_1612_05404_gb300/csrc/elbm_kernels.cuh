@@ -149,21 +149,26 @@ __device__ __forceinline__ int block_id() { return blockIdx.x + gridDim.x * (blo
 
 // Potential of the face neighbour along +-axis (Sec. II Poisson problem):
 // kind 0 = unknown (index in *nb), 1 = Dirichlet value in *v, 2 = no term.
-__device__ __forceinline__ int pois_nb(const Geom &g, const unsigned char *mask, const Nbr &n,
-                                       int x, int y, int z, int axis, int sign, ll *nb, double *v)
+template <typename T>
+__device__ __forceinline__ int pois_nb(const Geom &g, const Cst<T> &k, const unsigned char *mask,
+                                       const Nbr &n, int x, int y, int z, int axis, int sign, ll *nb, T *v)
 {
     int o[3] = {0, 0, 0};
     o[axis] = sign;
     ll i = nbr_idx(n, g, o[0], o[1], o[2]);
     if (i < 0) {
         int face = 2 * axis + (sign > 0 ? 1 : 0);
-        if (g.phi_kind[face] == ELBM_PHI_DIRICHLET) { *v = phi_ghost(g, face, x, y, z); return 1; }
+        if (g.phi_kind[face] == ELBM_PHI_DIRICHLET) { *v = phi_ghost<T>(g, k, face, x, y, z); return 1; }
         return 2;
     }
-    if (mask && mask[i] == ELBM_NODE_SOLID) { *v = g.phi_solid; return 1; }
+    if (mask && mask[i] == ELBM_NODE_SOLID) { *v = k.phi_solid; return 1; }
     *nb = i;
     return 0;
 }
+
+template <typename T> __device__ __forceinline__ T scal_of(const Bufs &b, int i);
+template <> __device__ __forceinline__ double scal_of<double>(const Bufs &b, int i) { return b.scal[i]; }
+template <> __device__ __forceinline__ float scal_of<float>(const Bufs &b, int i) { return b.scalf[i]; }
 
 // ===========================================================================
 // Initial state: f(r,0) = f^eq(rho0, u0) (Eq. 2) or the given f0, placed so
@@ -335,8 +340,9 @@ __global__ void __launch_bounds__(128) k_charge_ab(Geom g, Phys ph, Bufs b)
         sc K = -div;
         sc kp = K > sc(0) ? K : sc(0);
         sc r = ((const sc *)b.rho)[s];
-        av = r * theta_of<sc>(r, sc(ph.rho0), sc(ph.theta_width));
-        bv = nh[3 * g.N + s] * (sc(1) + pow(kp / sc(ph.K_d), sc(0.25)));
+        const Cst<sc> &k = cst<sc>(ph);
+        av = r * sc(0.5) * (sc(1) + tanh((r - k.rho0) * k.itw));
+        bv = nh[3 * g.N + s] * (sc(1) + sqrt(sqrt(kp * k.iKd)));
         sc *ab = (sc *)b.ab;
         ab[s] = av;
         ab[g.N + s] = bv;
@@ -357,11 +363,12 @@ __global__ void __launch_bounds__(128) k_charge_q(Geom g, Phys ph, Bufs b)
     sc qv = 0;
     if (active) {
         const sc *ab = (const sc *)b.ab;
+        const Cst<sc> &k = cst<sc>(ph);
         if (ph.charge_model == ELBM_CHARGE_CONSERVED) {
-            double Sa = b.scal[S_SA], Sb = b.scal[S_SB];
-            qv = (Sa > 0.0 ? sc(ph.Q_b / Sa) * ab[s] : sc(0)) + (Sb > 0.0 ? sc(ph.Q_s / Sb) * ab[g.N + s] : sc(0));
+            // S_SA / S_SB slots hold Q_b / sum(a) and Q_s / sum(b) (0 for an empty sum)
+            qv = scal_of<sc>(b, S_SA) * ab[s] + scal_of<sc>(b, S_SB) * ab[g.N + s];
         } else {
-            qv = sc(ph.xi_b) * ab[s] + sc(ph.xi_s) * ab[g.N + s];
+            qv = k.xib * ab[s] + k.xis * ab[g.N + s];
         }
         ((sc *)b.q)[s] = qv;
     } else if (inb) {
@@ -380,38 +387,40 @@ template <int PR>
 __global__ void __launch_bounds__(128) k_sor(Geom g, Phys ph, Bufs b, int color)
 {
     typedef typename Tr<PR>::sc sc;
-    int x, y, z;
-    bool inb;
-    ll s;
-    site_xyz(g, x, y, z, inb, s);
-    if (!inb || ((x + y + z) & 1) != color) return;
+    // one thread per site of the colour: x = 2 i + ((y + z + color) & 1)
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    const int x = 2 * i + ((y + z + color) & 1);
+    if (x >= g.nx || y >= g.ny) return;
+    const ll s = x + (ll)g.nx * (y + (ll)g.ny * z);
     unsigned char kind = b.mask ? b.mask[s] : 0;
     if (kind == ELBM_NODE_SOLID) return;
+    const Cst<sc> &k = cst<sc>(ph);
     Nbr n;
     nbr_init(n, g, x, y, z, s);
     sc *phi = (sc *)b.phi;
     const sc *rho = (const sc *)b.rho;
-    const sc kap = sc(ph.eps_kappa / ph.rho0);
-    sc es = sc(1) + kap * rho[s];
-    sc num = kind == ELBM_NODE_FLUID ? ((const sc *)b.q)[s] - sc(b.scal[S_QMEAN]) : sc(0);
+    sc es = sc(1) + k.kap * rho[s];
+    sc num = kind == ELBM_NODE_FLUID ? ((const sc *)b.q)[s] - scal_of<sc>(b, S_QMEAN) : sc(0);
     sc den = 0;
 #pragma unroll
     for (int a = 0; a < 3; a++)
 #pragma unroll
         for (int sg = -1; sg <= 1; sg += 2) {
             ll nb = 0;
-            double v = 0;
-            int k = pois_nb(g, b.mask, n, x, y, z, a, sg, &nb, &v);
-            if (k == 0) {
-                sc ef = sc(0.5) * (es + (sc(1) + kap * rho[nb]));
+            sc v = 0;
+            int kk = pois_nb<sc>(g, k, b.mask, n, x, y, z, a, sg, &nb, &v);
+            if (kk == 0) {
+                sc ef = sc(0.5) * (es + (sc(1) + k.kap * rho[nb]));
                 num += ef * phi[nb];
                 den += ef;
-            } else if (k == 1) {
-                num += es * sc(v);
+            } else if (kk == 1) {
+                num += es * v;
                 den += es;
             }
         }
-    if (den > sc(0)) phi[s] = (sc(1) - sc(ph.omega)) * phi[s] + sc(ph.omega) * num / den;
+    if (den > sc(0)) phi[s] = (sc(1) - k.omega) * phi[s] + k.omega * num / den;
 }
 
 // residual r = div(eps grad phi) + q - qmean with the reference norms:
@@ -432,10 +441,10 @@ __global__ void __launch_bounds__(128) k_resid(Geom g, Phys ph, Bufs b)
         nbr_init(n, g, x, y, z, s);
         const sc *phi = (const sc *)b.phi;
         const sc *rho = (const sc *)b.rho;
-        const sc kap = sc(ph.eps_kappa / ph.rho0);
-        sc es = sc(1) + kap * rho[s];
+        const Cst<sc> &k = cst<sc>(ph);
+        sc es = sc(1) + k.kap * rho[s];
         sc qs = kind == ELBM_NODE_FLUID ? ((const sc *)b.q)[s] : sc(0);
-        sc r = kind == ELBM_NODE_FLUID ? qs - sc(b.scal[S_QMEAN]) : sc(0);
+        sc r = kind == ELBM_NODE_FLUID ? qs - scal_of<sc>(b, S_QMEAN) : sc(0);
         sc bs = 0;
         sc ps = phi[s];
 #pragma unroll
@@ -443,10 +452,10 @@ __global__ void __launch_bounds__(128) k_resid(Geom g, Phys ph, Bufs b)
 #pragma unroll
             for (int sg = -1; sg <= 1; sg += 2) {
                 ll nb = 0;
-                double v = 0;
-                int k = pois_nb(g, b.mask, n, x, y, z, a, sg, &nb, &v);
-                if (k == 0) r += sc(0.5) * (es + (sc(1) + kap * rho[nb])) * (phi[nb] - ps);
-                else if (k == 1) { r += es * (sc(v) - ps); bs += es * sc(v); }
+                sc v = 0;
+                int kk = pois_nb<sc>(g, k, b.mask, n, x, y, z, a, sg, &nb, &v);
+                if (kk == 0) r += sc(0.5) * (es + (sc(1) + k.kap * rho[nb])) * (phi[nb] - ps);
+                else if (kk == 1) { r += es * (v - ps); bs += es * v; }
             }
         r2 = r * r;
         q2 = qs * qs;
@@ -478,7 +487,7 @@ __global__ void k_phi_shift(Geom g, Bufs b)
     ll s;
     site_xyz(g, x, y, z, inb, s);
     if (!inb || (b.mask && b.mask[s] == ELBM_NODE_SOLID)) return;
-    ((sc *)b.phi)[s] -= sc(b.scal[S_PHIMEAN]);
+    ((sc *)b.phi)[s] -= scal_of<sc>(b, S_PHIMEAN);
 }
 
 // ===========================================================================
@@ -488,7 +497,7 @@ __global__ void k_phi_shift(Geom g, Bufs b)
 // (carreau), (beta); exact-difference source Eq. (add); write f*; in
 // transport mode the D3Q7 charge update. Optional diagnostics per block.
 // ===========================================================================
-template <int PR>
+template <int PR, int AP>
 __global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int diag)
 {
     typedef Tr<PR> T;
@@ -523,8 +532,9 @@ __global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int di
         const ct r = T::dev ? ct(1) + rs : rs;
         const ct drho = T::dev ? rs : rs - ct(1);
 
+        const Cst<ct> &k = cst<ct>(ph);
         // Eq. (sc): F_int = -G psi(r) sum_fluid w psi(r+c) c - G_w psi(r) sum_wall w psi(r) c
-        const ct rho0 = ct(ph.rho0);
+        const ct rho0 = k.rho0;
         const ct ps = psi_of<ct>(r, rho0);
         ct sfx = 0, sfy = 0, sfz = 0, swx = 0, swy = 0, swz = 0;
 #pragma unroll
@@ -535,9 +545,9 @@ __global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int di
             if (wall) { swx += wv * ct(cx(p)); swy += wv * ct(cy(p)); swz += wv * ct(cz(p)); }
             else { sfx += wv * ct(cx(p)); sfy += wv * ct(cy(p)); sfz += wv * ct(cz(p)); }
         }
-        ct Fx = -ct(ph.G) * ps * sfx - ct(ph.Gw) * ps * swx;
-        ct Fy = -ct(ph.G) * ps * sfy - ct(ph.Gw) * ps * swy;
-        ct Fz = -ct(ph.G) * ps * sfz - ct(ph.Gw) * ps * swz;
+        ct Fx = -k.G * ps * sfx - k.Gw * ps * swx;
+        ct Fy = -k.G * ps * sfy - k.Gw * ps * swy;
+        ct Fz = -k.G * ps * sfz - k.Gw * ps * swz;
 
         // electric force q E, E = -grad phi (central differences) + E_ext
         ct qs = 0;
@@ -549,13 +559,13 @@ __global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int di
             for (int a = 0; a < 3; a++) {
                 ct pv[2];
 #pragma unroll
-                for (int k = 0; k < 2; k++) {
+                for (int kk = 0; kk < 2; kk++) {
                     ll nb = 0;
-                    double v = 0;
-                    int kind = pois_nb(g, b.mask, n, x, y, z, a, k ? 1 : -1, &nb, &v);
-                    pv[k] = kind == 0 ? ct(phi[nb]) : (kind == 1 ? ct(v) : phs);
+                    ct v = 0;
+                    int kind = pois_nb<ct>(g, k, b.mask, n, x, y, z, a, kk ? 1 : -1, &nb, &v);
+                    pv[kk] = kind == 0 ? ct(phi[nb]) : (kind == 1 ? v : phs);
                 }
-                E[a] = -(pv[1] - pv[0]) / ct(2) + ct(ph.E_ext[a]);
+                E[a] = -(pv[1] - pv[0]) * ct(0.5) + k.E[a];
             }
             Fx += qs * E[0];
             Fy += qs * E[1];
@@ -577,14 +587,14 @@ __global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int di
         AlphaOut ao;
         ao.alpha = 2.0; ao.herr = 0.0; ao.status = 0;
         if (ph.alpha_mode == ELBM_ALPHA_ENTROPIC) {
-            if (sizeof(ct) == 8 || ph.aprec == ELBM_APREC_FP64) {
+            if (sizeof(ct) == 8 || AP == ELBM_APREC_FP64) {
                 double fd[Q], dd[Q];
 #pragma unroll
                 for (int p = 0; p < Q; p++) {
                     fd[p] = T::dev ? wq(p) + double(f[p]) : double(f[p]);
                     dd[p] = double(D[p]);
                 }
-                ao = alpha_fp64(fd, dd, double(r), ph.eq_tol);
+                ao = alpha_fp64(fd, dd, double(r), ph.cd.eq_tol);
             } else {
                 float ff[Q], dd[Q], fv[Q];
 #pragma unroll
@@ -593,14 +603,14 @@ __global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int di
                     dd[p] = float(D[p]);
                     fv[p] = float(f[p]);
                 }
-                ao = alpha_fp32(ff, dd, fv, float(r), float(drho), float(ph.eq_tol));
+                ao = alpha_fp32(ff, dd, fv, float(r), float(drho), ph.cf.eq_tol);
             }
         }
         const ct alpha = ct(ao.alpha);
 
         // Eq. (stress): Pi = sum (f - f^eq) c c = -sum D c c; 2-norm; Carreau; Eq. (beta)
-        ct nu = ct(ph.rheo.nu0);
-        if (!ph.rheo.newtonian) {
+        ct nu = k.nu0;
+        if (!ph.newtonian) {
             ct pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
 #pragma unroll
             for (int p = 1; p < Q; p++) {
@@ -612,7 +622,7 @@ __global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int di
                 pyz -= D[p] * ct(cy(p) * cz(p));
             }
             ct Pn = sym3_norm2<ct>(pxx, pyy, pzz, pxy, pxz, pyz);
-            nu = carreau_nu<ct>(ph.rheo, Pn, alpha, r);
+            nu = carreau_nu<ct>(k, false, Pn, alpha, r);
         }
         const ct beta = ct(CS2) / (ct(2) * nu + ct(CS2));
         const ct ab = alpha * beta;
@@ -633,8 +643,7 @@ __global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int di
 
         if (ph.charge_model == ELBM_CHARGE_TRANSPORT) {
             // D3Q7 advection-diffusion of q with the Ohmic source R = div(sigma grad phi)
-            const ct ss = ct(ph.sigma_gas) + ct(ph.sigma_liq - ph.sigma_gas) *
-                          theta_of<ct>(ct(rho[s]), rho0, ct(ph.theta_width));
+            const ct ss = k.sig_g + k.dsig * ct(0.5) * (ct(1) + tanh((ct(rho[s]) - rho0) * k.itw));
             const ct phs = ct(phi[s]);
             ct R = 0;
 #pragma unroll
@@ -642,18 +651,17 @@ __global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int di
 #pragma unroll
                 for (int sg = -1; sg <= 1; sg += 2) {
                     ll nb = 0;
-                    double v = 0;
-                    int kind = pois_nb(g, b.mask, n, x, y, z, a, sg, &nb, &v);
+                    ct v = 0;
+                    int kind = pois_nb<ct>(g, k, b.mask, n, x, y, z, a, sg, &nb, &v);
                     if (kind == 0) {
-                        ct sn = ct(ph.sigma_gas) + ct(ph.sigma_liq - ph.sigma_gas) *
-                                theta_of<ct>(ct(rho[nb]), rho0, ct(ph.theta_width));
+                        ct sn = k.sig_g + k.dsig * ct(0.5) * (ct(1) + tanh((ct(rho[nb]) - rho0) * k.itw));
                         R += ct(0.5) * (ss + sn) * (ct(phi[nb]) - phs);
                     } else if (kind == 1) {
-                        R += ss * (ct(v) - phs);
+                        R += ss * (v - phs);
                     }
                 }
             gt *GB = (gt *)b.gB;
-            const ct itq = ct(1) / ct(ph.tau_q);
+            const ct itq = k.itau_q;
 #pragma unroll
             for (int i = 0; i < Q7; i++) {
                 ct gi = ct(gather_g<PR>(g, b.mask, b.gA, n, i));
@@ -806,7 +814,10 @@ struct Launchers {
     }
     static void collide(const Geom &g, const Phys &ph, const Bufs &b, int diag, const Launch &L, cudaStream_t s)
     {
-        k_collide<PR><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
+        if (PR == ELBM_PREC_FP64 || ph.aprec == ELBM_APREC_FP64)
+            k_collide<PR, ELBM_APREC_FP64><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
+        else
+            k_collide<PR, ELBM_APREC_FP32><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
     }
     static void export_pop(const Geom &g, const Bufs &b, double *out, const Launch &L, cudaStream_t s)
     {

@@ -53,11 +53,11 @@ def base_params(**kw) -> dict:
 
 def reduced_precision(p: dict) -> dict:
     """Thresholds for FP32 arithmetic: the near-equilibrium alpha shortcut
-    above the FP32 noise of Delta/f (about 3e-7), and a Poisson tolerance
-    the FP32 potential can reach."""
+    above the FP32 noise of Delta/f (about 3e-7), and a Poisson tolerance of
+    1e-6 (the FP32 potential stops earlier at its rounding floor)."""
     if p["precision"] != "fp64":
         p["alpha_eq_tol"] = max(p["alpha_eq_tol"], 1e-5)
-        p["poisson_tol"] = max(p["poisson_tol"], 1e-5)
+        p["poisson_tol"] = max(p["poisson_tol"], 1e-6)
     return p
 
 
