@@ -166,6 +166,31 @@ size_t elbm_fields_size(const elbm_handle *h, unsigned mask);
  * the paper's method: instrumentation for measuring the method's kernels. */
 elbm_status elbm_pass_times(const elbm_handle *h, double *out, int n);
 
+/* Allocation-free density and mass of a population array. The paper has no
+ * counterpart: this serves callers that may not allocate device memory
+ * (code running during CUDA stream capture, hosts that give the device to
+ * their own memory pool, latency-bound loops that forbid allocator calls).
+ *   f      device FP64 populations, planes f[p*n_sites + site], p = 0..18 (the
+ *          layout elbm_fields(ELBM_F_POP) returns);
+ *   mask   device uint8 node kinds, or NULL for all fluid;
+ *   rho    device FP64 out: sum_p f_p at fluid sites, 0 elsewhere;
+ *   mass   device FP64 out (one value): sum of rho;
+ *   stream cudaStream_t (NULL: the legacy default stream).
+ * All pointers are the caller's; nothing is allocated or freed. Scratch is a
+ * fixed device array of ELBM_NOALLOC_MAX_BLOCKS doubles inside the library,
+ * held by every GPU that loads it until the process exits, so
+ * n_sites <= ELBM_NOALLOC_MAX_SITES (else ELBM_E_INVAL). The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress); make
+ * the first call on each device before any stream capture. Every call uses
+ * the same scratch and leaves its contents behind (each call overwrites the
+ * slots it reads, so nothing needs clearing); calls whose kernels overlap on
+ * the GPU (several streams at once) race on it and must be serialised by the
+ * caller. Returns after enqueueing the work on `stream`. */
+#define ELBM_NOALLOC_MAX_BLOCKS 16384
+#define ELBM_NOALLOC_MAX_SITES (ELBM_NOALLOC_MAX_BLOCKS * 1024LL)
+elbm_status elbm_density_noalloc(const double *f, const unsigned char *mask, long long n_sites,
+                                 double *rho, double *mass, void *stream);
+
 /* Release the handle and its device memory. NULL is a no-op. */
 void elbm_free(elbm_handle *h);
 

@@ -23,7 +23,8 @@ DIAG_NAMES = [
     "max_u", "n_nonfinite", "q_mean", "step", "poisson_sweeps_total", "reserved",
 ]
 EXPORTS = ["elbm_init", "elbm_step", "elbm_fields", "elbm_fields_size", "elbm_free",
-           "elbm_strerror", "elbm_velocity_set", "elbm_pass_times"]
+           "elbm_strerror", "elbm_velocity_set", "elbm_pass_times", "elbm_density_noalloc"]
+NOALLOC_MAX_SITES = 16384 * 1024
 
 _FACE = {"periodic": 0, "wall": 1}
 _PHI = {"periodic": 0, "dirichlet": 1, "neumann": 2}
@@ -99,6 +100,8 @@ def lib():
         L.elbm_velocity_set.restype = ctypes.c_int
         L.elbm_pass_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
         L.elbm_pass_times.restype = ctypes.c_int
+        L.elbm_density_noalloc.argtypes = [vp, vp, ctypes.c_longlong, vp, vp, vp]
+        L.elbm_density_noalloc.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -162,6 +165,13 @@ def _cur_stream():
     except ImportError:
         pass
     return None
+
+
+def density_noalloc(f_ptr: int, mask_ptr, n_sites: int, rho_ptr: int, mass_ptr: int, stream=None) -> int:
+    """elbm_density_noalloc on caller-owned device pointers; returns the status."""
+    return lib().elbm_density_noalloc(ctypes.c_void_p(f_ptr), ctypes.c_void_p(mask_ptr or 0),
+                                      int(n_sites), ctypes.c_void_p(rho_ptr), ctypes.c_void_p(mass_ptr),
+                                      stream)
 
 
 class Sim:
