@@ -55,6 +55,11 @@ enum { ELBM_CHARGE_NONE = 0, ELBM_CHARGE_CONSERVED = 1, ELBM_CHARGE_XI = 2,
        ELBM_CHARGE_TRANSPORT = 3 };
 /* electric force: q E, or Eq. (force_el2) q E + (eps-1)/2 grad|E|^2 */
 enum { ELBM_FEL_QE = 0, ELBM_FEL_FULL = 1 };
+/* Poisson solver: red-black SOR as the paper states it, or geometric
+ * multigrid (red-black Gauss-Seidel smoothing) on the same fine operator with
+ * the same stopping rule; multigrid needs no interior solid nodes and lattice
+ * extents that halve at least once (even, and even on periodic axes) */
+enum { ELBM_POISSON_SOR = 0, ELBM_POISSON_MG = 1 };
 /* relaxation: entropic alpha (Eq. entropic) or alpha = 2 (BGK) */
 enum { ELBM_ALPHA_ENTROPIC = 0, ELBM_ALPHA_BGK = 1 };
 /* population storage / arithmetic:
@@ -94,8 +99,9 @@ typedef struct elbm_params {
     int charge_model;            /* ELBM_CHARGE_* */
     int force_el;                /* ELBM_FEL_* */
     int neutralize;              /* subtract the mean free charge before Poisson */
-    int poisson_maxit;           /* cap on red-black SOR sweeps per step */
-    int poisson_fixed_sweeps;    /* > 0: exactly this many sweeps, no convergence test */
+    int poisson_solver;          /* ELBM_POISSON_* */
+    int poisson_maxit;           /* cap on SOR sweeps (multigrid: V-cycles) per step */
+    int poisson_fixed_sweeps;    /* > 0: exactly this many sweeps (V-cycles), no test */
     int poisson_check_every;     /* convergence test every k sweeps (>= 1); with FP32
                                     potentials a test interval without progress
                                     (residual above 0.97 of the previous test)

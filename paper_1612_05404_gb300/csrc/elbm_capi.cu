@@ -11,8 +11,15 @@
 
 #include "elbm.h"
 #include "elbm_internal.h"
+#include "elbm_kernels.cuh"
 
 using namespace elbm;
+
+namespace {
+constexpr int kMaxLevels = 10;
+constexpr int kNu = 2;             // pre- and post-smoothing sweeps
+constexpr int kCoarseSweeps = 40;  // red-black sweeps on the coarsest level
+}
 
 struct elbm_handle {
     elbm_params p;
@@ -31,6 +38,9 @@ struct elbm_handle {
     double sweeps_total;
     int noconv;
     size_t pop_bytes, g_bytes, sc_bytes;
+    MGOps mg;
+    int nlev;                  // multigrid levels (0 = SOR)
+    MGLevel lev[kMaxLevels];
     cudaEvent_t ev[5];    // pass boundaries when profiling
     double pass_ms[4];
     double prof_steps, prof_collide, prof_sweeps, launches;
@@ -145,6 +155,7 @@ int validate(const elbm_params *p, const elbm_init_fields *in, int n_instances)
     }
     if (p->charge_model == ELBM_CHARGE_TRANSPORT && !(p->Dq >= 0.0)) return 1;
     if (p->diag_every < 0) return 1;
+    if (p->poisson_solver != ELBM_POISSON_SOR && p->poisson_solver != ELBM_POISSON_MG) return 1;
     return 0;
 }
 
@@ -156,6 +167,11 @@ void free_bufs(elbm_handle *h)
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (h->pin) cudaFreeHost(h->pin);
+    for (int l = 1; l < h->nlev; l++) {
+        if (h->lev[l].e) cudaFree(h->lev[l].e);
+        if (h->lev[l].b) cudaFree(h->lev[l].b);
+        if (h->lev[l].eps) cudaFree(h->lev[l].eps);
+    }
     for (int i = 0; i < 5; i++)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
 }
@@ -167,15 +183,41 @@ void finalize(elbm_handle *h, int K, int mode)
                                     h->b.diag, h->step);
 }
 
+void vcycle(elbm_handle *h, int l)
+{
+    const MGOps &m = h->mg;
+    if (l == h->nlev - 1) {
+        m.coarse(h->g, h->lev[l], l, kCoarseSweeps, h->s);
+        h->launches += 1;
+        return;
+    }
+    for (int i = 0; i < kNu; i++) {
+        m.smooth(h->g, h->ph, h->b, h->lev[l], l, 0, h->Lh, h->s);
+        m.smooth(h->g, h->ph, h->b, h->lev[l], l, 1, h->Lh, h->s);
+    }
+    m.restrict_(h->g, h->ph, h->b, h->lev[l], h->lev[l + 1], l, h->s);
+    vcycle(h, l + 1);
+    m.prolong(h->g, h->b, h->lev[l], h->lev[l + 1], l, h->s);
+    for (int i = 0; i < kNu; i++) {
+        m.smooth(h->g, h->ph, h->b, h->lev[l], l, 0, h->Lh, h->s);
+        m.smooth(h->g, h->ph, h->b, h->lev[l], l, 1, h->Lh, h->s);
+    }
+    h->launches += 4 * kNu + 2;
+}
+
 elbm_status poisson(elbm_handle *h)
 {
     const Ops &o = h->ops;
     const int fixed = h->p.poisson_fixed_sweeps;
-    const int ce = h->p.poisson_check_every > 0 ? h->p.poisson_check_every : 8;
+    const int ce = h->nlev > 0 ? 1 : (h->p.poisson_check_every > 0 ? h->p.poisson_check_every : 8);
     const int maxit = h->p.poisson_maxit;
     int k = 0;
     bool conv = false, checked_last = false;
     double prev = -1.0;
+    for (int l = 0; l + 1 < h->nlev; l++) {  // coarse permittivities of this step
+        h->mg.eps(h->g, h->ph, h->b, h->lev[l], h->lev[l + 1], l, h->s);
+        h->launches += 1;
+    }
     for (;;) {
         if (fixed > 0) {
             if (k >= fixed) break;
@@ -197,9 +239,13 @@ elbm_status poisson(elbm_handle *h)
             checked_last = true;
             if (conv || k >= maxit) break;
         }
-        o.sor(h->g, h->ph, h->b, 0, h->Lh, h->s);
-        o.sor(h->g, h->ph, h->b, 1, h->Lh, h->s);
-        h->launches += 2;
+        if (h->nlev > 0) {
+            vcycle(h, 0);
+        } else {
+            o.sor(h->g, h->ph, h->b, 0, h->Lh, h->s);
+            o.sor(h->g, h->ph, h->b, 1, h->Lh, h->s);
+            h->launches += 2;
+        }
         checked_last = false;
         k++;
     }
@@ -372,6 +418,32 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
         H.nblocks = (int)(H.grid.x * H.grid.y * H.grid.z);
     }
 
+    // multigrid hierarchy: halve while every extent is even (and stays even on
+    // periodic axes, for the red-black colouring) and the level has > 64 cells
+    h->nlev = 0;
+    if (p->charge_model != ELBM_CHARGE_NONE && p->poisson_solver == ELBM_POISSON_MG) {
+        if (n_solid > 0) { delete h; return ELBM_E_INVAL; }
+        int n[3] = {p->nx, p->ny, p->nz};
+        h->lev[0].nx = n[0]; h->lev[0].ny = n[1]; h->lev[0].nz = n[2]; h->lev[0].N = N;
+        int L = 1;
+        while (L < kMaxLevels) {
+            bool ok = (long long)n[0] * n[1] * n[2] > 64;
+            for (int a = 0; a < 3; a++) {
+                if ((n[a] & 1) || n[a] < 4) ok = false;
+                if (g.per[a] && ((n[a] / 2) & 1)) ok = false;
+            }
+            if (!ok) break;
+            for (int a = 0; a < 3; a++) n[a] /= 2;
+            h->lev[L].nx = n[0]; h->lev[L].ny = n[1]; h->lev[L].nz = n[2];
+            h->lev[L].N = (long long)n[0] * n[1] * n[2];
+            L++;
+        }
+        const size_t sc_b = p->precision == ELBM_PREC_FP64 ? 8 : 4;
+        if (L < 2 || 3 * (size_t)h->lev[L - 1].N * sc_b > 48 * 1024) { delete h; return ELBM_E_INVAL; }
+        h->nlev = L;
+        h->mg = p->precision == ELBM_PREC_FP64 ? mgops_fp64() : mgops_fp32();
+    }
+
     switch (p->precision) {
     case ELBM_PREC_FP64: h->ops = ops_fp64(); h->pop_bytes = 8; h->sc_bytes = 8; h->g_bytes = 8; break;
     case ELBM_PREC_FP32: h->ops = ops_fp32(); h->pop_bytes = 4; h->sc_bytes = 4; h->g_bytes = 4; break;
@@ -406,6 +478,11 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     if (p->charge_model == ELBM_CHARGE_CONSERVED || p->charge_model == ELBM_CHARGE_XI) {
         alloc(&b.nh, (size_t)4 * N * h->sc_bytes);
         alloc(&b.ab, (size_t)2 * N * h->sc_bytes);
+    }
+    for (int l = 1; l < h->nlev; l++) {
+        alloc(&h->lev[l].e, (size_t)h->lev[l].N * h->sc_bytes);
+        alloc(&h->lev[l].b, (size_t)h->lev[l].N * h->sc_bytes);
+        alloc(&h->lev[l].eps, (size_t)h->lev[l].N * h->sc_bytes);
     }
     alloc((void **)&b.part, (size_t)L.nblocks * D_NPART * sizeof(double));
     alloc((void **)&b.scal, S_NSCAL * sizeof(double));

@@ -68,8 +68,22 @@ struct Ops {
     void (*export_plane)(const void *plane, double *out, long long n, cudaStream_t);
 };
 
+struct MGLevel;  // elbm_kernels.cuh
+struct MGOps {
+    void (*smooth)(const Geom &, const Phys &, const Bufs &, const MGLevel &, int level, int color,
+                   const Launch &fine_half, cudaStream_t);
+    void (*restrict_)(const Geom &, const Phys &, const Bufs &, const MGLevel &F, const MGLevel &C, int level,
+                      cudaStream_t);
+    void (*eps)(const Geom &, const Phys &, const Bufs &, const MGLevel &F, const MGLevel &C, int level,
+                cudaStream_t);
+    void (*prolong)(const Geom &, const Bufs &, const MGLevel &F, const MGLevel &C, int level, cudaStream_t);
+    void (*coarse)(const Geom &, const MGLevel &, int level, int sweeps, cudaStream_t);
+};
+
 Ops ops_fp64();
 Ops ops_fp32();
 Ops ops_bf16();
+MGOps mgops_fp64();
+MGOps mgops_fp32();
 
 }  // namespace elbm

@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(128) k_charge_q(Geom g, Phys ph, Bufs b)
 // half-sweep over the sites of one colour, (x+y+z) mod 2 = color.
 // ===========================================================================
 template <int PR>
-__global__ void __launch_bounds__(128) k_sor(Geom g, Phys ph, Bufs b, int color)
+__global__ void __launch_bounds__(128) k_sor(Geom g, Phys ph, Bufs b, int color, int gauss_seidel)
 {
     typedef typename Tr<PR>::sc sc;
     // one thread per site of the colour: x = 2 i + ((y + z + color) & 1)
@@ -420,7 +420,8 @@ __global__ void __launch_bounds__(128) k_sor(Geom g, Phys ph, Bufs b, int color)
                 den += es;
             }
         }
-    if (den > sc(0)) phi[s] = (sc(1) - k.omega) * phi[s] + k.omega * num / den;
+    const sc w = gauss_seidel ? sc(1) : k.omega;
+    if (den > sc(0)) phi[s] = (sc(1) - w) * phi[s] + w * num / den;
 }
 
 // residual r = div(eps grad phi) + q - qmean with the reference norms:
@@ -801,7 +802,7 @@ struct Launchers {
     }
     static void sor(const Geom &g, const Phys &ph, const Bufs &b, int color, const Launch &L, cudaStream_t s)
     {
-        k_sor<PR><<<L.grid, L.block, 0, s>>>(g, ph, b, color);
+        k_sor<PR><<<L.grid, L.block, 0, s>>>(g, ph, b, color, 0);
     }
     static void resid(const Geom &g, const Phys &ph, const Bufs &b, const Launch &L, cudaStream_t s)
     {
@@ -844,6 +845,297 @@ struct Launchers {
         o.export_pop = export_pop;
         o.export_gpop = export_gpop;
         o.export_plane = export_plane;
+        return o;
+    }
+};
+
+
+// ===========================================================================
+// Geometric multigrid for the same fine-level Poisson operator (an
+// accelerator for the SOR / Gauss-Seidel solve of Sec. II; the stopping rule
+// is the same). Cell-centred coarsening by 2 per axis; coarse cell
+// permittivity = mean of its 8 children; coarse face coupling 2^l (eps_I +
+// eps_J)/2 (flux through a face of area 4^l over a distance 2^l); a coarse
+// Dirichlet face couples with 2 4^l/(2^l + 1) eps_I, which places the
+// boundary where the fine problem has it; restriction sums the 8 child
+// residuals; trilinear (cell-centred) prolongation; red-black Gauss-Seidel
+// smoothing. Level 0 works on phi, q and rho directly; level l >= 1 on the
+// correction e_l, right side b_l and permittivity eps_l.
+// ===========================================================================
+struct MGLevel {
+    int nx, ny, nz;
+    long long N;
+    void *e, *b, *eps;  // level >= 1
+};
+
+template <typename T>
+__device__ __forceinline__ int mg_nbr(int v, int n, int per) { return nbc(v, n, per); }
+
+// red-black Gauss-Seidel half sweep on a coarse level (homogeneous Dirichlet)
+template <typename T>
+__global__ void __launch_bounds__(128) k_mg_smooth(Geom g, MGLevel L, int level, int color)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    const int x = 2 * i + ((y + z + color) & 1);
+    if (x >= L.nx || y >= L.ny) return;
+    const ll s = x + (ll)L.nx * (y + (ll)L.ny * z);
+    T *e = (T *)L.e;
+    const T *b = (const T *)L.b, *ep = (const T *)L.eps;
+    const T kap = T(1 << level), kb = T(2.0 * double(1 << (2 * level)) / double((1 << level) + 1));
+    const T es = ep[s];
+    T num = b[s], den = 0;
+    const int cx_[3] = {x, y, z}, n_[3] = {L.nx, L.ny, L.nz};
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int sg = -1; sg <= 1; sg += 2) {
+            int c[3] = {cx_[0], cx_[1], cx_[2]};
+            int v = nbc(c[a] + sg, n_[a], g.per[a]);
+            if (v < 0) {
+                if (g.phi_kind[2 * a + (sg > 0)] == ELBM_PHI_DIRICHLET) den += kb * es;
+                continue;
+            }
+            c[a] = v;
+            ll nb = c[0] + (ll)L.nx * (c[1] + (ll)L.ny * c[2]);
+            T cf = kap * T(0.5) * (es + ep[nb]);
+            num += cf * e[nb];
+            den += cf;
+        }
+    if (den > T(0)) e[s] = num / den;
+}
+
+// residual of level l at one cell (level 0: phi / q / rho and the Dirichlet data)
+template <int PR>
+__device__ __forceinline__ typename Tr<PR>::sc mg_resid_at(const Geom &g, const Phys &ph, const Bufs &bf,
+                                                          const MGLevel &L, int level, int x, int y, int z)
+{
+    typedef typename Tr<PR>::sc T;
+    const ll s = x + (ll)L.nx * (y + (ll)L.ny * z);
+    const int cx_[3] = {x, y, z}, n_[3] = {L.nx, L.ny, L.nz};
+    if (level == 0) {
+        const Cst<T> &k = cst<T>(ph);
+        const T *phi = (const T *)bf.phi, *rho = (const T *)bf.rho;
+        unsigned char kind = bf.mask ? bf.mask[s] : 0;
+        const T es = T(1) + k.kap * rho[s];
+        const T ps = phi[s];
+        T r = kind == ELBM_NODE_FLUID ? ((const T *)bf.q)[s] - scal_of<T>(bf, S_QMEAN) : T(0);
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int sg = -1; sg <= 1; sg += 2) {
+                int c[3] = {cx_[0], cx_[1], cx_[2]};
+                int v = nbc(c[a] + sg, n_[a], g.per[a]);
+                if (v < 0) {
+                    int face = 2 * a + (sg > 0);
+                    if (g.phi_kind[face] == ELBM_PHI_DIRICHLET) r += es * (phi_ghost<T>(g, k, face, x, y, z) - ps);
+                    continue;
+                }
+                c[a] = v;
+                ll nb = c[0] + (ll)L.nx * (c[1] + (ll)L.ny * c[2]);
+                r += T(0.5) * (es + (T(1) + k.kap * rho[nb])) * (phi[nb] - ps);
+            }
+        return r;
+    }
+    const T *e = (const T *)L.e, *b = (const T *)L.b, *ep = (const T *)L.eps;
+    const T kap = T(1 << level), kb = T(2.0 * double(1 << (2 * level)) / double((1 << level) + 1));
+    const T es = ep[s], xs = e[s];
+    T r = b[s];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int sg = -1; sg <= 1; sg += 2) {
+            int c[3] = {cx_[0], cx_[1], cx_[2]};
+            int v = nbc(c[a] + sg, n_[a], g.per[a]);
+            if (v < 0) {
+                if (g.phi_kind[2 * a + (sg > 0)] == ELBM_PHI_DIRICHLET) r -= kb * es * xs;
+                continue;
+            }
+            c[a] = v;
+            ll nb = c[0] + (ll)L.nx * (c[1] + (ll)L.ny * c[2]);
+            r += kap * T(0.5) * (es + ep[nb]) * (e[nb] - xs);
+        }
+    return r;
+}
+
+// b_{l+1} = sum of the 8 child residuals of level l; e_{l+1} = 0
+template <int PR>
+__global__ void __launch_bounds__(128) k_mg_restrict(Geom g, Phys ph, Bufs bf, MGLevel F, MGLevel C, int level)
+{
+    typedef typename Tr<PR>::sc T;
+    const int X = blockIdx.x * blockDim.x + threadIdx.x;
+    const int Y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int Z = blockIdx.z;
+    if (X >= C.nx || Y >= C.ny) return;
+    T sum = 0;
+#pragma unroll
+    for (int c = 0; c < 8; c++)
+        sum += mg_resid_at<PR>(g, ph, bf, F, level, 2 * X + (c & 1), 2 * Y + ((c >> 1) & 1), 2 * Z + (c >> 2));
+    const ll S = X + (ll)C.nx * (Y + (ll)C.ny * Z);
+    ((T *)C.b)[S] = sum;
+    ((T *)C.e)[S] = T(0);
+}
+
+// coarse permittivity: mean of the 8 children (level 0 children from rho)
+template <int PR>
+__global__ void __launch_bounds__(128) k_mg_eps(Geom g, Phys ph, Bufs bf, MGLevel F, MGLevel C, int level)
+{
+    typedef typename Tr<PR>::sc T;
+    const int X = blockIdx.x * blockDim.x + threadIdx.x;
+    const int Y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int Z = blockIdx.z;
+    if (X >= C.nx || Y >= C.ny) return;
+    const Cst<T> &k = cst<T>(ph);
+    T sum = 0;
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        ll s = (2 * X + (c & 1)) + (ll)F.nx * ((2 * Y + ((c >> 1) & 1)) + (ll)F.ny * (2 * Z + (c >> 2)));
+        sum += level == 0 ? T(1) + k.kap * ((const T *)bf.rho)[s] : ((const T *)F.eps)[s];
+    }
+    ((T *)C.eps)[X + (ll)C.nx * (Y + (ll)C.ny * Z)] = sum * T(0.125);
+}
+
+// trilinear prolongation of e_{l+1} added to level l (phi at level 0).
+// Beyond a Dirichlet face the coarse error is 0, beyond a Neumann face the
+// edge value.
+template <int PR>
+__global__ void __launch_bounds__(128) k_mg_prolong(Geom g, Bufs bf, MGLevel F, MGLevel C, int level)
+{
+    typedef typename Tr<PR>::sc T;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= F.nx || y >= F.ny) return;
+    const T *ec = (const T *)C.e;
+    const int fc[3] = {x, y, z}, nc[3] = {C.nx, C.ny, C.nz};
+    int i0[3], i1[3];
+    bool z1[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        i0[a] = fc[a] >> 1;
+        int o = (fc[a] & 1) ? 1 : -1;  // the other coarse cell of the 3/4 - 1/4 pair
+        int v = nbc(i0[a] + o, nc[a], g.per[a]);
+        z1[a] = false;
+        if (v < 0) {
+            int face = 2 * a + (o > 0);
+            if (g.phi_kind[face] == ELBM_PHI_DIRICHLET) { z1[a] = true; v = i0[a]; }
+            else v = i0[a];
+        }
+        i1[a] = v;
+    }
+    T acc = 0;
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        int ax = c & 1, ay = (c >> 1) & 1, az = c >> 2;
+        if ((ax && z1[0]) || (ay && z1[1]) || (az && z1[2])) continue;
+        T w = (ax ? T(0.25) : T(0.75)) * (ay ? T(0.25) : T(0.75)) * (az ? T(0.25) : T(0.75));
+        int X = ax ? i1[0] : i0[0], Y = ay ? i1[1] : i0[1], Z = az ? i1[2] : i0[2];
+        acc += w * ec[X + (ll)C.nx * (Y + (ll)C.ny * Z)];
+    }
+    const ll s = x + (ll)F.nx * (y + (ll)F.ny * z);
+    if (level == 0) {
+        if (bf.mask && bf.mask[s] == ELBM_NODE_SOLID) return;
+        ((T *)bf.phi)[s] += acc;
+    } else {
+        ((T *)F.e)[s] += acc;
+    }
+}
+
+// coarsest level: red-black Gauss-Seidel sweeps by one block in shared memory
+template <typename T>
+__global__ void __launch_bounds__(1024) k_mg_coarse(Geom g, MGLevel L, int level, int sweeps)
+{
+    extern __shared__ unsigned char smem_raw[];
+    T *e = (T *)smem_raw;
+    T *b = e + L.N;
+    T *ep = b + L.N;
+    for (ll s = threadIdx.x; s < L.N; s += blockDim.x) {
+        e[s] = ((const T *)L.e)[s];
+        b[s] = ((const T *)L.b)[s];
+        ep[s] = ((const T *)L.eps)[s];
+    }
+    __syncthreads();
+    const T kap = T(1 << level), kb = T(2.0 * double(1 << (2 * level)) / double((1 << level) + 1));
+    const int n_[3] = {L.nx, L.ny, L.nz};
+    for (int it = 0; it < 2 * sweeps; it++) {
+        const int color = it & 1;
+        for (ll s = threadIdx.x; s < L.N; s += blockDim.x) {
+            int x = (int)(s % L.nx), y = (int)((s / L.nx) % L.ny), z = (int)(s / ((ll)L.nx * L.ny));
+            if (((x + y + z) & 1) != color) continue;
+            const int cx_[3] = {x, y, z};
+            T es = ep[s], num = b[s], den = 0;
+            for (int a = 0; a < 3; a++)
+                for (int sg = -1; sg <= 1; sg += 2) {
+                    int c[3] = {cx_[0], cx_[1], cx_[2]};
+                    int v = nbc(c[a] + sg, n_[a], g.per[a]);
+                    if (v < 0) {
+                        if (g.phi_kind[2 * a + (sg > 0)] == ELBM_PHI_DIRICHLET) den += kb * es;
+                        continue;
+                    }
+                    c[a] = v;
+                    ll nb = c[0] + (ll)L.nx * (c[1] + (ll)L.ny * c[2]);
+                    T cf = kap * T(0.5) * (es + ep[nb]);
+                    num += cf * e[nb];
+                    den += cf;
+                }
+            if (den > T(0)) e[s] = num / den;
+        }
+        __syncthreads();
+    }
+    for (ll s = threadIdx.x; s < L.N; s += blockDim.x) ((T *)L.e)[s] = e[s];
+}
+
+// ---------------------------------------------------------------------------
+// Multigrid launchers for one precision.
+// ---------------------------------------------------------------------------
+template <int PR>
+struct MGLaunchers {
+    typedef typename Tr<PR>::sc sc;
+    static dim3 grid_of(int nx, int ny, int nz, dim3 blk) { return dim3((nx + blk.x - 1) / blk.x, (ny + blk.y - 1) / blk.y, nz); }
+    static dim3 blk_of(int nx) { int bx = nx >= 128 ? 128 : ((nx + 31) / 32) * 32; return dim3(bx, 128 / bx, 1); }
+    static void smooth(const Geom &g, const Phys &ph, const Bufs &b, const MGLevel &L, int level, int color,
+                       const Launch &fine_half, cudaStream_t s)
+    {
+        if (level == 0) {
+            k_sor<PR><<<fine_half.grid, fine_half.block, 0, s>>>(g, ph, b, color, 1);
+        } else {
+            const int nh = (L.nx + 1) / 2;
+            dim3 blk = blk_of(nh);
+            k_mg_smooth<sc><<<grid_of(nh, L.ny, L.nz, blk), blk, 0, s>>>(g, L, level, color);
+        }
+    }
+    static void restrict_(const Geom &g, const Phys &ph, const Bufs &b, const MGLevel &F, const MGLevel &C,
+                          int level, cudaStream_t s)
+    {
+        dim3 blk = blk_of(C.nx);
+        k_mg_restrict<PR><<<grid_of(C.nx, C.ny, C.nz, blk), blk, 0, s>>>(g, ph, b, F, C, level);
+    }
+    static void eps(const Geom &g, const Phys &ph, const Bufs &b, const MGLevel &F, const MGLevel &C, int level,
+                    cudaStream_t s)
+    {
+        dim3 blk = blk_of(C.nx);
+        k_mg_eps<PR><<<grid_of(C.nx, C.ny, C.nz, blk), blk, 0, s>>>(g, ph, b, F, C, level);
+    }
+    static void prolong(const Geom &g, const Bufs &b, const MGLevel &F, const MGLevel &C, int level, cudaStream_t s)
+    {
+        dim3 blk = blk_of(F.nx);
+        k_mg_prolong<PR><<<grid_of(F.nx, F.ny, F.nz, blk), blk, 0, s>>>(g, b, F, C, level);
+    }
+    static void coarse(const Geom &g, const MGLevel &L, int level, int sweeps, cudaStream_t s)
+    {
+        size_t sm = 3 * (size_t)L.N * sizeof(sc);
+        int thr = L.N >= 1024 ? 1024 : (int)(((L.N + 31) / 32) * 32);
+        k_mg_coarse<sc><<<1, thr, sm, s>>>(g, L, level, sweeps);
+    }
+    static MGOps table()
+    {
+        MGOps o;
+        o.smooth = smooth;
+        o.restrict_ = restrict_;
+        o.eps = eps;
+        o.prolong = prolong;
+        o.coarse = coarse;
         return o;
     }
 };

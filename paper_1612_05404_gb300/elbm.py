@@ -46,7 +46,7 @@ class Params(ctypes.Structure):
         ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
         ("face_bc", ctypes.c_int * 6), ("phi_bc", ctypes.c_int * 6),
         ("phi_axis", ctypes.c_int), ("charge_model", ctypes.c_int), ("force_el", ctypes.c_int),
-        ("neutralize", ctypes.c_int), ("poisson_maxit", ctypes.c_int),
+        ("neutralize", ctypes.c_int), ("poisson_solver", ctypes.c_int), ("poisson_maxit", ctypes.c_int),
         ("poisson_fixed_sweeps", ctypes.c_int), ("poisson_check_every", ctypes.c_int),
         ("alpha_mode", ctypes.c_int), ("precision", ctypes.c_int),
         ("alpha_precision", ctypes.c_int), ("store_macro", ctypes.c_int),
@@ -128,7 +128,8 @@ def make_params(cfg: dict, stream=None) -> Params:
     P.charge_model = _CHARGE[cfg["charge_model"]]
     P.force_el = _FEL[cfg["force_el"]]
     P.neutralize = int(cfg["neutralize"])
-    P.poisson_maxit = cfg["poisson_maxit"]
+    P.poisson_solver = {"sor": 0, "mg": 1}[cfg.get("poisson_solver", "sor")]
+    P.poisson_maxit = cfg["poisson_maxit"] if P.poisson_solver == 0 else cfg.get("poisson_mg_cycles", 50)
     P.poisson_fixed_sweeps = cfg["poisson_fixed_sweeps"]
     P.poisson_check_every = cfg.get("poisson_check_every", 8)
     P.alpha_mode = _ALPHA[cfg["alpha_mode"]]

@@ -40,7 +40,7 @@ def base_params(**kw) -> dict:
         sor_omega=None, poisson_tol=1e-13, alpha_eq_tol=1e-8,
         rho_in=RHO_L, rho_out=RHO_V,
         # CUDA-side choices (the oracle ignores them)
-        precision="fp64", poisson_check_every=8,
+        precision="fp64", poisson_check_every=8, poisson_solver="sor", poisson_mg_cycles=50,
     )
     p["lambda"] = 0.0
     for k, v in kw.items():
@@ -100,7 +100,7 @@ def charged_drop_at_rest(n=32, radius=8.0, precision="fp64", steps=500, seed=SEE
     sig_l = eps_l / 50.0
     cfg = base_params(shape=shape, charge_model="transport", eps_kappa=kappa,
                       sigma_liq=sig_l, sigma_gas=sig_l / sigma_ratio, Dq=1e-3,
-                      precision=precision, poisson_tol=1e-13)
+                      precision=precision, poisson_tol=1e-13, poisson_solver="mg")
     reduced_precision(cfg)
     cfg["steps"] = steps
     N = n ** 3
@@ -128,7 +128,7 @@ def drop_in_field(E0=1e-3, n=64, radius=12.0, precision="fp32", steps=5000,
         phi_axis=2, phi_lo=0.0, phi_hi=-E0 * (n + 1),
         sigma_liq=sig_l, sigma_gas=sig_l / sigma_ratio, Dq=1e-3,
         nu0=nu0, nu_inf=nu0 / 10.0, n_carreau=n_carreau,
-        precision=precision, poisson_tol=1e-13)
+        precision=precision, poisson_tol=1e-13, poisson_solver="mg")
     reduced_precision(cfg)
     cfg["lambda"] = lam
     cfg["steps"] = steps
