@@ -112,6 +112,9 @@ typedef struct elbm_params {
     int store_macro;             /* keep u, alpha, nu planes for elbm_fields */
     int diag_every;              /* diagnostics every k steps (0 = never) */
     int profile;                 /* time each pass with CUDA events (elbm_pass_times) */
+    int graph;                   /* run each step as one CUDA graph, the Poisson loop a
+                                    device-side while node (needs diag_every = 1);
+                                    0: issue from the host, one sync per test */
     double phi_lo, phi_hi;       /* potential on the ghost planes at axis coord -1 and n */
     double phi_solid;            /* potential of interior solid (conductor) nodes */
     double nu0, nu_inf, lambda, n_carreau;  /* Carreau law; n = 1 is Newtonian nu0 */

@@ -18,7 +18,7 @@ using namespace elbm;
 namespace {
 constexpr int kMaxLevels = 10;
 constexpr int kNu = 2;             // pre- and post-smoothing sweeps
-constexpr int kCoarseSweeps = 40;  // red-black sweeps on the coarsest level
+constexpr int kCoarseSweeps = 8;   // red-black sweeps on the coarsest level (<= 8 cells per axis pair)
 }
 
 struct elbm_handle {
@@ -27,61 +27,74 @@ struct elbm_handle {
     Phys ph;
     Bufs b;
     Launch L;
-    Launch Lh;            // one thread per site of one red-black colour
+    Launch Lh;                 // one thread per site of one red-black colour
     Ops ops;
-    cudaStream_t s;
+    cudaStream_t s;            // the caller's stream: all work runs here
     int has_dirichlet;
-    double *pin;          // pinned host scalars (convergence flag, residual)
+    double *pin;               // pinned host scalars
     long long step;
-    int last_sweeps;
-    double last_resid;
-    double sweeps_total;
-    int noconv;
     size_t pop_bytes, g_bytes, sc_bytes;
     MGOps mg;
     int nlev;                  // multigrid levels (0 = SOR)
     MGLevel lev[kMaxLevels];
-    cudaEvent_t ev[5];    // pass boundaries when profiling
+    int lt;                    // first level solved by the one-CTA tail kernel
+    MGTail tail;
+    int ce;                    // SOR sweeps per convergence test (1 for multigrid)
+    int units_max;             // cap on Poisson units per step
+    cudaStream_t cap, cap2;    // private streams used only to capture graphs
+    cudaGraphExec_t gexec[2];  // one whole step for each A/B parity
+    cudaGraphExec_t gsec[2][3];  // profiling: the step as three section graphs
+    int use_graph;
+    int n_pre, n_body, n_post; // kernels per graph section (launch accounting)
+    double noconv_seen;
+    cudaEvent_t ev[5];         // pass boundaries when profiling
     double pass_ms[4];
     double prof_steps, prof_collide, prof_sweeps, launches;
 };
 
 namespace {
 
-enum { FIN_CHARGE_AB = 0, FIN_CHARGE_Q = 1, FIN_RESID = 2, FIN_PHI = 3, FIN_DIAG = 4 };
+enum { FIN_CHARGE_AB = 0, FIN_CHARGE_Q = 1, FIN_RESID_PRE = 2, FIN_PHI = 3, FIN_DIAG = 4, FIN_RESID_BODY = 5 };
+
+// Control of the Poisson loop, evaluated on the device after each
+// convergence test (so the loop can run inside a CUDA graph).
+struct Ctl {
+    unsigned long long cond;   // cudaGraphConditionalHandle of the while node
+    int use_cond;              // 1 inside a captured graph
+    int fixed;                 // > 0: exactly this many units
+    int units_max;
+    int reduced;               // FP32 potential: stop at the rounding floor
+    int ce;
+};
 
 // Sum (or min / max) each of the K columns of the per-block partials in a
 // fixed order, then derive the scalars of `mode`. One block of 256 threads:
 // run-to-run reproducible.
-__global__ void k_finalize(const double *part, int nblocks, int K, int mode, Phys ph,
-                           double *scal, float *scalf, double *diag, long long step)
+__global__ void k_finalize(const double *part, int nblocks, int K, int mode, Phys ph, Ctl ctl,
+                           double *scal, float *scalf, double *diag)
 {
-    __shared__ double sh[256];
     __shared__ double res[16];
-    const int t = threadIdx.x;
-    for (int k = 0; k < K; k++) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    // one warp per column: lanes stride over the blocks, then a fixed
+    // shuffle tree (reproducible order)
+    for (int k = warp; k < K; k += 8) {
         int op = 0;  // 0 sum, 1 min, 2 max
         if (mode == FIN_DIAG) {
             if (k == D_AMIN) op = 1;
             else if (k == D_AMAX || k == D_HERR || k == D_UMAX) op = 2;
         }
         double acc = op == 1 ? 1e300 : (op == 2 ? -1e300 : 0.0);
-        for (int i = t; i < nblocks; i += 256) {
+        for (int i = lane; i < nblocks; i += 32) {
             double v = part[(long long)i * K + k];
             acc = op == 0 ? acc + v : (op == 1 ? fmin(acc, v) : fmax(acc, v));
         }
-        sh[t] = acc;
-        __syncthreads();
-        for (int w = 128; w > 0; w >>= 1) {
-            if (t < w) {
-                double a = sh[t], c = sh[t + w];
-                sh[t] = op == 0 ? a + c : (op == 1 ? fmin(a, c) : fmax(a, c));
-            }
-            __syncthreads();
+        for (int o = 16; o > 0; o >>= 1) {
+            double c = __shfl_down_sync(0xffffffffu, acc, o);
+            acc = op == 0 ? acc + c : (op == 1 ? fmin(acc, c) : fmax(acc, c));
         }
-        if (t == 0) res[k] = sh[0];
-        __syncthreads();
+        if (lane == 0) res[k] = acc;
     }
+    __syncthreads();
     if (t != 0) return;
     if (mode == FIN_CHARGE_AB) {
         // the factors of Eq. (surface-q2): Q_b / sum(rho theta), Q_s / sum(|grad rho|^2 (1 + ...))
@@ -91,10 +104,27 @@ __global__ void k_finalize(const double *part, int nblocks, int K, int mode, Phy
         scal[S_QSUM] = res[0];
         scal[S_Q2] = res[1];
         scal[S_QMEAN] = (ph.neutralize && ph.n_fluid > 0) ? res[0] / ph.n_fluid : 0.0;
-    } else if (mode == FIN_RESID) {
+    } else if (mode == FIN_RESID_PRE || mode == FIN_RESID_BODY) {
         double rn = sqrt(res[0]), ref = sqrt(res[1]) + sqrt(res[2]);
         scal[S_RESID] = ref > 0.0 ? rn / ref : rn;
-        scal[S_CONV] = (rn <= ph.tol * ref) ? 1.0 : 0.0;
+        double iter = mode == FIN_RESID_PRE ? 0.0 : scal[S_ITER] + 1.0;
+        scal[S_ITER] = iter;
+        if (mode == FIN_RESID_BODY) scal[S_ITER_TOTAL] += 1.0;
+        bool conv = rn <= ph.tol * ref;
+        // FP32 potential: a test interval without progress means its
+        // rounding floor is reached
+        if (!conv && ctl.reduced && mode == FIN_RESID_BODY && rn > 0.97 * scal[S_PREV]) conv = true;
+        scal[S_PREV] = rn;
+        scal[S_CONV] = conv ? 1.0 : 0.0;
+        bool keep;
+        if (ctl.fixed > 0) {
+            keep = iter < ctl.fixed;
+        } else {
+            keep = !conv && iter < ctl.units_max;
+            if (!conv && iter >= ctl.units_max) scal[S_NOCONV] += 1.0;
+        }
+        scal[S_KEEP] = keep ? 1.0 : 0.0;
+        if (ctl.use_cond) cudaGraphSetConditional(ctl.cond, keep ? 1u : 0u);
     } else if (mode == FIN_PHI) {
         scal[S_PHISUM] = res[0];
         scal[S_PHIMEAN] = res[0] / ph.n_unknown;
@@ -110,11 +140,15 @@ __global__ void k_finalize(const double *part, int nblocks, int K, int mode, Phy
         diag[8] = res[D_NSHORT];
         diag[9] = res[D_NNOROOT];
         diag[10] = res[D_NCLIP];
+        diag[11] = scal[S_ITER] * ctl.ce;
+        diag[12] = scal[S_RESID];
         diag[13] = res[D_HERR];
         diag[14] = res[D_UMAX];
         diag[15] = res[D_NBAD];
         diag[16] = scal[S_QMEAN];
-        diag[17] = (double)step;
+        scal[S_STEPS] += 1.0;
+        diag[17] = scal[S_STEPS];
+        diag[18] = scal[S_ITER_TOTAL] * ctl.ce;
     }
     for (int i = 0; i < S_NSCAL; i++) scalf[i] = (float)scal[i];
 }
@@ -174,141 +208,207 @@ void free_bufs(elbm_handle *h)
     }
     for (int i = 0; i < 5; i++)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    for (int i = 0; i < 2; i++) {
+        if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
+        for (int k = 0; k < 3; k++)
+            if (h->gsec[i][k]) cudaGraphExecDestroy(h->gsec[i][k]);
+    }
+    if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->cap2) cudaStreamDestroy(h->cap2);
 }
 
-void finalize(elbm_handle *h, int K, int mode)
+Ctl make_ctl(const elbm_handle *h, unsigned long long cond, int use_cond)
 {
-    h->launches += 1;
-    k_finalize<<<1, 256, 0, h->s>>>(h->b.part, h->L.nblocks, K, mode, h->ph, h->b.scal, h->b.scalf,
-                                    h->b.diag, h->step);
+    Ctl c;
+    c.cond = cond;
+    c.use_cond = use_cond;
+    c.fixed = h->p.poisson_fixed_sweeps;
+    c.units_max = h->units_max;
+    c.reduced = h->p.precision != ELBM_PREC_FP64;
+    c.ce = h->ce;
+    return c;
 }
 
-void vcycle(elbm_handle *h, int l)
+int fin(elbm_handle *h, const Bufs &b, cudaStream_t s, int K, int mode, unsigned long long cond = 0,
+        int use_cond = 0)
+{
+    k_finalize<<<1, 256, 0, s>>>(b.part, h->L.nblocks, K, mode, h->ph, make_ctl(h, cond, use_cond),
+                                 b.scal, b.scalf, b.diag);
+    return 1;
+}
+
+int vcycle(elbm_handle *h, const Bufs &b, cudaStream_t s, int l)
 {
     const MGOps &m = h->mg;
-    if (l == h->nlev - 1) {
-        m.coarse(h->g, h->lev[l], l, kCoarseSweeps, h->s);
-        h->launches += 1;
-        return;
+    if (l == h->lt) {
+        m.tail(h->g, h->tail, kNu, s);
+        return 1;
     }
     for (int i = 0; i < kNu; i++) {
-        m.smooth(h->g, h->ph, h->b, h->lev[l], l, 0, h->Lh, h->s);
-        m.smooth(h->g, h->ph, h->b, h->lev[l], l, 1, h->Lh, h->s);
+        m.smooth(h->g, h->ph, b, h->lev[l], l, 0, h->Lh, s);
+        m.smooth(h->g, h->ph, b, h->lev[l], l, 1, h->Lh, s);
     }
-    m.restrict_(h->g, h->ph, h->b, h->lev[l], h->lev[l + 1], l, h->s);
-    vcycle(h, l + 1);
-    m.prolong(h->g, h->b, h->lev[l], h->lev[l + 1], l, h->s);
+    m.restrict_(h->g, h->ph, b, h->lev[l], h->lev[l + 1], l, s);
+    int n = vcycle(h, b, s, l + 1);
+    m.prolong(h->g, b, h->lev[l], h->lev[l + 1], l, s);
     for (int i = 0; i < kNu; i++) {
-        m.smooth(h->g, h->ph, h->b, h->lev[l], l, 0, h->Lh, h->s);
-        m.smooth(h->g, h->ph, h->b, h->lev[l], l, 1, h->Lh, h->s);
+        m.smooth(h->g, h->ph, b, h->lev[l], l, 0, h->Lh, s);
+        m.smooth(h->g, h->ph, b, h->lev[l], l, 1, h->Lh, s);
     }
-    h->launches += 4 * kNu + 2;
+    return n + 4 * kNu + 2;
 }
 
-elbm_status poisson(elbm_handle *h)
+// moments, and the free charge with its global sums (Sec. II C, item 3)
+int enq_pre(elbm_handle *h, const Bufs &b, cudaStream_t s)
 {
     const Ops &o = h->ops;
-    const int fixed = h->p.poisson_fixed_sweeps;
-    const int ce = h->nlev > 0 ? 1 : (h->p.poisson_check_every > 0 ? h->p.poisson_check_every : 8);
-    const int maxit = h->p.poisson_maxit;
-    int k = 0;
-    bool conv = false, checked_last = false;
-    double prev = -1.0;
-    for (int l = 0; l + 1 < h->nlev; l++) {  // coarse permittivities of this step
-        h->mg.eps(h->g, h->ph, h->b, h->lev[l], h->lev[l + 1], l, h->s);
-        h->launches += 1;
-    }
-    for (;;) {
-        if (fixed > 0) {
-            if (k >= fixed) break;
-        } else if (k % ce == 0 || k >= maxit) {
-            o.resid(h->g, h->ph, h->b, h->L, h->s);
-            h->launches += 1;
-            finalize(h, 3, FIN_RESID);
-            if (!cuda_ok(cudaMemcpyAsync(h->pin, h->b.scal + S_RESID, 2 * sizeof(double),
-                                         cudaMemcpyDeviceToHost, h->s)))
-                return ELBM_E_CUDA;
-            if (!cuda_ok(cudaStreamSynchronize(h->s))) return ELBM_E_CUDA;
-            h->last_resid = h->pin[0];
-            conv = h->pin[1] != 0.0;
-            // reduced precision: the FP32 potential has a rounding floor; a
-            // check interval without progress means the floor is reached
-            if (!conv && h->p.precision != ELBM_PREC_FP64 && prev >= 0.0 && h->pin[0] > 0.97 * prev)
-                conv = true;
-            prev = h->pin[0];
-            checked_last = true;
-            if (conv || k >= maxit) break;
-        }
-        if (h->nlev > 0) {
-            vcycle(h, 0);
-        } else {
-            o.sor(h->g, h->ph, h->b, 0, h->Lh, h->s);
-            o.sor(h->g, h->ph, h->b, 1, h->Lh, h->s);
-            h->launches += 2;
-        }
-        checked_last = false;
-        k++;
-    }
-    if (fixed == 0 && !conv) h->noconv = 1;
-    if (!h->has_dirichlet) {
-        o.phi_mean(h->g, h->ph, h->b, 0, h->L, h->s);
-        finalize(h, 1, FIN_PHI);
-        o.phi_mean(h->g, h->ph, h->b, 1, h->L, h->s);
-        h->launches += 2;
-    }
-    if (!checked_last) {
-        o.resid(h->g, h->ph, h->b, h->L, h->s);
-        h->launches += 1;
-        finalize(h, 3, FIN_RESID);
-        h->last_resid = -1.0;  // read lazily from the device scalars
-    }
-    h->last_sweeps = k;
-    h->sweeps_total += k;
-    return ELBM_OK;
-}
-
-elbm_status one_step(elbm_handle *h, bool diag)
-{
-    const Ops &o = h->ops;
-    const bool prof = h->p.profile != 0;
-    if (prof) cudaEventRecord(h->ev[0], h->s);
-    o.moments(h->g, h->ph, h->b, h->L, h->s);
-    h->launches += 1;
+    int n = 1;
+    o.moments(h->g, h->ph, b, h->L, s);
     const int cm = h->p.charge_model;
     if (cm == ELBM_CHARGE_TRANSPORT) {
-        finalize(h, 2, FIN_CHARGE_Q);
+        n += fin(h, b, s, 2, FIN_CHARGE_Q);
     } else if (cm == ELBM_CHARGE_CONSERVED || cm == ELBM_CHARGE_XI) {
-        o.charge(h->g, h->ph, h->b, 0, h->L, h->s);
-        finalize(h, 2, FIN_CHARGE_AB);
-        o.charge(h->g, h->ph, h->b, 1, h->L, h->s);
-        finalize(h, 2, FIN_CHARGE_Q);
-        h->launches += 3;
+        o.charge(h->g, h->ph, b, 0, h->L, s);
+        n += 2 + fin(h, b, s, 2, FIN_CHARGE_AB);
+        o.charge(h->g, h->ph, b, 1, h->L, s);
+        n += 1 + fin(h, b, s, 2, FIN_CHARGE_Q);
     }
-    if (prof) cudaEventRecord(h->ev[1], h->s);
-    int sweeps0 = (int)h->sweeps_total;
-    if (cm != ELBM_CHARGE_NONE) {
-        elbm_status st = poisson(h);
-        if (st != ELBM_OK) return st;
+    return n;
+}
+
+// coarse permittivities of this step (multigrid)
+int enq_eps(elbm_handle *h, const Bufs &b, cudaStream_t s)
+{
+    for (int l = 0; l < h->lt; l++) h->mg.eps(h->g, h->ph, b, h->lev[l], h->lev[l + 1], l, s);
+    return h->nlev > 0 ? h->lt : 0;
+}
+
+// convergence test: residual sums, then the device-side decision
+int enq_check(elbm_handle *h, const Bufs &b, cudaStream_t s, int mode, unsigned long long cond, int use_cond)
+{
+    h->ops.resid(h->g, h->ph, b, h->L, s);
+    return 1 + fin(h, b, s, 3, mode, cond, use_cond);
+}
+
+// one Poisson unit: a V-cycle, or ce red-black SOR sweeps
+int enq_unit(elbm_handle *h, const Bufs &b, cudaStream_t s)
+{
+    if (h->nlev > 0) return vcycle(h, b, s, 0);
+    for (int i = 0; i < h->ce; i++) {
+        h->ops.sor(h->g, h->ph, b, 0, h->Lh, s);
+        h->ops.sor(h->g, h->ph, b, 1, h->Lh, s);
     }
-    if (prof) cudaEventRecord(h->ev[2], h->s);
-    o.collide(h->g, h->ph, h->b, diag ? 1 : 0, h->L, h->s);
+    return 2 * h->ce;
+}
+
+// zero-mean potential when nothing pins its constant
+int enq_shift(elbm_handle *h, const Bufs &b, cudaStream_t s)
+{
+    if (h->has_dirichlet) return 0;
+    h->ops.phi_mean(h->g, h->ph, b, 0, h->L, s);
+    int n = 1 + fin(h, b, s, 1, FIN_PHI);
+    h->ops.phi_mean(h->g, h->ph, b, 1, h->L, s);
+    return n + 1;
+}
+
+void swap_ab(Bufs &b)
+{
+    void *t = b.fA; b.fA = b.fB; b.fB = t;
+    t = b.gA; b.gA = b.gB; b.gB = t;
+}
+
+// One step issued from the host; the Poisson loop reads the device decision
+// after each test (a host synchronisation per test).
+elbm_status step_host(elbm_handle *h, bool diag)
+{
+    const bool prof = h->p.profile != 0;
+    cudaStream_t s = h->s;
+    const Bufs &b = h->b;
+    const bool charged = h->p.charge_model != ELBM_CHARGE_NONE;
+    if (prof) cudaEventRecord(h->ev[0], s);
+    h->launches += enq_pre(h, b, s);
+    if (prof) cudaEventRecord(h->ev[1], s);
+    if (charged) {
+        h->launches += enq_eps(h, b, s);
+        h->launches += enq_check(h, b, s, FIN_RESID_PRE, 0, 0);
+        for (;;) {
+            if (!cuda_ok(cudaMemcpyAsync(h->pin, b.scal + S_KEEP, sizeof(double), cudaMemcpyDeviceToHost, s)) ||
+                !cuda_ok(cudaStreamSynchronize(s)))
+                return ELBM_E_CUDA;
+            if (h->pin[0] == 0.0) break;
+            h->launches += enq_unit(h, b, s);
+            h->launches += enq_check(h, b, s, FIN_RESID_BODY, 0, 0);
+        }
+        h->launches += enq_shift(h, b, s);
+    }
+    if (prof) cudaEventRecord(h->ev[2], s);
+    h->ops.collide(h->g, h->ph, b, diag ? 1 : 0, h->L, s);
     h->launches += 1;
-    if (prof) cudaEventRecord(h->ev[3], h->s);
-    if (diag) finalize(h, D_NPART, FIN_DIAG);
-    if (prof) {
-        cudaEventRecord(h->ev[4], h->s);
-        if (!cuda_ok(cudaEventSynchronize(h->ev[4]))) return ELBM_E_CUDA;
-        float ms[4];
-        for (int i = 0; i < 4; i++) cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]);
-        for (int i = 0; i < 4; i++) h->pass_ms[i] += ms[i];
-        h->prof_steps += 1;
-        h->prof_collide += 1;
-        h->prof_sweeps += h->sweeps_total - sweeps0;
-    }
-    void *t = h->b.fA; h->b.fA = h->b.fB; h->b.fB = t;
-    t = h->b.gA; h->b.gA = h->b.gB; h->b.gB = t;
-    h->step++;
+    if (prof) cudaEventRecord(h->ev[3], s);
+    if (diag) h->launches += fin(h, b, s, D_NPART, FIN_DIAG);
+    if (prof) cudaEventRecord(h->ev[4], s);
     return cuda_ok(cudaGetLastError()) ? ELBM_OK : ELBM_E_CUDA;
+}
+
+// Capture sections of one step into an executable graph for buffers of the
+// given A/B parity: bit 0 moments and charge, bit 1 the Poisson loop (a
+// device-side while node), bit 2 collision and diagnostics.
+bool capture_step(elbm_handle *h, int parity, cudaGraphExec_t *out, int sections = 7)
+{
+    Bufs b = h->b;
+    if (parity) swap_ab(b);
+    const bool charged = h->p.charge_model != ELBM_CHARGE_NONE && (sections & 2);
+    cudaStream_t s = h->cap;
+    cudaGraph_t graph = nullptr;
+    if (!cuda_ok(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal))) return false;
+    bool ok = true;
+    cudaGraphConditionalHandle cond = 0;
+    int n_pre = 0, n_body = 0, n_post = 0;
+    if (sections & 1) n_pre += enq_pre(h, b, s);
+    if (charged) {
+        cudaStreamCaptureStatus st;
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        ok = ok && cuda_ok(cudaStreamGetCaptureInfo(s, &st, nullptr, &cg, &deps, nullptr, &nd));
+        ok = ok && cuda_ok(cudaGraphConditionalHandleCreate(&cond, cg, 0, cudaGraphCondAssignDefault));
+        n_pre += enq_eps(h, b, s);
+        n_pre += enq_check(h, b, s, FIN_RESID_PRE, cond, 1);
+        cudaGraphNode_t node;
+        cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        ok = ok && cuda_ok(cudaStreamGetCaptureInfo(s, &st, nullptr, &cg, &deps, nullptr, &nd));
+        ok = ok && cuda_ok(cudaGraphAddNode(&node, cg, deps, nullptr, nd, &np));
+        if (ok) {
+            cudaGraph_t body = np.conditional.phGraph_out[0];
+            ok = cuda_ok(cudaStreamBeginCaptureToGraph(h->cap2, body, nullptr, nullptr, 0,
+                                                       cudaStreamCaptureModeThreadLocal));
+            if (ok) {
+                n_body += enq_unit(h, b, h->cap2);
+                n_body += enq_check(h, b, h->cap2, FIN_RESID_BODY, cond, 1);
+                ok = cuda_ok(cudaStreamEndCapture(h->cap2, &body));
+            }
+            ok = ok && cuda_ok(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
+                                                                   cudaStreamSetCaptureDependencies));
+        }
+        n_post += enq_shift(h, b, s);
+    }
+    if (sections & 4) {
+        h->ops.collide(h->g, h->ph, b, 1, h->L, s);
+        n_post += 1 + fin(h, b, s, D_NPART, FIN_DIAG);
+    }
+    ok = cuda_ok(cudaStreamEndCapture(s, &graph)) && ok;
+    if (ok) ok = cuda_ok(cudaGraphInstantiate(out, graph, 0));
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (parity == 0) {  // kernels per section, counted once
+        h->n_pre += n_pre;
+        h->n_body += n_body;
+        h->n_post += n_post;
+    }
+    return ok;
 }
 
 }  // namespace
@@ -427,7 +527,7 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
         h->lev[0].nx = n[0]; h->lev[0].ny = n[1]; h->lev[0].nz = n[2]; h->lev[0].N = N;
         int L = 1;
         while (L < kMaxLevels) {
-            bool ok = (long long)n[0] * n[1] * n[2] > 64;
+            bool ok = true;
             for (int a = 0; a < 3; a++) {
                 if ((n[a] & 1) || n[a] < 4) ok = false;
                 if (g.per[a] && ((n[a] / 2) & 1)) ok = false;
@@ -438,10 +538,26 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
             h->lev[L].N = (long long)n[0] * n[1] * n[2];
             L++;
         }
-        const size_t sc_b = p->precision == ELBM_PREC_FP64 ? 8 : 4;
-        if (L < 2 || 3 * (size_t)h->lev[L - 1].N * sc_b > 48 * 1024) { delete h; return ELBM_E_INVAL; }
+        if (L < 2) { delete h; return ELBM_E_INVAL; }
         h->nlev = L;
+        // tail: from the first level (>= 1) with at most kTailCells cells
+        int lt = 1;
+        while (lt < L - 1 && h->lev[lt].N > kTailCells) lt++;
+        if (h->lev[lt].N > kTailCells || L - lt > kTailMaxLevels) { delete h; return ELBM_E_INVAL; }
+        h->lt = lt;
+        MGTail &t = h->tail;
+        t.nt = L - lt;
+        t.lt = lt;
+        t.total = 0;
+        for (int k = 0; k < t.nt; k++) {
+            t.nx[k] = h->lev[lt + k].nx; t.ny[k] = h->lev[lt + k].ny; t.nz[k] = h->lev[lt + k].nz;
+            t.N[k] = h->lev[lt + k].N;
+            t.off[k] = t.total;
+            t.total += t.N[k];
+        }
+        t.coarse_sweeps = kCoarseSweeps;
         h->mg = p->precision == ELBM_PREC_FP64 ? mgops_fp64() : mgops_fp32();
+        h->mg.prepare();
     }
 
     switch (p->precision) {
@@ -484,6 +600,7 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
         alloc(&h->lev[l].b, (size_t)h->lev[l].N * h->sc_bytes);
         alloc(&h->lev[l].eps, (size_t)h->lev[l].N * h->sc_bytes);
     }
+    if (h->nlev > 0) h->tail.top = h->lev[h->lt];
     alloc((void **)&b.part, (size_t)L.nblocks * D_NPART * sizeof(double));
     alloc((void **)&b.scal, S_NSCAL * sizeof(double));
     alloc((void **)&b.scalf, S_NSCAL * sizeof(float));
@@ -515,6 +632,26 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     for (double *t : tmps)
         if (t) cudaFree(t);
     if (!ok) { free_bufs(h); delete h; return ELBM_E_CUDA; }
+
+    // Poisson loop control: a unit is one V-cycle, or ce SOR sweeps between tests
+    h->ce = (h->nlev > 0 || p->poisson_fixed_sweeps > 0) ? 1
+            : (p->poisson_check_every > 0 ? p->poisson_check_every : 8);
+    h->units_max = (p->poisson_maxit + h->ce - 1) / h->ce;
+    // one CUDA graph per A/B parity; any capture failure keeps the host loop
+    h->use_graph = 0;
+    if (p->graph && p->diag_every == 1) {
+        bool g_ok = cuda_ok(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking)) &&
+                    cuda_ok(cudaStreamCreateWithFlags(&h->cap2, cudaStreamNonBlocking));
+        h->n_pre = h->n_body = h->n_post = 0;
+        if (p->profile) {
+            for (int par = 0; par < 2 && g_ok; par++)
+                for (int sec = 0; sec < 3 && g_ok; sec++) g_ok = capture_step(h, par, &h->gsec[par][sec], 1 << sec);
+        } else {
+            g_ok = g_ok && capture_step(h, 0, &h->gexec[0]) && capture_step(h, 1, &h->gexec[1]);
+        }
+        h->use_graph = g_ok ? 1 : 0;
+        cudaGetLastError();
+    }
     *out = h;
     return ELBM_OK;
 }
@@ -522,19 +659,51 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
 elbm_status elbm_step(elbm_handle *h, int nsteps)
 {
     if (!h || nsteps < 0) return ELBM_E_INVAL;
-    h->noconv = 0;
+    const bool prof = h->p.profile != 0;
     for (int i = 0; i < nsteps; i++) {
-        bool diag = h->p.diag_every > 0 && (((h->step + 1) % h->p.diag_every) == 0 || i == nsteps - 1);
-        elbm_status st = one_step(h, diag);
-        if (st != ELBM_OK) return st;
+        if (h->use_graph && prof) {
+            cudaGraphExec_t *gs = h->gsec[h->step & 1];
+            cudaEventRecord(h->ev[0], h->s);
+            if (!cuda_ok(cudaGraphLaunch(gs[0], h->s))) return ELBM_E_CUDA;
+            cudaEventRecord(h->ev[1], h->s);
+            if (!cuda_ok(cudaGraphLaunch(gs[1], h->s))) return ELBM_E_CUDA;
+            cudaEventRecord(h->ev[2], h->s);
+            if (!cuda_ok(cudaGraphLaunch(gs[2], h->s))) return ELBM_E_CUDA;
+            cudaEventRecord(h->ev[3], h->s);
+            cudaEventRecord(h->ev[4], h->s);
+        } else if (h->use_graph) {
+            if (!cuda_ok(cudaGraphLaunch(h->gexec[h->step & 1], h->s))) return ELBM_E_CUDA;
+        } else {
+            bool diag = h->p.diag_every > 0 && (((h->step + 1) % h->p.diag_every) == 0 || i == nsteps - 1);
+            elbm_status st = step_host(h, diag);
+            if (st != ELBM_OK) return st;
+        }
+        if (prof) {
+            if (!cuda_ok(cudaEventSynchronize(h->ev[4]))) return ELBM_E_CUDA;
+            float ms[4];
+            for (int k = 0; k < 4; k++) cudaEventElapsedTime(&ms[k], h->ev[k], h->ev[k + 1]);
+            for (int k = 0; k < 4; k++) h->pass_ms[k] += ms[k];
+            if (!cuda_ok(cudaMemcpy(h->pin, h->b.scal + S_ITER, sizeof(double), cudaMemcpyDeviceToHost)))
+                return ELBM_E_CUDA;
+            h->prof_steps += 1;
+            h->prof_collide += 1;
+            h->prof_sweeps += h->pin[0] * h->ce;
+            if (h->use_graph) h->launches += h->n_pre + h->n_post + h->pin[0] * h->n_body;
+        }
+        swap_ab(h->b);
+        h->step++;
     }
     if (!cuda_ok(cudaStreamSynchronize(h->s))) return ELBM_E_CUDA;
-    if (nsteps > 0 && h->p.diag_every > 0) {
-        double bad = 0.0;
-        if (!cuda_ok(cudaMemcpy(&bad, h->b.diag + 15, sizeof(double), cudaMemcpyDeviceToHost))) return ELBM_E_CUDA;
-        if (bad != 0.0) return ELBM_E_NUMERIC;
+    if (nsteps > 0) {
+        double v[2] = {0.0, 0.0};
+        if (h->p.diag_every > 0 || h->use_graph) {
+            if (!cuda_ok(cudaMemcpy(&v[0], h->b.diag + 15, sizeof(double), cudaMemcpyDeviceToHost))) return ELBM_E_CUDA;
+            if (v[0] != 0.0) return ELBM_E_NUMERIC;
+        }
+        if (!cuda_ok(cudaMemcpy(&v[1], h->b.scal + S_NOCONV, sizeof(double), cudaMemcpyDeviceToHost))) return ELBM_E_CUDA;
+        if (v[1] > h->noconv_seen) { h->noconv_seen = v[1]; return ELBM_W_POISSON_NOCONV; }
     }
-    return h->noconv ? ELBM_W_POISSON_NOCONV : ELBM_OK;
+    return ELBM_OK;
 }
 
 size_t elbm_fields_size(const elbm_handle *h, unsigned mask)
@@ -616,9 +785,7 @@ elbm_status elbm_fields(elbm_handle *h, unsigned mask, double *out, size_t out_l
             !cuda_ok(cudaStreamSynchronize(h->s))) {
             st = ELBM_E_CUDA;
         } else {
-            out[off + 11] = h->last_sweeps;
-            out[off + 12] = sc[S_RESID];
-            out[off + 18] = h->sweeps_total;
+            (void)sc;
         }
         off += ELBM_NDIAG;
     }

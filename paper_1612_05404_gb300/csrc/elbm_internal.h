@@ -11,7 +11,14 @@ namespace elbm {
 // slots of the device scalar array
 enum {
     S_QSUM = 0, S_Q2, S_QMEAN, S_SA, S_SB, S_R2, S_RQ2, S_RB2, S_RESID, S_CONV,
-    S_PHISUM, S_PHIMEAN, S_NSCAL = 16
+    S_PHISUM, S_PHIMEAN,
+    S_ITER,        // Poisson units (V-cycles, or groups of SOR sweeps) of this step
+    S_PREV,        // residual norm at the previous convergence test
+    S_NOCONV,      // solves that hit the cap without converging (cumulative)
+    S_ITER_TOTAL,  // Poisson units over all steps
+    S_STEPS,       // completed steps
+    S_KEEP,        // 1 while the Poisson loop must go on
+    S_NSCAL = 24
 };
 // per-block partial slots of the collision diagnostics
 enum {
@@ -69,7 +76,10 @@ struct Ops {
 };
 
 struct MGLevel;  // elbm_kernels.cuh
+struct MGTail;   // elbm_kernels.cuh
 struct MGOps {
+    void (*tail)(const Geom &, const MGTail &, int nu, cudaStream_t);
+    void (*prepare)();  // kernel attributes (shared-memory opt-in), before any capture
     void (*smooth)(const Geom &, const Phys &, const Bufs &, const MGLevel &, int level, int color,
                    const Launch &fine_half, cudaStream_t);
     void (*restrict_)(const Geom &, const Phys &, const Bufs &, const MGLevel &F, const MGLevel &C, int level,

@@ -959,22 +959,32 @@ __device__ __forceinline__ typename Tr<PR>::sc mg_resid_at(const Geom &g, const 
     return r;
 }
 
-// b_{l+1} = sum of the 8 child residuals of level l; e_{l+1} = 0
+// b_{l+1} = sum of the 8 child residuals of level l; e_{l+1} = 0. Eight
+// consecutive lanes handle the 8 children of one coarse cell and sum them
+// with a fixed shuffle tree.
 template <int PR>
 __global__ void __launch_bounds__(128) k_mg_restrict(Geom g, Phys ph, Bufs bf, MGLevel F, MGLevel C, int level)
 {
     typedef typename Tr<PR>::sc T;
-    const int X = blockIdx.x * blockDim.x + threadIdx.x;
-    const int Y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int Z = blockIdx.z;
-    if (X >= C.nx || Y >= C.ny) return;
-    T sum = 0;
-#pragma unroll
-    for (int c = 0; c < 8; c++)
-        sum += mg_resid_at<PR>(g, ph, bf, F, level, 2 * X + (c & 1), 2 * Y + ((c >> 1) & 1), 2 * Z + (c >> 2));
-    const ll S = X + (ll)C.nx * (Y + (ll)C.ny * Z);
-    ((T *)C.b)[S] = sum;
-    ((T *)C.e)[S] = T(0);
+    const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long S = gid >> 3;
+    const int c = (int)(gid & 7);
+    const bool act = S < C.N;
+    T r = 0;
+    int X = 0, Y = 0, Z = 0;
+    if (act) {
+        X = (int)(S % C.nx);
+        Y = (int)((S / C.nx) % C.ny);
+        Z = (int)(S / ((long long)C.nx * C.ny));
+        r = mg_resid_at<PR>(g, ph, bf, F, level, 2 * X + (c & 1), 2 * Y + ((c >> 1) & 1), 2 * Z + (c >> 2));
+    }
+    r += __shfl_down_sync(0xffffffffu, r, 4, 8);
+    r += __shfl_down_sync(0xffffffffu, r, 2, 8);
+    r += __shfl_down_sync(0xffffffffu, r, 1, 8);
+    if (act && c == 0) {
+        ((T *)C.b)[S] = r;
+        ((T *)C.e)[S] = T(0);
+    }
 }
 
 // coarse permittivity: mean of the 8 children (level 0 children from rho)
@@ -1086,6 +1096,167 @@ __global__ void __launch_bounds__(1024) k_mg_coarse(Geom g, MGLevel L, int level
     for (ll s = threadIdx.x; s < L.N; s += blockDim.x) ((T *)L.e)[s] = e[s];
 }
 
+
+// ---------------------------------------------------------------------------
+// The bottom of the V-cycle in one CTA: every level from `lt` down (at most
+// kTailCells cells on level lt) lives in shared memory; smoothing,
+// restriction, the coarsest sweeps and prolongation run with block barriers
+// instead of kernel launches. Same operators as the launched levels.
+// ---------------------------------------------------------------------------
+constexpr int kTailCells = 4096;
+constexpr int kTailMaxLevels = 8;
+
+struct MGTail {
+    int nt;                       // levels in the tail
+    int lt;                       // global index of the first tail level
+    int nx[kTailMaxLevels], ny[kTailMaxLevels], nz[kTailMaxLevels];
+    long long N[kTailMaxLevels], off[kTailMaxLevels];  // cells, offset in each smem array
+    long long total;              // cells over all tail levels
+    int coarse_sweeps;
+    MGLevel top;                  // global arrays of level lt
+};
+
+template <typename T>
+__device__ __forceinline__ T tail_resid(const Geom &g, const T *e, const T *b, const T *ep, int nx, int ny, int nz,
+                                        int level, int x, int y, int z)
+{
+    const long long s = x + (long long)nx * (y + (long long)ny * z);
+    const T kap = T(1 << level), kb = T(2.0 * double(1 << (2 * level)) / double((1 << level) + 1));
+    const T es = ep[s], xs = e[s];
+    T r = b[s];
+    const int cc[3] = {x, y, z}, n_[3] = {nx, ny, nz};
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int sg = -1; sg <= 1; sg += 2) {
+            int c[3] = {cc[0], cc[1], cc[2]};
+            int v = nbc(c[a] + sg, n_[a], g.per[a]);
+            if (v < 0) {
+                if (g.phi_kind[2 * a + (sg > 0)] == ELBM_PHI_DIRICHLET) r -= kb * es * xs;
+                continue;
+            }
+            c[a] = v;
+            long long nb = c[0] + (long long)nx * (c[1] + (long long)ny * c[2]);
+            r += kap * T(0.5) * (es + ep[nb]) * (e[nb] - xs);
+        }
+    return r;
+}
+
+template <typename T>
+__device__ void tail_smooth(const Geom &g, const MGTail &t, T *E, T *B, T *P, int k, int sweeps)
+{
+    const int nx = t.nx[k], ny = t.ny[k], nz = t.nz[k];
+    const long long N = t.N[k];
+    T *e = E + t.off[k];
+    const T *b = B + t.off[k], *ep = P + t.off[k];
+    const int level = t.lt + k;
+    const T kap = T(1 << level), kb = T(2.0 * double(1 << (2 * level)) / double((1 << level) + 1));
+    const int n_[3] = {nx, ny, nz};
+    for (int it = 0; it < 2 * sweeps; it++) {
+        const int color = it & 1;
+        for (long long s = threadIdx.x; s < N; s += blockDim.x) {
+            int x = (int)(s % nx), y = (int)((s / nx) % ny), z = (int)(s / ((long long)nx * ny));
+            if (((x + y + z) & 1) != color) continue;
+            const int cc[3] = {x, y, z};
+            T es = ep[s], num = b[s], den = 0;
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+#pragma unroll
+                for (int sg = -1; sg <= 1; sg += 2) {
+                    int c[3] = {cc[0], cc[1], cc[2]};
+                    int v = nbc(c[a] + sg, n_[a], g.per[a]);
+                    if (v < 0) {
+                        if (g.phi_kind[2 * a + (sg > 0)] == ELBM_PHI_DIRICHLET) den += kb * es;
+                        continue;
+                    }
+                    c[a] = v;
+                    long long nb = c[0] + (long long)nx * (c[1] + (long long)ny * c[2]);
+                    T cf = kap * T(0.5) * (es + ep[nb]);
+                    num += cf * e[nb];
+                    den += cf;
+                }
+            if (den > T(0)) e[s] = num / den;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_mg_tail(Geom g, MGTail t, int nu)
+{
+    extern __shared__ unsigned char smem_raw[];
+    T *E = (T *)smem_raw;
+    T *B = E + t.total;
+    T *P = B + t.total;
+    for (long long s = threadIdx.x; s < t.N[0]; s += blockDim.x) {
+        E[s] = T(0);
+        B[s] = ((const T *)t.top.b)[s];
+        P[s] = ((const T *)t.top.eps)[s];
+    }
+    __syncthreads();
+    for (int k = 1; k < t.nt; k++) {  // coarse permittivities: mean of 8 children
+        const int nx = t.nx[k], ny = t.ny[k], fx = t.nx[k - 1], fy = t.ny[k - 1];
+        for (long long S = threadIdx.x; S < t.N[k]; S += blockDim.x) {
+            int X = (int)(S % nx), Y = (int)((S / nx) % ny), Z = (int)(S / ((long long)nx * ny));
+            T sum = 0;
+            for (int c = 0; c < 8; c++)
+                sum += P[t.off[k - 1] + (2 * X + (c & 1)) + (long long)fx * ((2 * Y + ((c >> 1) & 1)) + (long long)fy * (2 * Z + (c >> 2)))];
+            P[t.off[k] + S] = sum * T(0.125);
+        }
+        __syncthreads();
+    }
+    // down: smooth, restrict
+    for (int k = 0; k + 1 < t.nt; k++) {
+        tail_smooth<T>(g, t, E, B, P, k, nu);
+        const int nx = t.nx[k + 1], ny = t.ny[k + 1], fx = t.nx[k], fy = t.ny[k], fz = t.nz[k];
+        for (long long S = threadIdx.x; S < t.N[k + 1]; S += blockDim.x) {
+            int X = (int)(S % nx), Y = (int)((S / nx) % ny), Z = (int)(S / ((long long)nx * ny));
+            T sum = 0;
+            for (int c = 0; c < 8; c++)
+                sum += tail_resid<T>(g, E + t.off[k], B + t.off[k], P + t.off[k], fx, fy, fz, t.lt + k,
+                                     2 * X + (c & 1), 2 * Y + ((c >> 1) & 1), 2 * Z + (c >> 2));
+            B[t.off[k + 1] + S] = sum;
+            E[t.off[k + 1] + S] = T(0);
+        }
+        __syncthreads();
+    }
+    tail_smooth<T>(g, t, E, B, P, t.nt - 1, t.coarse_sweeps);
+    // up: prolong (trilinear), smooth
+    for (int k = t.nt - 2; k >= 0; k--) {
+        const int nx = t.nx[k], ny = t.ny[k];
+        const int nc[3] = {t.nx[k + 1], t.ny[k + 1], t.nz[k + 1]};
+        const T *ec = E + t.off[k + 1];
+        for (long long s = threadIdx.x; s < t.N[k]; s += blockDim.x) {
+            int fc[3] = {(int)(s % nx), (int)((s / nx) % ny), (int)(s / ((long long)nx * ny))};
+            int i0[3], i1[3];
+            bool z1[3];
+            for (int a = 0; a < 3; a++) {
+                i0[a] = fc[a] >> 1;
+                int o = (fc[a] & 1) ? 1 : -1;
+                int v = nbc(i0[a] + o, nc[a], g.per[a]);
+                z1[a] = false;
+                if (v < 0) {
+                    if (g.phi_kind[2 * a + (o > 0)] == ELBM_PHI_DIRICHLET) z1[a] = true;
+                    v = i0[a];
+                }
+                i1[a] = v;
+            }
+            T acc = 0;
+            for (int c = 0; c < 8; c++) {
+                int ax = c & 1, ay = (c >> 1) & 1, az = c >> 2;
+                if ((ax && z1[0]) || (ay && z1[1]) || (az && z1[2])) continue;
+                T w = (ax ? T(0.25) : T(0.75)) * (ay ? T(0.25) : T(0.75)) * (az ? T(0.25) : T(0.75));
+                int X = ax ? i1[0] : i0[0], Y = ay ? i1[1] : i0[1], Z = az ? i1[2] : i0[2];
+                acc += w * ec[X + (long long)nc[0] * (Y + (long long)nc[1] * Z)];
+            }
+            E[t.off[k] + s] += acc;
+        }
+        __syncthreads();
+        tail_smooth<T>(g, t, E, B, P, k, nu);
+    }
+    for (long long s = threadIdx.x; s < t.N[0]; s += blockDim.x) ((T *)t.top.e)[s] = E[s];
+}
+
 // ---------------------------------------------------------------------------
 // Multigrid launchers for one precision.
 // ---------------------------------------------------------------------------
@@ -1108,8 +1279,8 @@ struct MGLaunchers {
     static void restrict_(const Geom &g, const Phys &ph, const Bufs &b, const MGLevel &F, const MGLevel &C,
                           int level, cudaStream_t s)
     {
-        dim3 blk = blk_of(C.nx);
-        k_mg_restrict<PR><<<grid_of(C.nx, C.ny, C.nz, blk), blk, 0, s>>>(g, ph, b, F, C, level);
+        long long thr = 8 * C.N;
+        k_mg_restrict<PR><<<(unsigned)((thr + 127) / 128), 128, 0, s>>>(g, ph, b, F, C, level);
     }
     static void eps(const Geom &g, const Phys &ph, const Bufs &b, const MGLevel &F, const MGLevel &C, int level,
                     cudaStream_t s)
@@ -1128,9 +1299,21 @@ struct MGLaunchers {
         int thr = L.N >= 1024 ? 1024 : (int)(((L.N + 31) / 32) * 32);
         k_mg_coarse<sc><<<1, thr, sm, s>>>(g, L, level, sweeps);
     }
+    static void prepare()
+    {
+        cudaFuncSetAttribute(k_mg_tail<sc>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    }
+    static void tail_(const Geom &g, const MGTail &t, int nu, cudaStream_t s)
+    {
+        size_t sm = 3 * (size_t)t.total * sizeof(sc);
+        int thr = t.N[0] >= 1024 ? 1024 : (int)(((t.N[0] + 31) / 32) * 32);
+        k_mg_tail<sc><<<1, thr, sm, s>>>(g, t, nu);
+    }
     static MGOps table()
     {
         MGOps o;
+        o.tail = tail_;
+        o.prepare = prepare;
         o.smooth = smooth;
         o.restrict_ = restrict_;
         o.eps = eps;

@@ -50,7 +50,7 @@ class Params(ctypes.Structure):
         ("poisson_fixed_sweeps", ctypes.c_int), ("poisson_check_every", ctypes.c_int),
         ("alpha_mode", ctypes.c_int), ("precision", ctypes.c_int),
         ("alpha_precision", ctypes.c_int), ("store_macro", ctypes.c_int),
-        ("diag_every", ctypes.c_int), ("profile", ctypes.c_int),
+        ("diag_every", ctypes.c_int), ("profile", ctypes.c_int), ("graph", ctypes.c_int),
         ("phi_lo", ctypes.c_double), ("phi_hi", ctypes.c_double), ("phi_solid", ctypes.c_double),
         ("nu0", ctypes.c_double), ("nu_inf", ctypes.c_double), ("lam", ctypes.c_double),
         ("n_carreau", ctypes.c_double),
@@ -138,6 +138,7 @@ def make_params(cfg: dict, stream=None) -> Params:
     P.store_macro = int(cfg.get("store_macro", 1))
     P.diag_every = int(cfg.get("diag_every", 1))
     P.profile = int(cfg.get("profile", 0))
+    P.graph = int(cfg.get("graph", 1))
     P.phi_lo, P.phi_hi, P.phi_solid = cfg["phi_lo"], cfg["phi_hi"], cfg["phi_solid"]
     P.nu0, P.nu_inf, P.lam, P.n_carreau = cfg["nu0"], cfg["nu_inf"], cfg["lambda"], cfg["n_carreau"]
     P.G, P.Gw, P.rho0 = cfg["G"], cfg["Gw"], cfg["rho0"]
