@@ -70,32 +70,48 @@ struct Ctl {
 // Sum (or min / max) each of the K columns of the per-block partials in a
 // fixed order, then derive the scalars of `mode`. One block of 256 threads:
 // run-to-run reproducible.
-__global__ void k_finalize(const double *part, int nblocks, int K, int mode, Phys ph, Ctl ctl,
-                           double *scal, float *scalf, double *diag)
+__global__ void __launch_bounds__(256) k_finalize(const double *part, int nblocks, int K, int mode, Phys ph,
+                                                  Ctl ctl, double *scal, float *scalf, double *diag,
+                                                  double *colres, unsigned int *ticket)
 {
-    __shared__ double res[16];
+    // block k reduces column k of the column-major partials in a fixed order
+    __shared__ double wsum[8];
+    __shared__ bool last;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    // one warp per column: lanes stride over the blocks, then a fixed
-    // shuffle tree (reproducible order)
-    for (int k = warp; k < K; k += 8) {
-        int op = 0;  // 0 sum, 1 min, 2 max
-        if (mode == FIN_DIAG) {
-            if (k == D_AMIN) op = 1;
-            else if (k == D_AMAX || k == D_HERR || k == D_UMAX) op = 2;
-        }
-        double acc = op == 1 ? 1e300 : (op == 2 ? -1e300 : 0.0);
-        for (int i = lane; i < nblocks; i += 32) {
-            double v = part[(long long)i * K + k];
-            acc = op == 0 ? acc + v : (op == 1 ? fmin(acc, v) : fmax(acc, v));
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            double c = __shfl_down_sync(0xffffffffu, acc, o);
-            acc = op == 0 ? acc + c : (op == 1 ? fmin(acc, c) : fmax(acc, c));
-        }
-        if (lane == 0) res[k] = acc;
+    const int k = blockIdx.x;
+    int op = 0;  // 0 sum, 1 min, 2 max
+    if (mode == FIN_DIAG) {
+        if (k == D_AMIN) op = 1;
+        else if (k == D_AMAX || k == D_HERR || k == D_UMAX) op = 2;
+    }
+    const double id = op == 1 ? 1e300 : (op == 2 ? -1e300 : 0.0);
+    const double *col = part + (long long)k * nblocks;
+    double acc = id;
+    for (int i = t; i < nblocks; i += 256) {
+        double v = col[i];
+        acc = op == 0 ? acc + v : (op == 1 ? fmin(acc, v) : fmax(acc, v));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        double c = __shfl_down_sync(0xffffffffu, acc, o);
+        acc = op == 0 ? acc + c : (op == 1 ? fmin(acc, c) : fmax(acc, c));
+    }
+    if (lane == 0) wsum[warp] = acc;
+    __syncthreads();
+    if (t == 0) {
+        double r = wsum[0];
+        for (int w = 1; w < 8; w++) r = op == 0 ? r + wsum[w] : (op == 1 ? fmin(r, wsum[w]) : fmax(r, wsum[w]));
+        colres[k] = r;
+        __threadfence();
+        unsigned int tk = atomicAdd(ticket, 1u);
+        last = (tk == gridDim.x - 1);
     }
     __syncthreads();
-    if (t != 0) return;
+    if (!last || t != 0) return;
+    // the last block to finish derives the scalars of `mode`
+    __threadfence();
+    *ticket = 0u;
+    double res[16];
+    for (int c = 0; c < K; c++) res[c] = ((volatile double *)colres)[c];
     if (mode == FIN_CHARGE_AB) {
         // the factors of Eq. (surface-q2): Q_b / sum(rho theta), Q_s / sum(|grad rho|^2 (1 + ...))
         scal[S_SA] = res[0] > 0.0 ? ph.cd.Qb / res[0] : 0.0;
@@ -197,7 +213,7 @@ void free_bufs(elbm_handle *h)
 {
     void *ptrs[] = {h->b.fA, h->b.fB, h->b.gA, h->b.gB, h->b.rho, h->b.q, h->b.phi, h->b.ux,
                     h->b.uy, h->b.uz, h->b.alpha, h->b.nu, h->b.mask, h->b.nh, h->b.ab,
-                    h->b.part, h->b.scal, h->b.scalf, h->b.diag};
+                    h->b.part, h->b.scal, h->b.scalf, h->b.diag, h->b.colres, h->b.ticket};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (h->pin) cudaFreeHost(h->pin);
@@ -232,8 +248,8 @@ Ctl make_ctl(const elbm_handle *h, unsigned long long cond, int use_cond)
 int fin(elbm_handle *h, const Bufs &b, cudaStream_t s, int K, int mode, unsigned long long cond = 0,
         int use_cond = 0)
 {
-    k_finalize<<<1, 256, 0, s>>>(b.part, h->L.nblocks, K, mode, h->ph, make_ctl(h, cond, use_cond),
-                                 b.scal, b.scalf, b.diag);
+    k_finalize<<<K, 256, 0, s>>>(b.part, h->L.nblocks, K, mode, h->ph, make_ctl(h, cond, use_cond),
+                                 b.scal, b.scalf, b.diag, b.colres, b.ticket);
     return 1;
 }
 
@@ -604,6 +620,8 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     alloc((void **)&b.part, (size_t)L.nblocks * D_NPART * sizeof(double));
     alloc((void **)&b.scal, S_NSCAL * sizeof(double));
     alloc((void **)&b.scalf, S_NSCAL * sizeof(float));
+    alloc((void **)&b.colres, 16 * sizeof(double));
+    alloc((void **)&b.ticket, sizeof(unsigned int));
     alloc((void **)&b.diag, ELBM_NDIAG * sizeof(double));
     if (ok && !cuda_ok(cudaMallocHost((void **)&h->pin, 16 * sizeof(double)))) ok = false;
     if (ok && p->profile)

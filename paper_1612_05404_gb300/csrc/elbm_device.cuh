@@ -165,8 +165,10 @@ __device__ __forceinline__ T carreau_nu(const Cst<T> &k, bool newtonian, T Pn, T
     if (A == T(0)) return k.nu0;
     T lo = A * cs2 / (T(2) * k.nu0 + cs2), hi = A * cs2 / (T(2) * k.nu_inf + cs2);
     T x = lo;
-    const T eps = sizeof(T) == 8 ? T(4e-16) : T(2e-7);
-    const int itmax = sizeof(T) == 8 ? 100 : 30;
+    // FP32: stop at a relative step of 2e-6 or when g is at the noise floor
+    // of its two terms; FP64: to the last bits
+    const T eps = sizeof(T) == 8 ? T(4e-16) : T(2e-6);
+    const int itmax = sizeof(T) == 8 ? 100 : 16;
     for (int it = 0; it < itmax; it++) {
         T lg = k.lam * x;
         T base = T(1) + lg * lg;
@@ -181,7 +183,8 @@ __device__ __forceinline__ T carreau_nu(const Cst<T> &k, bool newtonian, T Pn, T
             T gp = T(1) - A * (T(-2) * cs2 / (den * den)) * dnu;
             T xn = x - gx / gp;
             if (!(xn > lo && xn < hi)) xn = T(0.5) * (lo + hi);
-            done = fabs(xn - x) <= eps * fabs(x) || hi - lo <= eps * hi;
+            done = fabs(xn - x) <= eps * fabs(x) || hi - lo <= eps * hi ||
+                   (sizeof(T) == 4 && fabs(gx) <= T(5e-7) * (x + A * cs2 / den));
             x = xn;
         }
         if (sizeof(T) == 8) {
@@ -204,6 +207,7 @@ __device__ __forceinline__ T carreau_nu(const Cst<T> &k, bool newtonian, T Pn, T
 // 3 clipped at the positivity bound. The fallback in 1 and 2 is a = 2 (BGK).
 // ---------------------------------------------------------------------------
 struct AlphaOut { double alpha, herr; int status; };
+struct AlphaOutF { float alpha, herr; int status; };
 
 // FP64: same root as the plain definition, Newton in the sign bracket from 2.
 __device__ __forceinline__ AlphaOut alpha_fp64(const double *f, const double *d, double rho,
@@ -287,12 +291,13 @@ __device__ __forceinline__ void lphi_f32(float y, float *l, float *ph)
 // Knuth); no term carries cancellation. Start from the root of the moment
 // expansion h(a)/a ~ h'(0) + a M2/2 - a^2 M3/6 + a^3 M4/12 (M_k = sum f x^k),
 // then safeguarded Newton steps on the exact h (at most 12; two or three near
-// equilibrium); the warp leaves the loop together once every lane has
+// equilibrium) until the step is below 1e-6 alpha or h is at the FP32 noise
+// floor of its terms; the warp leaves the loop together once every lane has
 // converged, so only warps holding strongly non-equilibrium sites iterate on.
-__device__ __forceinline__ AlphaOut alpha_fp32(const float *f, const float *d, const float *fdev,
-                                               float rho, float drho, float eq_tol)
+__device__ __forceinline__ AlphaOutF alpha_fp32(const float *f, const float *d, const float *fdev,
+                                                float rho, float drho, float eq_tol)
 {
-    AlphaOut o; o.alpha = 2.0; o.herr = 0.0; o.status = 0;
+    AlphaOutF o; o.alpha = 2.f; o.herr = 0.f; o.status = 0;
     float x[Q];
     float maxabs = 0.f, xneg = 0.f;
     float s = 0.f, c = 0.f, tl = 0.f, M2 = 0.f, M3 = 0.f, M4 = 0.f;
@@ -333,6 +338,13 @@ __device__ __forceinline__ AlphaOut alpha_fp32(const float *f, const float *d, c
     if (!(a > lo && a < hi)) a = fminf(2.f, 0.5f * hi);
     float h = 0.f;
     bool clipped = false;
+    // Converged lanes freeze their alpha while the rest of the warp iterates:
+    // a lane that kept iterating at an exact FP32 zero of h would bisect away
+    // from its root. Converged: h exactly 0, or |h| at the FP32 noise floor of
+    // its terms (hh = sum f phi >= 0) after a step below 1e-3 alpha, or a
+    // Newton step below 1e-6 alpha.
+    float step_prev = 1e30f;
+    bool conv = false;
     for (int it = 0; it < 12; it++) {
         float hh = 0.f, g = 0.f;
 #pragma unroll
@@ -344,14 +356,21 @@ __device__ __forceinline__ AlphaOut alpha_fp32(const float *f, const float *d, c
             hh += f[p] * ph;
             g += d[p] * l;
         }
-        h = hh + a * a0;
-        float hp = g + a0;
-        if (h < 0.f) lo = a; else hi = a;
-        float an = a - h / hp;
-        if (!(an > lo && an < hi)) an = 0.5f * (lo + hi);
-        bool done = fabsf(an - a) <= 4e-7f * a || h == 0.f;
-        a = an;
-        if (__all_sync(__activemask(), done)) break;
+        if (!conv) {
+            h = hh + a * a0;
+            if (h == 0.f || (step_prev <= 1e-3f * a && fabsf(h) <= 5e-7f * (hh + fabsf(a * a0)))) {
+                conv = true;
+            } else {
+                const float hp = g + a0;
+                if (h < 0.f) lo = a; else hi = a;
+                float an = a - h / hp;
+                if (!(an > lo && an < hi)) an = 0.5f * (lo + hi);
+                step_prev = fabsf(an - a);
+                a = an;
+                conv = step_prev <= 1e-6f * a;
+            }
+        }
+        if (__all_sync(__activemask(), conv)) break;
     }
     if (a >= amax * (1.f - 2e-6f)) clipped = true;
     o.alpha = a;

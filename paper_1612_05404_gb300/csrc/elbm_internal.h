@@ -48,6 +48,8 @@ struct Bufs {
     double *part;                     // per-block partial sums
     double *scal;                     // device scalars (S_*)
     float *scalf;                     // the same scalars rounded to FP32
+    double *colres;                   // per-column results of the finalize kernel
+    unsigned int *ticket;             // last-block-done counter of the finalize kernel
     double *diag;                     // ELBM_NDIAG diagnostics
 };
 

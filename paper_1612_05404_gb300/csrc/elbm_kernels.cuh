@@ -53,8 +53,12 @@ __device__ __forceinline__ double warp_sum(float v)
     return (double)hi + (double)lo;
 }
 
+__device__ __forceinline__ int num_blocks() { return gridDim.x * gridDim.y * gridDim.z; }
+
+// Per-block partial sums are stored column-major, part[k * nblocks + block],
+// so the finalize kernel reads each column with coalesced loads.
 template <int K, typename T>
-__device__ __forceinline__ void block_sums(const T (&v)[K], double *out)
+__device__ __forceinline__ void block_sums(const T (&v)[K], double *out, int stride = 1)
 {
     __shared__ double sh[K][8];
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
@@ -71,7 +75,7 @@ __device__ __forceinline__ void block_sums(const T (&v)[K], double *out)
         for (int k = 0; k < K; k++) {
             double t = 0.0;
             for (int i = 0; i < nw; i++) t += sh[k][i];
-            out[k] = t;
+            out[(long long)k * stride] = t;
         }
     }
 }
@@ -272,7 +276,7 @@ __global__ void __launch_bounds__(128) k_moments(Geom g, Phys ph, Bufs b)
     }
     if (ph.charge_model == ELBM_CHARGE_TRANSPORT) {
         gt v[2] = {qv, q2};
-        block_sums<2>(v, b.part + 2 * block_id());
+        block_sums<2>(v, b.part + block_id(), num_blocks());
     }
 }
 
@@ -348,7 +352,7 @@ __global__ void __launch_bounds__(128) k_charge_ab(Geom g, Phys ph, Bufs b)
         ab[g.N + s] = bv;
     }
     sc v[2] = {av, bv};
-    block_sums<2>(v, b.part + 2 * block_id());
+    block_sums<2>(v, b.part + block_id(), num_blocks());
 }
 
 template <int PR>
@@ -375,7 +379,7 @@ __global__ void __launch_bounds__(128) k_charge_q(Geom g, Phys ph, Bufs b)
         ((sc *)b.q)[s] = sc(0);
     }
     sc v[2] = {qv, qv * qv};
-    block_sums<2>(v, b.part + 2 * block_id());
+    block_sums<2>(v, b.part + block_id(), num_blocks());
 }
 
 // ===========================================================================
@@ -463,7 +467,7 @@ __global__ void __launch_bounds__(128) k_resid(Geom g, Phys ph, Bufs b)
         b2 = bs * bs;
     }
     sc v[3] = {r2, q2, b2};
-    block_sums<3>(v, b.part + 3 * block_id());
+    block_sums<3>(v, b.part + block_id(), num_blocks());
 }
 
 template <int PR>
@@ -476,7 +480,7 @@ __global__ void __launch_bounds__(128) k_phi_sum(Geom g, Phys ph, Bufs b)
     site_xyz(g, x, y, z, inb, s);
     bool active = inb && (!b.mask || b.mask[s] != ELBM_NODE_SOLID);
     sc v[1] = {active ? ((const sc *)b.phi)[s] : sc(0)};
-    block_sums<1>(v, b.part + block_id());
+    block_sums<1>(v, b.part + block_id(), num_blocks());
 }
 
 template <int PR>
@@ -585,8 +589,9 @@ __global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int di
         }
 
         // Eq. (entropic)
-        AlphaOut ao;
-        ao.alpha = 2.0; ao.herr = 0.0; ao.status = 0;
+        ct alpha = ct(2);
+        float a_herr = 0.f;
+        int a_status = 0;
         if (ph.alpha_mode == ELBM_ALPHA_ENTROPIC) {
             if (sizeof(ct) == 8 || AP == ELBM_APREC_FP64) {
                 double fd[Q], dd[Q];
@@ -595,7 +600,10 @@ __global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int di
                     fd[p] = T::dev ? wq(p) + double(f[p]) : double(f[p]);
                     dd[p] = double(D[p]);
                 }
-                ao = alpha_fp64(fd, dd, double(r), ph.cd.eq_tol);
+                AlphaOut ao = alpha_fp64(fd, dd, double(r), ph.cd.eq_tol);
+                alpha = ct(ao.alpha);
+                a_herr = float(ao.herr);
+                a_status = ao.status;
             } else {
                 float ff[Q], dd[Q], fv[Q];
 #pragma unroll
@@ -604,10 +612,12 @@ __global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int di
                     dd[p] = float(D[p]);
                     fv[p] = float(f[p]);
                 }
-                ao = alpha_fp32(ff, dd, fv, float(r), float(drho), ph.cf.eq_tol);
+                AlphaOutF ao = alpha_fp32(ff, dd, fv, float(r), float(drho), ph.cf.eq_tol);
+                alpha = ct(ao.alpha);
+                a_herr = ao.herr;
+                a_status = ao.status;
             }
         }
-        const ct alpha = ct(ao.alpha);
 
         // Eq. (stress): Pi = sum (f - f^eq) c c = -sum D c c; 2-norm; Carreau; Eq. (beta)
         ct nu = k.nu0;
@@ -688,10 +698,10 @@ __global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int di
             dasum = alpha;
             dnfl = 1;
             damin = damax = float(alpha);
-            if (ao.status == 1) dsh = 1;
-            else if (ao.status == 2) dnr = 1;
-            else if (ao.status == 3) dcl = 1;
-            dherr = float(ao.herr);
+            if (a_status == 1) dsh = 1;
+            else if (a_status == 2) dnr = 1;
+            else if (a_status == 3) dcl = 1;
+            dherr = a_herr;
             float um = float(sqrt(upx * upx + upy * upy + upz * upz));
             dumax = um;
             if (!(r > ct(0)) || !isfinite(float(r)) || !isfinite(um) || !isfinite(float(alpha))) dbad = 1;
@@ -713,17 +723,18 @@ __global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int di
         if (lane == 0) { mm[0][wid] = damin; mm[1][wid] = damax; mm[2][wid] = dherr; mm[3][wid] = dumax; }
         block_sums<11>(v, res);
         if (tid == 0) {
-            double *out = b.part + (ll)D_NPART * block_id();
-            out[D_MASS] = res[0]; out[D_MX] = res[1]; out[D_MY] = res[2]; out[D_MZ] = res[3];
-            out[D_Q] = res[4]; out[D_ASUM] = res[5]; out[D_NSHORT] = res[6]; out[D_NNOROOT] = res[7];
-            out[D_NCLIP] = res[8]; out[D_NBAD] = res[9]; out[D_NFLUID] = res[10];
+            const ll nbk = num_blocks();
+            double *out = b.part + block_id();
+            out[D_MASS * nbk] = res[0]; out[D_MX * nbk] = res[1]; out[D_MY * nbk] = res[2]; out[D_MZ * nbk] = res[3];
+            out[D_Q * nbk] = res[4]; out[D_ASUM * nbk] = res[5]; out[D_NSHORT * nbk] = res[6]; out[D_NNOROOT * nbk] = res[7];
+            out[D_NCLIP * nbk] = res[8]; out[D_NBAD * nbk] = res[9]; out[D_NFLUID * nbk] = res[10];
             const int nw = (blockDim.x * blockDim.y + 31) >> 5;
             float a0 = 1e30f, a1 = -1e30f, h = 0.f, u = 0.f;
             for (int i = 0; i < nw; i++) {
                 a0 = fminf(a0, mm[0][i]); a1 = fmaxf(a1, mm[1][i]);
                 h = fmaxf(h, mm[2][i]); u = fmaxf(u, mm[3][i]);
             }
-            out[D_AMIN] = a0; out[D_AMAX] = a1; out[D_HERR] = h; out[D_UMAX] = u;
+            out[D_AMIN * nbk] = a0; out[D_AMAX * nbk] = a1; out[D_HERR * nbk] = h; out[D_UMAX * nbk] = u;
         }
     }
 }
@@ -883,7 +894,7 @@ __global__ void __launch_bounds__(128) k_mg_smooth(Geom g, MGLevel L, int level,
     const ll s = x + (ll)L.nx * (y + (ll)L.ny * z);
     T *e = (T *)L.e;
     const T *b = (const T *)L.b, *ep = (const T *)L.eps;
-    const T kap = T(1 << level), kb = T(2.0 * double(1 << (2 * level)) / double((1 << level) + 1));
+    const T kap = T(1 << level), kb = T(2 * (1 << (2 * level))) / T((1 << level) + 1);
     const T es = ep[s];
     T num = b[s], den = 0;
     const int cx_[3] = {x, y, z}, n_[3] = {L.nx, L.ny, L.nz};
@@ -939,7 +950,7 @@ __device__ __forceinline__ typename Tr<PR>::sc mg_resid_at(const Geom &g, const 
         return r;
     }
     const T *e = (const T *)L.e, *b = (const T *)L.b, *ep = (const T *)L.eps;
-    const T kap = T(1 << level), kb = T(2.0 * double(1 << (2 * level)) / double((1 << level) + 1));
+    const T kap = T(1 << level), kb = T(2 * (1 << (2 * level))) / T((1 << level) + 1);
     const T es = ep[s], xs = e[s];
     T r = b[s];
 #pragma unroll
@@ -966,16 +977,18 @@ template <int PR>
 __global__ void __launch_bounds__(128) k_mg_restrict(Geom g, Phys ph, Bufs bf, MGLevel F, MGLevel C, int level)
 {
     typedef typename Tr<PR>::sc T;
-    const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long S = gid >> 3;
+    const unsigned gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned S = gid >> 3;
     const int c = (int)(gid & 7);
-    const bool act = S < C.N;
+    const bool act = S < (unsigned)C.N;
     T r = 0;
     int X = 0, Y = 0, Z = 0;
     if (act) {
-        X = (int)(S % C.nx);
-        Y = (int)((S / C.nx) % C.ny);
-        Z = (int)(S / ((long long)C.nx * C.ny));
+        const unsigned nxy = (unsigned)C.nx * (unsigned)C.ny;
+        Z = (int)(S / nxy);
+        const unsigned rem = S - (unsigned)Z * nxy;
+        Y = (int)(rem / (unsigned)C.nx);
+        X = (int)(rem - (unsigned)Y * (unsigned)C.nx);
         r = mg_resid_at<PR>(g, ph, bf, F, level, 2 * X + (c & 1), 2 * Y + ((c >> 1) & 1), 2 * Z + (c >> 2));
     }
     r += __shfl_down_sync(0xffffffffu, r, 4, 8);
@@ -1066,12 +1079,12 @@ __global__ void __launch_bounds__(1024) k_mg_coarse(Geom g, MGLevel L, int level
         ep[s] = ((const T *)L.eps)[s];
     }
     __syncthreads();
-    const T kap = T(1 << level), kb = T(2.0 * double(1 << (2 * level)) / double((1 << level) + 1));
+    const T kap = T(1 << level), kb = T(2 * (1 << (2 * level))) / T((1 << level) + 1);
     const int n_[3] = {L.nx, L.ny, L.nz};
     for (int it = 0; it < 2 * sweeps; it++) {
         const int color = it & 1;
         for (ll s = threadIdx.x; s < L.N; s += blockDim.x) {
-            int x = (int)(s % L.nx), y = (int)((s / L.nx) % L.ny), z = (int)(s / ((ll)L.nx * L.ny));
+            int si = (int)s, x = si % L.nx, y = (si / L.nx) % L.ny, z = si / (L.nx * L.ny);
             if (((x + y + z) & 1) != color) continue;
             const int cx_[3] = {x, y, z};
             T es = ep[s], num = b[s], den = 0;
@@ -1120,8 +1133,8 @@ template <typename T>
 __device__ __forceinline__ T tail_resid(const Geom &g, const T *e, const T *b, const T *ep, int nx, int ny, int nz,
                                         int level, int x, int y, int z)
 {
-    const long long s = x + (long long)nx * (y + (long long)ny * z);
-    const T kap = T(1 << level), kb = T(2.0 * double(1 << (2 * level)) / double((1 << level) + 1));
+    const int s = x + nx * (y + ny * z);
+    const T kap = T(1 << level), kb = T(2 * (1 << (2 * level))) / T((1 << level) + 1);
     const T es = ep[s], xs = e[s];
     T r = b[s];
     const int cc[3] = {x, y, z}, n_[3] = {nx, ny, nz};
@@ -1136,7 +1149,7 @@ __device__ __forceinline__ T tail_resid(const Geom &g, const T *e, const T *b, c
                 continue;
             }
             c[a] = v;
-            long long nb = c[0] + (long long)nx * (c[1] + (long long)ny * c[2]);
+            int nb = c[0] + nx * (c[1] + ny * c[2]);
             r += kap * T(0.5) * (es + ep[nb]) * (e[nb] - xs);
         }
     return r;
@@ -1150,12 +1163,12 @@ __device__ void tail_smooth(const Geom &g, const MGTail &t, T *E, T *B, T *P, in
     T *e = E + t.off[k];
     const T *b = B + t.off[k], *ep = P + t.off[k];
     const int level = t.lt + k;
-    const T kap = T(1 << level), kb = T(2.0 * double(1 << (2 * level)) / double((1 << level) + 1));
+    const T kap = T(1 << level), kb = T(2 * (1 << (2 * level))) / T((1 << level) + 1);
     const int n_[3] = {nx, ny, nz};
     for (int it = 0; it < 2 * sweeps; it++) {
         const int color = it & 1;
-        for (long long s = threadIdx.x; s < N; s += blockDim.x) {
-            int x = (int)(s % nx), y = (int)((s / nx) % ny), z = (int)(s / ((long long)nx * ny));
+        for (int s = threadIdx.x; s < (int)N; s += blockDim.x) {
+            int x = s % nx, y = (s / nx) % ny, z = s / (nx * ny);
             if (((x + y + z) & 1) != color) continue;
             const int cc[3] = {x, y, z};
             T es = ep[s], num = b[s], den = 0;
@@ -1170,7 +1183,7 @@ __device__ void tail_smooth(const Geom &g, const MGTail &t, T *E, T *B, T *P, in
                         continue;
                     }
                     c[a] = v;
-                    long long nb = c[0] + (long long)nx * (c[1] + (long long)ny * c[2]);
+                    int nb = c[0] + nx * (c[1] + ny * c[2]);
                     T cf = kap * T(0.5) * (es + ep[nb]);
                     num += cf * e[nb];
                     den += cf;
@@ -1197,7 +1210,7 @@ __global__ void __launch_bounds__(1024) k_mg_tail(Geom g, MGTail t, int nu)
     for (int k = 1; k < t.nt; k++) {  // coarse permittivities: mean of 8 children
         const int nx = t.nx[k], ny = t.ny[k], fx = t.nx[k - 1], fy = t.ny[k - 1];
         for (long long S = threadIdx.x; S < t.N[k]; S += blockDim.x) {
-            int X = (int)(S % nx), Y = (int)((S / nx) % ny), Z = (int)(S / ((long long)nx * ny));
+            int Si = (int)S, X = Si % nx, Y = (Si / nx) % ny, Z = Si / (nx * ny);
             T sum = 0;
             for (int c = 0; c < 8; c++)
                 sum += P[t.off[k - 1] + (2 * X + (c & 1)) + (long long)fx * ((2 * Y + ((c >> 1) & 1)) + (long long)fy * (2 * Z + (c >> 2)))];
@@ -1210,7 +1223,7 @@ __global__ void __launch_bounds__(1024) k_mg_tail(Geom g, MGTail t, int nu)
         tail_smooth<T>(g, t, E, B, P, k, nu);
         const int nx = t.nx[k + 1], ny = t.ny[k + 1], fx = t.nx[k], fy = t.ny[k], fz = t.nz[k];
         for (long long S = threadIdx.x; S < t.N[k + 1]; S += blockDim.x) {
-            int X = (int)(S % nx), Y = (int)((S / nx) % ny), Z = (int)(S / ((long long)nx * ny));
+            int Si = (int)S, X = Si % nx, Y = (Si / nx) % ny, Z = Si / (nx * ny);
             T sum = 0;
             for (int c = 0; c < 8; c++)
                 sum += tail_resid<T>(g, E + t.off[k], B + t.off[k], P + t.off[k], fx, fy, fz, t.lt + k,
@@ -1227,7 +1240,8 @@ __global__ void __launch_bounds__(1024) k_mg_tail(Geom g, MGTail t, int nu)
         const int nc[3] = {t.nx[k + 1], t.ny[k + 1], t.nz[k + 1]};
         const T *ec = E + t.off[k + 1];
         for (long long s = threadIdx.x; s < t.N[k]; s += blockDim.x) {
-            int fc[3] = {(int)(s % nx), (int)((s / nx) % ny), (int)(s / ((long long)nx * ny))};
+            int si = (int)s;
+            int fc[3] = {si % nx, (si / nx) % ny, si / (nx * ny)};
             int i0[3], i1[3];
             bool z1[3];
             for (int a = 0; a < 3; a++) {
