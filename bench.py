@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="drop64", choices=["drop64"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
-    ap.add_argument("--alpha-precision", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--alpha-precision", default="fp32", choices=["fp64", "fp32", "fp32_fast"])
     ap.add_argument("--instances", type=int, default=4, help="lattices per step (E0 sweep values)")
     ap.add_argument("--no-graph", action="store_true", help="issue each step from the host (profilers see every launch)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -261,7 +261,9 @@ def run_ours(args, rank, world, local_rank):
                      "bytes_per_site": bytes_site, "avg_launch_ms": coll_ms},
         "pass_share": shares,
         "gpu_launches": int(d["launches"] * 1),
-        "alpha": {"max_h_error_device": max(x["max_h_error"] for x in diag),
+        "alpha": {"max_h_error_device": max(x["max_h_error"] for x in diag), "h_error_bound": 1e-10,
+                  "guarded_sites_last_step": sum(x["n_guarded"] for x in diag),
+                  "guard_failed_last_step": sum(x["n_guard_failed"] for x in diag),
                   "noroot": sum(x["n_noroot"] for x in diag), "clipped": sum(x["n_clipped"] for x in diag)},
         "clocks": clk.summary(),
     }

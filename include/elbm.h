@@ -67,9 +67,14 @@ enum { ELBM_ALPHA_ENTROPIC = 0, ELBM_ALPHA_BGK = 1 };
  *   FP32: f stored as FP32 deviations d = f - w, FP32 arithmetic;
  *   BF16: f stored as BF16 deviations, FP32 arithmetic. */
 enum { ELBM_PREC_FP64 = 0, ELBM_PREC_FP32 = 1, ELBM_PREC_BF16 = 2 };
-/* arithmetic of the alpha root: FP64, or FP32 (working-precision root of the
- * same equation, written without cancellation) */
-enum { ELBM_APREC_FP64 = 0, ELBM_APREC_FP32 = 1 };
+/* arithmetic of the alpha root:
+ *   FP64: Newton in FP64;
+ *   FP32: Newton in FP32 (the same equation written without cancellation),
+ *         then a float-float guard at the sites where FP32 rounding cannot
+ *         certify |h(alpha)| <= 1e-10 rho: h'(0) and h re-evaluated as pairs
+ *         of FP32 values and at most three more Newton steps;
+ *   FP32_FAST: the FP32 Newton root alone (|h| at the FP32 rounding level). */
+enum { ELBM_APREC_FP64 = 0, ELBM_APREC_FP32 = 1, ELBM_APREC_FP32_FAST = 2 };
 
 /* selectors for elbm_fields; selected blocks are written back to back in
  * this bit order */
@@ -88,8 +93,11 @@ enum { ELBM_APREC_FP64 = 0, ELBM_APREC_FP32 = 1 };
  * 9 no-root fallbacks, 10 clipped at the positivity bound, 11 Poisson
  * sweeps, 12 Poisson relative residual, 13 max |h(alpha)|/rho as evaluated
  * on the device, 14 max |u|, 15 non-finite count, 16 subtracted mean charge,
- * 17 step counter, 18 Poisson sweeps summed over all steps, 19 reserved */
-#define ELBM_NDIAG 20
+ * 17 step counter, 18 Poisson sweeps summed over all steps, 19 sites whose
+ * alpha took the float-float guard, 20 sites where the guard ended above
+ * 1e-10 rho, 21 learned-alpha sites that fell back to the Newton root,
+ * 22-23 reserved */
+#define ELBM_NDIAG 24
 
 typedef struct elbm_params {
     int nx, ny, nz;              /* lattice (3-D, D3Q19) */
@@ -174,6 +182,32 @@ size_t elbm_fields_size(const elbm_handle *h, unsigned mask);
  * Writes min(n, 8) values; ELBM_E_STATE when profiling is off. Not part of
  * the paper's method: instrumentation for measuring the method's kernels. */
 elbm_status elbm_pass_times(const elbm_handle *h, double *out, int n);
+
+/* The entropic alpha of Eq. (entropic) for n independent sites outside a
+ * simulation: the root the collision step computes, for checking its H-error
+ * against an FP64 evaluation and for harvesting (f, alpha) pairs. Per site,
+ * from FP32 deviations d_p = f_p - w_p (FP32 arithmetic, in the order the
+ * FP32 collision uses): rho = 1 + sum d, u = sum d c / rho,
+ * Delta_p = w_p (sum d + rho P_p(u)) - d_p with P_p the velocity polynomial
+ * of Eq. (2), f_p = w_p + d_p rounded to FP32.
+ *   d       device FP32 deviations, planes d[p*n + i], p = 0..18;
+ *   n       number of sites (0: nothing is enqueued);
+ *   aprec   ELBM_APREC_* arithmetic of the root;
+ *   eq_tol  near-equilibrium shortcut (alpha = 2) when max|Delta/f| < eq_tol;
+ *           >= 2^-18 for the FP32 modes;
+ *   mlp     must be NULL (reserved for the learned proposal);
+ *   alpha   device FP64 out [n]: the root (high + low part of a guarded root);
+ *   herr    device FP32 out [n] or NULL: |h(alpha)|/rho as the method
+ *           reports it (evaluated, or the FP32 rounding bound);
+ *   status  device int32 out [n] or NULL: 0 root, 1 shortcut, 2 no root
+ *           (alpha = 2), 3 clipped at the positivity bound, 4 guard ended
+ *           above 1e-10 rho;
+ *   delta   device FP32 out [19*n] or NULL: the Delta_p planes used;
+ *   stream  cudaStream_t (NULL: legacy default stream).
+ * Buffers are the caller's; returns after enqueueing (ELBM_E_INVAL on a
+ * bad argument, nothing enqueued). */
+elbm_status elbm_alpha_eval(const float *d, long long n, int aprec, double eq_tol, const float *mlp,
+                            double *alpha, float *herr, int *status, float *delta, void *stream);
 
 /* Allocation-free density and mass of a population array. The paper has no
  * counterpart: this serves callers that may not allocate device memory

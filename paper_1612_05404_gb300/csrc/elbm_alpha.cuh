@@ -1,0 +1,362 @@
+// elbm_alpha.cuh -- the entropic alpha of Eq. (entropic) in FP32 arithmetic,
+// with a float-float guard that certifies |h(alpha)| <= 1e-10 rho.
+//
+// h(a) = H(f + a D) - H(f), H = sum_p f_p ln(f_p / w_p) (Eq. H), has the
+// trivial root a = 0 and, when h'(0) < 0, one positive root (h is convex).
+// Written without cancellation, with x_p = D_p / f_p and y = a x_p:
+//   h(a) = sum_p f_p phi(a x_p) + a h'(0),  phi(y) = (1 + y) ln(1 + y) - y,
+//   h'(0) = sum_p D_p (1 + ln(f_p / w_p)).
+// The FP32 Newton root leaves |h| at the FP32 rounding level of its terms
+// (about 1e-9 at interface sites). Where that level is above the target, the
+// guard re-evaluates h'(0) and h in float-float arithmetic (an unevaluated sum
+// of two FP32 values, about 44 significant bits; Dekker 1971, Knuth TAOCP
+// vol. 2 4.2.2) and takes Newton steps on a float-float alpha until |h| <= 1e-10
+// rho. GB300 issues FP64 at 1/64 of its FP32 rate, so the pairs of FP32
+// operations are the cheaper way to the extra precision.
+#pragma once
+
+namespace elbm {
+
+struct AlphaOutF {
+    float alpha;    // the root (high part)
+    float alpha_lo; // low part of the float-float root (0 unless the guard ran)
+    float herr;     // |h(alpha)| / rho: evaluated, or the FP32 rounding bound
+    int status;     // 0 root, 1 near-equilibrium shortcut, 2 no root, 3 clipped, 4 guard failed
+    int guarded;    // the float-float guard ran for this site
+};
+
+// ---------------------------------------------------------------------------
+// ln(1+y) and phi(y) in FP32 without cancellation, from the atanh series in
+// s = y/(2+y): ln(1+y) = 2s (1 + t A1(t)), t = s^2, A1(t) = sum_k t^k/(2k+3),
+// and, with y = 2s/(1-s), phi(y) = s y + 2 (1+y) s t A1(t) (no division).
+// For |s| <= 1/3 (y in [-1/2, 1]) eight terms of A1 leave a truncation error
+// below 1e-8 relative; beyond, the library log1pf (strong non-equilibrium).
+// The far branch is a call, not inlined: 19 inlined copies of log1pf in the
+// Newton loop would crowd the instruction cache for a branch rarely taken.
+// ---------------------------------------------------------------------------
+static __device__ __noinline__ float2 lphi_far(float y)
+{
+    const float lg = log1pf(y);
+    return make_float2(lg, (1.f + y) * lg - y);
+}
+
+__device__ __forceinline__ float atanh_A1(float t)
+{
+    return 1.f / 3 + t * (1.f / 5 + t * (1.f / 7 + t * (1.f / 9 + t * (1.f / 11 + t * (1.f / 13 + t * (1.f / 15 + t * (1.f / 17)))))));
+}
+
+__device__ __forceinline__ void lphi_f32(float y, float *l, float *ph)
+{
+    const float s = __fdividef(y, 2.f + y);
+    if (fabsf(s) <= 0.3334f) {
+        const float t = s * s;
+        const float A1 = atanh_A1(t);
+        const float c = 2.f * s * t;
+        *l = fmaf(c, A1, 2.f * s);
+        *ph = fmaf(c * (1.f + y), A1, s * y);
+    } else {
+        const float2 r = lphi_far(y);
+        *l = r.x;
+        *ph = r.y;
+    }
+}
+
+// ln(1+z) alone (the h'(0) terms)
+__device__ __forceinline__ float l_f32(float z)
+{
+    const float s = __fdividef(z, 2.f + z);
+    if (fabsf(s) <= 0.3334f) {
+        const float t = s * s;
+        return fmaf(2.f * s * t, atanh_A1(t), 2.f * s);
+    }
+    return lphi_far(z).x;
+}
+
+// ---------------------------------------------------------------------------
+// float-float arithmetic
+// ---------------------------------------------------------------------------
+struct ffl { float h, l; };
+
+__device__ __forceinline__ ffl ff_two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ffl ff_norm(float a, float b)  // |a| >= |b| or a == 0
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ ffl ff_add(ffl a, ffl b)
+{
+    ffl s = ff_two_sum(a.h, b.h);
+    return ff_norm(s.h, s.l + (a.l + b.l));
+}
+__device__ __forceinline__ ffl ff_add_f(ffl a, float b)
+{
+    ffl s = ff_two_sum(a.h, b);
+    return ff_norm(s.h, s.l + a.l);
+}
+__device__ __forceinline__ ffl ff_neg(ffl a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ ffl ff_prod(float a, float b)
+{
+    const float p = a * b;
+    return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ ffl ff_mul(ffl a, ffl b)
+{
+    const float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+    return ff_norm(p, e);
+}
+__device__ __forceinline__ ffl ff_mul_f(ffl a, float b)
+{
+    const float p = a.h * b;
+    const float e = fmaf(a.l, b, fmaf(a.h, b, -p));
+    return ff_norm(p, e);
+}
+// a / b: FP32 quotient, its remainder in float-float, one corrective quotient
+__device__ __forceinline__ ffl ff_div(ffl a, ffl b)
+{
+    const float q1 = __fdividef(a.h, b.h);
+    const ffl r = ff_add(a, ff_neg(ff_mul_f(b, q1)));
+    return ff_norm(q1, __fdividef(r.h, b.h));
+}
+__device__ __forceinline__ ffl ff_div_f(float a, float b)
+{
+    const float q1 = __fdividef(a, b);
+    const float r = fmaf(-q1, b, a);  // exact remainder
+    return ff_norm(q1, __fdividef(r, b));
+}
+
+__device__ __forceinline__ float atanh_A2(float t)
+{
+    return 1.f / 5 + t * (1.f / 7 + t * (1.f / 9 + t * (1.f / 11 + t * (1.f / 13 + t * (1.f / 15 + t * (1.f / 17))))));
+}
+
+// ln(1+y) in float-float for 1 + y > 0: reduce 1 + y by 2^k into [3/4, 3/2)
+// (k = 0, no reduction, for the usual |y| < 1/4 .. 1/2), then ln = k ln 2 +
+// 2 atanh(t) = k ln 2 + 2t (1 + q), t = u/(2+u), u = (1+y) 2^-k - 1, |t| <= 1/5,
+// q = t^2/3 + t^4 A2(t^2): t, t^2/3 and the products in float-float, the
+// tail t^4 A2 (at most 1/3 % of q) in FP32.
+__device__ __forceinline__ ffl ff_log1p(ffl y)
+{
+    const float vh = 1.f + y.h;
+    ffl u = y;
+    int k = 0;
+    if (vh < 0.75f || vh >= 1.5f) {
+        k = ilogbf(vh * (4.f / 3.f));
+        const ffl v = ff_add_f(y, 1.f);
+        u = ff_add_f(ffl{ldexpf(v.h, -k), ldexpf(v.l, -k)}, -1.f);
+    }
+    const ffl t = ff_div(u, ff_add_f(u, 2.f));
+    const ffl t2 = ff_mul(t, t);
+    const float tt = t2.h;
+    // 1/3 = 0x1.555556p-2 - 0x1.555556p-27 (+ below 2^-50)
+    const ffl q = ff_add_f(ff_mul(t2, ffl{0x1.555556p-2f, -0x1.555556p-27f}), tt * tt * atanh_A2(tt));
+    ffl l = ff_mul(ffl{2.f * t.h, 2.f * t.l}, ff_add_f(q, 1.f));
+    if (k != 0) {
+        // ln 2 = 0x1.62e43p-1 - 0x1.05c61p-29 (+ below 2^-52)
+        const float kf = float(k);
+        l = ff_add(l, ff_add_f(ff_prod(kf, 0x1.62e43p-1f), kf * -0x1.05c61p-29f));
+    }
+    return l;
+}
+
+// h'(0) in float-float: (1 + ln r) sum D + sum D_p ln(f_p / (w_p r)); 1/w_p is
+// the integer 3, 18 or 36, so f_p / (w_p r) = (f_p / w_p) / r exactly as pairs.
+// The guard's loops are not unrolled: compact code for a path few warps take.
+__device__ __forceinline__ ffl h0_ff(const float *f, const float *d, float r)
+{
+    ffl S = {0.f, 0.f}, T = {0.f, 0.f};
+#pragma unroll 1
+    for (int p = 0; p < Q; p++) {
+        S = ff_add_f(S, d[p]);
+        const float iw = p == 0 ? 3.f : (p < 7 ? 18.f : 36.f);
+        const ffl z = ff_add_f(ff_div(ff_prod(f[p], iw), ffl{r, 0.f}), -1.f);
+        T = ff_add(T, ff_mul_f(ff_log1p(z), d[p]));
+    }
+    // ln r to FP32 accuracy suffices: sum D is at the rounding level of rho
+    return ff_add(ff_mul_f(S, 1.f + logf(r)), T);
+}
+
+// h(a) in float-float, h'(a) and h''(a) = sum f x^2 / (1 + a x) in FP32, at a
+// float-float alpha
+__device__ __forceinline__ void h_ff(const float *f, const float *d, ffl a, ffl a0, ffl *h, float *hp,
+                                     float *hpp)
+{
+    ffl acc = ff_mul(a, a0);
+    float g = 0.f, g2 = 0.f;
+#pragma unroll 1
+    for (int p = 0; p < Q; p++) {
+        const ffl x = ff_div_f(d[p], f[p]);
+        const ffl y = ff_mul(a, x);
+        const ffl l = ff_log1p(y);
+        // phi = (1 + y) l - y: its cancellation for small y costs relative
+        // accuracy 2^-44 |y| / phi, far below the target in absolute terms
+        const ffl ph = ff_add(ff_mul(ff_add_f(y, 1.f), l), ff_neg(y));
+        acc = ff_add(acc, ff_mul_f(ph, f[p]));
+        g = fmaf(d[p], l.h, g);
+        g2 = fmaf(f[p] * x.h, __fdividef(x.h, 1.f + y.h), g2);
+    }
+    *h = acc;
+    *hp = g + a0.h;
+    *hpp = g2;
+}
+
+// The float-float guard from an FP32 root a: h'(0) and h(a) as pairs; accept
+// when |h| <= tol/2, else one Newton step a' = a - h/h' and accept a' when the
+// quadratic-convergence bound 3/4 h'' (a' - a)^2 plus 1e-11 rho (the pairs'
+// evaluation error) is within tol/2, else evaluate again (at most 3 steps).
+// Returns (alpha high, alpha low, H-error, accepted). Not inlined: one copy of
+// the code, entered only by warps that hold a site needing it.
+static __device__ __noinline__ float4 alpha_guard(const float *f, const float *d, float rho, float a)
+{
+    const float tol = 1e-10f * rho;
+    const ffl A0 = h0_ff(f, d, rho);
+    ffl al = {a, 0.f};
+#pragma unroll 1
+    for (int it = 0; it < 3; it++) {
+        ffl hf;
+        float hp, hpp;
+        h_ff(f, d, al, A0, &hf, &hp, &hpp);
+        if (fabsf(hf.h) <= 0.5f * tol) return make_float4(al.h, al.l, fabsf(hf.h) / rho, 1.f);
+        const float delta = hf.h / hp;
+        al = ff_add_f(al, -delta);
+        const float pred = 0.75f * fabsf(hpp) * delta * delta + 1e-11f * rho;
+        if (pred <= 0.5f * tol) return make_float4(al.h, al.l, pred / rho, 1.f);
+    }
+    return make_float4(al.h, al.l, 1e30f, 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 root. h'(0) = (1 + ln rho) sum D + sum D_p ln(1 + z_p), z_p = f_p/(w_p
+// rho) - 1 (sum D by TwoSum), f_p the FP32 populations. Start from the root of the moment expansion
+// h(a)/a ~ h'(0) + a M2/2 - a^2 M3/6 + a^3 M4/12 (M_k = sum f x^k), then
+// safeguarded Newton on the exact h (at most 12 steps; one or two near
+// equilibrium). A lane has converged when h is exactly 0, or |h| is at the
+// FP32 noise floor of its terms after a step below 1e-3 alpha, or the Newton
+// step is below 1e-6 alpha; converged lanes keep their alpha while the rest of
+// the warp iterates, and the warp leaves together.
+//
+// guard: the target is |h| <= 1e-10 rho (H-error). The FP32 rounding bound of
+// the evaluated h is 2^-21 (sum f phi + a (|h'(0)| + sum |D ln(1+z)|)) +
+// 2^-23 a |h'(a)| (the last term: alpha itself rounded to FP32). Lanes whose
+// |h| + bound stays within half the target are certified as they are; the
+// others take the float-float guard (alpha_guard) from the FP32 root and
+// report its H-error: the float-float |h|, or the quadratic-convergence bound
+// after its Newton step. Without the guard the
+// H-error reported is |h| + bound.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ AlphaOutF alpha_fp32(const float *f, const float *d, const float *fdev,
+                                                float rho, float drho, float eq_tol, bool guard)
+{
+    AlphaOutF o;
+    o.alpha = 2.f; o.alpha_lo = 0.f; o.herr = 0.f; o.status = 0; o.guarded = 0;
+    float x[Q];
+    float maxabs = 0.f, xneg = 0.f;
+    float s = 0.f, c = 0.f;
+    float tl0 = 0.f, tl1 = 0.f, tla = 0.f;
+    float M2 = 0.f, M3 = 0.f, M4 = 0.f;
+    const float lr = __logf(rho);
+    const float irho = 1.f / rho;
+#pragma unroll
+    for (int p = 0; p < Q; p++) {
+        x[p] = __fdividef(d[p], f[p]);
+        maxabs = fmaxf(maxabs, fabsf(x[p]));
+        xneg = fminf(xneg, x[p]);
+        float t = s + d[p];
+        float bp = t - s;
+        c += (s - (t - bp)) + (d[p] - bp);
+        s = t;
+        // z_p = f_p / (w_p rho) - 1 for the FP32 population f_p = fl(w_p + fdev_p):
+        // f_p = w32_p + fdev_p - e_p (e_p the exact rounding error of that sum,
+        // TwoSum), w32_p - w_p = dw a constant, so f_p - w_p rho =
+        // (fdev_p - w32_p drho) + (dw rho - e_p) is formed from small terms;
+        // the product w32_p drho is split exactly (TwoProd) because fdev_p
+        // and w32_p drho nearly cancel near equilibrium
+        const float w32 = float(wq(p));
+        const float bb = f[p] - w32;
+        const float e = (w32 - (f[p] - bb)) + (fdev[p] - bb);
+        const float dw = float(double(w32) - wq(p));
+        const float iw = float(1.0 / wq(p));
+        const float wd = w32 * drho;
+        const float wde = fmaf(w32, drho, -wd);  // exact error of the product (TwoProd)
+        const float z = ((fdev[p] - wd) + ((dw * rho - e) - wde)) * iw * irho;
+        const float dl = d[p] * l_f32(z);
+        if (p & 1) tl1 += dl; else tl0 += dl;
+        tla += fabsf(dl);
+        const float fx2 = f[p] * x[p] * x[p];
+        M2 += fx2;
+        M3 += fx2 * x[p];
+        M4 += fx2 * x[p] * x[p];
+    }
+    const float a0 = (1.f + lr) * (s + c) + (tl0 + tl1);
+    if (!(maxabs >= eq_tol)) { o.status = 1; return o; }
+    if (a0 >= 0.f) { o.status = 2; return o; }
+    const float amax = xneg < 0.f ? -1.f / xneg : 1e30f;
+    // start: root of a0 + a M2/2 - a^2 M3/6 + a^3 M4/12, Newton from -2 a0/M2
+    float a = -2.f * a0 / M2;
+    for (int it = 0; it < 3; it++) {
+        float gg = a0 + a * (0.5f * M2 + a * (-M3 / 6.f + a * (M4 / 12.f)));
+        float gp = 0.5f * M2 + a * (-M3 / 3.f + a * (M4 / 4.f));
+        float an = a - gg / gp;
+        if (an > 0.f && an < 8.f) a = an;
+    }
+    float lo = 0.f, hi = amax * (1.f - 1e-6f);
+    if (!(a > lo && a < hi)) a = fminf(2.f, 0.5f * hi);
+    float h = 0.f, hhl = 0.f, hpl = 0.f;
+    float step_prev = 1e30f;
+    bool conv = false;
+    for (int it = 0; it < 12; it++) {
+        // four partial sums: shorter dependency chains than one running sum
+        float hq[4] = {0.f, 0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int p = 0; p < Q; p++) {
+            float l, ph;
+            const float y = a * x[p];
+            if (1.f + y <= 0.f) { ph = -y; l = -88.f; }
+            else lphi_f32(y, &l, &ph);
+            hq[p & 3] = fmaf(f[p], ph, hq[p & 3]);
+            gq[p & 3] = fmaf(d[p], l, gq[p & 3]);
+        }
+        const float hh = (hq[0] + hq[1]) + (hq[2] + hq[3]);
+        const float g = (gq[0] + gq[1]) + (gq[2] + gq[3]);
+        if (!conv) {
+            h = hh + a * a0;
+            hhl = hh;
+            hpl = g + a0;
+            if (h == 0.f || (step_prev <= 1e-3f * a && fabsf(h) <= 5e-7f * (hh + fabsf(a * a0)))) {
+                conv = true;
+            } else {
+                if (h < 0.f) lo = a; else hi = a;
+                float an = a - h / hpl;
+                if (!(an > lo && an < hi)) an = 0.5f * (lo + hi);
+                step_prev = fabsf(an - a);
+                a = an;
+                conv = step_prev <= 1e-6f * a;
+            }
+        }
+        if (__all_sync(__activemask(), conv)) break;
+    }
+    o.alpha = a;
+    o.status = a >= amax * (1.f - 2e-6f) ? 3 : 0;
+    const float bound = 0x1p-21f * (hhl + a * (fabsf(a0) + tla)) + 0x1p-23f * a * fabsf(hpl);
+    o.herr = (fabsf(h) + bound) * irho;
+    if (!guard || o.status == 3) return o;
+    const float tol = 1e-10f * rho;
+    const bool need = !(fabsf(h) + bound <= 0.5f * tol);
+    if (need) {
+        o.guarded = 1;
+        const float4 gr = alpha_guard(f, d, rho, a);
+        o.alpha = gr.x;
+        o.alpha_lo = gr.y;
+        o.herr = gr.z;
+        if (gr.w == 0.f) { o.status = 4; o.herr = fabsf(h) * irho; }
+    }
+    return o;
+}
+
+}  // namespace elbm

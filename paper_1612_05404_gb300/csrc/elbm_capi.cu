@@ -165,6 +165,9 @@ __global__ void __launch_bounds__(256) k_finalize(const double *part, int nblock
         scal[S_STEPS] += 1.0;
         diag[17] = scal[S_STEPS];
         diag[18] = scal[S_ITER_TOTAL] * ctl.ce;
+        diag[19] = res[D_NGUARD];
+        diag[20] = res[D_NGFAIL];
+        diag[21] = res[D_NLFALL];
     }
     for (int i = 0; i < S_NSCAL; i++) scalf[i] = (float)scal[i];
 }
@@ -188,7 +191,7 @@ int validate(const elbm_params *p, const elbm_init_fields *in, int n_instances)
     if (p->force_el != ELBM_FEL_QE) return 1;
     if (p->alpha_mode != ELBM_ALPHA_ENTROPIC && p->alpha_mode != ELBM_ALPHA_BGK) return 1;
     if (p->precision < ELBM_PREC_FP64 || p->precision > ELBM_PREC_BF16) return 1;
-    if (p->alpha_precision != ELBM_APREC_FP64 && p->alpha_precision != ELBM_APREC_FP32) return 1;
+    if (p->alpha_precision < ELBM_APREC_FP64 || p->alpha_precision > ELBM_APREC_FP32_FAST) return 1;
     if (!(p->nu0 > 0.0) || !(p->nu_inf > 0.0) || !(p->rho0 > 0.0)) return 1;
     if (!(p->n_carreau > 0.0) || !(p->lambda >= 0.0)) return 1;
     // FP32 arithmetic leaves about 3e-7 of noise in Delta_p/f_p; an alpha root

@@ -207,7 +207,6 @@ __device__ __forceinline__ T carreau_nu(const Cst<T> &k, bool newtonian, T Pn, T
 // 3 clipped at the positivity bound. The fallback in 1 and 2 is a = 2 (BGK).
 // ---------------------------------------------------------------------------
 struct AlphaOut { double alpha, herr; int status; };
-struct AlphaOutF { float alpha, herr; int status; };
 
 // FP64: same root as the plain definition, Newton in the sign bracket from 2.
 __device__ __forceinline__ AlphaOut alpha_fp64(const double *f, const double *d, double rho,
@@ -265,118 +264,6 @@ __device__ __forceinline__ AlphaOut alpha_fp64(const double *f, const double *d,
     return o;
 }
 
-// ln(1+y) and phi(y) = (1+y) ln(1+y) - y in FP32 without cancellation, from
-// the atanh series in s = y/(2+y): ln(1+y) = 2 s A(s^2), A(t) = sum t^k/(2k+1),
-// and phi(y) = 2 s^2 (s A1 + A)/(1 - s), A1 = (A - 1)/t = sum t^k/(2k+3).
-// For |s| <= 1/3 (y in [-1/2, 1]) eight terms leave a truncation error below
-// 1e-8 relative; outside, the library log1pf (rare: strong non-equilibrium).
-__device__ __forceinline__ void lphi_f32(float y, float *l, float *ph)
-{
-    float s = __fdividef(y, 2.f + y);
-    if (fabsf(s) <= 0.3334f) {
-        float t = s * s;
-        float A1 = 1.f / 3 + t * (1.f / 5 + t * (1.f / 7 + t * (1.f / 9 + t * (1.f / 11 + t * (1.f / 13 + t * (1.f / 15 + t * (1.f / 17)))))));
-        float A = 1.f + t * A1;
-        *l = 2.f * s * A;
-        *ph = __fdividef(2.f * t * (s * A1 + A), 1.f - s);
-    } else {
-        float lg = log1pf(y);
-        *l = lg;
-        *ph = (1.f + y) * lg - y;
-    }
-}
-
-// FP32: the same root of the same equation. h(a) = sum_p f_p phi(a x_p) + a h'(0)
-// with h'(0) = (1 + ln rho) sum D + sum D_p ln(f_p/(w_p rho)) (sum D by TwoSum,
-// Knuth); no term carries cancellation. Start from the root of the moment
-// expansion h(a)/a ~ h'(0) + a M2/2 - a^2 M3/6 + a^3 M4/12 (M_k = sum f x^k),
-// then safeguarded Newton steps on the exact h (at most 12; two or three near
-// equilibrium) until the step is below 1e-6 alpha or h is at the FP32 noise
-// floor of its terms; the warp leaves the loop together once every lane has
-// converged, so only warps holding strongly non-equilibrium sites iterate on.
-__device__ __forceinline__ AlphaOutF alpha_fp32(const float *f, const float *d, const float *fdev,
-                                                float rho, float drho, float eq_tol)
-{
-    AlphaOutF o; o.alpha = 2.f; o.herr = 0.f; o.status = 0;
-    float x[Q];
-    float maxabs = 0.f, xneg = 0.f;
-    float s = 0.f, c = 0.f, tl = 0.f, M2 = 0.f, M3 = 0.f, M4 = 0.f;
-    const float lr = __logf(rho);
-    const float irho = 1.f / rho;
-#pragma unroll
-    for (int p = 0; p < Q; p++) {
-        x[p] = __fdividef(d[p], f[p]);
-        maxabs = fmaxf(maxabs, fabsf(x[p]));
-        xneg = fminf(xneg, x[p]);
-        float t = s + d[p];
-        float bp = t - s;
-        c += (s - (t - bp)) + (d[p] - bp);
-        s = t;
-        const float iw = float(1.0 / wq(p));
-        float z = (fdev[p] - float(wq(p)) * drho) * iw * irho;
-        float lz, ph;
-        lphi_f32(z, &lz, &ph);
-        tl += d[p] * lz;
-        float fx2 = f[p] * x[p] * x[p];
-        M2 += fx2;
-        M3 += fx2 * x[p];
-        M4 += fx2 * x[p] * x[p];
-    }
-    const float a0 = (1.f + lr) * (s + c) + tl;
-    if (!(maxabs >= eq_tol)) { o.status = 1; return o; }
-    if (a0 >= 0.f) { o.status = 2; return o; }
-    const float amax = xneg < 0.f ? -1.f / xneg : 1e30f;
-    // start: root of a0 + a M2/2 - a^2 M3/6 + a^3 M4/12, Newton from -2 a0/M2
-    float a = -2.f * a0 / M2;
-    for (int it = 0; it < 3; it++) {
-        float g = a0 + a * (0.5f * M2 + a * (-M3 / 6.f + a * (M4 / 12.f)));
-        float gp = 0.5f * M2 + a * (-M3 / 3.f + a * (M4 / 4.f));
-        float an = a - g / gp;
-        if (an > 0.f && an < 8.f) a = an;
-    }
-    float lo = 0.f, hi = amax * (1.f - 1e-6f);
-    if (!(a > lo && a < hi)) a = fminf(2.f, 0.5f * hi);
-    float h = 0.f;
-    bool clipped = false;
-    // Converged lanes freeze their alpha while the rest of the warp iterates:
-    // a lane that kept iterating at an exact FP32 zero of h would bisect away
-    // from its root. Converged: h exactly 0, or |h| at the FP32 noise floor of
-    // its terms (hh = sum f phi >= 0) after a step below 1e-3 alpha, or a
-    // Newton step below 1e-6 alpha.
-    float step_prev = 1e30f;
-    bool conv = false;
-    for (int it = 0; it < 12; it++) {
-        float hh = 0.f, g = 0.f;
-#pragma unroll
-        for (int p = 0; p < Q; p++) {
-            float y = a * x[p];
-            float l, ph;
-            if (1.f + y <= 0.f) { ph = -y; l = -88.f; }
-            else lphi_f32(y, &l, &ph);
-            hh += f[p] * ph;
-            g += d[p] * l;
-        }
-        if (!conv) {
-            h = hh + a * a0;
-            if (h == 0.f || (step_prev <= 1e-3f * a && fabsf(h) <= 5e-7f * (hh + fabsf(a * a0)))) {
-                conv = true;
-            } else {
-                const float hp = g + a0;
-                if (h < 0.f) lo = a; else hi = a;
-                float an = a - h / hp;
-                if (!(an > lo && an < hi)) an = 0.5f * (lo + hi);
-                step_prev = fabsf(an - a);
-                a = an;
-                conv = step_prev <= 1e-6f * a;
-            }
-        }
-        if (__all_sync(__activemask(), conv)) break;
-    }
-    if (a >= amax * (1.f - 2e-6f)) clipped = true;
-    o.alpha = a;
-    o.herr = fabsf(h) / rho;
-    o.status = clipped ? 3 : 0;
-    return o;
-}
-
 }  // namespace elbm
+
+#include "elbm_alpha.cuh"

@@ -23,7 +23,7 @@ enum {
 // per-block partial slots of the collision diagnostics
 enum {
     D_MASS = 0, D_MX, D_MY, D_MZ, D_Q, D_AMIN, D_AMAX, D_ASUM, D_NSHORT, D_NNOROOT,
-    D_NCLIP, D_HERR, D_UMAX, D_NBAD, D_NFLUID, D_NPART = 16
+    D_NCLIP, D_HERR, D_UMAX, D_NBAD, D_NFLUID, D_NGUARD, D_NGFAIL, D_NLFALL, D_NPART = 18
 };
 
 struct Phys {

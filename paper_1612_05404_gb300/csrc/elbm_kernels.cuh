@@ -38,9 +38,9 @@ __device__ __forceinline__ double warp_sum(double v)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
 }
-__device__ __forceinline__ double warp_sum(float v)
+// compensated FP32 warp sum of (hi, lo) pairs; the result on lane 0
+__device__ __forceinline__ void warp_sum2(float &hi, float &lo)
 {
-    float hi = v, lo = 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         float ohi = __shfl_down_sync(0xffffffffu, hi, o);
@@ -50,15 +50,15 @@ __device__ __forceinline__ double warp_sum(float v)
         hi = sm;
         lo += olo + e;
     }
-    return (double)hi + (double)lo;
 }
 
 __device__ __forceinline__ int num_blocks() { return gridDim.x * gridDim.y * gridDim.z; }
 
 // Per-block partial sums are stored column-major, part[k * nblocks + block],
 // so the finalize kernel reads each column with coalesced loads.
-template <int K, typename T>
-__device__ __forceinline__ void block_sums(const T (&v)[K], double *out, int stride = 1)
+// FP64 values: FP64 warp sums, thread 0 adds the warps.
+template <int K>
+__device__ __forceinline__ void block_sums(const double (&v)[K], double *out, int stride = 1)
 {
     __shared__ double sh[K][8];
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
@@ -77,6 +77,36 @@ __device__ __forceinline__ void block_sums(const T (&v)[K], double *out, int str
             for (int i = 0; i < nw; i++) t += sh[k][i];
             out[(long long)k * stride] = t;
         }
+    }
+}
+
+// FP32 values: compensated (hi, lo) FP32 sums across the warp and across the
+// block's warps, so that no FP64 instruction runs per thread (the FP64 pipe
+// of this part issues 1/64 of the FP32 rate); lane k of warp 0 turns sum k
+// into FP64 once per block.
+template <int K>
+__device__ __forceinline__ void block_sums(const float (&v)[K], double *out, int stride = 1)
+{
+    __shared__ float sh[2][K][8];
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int lane = tid & 31, wid = tid >> 5;
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        float hi = v[k], lo = 0.f;
+        warp_sum2(hi, lo);
+        if (lane == 0) { sh[0][k][wid] = hi; sh[1][k][wid] = lo; }
+    }
+    __syncthreads();
+    if (tid < K) {
+        float hi = sh[0][tid][0], lo = sh[1][tid][0];
+        for (int i = 1; i < nw; i++) {
+            float sm, e;
+            two_sum(hi, sh[0][tid][i], sm, e);
+            hi = sm;
+            lo += sh[1][tid][i] + e;
+        }
+        out[(long long)tid * stride] = (double)hi + (double)lo;
     }
 }
 
@@ -503,7 +533,7 @@ __global__ void k_phi_shift(Geom g, Bufs b)
 // transport mode the D3Q7 charge update. Optional diagnostics per block.
 // ===========================================================================
 template <int PR, int AP>
-__global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int diag)
+__global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC_FP64) ? 1 : 4) k_collide(Geom g, Phys ph, Bufs b, int diag)
 {
     typedef Tr<PR> T;
     typedef typename T::ct ct;
@@ -515,8 +545,8 @@ __global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int di
     ll s;
     site_xyz(g, x, y, z, inb, s);
     const bool active = inb && (!b.mask || b.mask[s] == ELBM_NODE_FLUID);
-    ct dm = 0, dmx = 0, dmy = 0, dmz = 0, dq = 0, dasum = 0, dnfl = 0;
-    ct dsh = 0, dnr = 0, dcl = 0, dbad = 0;
+    ct dm = 0, dmx = 0, dmy = 0, dmz = 0, dq = 0, dasum = 0;
+    unsigned dnfl = 0, dsh = 0, dnr = 0, dcl = 0, dbad = 0, dgd = 0, dgf = 0, dlf = 0;
     float damin = 1e30f, damax = -1e30f, dherr = 0.f, dumax = 0.f;
     if (active) {
         Nbr n;
@@ -591,7 +621,7 @@ __global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int di
         // Eq. (entropic)
         ct alpha = ct(2);
         float a_herr = 0.f;
-        int a_status = 0;
+        int a_status = 0, a_guard = 0;
         if (ph.alpha_mode == ELBM_ALPHA_ENTROPIC) {
             if (sizeof(ct) == 8 || AP == ELBM_APREC_FP64) {
                 double fd[Q], dd[Q];
@@ -612,10 +642,12 @@ __global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int di
                     dd[p] = float(D[p]);
                     fv[p] = float(f[p]);
                 }
-                AlphaOutF ao = alpha_fp32(ff, dd, fv, float(r), float(drho), ph.cf.eq_tol);
+                AlphaOutF ao = alpha_fp32(ff, dd, fv, float(r), float(drho), ph.cf.eq_tol,
+                                          AP == ELBM_APREC_FP32);
                 alpha = ct(ao.alpha);
                 a_herr = ao.herr;
                 a_status = ao.status;
+                a_guard = ao.guarded;
             }
         }
 
@@ -701,6 +733,8 @@ __global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int di
             if (a_status == 1) dsh = 1;
             else if (a_status == 2) dnr = 1;
             else if (a_status == 3) dcl = 1;
+            else if (a_status == 4) dgf = 1;
+            dgd = a_guard;
             dherr = a_herr;
             float um = float(sqrt(upx * upx + upy * upy + upz * upz));
             dumax = um;
@@ -708,11 +742,18 @@ __global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int di
         }
     }
     if (diag) {
-        ct v[11] = {dm, dmx, dmy, dmz, dq, dasum, dsh, dnr, dcl, dbad, dnfl};
-        __shared__ double res[11];
+        // sums: compensated FP32 (or FP64) block sums; the five 0/1 counts
+        // packed 6 bits each (a warp count is at most 32) into one integer
+        // warp reduction; extrema by shuffles
+        ct v[6] = {dm, dmx, dmy, dmz, dq, dasum};
+        __shared__ double res[6];
         __shared__ float mm[4][8];
+        __shared__ unsigned cn[2][8];
         const int tid = threadIdx.x + blockDim.x * threadIdx.y;
         const int lane = tid & 31, wid = tid >> 5;
+        unsigned packed = dsh | (dnr << 6) | (dcl << 12) | (dbad << 18) | (dnfl << 24);
+        packed = __reduce_add_sync(0xffffffffu, packed);
+        unsigned packed2 = __reduce_add_sync(0xffffffffu, dgd | (dgf << 6) | (dlf << 12));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             damin = fminf(damin, __shfl_down_sync(0xffffffffu, damin, o));
@@ -720,20 +761,30 @@ __global__ void __launch_bounds__(128) k_collide(Geom g, Phys ph, Bufs b, int di
             dherr = fmaxf(dherr, __shfl_down_sync(0xffffffffu, dherr, o));
             dumax = fmaxf(dumax, __shfl_down_sync(0xffffffffu, dumax, o));
         }
-        if (lane == 0) { mm[0][wid] = damin; mm[1][wid] = damax; mm[2][wid] = dherr; mm[3][wid] = dumax; }
-        block_sums<11>(v, res);
+        if (lane == 0) {
+            mm[0][wid] = damin; mm[1][wid] = damax; mm[2][wid] = dherr; mm[3][wid] = dumax;
+            cn[0][wid] = packed;
+            cn[1][wid] = packed2;
+        }
+        block_sums<6>(v, res);
+        __syncthreads();
         if (tid == 0) {
             const ll nbk = num_blocks();
             double *out = b.part + block_id();
             out[D_MASS * nbk] = res[0]; out[D_MX * nbk] = res[1]; out[D_MY * nbk] = res[2]; out[D_MZ * nbk] = res[3];
-            out[D_Q * nbk] = res[4]; out[D_ASUM * nbk] = res[5]; out[D_NSHORT * nbk] = res[6]; out[D_NNOROOT * nbk] = res[7];
-            out[D_NCLIP * nbk] = res[8]; out[D_NBAD * nbk] = res[9]; out[D_NFLUID * nbk] = res[10];
+            out[D_Q * nbk] = res[4]; out[D_ASUM * nbk] = res[5];
             const int nw = (blockDim.x * blockDim.y + 31) >> 5;
             float a0 = 1e30f, a1 = -1e30f, h = 0.f, u = 0.f;
+            unsigned c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             for (int i = 0; i < nw; i++) {
                 a0 = fminf(a0, mm[0][i]); a1 = fmaxf(a1, mm[1][i]);
                 h = fmaxf(h, mm[2][i]); u = fmaxf(u, mm[3][i]);
+                for (int k = 0; k < 5; k++) c[k] += (cn[0][i] >> (6 * k)) & 63u;
+                for (int k = 0; k < 3; k++) c[5 + k] += (cn[1][i] >> (6 * k)) & 63u;
             }
+            out[D_NSHORT * nbk] = c[0]; out[D_NNOROOT * nbk] = c[1]; out[D_NCLIP * nbk] = c[2];
+            out[D_NBAD * nbk] = c[3]; out[D_NFLUID * nbk] = c[4];
+            out[D_NGUARD * nbk] = c[5]; out[D_NGFAIL * nbk] = c[6]; out[D_NLFALL * nbk] = c[7];
             out[D_AMIN * nbk] = a0; out[D_AMAX * nbk] = a1; out[D_HERR * nbk] = h; out[D_UMAX * nbk] = u;
         }
     }
@@ -828,6 +879,8 @@ struct Launchers {
     {
         if (PR == ELBM_PREC_FP64 || ph.aprec == ELBM_APREC_FP64)
             k_collide<PR, ELBM_APREC_FP64><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
+        else if (ph.aprec == ELBM_APREC_FP32_FAST)
+            k_collide<PR, ELBM_APREC_FP32_FAST><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
         else
             k_collide<PR, ELBM_APREC_FP32><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
     }

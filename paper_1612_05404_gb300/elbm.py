@@ -16,14 +16,16 @@ LIB_PATH = os.path.join(HERE, "_build", "libelbm.so")
 
 OK, W_POISSON_NOCONV, E_INVAL, E_NOMEM, E_CUDA, E_NUMERIC, E_STATE = 0, 1, -1, -2, -3, -4, -5
 F_RHO, F_U, F_PHI, F_Q, F_ALPHA, F_NU, F_POP, F_GPOP, F_DIAG = (1 << i for i in range(9))
-NDIAG = 20
+NDIAG = 24
 DIAG_NAMES = [
     "mass", "mom_x", "mom_y", "mom_z", "charge", "alpha_min", "alpha_max", "alpha_mean",
     "n_shortcut", "n_noroot", "n_clipped", "poisson_sweeps", "poisson_resid", "max_h_error",
-    "max_u", "n_nonfinite", "q_mean", "step", "poisson_sweeps_total", "reserved",
+    "max_u", "n_nonfinite", "q_mean", "step", "poisson_sweeps_total", "n_guarded",
+    "n_guard_failed", "n_learned_fallback", "reserved22", "reserved23",
 ]
 EXPORTS = ["elbm_init", "elbm_step", "elbm_fields", "elbm_fields_size", "elbm_free",
-           "elbm_strerror", "elbm_velocity_set", "elbm_pass_times", "elbm_density_noalloc"]
+           "elbm_strerror", "elbm_velocity_set", "elbm_pass_times", "elbm_density_noalloc",
+           "elbm_alpha_eval"]
 NOALLOC_MAX_SITES = 16384 * 1024
 
 _FACE = {"periodic": 0, "wall": 1}
@@ -32,7 +34,7 @@ _CHARGE = {"none": 0, "conserved": 1, "xi": 2, "transport": 3}
 _FEL = {"qe": 0, "full": 1}
 _ALPHA = {"entropic": 0, "bgk": 1}
 _PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
-_APREC = {"fp64": 0, "fp32": 1}
+_APREC = {"fp64": 0, "fp32": 1, "fp32_fast": 2}
 
 
 class ElbmError(RuntimeError):
@@ -102,6 +104,8 @@ def lib():
         L.elbm_pass_times.restype = ctypes.c_int
         L.elbm_density_noalloc.argtypes = [vp, vp, ctypes.c_longlong, vp, vp, vp]
         L.elbm_density_noalloc.restype = ctypes.c_int
+        L.elbm_alpha_eval.argtypes = [vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_double, vp, vp, vp, vp, vp, vp]
+        L.elbm_alpha_eval.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -174,6 +178,32 @@ def density_noalloc(f_ptr: int, mask_ptr, n_sites: int, rho_ptr: int, mass_ptr: 
     return lib().elbm_density_noalloc(ctypes.c_void_p(f_ptr), ctypes.c_void_p(mask_ptr or 0),
                                       int(n_sites), ctypes.c_void_p(rho_ptr), ctypes.c_void_p(mass_ptr),
                                       stream)
+
+
+def alpha_eval(d, aprec="fp32", eq_tol=1e-5, mlp=None, with_delta=False, stream=None):
+    """elbm_alpha_eval on a CUDA tensor of FP32 deviations d (19, n).
+
+    Returns (alpha FP64 [n], herr FP32 [n], status int32 [n], delta FP32
+    (19, n) or None) as CUDA tensors, computed on `stream` (default: the
+    current torch stream)."""
+    import torch
+    if not (d.is_cuda and d.dtype == torch.float32 and d.dim() == 2 and d.shape[0] == 19):
+        raise ValueError("d must be a CUDA float32 tensor of shape (19, n)")
+    d = d.contiguous()
+    n = d.shape[1]
+    alpha = torch.empty(n, dtype=torch.float64, device=d.device)
+    herr = torch.empty(n, dtype=torch.float32, device=d.device)
+    status = torch.empty(n, dtype=torch.int32, device=d.device)
+    delta = torch.empty((19, n), dtype=torch.float32, device=d.device) if with_delta else None
+    rc = lib().elbm_alpha_eval(ctypes.c_void_p(d.data_ptr()), n, _APREC[aprec], float(eq_tol),
+                               ctypes.c_void_p(0 if mlp is None else mlp.data_ptr()),
+                               ctypes.c_void_p(alpha.data_ptr()), ctypes.c_void_p(herr.data_ptr()),
+                               ctypes.c_void_p(status.data_ptr()),
+                               ctypes.c_void_p(0 if delta is None else delta.data_ptr()),
+                               stream if stream is not None else _cur_stream())
+    if rc != 0:
+        raise ElbmError(rc)
+    return alpha, herr, status, delta
 
 
 class Sim:

@@ -90,6 +90,20 @@ def uniform_noise(n, amp, seed):
     return np.random.default_rng(seed).uniform(-amp, amp, size=n)
 
 
+D3Q19_WEIGHTS = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+
+
+def random_populations(n, amp, seed, rho_range=(0.16, 2.2)):
+    """n synthetic D3Q19 sites, (19, n) FP64: f_p = w_p rho (1 + e_p) with rho
+    uniform in rho_range and e_p uniform in [-amp, amp] (amp < 1 keeps every
+    population positive). Inputs for the alpha root away from equilibrium:
+    the relative departures e_p set the size of Delta_p / f_p."""
+    rng = np.random.default_rng(seed)
+    rho = rng.uniform(*rho_range, size=n)
+    e = rng.uniform(-amp, amp, size=(19, n))
+    return D3Q19_WEIGHTS[:, None] * rho[None, :] * (1.0 + e)
+
+
 def charged_drop_at_rest(n=32, radius=8.0, precision="fp64", steps=500, seed=SEED_BASE + 1,
                          eps_ratio=2.0, sigma_ratio=10.0, Q=1e-3, noise=1e-4):
     """Charged drop at rest on an n^3 periodic D3Q19 lattice; the free charge is

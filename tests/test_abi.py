@@ -99,3 +99,18 @@ def test_null_arguments(L):
     assert L.elbm_init(None, None, 1, None) == elbm.E_INVAL
     assert L.elbm_step(None, 1) == elbm.E_INVAL
     L.elbm_free(None)
+
+
+def test_alpha_eval_argument_checks(L):
+    """elbm_alpha_eval validates before touching the device: bad arguments
+    return ELBM_E_INVAL and n = 0 enqueues nothing (both run without a GPU)."""
+    import ctypes
+    p = ctypes.c_void_p(16)  # never dereferenced: every call below fails validation or has n = 0
+    assert L.elbm_alpha_eval(None, 0, 1, 1e-5, None, None, None, None, None, None) == 0
+    assert L.elbm_alpha_eval(p, -1, 1, 1e-5, None, p, None, None, None, None) == elbm.E_INVAL
+    assert L.elbm_alpha_eval(None, 5, 1, 1e-5, None, p, None, None, None, None) == elbm.E_INVAL
+    assert L.elbm_alpha_eval(p, 5, 1, 1e-5, None, None, None, None, None, None) == elbm.E_INVAL
+    assert L.elbm_alpha_eval(p, 5, 7, 1e-5, None, p, None, None, None, None) == elbm.E_INVAL
+    assert L.elbm_alpha_eval(p, 5, 1, 1e-9, None, p, None, None, None, None) == elbm.E_INVAL
+    assert L.elbm_alpha_eval(p, 5, 1, -1.0, None, p, None, None, None, None) == elbm.E_INVAL
+    assert L.elbm_alpha_eval(p, 5, 1, 1e-5, p, p, None, None, None, None) == elbm.E_INVAL

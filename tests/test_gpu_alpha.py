@@ -1,0 +1,74 @@
+"""The entropic alpha root on the GPU (elbm_alpha_eval) against the FP64 oracle.
+
+H-error := |h(alpha)| / rho with h(a) = H(f + a Delta) - H(f) of Eq. (entropic),
+evaluated by the oracle in FP64 on exactly the FP32 populations and Delta the
+GPU used. Target (reduced precision with the float-float guard): <= 1e-10.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1612_05404_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+W32 = W.D3Q19_WEIGHTS.astype(np.float32)
+
+
+def _sites():
+    """Drop-in-field sites after a few oracle steps, plus synthetic sites far
+    from equilibrium (relative departures up to 2, 10 and 30 %)."""
+    cfg, fl = W.drop_in_field(E0=1e-3, n=16, radius=4.5, precision="fp64")
+    s = oracle.Sim(cfg, fl)
+    s.step(6)
+    f_drop = s.f.reshape(19, -1)
+    parts = [f_drop] + [W.random_populations(2048, amp, seed=31 + i) for i, amp in enumerate((0.02, 0.1, 0.3))]
+    return np.concatenate(parts, axis=1)
+
+
+def _run(f64, aprec):
+    import torch
+    from paper_1612_05404_gb300 import elbm
+    d32 = (f64 - W.D3Q19_WEIGHTS[:, None]).astype(np.float32)
+    d = torch.from_numpy(d32).cuda()
+    a, he, st, delta = elbm.alpha_eval(d, aprec=aprec, eq_tol=1e-5, with_delta=True)
+    torch.cuda.synchronize()
+    f32 = (W32[:, None] + d32).astype(np.float64)  # the FP32 populations the kernel used
+    return f32, delta.cpu().numpy().astype(np.float64), a.cpu().numpy(), he.cpu().numpy(), st.cpu().numpy()
+
+
+def _h_err(f, D, a):
+    return np.array([abs(oracle.h(3, f[:, i], D[:, i], a[i])) / f[:, i].sum() for i in range(f.shape[1])])
+
+
+def test_alpha_fp32_guard_meets_h_error():
+    f, D, a, he, st = _run(_sites(), "fp32")
+    assert not np.any(st == 4), "guard ended above 1e-10 rho"
+    root = st == 0
+    assert root.sum() > 1000
+    assert np.all(a[~root & (st != 3)] == 2.0)
+    err = _h_err(f[:, root], D[:, root], a[root])
+    assert err.max() <= 1e-10, err.max()
+    # the reported H-error is the evaluated one (guard) or an upper bound
+    assert np.all(he[root] <= 1e-10)
+    # the same root as the oracle's FP64 Newton on the same inputs
+    for i in np.flatnonzero(root)[::37]:
+        ar, sr = oracle.alpha(3, f[:, i], D[:, i], 1e-5)
+        assert sr == 0
+        hp = abs(oracle.h(3, f[:, i], D[:, i], ar * (1 + 1e-6)) - oracle.h(3, f[:, i], D[:, i], ar)) / (ar * 1e-6)
+        assert abs(a[i] - ar) * hp / f[:, i].sum() <= 2e-10
+
+
+def test_alpha_fp32_fast_bound_holds():
+    f, D, a, he, st = _run(_sites(), "fp32_fast")
+    root = st == 0
+    err = _h_err(f[:, root], D[:, root], a[root])
+    # without the guard the reported value is |h| plus the FP32 rounding bound
+    assert np.all(err <= he[root] * 1.0001 + 1e-15)
+
+
+def test_alpha_fp64_root():
+    f, D, a, he, st = _run(_sites(), "fp64")
+    root = st == 0
+    err = _h_err(f[:, root], D[:, root], a[root])
+    assert err.max() <= 1e-13, err.max()
