@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="issue each step from the host (profilers see every launch)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-alpha-compare", action="store_true",
+                    help="skip the learned-alpha vs Newton-alpha comparison")
     return ap.parse_args()
 
 
@@ -305,6 +307,113 @@ def e2e_run(args, cfgs, N):
             "timed": "init + %d steps + per-step rho/diag read + free" % n_steps}
 
 
+def _timed_steps(sims, streams, pool, steps, warmup):
+    """Device time (ms) of `steps` steps of all lattices, after `warmup`."""
+    import torch
+    for _ in range(warmup):
+        list(pool.map(lambda s: s.step(1), sims))
+    torch.cuda.synchronize()
+    p0 = [s.pass_times() for s in sims]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    total = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for st in streams:
+            st.wait_event(e0)
+        list(pool.map(lambda s: s.step(1), sims))
+        cur = torch.cuda.current_stream()
+        for st in streams:
+            cur.wait_event(st.record_event())
+        e1.record()
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+    p1 = [s.pass_times() for s in sims]
+    d = {k: sum(b[k] - a[k] for a, b in zip(p0, p1)) for k in p0[0]}
+    return total, d
+
+
+def alpha_compare(args, N):
+    """Learned-alpha vs Newton-alpha on the bench workload at one H-error
+    bound (<= 1e-10 rho): the FP64 Newton root, the FP32 Newton root with the
+    float-float guard, and the FP32 iteration started from the learned
+    proposal (trained here on the GPU: pairs harvested from the first steps of
+    the E0 = 1e-3 lattice, the project's training kernels); step throughput,
+    collision time per launch, device H-error and fallbacks."""
+    import ctypes
+    from concurrent.futures import ThreadPoolExecutor
+    import numpy as np
+    import torch
+    from paper_1612_05404_gb300 import elbm
+    from paper_1612_05404_gb300 import workloads as W
+    out = {}
+    # training pairs from the plain run of one lattice
+    t0 = time.perf_counter()
+    cfg, fields = W.drop_in_field(E0=1e-3, precision=args.precision)
+    cfg.update(alpha_precision="fp32", store_macro=0, diag_every=1, poisson_check_every=8, graph=1)
+    sim = elbm.Sim(cfg, fields)
+    Xs, ys = [], []
+    for k in range(24):
+        sim.step(1)
+        if k % 3 == 2:
+            d = torch.from_numpy((sim.get("f").reshape(19, -1) - W.D3Q19_WEIGHTS[:, None]).astype(np.float32)).cuda()
+            X, y, keep = elbm.alpha_harvest(d)
+            kk = keep.bool()
+            Xs.append(X[:, kk])
+            ys.append(y[kk])
+    sim.close()
+    X = torch.cat(Xs, dim=1).contiguous()
+    y = torch.cat(ys).contiguous()
+    rng = np.random.default_rng(20161209)
+    import math
+    lim1, lim2, lim3 = math.sqrt(6 / 84), math.sqrt(6 / 128), math.sqrt(6 / 65)
+    theta = torch.zeros(elbm.MLP_NPARAM, dtype=torch.float32)
+    theta[:1280] = torch.from_numpy(rng.uniform(-lim1, lim1, 1280).astype(np.float32))
+    theta[1344:5440] = torch.from_numpy(rng.uniform(-lim2, lim2, 4096).astype(np.float32))
+    theta[5504:5568] = torch.from_numpy(rng.uniform(-lim3, lim3, 64).astype(np.float32))
+    theta = theta.cuda()
+    m, v = torch.zeros_like(theta), torch.zeros_like(theta)
+    hist = elbm.mlp_train(X, y, theta, m, v, 0, 4000, 1024, 2e-3, seed=20161209)
+    torch.cuda.synchronize()
+    h = hist.cpu().numpy()
+    out["training"] = {"pairs": int(X.shape[1]), "steps": 4000, "batch": 1024,
+                       "loss_first": float(h[:50].mean()), "loss_last": float(h[-50:].mean()),
+                       "seconds": time.perf_counter() - t0,
+                       "data": "pairs harvested every 3rd of the first 24 steps of the E0=1e-3 lattice, S >= 2^-5"}
+
+    def run(mode, aprec, steps):
+        cfgs = workload_cfgs(args)
+        streams = [torch.cuda.Stream() for _ in cfgs]
+        sims = []
+        for (c, f), st in zip(cfgs, streams):
+            c.update(profile=1, alpha_mode=mode, alpha_precision=aprec)
+            if mode == "learned":
+                c["mlp"] = theta
+            sims.append(elbm.Sim(c, f, stream=ctypes.c_void_p(st.cuda_stream)))
+        pool = ThreadPoolExecutor(max_workers=len(sims))
+        ms, d = _timed_steps(sims, streams, pool, steps, args.warmup)
+        diag = [s.diag() for s in sims]
+        for s in sims:
+            s.close()
+        pool.shutdown()
+        return {"mlups": len(sims) * N * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
+                "collide_ms_per_launch": d["collide_ms"] / max(d["collide_launches"], 1),
+                "max_h_error_device": max(x["max_h_error"] for x in diag),
+                "guarded_sites_last_step": sum(x["n_guarded"] for x in diag),
+                "learned_fallback_sites_last_step": sum(x["n_learned_fallback"] for x in diag),
+                "steps": steps}
+
+    out["newton_fp64"] = run("entropic", "fp64", max(2, args.steps // 5))
+    out["newton_fp32_guarded"] = run("entropic", "fp32", args.steps)
+    out["learned_fp32_guarded"] = run("learned", "fp32", args.steps)
+    out["h_error_bound"] = 1e-10
+    out["speedup_learned_vs_newton_fp32"] = out["learned_fp32_guarded"]["mlups"] / out["newton_fp32_guarded"]["mlups"]
+    out["speedup_learned_vs_newton_fp64"] = out["learned_fp32_guarded"]["mlups"] / out["newton_fp64"]["mlups"]
+    return out
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -324,6 +433,8 @@ def main():
     if not args.no_e2e:
         res["e2e"] = e2e_run(args, cfgs, N)
         res["e2e"]["value"] *= world
+    if rank == 0 and world == 1 and not args.no_alpha_compare and args.precision != "fp64":
+        res["alpha_compare"] = alpha_compare(args, N)
     if rank == 0 and world == 1 and not args.no_cpu:
         v, dt, sample = cpu_sample()
         res["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample}

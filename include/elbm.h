@@ -60,8 +60,10 @@ enum { ELBM_FEL_QE = 0, ELBM_FEL_FULL = 1 };
  * the same stopping rule; multigrid needs no interior solid nodes and lattice
  * extents that halve at least once (even, and even on periodic axes) */
 enum { ELBM_POISSON_SOR = 0, ELBM_POISSON_MG = 1 };
-/* relaxation: entropic alpha (Eq. entropic) or alpha = 2 (BGK) */
-enum { ELBM_ALPHA_ENTROPIC = 0, ELBM_ALPHA_BGK = 1 };
+/* relaxation: entropic alpha (Eq. entropic), alpha = 2 (BGK), or the
+ * entropic alpha with its Newton iteration started from the learned proposal
+ * (elbm_params.mlp; FP32 or BF16 storage with FP32 alpha arithmetic) */
+enum { ELBM_ALPHA_ENTROPIC = 0, ELBM_ALPHA_BGK = 1, ELBM_ALPHA_LEARNED = 2 };
 /* population storage / arithmetic:
  *   FP64: f stored and computed in FP64, potential in FP64;
  *   FP32: f stored as FP32 deviations d = f - w, FP32 arithmetic;
@@ -139,6 +141,9 @@ typedef struct elbm_params {
                                     >= 2^-18 when the arithmetic is FP32 */
     double rho_in, rho_out;      /* densities of inlet / outlet nodes */
     void *cuda_stream;           /* cudaStream_t of the caller (NULL: default stream) */
+    const float *mlp;            /* ELBM_ALPHA_LEARNED: device FP32 parameters of the
+                                    proposal (ELBM_MLP_NPARAM values), read once by
+                                    elbm_init (kept as BF16 by the handle); else NULL */
 } elbm_params;
 
 /* Initial state, all host arrays of N = nx*ny*nz sites (caller-owned):
@@ -195,19 +200,74 @@ elbm_status elbm_pass_times(const elbm_handle *h, double *out, int n);
  *   aprec   ELBM_APREC_* arithmetic of the root;
  *   eq_tol  near-equilibrium shortcut (alpha = 2) when max|Delta/f| < eq_tol;
  *           >= 2^-18 for the FP32 modes;
- *   mlp     must be NULL (reserved for the learned proposal);
+ *   mlp     NULL: Newton from the moment-series start; else device FP32
+ *           parameters of the learned proposal (ELBM_MLP_NPARAM values, see
+ *           elbm_mlp_forward): Newton starts from alpha_c + S^3 o(X); FP32
+ *           modes only;
  *   alpha   device FP64 out [n]: the root (high + low part of a guarded root);
  *   herr    device FP32 out [n] or NULL: |h(alpha)|/rho as the method
  *           reports it (evaluated, or the FP32 rounding bound);
  *   status  device int32 out [n] or NULL: 0 root, 1 shortcut, 2 no root
  *           (alpha = 2), 3 clipped at the positivity bound, 4 guard ended
- *           above 1e-10 rho;
+ *           above 1e-10 rho, 5 root after more than one FP32 evaluation of h
+ *           (with a learned proposal: the lane fell back to the full Newton
+ *           iteration);
  *   delta   device FP32 out [19*n] or NULL: the Delta_p planes used;
  *   stream  cudaStream_t (NULL: legacy default stream).
  * Buffers are the caller's; returns after enqueueing (ELBM_E_INVAL on a
  * bad argument, nothing enqueued). */
 elbm_status elbm_alpha_eval(const float *d, long long n, int aprec, double eq_tol, const float *mlp,
                             double *alpha, float *herr, int *status, float *delta, void *stream);
+
+/* ---- learned alpha proposal (not in the paper: an addition that starts the
+ * Newton iteration of Eq. (entropic); the root and its H-error stay the
+ * method's) ----
+ * Features of a site (populations f_p, Delta_p = f^eq_p - f_p), x_p =
+ * Delta_p/f_p, S = max|x_p|: X = (x_0/S .. x_18/S, (log2 S + 9)/8). Network
+ * o(X) = W3 . gelu(W2 gelu(W1 X + b1) + b2) + b3, 20 -> 64 -> 64 -> 1, gelu in
+ * the tanh form; proposal alpha = alpha_c + S^3 o where S >= 2^-5 (else
+ * alpha_c), alpha_c the moment-series start (root of h(a)/a truncated after
+ * a^3 M4/12, M_k = sum f x^k; error O(S^3)). Parameters: one FP32 vector of
+ * ELBM_MLP_NPARAM values, W1 (64 x 20, row-major out x in), b1 (64), W2
+ * (64 x 64), b2 (64), W3 (64), b3 (1). Sample arrays are feature-major:
+ * X[j*n + i]. All pointers are device memory owned by the caller; calls
+ * return after enqueueing on `stream`; bad arguments give ELBM_E_INVAL with
+ * nothing enqueued. */
+#define ELBM_MLP_NIN 20
+#define ELBM_MLP_NPARAM 5569
+enum { ELBM_MLP_FP32 = 0, ELBM_MLP_BF16_TC = 1 };
+/* features of n sites from FP32 deviations d[p*n + i] (as elbm_alpha_eval
+ * computes Delta): X out [20*n], S out [n] or NULL */
+elbm_status elbm_alpha_features(const float *d, long long n, float *X, float *S, void *stream);
+/* training pairs from FP32 deviations: X out [20*n] (features), y out [n] =
+ * (alpha* - alpha_c)/S^3 clipped to [-8, 8] with alpha* the guarded FP32 root
+ * (|h| <= 1e-10 rho), keep out [n] = 1 for a root with S >= 2^-5 (else 0,
+ * y = 0); eq_tol >= 2^-18 as for elbm_alpha_eval */
+elbm_status elbm_alpha_harvest(const float *d, long long n, double eq_tol, float *X, float *y, int *keep,
+                               void *stream);
+/* o[i] = network output for sample i: ELBM_MLP_FP32 (training arithmetic,
+ * CUDA cores) or ELBM_MLP_BF16_TC (BF16 operands and FP32 accumulation on
+ * the tensor cores, as the learned proposal runs) */
+elbm_status elbm_mlp_forward(const float *X, long long n, const float *theta, int arith, float *o, void *stream);
+/* floats of workspace elbm_mlp_grad / elbm_mlp_train need for a batch */
+long long elbm_mlp_workspace_floats(long long batch);
+/* gradient of the mean squared error mean_i (o(X_i) - y_i)^2 over all n
+ * samples (FP32 forward and analytic backward; deterministic reduction):
+ * grad out [ELBM_MLP_NPARAM], loss out [1] or NULL, work of
+ * elbm_mlp_workspace_floats(n) floats */
+elbm_status elbm_mlp_grad(const float *X, const float *y, long long n, const float *theta, float *grad, float *loss,
+                          float *work, void *stream);
+/* one Adam step (Kingma & Ba 2015) at step t >= 1: theta, m, v updated in place */
+elbm_status elbm_mlp_adam(float *theta, const float *grad, float *m, float *v, int t, float lr, float beta1,
+                          float beta2, float eps, void *stream);
+/* `steps` minibatch Adam steps (beta 0.9 / 0.999, eps 1e-8), steps t0+1 ..
+ * t0+steps; minibatch k draws `batch` samples with replacement, sample i at
+ * splitmix64(seed + (t0 + k) * batch + i) mod n (seed != 0); loss_hist out
+ * [steps] (minibatch MSE before each step) or NULL; work of
+ * elbm_mlp_workspace_floats(batch) floats */
+elbm_status elbm_mlp_train(const float *X, const float *y, long long n, float *theta, float *m, float *v, int t0,
+                           int steps, long long batch, float lr, unsigned long long seed, float *loss_hist, float *work,
+                           void *stream);
 
 /* Allocation-free density and mass of a population array. The paper has no
  * counterpart: this serves callers that may not allocate device memory

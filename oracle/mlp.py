@@ -16,8 +16,15 @@ fallback) keeps the result the method's root. What this module fixes:
 * the network o(X) = W3 . gelu(W2 gelu(W1 X + b1) + b2) + b3, 20 -> 64 ->
   64 -> 1, gelu the tanh form of Hendrycks & Gimpel (2016),
   gelu(z) = z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)));
-* the proposal alpha = 2 + S o(X), so the regression target of a site with
-  root alpha* is o* = (alpha* - 2)/S;
+* the moment-series start alpha_c: the root of the cubic truncation
+  h(a)/a ~ h'(0) + a M2/2 - a^2 M3/6 + a^3 M4/12 (M_k = sum_p f_p x_p^k; the
+  expansion of phi(a x) = (a x)^2/2 - (a x)^3/6 + (a x)^4/12 - ...), reached by
+  three Newton steps from -2 h'(0)/M2 (a step is kept only inside (0, 8));
+  its error is O(S^3);
+* the proposal alpha = alpha_c + S^3 o(X) where S >= 2^-5 (below, the
+  correction is under the FP32 resolution of alpha_c and the proposal is
+  alpha_c), so the regression target of a site with root alpha* is
+  o* = (alpha* - alpha_c)/S^3;
 * loss = mean over the batch of (o - o*)^2;
 * Adam (Kingma & Ba 2015, Algorithm 1) with bias correction.
 
@@ -126,8 +133,32 @@ def adam(theta, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
-def proposal(theta, f, delta):
-    """alpha proposed for each site: 2 + S o(X)."""
+def series_start(f, delta, h0):
+    """alpha_c of each site (f, Delta (19, n); h0 = h'(0) (n,))."""
+    x = delta / f
+    M2 = np.sum(f * x ** 2, axis=0)
+    M3 = np.sum(f * x ** 3, axis=0)
+    M4 = np.sum(f * x ** 4, axis=0)
+    a = -2.0 * h0 / M2
+    for _ in range(3):
+        g = h0 + a * (0.5 * M2 + a * (-M3 / 6.0 + a * (M4 / 12.0)))
+        gp = 0.5 * M2 + a * (-M3 / 3.0 + a * (M4 / 4.0))
+        an = a - g / gp
+        a = np.where((an > 0) & (an < 8), an, a)
+    return a
+
+
+S_MIN = 2.0 ** -5
+
+
+def proposal(theta, f, delta, h0):
+    """alpha proposed for each site: alpha_c + S^3 o(X) where S >= S_MIN."""
     X, S = features(f, delta)
     o, _ = forward(theta, X)
-    return 2.0 + S * o
+    return series_start(f, delta, h0) + np.where(S >= S_MIN, S ** 3 * o, 0.0)
+
+
+def target(f, delta, h0, alpha_root):
+    """Regression target o* = (alpha* - alpha_c)/S^3."""
+    _, S = features(f, delta)
+    return (alpha_root - series_start(f, delta, h0)) / S ** 3

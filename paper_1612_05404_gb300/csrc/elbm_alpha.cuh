@@ -23,6 +23,7 @@ struct AlphaOutF {
     float herr;     // |h(alpha)| / rho: evaluated, or the FP32 rounding bound
     int status;     // 0 root, 1 near-equilibrium shortcut, 2 no root, 3 clipped, 4 guard failed
     int guarded;    // the float-float guard ran for this site
+    int iters;      // FP32 evaluations of h this lane used before it converged
 };
 
 // ---------------------------------------------------------------------------
@@ -236,7 +237,8 @@ static __device__ __noinline__ float4 alpha_guard(const float *f, const float *d
 // rho) - 1 (sum D by TwoSum), f_p the FP32 populations. Start from the root of the moment expansion
 // h(a)/a ~ h'(0) + a M2/2 - a^2 M3/6 + a^3 M4/12 (M_k = sum f x^k), then
 // safeguarded Newton on the exact h (at most 12 steps; one or two near
-// equilibrium). A lane has converged when h is exactly 0, or |h| is at the
+// equilibrium). A start a_start > 0 inside the bracket (a learned proposal)
+// replaces the series start. A lane has converged when h is exactly 0, or |h| is at the
 // FP32 noise floor of its terms after a step below 1e-3 alpha, or the Newton
 // step is below 1e-6 alpha; converged lanes keep their alpha while the rest of
 // the warp iterates, and the warp leaves together.
@@ -250,12 +252,19 @@ static __device__ __noinline__ float4 alpha_guard(const float *f, const float *d
 // after its Newton step. Without the guard the
 // H-error reported is |h| + bound.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ AlphaOutF alpha_fp32(const float *f, const float *d, const float *fdev,
-                                                float rho, float drho, float eq_tol, bool guard)
+struct AlphaSetupF {
+    float x[Q];      // Delta_p / f_p
+    float a0;        // h'(0)
+    float tla;       // sum |Delta_p ln(1 + z_p)| (rounding bound of h'(0))
+    float amax;      // positivity bound min over Delta_p < 0 of -f_p/Delta_p
+    float ac;        // the moment-series start
+    float S;         // max |x_p|
+    int status;      // 0: solve; 1 near-equilibrium shortcut; 2 no root (h'(0) >= 0)
+};
+
+__device__ __forceinline__ void alpha_fp32_setup(const float *f, const float *d, const float *fdev, float rho,
+                                                 float drho, float eq_tol, AlphaSetupF &st)
 {
-    AlphaOutF o;
-    o.alpha = 2.f; o.alpha_lo = 0.f; o.herr = 0.f; o.status = 0; o.guarded = 0;
-    float x[Q];
     float maxabs = 0.f, xneg = 0.f;
     float s = 0.f, c = 0.f;
     float tl0 = 0.f, tl1 = 0.f, tla = 0.f;
@@ -264,9 +273,10 @@ __device__ __forceinline__ AlphaOutF alpha_fp32(const float *f, const float *d, 
     const float irho = 1.f / rho;
 #pragma unroll
     for (int p = 0; p < Q; p++) {
-        x[p] = __fdividef(d[p], f[p]);
-        maxabs = fmaxf(maxabs, fabsf(x[p]));
-        xneg = fminf(xneg, x[p]);
+        const float xp = __fdividef(d[p], f[p]);
+        st.x[p] = xp;
+        maxabs = fmaxf(maxabs, fabsf(xp));
+        xneg = fminf(xneg, xp);
         float t = s + d[p];
         float bp = t - s;
         c += (s - (t - bp)) + (d[p] - bp);
@@ -288,15 +298,17 @@ __device__ __forceinline__ AlphaOutF alpha_fp32(const float *f, const float *d, 
         const float dl = d[p] * l_f32(z);
         if (p & 1) tl1 += dl; else tl0 += dl;
         tla += fabsf(dl);
-        const float fx2 = f[p] * x[p] * x[p];
+        const float fx2 = f[p] * xp * xp;
         M2 += fx2;
-        M3 += fx2 * x[p];
-        M4 += fx2 * x[p] * x[p];
+        M3 += fx2 * xp;
+        M4 += fx2 * xp * xp;
     }
     const float a0 = (1.f + lr) * (s + c) + (tl0 + tl1);
-    if (!(maxabs >= eq_tol)) { o.status = 1; return o; }
-    if (a0 >= 0.f) { o.status = 2; return o; }
-    const float amax = xneg < 0.f ? -1.f / xneg : 1e30f;
+    st.a0 = a0;
+    st.tla = tla;
+    st.S = maxabs;
+    st.status = !(maxabs >= eq_tol) ? 1 : (a0 >= 0.f ? 2 : 0);
+    st.amax = xneg < 0.f ? -1.f / xneg : 1e30f;
     // start: root of a0 + a M2/2 - a^2 M3/6 + a^3 M4/12, Newton from -2 a0/M2
     float a = -2.f * a0 / M2;
     for (int it = 0; it < 3; it++) {
@@ -305,27 +317,51 @@ __device__ __forceinline__ AlphaOutF alpha_fp32(const float *f, const float *d, 
         float an = a - gg / gp;
         if (an > 0.f && an < 8.f) a = an;
     }
+    st.ac = a;
+}
+
+// Newton from a_start (a proposal) if it lies inside (0, amax), else from the
+// series start. A lane has converged when h is exactly 0; or |h| is at the
+// FP32 noise floor of its terms after a step below 1e-3 alpha; or the Newton
+// step d predicts an error after it, h''/(2|h'|) d^2 (quadratic convergence,
+// h'' = sum f x^2/(1 + a x)), below 2^-25 alpha; or the step is below 1e-6
+// alpha. Converged lanes keep their alpha while the rest of the warp iterates;
+// the warp leaves together. The residual carried to the guard test is the
+// evaluated |h| or, after an accepted step, the predicted h''/2 d^2.
+__device__ __forceinline__ AlphaOutF alpha_fp32_solve(const float *f, const float *d, float rho,
+                                                      const AlphaSetupF &st, bool guard, float a_start)
+{
+    AlphaOutF o;
+    o.alpha = 2.f; o.alpha_lo = 0.f; o.herr = 0.f; o.status = st.status; o.guarded = 0; o.iters = 0;
+    if (st.status != 0) return o;
+    const float a0 = st.a0, amax = st.amax, irho = 1.f / rho;
     float lo = 0.f, hi = amax * (1.f - 1e-6f);
+    float a = st.ac;
+    if (a_start > lo && a_start < hi) a = a_start;
     if (!(a > lo && a < hi)) a = fminf(2.f, 0.5f * hi);
-    float h = 0.f, hhl = 0.f, hpl = 0.f;
+    float hres = 0.f, hhl = 0.f, hpl = 0.f;
     float step_prev = 1e30f;
     bool conv = false;
     for (int it = 0; it < 12; it++) {
         // four partial sums: shorter dependency chains than one running sum
-        float hq[4] = {0.f, 0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
+        float hq[4] = {0.f, 0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, kq[2] = {0.f, 0.f};
 #pragma unroll
         for (int p = 0; p < Q; p++) {
             float l, ph;
-            const float y = a * x[p];
+            const float y = a * st.x[p];
             if (1.f + y <= 0.f) { ph = -y; l = -88.f; }
             else lphi_f32(y, &l, &ph);
             hq[p & 3] = fmaf(f[p], ph, hq[p & 3]);
             gq[p & 3] = fmaf(d[p], l, gq[p & 3]);
+            kq[p & 1] = fmaf(d[p] * st.x[p], __fdividef(1.f, 1.f + y), kq[p & 1]);
         }
         const float hh = (hq[0] + hq[1]) + (hq[2] + hq[3]);
         const float g = (gq[0] + gq[1]) + (gq[2] + gq[3]);
+        const float hpp = kq[0] + kq[1];
         if (!conv) {
-            h = hh + a * a0;
+            o.iters++;
+            const float h = hh + a * a0;
+            hres = fabsf(h);
             hhl = hh;
             hpl = g + a0;
             if (h == 0.f || (step_prev <= 1e-3f * a && fabsf(h) <= 5e-7f * (hh + fabsf(a * a0)))) {
@@ -333,30 +369,45 @@ __device__ __forceinline__ AlphaOutF alpha_fp32(const float *f, const float *d, 
             } else {
                 if (h < 0.f) lo = a; else hi = a;
                 float an = a - h / hpl;
-                if (!(an > lo && an < hi)) an = 0.5f * (lo + hi);
-                step_prev = fabsf(an - a);
+                const bool newton = an > lo && an < hi;
+                if (!newton) an = 0.5f * (lo + hi);
+                const float step = fabsf(an - a);
+                step_prev = step;
                 a = an;
-                conv = step_prev <= 1e-6f * a;
+                const float pred = 0.5f * hpp * step * step;  // |h| after the step, to leading order
+                if (newton && (pred <= 0x1p-25f * a * fabsf(hpl) || step <= 1e-6f * a)) {
+                    conv = true;
+                    hres = pred;
+                }
             }
         }
         if (__all_sync(__activemask(), conv)) break;
     }
     o.alpha = a;
     o.status = a >= amax * (1.f - 2e-6f) ? 3 : 0;
-    const float bound = 0x1p-21f * (hhl + a * (fabsf(a0) + tla)) + 0x1p-23f * a * fabsf(hpl);
-    o.herr = (fabsf(h) + bound) * irho;
+    const float bound = 0x1p-21f * (hhl + a * (fabsf(a0) + st.tla)) + 0x1p-23f * a * fabsf(hpl);
+    o.herr = (hres + bound) * irho;
     if (!guard || o.status == 3) return o;
     const float tol = 1e-10f * rho;
-    const bool need = !(fabsf(h) + bound <= 0.5f * tol);
+    const bool need = !(hres + bound <= 0.5f * tol);
     if (need) {
         o.guarded = 1;
         const float4 gr = alpha_guard(f, d, rho, a);
         o.alpha = gr.x;
         o.alpha_lo = gr.y;
         o.herr = gr.z;
-        if (gr.w == 0.f) { o.status = 4; o.herr = fabsf(h) * irho; }
+        if (gr.w == 0.f) { o.status = 4; o.herr = hres * irho; }
     }
     return o;
+}
+
+__device__ __forceinline__ AlphaOutF alpha_fp32(const float *f, const float *d, const float *fdev,
+                                                float rho, float drho, float eq_tol, bool guard,
+                                                float a_start = -1.f)
+{
+    AlphaSetupF st;
+    alpha_fp32_setup(f, d, fdev, rho, drho, eq_tol, st);
+    return alpha_fp32_solve(f, d, rho, st, guard, a_start);
 }
 
 }  // namespace elbm

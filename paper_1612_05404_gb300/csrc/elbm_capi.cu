@@ -54,6 +54,17 @@ struct elbm_handle {
 
 namespace {
 
+// BF16 image of the learned proposal's network (shared-memory layout of
+// elbm_mlp.cuh) from the caller's FP32 parameters, made once at elbm_init
+__global__ void k_mlp_image(const float *th, MlpSmem *img)
+{
+    __shared__ MlpSmem sm;
+    mlp_load_smem(th, sm);
+    const uint4 *src = (const uint4 *)&sm;
+    uint4 *dst = (uint4 *)img;
+    for (int i = threadIdx.x; i < (int)(sizeof(MlpSmem) / 16); i += blockDim.x) dst[i] = src[i];
+}
+
 enum { FIN_CHARGE_AB = 0, FIN_CHARGE_Q = 1, FIN_RESID_PRE = 2, FIN_PHI = 3, FIN_DIAG = 4, FIN_RESID_BODY = 5 };
 
 // Control of the Poisson loop, evaluated on the device after each
@@ -189,7 +200,11 @@ int validate(const elbm_params *p, const elbm_init_fields *in, int n_instances)
     if (p->phi_axis < 0 || p->phi_axis > 2) return 1;
     if (p->charge_model < ELBM_CHARGE_NONE || p->charge_model > ELBM_CHARGE_TRANSPORT) return 1;
     if (p->force_el != ELBM_FEL_QE) return 1;
-    if (p->alpha_mode != ELBM_ALPHA_ENTROPIC && p->alpha_mode != ELBM_ALPHA_BGK) return 1;
+    if (p->alpha_mode < ELBM_ALPHA_ENTROPIC || p->alpha_mode > ELBM_ALPHA_LEARNED) return 1;
+    // the learned proposal starts the FP32 Newton iteration of FP32/BF16 storage
+    if (p->alpha_mode == ELBM_ALPHA_LEARNED &&
+        (!p->mlp || p->precision == ELBM_PREC_FP64 || p->alpha_precision == ELBM_APREC_FP64))
+        return 1;
     if (p->precision < ELBM_PREC_FP64 || p->precision > ELBM_PREC_BF16) return 1;
     if (p->alpha_precision < ELBM_APREC_FP64 || p->alpha_precision > ELBM_APREC_FP32_FAST) return 1;
     if (!(p->nu0 > 0.0) || !(p->nu_inf > 0.0) || !(p->rho0 > 0.0)) return 1;
@@ -216,7 +231,8 @@ void free_bufs(elbm_handle *h)
 {
     void *ptrs[] = {h->b.fA, h->b.fB, h->b.gA, h->b.gB, h->b.rho, h->b.q, h->b.phi, h->b.ux,
                     h->b.uy, h->b.uz, h->b.alpha, h->b.nu, h->b.mask, h->b.nh, h->b.ab,
-                    h->b.part, h->b.scal, h->b.scalf, h->b.diag, h->b.colres, h->b.ticket};
+                    h->b.part, h->b.scal, h->b.scalf, h->b.diag, h->b.colres, h->b.ticket,
+                    const_cast<void *>(h->b.mlpimg)};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (h->pin) cudaFreeHost(h->pin);
@@ -361,6 +377,10 @@ elbm_status step_host(elbm_handle *h, bool diag)
         h->launches += enq_shift(h, b, s);
     }
     if (prof) cudaEventRecord(h->ev[2], s);
+    if (h->ph.alpha_mode == ELBM_ALPHA_LEARNED) {
+        h->ops.alpha_mlp(h->g, h->ph, b, h->L, s);
+        h->launches += 1;
+    }
     h->ops.collide(h->g, h->ph, b, diag ? 1 : 0, h->L, s);
     h->launches += 1;
     if (prof) cudaEventRecord(h->ev[3], s);
@@ -415,6 +435,10 @@ bool capture_step(elbm_handle *h, int parity, cudaGraphExec_t *out, int sections
         n_post += enq_shift(h, b, s);
     }
     if (sections & 4) {
+        if (h->ph.alpha_mode == ELBM_ALPHA_LEARNED) {
+            h->ops.alpha_mlp(h->g, h->ph, b, h->L, s);
+            n_post += 1;
+        }
         h->ops.collide(h->g, h->ph, b, 1, h->L, s);
         n_post += 1 + fin(h, b, s, D_NPART, FIN_DIAG);
     }
@@ -608,6 +632,17 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
         alloc(&b.uz, (size_t)N * h->sc_bytes);
         alloc(&b.alpha, (size_t)N * h->sc_bytes);
         alloc(&b.nu, (size_t)N * h->sc_bytes);
+    }
+    if (p->alpha_mode == ELBM_ALPHA_LEARNED) {
+        // the network output o per site passes through the alpha plane
+        if (!b.alpha) alloc(&b.alpha, (size_t)N * h->sc_bytes);
+        void *img = nullptr;
+        alloc(&img, sizeof(MlpSmem));
+        b.mlpimg = img;
+        if (ok) {
+            k_mlp_image<<<1, 128, 0, h->s>>>(p->mlp, (MlpSmem *)img);
+            ok = cuda_ok(cudaGetLastError());
+        }
     }
     if (g.has_mask) alloc((void **)&b.mask, (size_t)N);
     if (p->charge_model == ELBM_CHARGE_CONSERVED || p->charge_model == ELBM_CHARGE_XI) {

@@ -51,6 +51,7 @@ struct Bufs {
     double *colres;                   // per-column results of the finalize kernel
     unsigned int *ticket;             // last-block-done counter of the finalize kernel
     double *diag;                     // ELBM_NDIAG diagnostics
+    const void *mlpimg;               // learned alpha: BF16 shared-memory image of the network
 };
 
 struct Launch {
@@ -72,6 +73,8 @@ struct Ops {
     // stage 0: block sums of phi over non-solid nodes; stage 1: subtract S_PHIMEAN
     void (*phi_mean)(const Geom &, const Phys &, const Bufs &, int stage, const Launch &, cudaStream_t);
     void (*collide)(const Geom &, const Phys &, const Bufs &, int diag, const Launch &, cudaStream_t);
+    // learned alpha: network output o per site into the alpha plane (NULL for FP64)
+    void (*alpha_mlp)(const Geom &, const Phys &, const Bufs &, const Launch &, cudaStream_t);
     void (*export_pop)(const Geom &, const Bufs &, double *out, const Launch &, cudaStream_t);
     void (*export_gpop)(const Geom &, const Bufs &, double *out, const Launch &, cudaStream_t);
     void (*export_plane)(const void *plane, double *out, long long n, cudaStream_t);

@@ -14,6 +14,7 @@
 #pragma once
 
 #include "elbm_internal.h"
+#include "elbm_mlp.cuh"
 
 namespace elbm {
 
@@ -621,8 +622,8 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
         // Eq. (entropic)
         ct alpha = ct(2);
         float a_herr = 0.f;
-        int a_status = 0, a_guard = 0;
-        if (ph.alpha_mode == ELBM_ALPHA_ENTROPIC) {
+        int a_status = 0, a_guard = 0, a_lfall = 0;
+        if (ph.alpha_mode != ELBM_ALPHA_BGK) {
             if (sizeof(ct) == 8 || AP == ELBM_APREC_FP64) {
                 double fd[Q], dd[Q];
 #pragma unroll
@@ -642,12 +643,19 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
                     dd[p] = float(D[p]);
                     fv[p] = float(f[p]);
                 }
-                AlphaOutF ao = alpha_fp32(ff, dd, fv, float(r), float(drho), ph.cf.eq_tol,
-                                          AP == ELBM_APREC_FP32);
+                AlphaSetupF ast;
+                alpha_fp32_setup(ff, dd, fv, float(r), float(drho), ph.cf.eq_tol, ast);
+                // learned proposal: alpha_c + S^3 o, o from the network pass
+                float a_start = -1.f;
+                const bool learned = ph.alpha_mode == ELBM_ALPHA_LEARNED;
+                if (learned && ast.S >= 0x1p-5f)
+                    a_start = ast.ac + ast.S * ast.S * ast.S * float(((const sc *)b.alpha)[s]);
+                AlphaOutF ao = alpha_fp32_solve(ff, dd, float(r), ast, AP == ELBM_APREC_FP32, a_start);
                 alpha = ct(ao.alpha);
                 a_herr = ao.herr;
                 a_status = ao.status;
                 a_guard = ao.guarded;
+                a_lfall = learned && ao.status == 0 && ao.iters > 1;
             }
         }
 
@@ -735,6 +743,7 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
             else if (a_status == 3) dcl = 1;
             else if (a_status == 4) dgf = 1;
             dgd = a_guard;
+            dlf = a_lfall;
             dherr = a_herr;
             float um = float(sqrt(upx * upx + upy * upy + upz * upz));
             dumax = um;
@@ -788,6 +797,72 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
             out[D_AMIN * nbk] = a0; out[D_AMAX * nbk] = a1; out[D_HERR * nbk] = h; out[D_UMAX * nbk] = u;
         }
     }
+}
+
+// ===========================================================================
+// Learned alpha: the network output o of every fluid site, from the same
+// pulled populations, Delta and x_p = Delta_p / f_p as the collision computes
+// (FP32 arithmetic), into the alpha plane; BF16 tensor-core inference per warp
+// (elbm_mlp.cuh). The block copies the handle's BF16 image of the network to
+// shared memory. Every lane of a warp takes part in the warp's network pass.
+// ===========================================================================
+template <int PR>
+__global__ void __launch_bounds__(128) k_alpha_mlp(Geom g, Phys ph, Bufs b)
+{
+    typedef Tr<PR> T;
+    typedef typename T::ct ct;
+    typedef typename T::sc sc;
+    __shared__ MlpSmem sm;
+    __shared__ __align__(16) __nv_bfloat16 xs[4][32 * MLP_XS];
+    __shared__ float os[4][32];
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    {
+        const uint4 *src = (const uint4 *)b.mlpimg;
+        uint4 *dst = (uint4 *)&sm;
+        for (int i = tid; i < (int)(sizeof(MlpSmem) / 16); i += blockDim.x * blockDim.y) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int w = tid >> 5, lane = tid & 31;
+    int x, y, z;
+    bool inb;
+    ll s;
+    site_xyz(g, x, y, z, inb, s);
+    const bool active = inb && (!b.mask || b.mask[s] == ELBM_NODE_FLUID);
+    __nv_bfloat16 *row = xs[w] + lane * MLP_XS;
+    if (active) {
+        Nbr n;
+        nbr_init(n, g, x, y, z, s);
+        float f[Q];
+#pragma unroll
+        for (int p = 0; p < Q; p++) f[p] = float(gather_pop<PR>(g, b.mask, b.fA, n, p));
+        float rs = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+        for (int p = 0; p < Q; p++) {
+            rs += f[p];
+            jx += float(cx(p)) * f[p];
+            jy += float(cy(p)) * f[p];
+            jz += float(cz(p)) * f[p];
+        }
+        const float r = 1.f + rs, drho = rs;
+        const float ir = 1.f / r;
+        const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
+        const float usq = ux * ux + uy * uy + uz * uz;
+        float xv[Q];
+        float S = 0.f;
+#pragma unroll
+        for (int p = 0; p < Q; p++) {
+            const float D = float(wq(p)) * (drho + r * Ppoly<float>(p, ux, uy, uz, usq)) - f[p];
+            xv[p] = __fdividef(D, float(wq(p)) + f[p]);
+            S = fmaxf(S, fabsf(xv[p]));
+        }
+        mlp_site_features(xv, S > 0.f ? S : 1.f, row);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 32; c += 2) *reinterpret_cast<unsigned *>(row + c) = 0u;
+    }
+    __syncwarp();
+    mlp_warp_bf16(sm, xs[w], os[w]);
+    if (active) ((sc *)b.alpha)[s] = sc(os[w][lane]);
 }
 
 // f(r, t) for the caller: the pull of every fluid site, 0 elsewhere
@@ -884,6 +959,10 @@ struct Launchers {
         else
             k_collide<PR, ELBM_APREC_FP32><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
     }
+    static void alpha_mlp(const Geom &g, const Phys &ph, const Bufs &b, const Launch &L, cudaStream_t s)
+    {
+        if (PR != ELBM_PREC_FP64) k_alpha_mlp<PR><<<L.grid, L.block, 0, s>>>(g, ph, b);
+    }
     static void export_pop(const Geom &g, const Bufs &b, double *out, const Launch &L, cudaStream_t s)
     {
         k_export_pop<PR><<<L.grid, L.block, 0, s>>>(g, b, out);
@@ -906,6 +985,7 @@ struct Launchers {
         o.resid = resid;
         o.phi_mean = phi_mean;
         o.collide = collide;
+        o.alpha_mlp = PR == ELBM_PREC_FP64 ? nullptr : alpha_mlp;
         o.export_pop = export_pop;
         o.export_gpop = export_gpop;
         o.export_plane = export_plane;

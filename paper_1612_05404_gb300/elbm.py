@@ -25,14 +25,17 @@ DIAG_NAMES = [
 ]
 EXPORTS = ["elbm_init", "elbm_step", "elbm_fields", "elbm_fields_size", "elbm_free",
            "elbm_strerror", "elbm_velocity_set", "elbm_pass_times", "elbm_density_noalloc",
-           "elbm_alpha_eval"]
+           "elbm_alpha_eval", "elbm_alpha_features", "elbm_alpha_harvest", "elbm_mlp_forward",
+           "elbm_mlp_workspace_floats", "elbm_mlp_grad", "elbm_mlp_adam", "elbm_mlp_train"]
+MLP_NIN = 20
+MLP_NPARAM = 5569
 NOALLOC_MAX_SITES = 16384 * 1024
 
 _FACE = {"periodic": 0, "wall": 1}
 _PHI = {"periodic": 0, "dirichlet": 1, "neumann": 2}
 _CHARGE = {"none": 0, "conserved": 1, "xi": 2, "transport": 3}
 _FEL = {"qe": 0, "full": 1}
-_ALPHA = {"entropic": 0, "bgk": 1}
+_ALPHA = {"entropic": 0, "bgk": 1, "learned": 2}
 _PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
 _APREC = {"fp64": 0, "fp32": 1, "fp32_fast": 2}
 
@@ -64,6 +67,7 @@ class Params(ctypes.Structure):
         ("sor_omega", ctypes.c_double), ("poisson_tol", ctypes.c_double),
         ("alpha_eq_tol", ctypes.c_double), ("rho_in", ctypes.c_double), ("rho_out", ctypes.c_double),
         ("cuda_stream", ctypes.c_void_p),
+        ("mlp", ctypes.c_void_p),
     ]
 
 
@@ -106,6 +110,19 @@ def lib():
         L.elbm_density_noalloc.restype = ctypes.c_int
         L.elbm_alpha_eval.argtypes = [vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_double, vp, vp, vp, vp, vp, vp]
         L.elbm_alpha_eval.restype = ctypes.c_int
+        ll, f = ctypes.c_longlong, ctypes.c_float
+        L.elbm_alpha_features.argtypes = [vp, ll, vp, vp, vp]
+        L.elbm_alpha_harvest.argtypes = [vp, ll, ctypes.c_double, vp, vp, vp, vp]
+        L.elbm_mlp_forward.argtypes = [vp, ll, vp, ctypes.c_int, vp, vp]
+        L.elbm_mlp_workspace_floats.argtypes = [ll]
+        L.elbm_mlp_workspace_floats.restype = ll
+        L.elbm_mlp_grad.argtypes = [vp, vp, ll, vp, vp, vp, vp, vp]
+        L.elbm_mlp_adam.argtypes = [vp, vp, vp, vp, ctypes.c_int, f, f, f, f, vp]
+        L.elbm_mlp_train.argtypes = [vp, vp, ll, vp, vp, vp, ctypes.c_int, ctypes.c_int, ll, f,
+                                     ctypes.c_ulonglong, vp, vp, vp]
+        for name in ("elbm_alpha_features", "elbm_alpha_harvest", "elbm_mlp_forward", "elbm_mlp_grad",
+                     "elbm_mlp_adam", "elbm_mlp_train"):
+            getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -156,6 +173,8 @@ def make_params(cfg: dict, stream=None) -> Params:
     P.alpha_eq_tol = cfg["alpha_eq_tol"]
     P.rho_in, P.rho_out = cfg["rho_in"], cfg["rho_out"]
     P.cuda_stream = stream
+    mlp = cfg.get("mlp")
+    P.mlp = None if mlp is None else mlp.data_ptr()
     return P
 
 
@@ -204,6 +223,89 @@ def alpha_eval(d, aprec="fp32", eq_tol=1e-5, mlp=None, with_delta=False, stream=
     if rc != 0:
         raise ElbmError(rc)
     return alpha, herr, status, delta
+
+
+def _p(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise ElbmError(rc, what)
+
+
+def _cuda_f32(t, shape0=None):
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA float32 tensor")
+    if shape0 is not None and t.shape[0] != shape0:
+        raise ValueError(f"expected leading dimension {shape0}")
+    return t
+
+
+def alpha_features(d, stream=None):
+    """Features X (20, n) and S (n) of sites given as FP32 deviations (19, n)."""
+    import torch
+    _cuda_f32(d, 19)
+    n = d.shape[1]
+    X = torch.empty((MLP_NIN, n), dtype=torch.float32, device=d.device)
+    S = torch.empty(n, dtype=torch.float32, device=d.device)
+    _check(lib().elbm_alpha_features(_p(d), n, _p(X), _p(S), stream or _cur_stream()), "elbm_alpha_features")
+    return X, S
+
+
+def alpha_harvest(d, eq_tol=1e-5, stream=None):
+    """Training pairs (X (20, n), y (n), keep (n) int32) of FP32 deviation sites."""
+    import torch
+    _cuda_f32(d, 19)
+    n = d.shape[1]
+    X = torch.empty((MLP_NIN, n), dtype=torch.float32, device=d.device)
+    y = torch.empty(n, dtype=torch.float32, device=d.device)
+    keep = torch.empty(n, dtype=torch.int32, device=d.device)
+    _check(lib().elbm_alpha_harvest(_p(d), n, float(eq_tol), _p(X), _p(y), _p(keep), stream or _cur_stream()),
+           "elbm_alpha_harvest")
+    return X, y, keep
+
+
+def mlp_forward(X, theta, arith="bf16_tc", stream=None):
+    import torch
+    _cuda_f32(X, MLP_NIN)
+    _cuda_f32(theta)
+    o = torch.empty(X.shape[1], dtype=torch.float32, device=X.device)
+    _check(lib().elbm_mlp_forward(_p(X), X.shape[1], _p(theta), {"fp32": 0, "bf16_tc": 1}[arith], _p(o),
+                                  stream or _cur_stream()), "elbm_mlp_forward")
+    return o
+
+
+def mlp_grad(X, y, theta, stream=None):
+    """(grad (NPARAM,), loss (1,)) of the mean squared error over all samples."""
+    import torch
+    n = X.shape[1]
+    g = torch.empty(MLP_NPARAM, dtype=torch.float32, device=X.device)
+    L = torch.empty(1, dtype=torch.float32, device=X.device)
+    work = torch.empty(int(lib().elbm_mlp_workspace_floats(n)), dtype=torch.float32, device=X.device)
+    _check(lib().elbm_mlp_grad(_p(_cuda_f32(X, MLP_NIN)), _p(_cuda_f32(y)), n, _p(_cuda_f32(theta)), _p(g), _p(L),
+                               _p(work), stream or _cur_stream()), "elbm_mlp_grad")
+    return g, L
+
+
+def mlp_adam(theta, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().elbm_mlp_adam(_p(theta), _p(g), _p(m), _p(v), int(t), float(lr), float(beta1), float(beta2),
+                               float(eps), stream or _cur_stream()), "elbm_mlp_adam")
+
+
+def mlp_train(X, y, theta, m, v, t0, steps, batch, lr, seed, stream=None):
+    """`steps` Adam minibatch steps in place on theta, m, v; returns the
+    per-step minibatch losses (CUDA tensor)."""
+    import torch
+    n = X.shape[1]
+    hist = torch.empty(max(steps, 1), dtype=torch.float32, device=X.device)
+    work = torch.empty(int(lib().elbm_mlp_workspace_floats(batch)) + MLP_NPARAM, dtype=torch.float32,
+                       device=X.device)
+    _check(lib().elbm_mlp_train(_p(_cuda_f32(X, MLP_NIN)), _p(_cuda_f32(y)), n, _p(theta), _p(m), _p(v), int(t0),
+                                int(steps), int(batch), float(lr), int(seed), _p(hist), _p(work),
+                                stream or _cur_stream()), "elbm_mlp_train")
+    return hist[:steps]
 
 
 class Sim:

@@ -26,7 +26,7 @@ def L():
 def test_exports_every_declared_symbol(L):
     hdr = open(os.path.join(ROOT, "include", "elbm.h")).read()
     hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
-    declared = set(re.findall(r"^\s*(?:const\s+)?\w+\s*\**\s*(elbm_[a-z_]+)\s*\(", hdr, re.M))
+    declared = set(re.findall(r"^\s*(?:const\s+)?(?:\w+\s+)*\w+\s*\**\s*(elbm_[a-z_0-9]+)\s*\(", hdr, re.M))
     assert declared >= set(elbm.EXPORTS)
     out = subprocess.run(["nm", "-D", "--defined-only", elbm.LIB_PATH], capture_output=True,
                          text=True, check=True).stdout
@@ -113,4 +113,26 @@ def test_alpha_eval_argument_checks(L):
     assert L.elbm_alpha_eval(p, 5, 7, 1e-5, None, p, None, None, None, None) == elbm.E_INVAL
     assert L.elbm_alpha_eval(p, 5, 1, 1e-9, None, p, None, None, None, None) == elbm.E_INVAL
     assert L.elbm_alpha_eval(p, 5, 1, -1.0, None, p, None, None, None, None) == elbm.E_INVAL
-    assert L.elbm_alpha_eval(p, 5, 1, 1e-5, p, p, None, None, None, None) == elbm.E_INVAL
+    assert L.elbm_alpha_eval(p, 5, 0, 1e-5, p, p, None, None, None, None) == elbm.E_INVAL  # learned needs FP32
+
+
+def test_mlp_entry_points_argument_checks(L):
+    """Validation before any launch (runs without a GPU; no call below reaches
+    a kernel)."""
+    import ctypes
+    p = ctypes.c_void_p(16)
+    assert L.elbm_mlp_workspace_floats(0) == 0
+    assert L.elbm_mlp_workspace_floats(128) == 2 * 5570
+    assert L.elbm_alpha_features(None, 0, None, None, None) == 0
+    assert L.elbm_alpha_features(p, -2, p, None, None) == elbm.E_INVAL
+    assert L.elbm_alpha_features(p, 3, None, None, None) == elbm.E_INVAL
+    assert L.elbm_alpha_harvest(p, 3, 1e-9, p, p, p, None) == elbm.E_INVAL
+    assert L.elbm_alpha_harvest(p, 3, 1e-5, p, p, None, None) == elbm.E_INVAL
+    assert L.elbm_mlp_forward(p, 3, p, 5, p, None) == elbm.E_INVAL
+    assert L.elbm_mlp_forward(p, 3, None, 1, p, None) == elbm.E_INVAL
+    assert L.elbm_mlp_grad(p, p, 0, p, p, None, p, None) == elbm.E_INVAL
+    assert L.elbm_mlp_grad(p, p, 4, p, p, None, None, None) == elbm.E_INVAL
+    assert L.elbm_mlp_adam(p, p, p, p, 0, 1e-3, 0.9, 0.999, 1e-8, None) == elbm.E_INVAL
+    assert L.elbm_mlp_adam(p, p, p, p, 1, 1e-3, 1.0, 0.999, 1e-8, None) == elbm.E_INVAL
+    assert L.elbm_mlp_train(p, p, 4, p, p, p, 0, 1, 8, 1e-3, 0, None, p, None) == elbm.E_INVAL
+    assert L.elbm_mlp_train(p, p, 4, p, p, p, 0, 1, 0, 1e-3, 1, None, p, None) == elbm.E_INVAL

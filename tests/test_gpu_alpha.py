@@ -44,7 +44,7 @@ def _h_err(f, D, a):
 def test_alpha_fp32_guard_meets_h_error():
     f, D, a, he, st = _run(_sites(), "fp32")
     assert not np.any(st == 4), "guard ended above 1e-10 rho"
-    root = st == 0
+    root = np.isin(st, (0, 5))  # 5: a root that took more than one FP32 evaluation
     assert root.sum() > 1000
     assert np.all(a[~root & (st != 3)] == 2.0)
     err = _h_err(f[:, root], D[:, root], a[root])
@@ -61,7 +61,7 @@ def test_alpha_fp32_guard_meets_h_error():
 
 def test_alpha_fp32_fast_bound_holds():
     f, D, a, he, st = _run(_sites(), "fp32_fast")
-    root = st == 0
+    root = np.isin(st, (0, 5))
     err = _h_err(f[:, root], D[:, root], a[root])
     # without the guard the reported value is |h| plus the FP32 rounding bound
     assert np.all(err <= he[root] * 1.0001 + 1e-15)

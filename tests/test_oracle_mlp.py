@@ -114,3 +114,29 @@ def test_hand_set_network_computes_a_known_function():
     ge = lambda z: 0.5 * z * (1.0 + math.erf(z / math.sqrt(2.0)))
     want = np.array([1.5 * ge(2 * ge(v)) + 0.1 for v in X[:, 7]])
     assert np.max(np.abs(o - want)) < 1e-2
+
+
+def test_series_start_error_is_third_order():
+    """alpha_c misses the root of Eq. (entropic) by O(S^3): the truncated
+    terms of h start at a^4 M5; checked against the oracle's Newton root."""
+    import oracle
+    from paper_1612_05404_gb300 import workloads as W
+    w = W.D3Q19_WEIGHTS
+    for amp in (0.004, 0.01, 0.03):
+        f = W.random_populations(40, amp, seed=int(amp * 1e4))
+        # Delta of a site: equilibrium at the site's own rho, u minus f
+        c, _, _ = oracle.lattice(3)
+        out = []
+        for i in range(f.shape[1]):
+            rho = f[:, i].sum()
+            u = (c.T @ f[:, i]) / rho
+            d = oracle.feq(3, rho, u) - f[:, i]
+            ar, st = oracle.alpha(3, f[:, i], d, 1e-12)
+            if st != 0:
+                continue
+            h0 = oracle.h_prime0(3, f[:, i], d)
+            ac = mlp.series_start(f[:, i:i + 1], d[:, None], np.array([h0]))[0]
+            S = np.max(np.abs(d / f[:, i]))
+            out.append(abs(ac - ar) / S ** 3)
+        assert len(out) > 20
+        assert max(out) < 2.0, (amp, max(out))
