@@ -125,6 +125,9 @@ typedef struct elbm_params {
     int graph;                   /* run each step as one CUDA graph, the Poisson loop a
                                     device-side while node (needs diag_every = 1);
                                     0: issue from the host, one sync per test */
+    int autotune;                /* 1: choose the block shape of the site kernels by
+                                    timing the collision at elbm_init (cached per
+                                    lattice size for the process); 0: fixed shape */
     double phi_lo, phi_hi;       /* potential on the ghost planes at axis coord -1 and n */
     double phi_solid;            /* potential of interior solid (conductor) nodes */
     double nu0, nu_inf, lambda, n_carreau;  /* Carreau law; n = 1 is Newtonian nu0 */
@@ -187,6 +190,23 @@ size_t elbm_fields_size(const elbm_handle *h, unsigned mask);
  * Writes min(n, 8) values; ELBM_E_STATE when profiling is off. Not part of
  * the paper's method: instrumentation for measuring the method's kernels. */
 elbm_status elbm_pass_times(const elbm_handle *h, double *out, int n);
+
+/* Batched lattices (not in the paper: an execution form). One batch handle
+ * advances n existing instance handles (each made by elbm_init, with
+ * diag_every = 1 and profile = 0) by one CUDA graph launch per step: each
+ * instance's whole step, its Poisson loop a device-side while node of its
+ * own, is a parallel branch of that graph, so instances of uneven size and
+ * uneven Poisson work run side by side.
+ *   inst   array of n distinct instance handles (not batches); the batch
+ *          keeps the pointers: free the batch before its instances, and step
+ *          the instances only through the batch while it exists (elbm_step
+ *          on the batch returns ELBM_E_STATE if one was stepped alone);
+ *   stream cudaStream_t on which elbm_step(batch) launches the graph.
+ * elbm_step(batch, k) advances every instance k steps and returns the worst
+ * status of the instances (non-finite state, Poisson non-convergence);
+ * elbm_fields and elbm_pass_times on a batch return ELBM_E_STATE (read each
+ * instance); elbm_free(batch) frees the batch only. */
+elbm_status elbm_batch_create(elbm_handle *const *inst, int n, void *stream, elbm_handle **out);
 
 /* The entropic alpha of Eq. (entropic) for n independent sites outside a
  * simulation: the root the collision step computes, for checking its H-error

@@ -7,6 +7,9 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <array>
+#include <map>
+#include <mutex>
 #include <new>
 
 #include "elbm.h"
@@ -50,6 +53,13 @@ struct elbm_handle {
     cudaEvent_t ev[5];         // pass boundaries when profiling
     double pass_ms[4];
     double prof_steps, prof_collide, prof_sweeps, launches;
+    // batch of instances (elbm_batch_create): n_sub > 0
+    int n_sub;
+    elbm_handle **sub;
+    long long *sub_step0;      // each instance's step counter when the batch was made
+    cudaGraphExec_t bexec[2];  // all instances' steps, one graph per A/B parity
+    cudaEvent_t ev_fork;
+    cudaEvent_t *ev_join;
 };
 
 namespace {
@@ -224,6 +234,7 @@ int validate(const elbm_params *p, const elbm_init_fields *in, int n_instances)
     if (p->charge_model == ELBM_CHARGE_TRANSPORT && !(p->Dq >= 0.0)) return 1;
     if (p->diag_every < 0) return 1;
     if (p->poisson_solver != ELBM_POISSON_SOR && p->poisson_solver != ELBM_POISSON_MG) return 1;
+    if (p->autotune != 0 && p->autotune != 1) return 1;
     return 0;
 }
 
@@ -392,17 +403,15 @@ elbm_status step_host(elbm_handle *h, bool diag)
 // Capture sections of one step into an executable graph for buffers of the
 // given A/B parity: bit 0 moments and charge, bit 1 the Poisson loop (a
 // device-side while node), bit 2 collision and diagnostics.
-bool capture_step(elbm_handle *h, int parity, cudaGraphExec_t *out, int sections = 7)
+// One step of h enqueued into stream s, which is being captured (the Poisson
+// loop becomes a conditional while node whose body is captured on h->cap2).
+bool enqueue_step(elbm_handle *h, int parity, cudaStream_t s, int sections, int &n_pre, int &n_body, int &n_post)
 {
     Bufs b = h->b;
     if (parity) swap_ab(b);
     const bool charged = h->p.charge_model != ELBM_CHARGE_NONE && (sections & 2);
-    cudaStream_t s = h->cap;
-    cudaGraph_t graph = nullptr;
-    if (!cuda_ok(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal))) return false;
     bool ok = true;
     cudaGraphConditionalHandle cond = 0;
-    int n_pre = 0, n_body = 0, n_post = 0;
     if (sections & 1) n_pre += enq_pre(h, b, s);
     if (charged) {
         cudaStreamCaptureStatus st;
@@ -442,6 +451,16 @@ bool capture_step(elbm_handle *h, int parity, cudaGraphExec_t *out, int sections
         h->ops.collide(h->g, h->ph, b, 1, h->L, s);
         n_post += 1 + fin(h, b, s, D_NPART, FIN_DIAG);
     }
+    return ok;
+}
+
+bool capture_step(elbm_handle *h, int parity, cudaGraphExec_t *out, int sections = 7)
+{
+    cudaStream_t s = h->cap;
+    cudaGraph_t graph = nullptr;
+    if (!cuda_ok(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal))) return false;
+    int n_pre = 0, n_body = 0, n_post = 0;
+    bool ok = enqueue_step(h, parity, s, sections, n_pre, n_body, n_post);
     ok = cuda_ok(cudaStreamEndCapture(s, &graph)) && ok;
     if (ok) ok = cuda_ok(cudaGraphInstantiate(out, graph, 0));
     if (graph) cudaGraphDestroy(graph);
@@ -452,6 +471,101 @@ bool capture_step(elbm_handle *h, int parity, cudaGraphExec_t *out, int sections
         h->n_post += n_post;
     }
     return ok;
+}
+
+// The batch's step for one A/B parity: every instance's step as a parallel
+// branch (fork from one event, join into the batch's capture stream).
+bool capture_batch(elbm_handle *B, int parity, cudaGraphExec_t *out)
+{
+    cudaStream_t s = B->cap;
+    cudaGraph_t graph = nullptr;
+    if (!cuda_ok(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal))) return false;
+    bool ok = cuda_ok(cudaEventRecord(B->ev_fork, s));
+    int n_pre = 0, n_body = 0, n_post = 0;
+    for (int i = 0; i < B->n_sub && ok; i++) {
+        elbm_handle *h = B->sub[i];
+        ok = cuda_ok(cudaStreamWaitEvent(h->cap, B->ev_fork, 0));
+        ok = ok && enqueue_step(h, parity, h->cap, 7, n_pre, n_body, n_post);
+        ok = ok && cuda_ok(cudaEventRecord(B->ev_join[i], h->cap));
+        ok = ok && cuda_ok(cudaStreamWaitEvent(s, B->ev_join[i], 0));
+    }
+    ok = cuda_ok(cudaStreamEndCapture(s, &graph)) && ok;
+    if (ok) ok = cuda_ok(cudaGraphInstantiate(out, graph, 0));
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (parity == 0) {
+        B->n_pre = n_pre;
+        B->n_body = n_body;
+        B->n_post = n_post;
+    }
+    return ok;
+}
+
+// ---------------------------------------------------------------------------
+// Launch-shape autotuner: the block shape of the site kernels (128 threads,
+// bx x by) chosen by timing the collision launch on the handle's own state;
+// cached per lattice size, precision and alpha settings for the process.
+// ---------------------------------------------------------------------------
+constexpr int kShapes[5][2] = {{128, 1}, {64, 2}, {32, 4}, {16, 8}, {8, 16}};
+
+void set_launch(Launch &L, int bx, int by, const elbm_params *p)
+{
+    L.block = dim3(bx, by, 1);
+    L.grid = dim3((p->nx + bx - 1) / bx, (p->ny + by - 1) / by, p->nz);
+    L.nblocks = (int)(L.grid.x * L.grid.y * L.grid.z);
+}
+
+long long max_blocks_over_shapes(const elbm_params *p)
+{
+    long long m = 0;
+    for (auto &c : kShapes) {
+        long long nb = (long long)((p->nx + c[0] - 1) / c[0]) * ((p->ny + c[1] - 1) / c[1]) * p->nz;
+        if (nb > m) m = nb;
+    }
+    return m;
+}
+
+std::mutex g_tune_mutex;
+std::map<std::array<int, 8>, int> g_tune_cache;
+
+bool autotune(elbm_handle *h)
+{
+    const elbm_params *p = &h->p;
+    const std::array<int, 8> key = {p->nx, p->ny, p->nz, p->precision, h->ph.aprec, p->alpha_mode,
+                                    p->charge_model, h->g.has_mask};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            set_launch(h->L, kShapes[it->second][0], kShapes[it->second][1], p);
+            return true;
+        }
+    }
+    cudaEvent_t e0, e1;
+    if (!cuda_ok(cudaEventCreate(&e0))) return false;
+    if (!cuda_ok(cudaEventCreate(&e1))) { cudaEventDestroy(e0); return false; }
+    int best = -1;
+    float best_ms = 1e30f;
+    bool ok = true;
+    for (int c = 0; c < 5 && ok; c++) {
+        if (kShapes[c][0] > 32 && kShapes[c][0] / 2 >= p->nx) continue;  // half the block idle
+        set_launch(h->L, kShapes[c][0], kShapes[c][1], p);
+        if (h->L.grid.y > 65535) continue;
+        h->ops.collide(h->g, h->ph, h->b, 1, h->L, h->s);  // warm-up
+        ok = cuda_ok(cudaEventRecord(e0, h->s));
+        for (int r = 0; r < 3; r++) h->ops.collide(h->g, h->ph, h->b, 1, h->L, h->s);
+        ok = ok && cuda_ok(cudaEventRecord(e1, h->s)) && cuda_ok(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        ok = ok && cuda_ok(cudaEventElapsedTime(&ms, e0, e1));
+        if (ok && ms < best_ms) { best_ms = ms; best = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!ok || best < 0) return false;
+    set_launch(h->L, kShapes[best][0], kShapes[best][1], p);
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = best;
+    return true;
 }
 
 }  // namespace
@@ -655,7 +769,8 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
         alloc(&h->lev[l].eps, (size_t)h->lev[l].N * h->sc_bytes);
     }
     if (h->nlev > 0) h->tail.top = h->lev[h->lt];
-    alloc((void **)&b.part, (size_t)L.nblocks * D_NPART * sizeof(double));
+    const long long part_blocks = p->autotune ? max_blocks_over_shapes(p) : L.nblocks;
+    alloc((void **)&b.part, (size_t)part_blocks * D_NPART * sizeof(double));
     alloc((void **)&b.scal, S_NSCAL * sizeof(double));
     alloc((void **)&b.scalf, S_NSCAL * sizeof(float));
     alloc((void **)&b.colres, 16 * sizeof(double));
@@ -689,6 +804,8 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
         if (t) cudaFree(t);
     if (!ok) { free_bufs(h); delete h; return ELBM_E_CUDA; }
 
+    if (p->autotune && !autotune(h)) { free_bufs(h); delete h; return ELBM_E_CUDA; }
+
     // Poisson loop control: a unit is one V-cycle, or ce SOR sweeps between tests
     h->ce = (h->nlev > 0 || p->poisson_fixed_sweeps > 0) ? 1
             : (p->poisson_check_every > 0 ? p->poisson_check_every : 8);
@@ -712,9 +829,78 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     return ELBM_OK;
 }
 
+elbm_status elbm_batch_create(elbm_handle *const *inst, int n, void *stream, elbm_handle **out)
+{
+    if (!out) return ELBM_E_INVAL;
+    *out = nullptr;
+    if (!inst || n < 1) return ELBM_E_INVAL;
+    for (int i = 0; i < n; i++) {
+        if (!inst[i] || inst[i]->n_sub > 0) return ELBM_E_INVAL;
+        if (inst[i]->p.diag_every != 1 || inst[i]->p.profile) return ELBM_E_INVAL;
+        for (int j = 0; j < i; j++)
+            if (inst[j] == inst[i]) return ELBM_E_INVAL;
+    }
+    elbm_handle *B = new (std::nothrow) elbm_handle;
+    if (!B) return ELBM_E_NOMEM;
+    std::memset(B, 0, sizeof(*B));
+    B->s = (cudaStream_t)stream;
+    B->n_sub = n;
+    B->sub = new (std::nothrow) elbm_handle *[n];
+    B->sub_step0 = new (std::nothrow) long long[n];
+    B->ev_join = new (std::nothrow) cudaEvent_t[n]();
+    bool ok = B->sub && B->sub_step0 && B->ev_join;
+    for (int i = 0; ok && i < n; i++) {
+        B->sub[i] = inst[i];
+        B->sub_step0[i] = inst[i]->step;
+        elbm_handle *h = inst[i];
+        if (!h->cap) ok = cuda_ok(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+        if (ok && !h->cap2) ok = cuda_ok(cudaStreamCreateWithFlags(&h->cap2, cudaStreamNonBlocking));
+        ok = ok && cuda_ok(cudaEventCreateWithFlags(&B->ev_join[i], cudaEventDisableTiming));
+    }
+    ok = ok && cuda_ok(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+    ok = ok && cuda_ok(cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming));
+    ok = ok && capture_batch(B, 0, &B->bexec[0]) && capture_batch(B, 1, &B->bexec[1]);
+    if (!ok) {
+        cudaGetLastError();
+        elbm_free(B);
+        return ELBM_E_CUDA;
+    }
+    *out = B;
+    return ELBM_OK;
+}
+
 elbm_status elbm_step(elbm_handle *h, int nsteps)
 {
     if (!h || nsteps < 0) return ELBM_E_INVAL;
+    if (h->n_sub > 0) {
+        for (int i = 0; i < h->n_sub; i++)
+            if (h->sub[i]->step - h->sub_step0[i] != h->step) return ELBM_E_STATE;
+        for (int k = 0; k < nsteps; k++) {
+            if (!cuda_ok(cudaGraphLaunch(h->bexec[h->step & 1], h->s))) return ELBM_E_CUDA;
+            for (int i = 0; i < h->n_sub; i++) {
+                swap_ab(h->sub[i]->b);
+                h->sub[i]->step++;
+            }
+            h->step++;
+        }
+        if (!cuda_ok(cudaStreamSynchronize(h->s))) return ELBM_E_CUDA;
+        elbm_status worst = ELBM_OK;
+        if (nsteps > 0) {
+            for (int i = 0; i < h->n_sub; i++) {
+                elbm_handle *q = h->sub[i];
+                double v[2] = {0.0, 0.0};
+                if (!cuda_ok(cudaMemcpy(&v[0], q->b.diag + 15, sizeof(double), cudaMemcpyDeviceToHost)) ||
+                    !cuda_ok(cudaMemcpy(&v[1], q->b.scal + S_NOCONV, sizeof(double), cudaMemcpyDeviceToHost)))
+                    return ELBM_E_CUDA;
+                if (v[0] != 0.0) worst = ELBM_E_NUMERIC;
+                if (v[1] > q->noconv_seen) {
+                    q->noconv_seen = v[1];
+                    if (worst == ELBM_OK) worst = ELBM_W_POISSON_NOCONV;
+                }
+            }
+        }
+        return worst;
+    }
     const bool prof = h->p.profile != 0;
     for (int i = 0; i < nsteps; i++) {
         if (h->use_graph && prof) {
@@ -780,6 +966,7 @@ size_t elbm_fields_size(const elbm_handle *h, unsigned mask)
 
 elbm_status elbm_fields(elbm_handle *h, unsigned mask, double *out, size_t out_len)
 {
+    if (h && h->n_sub > 0) return ELBM_E_STATE;
     if (!h || !out) return ELBM_E_INVAL;
     if (mask & ~0x1FFu) return ELBM_E_INVAL;
     if (out_len < elbm_fields_size(h, mask)) return ELBM_E_INVAL;
@@ -851,6 +1038,7 @@ elbm_status elbm_fields(elbm_handle *h, unsigned mask, double *out, size_t out_l
 
 elbm_status elbm_pass_times(const elbm_handle *h, double *out, int n)
 {
+    if (h && h->n_sub > 0) return ELBM_E_STATE;
     if (!h || !out || n < 0) return ELBM_E_INVAL;
     if (!h->p.profile) return ELBM_E_STATE;
     double v[8] = {h->pass_ms[0], h->pass_ms[1], h->pass_ms[2], h->pass_ms[3], h->prof_steps,
@@ -863,6 +1051,20 @@ void elbm_free(elbm_handle *h)
 {
     if (!h) return;
     cudaStreamSynchronize(h->s);
+    if (h->n_sub > 0) {  // a batch: its graphs and events only, not the instances
+        for (int i = 0; i < 2; i++)
+            if (h->bexec[i]) cudaGraphExecDestroy(h->bexec[i]);
+        if (h->ev_join)
+            for (int i = 0; i < h->n_sub; i++)
+                if (h->ev_join[i]) cudaEventDestroy(h->ev_join[i]);
+        if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+        if (h->cap) cudaStreamDestroy(h->cap);
+        delete[] h->sub;
+        delete[] h->sub_step0;
+        delete[] h->ev_join;
+        delete h;
+        return;
+    }
     free_bufs(h);
     delete h;
 }

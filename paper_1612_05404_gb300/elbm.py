@@ -26,7 +26,8 @@ DIAG_NAMES = [
 EXPORTS = ["elbm_init", "elbm_step", "elbm_fields", "elbm_fields_size", "elbm_free",
            "elbm_strerror", "elbm_velocity_set", "elbm_pass_times", "elbm_density_noalloc",
            "elbm_alpha_eval", "elbm_alpha_features", "elbm_alpha_harvest", "elbm_mlp_forward",
-           "elbm_mlp_workspace_floats", "elbm_mlp_grad", "elbm_mlp_adam", "elbm_mlp_train"]
+           "elbm_mlp_workspace_floats", "elbm_mlp_grad", "elbm_mlp_adam", "elbm_mlp_train",
+           "elbm_batch_create"]
 MLP_NIN = 20
 MLP_NPARAM = 5569
 NOALLOC_MAX_SITES = 16384 * 1024
@@ -56,6 +57,7 @@ class Params(ctypes.Structure):
         ("alpha_mode", ctypes.c_int), ("precision", ctypes.c_int),
         ("alpha_precision", ctypes.c_int), ("store_macro", ctypes.c_int),
         ("diag_every", ctypes.c_int), ("profile", ctypes.c_int), ("graph", ctypes.c_int),
+        ("autotune", ctypes.c_int),
         ("phi_lo", ctypes.c_double), ("phi_hi", ctypes.c_double), ("phi_solid", ctypes.c_double),
         ("nu0", ctypes.c_double), ("nu_inf", ctypes.c_double), ("lam", ctypes.c_double),
         ("n_carreau", ctypes.c_double),
@@ -110,6 +112,8 @@ def lib():
         L.elbm_density_noalloc.restype = ctypes.c_int
         L.elbm_alpha_eval.argtypes = [vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_double, vp, vp, vp, vp, vp, vp]
         L.elbm_alpha_eval.restype = ctypes.c_int
+        L.elbm_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]
+        L.elbm_batch_create.restype = ctypes.c_int
         ll, f = ctypes.c_longlong, ctypes.c_float
         L.elbm_alpha_features.argtypes = [vp, ll, vp, vp, vp]
         L.elbm_alpha_harvest.argtypes = [vp, ll, ctypes.c_double, vp, vp, vp, vp]
@@ -160,6 +164,7 @@ def make_params(cfg: dict, stream=None) -> Params:
     P.diag_every = int(cfg.get("diag_every", 1))
     P.profile = int(cfg.get("profile", 0))
     P.graph = int(cfg.get("graph", 1))
+    P.autotune = int(cfg.get("autotune", 0))
     P.phi_lo, P.phi_hi, P.phi_solid = cfg["phi_lo"], cfg["phi_hi"], cfg["phi_solid"]
     P.nu0, P.nu_inf, P.lam, P.n_carreau = cfg["nu0"], cfg["nu_inf"], cfg["lambda"], cfg["n_carreau"]
     P.G, P.Gw, P.rho0 = cfg["G"], cfg["Gw"], cfg["rho0"]
@@ -336,6 +341,7 @@ class Sim:
             raise ElbmError(rc, "elbm_init")
         self.h = h
         self.last_status = OK
+        self._keep = None  # elbm_init has copied the host fields
 
     def step(self, n: int = 1) -> int:
         rc = lib().elbm_step(self.h, int(n))
@@ -380,3 +386,37 @@ class Sim:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Lattices advanced together, one CUDA graph launch per step
+    (elbm_batch_create). The batch keeps references to its Sim instances; step
+    them only through the batch; read fields from each instance."""
+
+    def __init__(self, sims, stream=None):
+        self.sims = list(sims)
+        arr = (ctypes.c_void_p * len(self.sims))(*[s.h.value for s in self.sims])
+        h = ctypes.c_void_p()
+        rc = lib().elbm_batch_create(arr, len(self.sims), stream if stream is not None else _cur_stream(),
+                                     ctypes.byref(h))
+        if rc != OK:
+            raise ElbmError(rc, "elbm_batch_create")
+        self.h = h
+
+    def step(self, n: int = 1) -> int:
+        rc = lib().elbm_step(self.h, int(n))
+        if rc < 0:
+            raise ElbmError(rc, "elbm_step (batch)")
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().elbm_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -125,6 +125,47 @@ def charged_drop_at_rest(n=32, radius=8.0, precision="fp64", steps=500, seed=SEE
     return cfg, fields
 
 
+# Box edges for batched droplets: the multiples of 8 in [24, 96] whose
+# multigrid halving chain (periodic axes stay even) reaches <= 16^3 cells for
+# the one-CTA coarse tail; 72 and 88 stop at 18^3 and 22^3 and are left out.
+BATCH_EDGES = (24, 32, 40, 48, 56, 64, 80, 96)
+
+
+def batched_droplet_params(n_boxes=512, seed=SEED_BASE + 5):
+    """Per box (edge, E0, Carreau n), drawn from one seeded generator: edge
+    uniform over BATCH_EDGES, E0 uniform in [0, 1e-3] (a uniform applied
+    field along z), n uniform in [0.5, 1.0]."""
+    rng = np.random.default_rng(seed)
+    edges = rng.choice(BATCH_EDGES, size=n_boxes)
+    E0 = rng.uniform(0.0, 1e-3, size=n_boxes)
+    nc = rng.uniform(0.5, 1.0, size=n_boxes)
+    return [(int(e), float(a), float(b)) for e, a, b in zip(edges, E0, nc)]
+
+
+def batched_droplet(edge, E0, n_carreau, precision="fp32", seed=SEED_BASE + 5, Q=1e-3, noise=1e-4,
+                    eps_ratio=2.0, sigma_ratio=10.0):
+    """One box of the batched-droplets workload: periodic edge^3 lattice, drop
+    of radius edge/4 at the centre, uniform applied field E0 along z, Carreau
+    n_carreau with lambda = 10 and nu_inf = nu0/10, transported charge Q
+    spread over rho > 1 (eps ratio 2, sigma ratio 10), density noise +-1e-4."""
+    shape = (edge, edge, edge)
+    kappa = kappa_for_ratio(eps_ratio)
+    eps_l = 1.0 + kappa * RHO_L
+    sig_l = eps_l / 50.0
+    nu0 = 1.0 / 6.0
+    cfg = base_params(shape=shape, charge_model="transport", eps_kappa=kappa,
+                      sigma_liq=sig_l, sigma_gas=sig_l / sigma_ratio, Dq=1e-3,
+                      E_ext=(0.0, 0.0, E0), nu0=nu0, nu_inf=nu0 / 10.0, n_carreau=n_carreau,
+                      precision=precision, poisson_tol=1e-13, poisson_solver="mg")
+    cfg["lambda"] = 10.0
+    reduced_precision(cfg)
+    N = edge ** 3
+    rho = drop_profile(shape, edge / 4.0) + uniform_noise(N, noise, seed + edge)
+    inside = rho > 1.0
+    q = np.where(inside, Q / max(int(inside.sum()), 1), 0.0)
+    return cfg, dict(rho=rho, q=q)
+
+
 def drop_in_field(E0=1e-3, n=64, radius=12.0, precision="fp32", steps=5000,
                   seed=SEED_BASE + 2, eps_ratio=2.0, sigma_ratio=10.0, noise=1e-4,
                   n_carreau=0.6, lam=10.0):

@@ -136,3 +136,14 @@ def test_mlp_entry_points_argument_checks(L):
     assert L.elbm_mlp_adam(p, p, p, p, 1, 1e-3, 1.0, 0.999, 1e-8, None) == elbm.E_INVAL
     assert L.elbm_mlp_train(p, p, 4, p, p, p, 0, 1, 8, 1e-3, 0, None, p, None) == elbm.E_INVAL
     assert L.elbm_mlp_train(p, p, 4, p, p, p, 0, 1, 0, 1e-3, 1, None, p, None) == elbm.E_INVAL
+
+
+def test_batch_create_argument_checks(L):
+    import ctypes
+    out = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * 1)(None)
+    assert L.elbm_batch_create(arr, 1, None, None) == elbm.E_INVAL
+    assert L.elbm_batch_create(None, 1, None, ctypes.byref(out)) == elbm.E_INVAL
+    assert L.elbm_batch_create(arr, 0, None, ctypes.byref(out)) == elbm.E_INVAL
+    assert L.elbm_batch_create(arr, 1, None, ctypes.byref(out)) == elbm.E_INVAL  # a NULL instance
+    assert not out.value

@@ -1,0 +1,81 @@
+"""Batched lattices (elbm_batch_create): one CUDA graph launch per step for
+instances of uneven size and parameters must reproduce the same instances run
+one by one, bit for bit (same kernels, launch shapes and reduction order);
+the autotuned launch shape changes only the grouping of the block sums."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1612_05404_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+BOXES = [(16, 2e-4, 0.6), (24, 9e-4, 1.0), (32, 5e-4, 0.8)]
+
+
+def _make(precision="fp32", **extra):
+    from paper_1612_05404_gb300 import elbm
+    sims = []
+    for edge, E0, nc in BOXES:
+        cfg, fields = W.batched_droplet(edge, E0, nc, precision=precision)
+        cfg.update(extra)
+        sims.append(elbm.Sim(cfg, fields))
+    return sims
+
+
+def test_batch_reproduces_single_instances_bitwise():
+    from paper_1612_05404_gb300 import elbm
+    single = _make()
+    for s in single:
+        s.step(5)
+    grouped = _make()
+    batch = elbm.Batch(grouped)
+    assert batch.step(2) >= 0
+    assert batch.step(3) >= 0
+    for a, b in zip(single, grouped):
+        for name in ("rho", "phi", "q", "f"):
+            assert np.array_equal(a.get(name), b.get(name)), name
+        assert a.diag()["step"] == b.diag()["step"] == 5
+    batch.close()
+
+
+def test_batched_fp64_instance_matches_oracle():
+    from paper_1612_05404_gb300 import elbm
+    sims = _make(precision="fp64")
+    batch = elbm.Batch(sims)
+    batch.step(3)
+    edge, E0, nc = BOXES[1]
+    cfg, fields = W.batched_droplet(edge, E0, nc, precision="fp64")
+    o = oracle.Sim(cfg, fields)
+    o.step(3)
+    g = sims[1]
+    for name, ref in (("rho", o.rho), ("phi", o.phi), ("q", o.q)):
+        v = g.get(name)
+        assert np.linalg.norm(v - ref) <= 1e-10 * np.linalg.norm(ref), name
+    batch.close()
+
+
+def test_autotuned_shapes_keep_the_results():
+    from paper_1612_05404_gb300 import elbm
+    plain = _make(precision="fp64")
+    tuned = _make(precision="fp64", autotune=1)
+    for s in plain:
+        s.step(3)
+    batch = elbm.Batch(tuned)
+    batch.step(3)
+    for a, b in zip(plain, tuned):
+        for name in ("rho", "phi"):
+            x, y = a.get(name), b.get(name)
+            assert np.linalg.norm(x - y) <= 1e-11 * np.linalg.norm(x), name
+    batch.close()
+
+
+def test_stepping_an_instance_alone_is_refused():
+    from paper_1612_05404_gb300 import elbm
+    sims = _make()
+    batch = elbm.Batch(sims)
+    batch.step(1)
+    sims[0].step(1)
+    with pytest.raises(elbm.ElbmError):
+        batch.step(1)
+    batch.close()
