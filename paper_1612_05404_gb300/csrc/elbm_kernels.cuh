@@ -1288,11 +1288,14 @@ __device__ __forceinline__ T tail_resid(const Geom &g, const T *e, const T *b, c
     return r;
 }
 
+// The tail runs as one CTA of (BX, BY, BZ) threads: a level is swept with
+// x = tx + BX i (or, in a red-black pass, x = 2 (tx + BX i) + parity so that
+// every thread owns cells of the active colour), y = ty + BY j, z = tz + BZ k;
+// no integer division, no idle half in a colour pass.
 template <typename T>
 __device__ void tail_smooth(const Geom &g, const MGTail &t, T *E, T *B, T *P, int k, int sweeps)
 {
     const int nx = t.nx[k], ny = t.ny[k], nz = t.nz[k];
-    const long long N = t.N[k];
     T *e = E + t.off[k];
     const T *b = B + t.off[k], *ep = P + t.off[k];
     const int level = t.lt + k;
@@ -1300,29 +1303,32 @@ __device__ void tail_smooth(const Geom &g, const MGTail &t, T *E, T *B, T *P, in
     const int n_[3] = {nx, ny, nz};
     for (int it = 0; it < 2 * sweeps; it++) {
         const int color = it & 1;
-        for (int s = threadIdx.x; s < (int)N; s += blockDim.x) {
-            int x = s % nx, y = (s / nx) % ny, z = s / (nx * ny);
-            if (((x + y + z) & 1) != color) continue;
-            const int cc[3] = {x, y, z};
-            T es = ep[s], num = b[s], den = 0;
+        for (int z = threadIdx.z; z < nz; z += blockDim.z)
+            for (int y = threadIdx.y; y < ny; y += blockDim.y)
+                for (int xi = threadIdx.x;; xi += blockDim.x) {
+                    const int x = 2 * xi + ((y + z + color) & 1);
+                    if (x >= nx) break;
+                    const int s = x + nx * (y + ny * z);
+                    const int cc[3] = {x, y, z};
+                    T es = ep[s], num = b[s], den = 0;
 #pragma unroll
-            for (int a = 0; a < 3; a++)
+                    for (int a = 0; a < 3; a++)
 #pragma unroll
-                for (int sg = -1; sg <= 1; sg += 2) {
-                    int c[3] = {cc[0], cc[1], cc[2]};
-                    int v = nbc(c[a] + sg, n_[a], g.per[a]);
-                    if (v < 0) {
-                        if (g.phi_kind[2 * a + (sg > 0)] == ELBM_PHI_DIRICHLET) den += kb * es;
-                        continue;
-                    }
-                    c[a] = v;
-                    int nb = c[0] + nx * (c[1] + ny * c[2]);
-                    T cf = kap * T(0.5) * (es + ep[nb]);
-                    num += cf * e[nb];
-                    den += cf;
+                        for (int sg = -1; sg <= 1; sg += 2) {
+                            int c[3] = {cc[0], cc[1], cc[2]};
+                            int v = nbc(c[a] + sg, n_[a], g.per[a]);
+                            if (v < 0) {
+                                if (g.phi_kind[2 * a + (sg > 0)] == ELBM_PHI_DIRICHLET) den += kb * es;
+                                continue;
+                            }
+                            c[a] = v;
+                            int nb = c[0] + nx * (c[1] + ny * c[2]);
+                            T cf = kap * T(0.5) * (es + ep[nb]);
+                            num += cf * e[nb];
+                            den += cf;
+                        }
+                    if (den > T(0)) e[s] = num / den;
                 }
-            if (den > T(0)) e[s] = num / den;
-        }
         __syncthreads();
     }
 }
@@ -1334,74 +1340,93 @@ __global__ void __launch_bounds__(1024) k_mg_tail(Geom g, MGTail t, int nu)
     T *E = (T *)smem_raw;
     T *B = E + t.total;
     T *P = B + t.total;
-    for (long long s = threadIdx.x; s < t.N[0]; s += blockDim.x) {
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    for (int s = tid; s < (int)t.N[0]; s += nthr) {
         E[s] = T(0);
         B[s] = ((const T *)t.top.b)[s];
         P[s] = ((const T *)t.top.eps)[s];
     }
     __syncthreads();
     for (int k = 1; k < t.nt; k++) {  // coarse permittivities: mean of 8 children
-        const int nx = t.nx[k], ny = t.ny[k], fx = t.nx[k - 1], fy = t.ny[k - 1];
-        for (long long S = threadIdx.x; S < t.N[k]; S += blockDim.x) {
-            int Si = (int)S, X = Si % nx, Y = (Si / nx) % ny, Z = Si / (nx * ny);
-            T sum = 0;
-            for (int c = 0; c < 8; c++)
-                sum += P[t.off[k - 1] + (2 * X + (c & 1)) + (long long)fx * ((2 * Y + ((c >> 1) & 1)) + (long long)fy * (2 * Z + (c >> 2)))];
-            P[t.off[k] + S] = sum * T(0.125);
-        }
+        const int nx = t.nx[k], ny = t.ny[k], nz = t.nz[k], fx = t.nx[k - 1], fy = t.ny[k - 1];
+        const T *pf = P + t.off[k - 1];
+        for (int Z = threadIdx.z; Z < nz; Z += blockDim.z)
+            for (int Y = threadIdx.y; Y < ny; Y += blockDim.y)
+                for (int X = threadIdx.x; X < nx; X += blockDim.x) {
+                    T sum = 0;
+                    for (int c = 0; c < 8; c++)
+                        sum += pf[(2 * X + (c & 1)) + fx * ((2 * Y + ((c >> 1) & 1)) + fy * (2 * Z + (c >> 2)))];
+                    P[t.off[k] + X + nx * (Y + ny * Z)] = sum * T(0.125);
+                }
         __syncthreads();
     }
     // down: smooth, restrict
     for (int k = 0; k + 1 < t.nt; k++) {
         tail_smooth<T>(g, t, E, B, P, k, nu);
-        const int nx = t.nx[k + 1], ny = t.ny[k + 1], fx = t.nx[k], fy = t.ny[k], fz = t.nz[k];
-        for (long long S = threadIdx.x; S < t.N[k + 1]; S += blockDim.x) {
-            int Si = (int)S, X = Si % nx, Y = (Si / nx) % ny, Z = Si / (nx * ny);
-            T sum = 0;
-            for (int c = 0; c < 8; c++)
-                sum += tail_resid<T>(g, E + t.off[k], B + t.off[k], P + t.off[k], fx, fy, fz, t.lt + k,
-                                     2 * X + (c & 1), 2 * Y + ((c >> 1) & 1), 2 * Z + (c >> 2));
-            B[t.off[k + 1] + S] = sum;
-            E[t.off[k + 1] + S] = T(0);
-        }
+        const int nx = t.nx[k + 1], ny = t.ny[k + 1], nz = t.nz[k + 1];
+        const int fx = t.nx[k], fy = t.ny[k], fz = t.nz[k];
+        for (int Z = threadIdx.z; Z < nz; Z += blockDim.z)
+            for (int Y = threadIdx.y; Y < ny; Y += blockDim.y)
+                for (int X = threadIdx.x; X < nx; X += blockDim.x) {
+                    T sum = 0;
+                    for (int c = 0; c < 8; c++)
+                        sum += tail_resid<T>(g, E + t.off[k], B + t.off[k], P + t.off[k], fx, fy, fz, t.lt + k,
+                                             2 * X + (c & 1), 2 * Y + ((c >> 1) & 1), 2 * Z + (c >> 2));
+                    const int S = X + nx * (Y + ny * Z);
+                    B[t.off[k + 1] + S] = sum;
+                    E[t.off[k + 1] + S] = T(0);
+                }
         __syncthreads();
     }
     tail_smooth<T>(g, t, E, B, P, t.nt - 1, t.coarse_sweeps);
     // up: prolong (trilinear), smooth
     for (int k = t.nt - 2; k >= 0; k--) {
-        const int nx = t.nx[k], ny = t.ny[k];
+        const int nx = t.nx[k], ny = t.ny[k], nz = t.nz[k];
         const int nc[3] = {t.nx[k + 1], t.ny[k + 1], t.nz[k + 1]};
         const T *ec = E + t.off[k + 1];
-        for (long long s = threadIdx.x; s < t.N[k]; s += blockDim.x) {
-            int si = (int)s;
-            int fc[3] = {si % nx, (si / nx) % ny, si / (nx * ny)};
-            int i0[3], i1[3];
-            bool z1[3];
-            for (int a = 0; a < 3; a++) {
-                i0[a] = fc[a] >> 1;
-                int o = (fc[a] & 1) ? 1 : -1;
-                int v = nbc(i0[a] + o, nc[a], g.per[a]);
-                z1[a] = false;
-                if (v < 0) {
-                    if (g.phi_kind[2 * a + (o > 0)] == ELBM_PHI_DIRICHLET) z1[a] = true;
-                    v = i0[a];
+        for (int fz_ = threadIdx.z; fz_ < nz; fz_ += blockDim.z)
+            for (int fy_ = threadIdx.y; fy_ < ny; fy_ += blockDim.y)
+                for (int fx_ = threadIdx.x; fx_ < nx; fx_ += blockDim.x) {
+                    const int fc[3] = {fx_, fy_, fz_};
+                    int i0[3], i1[3];
+                    bool z1[3];
+                    for (int a = 0; a < 3; a++) {
+                        i0[a] = fc[a] >> 1;
+                        int o = (fc[a] & 1) ? 1 : -1;
+                        int v = nbc(i0[a] + o, nc[a], g.per[a]);
+                        z1[a] = false;
+                        if (v < 0) {
+                            if (g.phi_kind[2 * a + (o > 0)] == ELBM_PHI_DIRICHLET) z1[a] = true;
+                            v = i0[a];
+                        }
+                        i1[a] = v;
+                    }
+                    T acc = 0;
+                    for (int c = 0; c < 8; c++) {
+                        int ax = c & 1, ay = (c >> 1) & 1, az = c >> 2;
+                        if ((ax && z1[0]) || (ay && z1[1]) || (az && z1[2])) continue;
+                        T w = (ax ? T(0.25) : T(0.75)) * (ay ? T(0.25) : T(0.75)) * (az ? T(0.25) : T(0.75));
+                        int X = ax ? i1[0] : i0[0], Y = ay ? i1[1] : i0[1], Z = az ? i1[2] : i0[2];
+                        acc += w * ec[X + nc[0] * (Y + nc[1] * Z)];
+                    }
+                    E[t.off[k] + fx_ + nx * (fy_ + ny * fz_)] += acc;
                 }
-                i1[a] = v;
-            }
-            T acc = 0;
-            for (int c = 0; c < 8; c++) {
-                int ax = c & 1, ay = (c >> 1) & 1, az = c >> 2;
-                if ((ax && z1[0]) || (ay && z1[1]) || (az && z1[2])) continue;
-                T w = (ax ? T(0.25) : T(0.75)) * (ay ? T(0.25) : T(0.75)) * (az ? T(0.25) : T(0.75));
-                int X = ax ? i1[0] : i0[0], Y = ay ? i1[1] : i0[1], Z = az ? i1[2] : i0[2];
-                acc += w * ec[X + (long long)nc[0] * (Y + (long long)nc[1] * Z)];
-            }
-            E[t.off[k] + s] += acc;
-        }
         __syncthreads();
         tail_smooth<T>(g, t, E, B, P, k, nu);
     }
-    for (long long s = threadIdx.x; s < t.N[0]; s += blockDim.x) ((T *)t.top.e)[s] = E[s];
+    for (int s = tid; s < (int)t.N[0]; s += nthr) ((T *)t.top.e)[s] = E[s];
+}
+
+// One CTA of at most 1024 threads for a tail whose top level is nx x ny x nz:
+// BX covers half a row (colour-compacted passes), then BY, BZ.
+inline dim3 tail_block(int nx, int ny, int nz)
+{
+    int bx = (nx + 1) / 2;
+    if (bx > 32) bx = 32;
+    int by = ny < 1024 / bx ? ny : 1024 / bx;
+    int bz = nz < 1024 / (bx * by) ? nz : 1024 / (bx * by);
+    return dim3(bx, by, bz < 1 ? 1 : bz);
 }
 
 // ---------------------------------------------------------------------------
@@ -1453,8 +1478,7 @@ struct MGLaunchers {
     static void tail_(const Geom &g, const MGTail &t, int nu, cudaStream_t s)
     {
         size_t sm = 3 * (size_t)t.total * sizeof(sc);
-        int thr = t.N[0] >= 1024 ? 1024 : (int)(((t.N[0] + 31) / 32) * 32);
-        k_mg_tail<sc><<<1, thr, sm, s>>>(g, t, nu);
+        k_mg_tail<sc><<<1, tail_block(t.nx[0], t.ny[0], t.nz[0]), sm, s>>>(g, t, nu);
     }
     static MGOps table()
     {
