@@ -276,7 +276,7 @@ def run_ours(args, rank, world, local_rank):
                    if args.precision != "fp64" else "fp64",
                    "alpha_arithmetic": args.alpha_precision,
                    "l2": "256 MiB flush between timed steps (outside timing); state 190 MB > L2",
-                   "poisson": "multigrid V(2,2), red-black Gauss-Seidel, tol 1e-6 (FP32 floor stop), warm start",
+                   "poisson": "multigrid V(2,2), red-black Gauss-Seidel, tol 1e-6 (FP32 floor stop), warm start extrapolated from the two previous potentials",
                    "poisson_vcycles_per_step": sweeps / max(args.steps, 1) / len(sims),
                    "launch": ("one CUDA graph per step for all lattices (batch), autotuned block shapes"
                               if args.launch == "batch" else "one graph per lattice on concurrent streams"),

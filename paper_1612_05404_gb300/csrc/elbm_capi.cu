@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(256) k_finalize(const double *part, int nblock
         scal[S_Q2] = res[1];
         scal[S_QMEAN] = (ph.neutralize && ph.n_fluid > 0) ? res[0] / ph.n_fluid : 0.0;
     } else if (mode == FIN_RESID_PRE || mode == FIN_RESID_BODY) {
+        if (mode == FIN_RESID_PRE) scal[S_HAVE_OLD] = 1.0;
         double rn = sqrt(res[0]), ref = sqrt(res[1]) + sqrt(res[2]);
         scal[S_RESID] = ref > 0.0 ? rn / ref : rn;
         double iter = mode == FIN_RESID_PRE ? 0.0 : scal[S_ITER] + 1.0;
@@ -243,7 +244,7 @@ void free_bufs(elbm_handle *h)
     void *ptrs[] = {h->b.fA, h->b.fB, h->b.gA, h->b.gB, h->b.rho, h->b.q, h->b.phi, h->b.ux,
                     h->b.uy, h->b.uz, h->b.alpha, h->b.nu, h->b.mask, h->b.nh, h->b.ab,
                     h->b.part, h->b.scal, h->b.scalf, h->b.diag, h->b.colres, h->b.ticket,
-                    const_cast<void *>(h->b.mlpimg)};
+                    const_cast<void *>(h->b.mlpimg), h->b.phi_old};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (h->pin) cudaFreeHost(h->pin);
@@ -322,11 +323,18 @@ int enq_pre(elbm_handle *h, const Bufs &b, cudaStream_t s)
     return n;
 }
 
+// the extrapolated warm start (not with a fixed sweep count, which the
+// caller means as an exact number of smoothing sweeps from phi(t-1)) and the
 // coarse permittivities of this step (multigrid)
 int enq_eps(elbm_handle *h, const Bufs &b, cudaStream_t s)
 {
+    int n = 0;
+    if (b.phi_old) {
+        h->ops.phi_extrap(h->g, b, s);
+        n++;
+    }
     for (int l = 0; l < h->lt; l++) h->mg.eps(h->g, h->ph, b, h->lev[l], h->lev[l + 1], l, s);
-    return h->nlev > 0 ? h->lt : 0;
+    return n + (h->nlev > 0 ? h->lt : 0);
 }
 
 // convergence test: residual sums, then the device-side decision
@@ -740,6 +748,10 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     alloc(&b.rho, (size_t)N * h->sc_bytes);
     alloc(&b.q, (size_t)N * h->sc_bytes);
     alloc(&b.phi, (size_t)N * h->sc_bytes);
+    // extrapolated warm start in reduced precision (FP64 keeps phi(t-1), the
+    // start the FP64 oracle uses, so that the two solves agree to 1e-12)
+    if (p->charge_model != ELBM_CHARGE_NONE && p->poisson_fixed_sweeps == 0 && p->precision != ELBM_PREC_FP64)
+        alloc(&b.phi_old, (size_t)N * h->sc_bytes);
     if (p->store_macro) {
         alloc(&b.ux, (size_t)N * h->sc_bytes);
         alloc(&b.uy, (size_t)N * h->sc_bytes);

@@ -18,6 +18,7 @@ enum {
     S_ITER_TOTAL,  // Poisson units over all steps
     S_STEPS,       // completed steps
     S_KEEP,        // 1 while the Poisson loop must go on
+    S_HAVE_OLD,    // 1 once phi(t-1) is recorded for the extrapolated warm start
     S_NSCAL = 24
 };
 // per-block partial slots of the collision diagnostics
@@ -52,6 +53,7 @@ struct Bufs {
     unsigned int *ticket;             // last-block-done counter of the finalize kernel
     double *diag;                     // ELBM_NDIAG diagnostics
     const void *mlpimg;               // learned alpha: BF16 shared-memory image of the network
+    void *phi_old;                    // potential of the previous step (extrapolated warm start)
 };
 
 struct Launch {
@@ -73,6 +75,8 @@ struct Ops {
     // stage 0: block sums of phi over non-solid nodes; stage 1: subtract S_PHIMEAN
     void (*phi_mean)(const Geom &, const Phys &, const Bufs &, int stage, const Launch &, cudaStream_t);
     void (*collide)(const Geom &, const Phys &, const Bufs &, int diag, const Launch &, cudaStream_t);
+    // warm start of the Poisson solve: phi <- 2 phi - phi_old, phi_old <- phi
+    void (*phi_extrap)(const Geom &, const Bufs &, cudaStream_t);
     // learned alpha: network output o per site into the alpha plane (NULL for FP64)
     void (*alpha_mlp)(const Geom &, const Phys &, const Bufs &, const Launch &, cudaStream_t);
     void (*export_pop)(const Geom &, const Bufs &, double *out, const Launch &, cudaStream_t);

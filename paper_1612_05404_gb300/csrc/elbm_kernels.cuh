@@ -865,6 +865,20 @@ __global__ void __launch_bounds__(128) k_alpha_mlp(Geom g, Phys ph, Bufs b)
     if (active) ((sc *)b.alpha)[s] = sc(os[w][lane]);
 }
 
+// Warm start of the Poisson solve by linear extrapolation in time,
+// phi <- 2 phi(t-1) - phi(t-2); the first call (no phi(t-2) yet, flag set by
+// the following pre-solve test) only records phi(t-1). Solid (conductor)
+// nodes hold a constant, which the extrapolation keeps.
+template <typename T>
+__global__ void k_phi_extrap(T *__restrict__ phi, T *__restrict__ phi_old, const double *__restrict__ scal, ll N)
+{
+    const ll i = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const T p = phi[i];
+    if (scal[S_HAVE_OLD] != 0.0) phi[i] = T(2) * p - phi_old[i];
+    phi_old[i] = p;
+}
+
 // f(r, t) for the caller: the pull of every fluid site, 0 elsewhere
 template <int PR>
 __global__ void k_export_pop(Geom g, Bufs b, double *out)
@@ -959,6 +973,10 @@ struct Launchers {
         else
             k_collide<PR, ELBM_APREC_FP32><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
     }
+    static void phi_extrap(const Geom &g, const Bufs &b, cudaStream_t s)
+    {
+        k_phi_extrap<sc><<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>((sc *)b.phi, (sc *)b.phi_old, b.scal, g.N);
+    }
     static void alpha_mlp(const Geom &g, const Phys &ph, const Bufs &b, const Launch &L, cudaStream_t s)
     {
         if (PR != ELBM_PREC_FP64) k_alpha_mlp<PR><<<L.grid, L.block, 0, s>>>(g, ph, b);
@@ -986,6 +1004,7 @@ struct Launchers {
         o.phi_mean = phi_mean;
         o.collide = collide;
         o.alpha_mlp = PR == ELBM_PREC_FP64 ? nullptr : alpha_mlp;
+        o.phi_extrap = phi_extrap;
         o.export_pop = export_pop;
         o.export_gpop = export_gpop;
         o.export_plane = export_plane;
