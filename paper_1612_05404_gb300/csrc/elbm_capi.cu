@@ -149,8 +149,10 @@ __global__ void __launch_bounds__(256) k_finalize(const double *part, int nblock
         scal[S_ITER] = iter;
         if (mode == FIN_RESID_BODY) scal[S_ITER_TOTAL] += 1.0;
         bool conv = rn <= ph.tol * ref;
-        // FP32 potential: a test interval without progress means its
-        // rounding floor is reached
+        // FP32 potential: stop at its rounding floor, once the residual is
+        // within 2^-23 |t| (t: magnitude of the residual's terms), or when a
+        // test interval brought no progress
+        if (!conv && ctl.reduced && rn <= 0x1p-23 * sqrt(res[3])) conv = true;
         if (!conv && ctl.reduced && mode == FIN_RESID_BODY && rn > 0.97 * scal[S_PREV]) conv = true;
         scal[S_PREV] = rn;
         scal[S_CONV] = conv ? 1.0 : 0.0;
@@ -341,7 +343,7 @@ int enq_eps(elbm_handle *h, const Bufs &b, cudaStream_t s)
 int enq_check(elbm_handle *h, const Bufs &b, cudaStream_t s, int mode, unsigned long long cond, int use_cond)
 {
     h->ops.resid(h->g, h->ph, b, h->L, s);
-    return 1 + fin(h, b, s, 3, mode, cond, use_cond);
+    return 1 + fin(h, b, s, 4, mode, cond, use_cond);
 }
 
 // one Poisson unit: a V-cycle, or ce red-black SOR sweeps

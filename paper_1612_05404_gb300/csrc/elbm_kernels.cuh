@@ -471,7 +471,10 @@ __global__ void __launch_bounds__(128) k_resid(Geom g, Phys ph, Bufs b)
     site_xyz(g, x, y, z, inb, s);
     unsigned char kind = (inb && b.mask) ? b.mask[s] : 0;
     bool active = inb && kind != ELBM_NODE_SOLID;
-    sc r2 = 0, q2 = 0, b2 = 0;
+    // r^2, q^2, b^2 and t^2, t = the magnitude of the terms of r (source and
+    // every face term with |phi| in place of its difference): the residual of
+    // a potential stored in FP32 cannot fall much below 2^-24 |t|
+    sc r2 = 0, q2 = 0, b2 = 0, t2 = 0;
     if (active) {
         Nbr n;
         nbr_init(n, g, x, y, z, s);
@@ -483,6 +486,7 @@ __global__ void __launch_bounds__(128) k_resid(Geom g, Phys ph, Bufs b)
         sc r = kind == ELBM_NODE_FLUID ? qs - scal_of<sc>(b, S_QMEAN) : sc(0);
         sc bs = 0;
         sc ps = phi[s];
+        sc t = fabs(r);
 #pragma unroll
         for (int a = 0; a < 3; a++)
 #pragma unroll
@@ -490,15 +494,23 @@ __global__ void __launch_bounds__(128) k_resid(Geom g, Phys ph, Bufs b)
                 ll nb = 0;
                 sc v = 0;
                 int kk = pois_nb<sc>(g, k, b.mask, n, x, y, z, a, sg, &nb, &v);
-                if (kk == 0) r += sc(0.5) * (es + (sc(1) + k.kap * rho[nb])) * (phi[nb] - ps);
-                else if (kk == 1) { r += es * (v - ps); bs += es * v; }
+                if (kk == 0) {
+                    const sc cf = sc(0.5) * (es + (sc(1) + k.kap * rho[nb]));
+                    r += cf * (phi[nb] - ps);
+                    t += cf * (fabs(phi[nb]) + fabs(ps));
+                } else if (kk == 1) {
+                    r += es * (v - ps);
+                    bs += es * v;
+                    t += es * (fabs(v) + fabs(ps));
+                }
             }
         r2 = r * r;
         q2 = qs * qs;
         b2 = bs * bs;
+        t2 = t * t;
     }
-    sc v[3] = {r2, q2, b2};
-    block_sums<3>(v, b.part + block_id(), num_blocks());
+    sc v[4] = {r2, q2, b2, t2};
+    block_sums<4>(v, b.part + block_id(), num_blocks());
 }
 
 template <int PR>
