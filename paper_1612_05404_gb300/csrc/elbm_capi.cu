@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256) k_finalize(const double *part, int nblock
         scal[S_Q2] = res[1];
         scal[S_QMEAN] = (ph.neutralize && ph.n_fluid > 0) ? res[0] / ph.n_fluid : 0.0;
     } else if (mode == FIN_RESID_PRE || mode == FIN_RESID_BODY) {
-        if (mode == FIN_RESID_PRE) scal[S_HAVE_OLD] = 1.0;
+        scal[S_HAVE_OLD] = 1.0;
         double rn = sqrt(res[0]), ref = sqrt(res[1]) + sqrt(res[2]);
         scal[S_RESID] = ref > 0.0 ? rn / ref : rn;
         double iter = mode == FIN_RESID_PRE ? 0.0 : scal[S_ITER] + 1.0;
@@ -326,17 +326,13 @@ int enq_pre(elbm_handle *h, const Bufs &b, cudaStream_t s)
 }
 
 // the extrapolated warm start (not with a fixed sweep count, which the
-// caller means as an exact number of smoothing sweeps from phi(t-1)) and the
-// coarse permittivities of this step (multigrid)
+// caller means as an exact number of smoothing sweeps from phi(t-1))
 int enq_eps(elbm_handle *h, const Bufs &b, cudaStream_t s)
 {
-    int n = 0;
-    if (b.phi_old) {
-        h->ops.phi_extrap(h->g, b, s);
-        n++;
-    }
-    for (int l = 0; l < h->lt; l++) h->mg.eps(h->g, h->ph, b, h->lev[l], h->lev[l + 1], l, s);
-    return n + (h->nlev > 0 ? h->lt : 0);
+    // (the coarse permittivities of the multigrid come with each restriction)
+    if (!b.phi_old) return 0;
+    h->ops.phi_extrap(h->g, b, s);
+    return 1;
 }
 
 // convergence test: residual sums, then the device-side decision
@@ -386,12 +382,15 @@ elbm_status step_host(elbm_handle *h, bool diag)
     if (prof) cudaEventRecord(h->ev[1], s);
     if (charged) {
         h->launches += enq_eps(h, b, s);
-        h->launches += enq_check(h, b, s, FIN_RESID_PRE, 0, 0);
-        for (;;) {
-            if (!cuda_ok(cudaMemcpyAsync(h->pin, b.scal + S_KEEP, sizeof(double), cudaMemcpyDeviceToHost, s)) ||
-                !cuda_ok(cudaStreamSynchronize(s)))
-                return ELBM_E_CUDA;
-            if (h->pin[0] == 0.0) break;
+        const bool dowhile = b.phi_old != nullptr;
+        if (!dowhile) h->launches += enq_check(h, b, s, FIN_RESID_PRE, 0, 0);
+        for (bool first = true;; first = false) {
+            if (!(dowhile && first)) {
+                if (!cuda_ok(cudaMemcpyAsync(h->pin, b.scal + S_KEEP, sizeof(double), cudaMemcpyDeviceToHost, s)) ||
+                    !cuda_ok(cudaStreamSynchronize(s)))
+                    return ELBM_E_CUDA;
+                if (h->pin[0] == 0.0) break;
+            }
             h->launches += enq_unit(h, b, s);
             h->launches += enq_check(h, b, s, FIN_RESID_BODY, 0, 0);
         }
@@ -429,9 +428,12 @@ bool enqueue_step(elbm_handle *h, int parity, cudaStream_t s, int sections, int 
         const cudaGraphNode_t *deps = nullptr;
         size_t nd = 0;
         ok = ok && cuda_ok(cudaStreamGetCaptureInfo(s, &st, nullptr, &cg, &deps, nullptr, &nd));
-        ok = ok && cuda_ok(cudaGraphConditionalHandleCreate(&cond, cg, 0, cudaGraphCondAssignDefault));
+        // do-while (reduced precision, extrapolated start): the loop's first
+        // unit runs untested; else the test before the loop decides
+        const bool dowhile = b.phi_old != nullptr;
+        ok = ok && cuda_ok(cudaGraphConditionalHandleCreate(&cond, cg, dowhile ? 1u : 0u, cudaGraphCondAssignDefault));
         n_pre += enq_eps(h, b, s);
-        n_pre += enq_check(h, b, s, FIN_RESID_PRE, cond, 1);
+        if (!dowhile) n_pre += enq_check(h, b, s, FIN_RESID_PRE, cond, 1);
         cudaGraphNode_t node;
         cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
         np.conditional.handle = cond;

@@ -881,10 +881,16 @@ __global__ void __launch_bounds__(128) k_alpha_mlp(Geom g, Phys ph, Bufs b)
 // phi <- 2 phi(t-1) - phi(t-2); the first call (no phi(t-2) yet, flag set by
 // the following pre-solve test) only records phi(t-1). Solid (conductor)
 // nodes hold a constant, which the extrapolation keeps.
+// It also opens the step's Poisson loop, which then runs as do-while (no
+// test before the first unit): unit counter 0, no previous residual.
 template <typename T>
-__global__ void k_phi_extrap(T *__restrict__ phi, T *__restrict__ phi_old, const double *__restrict__ scal, ll N)
+__global__ void k_phi_extrap(T *__restrict__ phi, T *__restrict__ phi_old, double *__restrict__ scal, ll N)
 {
     const ll i = (ll)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        scal[S_ITER] = 0.0;
+        scal[S_PREV] = 1e300;
+    }
     if (i >= N) return;
     const T p = phi[i];
     if (scal[S_HAVE_OLD] != 0.0) phi[i] = T(2) * p - phi_old[i];
@@ -1145,7 +1151,7 @@ __global__ void __launch_bounds__(128) k_mg_restrict(Geom g, Phys ph, Bufs bf, M
     const unsigned S = gid >> 3;
     const int c = (int)(gid & 7);
     const bool act = S < (unsigned)C.N;
-    T r = 0;
+    T r = 0, ep = 0;
     int X = 0, Y = 0, Z = 0;
     if (act) {
         const unsigned nxy = (unsigned)C.nx * (unsigned)C.ny;
@@ -1153,14 +1159,23 @@ __global__ void __launch_bounds__(128) k_mg_restrict(Geom g, Phys ph, Bufs bf, M
         const unsigned rem = S - (unsigned)Z * nxy;
         Y = (int)(rem / (unsigned)C.nx);
         X = (int)(rem - (unsigned)Y * (unsigned)C.nx);
-        r = mg_resid_at<PR>(g, ph, bf, F, level, 2 * X + (c & 1), 2 * Y + ((c >> 1) & 1), 2 * Z + (c >> 2));
+        const int fx = 2 * X + (c & 1), fy = 2 * Y + ((c >> 1) & 1), fz = 2 * Z + (c >> 2);
+        r = mg_resid_at<PR>(g, ph, bf, F, level, fx, fy, fz);
+        // the coarse permittivity (mean of the 8 children) comes with the
+        // restriction: the coarse level's smoothing and residual read it next
+        const ll fs = fx + (ll)F.nx * (fy + (ll)F.ny * fz);
+        ep = level == 0 ? T(1) + cst<T>(ph).kap * ((const T *)bf.rho)[fs] : ((const T *)F.eps)[fs];
     }
     r += __shfl_down_sync(0xffffffffu, r, 4, 8);
     r += __shfl_down_sync(0xffffffffu, r, 2, 8);
     r += __shfl_down_sync(0xffffffffu, r, 1, 8);
+    ep += __shfl_down_sync(0xffffffffu, ep, 4, 8);
+    ep += __shfl_down_sync(0xffffffffu, ep, 2, 8);
+    ep += __shfl_down_sync(0xffffffffu, ep, 1, 8);
     if (act && c == 0) {
         ((T *)C.b)[S] = r;
         ((T *)C.e)[S] = T(0);
+        ((T *)C.eps)[S] = ep * T(0.125);
     }
 }
 
