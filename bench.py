@@ -54,6 +54,7 @@ def parse():
                     help="skip the learned-alpha vs Newton-alpha comparison")
     ap.add_argument("--boxes", type=int, default=512,
                     help="batched-droplets comparison: number of boxes (0 skips it)")
+    ap.add_argument("--no-jet", action="store_true", help="skip the electrified-jet measurement")
     return ap.parse_args()
 
 
@@ -283,7 +284,10 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                     "frac_of_8TBps": achieved / NOMINAL_HBM_GBS, "traffic": None,
+                     "frac_of_8TBps": achieved / NOMINAL_HBM_GBS,
+                     # ncu dram__bytes_read.sum + dram__bytes_write.sum of one 64^3 FP32
+                     # launch of this kernel (cold caches)
+                     "traffic": 31.95e6 if args.precision == "fp32" else None,
                      "bytes_per_site": bytes_site, "avg_launch_ms": coll_ms,
                      "timed": "one 64^3 lattice alone, CUDA events around each collision launch"},
         "pass_share": shares,
@@ -439,6 +443,44 @@ def alpha_compare(args, N):
     return out
 
 
+def jet_run(args):
+    """The electrified jet at full size: 128 x 128 x 512, nozzle of radius 8
+    injecting Carreau liquid (n = 0.5, lambda = 20) at 0.02 along z, E0 = 5e-4,
+    xi-form charge, BF16 deviation storage with FP32 arithmetic, guarded FP32
+    alpha, multigrid Poisson with the nozzle as a conductor."""
+    import torch
+    from paper_1612_05404_gb300 import elbm
+    from paper_1612_05404_gb300 import workloads as W
+    cfg, fields = W.jet(precision="bf16")
+    cfg.update(alpha_precision="fp32", poisson_solver="mg", graph=1, diag_every=1, autotune=1)
+    N = cfg["shape"][0] * cfg["shape"][1] * cfg["shape"][2]
+    sim = elbm.Sim(cfg, fields)
+    del fields
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    total, cycles, herr, guarded = 0.0, 0.0, 0.0, 0.0
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sim.step(1)
+        e1.record()
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+        d = sim.diag()
+        cycles += d["poisson_sweeps"]
+        herr = max(herr, d["max_h_error"])
+        guarded += d["n_guarded"]
+    sim.close()
+    return {"workload": "electrified jet 128x128x512, nozzle r=8, Carreau n=0.5 lambda=20, E0=5e-4, xi-form charge",
+            "storage": "bf16 deviation", "sites": N, "mlups": N * args.steps / (total * 1e-3) / 1e6,
+            "ms_per_step": total / args.steps, "poisson": "multigrid, nozzle as conductor",
+            "poisson_vcycles_per_step": cycles / args.steps, "max_h_error_device": herr,
+            "guarded_site_fraction": guarded / (N * args.steps)}
+
+
 def batched_compare(args):
     """Batched droplets (uneven boxes, one CUDA graph launch per step for all)
     against the same boxes stepped one at a time, at the same H-error bound
@@ -517,6 +559,8 @@ def main():
         res["alpha_compare"] = alpha_compare(args, N)
     if rank == 0 and world == 1 and args.boxes > 0:
         res["batched_compare"] = batched_compare(args)
+    if rank == 0 and world == 1 and not args.no_jet:
+        res["jet"] = jet_run(args)
     if rank == 0 and world == 1 and not args.no_cpu:
         v, dt, sample = cpu_sample()
         res["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample}

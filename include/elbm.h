@@ -57,8 +57,10 @@ enum { ELBM_CHARGE_NONE = 0, ELBM_CHARGE_CONSERVED = 1, ELBM_CHARGE_XI = 2,
 enum { ELBM_FEL_QE = 0, ELBM_FEL_FULL = 1 };
 /* Poisson solver: red-black SOR as the paper states it, or geometric
  * multigrid (red-black Gauss-Seidel smoothing) on the same fine operator with
- * the same stopping rule; multigrid needs no interior solid nodes and lattice
- * extents that halve at least once (even, and even on periodic axes) */
+ * the same stopping rule; interior solid nodes are conductors held at
+ * phi_solid on the fine level (the coarse levels correct the other nodes);
+ * multigrid needs lattice extents that halve at least once (even, and even
+ * on periodic axes) and a level of at most 4096 cells */
 enum { ELBM_POISSON_SOR = 0, ELBM_POISSON_MG = 1 };
 /* relaxation: entropic alpha (Eq. entropic), alpha = 2 (BGK), or the
  * entropic alpha with its Newton iteration started from the learned proposal

@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <array>
+#include <vector>
 #include <map>
 #include <mutex>
 #include <new>
@@ -151,9 +152,13 @@ __global__ void __launch_bounds__(256) k_finalize(const double *part, int nblock
         bool conv = rn <= ph.tol * ref;
         // FP32 potential: stop at its rounding floor, once the residual is
         // within 2^-23 |t| (t: magnitude of the residual's terms), or when a
-        // test interval brought no progress
+        // test interval brought no progress within 2^-17 |t|
         if (!conv && ctl.reduced && rn <= 0x1p-23 * sqrt(res[3])) conv = true;
-        if (!conv && ctl.reduced && mode == FIN_RESID_BODY && rn > 0.97 * scal[S_PREV]) conv = true;
+        // (the no-progress rule only near the floor: SOR's residual is not
+        // monotone early in a solve)
+        if (!conv && ctl.reduced && mode == FIN_RESID_BODY && rn > 0.97 * scal[S_PREV] &&
+            rn <= 0x1p-17 * sqrt(res[3]))
+            conv = true;
         scal[S_PREV] = rn;
         scal[S_CONV] = conv ? 1.0 : 0.0;
         bool keep;
@@ -254,7 +259,9 @@ void free_bufs(elbm_handle *h)
         if (h->lev[l].e) cudaFree(h->lev[l].e);
         if (h->lev[l].b) cudaFree(h->lev[l].b);
         if (h->lev[l].eps) cudaFree(h->lev[l].eps);
+        if (l < h->lt && h->lev[l].m) cudaFree(const_cast<unsigned char *>(h->lev[l].m));
     }
+    if (h->tail.m) cudaFree(const_cast<unsigned char *>(h->tail.m));
     for (int i = 0; i < 5; i++)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     for (int i = 0; i < 2; i++) {
@@ -691,7 +698,6 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     // periodic axes, for the red-black colouring) and the level has > 64 cells
     h->nlev = 0;
     if (p->charge_model != ELBM_CHARGE_NONE && p->poisson_solver == ELBM_POISSON_MG) {
-        if (n_solid > 0) { delete h; return ELBM_E_INVAL; }
         int n[3] = {p->nx, p->ny, p->nz};
         h->lev[0].nx = n[0]; h->lev[0].ny = n[1]; h->lev[0].nz = n[2]; h->lev[0].N = N;
         int L = 1;
@@ -783,6 +789,38 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
         alloc(&h->lev[l].e, (size_t)h->lev[l].N * h->sc_bytes);
         alloc(&h->lev[l].b, (size_t)h->lev[l].N * h->sc_bytes);
         alloc(&h->lev[l].eps, (size_t)h->lev[l].N * h->sc_bytes);
+    }
+    // conductor masks of the coarse levels: a cell is a conductor (its
+    // correction held at 0) when any of its 8 children is one
+    if (h->nlev > 0 && n_solid > 0 && ok) {
+        std::vector<std::vector<unsigned char>> hm(h->nlev);
+        hm[0].resize(N);
+        for (long long i = 0; i < N; i++) hm[0][i] = in->mask[i] == ELBM_NODE_SOLID;
+        for (int l = 1; l < h->nlev; l++) {
+            const MGLevel &F = h->lev[l - 1], &C = h->lev[l];
+            hm[l].assign(C.N, 0);
+            for (int Z = 0; Z < C.nz; Z++)
+                for (int Y = 0; Y < C.ny; Y++)
+                    for (int X = 0; X < C.nx; X++) {
+                        unsigned char any = 0;
+                        for (int c = 0; c < 8; c++)
+                            any |= hm[l - 1][(2 * X + (c & 1)) + (long long)F.nx * ((2 * Y + ((c >> 1) & 1)) + (long long)F.ny * (2 * Z + (c >> 2)))];
+                        hm[l][X + (long long)C.nx * (Y + (long long)C.ny * Z)] = any;
+                    }
+        }
+        for (int l = 1; l < h->lt && ok; l++) {
+            void *d = nullptr;
+            alloc(&d, (size_t)h->lev[l].N);
+            if (ok) ok = cuda_ok(cudaMemcpy(d, hm[l].data(), (size_t)h->lev[l].N, cudaMemcpyHostToDevice));
+            h->lev[l].m = (const unsigned char *)d;
+        }
+        void *dt = nullptr;
+        alloc(&dt, (size_t)h->tail.total);
+        for (int k = 0; k < h->tail.nt && ok; k++)
+            ok = cuda_ok(cudaMemcpy((unsigned char *)dt + h->tail.off[k], hm[h->lt + k].data(),
+                                    (size_t)h->tail.N[k], cudaMemcpyHostToDevice));
+        h->tail.m = (const unsigned char *)dt;
+        h->lev[h->lt].m = (const unsigned char *)dt;  // the tail's first level is level lt
     }
     if (h->nlev > 0) h->tail.top = h->lev[h->lt];
     const long long part_blocks = p->autotune ? max_blocks_over_shapes(p) : L.nblocks;

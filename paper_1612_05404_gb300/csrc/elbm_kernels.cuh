@@ -1046,7 +1046,8 @@ struct Launchers {
 struct MGLevel {
     int nx, ny, nz;
     long long N;
-    void *e, *b, *eps;  // level >= 1
+    void *e, *b, *eps;     // level >= 1
+    const unsigned char *m;  // level >= 1: 1 = conductor cell (correction held at 0), or NULL
 };
 
 template <typename T>
@@ -1062,6 +1063,7 @@ __global__ void __launch_bounds__(128) k_mg_smooth(Geom g, MGLevel L, int level,
     const int x = 2 * i + ((y + z + color) & 1);
     if (x >= L.nx || y >= L.ny) return;
     const ll s = x + (ll)L.nx * (y + (ll)L.ny * z);
+    if (L.m && L.m[s]) return;  // conductor cell: correction stays 0
     T *e = (T *)L.e;
     const T *b = (const T *)L.b, *ep = (const T *)L.eps;
     const T kap = T(1 << level), kb = T(2 * (1 << (2 * level))) / T((1 << level) + 1);
@@ -1096,29 +1098,31 @@ __device__ __forceinline__ typename Tr<PR>::sc mg_resid_at(const Geom &g, const 
     const ll s = x + (ll)L.nx * (y + (ll)L.ny * z);
     const int cx_[3] = {x, y, z}, n_[3] = {L.nx, L.ny, L.nz};
     if (level == 0) {
+        // the fine operator exactly as the fine smoother and residual use it
+        // (pois_nb): solid (conductor) nodes are fixed, with residual 0, and a
+        // solid neighbour enters as Dirichlet data at phi_solid
         const Cst<T> &k = cst<T>(ph);
         const T *phi = (const T *)bf.phi, *rho = (const T *)bf.rho;
         unsigned char kind = bf.mask ? bf.mask[s] : 0;
+        if (kind == ELBM_NODE_SOLID) return T(0);
         const T es = T(1) + k.kap * rho[s];
         const T ps = phi[s];
         T r = kind == ELBM_NODE_FLUID ? ((const T *)bf.q)[s] - scal_of<T>(bf, S_QMEAN) : T(0);
+        Nbr n;
+        nbr_init(n, g, x, y, z, s);
 #pragma unroll
         for (int a = 0; a < 3; a++)
 #pragma unroll
             for (int sg = -1; sg <= 1; sg += 2) {
-                int c[3] = {cx_[0], cx_[1], cx_[2]};
-                int v = nbc(c[a] + sg, n_[a], g.per[a]);
-                if (v < 0) {
-                    int face = 2 * a + (sg > 0);
-                    if (g.phi_kind[face] == ELBM_PHI_DIRICHLET) r += es * (phi_ghost<T>(g, k, face, x, y, z) - ps);
-                    continue;
-                }
-                c[a] = v;
-                ll nb = c[0] + (ll)L.nx * (c[1] + (ll)L.ny * c[2]);
-                r += T(0.5) * (es + (T(1) + k.kap * rho[nb])) * (phi[nb] - ps);
+                ll nb = 0;
+                T v = 0;
+                const int kk = pois_nb<T>(g, k, bf.mask, n, x, y, z, a, sg, &nb, &v);
+                if (kk == 0) r += T(0.5) * (es + (T(1) + k.kap * rho[nb])) * (phi[nb] - ps);
+                else if (kk == 1) r += es * (v - ps);
             }
         return r;
     }
+    if (L.m && L.m[s]) return T(0);
     const T *e = (const T *)L.e, *b = (const T *)L.b, *ep = (const T *)L.eps;
     const T kap = T(1 << level), kb = T(2 * (1 << (2 * level))) / T((1 << level) + 1);
     const T es = ep[s], xs = e[s];
@@ -1173,7 +1177,7 @@ __global__ void __launch_bounds__(128) k_mg_restrict(Geom g, Phys ph, Bufs bf, M
     ep += __shfl_down_sync(0xffffffffu, ep, 2, 8);
     ep += __shfl_down_sync(0xffffffffu, ep, 1, 8);
     if (act && c == 0) {
-        ((T *)C.b)[S] = r;
+        ((T *)C.b)[S] = (C.m && C.m[S]) ? T(0) : r;
         ((T *)C.e)[S] = T(0);
         ((T *)C.eps)[S] = ep * T(0.125);
     }
@@ -1240,6 +1244,7 @@ __global__ void __launch_bounds__(128) k_mg_prolong(Geom g, Bufs bf, MGLevel F, 
         if (bf.mask && bf.mask[s] == ELBM_NODE_SOLID) return;
         ((T *)bf.phi)[s] += acc;
     } else {
+        if (F.m && F.m[s]) return;
         ((T *)F.e)[s] += acc;
     }
 }
@@ -1306,13 +1311,15 @@ struct MGTail {
     long long total;              // cells over all tail levels
     int coarse_sweeps;
     MGLevel top;                  // global arrays of level lt
+    const unsigned char *m;       // conductor masks of the tail levels (offsets off[k]), or NULL
 };
 
 template <typename T>
-__device__ __forceinline__ T tail_resid(const Geom &g, const T *e, const T *b, const T *ep, int nx, int ny, int nz,
-                                        int level, int x, int y, int z)
+__device__ __forceinline__ T tail_resid(const Geom &g, const T *e, const T *b, const T *ep, const unsigned char *m,
+                                        int nx, int ny, int nz, int level, int x, int y, int z)
 {
     const int s = x + nx * (y + ny * z);
+    if (m && m[s]) return T(0);
     const T kap = T(1 << level), kb = T(2 * (1 << (2 * level))) / T((1 << level) + 1);
     const T es = ep[s], xs = e[s];
     T r = b[s];
@@ -1339,9 +1346,11 @@ __device__ __forceinline__ T tail_resid(const Geom &g, const T *e, const T *b, c
 // every thread owns cells of the active colour), y = ty + BY j, z = tz + BZ k;
 // no integer division, no idle half in a colour pass.
 template <typename T>
-__device__ void tail_smooth(const Geom &g, const MGTail &t, T *E, T *B, T *P, int k, int sweeps)
+__device__ void tail_smooth(const Geom &g, const MGTail &t, T *E, T *B, T *P, const unsigned char *M, int k,
+                            int sweeps)
 {
     const int nx = t.nx[k], ny = t.ny[k], nz = t.nz[k];
+    const unsigned char *m = M ? M + t.off[k] : nullptr;
     T *e = E + t.off[k];
     const T *b = B + t.off[k], *ep = P + t.off[k];
     const int level = t.lt + k;
@@ -1355,6 +1364,7 @@ __device__ void tail_smooth(const Geom &g, const MGTail &t, T *E, T *B, T *P, in
                     const int x = 2 * xi + ((y + z + color) & 1);
                     if (x >= nx) break;
                     const int s = x + nx * (y + ny * z);
+                    if (m && m[s]) continue;  // conductor cell: correction stays 0
                     const int cc[3] = {x, y, z};
                     T es = ep[s], num = b[s], den = 0;
 #pragma unroll
@@ -1386,6 +1396,7 @@ __global__ void __launch_bounds__(1024) k_mg_tail(Geom g, MGTail t, int nu)
     T *E = (T *)smem_raw;
     T *B = E + t.total;
     T *P = B + t.total;
+    unsigned char *M = t.m ? (unsigned char *)(P + t.total) : nullptr;
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
     const int nthr = blockDim.x * blockDim.y * blockDim.z;
     for (int s = tid; s < (int)t.N[0]; s += nthr) {
@@ -1393,6 +1404,8 @@ __global__ void __launch_bounds__(1024) k_mg_tail(Geom g, MGTail t, int nu)
         B[s] = ((const T *)t.top.b)[s];
         P[s] = ((const T *)t.top.eps)[s];
     }
+    if (M)
+        for (int s = tid; s < (int)t.total; s += nthr) M[s] = t.m[s];
     __syncthreads();
     for (int k = 1; k < t.nt; k++) {  // coarse permittivities: mean of 8 children
         const int nx = t.nx[k], ny = t.ny[k], nz = t.nz[k], fx = t.nx[k - 1], fy = t.ny[k - 1];
@@ -1409,7 +1422,7 @@ __global__ void __launch_bounds__(1024) k_mg_tail(Geom g, MGTail t, int nu)
     }
     // down: smooth, restrict
     for (int k = 0; k + 1 < t.nt; k++) {
-        tail_smooth<T>(g, t, E, B, P, k, nu);
+        tail_smooth<T>(g, t, E, B, P, M, k, nu);
         const int nx = t.nx[k + 1], ny = t.ny[k + 1], nz = t.nz[k + 1];
         const int fx = t.nx[k], fy = t.ny[k], fz = t.nz[k];
         for (int Z = threadIdx.z; Z < nz; Z += blockDim.z)
@@ -1417,15 +1430,16 @@ __global__ void __launch_bounds__(1024) k_mg_tail(Geom g, MGTail t, int nu)
                 for (int X = threadIdx.x; X < nx; X += blockDim.x) {
                     T sum = 0;
                     for (int c = 0; c < 8; c++)
-                        sum += tail_resid<T>(g, E + t.off[k], B + t.off[k], P + t.off[k], fx, fy, fz, t.lt + k,
-                                             2 * X + (c & 1), 2 * Y + ((c >> 1) & 1), 2 * Z + (c >> 2));
+                        sum += tail_resid<T>(g, E + t.off[k], B + t.off[k], P + t.off[k], M ? M + t.off[k] : nullptr,
+                                             fx, fy, fz, t.lt + k, 2 * X + (c & 1), 2 * Y + ((c >> 1) & 1),
+                                             2 * Z + (c >> 2));
                     const int S = X + nx * (Y + ny * Z);
-                    B[t.off[k + 1] + S] = sum;
+                    B[t.off[k + 1] + S] = (M && M[t.off[k + 1] + S]) ? T(0) : sum;
                     E[t.off[k + 1] + S] = T(0);
                 }
         __syncthreads();
     }
-    tail_smooth<T>(g, t, E, B, P, t.nt - 1, t.coarse_sweeps);
+    tail_smooth<T>(g, t, E, B, P, M, t.nt - 1, t.coarse_sweeps);
     // up: prolong (trilinear), smooth
     for (int k = t.nt - 2; k >= 0; k--) {
         const int nx = t.nx[k], ny = t.ny[k], nz = t.nz[k];
@@ -1456,10 +1470,11 @@ __global__ void __launch_bounds__(1024) k_mg_tail(Geom g, MGTail t, int nu)
                         int X = ax ? i1[0] : i0[0], Y = ay ? i1[1] : i0[1], Z = az ? i1[2] : i0[2];
                         acc += w * ec[X + nc[0] * (Y + nc[1] * Z)];
                     }
-                    E[t.off[k] + fx_ + nx * (fy_ + ny * fz_)] += acc;
+                    const int fs = fx_ + nx * (fy_ + ny * fz_);
+                    if (!(M && M[t.off[k] + fs])) E[t.off[k] + fs] += acc;
                 }
         __syncthreads();
-        tail_smooth<T>(g, t, E, B, P, k, nu);
+        tail_smooth<T>(g, t, E, B, P, M, k, nu);
     }
     for (int s = tid; s < (int)t.N[0]; s += nthr) ((T *)t.top.e)[s] = E[s];
 }
@@ -1523,7 +1538,7 @@ struct MGLaunchers {
     }
     static void tail_(const Geom &g, const MGTail &t, int nu, cudaStream_t s)
     {
-        size_t sm = 3 * (size_t)t.total * sizeof(sc);
+        size_t sm = 3 * (size_t)t.total * sizeof(sc) + (t.m ? (size_t)t.total : 0);
         k_mg_tail<sc><<<1, tail_block(t.nx[0], t.ny[0], t.nz[0]), sm, s>>>(g, t, nu);
     }
     static MGOps table()

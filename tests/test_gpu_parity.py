@@ -162,6 +162,23 @@ def test_fp64_nozzle_inlet_outlet_xi_charge(E):
     compare_fp64(g, o, cfg)
 
 
+def test_fp64_nozzle_multigrid_with_conductor_nodes(E):
+    """Multigrid on a geometry with interior solid (conductor) nodes, against
+    the oracle's SOR solution of the same operator (1e-10, as the other
+    multigrid parity cases)."""
+    cfg, fields = W.jet(shape=(16, 16, 20), nozzle_r=3, wall=1, nozzle_len=5, precision="fp64")
+    _tight(cfg, "mg")
+    g = E.Sim(cfg, fields)
+    o = oracle.Sim(cfg, fields)
+    for _ in range(3):
+        assert g.step(1) == 0  # converged (no Poisson cap warning)
+        o.step(1)
+        d = g.diag()
+        assert d["poisson_resid"] <= 1e-13, d
+    print("phi", rel_inf(g.get("phi"), o.phi), "cycles", d["poisson_sweeps"])
+    compare_fp64(g, o, cfg, tol=1e-10)
+
+
 def test_fp64_multi_step_drop(E):
     cfg, fields = W.charged_drop_at_rest(n=16, radius=4.0)
     _tight(cfg)
