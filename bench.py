@@ -58,6 +58,23 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(ms, device):
+    """The slowest rank's time of the timed region (every rank the same
+    number of units): all-reduce MAX over the default process group (NCCL on
+    the GPUs; any backend whose tensors live on `device`)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(units_per_rank, world, ms_max):
+    """Whole-job throughput: every rank's replicas (weak scaling, no data-path
+    collective) over the slowest rank's time."""
+    return units_per_rank * world / (ms_max * 1e-3) / 1e6
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -232,9 +249,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     total_ms = sum(times)
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, "cuda")
         dist.barrier()
     diag = [s.diag() for s in sims]
     if args.launch == "batch":
@@ -243,8 +258,7 @@ def run_ours(args, rank, world, local_rank):
         pool.shutdown()
     for s in sims:
         s.close()
-    units = world * len(sims) * N * args.steps
-    value = units / (total_ms * 1e-3) / 1e6
+    value = job_mlups(len(sims) * N * args.steps, world, total_ms)
 
     # the collision kernel alone: one lattice (E0 = 1e-3), each pass timed with
     # CUDA events on its stream (three section graphs per step)
