@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--workload", default="drop64", choices=["drop64"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--alpha-precision", default="fp32", choices=["fp64", "fp32", "fp32_fast"])
+    ap.add_argument("--alpha-mode", default="entropic", choices=["entropic", "bgk"],
+                    help="bgk: alpha = 2 (the method without its entropic step; for cost attribution)")
     ap.add_argument("--instances", type=int, default=4, help="lattices per step (E0 sweep values)")
     ap.add_argument("--no-graph", action="store_true", help="issue each step from the host (profilers see every launch)")
     ap.add_argument("--launch", default="batch", choices=["batch", "streams"],
@@ -89,7 +91,7 @@ def workload_cfgs(args):
     out = []
     for E0 in W.E0_SWEEP[len(W.E0_SWEEP) - args.instances:]:
         cfg, fields = W.drop_in_field(E0=E0, precision=args.precision)
-        cfg.update(alpha_precision=args.alpha_precision, store_macro=0, diag_every=1,
+        cfg.update(alpha_precision=args.alpha_precision, alpha_mode=args.alpha_mode, store_macro=0, diag_every=1,
                    poisson_check_every=8, graph=0 if args.no_graph else 1)
         out.append((cfg, fields))
     return out

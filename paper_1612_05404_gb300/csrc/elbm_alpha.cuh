@@ -329,7 +329,8 @@ __device__ __forceinline__ void alpha_fp32_setup(const float *f, const float *d,
 // the warp leaves together. The residual carried to the guard test is the
 // evaluated |h| or, after an accepted step, the predicted h''/2 d^2.
 __device__ __forceinline__ AlphaOutF alpha_fp32_solve(const float *f, const float *d, float rho,
-                                                      const AlphaSetupF &st, bool guard, float a_start)
+                                                      const AlphaSetupF &st, bool guard, float a_start,
+                                                      bool defer_guard = false)
 {
     AlphaOutF o;
     o.alpha = 2.f; o.alpha_lo = 0.f; o.herr = 0.f; o.status = st.status; o.guarded = 0; o.iters = 0;
@@ -390,6 +391,10 @@ __device__ __forceinline__ AlphaOutF alpha_fp32_solve(const float *f, const floa
     if (!guard || o.status == 3) return o;
     const float tol = 1e-10f * rho;
     const bool need = !(hres + bound <= 0.5f * tol);
+    if (need && defer_guard) {  // the caller runs alpha_guard (compacted) and fills in the result
+        o.guarded = 2;
+        return o;
+    }
     if (need) {
         o.guarded = 1;
         const float4 gr = alpha_guard(f, d, rho, a);

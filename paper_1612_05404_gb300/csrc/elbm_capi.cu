@@ -22,6 +22,8 @@ using namespace elbm;
 namespace {
 constexpr int kMaxLevels = 10;
 constexpr int kNu = 2;             // pre- and post-smoothing sweeps
+constexpr int kNuTail = 1;         // the same on the levels of the one-CTA tail (reduced precision;
+                                   // FP64 solves to 1e-13 keep kNu)
 constexpr int kCoarseSweeps = 8;   // red-black sweeps on the coarsest level (<= 8 cells per axis pair)
 }
 
@@ -297,7 +299,7 @@ int vcycle(elbm_handle *h, const Bufs &b, cudaStream_t s, int l)
 {
     const MGOps &m = h->mg;
     if (l == h->lt) {
-        m.tail(h->g, h->tail, kNu, s);
+        m.tail(h->g, h->tail, h->p.precision == ELBM_PREC_FP64 ? kNu : kNuTail, s);
         return 1;
     }
     for (int i = 0; i < kNu; i++) {

@@ -545,6 +545,18 @@ __global__ void k_phi_shift(Geom g, Bufs b)
 // (carreau), (beta); exact-difference source Eq. (add); write f*; in
 // transport mode the D3Q7 charge update. Optional diagnostics per block.
 // ===========================================================================
+// Guarded FP32 alpha: lanes whose root needs the float-float guard queue their
+// inputs in shared memory; after a barrier the block's first threads run the
+// queued guards together (full warps instead of a few lanes in many warps),
+// and the results return through the queue. Beyond kGuardQ queued lanes a
+// lane runs its guard itself.
+constexpr int kGuardQ = 128;
+struct GuardEntry {
+    float f[Q], d[Q];
+    float rho, a;
+    float4 res;
+};
+
 template <int PR, int AP>
 __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC_FP64) ? 1 : 4) k_collide(Geom g, Phys ph, Bufs b, int diag)
 {
@@ -553,6 +565,14 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
     typedef typename T::sc sc;
     typedef typename T::st st;
     typedef typename T::gt gt;
+    constexpr bool kQueue = AP == ELBM_APREC_FP32 && sizeof(ct) == 4;
+    __shared__ GuardEntry gq[kQueue ? kGuardQ : 1];
+    __shared__ int gq_n;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    if (kQueue) {
+        if (tid == 0) gq_n = 0;
+        __syncthreads();
+    }
     int x, y, z;
     bool inb;
     ll s;
@@ -561,15 +581,22 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
     ct dm = 0, dmx = 0, dmy = 0, dmz = 0, dq = 0, dasum = 0;
     unsigned dnfl = 0, dsh = 0, dnr = 0, dcl = 0, dbad = 0, dgd = 0, dgf = 0, dlf = 0;
     float damin = 1e30f, damax = -1e30f, dherr = 0.f, dumax = 0.f;
+    // the first part's results, carried across the block-level guard section
+    Nbr n;
+    ct f[Q], D[Q];
+    ct r = 0, drho = 0, jx = 0, jy = 0, jz = 0, Fx = 0, Fy = 0, Fz = 0, qs = 0;
+    ct ir = 0, ux = 0, uy = 0, uz = 0, usq = 0;
+    ct alpha = ct(2);
+    float a_herr = 0.f;
+    int a_status = 0, a_guard = 0, a_lfall = 0;
+    int gslot = -1;
     if (active) {
-        Nbr n;
         nbr_init(n, g, x, y, z, s);
         const sc *rho = (const sc *)b.rho;
         const sc *phi = (const sc *)b.phi;
-        ct f[Q];
 #pragma unroll
         for (int p = 0; p < Q; p++) f[p] = gather_pop<PR>(g, b.mask, b.fA, n, p);
-        ct rs = 0, jx = 0, jy = 0, jz = 0;
+        ct rs = 0;
 #pragma unroll
         for (int p = 0; p < Q; p++) {
             rs += f[p];
@@ -577,8 +604,8 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
             jy += ct(cy(p)) * f[p];
             jz += ct(cz(p)) * f[p];
         }
-        const ct r = T::dev ? ct(1) + rs : rs;
-        const ct drho = T::dev ? rs : rs - ct(1);
+        r = T::dev ? ct(1) + rs : rs;
+        drho = T::dev ? rs : rs - ct(1);
 
         const Cst<ct> &k = cst<ct>(ph);
         // Eq. (sc): F_int = -G psi(r) sum_fluid w psi(r+c) c - G_w psi(r) sum_wall w psi(r) c
@@ -593,12 +620,11 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
             if (wall) { swx += wv * ct(cx(p)); swy += wv * ct(cy(p)); swz += wv * ct(cz(p)); }
             else { sfx += wv * ct(cx(p)); sfy += wv * ct(cy(p)); sfz += wv * ct(cz(p)); }
         }
-        ct Fx = -k.G * ps * sfx - k.Gw * ps * swx;
-        ct Fy = -k.G * ps * sfy - k.Gw * ps * swy;
-        ct Fz = -k.G * ps * sfz - k.Gw * ps * swz;
+        Fx = -k.G * ps * sfx - k.Gw * ps * swx;
+        Fy = -k.G * ps * sfy - k.Gw * ps * swy;
+        Fz = -k.G * ps * sfz - k.Gw * ps * swz;
 
         // electric force q E, E = -grad phi (central differences) + E_ext
-        ct qs = 0;
         if (ph.charge_model != ELBM_CHARGE_NONE) {
             qs = ct(((const sc *)b.q)[s]);
             ct E[3];
@@ -621,10 +647,9 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
         }
 
         // Eq. (2) at the bare velocity, Delta = f^eq - f
-        const ct ir = ct(1) / r;
-        const ct ux = jx * ir, uy = jy * ir, uz = jz * ir;
-        const ct usq = ux * ux + uy * uy + uz * uz;
-        ct D[Q];
+        ir = ct(1) / r;
+        ux = jx * ir; uy = jy * ir; uz = jz * ir;
+        usq = ux * ux + uy * uy + uz * uz;
 #pragma unroll
         for (int p = 0; p < Q; p++) {
             ct P = Ppoly<ct>(p, ux, uy, uz, usq);
@@ -632,9 +657,6 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
         }
 
         // Eq. (entropic)
-        ct alpha = ct(2);
-        float a_herr = 0.f;
-        int a_status = 0, a_guard = 0, a_lfall = 0;
         if (ph.alpha_mode != ELBM_ALPHA_BGK) {
             if (sizeof(ct) == 8 || AP == ELBM_APREC_FP64) {
                 double fd[Q], dd[Q];
@@ -662,15 +684,52 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
                 const bool learned = ph.alpha_mode == ELBM_ALPHA_LEARNED;
                 if (learned && ast.S >= 0x1p-5f)
                     a_start = ast.ac + ast.S * ast.S * ast.S * float(((const sc *)b.alpha)[s]);
-                AlphaOutF ao = alpha_fp32_solve(ff, dd, float(r), ast, AP == ELBM_APREC_FP32, a_start);
+                AlphaOutF ao = alpha_fp32_solve(ff, dd, float(r), ast, AP == ELBM_APREC_FP32, a_start, kQueue);
                 alpha = ct(ao.alpha);
                 a_herr = ao.herr;
                 a_status = ao.status;
                 a_guard = ao.guarded;
                 a_lfall = learned && ao.status == 0 && ao.iters > 1;
+                if (kQueue && ao.guarded == 2) {
+                    a_guard = 1;
+                    gslot = atomicAdd(&gq_n, 1);
+                    if (gslot < kGuardQ) {
+                        GuardEntry &e = gq[gslot];
+#pragma unroll
+                        for (int p = 0; p < Q; p++) {
+                            e.f[p] = ff[p];
+                            e.d[p] = dd[p];
+                        }
+                        e.rho = float(r);
+                        e.a = ao.alpha;
+                    } else {  // queue full: this lane's guard runs here
+                        const float4 gr = alpha_guard(ff, dd, float(r), ao.alpha);
+                        alpha = ct(gr.x);
+                        if (gr.w != 0.f) a_herr = gr.z;
+                        else a_status = 4;  // not certified: the FP32 report stays
+                        gslot = -1;
+                    }
+                }
             }
         }
-
+    }
+    if (kQueue) {
+        __syncthreads();
+        const int nq = gq_n < kGuardQ ? gq_n : kGuardQ;
+        if (tid < nq) gq[tid].res = alpha_guard(gq[tid].f, gq[tid].d, gq[tid].rho, gq[tid].a);
+        __syncthreads();
+        if (gslot >= 0) {
+            const float4 gr = gq[gslot].res;
+            alpha = ct(gr.x);
+            if (gr.w != 0.f) a_herr = gr.z;
+            else a_status = 4;  // not certified: the FP32 report stays
+        }
+    }
+    if (active) {
+        const sc *rho = (const sc *)b.rho;
+        const sc *phi = (const sc *)b.phi;
+        const Cst<ct> &k = cst<ct>(ph);
+        const ct rho0 = k.rho0;
         // Eq. (stress): Pi = sum (f - f^eq) c c = -sum D c c; 2-norm; Carreau; Eq. (beta)
         ct nu = k.nu0;
         if (!ph.newtonian) {
