@@ -166,6 +166,16 @@ __device__ __forceinline__ ffl ff_log1p(ffl y)
     return l;
 }
 
+// ln(1+z) for |z| <= 1/8: z - z^2/2 in float-float, the tail z^3 R3(z),
+// R3 = 1/3 - z/4 + z^2/5 - ... (8 terms; below 3 % of ln), in FP32
+__device__ __forceinline__ ffl ff_log1p_small(ffl z)
+{
+    const ffl z2 = ff_mul(z, z);
+    const float zh = z.h;
+    const float R3 = 1.f / 3 + zh * (-1.f / 4 + zh * (1.f / 5 + zh * (-1.f / 6 + zh * (1.f / 7 + zh * (-1.f / 8 + zh * (1.f / 9 + zh * (-1.f / 10)))))));
+    return ff_add_f(ff_add(z, ffl{-0.5f * z2.h, -0.5f * z2.l}), z2.h * zh * R3);
+}
+
 // h'(0) in float-float: (1 + ln r) sum D + sum D_p ln(f_p / (w_p r)); 1/w_p is
 // the integer 3, 18 or 36, so f_p / (w_p r) = (f_p / w_p) / r exactly as pairs.
 // The guard's loops are not unrolled: compact code for a path few warps take.
@@ -177,7 +187,9 @@ __device__ __forceinline__ ffl h0_ff(const float *f, const float *d, float r)
         S = ff_add_f(S, d[p]);
         const float iw = p == 0 ? 3.f : (p < 7 ? 18.f : 36.f);
         const ffl z = ff_add_f(ff_div(ff_prod(f[p], iw), ffl{r, 0.f}), -1.f);
-        T = ff_add(T, ff_mul_f(ff_log1p(z), d[p]));
+        // warp-uniform choice: a warp whose lanes disagree would run both paths
+        const ffl l = __all_sync(__activemask(), fabsf(z.h) <= 0.125f) ? ff_log1p_small(z) : ff_log1p(z);
+        T = ff_add(T, ff_mul_f(l, d[p]));
     }
     // ln r to FP32 accuracy suffices: sum D is at the rounding level of rho
     return ff_add(ff_mul_f(S, 1.f + logf(r)), T);
@@ -207,22 +219,92 @@ __device__ __forceinline__ void h_ff(const float *f, const float *d, ffl a, ffl 
     *hpp = g2;
 }
 
+// h(a) from the site's moments when |a x_p| <= 1/16 for every p: the series
+// phi(y) = y^2/2 - y^3/6 + sum_{n>=4} (-1)^n y^n / (n (n-1)) summed over p gives
+//   h(a) = a h'(0) + a^2 M2/2 - a^3 M3/6 + sum_{n=4}^{8} (-1)^n a^n M_n/(n(n-1)),
+// M_n = sum_p f_p x_p^n. M2 and M3 in float-float, M4..M8 in FP32 (their terms
+// are below 1/1000 of the M2 term); truncation after n = 8 leaves below
+// 1e-10 of the M2 term. The moments do not depend on a, so each Newton step
+// of the guard costs a few dozen operations instead of 19 float-float logs.
+struct MomFF {
+    ffl M2, M3;
+    float Mh[9];  // Mh[n], n = 4..8
+    float xmax;
+};
+
+__device__ __forceinline__ void mom_ff(const float *f, const float *d, MomFF &m)
+{
+    m.M2 = ffl{0.f, 0.f};
+    m.M3 = ffl{0.f, 0.f};
+#pragma unroll
+    for (int n = 0; n < 9; n++) m.Mh[n] = 0.f;
+    m.xmax = 0.f;
+#pragma unroll 1
+    for (int p = 0; p < Q; p++) {
+        const ffl x = ff_div_f(d[p], f[p]);
+        const ffl fx2 = ff_mul_f(ff_mul(x, x), f[p]);
+        const ffl fx3 = ff_mul_f(fx2, x.h);
+        m.M2 = ff_add(m.M2, fx2);
+        m.M3 = ff_add(m.M3, fx3);
+        float t = fx3.h;
+#pragma unroll
+        for (int n = 4; n <= 8; n++) {
+            t *= x.h;
+            m.Mh[n] += t;
+        }
+        m.xmax = fmaxf(m.xmax, fabsf(x.h));
+    }
+}
+
+__device__ __forceinline__ ffl h_mom(ffl a, ffl a0, const MomFF &m, float *hp, float *hpp)
+{
+    const ffl a2 = ff_mul(a, a);
+    const ffl a3 = ff_mul(a2, a);
+    ffl h = ff_mul(a, a0);
+    const ffl t2 = ff_mul(a2, m.M2);
+    h = ff_add(h, ffl{0.5f * t2.h, 0.5f * t2.l});
+    // 1/6 = 0x1.555556p-3 - 0x1.555556p-28 (+ below 2^-51)
+    const ffl t3 = ff_mul(ff_mul(a3, m.M3), ffl{0x1.555556p-3f, -0x1.555556p-28f});
+    h = ff_add(h, ff_neg(t3));
+    const float ah = a.h;
+    float tail = 0.f, d1 = 0.f, d2 = 0.f;
+#pragma unroll
+    for (int n = 8; n >= 4; n--) {
+        const float cn = ((n & 1) ? -1.f : 1.f) / float(n * (n - 1));
+        tail = fmaf(tail, ah, cn * m.Mh[n]);
+        d1 = fmaf(d1, ah, float(n) * cn * m.Mh[n]);
+        d2 = fmaf(d2, ah, float(n * (n - 1)) * cn * m.Mh[n]);
+    }
+    const float a_2 = ah * ah;
+    h = ff_add_f(h, tail * a_2 * a_2);
+    *hp = a0.h + ah * m.M2.h - 0.5f * a_2 * m.M3.h + d1 * a_2 * ah;
+    *hpp = m.M2.h - ah * m.M3.h + d2 * a_2;
+    return h;
+}
+
 // The float-float guard from an FP32 root a: h'(0) and h(a) as pairs; accept
 // when |h| <= tol/2, else one Newton step a' = a - h/h' and accept a' when the
 // quadratic-convergence bound 3/4 h'' (a' - a)^2 plus 1e-11 rho (the pairs'
 // evaluation error) is within tol/2, else evaluate again (at most 3 steps).
 // Returns (alpha high, alpha low, H-error, accepted). Not inlined: one copy of
 // the code, entered only by warps that hold a site needing it.
-static __device__ __noinline__ float4 alpha_guard(const float *f, const float *d, float rho, float a)
+static __device__ __noinline__ float4 alpha_guard(const float *f, const float *d, float rho, float a, float S)
 {
     const float tol = 1e-10f * rho;
     const ffl A0 = h0_ff(f, d, rho);
+    // the moment series only where it holds (S = max |Delta/f| of the FP32
+    // setup, with margin), chosen for the whole warp
+    const bool use_mom = __all_sync(__activemask(), a * S <= 0.06f);
+    MomFF mom;
+    mom.xmax = 1e30f;
+    if (use_mom) mom_ff(f, d, mom);
     ffl al = {a, 0.f};
 #pragma unroll 1
     for (int it = 0; it < 3; it++) {
         ffl hf;
         float hp, hpp;
-        h_ff(f, d, al, A0, &hf, &hp, &hpp);
+        if (__all_sync(__activemask(), al.h * mom.xmax <= 0.0625f)) hf = h_mom(al, A0, mom, &hp, &hpp);
+        else h_ff(f, d, al, A0, &hf, &hp, &hpp);
         if (fabsf(hf.h) <= 0.5f * tol) return make_float4(al.h, al.l, fabsf(hf.h) / rho, 1.f);
         const float delta = hf.h / hp;
         al = ff_add_f(al, -delta);
@@ -397,7 +479,7 @@ __device__ __forceinline__ AlphaOutF alpha_fp32_solve(const float *f, const floa
     }
     if (need) {
         o.guarded = 1;
-        const float4 gr = alpha_guard(f, d, rho, a);
+        const float4 gr = alpha_guard(f, d, rho, a, st.S);
         o.alpha = gr.x;
         o.alpha_lo = gr.y;
         o.herr = gr.z;

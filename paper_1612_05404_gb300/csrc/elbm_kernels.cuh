@@ -553,7 +553,7 @@ __global__ void k_phi_shift(Geom g, Bufs b)
 constexpr int kGuardQ = 128;
 struct GuardEntry {
     float f[Q], d[Q];
-    float rho, a;
+    float rho, a, S;
     float4 res;
 };
 
@@ -702,8 +702,9 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
                         }
                         e.rho = float(r);
                         e.a = ao.alpha;
+                        e.S = ast.S;
                     } else {  // queue full: this lane's guard runs here
-                        const float4 gr = alpha_guard(ff, dd, float(r), ao.alpha);
+                        const float4 gr = alpha_guard(ff, dd, float(r), ao.alpha, ast.S);
                         alpha = ct(gr.x);
                         if (gr.w != 0.f) a_herr = gr.z;
                         else a_status = 4;  // not certified: the FP32 report stays
@@ -716,7 +717,7 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
     if (kQueue) {
         __syncthreads();
         const int nq = gq_n < kGuardQ ? gq_n : kGuardQ;
-        if (tid < nq) gq[tid].res = alpha_guard(gq[tid].f, gq[tid].d, gq[tid].rho, gq[tid].a);
+        if (tid < nq) gq[tid].res = alpha_guard(gq[tid].f, gq[tid].d, gq[tid].rho, gq[tid].a, gq[tid].S);
         __syncthreads();
         if (gslot >= 0) {
             const float4 gr = gq[gslot].res;
