@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="issue each step from the host (profilers see every launch)")
     ap.add_argument("--launch", default="batch", choices=["batch", "streams"],
                     help="batch: all lattices in one graph per step; streams: one graph per lattice per stream")
+    ap.add_argument("--pipeline", default="on", choices=["on", "off"],
+                    help="batch: odd-position lattices run half a step ahead (ELBM_BATCH_PIPELINE)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-alpha-compare", action="store_true",
@@ -208,7 +210,7 @@ def run_ours(args, rank, world, local_rank):
         for c, _ in cfgs:
             c.update(autotune=1, profile=0)
         sims = [elbm.Sim(c, f) for c, f in cfgs]
-        batch = elbm.Batch(sims)
+        batch = elbm.Batch(sims, pipeline=args.pipeline == "on")
         step_all = lambda: batch.step(1)
         streams = None
     else:
@@ -296,6 +298,7 @@ def run_ours(args, rank, world, local_rank):
                    "poisson": "multigrid V(2,2), red-black Gauss-Seidel, tol 1e-6 (FP32 floor stop), warm start extrapolated from the two previous potentials",
                    "poisson_vcycles_per_step": sweeps / max(args.steps, 1) / len(sims),
                    "launch": ("one CUDA graph per step for all lattices (batch), autotuned block shapes"
+                              + (", odd lattices half a step ahead" if args.pipeline == "on" else "")
                               if args.launch == "batch" else "one graph per lattice on concurrent streams"),
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak,
@@ -514,7 +517,7 @@ def batched_compare(args):
     t_init = time.perf_counter() - t0
     sites = sum(e ** 3 for e, _, _ in params)
     t0 = time.perf_counter()
-    batch = elbm.Batch(sims)
+    batch = elbm.Batch(sims, pipeline=args.pipeline == "on")
     t_capture = time.perf_counter() - t0
     batch.step(args.warmup)
     torch.cuda.synchronize()
@@ -543,7 +546,7 @@ def batched_compare(args):
         s.close()
     return {"boxes": len(params), "sites": sites, "edges": sorted(set(e for e, _, _ in params)),
             "batched": {"mlups": sites / (ms_b * 1e-3) / 1e6, "ms_per_step": ms_b, "max_h_error_device": hmax_b,
-                        "graph_launches_per_step": 1},
+                        "graph_launches_per_step": 1, "pipelined": args.pipeline == "on"},
             "one_at_a_time": {"mlups": sites / (single_ms * 1e-3) / 1e6, "ms_per_step": single_ms,
                               "max_h_error_device": hmax_s},
             "speedup_batched_vs_single": single_ms / ms_b,

@@ -193,6 +193,9 @@ size_t elbm_fields_size(const elbm_handle *h, unsigned mask);
  * the paper's method: instrumentation for measuring the method's kernels. */
 elbm_status elbm_pass_times(const elbm_handle *h, double *out, int n);
 
+/* elbm_batch_create flags */
+#define ELBM_BATCH_PIPELINE 1 /* instances at odd positions run half a step ahead */
+
 /* Batched lattices (not in the paper: an execution form). One batch handle
  * advances n existing instance handles (each made by elbm_init, with
  * diag_every = 1 and profile = 0) by one CUDA graph launch per step: each
@@ -203,12 +206,22 @@ elbm_status elbm_pass_times(const elbm_handle *h, double *out, int n);
  *          keeps the pointers: free the batch before its instances, and step
  *          the instances only through the batch while it exists (elbm_step
  *          on the batch returns ELBM_E_STATE if one was stepped alone);
+ *   flags  0, or ELBM_BATCH_PIPELINE: each graph launch runs the instances
+ *          at odd positions half a step ahead (their collision of the step,
+ *          then the moments and potential solve of the next), so that the
+ *          latency-bound potential solves of one half overlap the collisions
+ *          of the other. The populations and the step counter of every
+ *          instance are as without the flag; an instance running ahead holds
+ *          the density, charge and potential of the populations it stores
+ *          (one step later than an instance not ahead). Its first moments
+ *          and solve run once here. After the batch is freed, such an
+ *          instance stepped alone repeats that solve (warm-started);
  *   stream cudaStream_t on which elbm_step(batch) launches the graph.
  * elbm_step(batch, k) advances every instance k steps and returns the worst
  * status of the instances (non-finite state, Poisson non-convergence);
  * elbm_fields and elbm_pass_times on a batch return ELBM_E_STATE (read each
  * instance); elbm_free(batch) frees the batch only. */
-elbm_status elbm_batch_create(elbm_handle *const *inst, int n, void *stream, elbm_handle **out);
+elbm_status elbm_batch_create(elbm_handle *const *inst, int n, int flags, void *stream, elbm_handle **out);
 
 /* The entropic alpha of Eq. (entropic) for n independent sites outside a
  * simulation: the root the collision step computes, for checking its H-error

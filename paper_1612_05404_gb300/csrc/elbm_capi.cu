@@ -63,6 +63,7 @@ struct elbm_handle {
     cudaGraphExec_t bexec[2];  // all instances' steps, one graph per A/B parity
     cudaEvent_t ev_fork;
     cudaEvent_t *ev_join;
+    int pipe;                  // ELBM_BATCH_PIPELINE: odd positions run half a step ahead
 };
 
 namespace {
@@ -495,8 +496,13 @@ bool capture_step(elbm_handle *h, int parity, cudaGraphExec_t *out, int sections
 }
 
 // The batch's step for one A/B parity: every instance's step as a parallel
-// branch (fork from one event, join into the batch's capture stream).
-bool capture_batch(elbm_handle *B, int parity, cudaGraphExec_t *out)
+// branch (fork from one event, join into the batch's capture stream). With
+// pipelining, an instance at an odd position runs its collision of this step
+// and then the moments and potential solve of the next one, so that its
+// latency-bound solve overlaps the other instances' collisions and the
+// reverse; its prologue (prologue = true) is the first step's moments and
+// solve alone.
+bool capture_batch(elbm_handle *B, int parity, cudaGraphExec_t *out, bool prologue = false)
 {
     cudaStream_t s = B->cap;
     cudaGraph_t graph = nullptr;
@@ -505,11 +511,21 @@ bool capture_batch(elbm_handle *B, int parity, cudaGraphExec_t *out)
     int n_pre = 0, n_body = 0, n_post = 0;
     for (int i = 0; i < B->n_sub && ok; i++) {
         elbm_handle *h = B->sub[i];
+        const bool ahead = B->pipe && (i & 1);
+        if (prologue && !ahead) continue;
         ok = cuda_ok(cudaStreamWaitEvent(h->cap, B->ev_fork, 0));
-        ok = ok && enqueue_step(h, parity, h->cap, 7, n_pre, n_body, n_post);
+        if (prologue) {
+            ok = ok && enqueue_step(h, parity, h->cap, 3, n_pre, n_body, n_post);
+        } else if (ahead) {
+            ok = ok && enqueue_step(h, parity, h->cap, 4, n_pre, n_body, n_post);
+            ok = ok && enqueue_step(h, parity ^ 1, h->cap, 3, n_pre, n_body, n_post);
+        } else {
+            ok = ok && enqueue_step(h, parity, h->cap, 7, n_pre, n_body, n_post);
+        }
         ok = ok && cuda_ok(cudaEventRecord(B->ev_join[i], h->cap));
         ok = ok && cuda_ok(cudaStreamWaitEvent(s, B->ev_join[i], 0));
     }
+    if (prologue) parity = 1;  // kernel counts belong to the steady graphs
     ok = cuda_ok(cudaStreamEndCapture(s, &graph)) && ok;
     if (ok) ok = cuda_ok(cudaGraphInstantiate(out, graph, 0));
     if (graph) cudaGraphDestroy(graph);
@@ -885,11 +901,11 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     return ELBM_OK;
 }
 
-elbm_status elbm_batch_create(elbm_handle *const *inst, int n, void *stream, elbm_handle **out)
+elbm_status elbm_batch_create(elbm_handle *const *inst, int n, int flags, void *stream, elbm_handle **out)
 {
     if (!out) return ELBM_E_INVAL;
     *out = nullptr;
-    if (!inst || n < 1) return ELBM_E_INVAL;
+    if (!inst || n < 1 || (flags & ~ELBM_BATCH_PIPELINE)) return ELBM_E_INVAL;
     for (int i = 0; i < n; i++) {
         if (!inst[i] || inst[i]->n_sub > 0) return ELBM_E_INVAL;
         if (inst[i]->p.diag_every != 1 || inst[i]->p.profile) return ELBM_E_INVAL;
@@ -901,6 +917,7 @@ elbm_status elbm_batch_create(elbm_handle *const *inst, int n, void *stream, elb
     std::memset(B, 0, sizeof(*B));
     B->s = (cudaStream_t)stream;
     B->n_sub = n;
+    B->pipe = (flags & ELBM_BATCH_PIPELINE) && n > 1;
     B->sub = new (std::nothrow) elbm_handle *[n];
     B->sub_step0 = new (std::nothrow) long long[n];
     B->ev_join = new (std::nothrow) cudaEvent_t[n]();
@@ -916,6 +933,12 @@ elbm_status elbm_batch_create(elbm_handle *const *inst, int n, void *stream, elb
     ok = ok && cuda_ok(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
     ok = ok && cuda_ok(cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming));
     ok = ok && capture_batch(B, 0, &B->bexec[0]) && capture_batch(B, 1, &B->bexec[1]);
+    if (ok && B->pipe) {  // the odd positions' first moments and potential solve, once
+        cudaGraphExec_t pro = nullptr;
+        ok = capture_batch(B, 0, &pro, true);
+        ok = ok && cuda_ok(cudaGraphLaunch(pro, B->s)) && cuda_ok(cudaStreamSynchronize(B->s));
+        if (pro) cudaGraphExecDestroy(pro);
+    }
     if (!ok) {
         cudaGetLastError();
         elbm_free(B);

@@ -112,7 +112,7 @@ def lib():
         L.elbm_density_noalloc.restype = ctypes.c_int
         L.elbm_alpha_eval.argtypes = [vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_double, vp, vp, vp, vp, vp, vp]
         L.elbm_alpha_eval.restype = ctypes.c_int
-        L.elbm_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]
+        L.elbm_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(vp)]
         L.elbm_batch_create.restype = ctypes.c_int
         ll, f = ctypes.c_longlong, ctypes.c_float
         L.elbm_alpha_features.argtypes = [vp, ll, vp, vp, vp]
@@ -393,12 +393,12 @@ class Batch:
     (elbm_batch_create). The batch keeps references to its Sim instances; step
     them only through the batch; read fields from each instance."""
 
-    def __init__(self, sims, stream=None):
+    def __init__(self, sims, pipeline=False, stream=None):
         self.sims = list(sims)
         arr = (ctypes.c_void_p * len(self.sims))(*[s.h.value for s in self.sims])
         h = ctypes.c_void_p()
-        rc = lib().elbm_batch_create(arr, len(self.sims), stream if stream is not None else _cur_stream(),
-                                     ctypes.byref(h))
+        rc = lib().elbm_batch_create(arr, len(self.sims), 1 if pipeline else 0,
+                                     stream if stream is not None else _cur_stream(), ctypes.byref(h))
         if rc != OK:
             raise ElbmError(rc, "elbm_batch_create")
         self.h = h

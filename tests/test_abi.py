@@ -142,8 +142,9 @@ def test_batch_create_argument_checks(L):
     import ctypes
     out = ctypes.c_void_p()
     arr = (ctypes.c_void_p * 1)(None)
-    assert L.elbm_batch_create(arr, 1, None, None) == elbm.E_INVAL
-    assert L.elbm_batch_create(None, 1, None, ctypes.byref(out)) == elbm.E_INVAL
-    assert L.elbm_batch_create(arr, 0, None, ctypes.byref(out)) == elbm.E_INVAL
-    assert L.elbm_batch_create(arr, 1, None, ctypes.byref(out)) == elbm.E_INVAL  # a NULL instance
+    assert L.elbm_batch_create(arr, 1, 0, None, None) == elbm.E_INVAL
+    assert L.elbm_batch_create(None, 1, 0, None, ctypes.byref(out)) == elbm.E_INVAL
+    assert L.elbm_batch_create(arr, 0, 0, None, ctypes.byref(out)) == elbm.E_INVAL
+    assert L.elbm_batch_create(arr, 1, 0, None, ctypes.byref(out)) == elbm.E_INVAL  # a NULL instance
+    assert L.elbm_batch_create(arr, 1, 6, None, ctypes.byref(out)) == elbm.E_INVAL  # unknown flag
     assert not out.value
