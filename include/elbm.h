@@ -104,7 +104,7 @@ enum { ELBM_APREC_FP64 = 0, ELBM_APREC_FP32 = 1, ELBM_APREC_FP32_FAST = 2 };
 #define ELBM_NDIAG 24
 
 typedef struct elbm_params {
-    int nx, ny, nz;              /* lattice (3-D, D3Q19) */
+    int nx, ny, nz;              /* lattice (3-D, D3Q19); nx*ny*nz < 2^31 (ELBM_E_INVAL otherwise) */
     int face_bc[6];              /* ELBM_FACE_* ; opposite faces must agree when periodic */
     int phi_bc[6];               /* ELBM_PHI_* ; PERIODIC exactly where face_bc is */
     int phi_axis;                /* axis normal to the electrode planes (0,1,2) */

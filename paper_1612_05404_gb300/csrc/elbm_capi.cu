@@ -210,7 +210,7 @@ int validate(const elbm_params *p, const elbm_init_fields *in, int n_instances)
 {
     if (!p || !in || !in->rho0 || n_instances != 1) return 1;
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return 1;
-    if ((long long)p->nx * p->ny * p->nz > (1LL << 34)) return 1;
+    if ((long long)p->nx * p->ny * p->nz >= (1LL << 31)) return 1;  // 32-bit site indices
     for (int f = 0; f < 6; f++) {
         if (p->face_bc[f] != ELBM_FACE_PERIODIC && p->face_bc[f] != ELBM_FACE_WALL) return 1;
         if (p->phi_bc[f] < ELBM_PHI_PERIODIC || p->phi_bc[f] > ELBM_PHI_NEUMANN) return 1;

@@ -125,25 +125,33 @@ __device__ __forceinline__ T Ppoly(int p, T ux, T uy, T uz, T usq)
 // the closed-form trigonometric solution of the characteristic cubic
 // (Smith 1961).
 // ---------------------------------------------------------------------------
+// FP32 quotient and cosine in the fast forms (a few ulp; the quotient is 0
+// for |b| > 2^126), FP64 exact: used where that error stays below the FP32
+// result's own tolerance
+__device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float qcos(float a) { return __cosf(a); }
+__device__ __forceinline__ double qcos(double a) { return cos(a); }
+
 template <typename T>
 __device__ __forceinline__ T sym3_norm2(T a00, T a11, T a22, T a01, T a02, T a12)
 {
     T p1 = a01 * a01 + a02 * a02 + a12 * a12;
-    T q = (a00 + a11 + a22) / T(3);
+    T q = (a00 + a11 + a22) * T(1.0 / 3.0);
     T b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
     T p2 = b00 * b00 + b11 * b11 + b22 * b22 + T(2) * p1;
     if (p2 <= T(0)) return fabs(q);
     if (p1 == T(0)) return fmax(fabs(a00), fmax(fabs(a11), fabs(a22)));
-    T pp = sqrt(p2 / T(6));
+    T pp = sqrt(p2 * T(1.0 / 6.0));
     T ip = T(1) / pp;
     b00 *= ip; b11 *= ip; b22 *= ip;
     T c01 = a01 * ip, c02 = a02 * ip, c12 = a12 * ip;
     T det = b00 * (b11 * b22 - c12 * c12) - c01 * (c01 * b22 - c12 * c02) + c02 * (c01 * c12 - b11 * c02);
-    T r = det / T(2);
+    T r = det * T(0.5);
     r = fmin(T(1), fmax(T(-1), r));
-    T phi = acos(r) / T(3);
-    T e1 = q + T(2) * pp * cos(phi);
-    T e3 = q + T(2) * pp * cos(phi + T(2.0943951023931954923));
+    T phi = acos(r) * T(1.0 / 3.0);
+    T e1 = q + T(2) * pp * qcos(phi);
+    T e3 = q + T(2) * pp * qcos(phi + T(2.0943951023931954923));
     return fmax(fabs(e1), fabs(e3));
 }
 
@@ -175,16 +183,16 @@ __device__ __forceinline__ T carreau_nu(const Cst<T> &k, bool newtonian, T Pn, T
         T pw = powT(base, k.nexp);
         T nux = k.nu_inf + (k.nu0 - k.nu_inf) * pw;
         T den = T(2) * nux + cs2;
-        T gx = x - A * cs2 / den;
+        T gx = x - qdiv(A * cs2, den);
         bool done = (gx == T(0));
         if (!done) {
             if (gx < T(0)) lo = x; else hi = x;
-            T dnu = (k.nu0 - k.nu_inf) * T(2) * k.nexp * k.lam * k.lam * x * pw / base;
-            T gp = T(1) - A * (T(-2) * cs2 / (den * den)) * dnu;
-            T xn = x - gx / gp;
+            T dnu = qdiv((k.nu0 - k.nu_inf) * T(2) * k.nexp * k.lam * k.lam * x * pw, base);
+            T gp = T(1) + qdiv(T(2) * cs2 * A * dnu, den * den);
+            T xn = x - qdiv(gx, gp);
             if (!(xn > lo && xn < hi)) xn = T(0.5) * (lo + hi);
             done = fabs(xn - x) <= eps * fabs(x) || hi - lo <= eps * hi ||
-                   (sizeof(T) == 4 && fabs(gx) <= T(5e-7) * (x + A * cs2 / den));
+                   (sizeof(T) == 4 && fabs(gx) <= T(5e-7) * (x + qdiv(A * cs2, den)));
             x = xn;
         }
         if (sizeof(T) == 8) {

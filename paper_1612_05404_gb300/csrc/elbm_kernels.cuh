@@ -39,20 +39,6 @@ __device__ __forceinline__ double warp_sum(double v)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
 }
-// compensated FP32 warp sum of (hi, lo) pairs; the result on lane 0
-__device__ __forceinline__ void warp_sum2(float &hi, float &lo)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        float ohi = __shfl_down_sync(0xffffffffu, hi, o);
-        float olo = __shfl_down_sync(0xffffffffu, lo, o);
-        float sm, e;
-        two_sum(hi, ohi, sm, e);
-        hi = sm;
-        lo += olo + e;
-    }
-}
-
 __device__ __forceinline__ int num_blocks() { return gridDim.x * gridDim.y * gridDim.z; }
 
 // Per-block partial sums are stored column-major, part[k * nblocks + block],
@@ -92,11 +78,47 @@ __device__ __forceinline__ void block_sums(const float (&v)[K], double *out, int
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     const int lane = tid & 31, wid = tid >> 5;
     const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    // Within the warp, K values (padded to P = 1, 2, 4 or 8) are summed by a
+    // transposed butterfly: at offsets 16, 8, ... each lane keeps half of its
+    // values and adds its partner's copy of them, until one value per lane
+    // remains, summed over the lanes that share the top lg P lane bits; the
+    // last offsets sum that value over the rest. Lane L ends with value
+    // L >> (5 - lg P): about 2 (P - 1) + 2 (5 - lg P) shuffles instead of 10 K.
+    constexpr int P = K <= 1 ? 1 : (K <= 2 ? 2 : (K <= 4 ? 4 : 8));
+    constexpr int LG = P == 1 ? 0 : (P == 2 ? 1 : (P == 4 ? 2 : 3));
+    static_assert(K <= 8, "at most 8 sums per call");
+    float hi[P], lo[P];
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-        float hi = v[k], lo = 0.f;
-        warp_sum2(hi, lo);
-        if (lane == 0) { sh[0][k][wid] = hi; sh[1][k][wid] = lo; }
+    for (int k = 0; k < P; k++) {
+        hi[k] = k < K ? v[k] : 0.f;
+        lo[k] = 0.f;
+    }
+#pragma unroll
+    for (int st = 0; st < LG; st++) {
+        const int o = 16 >> st, half = (P >> st) / 2;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < half; k++) {
+            const float kh = up ? hi[k + half] : hi[k], kl = up ? lo[k + half] : lo[k];
+            const float sh_ = up ? hi[k] : hi[k + half], sl = up ? lo[k] : lo[k + half];
+            const float rh = __shfl_xor_sync(0xffffffffu, sh_, o), rl = __shfl_xor_sync(0xffffffffu, sl, o);
+            float sm, e;
+            two_sum(kh, rh, sm, e);
+            hi[k] = sm;
+            lo[k] = kl + rl + e;
+        }
+    }
+#pragma unroll
+    for (int o = 16 >> LG; o > 0; o >>= 1) {
+        const float rh = __shfl_xor_sync(0xffffffffu, hi[0], o), rl = __shfl_xor_sync(0xffffffffu, lo[0], o);
+        float sm, e;
+        two_sum(hi[0], rh, sm, e);
+        hi[0] = sm;
+        lo[0] += rl + e;
+    }
+    {
+        const int k = lane >> (5 - LG);
+        if ((lane & ((32 >> LG) - 1)) == 0 && k < K) { sh[0][k][wid] = hi[0]; sh[1][k][wid] = lo[0]; }
     }
     __syncthreads();
     if (tid < K) {
@@ -112,34 +134,58 @@ __device__ __forceinline__ void block_sums(const float (&v)[K], double *out, int
 }
 
 // ---------------------------------------------------------------------------
-// Neighbourhood of a site: coordinates for offsets -1, 0, +1 per axis (-1 when
-// the offset leaves through a wall face).
+// Neighbourhood of a site: the index offsets of the -1, 0, +1 neighbours per
+// axis with the periodic wrap folded in, and whether each exists (not beyond
+// a wall face). Site indices are 32-bit (elbm_init refuses lattices of 2^31
+// sites or more); plane offsets p * N are formed in 64 bits, once per plane.
 // ---------------------------------------------------------------------------
 struct Nbr {
-    int xs[3], ys[3], zs[3];
-    ll s;
+    int s;
+    int ox[3], oy[3], oz[3];
+    bool vx[3], vy[3], vz[3];
 };
 
 __device__ __forceinline__ void nbr_init(Nbr &n, const Geom &g, int x, int y, int z, ll s)
 {
-    n.xs[0] = nbc(x - 1, g.nx, g.per[0]); n.xs[1] = x; n.xs[2] = nbc(x + 1, g.nx, g.per[0]);
-    n.ys[0] = nbc(y - 1, g.ny, g.per[1]); n.ys[1] = y; n.ys[2] = nbc(y + 1, g.ny, g.per[1]);
-    n.zs[0] = nbc(z - 1, g.nz, g.per[2]); n.zs[1] = z; n.zs[2] = nbc(z + 1, g.nz, g.per[2]);
-    n.s = s;
+    const int nx = g.nx, nxy = g.nx * g.ny;
+    n.s = (int)s;
+    n.ox[0] = x > 0 ? -1 : nx - 1;
+    n.ox[1] = 0;
+    n.ox[2] = x < nx - 1 ? 1 : 1 - nx;
+    n.oy[0] = y > 0 ? -nx : (g.ny - 1) * nx;
+    n.oy[1] = 0;
+    n.oy[2] = y < g.ny - 1 ? nx : -(g.ny - 1) * nx;
+    n.oz[0] = z > 0 ? -nxy : (g.nz - 1) * nxy;
+    n.oz[1] = 0;
+    n.oz[2] = z < g.nz - 1 ? nxy : -(g.nz - 1) * nxy;
+    n.vx[0] = x > 0 || g.per[0]; n.vx[1] = true; n.vx[2] = x < nx - 1 || g.per[0];
+    n.vy[0] = y > 0 || g.per[1]; n.vy[1] = true; n.vy[2] = y < g.ny - 1 || g.per[1];
+    n.vz[0] = z > 0 || g.per[2]; n.vz[1] = true; n.vz[2] = z < g.nz - 1 || g.per[2];
 }
 
 // index of the site at offset (ox, oy, oz) in {-1,0,1}^3, or -1 beyond a wall
-__device__ __forceinline__ ll nbr_idx(const Nbr &n, const Geom &g, int ox, int oy, int oz)
+__device__ __forceinline__ int nbr_idx(const Nbr &n, const Geom &, int ox, int oy, int oz)
 {
-    int a = n.xs[ox + 1], b = n.ys[oy + 1], c = n.zs[oz + 1];
-    if (a < 0 || b < 0 || c < 0) return -1;
-    return a + (ll)g.nx * (b + (ll)g.ny * c);
+    if (!(n.vx[ox + 1] && n.vy[oy + 1] && n.vz[oz + 1])) return -1;
+    return n.s + n.ox[ox + 1] + n.oy[oy + 1] + n.oz[oz + 1];
+}
+
+// plane p of a population array
+template <typename S>
+__device__ __forceinline__ const S *plane(const void *A, int p, ll N)
+{
+    return (const S *)A + (ll)p * N;
+}
+template <typename S>
+__device__ __forceinline__ S *plane(void *A, int p, ll N)
+{
+    return (S *)A + (ll)p * N;
 }
 
 template <int PR>
-__device__ __forceinline__ typename Tr<PR>::ct ldp(const void *A, int p, ll idx, ll N)
+__device__ __forceinline__ typename Tr<PR>::ct ldp(const void *A, int p, int idx, ll N)
 {
-    return to_ct(((const typename Tr<PR>::st *)A)[(ll)p * N + idx]);
+    return to_ct(plane<typename Tr<PR>::st>(A, p, N)[idx]);
 }
 
 // f_p(r, t): pull from r - c_p, bounce-back across walls and from solids.
@@ -148,7 +194,7 @@ template <int PR>
 __device__ __forceinline__ typename Tr<PR>::ct gather_pop(const Geom &g, const unsigned char *mask,
                                                           const void *A, const Nbr &n, int p)
 {
-    ll src = nbr_idx(n, g, -cx(p), -cy(p), -cz(p));
+    const int src = nbr_idx(n, g, -cx(p), -cy(p), -cz(p));
     bool bb = src < 0;
     if (!bb && mask) bb = mask[src] == ELBM_NODE_SOLID;
     return bb ? ldp<PR>(A, opp(p), n.s, g.N) : ldp<PR>(A, p, src, g.N);
@@ -159,16 +205,30 @@ __device__ __forceinline__ typename Tr<PR>::gt gather_g(const Geom &g, const uns
                                                         const void *A, const Nbr &n, int i)
 {
     typedef typename Tr<PR>::gt gt;
-    ll src = nbr_idx(n, g, -c7x(i), -c7y(i), -c7z(i));
+    const int src = nbr_idx(n, g, -c7x(i), -c7y(i), -c7z(i));
     bool bb = src < 0;
     if (!bb && mask) bb = mask[src] == ELBM_NODE_SOLID;
-    int io = i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
-    const gt *G = (const gt *)A;
-    return bb ? G[(ll)io * g.N + n.s] : G[(ll)i * g.N + src];
+    const int io = i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+    return bb ? plane<gt>(A, io, g.N)[n.s] : plane<gt>(A, i, g.N)[src];
 }
 
 template <typename T>
 __device__ __forceinline__ T psi_of(T rho, T rho0) { return rho0 * (T(1) - exp(-rho / rho0)); }
+// the same in the collision's arithmetic: FP32 as rho0 - rho0 2^(rho c),
+// c = -log2(e)/rho0 (no division per neighbour); FP64 as psi_of
+__device__ __forceinline__ float psi_nb(float rho, float rho0, float c) { return fmaf(-rho0, exp2f(rho * c), rho0); }
+__device__ __forceinline__ double psi_nb(double rho, double rho0, double) { return psi_of<double>(rho, rho0); }
+// conductivity sigma = sig_g + dsig (1 + tanh((rho - rho0)/w))/2; FP32 through
+// (1 + tanh x)/2 = 1/(1 + e^(-2x)) with the fast exponential and quotient
+// (the quotient tends to 0 as the exponential overflows)
+__device__ __forceinline__ float sigma_of(const Cst<float> &k, float rho)
+{
+    return k.sig_g + __fdividef(k.dsig, 1.f + __expf(-2.f * (rho - k.rho0) * k.itw));
+}
+__device__ __forceinline__ double sigma_of(const Cst<double> &k, double rho)
+{
+    return k.sig_g + k.dsig * 0.5 * (1.0 + tanh((rho - k.rho0) * k.itw));
+}
 template <typename T>
 __device__ __forceinline__ T theta_of(T rho, T rho0, T w) { return T(0.5) * (T(1) + tanh((rho - rho0) / w)); }
 
@@ -186,11 +246,11 @@ __device__ __forceinline__ int block_id() { return blockIdx.x + gridDim.x * (blo
 // kind 0 = unknown (index in *nb), 1 = Dirichlet value in *v, 2 = no term.
 template <typename T>
 __device__ __forceinline__ int pois_nb(const Geom &g, const Cst<T> &k, const unsigned char *mask,
-                                       const Nbr &n, int x, int y, int z, int axis, int sign, ll *nb, T *v)
+                                       const Nbr &n, int x, int y, int z, int axis, int sign, int *nb, T *v)
 {
     int o[3] = {0, 0, 0};
     o[axis] = sign;
-    ll i = nbr_idx(n, g, o[0], o[1], o[2]);
+    const int i = nbr_idx(n, g, o[0], o[1], o[2]);
     if (i < 0) {
         int face = 2 * axis + (sign > 0 ? 1 : 0);
         if (g.phi_kind[face] == ELBM_PHI_DIRICHLET) { *v = phi_ghost<T>(g, k, face, x, y, z); return 1; }
@@ -333,7 +393,7 @@ __global__ void __launch_bounds__(128) k_charge_grad(Geom g, Phys ph, Bufs b)
     sc gx = 0, gy = 0, gz = 0;
 #pragma unroll
     for (int p = 1; p < Q; p++) {
-        ll nb = nbr_idx(n, g, cx(p), cy(p), cz(p));
+        const int nb = nbr_idx(n, g, cx(p), cy(p), cz(p));
         sc v = (nb < 0 || (b.mask && b.mask[nb] == ELBM_NODE_SOLID)) ? rs : rho[nb];
         sc wv = sc(wq(p)) * v / sc(CS2);
         gx += wv * sc(cx(p));
@@ -367,8 +427,8 @@ __global__ void __launch_bounds__(128) k_charge_ab(Geom g, Phys ph, Bufs b)
         sc div = 0;
 #pragma unroll
         for (int p = 1; p < Q; p++) {
-            ll nb = nbr_idx(n, g, cx(p), cy(p), cz(p));
-            ll src = (nb < 0 || (b.mask && b.mask[nb] == ELBM_NODE_SOLID)) ? s : nb;
+            const int nb = nbr_idx(n, g, cx(p), cy(p), cz(p));
+            const int src = (nb < 0 || (b.mask && b.mask[nb] == ELBM_NODE_SOLID)) ? n.s : nb;
             sc wv = sc(wq(p)) / sc(CS2);
             div += wv * (nh[src] * sc(cx(p)) + nh[g.N + src] * sc(cy(p)) + nh[2 * g.N + src] * sc(cz(p)));
         }
@@ -443,7 +503,7 @@ __global__ void __launch_bounds__(128) k_sor(Geom g, Phys ph, Bufs b, int color,
     for (int a = 0; a < 3; a++)
 #pragma unroll
         for (int sg = -1; sg <= 1; sg += 2) {
-            ll nb = 0;
+            int nb = 0;
             sc v = 0;
             int kk = pois_nb<sc>(g, k, b.mask, n, x, y, z, a, sg, &nb, &v);
             if (kk == 0) {
@@ -491,7 +551,7 @@ __global__ void __launch_bounds__(128) k_resid(Geom g, Phys ph, Bufs b)
         for (int a = 0; a < 3; a++)
 #pragma unroll
             for (int sg = -1; sg <= 1; sg += 2) {
-                ll nb = 0;
+                int nb = 0;
                 sc v = 0;
                 int kk = pois_nb<sc>(g, k, b.mask, n, x, y, z, a, sg, &nb, &v);
                 if (kk == 0) {
@@ -611,12 +671,13 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
         // Eq. (sc): F_int = -G psi(r) sum_fluid w psi(r+c) c - G_w psi(r) sum_wall w psi(r) c
         const ct rho0 = k.rho0;
         const ct ps = psi_of<ct>(r, rho0);
+        const ct psic = ct(-1.4426950408889634) * k.irho0;
         ct sfx = 0, sfy = 0, sfz = 0, swx = 0, swy = 0, swz = 0;
 #pragma unroll
         for (int p = 1; p < Q; p++) {
-            ll nb = nbr_idx(n, g, cx(p), cy(p), cz(p));
+            const int nb = nbr_idx(n, g, cx(p), cy(p), cz(p));
             bool wall = nb < 0 || (b.mask && b.mask[nb] == ELBM_NODE_SOLID);
-            ct wv = ct(wq(p)) * (wall ? ps : psi_of<ct>(ct(rho[nb]), rho0));
+            ct wv = ct(wq(p)) * (wall ? ps : psi_nb(ct(rho[nb]), rho0, psic));
             if (wall) { swx += wv * ct(cx(p)); swy += wv * ct(cy(p)); swz += wv * ct(cz(p)); }
             else { sfx += wv * ct(cx(p)); sfy += wv * ct(cy(p)); sfz += wv * ct(cz(p)); }
         }
@@ -634,7 +695,7 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
                 ct pv[2];
 #pragma unroll
                 for (int kk = 0; kk < 2; kk++) {
-                    ll nb = 0;
+                    int nb = 0;
                     ct v = 0;
                     int kind = pois_nb<ct>(g, k, b.mask, n, x, y, z, a, kk ? 1 : -1, &nb, &v);
                     pv[kk] = kind == 0 ? ct(phi[nb]) : (kind == 1 ? v : phs);
@@ -753,12 +814,11 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
         // Eq. (add): S = f^eq(rho, u + F/rho) - f^eq(rho, u); Eq. (lattice-b)
         const ct vx = ux + Fx * ir, vy = uy + Fy * ir, vz = uz + Fz * ir;
         const ct vsq = vx * vx + vy * vy + vz * vz;
-        st *B = (st *)b.fB;
 #pragma unroll
         for (int p = 0; p < Q; p++) {
             ct Sp = ct(wq(p)) * r * (Ppoly<ct>(p, vx, vy, vz, vsq) - Ppoly<ct>(p, ux, uy, uz, usq));
             ct fo = f[p] + ab * D[p] + Sp;
-            B[(ll)p * g.N + s] = from_ct<st>(fo);
+            plane<st>(b.fB, p, g.N)[n.s] = from_ct<st>(fo);
         }
 
         // half-step velocity (Sec. II): rho u = sum f c + F/2
@@ -766,31 +826,30 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
 
         if (ph.charge_model == ELBM_CHARGE_TRANSPORT) {
             // D3Q7 advection-diffusion of q with the Ohmic source R = div(sigma grad phi)
-            const ct ss = k.sig_g + k.dsig * ct(0.5) * (ct(1) + tanh((ct(rho[s]) - rho0) * k.itw));
+            const ct ss = sigma_of(k, ct(rho[s]));
             const ct phs = ct(phi[s]);
             ct R = 0;
 #pragma unroll
             for (int a = 0; a < 3; a++)
 #pragma unroll
                 for (int sg = -1; sg <= 1; sg += 2) {
-                    ll nb = 0;
+                    int nb = 0;
                     ct v = 0;
                     int kind = pois_nb<ct>(g, k, b.mask, n, x, y, z, a, sg, &nb, &v);
                     if (kind == 0) {
-                        ct sn = k.sig_g + k.dsig * ct(0.5) * (ct(1) + tanh((ct(rho[nb]) - rho0) * k.itw));
+                        const ct sn = sigma_of(k, ct(rho[nb]));
                         R += ct(0.5) * (ss + sn) * (ct(phi[nb]) - phs);
                     } else if (kind == 1) {
                         R += ss * (v - phs);
                     }
                 }
-            gt *GB = (gt *)b.gB;
             const ct itq = k.itau_q;
 #pragma unroll
             for (int i = 0; i < Q7; i++) {
                 ct gi = ct(gather_g<PR>(g, b.mask, b.gA, n, i));
                 ct cu = ct(c7x(i)) * upx + ct(c7y(i)) * upy + ct(c7z(i)) * upz;
                 ct geq = ct(w7(i)) * qs * (ct(1) + cu / ct(CS2Q));
-                GB[(ll)i * g.N + s] = gt(gi - (gi - geq) * itq + ct(w7(i)) * R);
+                plane<gt>(b.gB, i, g.N)[n.s] = gt(gi - (gi - geq) * itq + ct(w7(i)) * R);
             }
         }
 
@@ -1174,7 +1233,7 @@ __device__ __forceinline__ typename Tr<PR>::sc mg_resid_at(const Geom &g, const 
         for (int a = 0; a < 3; a++)
 #pragma unroll
             for (int sg = -1; sg <= 1; sg += 2) {
-                ll nb = 0;
+                int nb = 0;
                 T v = 0;
                 const int kk = pois_nb<T>(g, k, bf.mask, n, x, y, z, a, sg, &nb, &v);
                 if (kk == 0) r += T(0.5) * (es + (T(1) + k.kap * rho[nb])) * (phi[nb] - ps);
