@@ -424,6 +424,37 @@ elbm_status step_host(elbm_handle *h, bool diag)
 // device-side while node), bit 2 collision and diagnostics.
 // One step of h enqueued into stream s, which is being captured (the Poisson
 // loop becomes a conditional while node whose body is captured on h->cap2).
+// Kernel priorities in a captured graph: every kernel node except the
+// site-wide compute kernels (Ops::heavy) gets the device's highest stream
+// priority, so that when several instances share the GPU the block scheduler
+// serves the short, latency-bound Poisson chain of one instance ahead of the
+// pending blocks of another's collision. Takes effect in graphs instantiated
+// with cudaGraphInstantiateFlagUseNodePriority.
+bool prioritize(cudaGraph_t graph, const std::vector<const void *> &heavy_fns)
+{
+    int least = 0, greatest = 0;
+    if (!cuda_ok(cudaDeviceGetStreamPriorityRange(&least, &greatest))) return false;
+    size_t n = 0;
+    if (!cuda_ok(cudaGraphGetNodes(graph, nullptr, &n))) return false;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n && !cuda_ok(cudaGraphGetNodes(graph, nodes.data(), &n))) return false;
+    for (cudaGraphNode_t node : nodes) {
+        cudaGraphNodeType type;
+        if (!cuda_ok(cudaGraphNodeGetType(node, &type))) return false;
+        if (type != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp;
+        if (!cuda_ok(cudaGraphKernelNodeGetParams(node, &kp))) return false;
+        bool heavy = false;
+        for (const void *f : heavy_fns) heavy = heavy || (f && kp.func == f);
+        if (heavy) continue;
+        cudaKernelNodeAttrValue v;
+        std::memset(&v, 0, sizeof(v));
+        v.priority = greatest;
+        if (!cuda_ok(cudaGraphKernelNodeSetAttribute(node, cudaKernelNodeAttributePriority, &v))) return false;
+    }
+    return true;
+}
+
 bool enqueue_step(elbm_handle *h, int parity, cudaStream_t s, int sections, int &n_pre, int &n_body, int &n_post)
 {
     Bufs b = h->b;
@@ -459,6 +490,7 @@ bool enqueue_step(elbm_handle *h, int parity, cudaStream_t s, int sections, int 
                 n_body += enq_unit(h, b, h->cap2);
                 n_body += enq_check(h, b, h->cap2, FIN_RESID_BODY, cond, 1);
                 ok = cuda_ok(cudaStreamEndCapture(h->cap2, &body));
+                ok = ok && prioritize(body, std::vector<const void *>(h->ops.heavy, h->ops.heavy + 4));
             }
             ok = ok && cuda_ok(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
                                                                    cudaStreamSetCaptureDependencies));
@@ -527,7 +559,10 @@ bool capture_batch(elbm_handle *B, int parity, cudaGraphExec_t *out, bool prolog
     }
     if (prologue) parity = 1;  // kernel counts belong to the steady graphs
     ok = cuda_ok(cudaStreamEndCapture(s, &graph)) && ok;
-    if (ok) ok = cuda_ok(cudaGraphInstantiate(out, graph, 0));
+    std::vector<const void *> heavy;
+    for (int i = 0; i < B->n_sub; i++) heavy.insert(heavy.end(), B->sub[i]->ops.heavy, B->sub[i]->ops.heavy + 4);
+    ok = ok && prioritize(graph, heavy);
+    if (ok) ok = cuda_ok(cudaGraphInstantiate(out, graph, cudaGraphInstantiateFlagUseNodePriority));
     if (graph) cudaGraphDestroy(graph);
     cudaGetLastError();
     if (parity == 0) {

@@ -82,6 +82,9 @@ struct Ops {
     void (*export_pop)(const Geom &, const Bufs &, double *out, const Launch &, cudaStream_t);
     void (*export_gpop)(const Geom &, const Bufs &, double *out, const Launch &, cudaStream_t);
     void (*export_plane)(const void *plane, double *out, long long n, cudaStream_t);
+    // the site-wide compute kernels (collision variants, learned-alpha pass):
+    // in a batch graph every other kernel runs at a higher priority
+    const void *heavy[4];
 };
 
 struct MGLevel;  // elbm_kernels.cuh

@@ -1145,6 +1145,10 @@ struct Launchers {
         o.export_pop = export_pop;
         o.export_gpop = export_gpop;
         o.export_plane = export_plane;
+        o.heavy[0] = (const void *)k_collide<PR, ELBM_APREC_FP64>;
+        o.heavy[1] = (const void *)k_collide<PR, ELBM_APREC_FP32>;
+        o.heavy[2] = (const void *)k_collide<PR, ELBM_APREC_FP32_FAST>;
+        o.heavy[3] = PR == ELBM_PREC_FP64 ? nullptr : (const void *)k_alpha_mlp<PR>;
         return o;
     }
 };
