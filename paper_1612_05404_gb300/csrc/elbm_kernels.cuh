@@ -39,6 +39,15 @@ __device__ __forceinline__ double warp_sum(double v)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
 }
+// float <-> int with the same order (two's complement: negative floats
+// have their magnitude bits flipped); a NaN maps to the stand-in value
+__device__ __forceinline__ int float_ord(float v, float nan_as)
+{
+    const int i = __float_as_int(v == v ? v : nan_as);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ord_float(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
 __device__ __forceinline__ int num_blocks() { return gridDim.x * gridDim.y * gridDim.z; }
 
 // Per-block partial sums are stored column-major, part[k * nblocks + block],
@@ -608,8 +617,8 @@ __global__ void k_phi_shift(Geom g, Bufs b)
 // Guarded FP32 alpha: lanes whose root needs the float-float guard queue their
 // inputs in shared memory; after a barrier the block's first threads run the
 // queued guards together (full warps instead of a few lanes in many warps),
-// and the results return through the queue. Beyond kGuardQ queued lanes a
-// lane runs its guard itself.
+// and the results return through the queue. The queue holds one entry per
+// thread of the block (the kernel is launched with 128 threads).
 constexpr int kGuardQ = 128;
 struct GuardEntry {
     float f[Q], d[Q];
@@ -645,7 +654,7 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
     Nbr n;
     ct f[Q], D[Q];
     ct r = 0, drho = 0, jx = 0, jy = 0, jz = 0, Fx = 0, Fy = 0, Fz = 0, qs = 0;
-    ct ir = 0, ux = 0, uy = 0, uz = 0, usq = 0;
+    ct ir = 0, ux = 0, uy = 0, uz = 0, usq = 0, Rq = 0;
     ct alpha = ct(2);
     float a_herr = 0.f;
     int a_status = 0, a_guard = 0, a_lfall = 0;
@@ -685,11 +694,15 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
         Fy = -k.G * ps * sfy - k.Gw * ps * swy;
         Fz = -k.G * ps * sfz - k.Gw * ps * swz;
 
-        // electric force q E, E = -grad phi (central differences) + E_ext
+        // electric force q E, E = -grad phi (central differences) + E_ext; in
+        // transport mode the same face neighbours give the Ohmic source
+        // R = div(sigma grad phi) of the charge update
         if (ph.charge_model != ELBM_CHARGE_NONE) {
             qs = ct(((const sc *)b.q)[s]);
             ct E[3];
             const ct phs = ct(phi[s]);
+            const bool tr = ph.charge_model == ELBM_CHARGE_TRANSPORT;
+            const ct ss = tr ? sigma_of(k, ct(rho[s])) : ct(0);
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 ct pv[2];
@@ -699,6 +712,10 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
                     ct v = 0;
                     int kind = pois_nb<ct>(g, k, b.mask, n, x, y, z, a, kk ? 1 : -1, &nb, &v);
                     pv[kk] = kind == 0 ? ct(phi[nb]) : (kind == 1 ? v : phs);
+                    if (tr) {
+                        if (kind == 0) Rq += ct(0.5) * (ss + sigma_of(k, ct(rho[nb]))) * (pv[kk] - phs);
+                        else if (kind == 1) Rq += ss * (v - phs);
+                    }
                 }
                 E[a] = -(pv[1] - pv[0]) * ct(0.5) + k.E[a];
             }
@@ -753,31 +770,24 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
                 a_lfall = learned && ao.status == 0 && ao.iters > 1;
                 if (kQueue && ao.guarded == 2) {
                     a_guard = 1;
-                    gslot = atomicAdd(&gq_n, 1);
-                    if (gslot < kGuardQ) {
-                        GuardEntry &e = gq[gslot];
+                    gslot = atomicAdd(&gq_n, 1);  // < kGuardQ: one entry per thread
+                    GuardEntry &e = gq[gslot];
 #pragma unroll
-                        for (int p = 0; p < Q; p++) {
-                            e.f[p] = ff[p];
-                            e.d[p] = dd[p];
-                        }
-                        e.rho = float(r);
-                        e.a = ao.alpha;
-                        e.S = ast.S;
-                    } else {  // queue full: this lane's guard runs here
-                        const float4 gr = alpha_guard(ff, dd, float(r), ao.alpha, ast.S);
-                        alpha = ct(gr.x);
-                        if (gr.w != 0.f) a_herr = gr.z;
-                        else a_status = 4;  // not certified: the FP32 report stays
-                        gslot = -1;
+                    for (int p = 0; p < Q; p++) {
+                        e.f[p] = ff[p];
+                        e.d[p] = dd[p];
                     }
+                    e.rho = float(r);
+                    e.a = ao.alpha;
+                    e.S = ast.S;
                 }
             }
         }
     }
     if (kQueue) {
+        static_assert(!kQueue || kGuardQ >= 128, "one guard-queue entry per thread of a 128-thread block");
         __syncthreads();
-        const int nq = gq_n < kGuardQ ? gq_n : kGuardQ;
+        const int nq = gq_n;
         if (tid < nq) gq[tid].res = alpha_guard(gq[tid].f, gq[tid].d, gq[tid].rho, gq[tid].a, gq[tid].S);
         __syncthreads();
         if (gslot >= 0) {
@@ -788,10 +798,7 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
         }
     }
     if (active) {
-        const sc *rho = (const sc *)b.rho;
-        const sc *phi = (const sc *)b.phi;
         const Cst<ct> &k = cst<ct>(ph);
-        const ct rho0 = k.rho0;
         // Eq. (stress): Pi = sum (f - f^eq) c c = -sum D c c; 2-norm; Carreau; Eq. (beta)
         ct nu = k.nu0;
         if (!ph.newtonian) {
@@ -825,24 +832,8 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
         const ct upx = (jx + ct(0.5) * Fx) * ir, upy = (jy + ct(0.5) * Fy) * ir, upz = (jz + ct(0.5) * Fz) * ir;
 
         if (ph.charge_model == ELBM_CHARGE_TRANSPORT) {
-            // D3Q7 advection-diffusion of q with the Ohmic source R = div(sigma grad phi)
-            const ct ss = sigma_of(k, ct(rho[s]));
-            const ct phs = ct(phi[s]);
-            ct R = 0;
-#pragma unroll
-            for (int a = 0; a < 3; a++)
-#pragma unroll
-                for (int sg = -1; sg <= 1; sg += 2) {
-                    int nb = 0;
-                    ct v = 0;
-                    int kind = pois_nb<ct>(g, k, b.mask, n, x, y, z, a, sg, &nb, &v);
-                    if (kind == 0) {
-                        const ct sn = sigma_of(k, ct(rho[nb]));
-                        R += ct(0.5) * (ss + sn) * (ct(phi[nb]) - phs);
-                    } else if (kind == 1) {
-                        R += ss * (v - phs);
-                    }
-                }
+            // D3Q7 advection-diffusion of q with the Ohmic source R (above)
+            const ct R = Rq;
             const ct itq = k.itau_q;
 #pragma unroll
             for (int i = 0; i < Q7; i++) {
@@ -894,13 +885,12 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
         unsigned packed = dsh | (dnr << 6) | (dcl << 12) | (dbad << 18) | (dnfl << 24);
         packed = __reduce_add_sync(0xffffffffu, packed);
         unsigned packed2 = __reduce_add_sync(0xffffffffu, dgd | (dgf << 6) | (dlf << 12));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            damin = fminf(damin, __shfl_down_sync(0xffffffffu, damin, o));
-            damax = fmaxf(damax, __shfl_down_sync(0xffffffffu, damax, o));
-            dherr = fmaxf(dherr, __shfl_down_sync(0xffffffffu, dherr, o));
-            dumax = fmaxf(dumax, __shfl_down_sync(0xffffffffu, dumax, o));
-        }
+        // extrema as order-preserving integers (NaN lanes left out), one
+        // warp-wide integer min/max each
+        damin = ord_float(__reduce_min_sync(0xffffffffu, float_ord(damin, 1e30f)));
+        damax = ord_float(__reduce_max_sync(0xffffffffu, float_ord(damax, -1e30f)));
+        dherr = ord_float(__reduce_max_sync(0xffffffffu, float_ord(dherr, 0.f)));
+        dumax = ord_float(__reduce_max_sync(0xffffffffu, float_ord(dumax, 0.f)));
         if (lane == 0) {
             mm[0][wid] = damin; mm[1][wid] = damax; mm[2][wid] = dherr; mm[3][wid] = dumax;
             cn[0][wid] = packed;
