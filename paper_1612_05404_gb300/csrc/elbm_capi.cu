@@ -251,7 +251,7 @@ int validate(const elbm_params *p, const elbm_init_fields *in, int n_instances)
 
 void free_bufs(elbm_handle *h)
 {
-    void *ptrs[] = {h->b.fA, h->b.fB, h->b.gA, h->b.gB, h->b.rho, h->b.q, h->b.phi, h->b.ux,
+    void *ptrs[] = {h->b.fA, h->b.fB, h->b.gA, h->b.gB, h->b.rho, h->b.q, h->b.phi, h->b.psi, h->b.sig, h->b.ux,
                     h->b.uy, h->b.uz, h->b.alpha, h->b.nu, h->b.mask, h->b.nh, h->b.ab,
                     h->b.part, h->b.scal, h->b.scalf, h->b.diag, h->b.colres, h->b.ticket,
                     const_cast<void *>(h->b.mlpimg), h->b.phi_old};
@@ -811,6 +811,8 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     alloc(&b.rho, (size_t)N * h->sc_bytes);
     alloc(&b.q, (size_t)N * h->sc_bytes);
     alloc(&b.phi, (size_t)N * h->sc_bytes);
+    alloc(&b.psi, (size_t)N * h->sc_bytes);
+    if (transport) alloc(&b.sig, (size_t)N * h->sc_bytes);
     // extrapolated warm start in reduced precision (FP64 keeps phi(t-1), the
     // start the FP64 oracle uses, so that the two solves agree to 1e-12)
     if (p->charge_model != ELBM_CHARGE_NONE && p->poisson_fixed_sweeps == 0 && p->precision != ELBM_PREC_FP64)

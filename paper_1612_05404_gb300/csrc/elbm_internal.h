@@ -42,6 +42,7 @@ template <> __host__ __device__ __forceinline__ const Cst<float> &cst<float>(con
 struct Bufs {
     void *fA, *fB, *gA, *gB;          // populations (current A, next B)
     void *rho, *q, *phi;              // scalar planes
+    void *psi, *sig;                  // psi(rho) of the Shan-Chen force; sigma(rho) (transport mode)
     void *ux, *uy, *uz, *alpha, *nu;  // optional macroscopic planes
     unsigned char *mask;              // node kinds (NULL when all fluid)
     void *nh;                         // paper-mode charge: 4 planes n_x, n_y, n_z, |grad rho|^2

@@ -374,6 +374,16 @@ __global__ void __launch_bounds__(128) k_moments(Geom g, Phys ph, Bufs b)
             q2 = qs * qs;
         }
     }
+    if (inb) {
+        // the per-site functions of rho that the collision takes at its
+        // neighbours, at every node (inlet and outlet nodes keep their
+        // prescribed density): psi of the Shan-Chen force, sigma of the
+        // Ohmic current
+        const Cst<ct> &k = cst<ct>(ph);
+        const ct rv = ct(((const sc *)b.rho)[s]);
+        ((sc *)b.psi)[s] = sc(psi_nb(rv, k.rho0, ct(-1.4426950408889634) * k.irho0));
+        if (ph.charge_model == ELBM_CHARGE_TRANSPORT) ((sc *)b.sig)[s] = sc(sigma_of(k, rv));
+    }
     if (ph.charge_model == ELBM_CHARGE_TRANSPORT) {
         gt v[2] = {qv, q2};
         block_sums<2>(v, b.part + block_id(), num_blocks());
@@ -661,7 +671,6 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
     int gslot = -1;
     if (active) {
         nbr_init(n, g, x, y, z, s);
-        const sc *rho = (const sc *)b.rho;
         const sc *phi = (const sc *)b.phi;
 #pragma unroll
         for (int p = 0; p < Q; p++) f[p] = gather_pop<PR>(g, b.mask, b.fA, n, p);
@@ -680,13 +689,13 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
         // Eq. (sc): F_int = -G psi(r) sum_fluid w psi(r+c) c - G_w psi(r) sum_wall w psi(r) c
         const ct rho0 = k.rho0;
         const ct ps = psi_of<ct>(r, rho0);
-        const ct psic = ct(-1.4426950408889634) * k.irho0;
+        const sc *psi = (const sc *)b.psi;
         ct sfx = 0, sfy = 0, sfz = 0, swx = 0, swy = 0, swz = 0;
 #pragma unroll
         for (int p = 1; p < Q; p++) {
             const int nb = nbr_idx(n, g, cx(p), cy(p), cz(p));
             bool wall = nb < 0 || (b.mask && b.mask[nb] == ELBM_NODE_SOLID);
-            ct wv = ct(wq(p)) * (wall ? ps : psi_nb(ct(rho[nb]), rho0, psic));
+            ct wv = ct(wq(p)) * (wall ? ps : ct(psi[nb]));
             if (wall) { swx += wv * ct(cx(p)); swy += wv * ct(cy(p)); swz += wv * ct(cz(p)); }
             else { sfx += wv * ct(cx(p)); sfy += wv * ct(cy(p)); sfz += wv * ct(cz(p)); }
         }
@@ -702,7 +711,8 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
             ct E[3];
             const ct phs = ct(phi[s]);
             const bool tr = ph.charge_model == ELBM_CHARGE_TRANSPORT;
-            const ct ss = tr ? sigma_of(k, ct(rho[s])) : ct(0);
+            const sc *sig = (const sc *)b.sig;
+            const ct ss = tr ? ct(sig[s]) : ct(0);
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 ct pv[2];
@@ -713,7 +723,7 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
                     int kind = pois_nb<ct>(g, k, b.mask, n, x, y, z, a, kk ? 1 : -1, &nb, &v);
                     pv[kk] = kind == 0 ? ct(phi[nb]) : (kind == 1 ? v : phs);
                     if (tr) {
-                        if (kind == 0) Rq += ct(0.5) * (ss + sigma_of(k, ct(rho[nb]))) * (pv[kk] - phs);
+                        if (kind == 0) Rq += ct(0.5) * (ss + ct(sig[nb])) * (pv[kk] - phs);
                         else if (kind == 1) Rq += ss * (v - phs);
                     }
                 }
@@ -867,9 +877,9 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
             dgd = a_guard;
             dlf = a_lfall;
             dherr = a_herr;
-            float um = float(sqrt(upx * upx + upy * upy + upz * upz));
-            dumax = um;
-            if (!(r > ct(0)) || !isfinite(float(r)) || !isfinite(um) || !isfinite(float(alpha))) dbad = 1;
+            const float um2 = float(upx * upx + upy * upy + upz * upz);  // |u|^2; the root once per block
+            dumax = um2;
+            if (!(r > ct(0)) || !isfinite(float(r)) || !isfinite(um2) || !isfinite(float(alpha))) dbad = 1;
         }
     }
     if (diag) {
@@ -898,24 +908,28 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
         }
         block_sums<6>(v, res);
         __syncthreads();
-        if (tid == 0) {
-            const ll nbk = num_blocks();
-            double *out = b.part + block_id();
-            out[D_MASS * nbk] = res[0]; out[D_MX * nbk] = res[1]; out[D_MY * nbk] = res[2]; out[D_MZ * nbk] = res[3];
-            out[D_Q * nbk] = res[4]; out[D_ASUM * nbk] = res[5];
+        // thread j writes column j of the block's partials (one lane each,
+        // so the block does not wait on one thread's serial loop)
+        if (tid < D_NPART) {
+            const int j = tid;
             const int nw = (blockDim.x * blockDim.y + 31) >> 5;
-            float a0 = 1e30f, a1 = -1e30f, h = 0.f, u = 0.f;
-            unsigned c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            for (int i = 0; i < nw; i++) {
-                a0 = fminf(a0, mm[0][i]); a1 = fmaxf(a1, mm[1][i]);
-                h = fmaxf(h, mm[2][i]); u = fmaxf(u, mm[3][i]);
-                for (int k = 0; k < 5; k++) c[k] += (cn[0][i] >> (6 * k)) & 63u;
-                for (int k = 0; k < 3; k++) c[5 + k] += (cn[1][i] >> (6 * k)) & 63u;
+            double val;
+            if (j <= D_Q || j == D_ASUM) {
+                val = res[j == D_ASUM ? 5 : j];
+            } else if (j == D_AMIN || j == D_AMAX || j == D_HERR || j == D_UMAX) {
+                const int m = j == D_AMIN ? 0 : (j == D_AMAX ? 1 : (j == D_HERR ? 2 : 3));
+                float e = mm[m][0];
+                for (int i = 1; i < nw; i++) e = m == 0 ? fminf(e, mm[m][i]) : fmaxf(e, mm[m][i]);
+                val = m == 3 ? sqrt(double(e)) : double(e);
+            } else {
+                const int word = j >= D_NGUARD ? 1 : 0;
+                const int field = word ? j - D_NGUARD
+                                       : (j == D_NBAD ? 3 : (j == D_NFLUID ? 4 : j - D_NSHORT));
+                unsigned c = 0;
+                for (int i = 0; i < nw; i++) c += (cn[word][i] >> (6 * field)) & 63u;
+                val = double(c);
             }
-            out[D_NSHORT * nbk] = c[0]; out[D_NNOROOT * nbk] = c[1]; out[D_NCLIP * nbk] = c[2];
-            out[D_NBAD * nbk] = c[3]; out[D_NFLUID * nbk] = c[4];
-            out[D_NGUARD * nbk] = c[5]; out[D_NGFAIL * nbk] = c[6]; out[D_NLFALL * nbk] = c[7];
-            out[D_AMIN * nbk] = a0; out[D_AMAX * nbk] = a1; out[D_HERR * nbk] = h; out[D_UMAX * nbk] = u;
+            b.part[(ll)j * num_blocks() + block_id()] = val;
         }
     }
 }
