@@ -637,7 +637,7 @@ struct GuardEntry {
 };
 
 template <int PR, int AP>
-__global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC_FP64) ? 1 : 4) k_collide(Geom g, Phys ph, Bufs b, int diag)
+__global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC_FP64) ? 1 : 5) k_collide(Geom g, Phys ph, Bufs b, int diag)
 {
     typedef Tr<PR> T;
     typedef typename T::ct ct;
