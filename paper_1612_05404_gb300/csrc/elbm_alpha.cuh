@@ -176,14 +176,48 @@ __device__ __forceinline__ ffl ff_log1p_small(ffl z)
     return ff_add_f(ff_add(z, ffl{-0.5f * z2.h, -0.5f * z2.l}), z2.h * zh * R3);
 }
 
+// A guard runs on a group of L (1, 2, 4 or 8) consecutive lanes of a warp:
+// member j takes the populations p = j, j + L, ... and the group's sums are
+// combined by an XOR butterfly. Float and float-float addition are
+// commutative bit for bit (TwoSum is exact in either order), so every member
+// ends with the same totals and the group takes one path.
+struct Grp {
+    int j, L;
+    unsigned mask;  // the group's lanes
+};
+
+__device__ __forceinline__ Grp grp_make(int j, int L)
+{
+    unsigned lane;
+    asm("mov.u32 %0, %%laneid;" : "=r"(lane));
+    const unsigned ones = L >= 32 ? 0xffffffffu : ((1u << L) - 1u);
+    return Grp{j, L, ones << (lane & ~unsigned(L - 1))};
+}
+__device__ __forceinline__ float grp_sum(const Grp &g, float v)
+{
+    for (int o = 1; o < g.L; o <<= 1) v += __shfl_xor_sync(g.mask, v, o);
+    return v;
+}
+__device__ __forceinline__ float grp_max(const Grp &g, float v)
+{
+    for (int o = 1; o < g.L; o <<= 1) v = fmaxf(v, __shfl_xor_sync(g.mask, v, o));
+    return v;
+}
+__device__ __forceinline__ ffl grp_sum(const Grp &g, ffl v)
+{
+    for (int o = 1; o < g.L; o <<= 1)
+        v = ff_add(v, ffl{__shfl_xor_sync(g.mask, v.h, o), __shfl_xor_sync(g.mask, v.l, o)});
+    return v;
+}
+
 // h'(0) in float-float: (1 + ln r) sum D + sum D_p ln(f_p / (w_p r)); 1/w_p is
 // the integer 3, 18 or 36, so f_p / (w_p r) = (f_p / w_p) / r exactly as pairs.
 // The guard's loops are not unrolled: compact code for a path few warps take.
-__device__ __forceinline__ ffl h0_ff(const float *f, const float *d, float r)
+__device__ __forceinline__ ffl h0_ff(const float *f, const float *d, float r, const Grp &gp)
 {
     ffl S = {0.f, 0.f}, T = {0.f, 0.f};
 #pragma unroll 1
-    for (int p = 0; p < Q; p++) {
+    for (int p = gp.j; p < Q; p += gp.L) {
         S = ff_add_f(S, d[p]);
         const float iw = p == 0 ? 3.f : (p < 7 ? 18.f : 36.f);
         const ffl z = ff_add_f(ff_div(ff_prod(f[p], iw), ffl{r, 0.f}), -1.f);
@@ -191,6 +225,8 @@ __device__ __forceinline__ ffl h0_ff(const float *f, const float *d, float r)
         const ffl l = __all_sync(__activemask(), fabsf(z.h) <= 0.125f) ? ff_log1p_small(z) : ff_log1p(z);
         T = ff_add(T, ff_mul_f(l, d[p]));
     }
+    S = grp_sum(gp, S);
+    T = grp_sum(gp, T);
     // ln r to FP32 accuracy suffices: sum D is at the rounding level of rho
     return ff_add(ff_mul_f(S, 1.f + logf(r)), T);
 }
@@ -198,12 +234,12 @@ __device__ __forceinline__ ffl h0_ff(const float *f, const float *d, float r)
 // h(a) in float-float, h'(a) and h''(a) = sum f x^2 / (1 + a x) in FP32, at a
 // float-float alpha
 __device__ __forceinline__ void h_ff(const float *f, const float *d, ffl a, ffl a0, ffl *h, float *hp,
-                                     float *hpp)
+                                     float *hpp, const Grp &gp)
 {
-    ffl acc = ff_mul(a, a0);
+    ffl acc = {0.f, 0.f};
     float g = 0.f, g2 = 0.f;
 #pragma unroll 1
-    for (int p = 0; p < Q; p++) {
+    for (int p = gp.j; p < Q; p += gp.L) {
         const ffl x = ff_div_f(d[p], f[p]);
         const ffl y = ff_mul(a, x);
         const ffl l = ff_log1p(y);
@@ -214,9 +250,9 @@ __device__ __forceinline__ void h_ff(const float *f, const float *d, ffl a, ffl 
         g = fmaf(d[p], l.h, g);
         g2 = fmaf(f[p] * x.h, __fdividef(x.h, 1.f + y.h), g2);
     }
-    *h = acc;
-    *hp = g + a0.h;
-    *hpp = g2;
+    *h = ff_add(grp_sum(gp, acc), ff_mul(a, a0));
+    *hp = grp_sum(gp, g) + a0.h;
+    *hpp = grp_sum(gp, g2);
 }
 
 // h(a) from the site's moments when |a x_p| <= 1/16 for every p: the series
@@ -232,7 +268,7 @@ struct MomFF {
     float xmax;
 };
 
-__device__ __forceinline__ void mom_ff(const float *f, const float *d, MomFF &m)
+__device__ __forceinline__ void mom_ff(const float *f, const float *d, MomFF &m, const Grp &gp)
 {
     m.M2 = ffl{0.f, 0.f};
     m.M3 = ffl{0.f, 0.f};
@@ -240,7 +276,7 @@ __device__ __forceinline__ void mom_ff(const float *f, const float *d, MomFF &m)
     for (int n = 0; n < 9; n++) m.Mh[n] = 0.f;
     m.xmax = 0.f;
 #pragma unroll 1
-    for (int p = 0; p < Q; p++) {
+    for (int p = gp.j; p < Q; p += gp.L) {
         const ffl x = ff_div_f(d[p], f[p]);
         const ffl fx2 = ff_mul_f(ff_mul(x, x), f[p]);
         const ffl fx3 = ff_mul_f(fx2, x.h);
@@ -254,6 +290,11 @@ __device__ __forceinline__ void mom_ff(const float *f, const float *d, MomFF &m)
         }
         m.xmax = fmaxf(m.xmax, fabsf(x.h));
     }
+    m.M2 = grp_sum(gp, m.M2);
+    m.M3 = grp_sum(gp, m.M3);
+#pragma unroll
+    for (int n = 4; n <= 8; n++) m.Mh[n] = grp_sum(gp, m.Mh[n]);
+    m.xmax = grp_max(gp, m.xmax);
 }
 
 __device__ __forceinline__ ffl h_mom(ffl a, ffl a0, const MomFF &m, float *hp, float *hpp)
@@ -286,25 +327,28 @@ __device__ __forceinline__ ffl h_mom(ffl a, ffl a0, const MomFF &m, float *hp, f
 // when |h| <= tol/2, else one Newton step a' = a - h/h' and accept a' when the
 // quadratic-convergence bound 3/4 h'' (a' - a)^2 plus 1e-11 rho (the pairs'
 // evaluation error) is within tol/2, else evaluate again (at most 3 steps).
-// Returns (alpha high, alpha low, H-error, accepted). Not inlined: one copy of
-// the code, entered only by warps that hold a site needing it.
-static __device__ __noinline__ float4 alpha_guard(const float *f, const float *d, float rho, float a, float S)
+// Returns (alpha high, alpha low, H-error, accepted) on every lane of the
+// group (j its member index, L its size). Not inlined: one copy of the code,
+// entered only by warps that hold a site needing it.
+static __device__ __noinline__ float4 alpha_guard(const float *f, const float *d, float rho, float a, float S,
+                                                  int j, int L)
 {
+    const Grp gp = grp_make(j, L);
     const float tol = 1e-10f * rho;
-    const ffl A0 = h0_ff(f, d, rho);
+    const ffl A0 = h0_ff(f, d, rho, gp);
     // the moment series only where it holds (S = max |Delta/f| of the FP32
     // setup, with margin), chosen for the whole warp
     const bool use_mom = __all_sync(__activemask(), a * S <= 0.06f);
     MomFF mom;
     mom.xmax = 1e30f;
-    if (use_mom) mom_ff(f, d, mom);
+    if (use_mom) mom_ff(f, d, mom, gp);
     ffl al = {a, 0.f};
 #pragma unroll 1
     for (int it = 0; it < 3; it++) {
         ffl hf;
         float hp, hpp;
         if (__all_sync(__activemask(), al.h * mom.xmax <= 0.0625f)) hf = h_mom(al, A0, mom, &hp, &hpp);
-        else h_ff(f, d, al, A0, &hf, &hp, &hpp);
+        else h_ff(f, d, al, A0, &hf, &hp, &hpp, gp);
         if (fabsf(hf.h) <= 0.5f * tol) return make_float4(al.h, al.l, fabsf(hf.h) / rho, 1.f);
         const float delta = hf.h / hp;
         al = ff_add_f(al, -delta);
@@ -479,7 +523,7 @@ __device__ __forceinline__ AlphaOutF alpha_fp32_solve(const float *f, const floa
     }
     if (need) {
         o.guarded = 1;
-        const float4 gr = alpha_guard(f, d, rho, a, st.S);
+        const float4 gr = alpha_guard(f, d, rho, a, st.S, 0, 1);
         o.alpha = gr.x;
         o.alpha_lo = gr.y;
         o.herr = gr.z;
