@@ -625,9 +625,10 @@ __global__ void k_phi_shift(Geom g, Bufs b)
 // transport mode the D3Q7 charge update. Optional diagnostics per block.
 // ===========================================================================
 // Guarded FP32 alpha: lanes whose root needs the float-float guard queue their
-// inputs in shared memory; after a barrier the block's first threads run the
-// queued guards together (full warps instead of a few lanes in many warps),
-// and the results return through the queue. The queue holds one entry per
+// inputs in shared memory; after a barrier the block's threads run the
+// queued guards together, L lanes per site (L = 8, 4, 2 or 1 for up to 16,
+// 32, 64 or 128 sites: full warps instead of a few lanes in many warps), and
+// the results return through the queue. The queue holds one entry per
 // thread of the block (the kernel is launched with 128 threads).
 constexpr int kGuardQ = 128;
 struct GuardEntry {
@@ -798,7 +799,14 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
         static_assert(!kQueue || kGuardQ >= 128, "one guard-queue entry per thread of a 128-thread block");
         __syncthreads();
         const int nq = gq_n;
-        if (tid < nq) gq[tid].res = alpha_guard(gq[tid].f, gq[tid].d, gq[tid].rho, gq[tid].a, gq[tid].S);
+        // L lanes per queued site (the fewer the sites, the more lanes each)
+        const int lg = nq <= 16 ? 3 : (nq <= 32 ? 2 : (nq <= 64 ? 1 : 0));
+        const int site = tid >> lg, j = tid & ((1 << lg) - 1);
+        if (site < nq) {
+            const GuardEntry &e = gq[site];
+            const float4 gr = alpha_guard(e.f, e.d, e.rho, e.a, e.S, j, 1 << lg);
+            if (j == 0) gq[site].res = gr;
+        }
         __syncthreads();
         if (gslot >= 0) {
             const float4 gr = gq[gslot].res;
