@@ -37,7 +37,7 @@ struct elbm_handle {
     Ops ops;
     cudaStream_t s;            // the caller's stream: all work runs here
     int has_dirichlet;
-    double *pin;               // pinned host scalars
+    double *pin;               // pinned host scalars; [8], [9]: the step's status words (below)
     long long step;
     size_t pop_bytes, g_bytes, sc_bytes;
     MGOps mg;
@@ -508,6 +508,16 @@ bool enqueue_step(elbm_handle *h, int parity, cudaStream_t s, int sections, int 
     return ok;
 }
 
+// The two words elbm_step checks after a step, copied into pinned host
+// memory as the last nodes of a step graph (one wait on the stream, no
+// synchronous copies): the non-finite site count and the Poisson no-convergence
+// counter.
+bool enqueue_status(elbm_handle *h, cudaStream_t s)
+{
+    return cuda_ok(cudaMemcpyAsync(h->pin + 8, h->b.diag + 15, sizeof(double), cudaMemcpyDeviceToHost, s)) &&
+           cuda_ok(cudaMemcpyAsync(h->pin + 9, h->b.scal + S_NOCONV, sizeof(double), cudaMemcpyDeviceToHost, s));
+}
+
 bool capture_step(elbm_handle *h, int parity, cudaGraphExec_t *out, int sections = 7)
 {
     cudaStream_t s = h->cap;
@@ -515,6 +525,7 @@ bool capture_step(elbm_handle *h, int parity, cudaGraphExec_t *out, int sections
     if (!cuda_ok(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal))) return false;
     int n_pre = 0, n_body = 0, n_post = 0;
     bool ok = enqueue_step(h, parity, s, sections, n_pre, n_body, n_post);
+    if (sections == 7) ok = ok && enqueue_status(h, s);
     ok = cuda_ok(cudaStreamEndCapture(s, &graph)) && ok;
     if (ok) ok = cuda_ok(cudaGraphInstantiate(out, graph, 0));
     if (graph) cudaGraphDestroy(graph);
@@ -554,6 +565,7 @@ bool capture_batch(elbm_handle *B, int parity, cudaGraphExec_t *out, bool prolog
         } else {
             ok = ok && enqueue_step(h, parity, h->cap, 7, n_pre, n_body, n_post);
         }
+        if (!prologue) ok = ok && enqueue_status(h, h->cap);
         ok = ok && cuda_ok(cudaEventRecord(B->ev_join[i], h->cap));
         ok = ok && cuda_ok(cudaStreamWaitEvent(s, B->ev_join[i], 0));
     }
@@ -1004,10 +1016,7 @@ elbm_status elbm_step(elbm_handle *h, int nsteps)
         if (nsteps > 0) {
             for (int i = 0; i < h->n_sub; i++) {
                 elbm_handle *q = h->sub[i];
-                double v[2] = {0.0, 0.0};
-                if (!cuda_ok(cudaMemcpy(&v[0], q->b.diag + 15, sizeof(double), cudaMemcpyDeviceToHost)) ||
-                    !cuda_ok(cudaMemcpy(&v[1], q->b.scal + S_NOCONV, sizeof(double), cudaMemcpyDeviceToHost)))
-                    return ELBM_E_CUDA;
+                const double v[2] = {q->pin[8], q->pin[9]};  // copied by the graph's last nodes
                 if (v[0] != 0.0) worst = ELBM_E_NUMERIC;
                 if (v[1] > q->noconv_seen) {
                     q->noconv_seen = v[1];
@@ -1054,11 +1063,19 @@ elbm_status elbm_step(elbm_handle *h, int nsteps)
     if (!cuda_ok(cudaStreamSynchronize(h->s))) return ELBM_E_CUDA;
     if (nsteps > 0) {
         double v[2] = {0.0, 0.0};
-        if (h->p.diag_every > 0 || h->use_graph) {
-            if (!cuda_ok(cudaMemcpy(&v[0], h->b.diag + 15, sizeof(double), cudaMemcpyDeviceToHost))) return ELBM_E_CUDA;
+        if (h->use_graph && !prof) {  // copied by the step graph's last nodes
+            v[0] = h->pin[8];
+            v[1] = h->pin[9];
             if (v[0] != 0.0) return ELBM_E_NUMERIC;
+        } else {
+            if (h->p.diag_every > 0 || h->use_graph) {
+                if (!cuda_ok(cudaMemcpy(&v[0], h->b.diag + 15, sizeof(double), cudaMemcpyDeviceToHost)))
+                    return ELBM_E_CUDA;
+                if (v[0] != 0.0) return ELBM_E_NUMERIC;
+            }
+            if (!cuda_ok(cudaMemcpy(&v[1], h->b.scal + S_NOCONV, sizeof(double), cudaMemcpyDeviceToHost)))
+                return ELBM_E_CUDA;
         }
-        if (!cuda_ok(cudaMemcpy(&v[1], h->b.scal + S_NOCONV, sizeof(double), cudaMemcpyDeviceToHost))) return ELBM_E_CUDA;
         if (v[1] > h->noconv_seen) { h->noconv_seen = v[1]; return ELBM_W_POISSON_NOCONV; }
     }
     return ELBM_OK;
