@@ -106,3 +106,29 @@ def test_pipelined_batch_keeps_populations_bitwise():
     # stepped alone after the batch, the instance ahead repeats its solve
     grouped[1].step(1)
     assert np.linalg.norm(grouped[1].get("f") - s6[1].get("f")) <= 1e-5 * np.linalg.norm(s6[1].get("f"))
+
+
+def test_batch_reports_each_instance_status():
+    """The step's status words come back through the batch graph: a
+    non-finite instance makes the batch step fail with ELBM_E_NUMERIC, and a
+    Poisson solve stopped at its cap gives the warning, as for a lone
+    instance."""
+    from paper_1612_05404_gb300 import elbm
+    cfg = W.base_params(shape=(8, 8, 8), precision="fp64", charge_model="transport", poisson_maxit=50)
+    rho = np.ones(512)
+    rho[100] = -1.0
+    good = _make()
+    bad = elbm.Sim(cfg, dict(rho=rho))
+    batch = elbm.Batch(good + [bad])
+    with pytest.raises(elbm.ElbmError) as ei:
+        batch.step(1)
+    assert ei.value.code == elbm.E_NUMERIC
+    batch.close()
+
+    cfg2, fields2 = W.charged_drop_at_rest(n=12, radius=3.5)
+    cfg2.update(precision="fp64", poisson_solver="sor", poisson_maxit=3, poisson_check_every=1)
+    capped = elbm.Sim(cfg2, fields2)
+    batch = elbm.Batch(_make() + [capped])
+    assert batch.step(1) == elbm.W_POISSON_NOCONV
+    assert capped.diag()["poisson_sweeps"] == 3
+    batch.close()
