@@ -74,7 +74,10 @@ __device__ __forceinline__ float l_f32(float z)
 }
 
 // ---------------------------------------------------------------------------
-// float-float arithmetic
+// float-float arithmetic. The rounded products that an error term is taken
+// against are formed with __fmul_rn, which the compiler never fuses with a
+// later addition: a fused p + e would count the product's rounding error
+// twice, and whether the compiler fuses can change with register pressure.
 // ---------------------------------------------------------------------------
 struct ffl { float h, l; };
 
@@ -102,19 +105,19 @@ __device__ __forceinline__ ffl ff_add_f(ffl a, float b)
 __device__ __forceinline__ ffl ff_neg(ffl a) { return {-a.h, -a.l}; }
 __device__ __forceinline__ ffl ff_prod(float a, float b)
 {
-    const float p = a * b;
+    const float p = __fmul_rn(a, b);
     return {p, fmaf(a, b, -p)};
 }
 __device__ __forceinline__ ffl ff_mul(ffl a, ffl b)
 {
-    const float p = a.h * b.h;
+    const float p = __fmul_rn(a.h, b.h);
     float e = fmaf(a.h, b.h, -p);
     e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
     return ff_norm(p, e);
 }
 __device__ __forceinline__ ffl ff_mul_f(ffl a, float b)
 {
-    const float p = a.h * b;
+    const float p = __fmul_rn(a.h, b);
     const float e = fmaf(a.l, b, fmaf(a.h, b, -p));
     return ff_norm(p, e);
 }
@@ -418,9 +421,9 @@ __device__ __forceinline__ void alpha_fp32_setup(const float *f, const float *d,
         const float e = (w32 - (f[p] - bb)) + (fdev[p] - bb);
         const float dw = float(double(w32) - wq(p));
         const float iw = float(1.0 / wq(p));
-        const float wd = w32 * drho;
+        const float wd = __fmul_rn(w32, drho);   // not fused into the difference below
         const float wde = fmaf(w32, drho, -wd);  // exact error of the product (TwoProd)
-        const float z = ((fdev[p] - wd) + ((dw * rho - e) - wde)) * iw * irho;
+        const float z = (__fsub_rn(fdev[p], wd) + ((dw * rho - e) - wde)) * iw * irho;
         const float dl = d[p] * l_f32(z);
         if (p & 1) tl1 += dl; else tl0 += dl;
         tla += fabsf(dl);

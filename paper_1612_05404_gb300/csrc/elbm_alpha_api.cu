@@ -21,27 +21,11 @@ k_alpha_eval(const float *__restrict__ dev, long long n, float eq_tol_f, double 
     float d[Q];
 #pragma unroll
     for (int p = 0; p < Q; p++) d[p] = dev[(long long)p * n + i];
-    // moments and Eq. (2) in FP32, in the order of the FP32 collision
-    float rs = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-    for (int p = 0; p < Q; p++) {
-        rs += d[p];
-        jx += float(cx(p)) * d[p];
-        jy += float(cy(p)) * d[p];
-        jz += float(cz(p)) * d[p];
-    }
-    const float r = 1.f + rs, drho = rs;
-    const float ir = 1.f / r;
-    const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
-    const float usq = ux * ux + uy * uy + uz * uz;
-    float D[Q], f[Q];
-#pragma unroll
-    for (int p = 0; p < Q; p++) {
-        const float P = Ppoly<float>(p, ux, uy, uz, usq);
-        D[p] = float(wq(p)) * (drho + r * P) - d[p];
-        f[p] = float(wq(p)) + d[p];
-        if (delta) delta[(long long)p * n + i] = D[p];
-    }
+    // moments and Eq. (2) in FP32, as the FP32 collision forms them
+    float D[Q], f[Q], drho;
+    const float r = site_delta(d, f, D, &drho);
+    if (delta)
+        for (int p = 0; p < Q; p++) delta[(long long)p * n + i] = D[p];
     double a;
     float he;
     int st;
@@ -65,32 +49,6 @@ k_alpha_eval(const float *__restrict__ dev, long long n, float eq_tol_f, double 
     alpha[i] = a;
     if (herr) herr[i] = he;
     if (status) status[i] = st;
-}
-
-// FP32 moments and Delta of a site from its deviations, in the order of the
-// FP32 collision; returns rho
-__device__ __forceinline__ float site_delta(const float *d, float *f, float *D, float *drho_out)
-{
-    float rs = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-    for (int p = 0; p < Q; p++) {
-        rs += d[p];
-        jx += float(cx(p)) * d[p];
-        jy += float(cy(p)) * d[p];
-        jz += float(cz(p)) * d[p];
-    }
-    const float r = 1.f + rs;
-    const float ir = 1.f / r;
-    const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
-    const float usq = ux * ux + uy * uy + uz * uz;
-#pragma unroll
-    for (int p = 0; p < Q; p++) {
-        const float P = Ppoly<float>(p, ux, uy, uz, usq);
-        D[p] = float(wq(p)) * (rs + r * P) - d[p];
-        f[p] = float(wq(p)) + d[p];
-    }
-    *drho_out = rs;
-    return r;
 }
 
 // The learned proposal: series start, features and the BF16 tensor-core

@@ -121,6 +121,68 @@ __device__ __forceinline__ T Ppoly(int p, T ux, T uy, T uz, T usq)
 }
 
 // ---------------------------------------------------------------------------
+// Delta = f^eq(rho, u) - f with deviation storage (FP32 arithmetic), from the
+// deviations d_p = f_p - w_p and drho = rho - 1 as an unevaluated sum
+// (drho_hi + drho_lo). At a low-density site w_p drho and d_p nearly cancel,
+// so their difference is formed in one rounding (fmaf), the FP32 rounding of
+// the weight dw_p = w_p - fl(w_p) is added back, and the compensated sum of
+// the result is taken off Delta_0: the exact Delta conserves mass (f^eq has
+// the density rho), and an O(ulp) residual would enter h'(0) of Eq.
+// (entropic) through (1 + ln rho) sum Delta, which is larger than h'(0)
+// itself near equilibrium.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum_acc(float v, float &s, float &c)
+{
+    const float t = s + v;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (v - bp);
+    s = t;
+}
+
+__device__ __forceinline__ void delta_dev(const float *d, float drho_hi, float drho_lo, float r, float ux, float uy,
+                                          float uz, float usq, float *D)
+{
+    float s = 0.f, c = 0.f;
+#pragma unroll
+    for (int p = 0; p < Q; p++) {
+        const float w32 = float(wq(p));
+        const float dw = float(wq(p) - double(w32));
+        const float P = Ppoly<float>(p, ux, uy, uz, usq);
+        D[p] = fmaf(w32, drho_hi, -d[p]) + fmaf(w32, drho_lo, fmaf(dw, drho_hi, w32 * r * P));
+        two_sum_acc(D[p], s, c);
+    }
+    D[0] -= s + c;
+}
+
+// FP32 moments and Delta of a site from its deviations d (populations
+// f = w + d), as the FP32 collision forms them; returns rho
+__device__ __forceinline__ float site_delta(const float *d, float *f, float *D, float *drho_out)
+{
+    float rs = 0.f, rs_lo = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int p = 0; p < Q; p++) {
+        two_sum_acc(d[p], rs, rs_lo);
+        jx += float(cx(p)) * d[p];
+        jy += float(cy(p)) * d[p];
+        jz += float(cz(p)) * d[p];
+    }
+    {
+        const float t = rs + rs_lo;
+        rs_lo = rs_lo - (t - rs);
+        rs = t;
+    }
+    const float r = 1.f + rs;
+    const float ir = 1.f / r;
+    const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
+    const float usq = ux * ux + uy * uy + uz * uz;
+    delta_dev(d, rs, rs_lo, r, ux, uy, uz, usq, D);
+#pragma unroll
+    for (int p = 0; p < Q; p++) f[p] = float(wq(p)) + d[p];
+    *drho_out = rs;
+    return r;
+}
+
+// ---------------------------------------------------------------------------
 // Matrix 2-norm of the symmetric stress (Sec. II B): max |eigenvalue|, by
 // the closed-form trigonometric solution of the characteristic cubic
 // (Smith 1961).

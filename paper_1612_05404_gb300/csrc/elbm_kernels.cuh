@@ -675,13 +675,19 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
         const sc *phi = (const sc *)b.phi;
 #pragma unroll
         for (int p = 0; p < Q; p++) f[p] = gather_pop<PR>(g, b.mask, b.fA, n, p);
-        ct rs = 0;
+        ct rs = 0, rs_lo = 0;  // deviations: sum d_p compensated (Delta below)
 #pragma unroll
         for (int p = 0; p < Q; p++) {
-            rs += f[p];
+            if constexpr (T::dev) two_sum_acc(f[p], rs, rs_lo);
+            else rs += f[p];
             jx += ct(cx(p)) * f[p];
             jy += ct(cy(p)) * f[p];
             jz += ct(cz(p)) * f[p];
+        }
+        if constexpr (T::dev) {  // the pair (rs, rs_lo) normalised
+            const ct t = rs + rs_lo;
+            rs_lo = rs_lo - (t - rs);
+            rs = t;
         }
         r = T::dev ? ct(1) + rs : rs;
         drho = T::dev ? rs : rs - ct(1);
@@ -739,10 +745,11 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
         ir = ct(1) / r;
         ux = jx * ir; uy = jy * ir; uz = jz * ir;
         usq = ux * ux + uy * uy + uz * uz;
+        if constexpr (T::dev) {
+            delta_dev(f, drho, rs_lo, r, ux, uy, uz, usq, D);
+        } else {
 #pragma unroll
-        for (int p = 0; p < Q; p++) {
-            ct P = Ppoly<ct>(p, ux, uy, uz, usq);
-            D[p] = T::dev ? ct(wq(p)) * (drho + r * P) - f[p] : ct(wq(p)) * r * (ct(1) + P) - f[p];
+            for (int p = 0; p < Q; p++) D[p] = ct(wq(p)) * r * (ct(1) + Ppoly<ct>(p, ux, uy, uz, usq)) - f[p];
         }
 
         // Eq. (entropic)
@@ -978,24 +985,29 @@ __global__ void __launch_bounds__(128) k_alpha_mlp(Geom g, Phys ph, Bufs b)
         float f[Q];
 #pragma unroll
         for (int p = 0; p < Q; p++) f[p] = float(gather_pop<PR>(g, b.mask, b.fA, n, p));
-        float rs = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+        float rs = 0.f, rs_lo = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
         for (int p = 0; p < Q; p++) {
-            rs += f[p];
+            two_sum_acc(f[p], rs, rs_lo);
             jx += float(cx(p)) * f[p];
             jy += float(cy(p)) * f[p];
             jz += float(cz(p)) * f[p];
         }
-        const float r = 1.f + rs, drho = rs;
+        {
+            const float t = rs + rs_lo;
+            rs_lo = rs_lo - (t - rs);
+            rs = t;
+        }
+        const float r = 1.f + rs;
         const float ir = 1.f / r;
         const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
         const float usq = ux * ux + uy * uy + uz * uz;
-        float xv[Q];
+        float D[Q], xv[Q];
+        delta_dev(f, rs, rs_lo, r, ux, uy, uz, usq, D);
         float S = 0.f;
 #pragma unroll
         for (int p = 0; p < Q; p++) {
-            const float D = float(wq(p)) * (drho + r * Ppoly<float>(p, ux, uy, uz, usq)) - f[p];
-            xv[p] = __fdividef(D, float(wq(p)) + f[p]);
+            xv[p] = __fdividef(D[p], float(wq(p)) + f[p]);
             S = fmaxf(S, fabsf(xv[p]));
         }
         mlp_site_features(xv, S > 0.f ? S : 1.f, row);

@@ -234,26 +234,13 @@ __global__ void __launch_bounds__(128) k_alpha_features(const float *__restrict_
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float d[Q], f[Q], D[Q];
-    float rs = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+    float d[Q], f[Q], D[Q], drho;
 #pragma unroll
-    for (int p = 0; p < Q; p++) {
-        d[p] = dev[(long long)p * n + i];
-        rs += d[p];
-        jx += float(cx(p)) * d[p];
-        jy += float(cy(p)) * d[p];
-        jz += float(cz(p)) * d[p];
-    }
-    const float r = 1.f + rs, ir = 1.f / r;
-    const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
-    const float usq = ux * ux + uy * uy + uz * uz;
+    for (int p = 0; p < Q; p++) d[p] = dev[(long long)p * n + i];
+    site_delta(d, f, D, &drho);
     float S = 0.f;
 #pragma unroll
-    for (int p = 0; p < Q; p++) {
-        D[p] = float(wq(p)) * (rs + r * Ppoly<float>(p, ux, uy, uz, usq)) - d[p];
-        f[p] = float(wq(p)) + d[p];
-        S = fmaxf(S, fabsf(D[p] / f[p]));
-    }
+    for (int p = 0; p < Q; p++) S = fmaxf(S, fabsf(D[p] / f[p]));
     if (!(S > 0.f)) S = 1.f;
 #pragma unroll
     for (int p = 0; p < Q; p++) X[(long long)p * n + i] = (D[p] / f[p]) / S;
