@@ -499,15 +499,22 @@ __device__ __forceinline__ AlphaOutF alpha_fp32_solve(const float *f, const floa
             } else {
                 if (h < 0.f) lo = a; else hi = a;
                 float an = a - h / hpl;
-                const bool newton = an > lo && an < hi;
-                if (!newton) an = 0.5f * (lo + hi);
-                const float step = fabsf(an - a);
-                step_prev = step;
-                a = an;
-                const float pred = 0.5f * hpp * step * step;  // |h| after the step, to leading order
-                if (newton && (pred <= 0x1p-25f * a * fabsf(hpl) || step <= 1e-6f * a)) {
+                if (an == a) {
+                    // the Newton step is below the FP32 resolution of alpha: a
+                    // is the root at this precision (a bracket bound now, so
+                    // the strict test below would send it to a bisection)
                     conv = true;
-                    hres = pred;
+                } else {
+                    const bool newton = an > lo && an < hi;
+                    if (!newton) an = 0.5f * (lo + hi);
+                    const float step = fabsf(an - a);
+                    step_prev = step;
+                    a = an;
+                    const float pred = 0.5f * hpp * step * step;  // |h| after the step, to leading order
+                    if (newton && (pred <= 0x1p-25f * a * fabsf(hpl) || step <= 1e-6f * a)) {
+                        conv = true;
+                        hres = pred;
+                    }
                 }
             }
         }

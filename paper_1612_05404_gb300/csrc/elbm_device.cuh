@@ -252,10 +252,14 @@ __device__ __forceinline__ T carreau_nu(const Cst<T> &k, bool newtonian, T Pn, T
             T dnu = qdiv((k.nu0 - k.nu_inf) * T(2) * k.nexp * k.lam * k.lam * x * pw, base);
             T gp = T(1) + qdiv(T(2) * cs2 * A * dnu, den * den);
             T xn = x - qdiv(gx, gp);
-            if (!(xn > lo && xn < hi)) xn = T(0.5) * (lo + hi);
-            done = fabs(xn - x) <= eps * fabs(x) || hi - lo <= eps * hi ||
-                   (sizeof(T) == 4 && fabs(gx) <= T(5e-7) * (x + qdiv(A * cs2, den)));
-            x = xn;
+            if (xn == x) {
+                done = true;  // step below the resolution of x (x is a bracket bound now)
+            } else {
+                if (!(xn > lo && xn < hi)) xn = T(0.5) * (lo + hi);
+                done = fabs(xn - x) <= eps * fabs(x) || hi - lo <= eps * hi ||
+                       (sizeof(T) == 4 && fabs(gx) <= T(5e-7) * (x + qdiv(A * cs2, den)));
+                x = xn;
+            }
         }
         if (sizeof(T) == 8) {
             if (done) break;
@@ -325,6 +329,7 @@ __device__ __forceinline__ AlphaOut alpha_fp64(const double *f, const double *d,
         if (h == 0.0) break;
         if (h < 0.0) lo = a; else hi = a;
         double an = a - h / hp;
+        if (an == a) break;  // step below the FP64 resolution of alpha
         if (!(an > lo && an < hi)) an = 0.5 * (lo + hi);
         if (fabs(an - a) <= 4e-16 * fabs(a) || hi - lo <= 4e-16 * hi) { a = an; break; }
         a = an;
