@@ -72,3 +72,36 @@ def test_alpha_fp64_root():
     root = st == 0
     err = _h_err(f[:, root], D[:, root], a[root])
     assert err.max() <= 1e-13, err.max()
+
+
+def _near_equilibrium_sites(n=4096, seed=5):
+    """Gas- and liquid-phase sites (rho 0.16 and 1) a relative 1e-5 .. 1e-3
+    from the polynomial equilibrium: there the series start is the root to
+    FP32 resolution and the first Newton step rounds to zero."""
+    rng = np.random.default_rng(seed)
+    c, _, _ = oracle.lattice(3)
+    out = np.empty((19, n))
+    for i in range(n):
+        rho = 0.16 if i % 2 else 1.0
+        u = rng.normal(scale=1e-3, size=3)
+        eps = 10.0 ** rng.uniform(-5, -3)
+        feq = oracle.feq(3, rho, u)
+        eta = rng.normal(size=19)
+        eta -= eta.mean()
+        out[:, i] = feq * (1.0 + eps * eta)
+    return out
+
+
+@pytest.mark.parametrize("aprec", ["fp32", "fp32_fast"])
+def test_alpha_near_equilibrium_newton_step_below_resolution(aprec):
+    f, D, a, he, st = _run(_near_equilibrium_sites(), aprec)
+    root = np.isin(st, (0, 5))
+    assert root.sum() > 3000
+    # one FP32 evaluation suffices: the start is the root at this precision
+    assert np.mean(st[root] == 0) > 0.95
+    err = _h_err(f[:, root], D[:, root], a[root])
+    assert np.all(err <= np.maximum(he[root] * 1.0001, 1e-10) + 1e-15), err.max()
+    # the root of the FP32 Delta moves with that Delta's rounding (~1 % at a
+    # relative departure of 1e-5); a bisection towards alpha_max lands far off
+    dev = np.abs(a[root] - 2.0)
+    assert np.all(dev < 0.5), (dev.max(), a[root][np.argmax(dev)])
