@@ -235,6 +235,28 @@ def test_fp32_single_step_from_identical_state(E, aprec):
     assert max(errs.values()) < 1e-5, errs
 
 
+def test_fp32_single_step_populations_and_viscosity(E):
+    """The FP32 collision's own outputs, one step from the oracle's state:
+    post-collision populations within 1e-6 relative L2 (FP32 deviation
+    storage rounds d = f - w to 2^-24 |d|, up to 3e-7 of f in the gas phase,
+    rho 0.16; alpha enters through alpha beta Delta) and the Carreau
+    viscosity within 5e-5 relative at every fluid site (FP32 root stopped at
+    a relative step of 2e-6)."""
+    cfg, fields = W.drop_in_field(E0=1e-3, n=16, radius=4.5, precision="fp32")
+    cfg.update(store_macro=1, alpha_precision="fp32")
+    o = oracle.Sim(dict(cfg, poisson_tol=1e-13), fields)
+    o.step(6)
+    N = o.N
+    state = dict(fields, f=o.f.copy(), q=o.g.reshape(7, N).sum(0))
+    g = E.Sim(cfg, state)
+    g.step(1)
+    o.step(1)
+    assert rel_l2(g.get("f"), o.f) <= 1e-6
+    nu_g, nu_o = g.get("nu"), o.nu
+    fluid = nu_o > 0
+    assert np.max(np.abs(nu_g[fluid] - nu_o[fluid]) / nu_o[fluid]) <= 5e-5
+
+
 @pytest.mark.parametrize("aprec", ["fp64", "fp32"])
 def test_fp32_parity_multi_step(E, aprec):
     """FP32 against the FP64 oracle over several steps from the same initial
