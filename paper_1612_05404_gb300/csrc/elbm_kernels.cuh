@@ -1491,46 +1491,10 @@ __device__ __forceinline__ T tail_resid(const Geom &g, const T *e, const T *b, c
 // The tail runs as one CTA of (BX, BY, BZ) threads: a level is swept with
 // x = tx + BX i (or, in a red-black pass, x = 2 (tx + BX i) + parity so that
 // every thread owns cells of the active colour), y = ty + BY j, z = tz + BZ k;
-// no integer division, no idle half in a colour pass. Levels of at most
-// kTailWarpCells cells (the coarsest two or three) are swept by warp 0 alone
-// with warp barriers: a block barrier over 32 warps per pass of a few dozen
-// cells would cost more than the pass.
-constexpr int kTailWarpCells = 64;
-
-struct TMap {
-    int tx, ty, tz, bx, by, bz;
-    bool warp;  // warp 0 alone (warp barriers) instead of the whole CTA
-};
-
-__device__ __forceinline__ TMap tmap_block()
-{
-    return TMap{(int)threadIdx.x, (int)threadIdx.y, (int)threadIdx.z,
-                (int)blockDim.x, (int)blockDim.y, (int)blockDim.z, false};
-}
-
-// the 32 lanes of warp 0 as bx x by x bz for a level nx x ny x nz (bx covers
-// half a row); lanes beyond bx by bz get no cells
-__device__ __forceinline__ TMap tmap_warp(int nx, int ny, int nz, int lane)
-{
-    int bx = (nx + 1) / 2;
-    if (bx > 32) bx = 32;
-    int by = ny < 32 / bx ? ny : 32 / bx;
-    int bz = nz < 32 / (bx * by) ? nz : 32 / (bx * by);
-    if (bz < 1) bz = 1;
-    TMap m{lane % bx, (lane / bx) % by, lane / (bx * by), bx, by, bz, true};
-    if (m.tz >= bz) m.tz = nz;  // idle lane
-    return m;
-}
-
-__device__ __forceinline__ void tsync(const TMap &m)
-{
-    if (m.warp) __syncwarp();
-    else __syncthreads();
-}
-
+// no integer division, no idle half in a colour pass.
 template <typename T>
 __device__ void tail_smooth(const Geom &g, const MGTail &t, T *E, T *B, T *P, const unsigned char *M, int k,
-                            int sweeps, const TMap &tm)
+                            int sweeps)
 {
     const int nx = t.nx[k], ny = t.ny[k], nz = t.nz[k];
     const unsigned char *m = M ? M + t.off[k] : nullptr;
@@ -1541,9 +1505,9 @@ __device__ void tail_smooth(const Geom &g, const MGTail &t, T *E, T *B, T *P, co
     const int n_[3] = {nx, ny, nz};
     for (int it = 0; it < 2 * sweeps; it++) {
         const int color = it & 1;
-        for (int z = tm.tz; z < nz; z += tm.bz)
-            for (int y = tm.ty; y < ny; y += tm.by)
-                for (int xi = tm.tx;; xi += tm.bx) {
+        for (int z = threadIdx.z; z < nz; z += blockDim.z)
+            for (int y = threadIdx.y; y < ny; y += blockDim.y)
+                for (int xi = threadIdx.x;; xi += blockDim.x) {
                     const int x = 2 * xi + ((y + z + color) & 1);
                     if (x >= nx) break;
                     const int s = x + nx * (y + ny * z);
@@ -1568,86 +1532,8 @@ __device__ void tail_smooth(const Geom &g, const MGTail &t, T *E, T *B, T *P, co
                         }
                     if (den > T(0)) e[s] = num / den;
                 }
-        tsync(tm);
+        __syncthreads();
     }
-}
-
-// coarse permittivity of tail level k (>= 1): the mean of its 8 children
-template <typename T>
-__device__ void tail_eps(const MGTail &t, T *P, int k, const TMap &tm)
-{
-    const int nx = t.nx[k], ny = t.ny[k], nz = t.nz[k], fx = t.nx[k - 1], fy = t.ny[k - 1];
-    const T *pf = P + t.off[k - 1];
-    for (int Z = tm.tz; Z < nz; Z += tm.bz)
-        for (int Y = tm.ty; Y < ny; Y += tm.by)
-            for (int X = tm.tx; X < nx; X += tm.bx) {
-                T sum = 0;
-                for (int c = 0; c < 8; c++)
-                    sum += pf[(2 * X + (c & 1)) + fx * ((2 * Y + ((c >> 1) & 1)) + fy * (2 * Z + (c >> 2)))];
-                P[t.off[k] + X + nx * (Y + ny * Z)] = sum * T(0.125);
-            }
-    tsync(tm);
-}
-
-// restriction of level k's residual to level k + 1 (sum of the 8 children),
-// whose correction starts at 0
-template <typename T>
-__device__ void tail_restrict(const Geom &g, const MGTail &t, T *E, T *B, T *P, const unsigned char *M, int k,
-                              const TMap &tm)
-{
-    const int nx = t.nx[k + 1], ny = t.ny[k + 1], nz = t.nz[k + 1];
-    const int fx = t.nx[k], fy = t.ny[k], fz = t.nz[k];
-    for (int Z = tm.tz; Z < nz; Z += tm.bz)
-        for (int Y = tm.ty; Y < ny; Y += tm.by)
-            for (int X = tm.tx; X < nx; X += tm.bx) {
-                T sum = 0;
-                for (int c = 0; c < 8; c++)
-                    sum += tail_resid<T>(g, E + t.off[k], B + t.off[k], P + t.off[k], M ? M + t.off[k] : nullptr,
-                                         fx, fy, fz, t.lt + k, 2 * X + (c & 1), 2 * Y + ((c >> 1) & 1),
-                                         2 * Z + (c >> 2));
-                const int S = X + nx * (Y + ny * Z);
-                B[t.off[k + 1] + S] = (M && M[t.off[k + 1] + S]) ? T(0) : sum;
-                E[t.off[k + 1] + S] = T(0);
-            }
-    tsync(tm);
-}
-
-// trilinear prolongation of level k + 1's correction, added on level k
-template <typename T>
-__device__ void tail_prolong(const Geom &g, const MGTail &t, T *E, const unsigned char *M, int k, const TMap &tm)
-{
-    const int nx = t.nx[k], ny = t.ny[k], nz = t.nz[k];
-    const int nc[3] = {t.nx[k + 1], t.ny[k + 1], t.nz[k + 1]};
-    const T *ec = E + t.off[k + 1];
-    for (int fz_ = tm.tz; fz_ < nz; fz_ += tm.bz)
-        for (int fy_ = tm.ty; fy_ < ny; fy_ += tm.by)
-            for (int fx_ = tm.tx; fx_ < nx; fx_ += tm.bx) {
-                const int fc[3] = {fx_, fy_, fz_};
-                int i0[3], i1[3];
-                bool z1[3];
-                for (int a = 0; a < 3; a++) {
-                    i0[a] = fc[a] >> 1;
-                    int o = (fc[a] & 1) ? 1 : -1;
-                    int v = nbc(i0[a] + o, nc[a], g.per[a]);
-                    z1[a] = false;
-                    if (v < 0) {
-                        if (g.phi_kind[2 * a + (o > 0)] == ELBM_PHI_DIRICHLET) z1[a] = true;
-                        v = i0[a];
-                    }
-                    i1[a] = v;
-                }
-                T acc = 0;
-                for (int c = 0; c < 8; c++) {
-                    int ax = c & 1, ay = (c >> 1) & 1, az = c >> 2;
-                    if ((ax && z1[0]) || (ay && z1[1]) || (az && z1[2])) continue;
-                    T w = (ax ? T(0.25) : T(0.75)) * (ay ? T(0.25) : T(0.75)) * (az ? T(0.25) : T(0.75));
-                    int X = ax ? i1[0] : i0[0], Y = ay ? i1[1] : i0[1], Z = az ? i1[2] : i0[2];
-                    acc += w * ec[X + nc[0] * (Y + nc[1] * Z)];
-                }
-                const int fs = fx_ + nx * (fy_ + ny * fz_);
-                if (!(M && M[t.off[k] + fs])) E[t.off[k] + fs] += acc;
-            }
-    tsync(tm);
 }
 
 template <typename T>
@@ -1668,43 +1554,74 @@ __global__ void __launch_bounds__(1024) k_mg_tail(Geom g, MGTail t, int nu)
     if (M)
         for (int s = tid; s < (int)t.total; s += nthr) M[s] = t.m[s];
     __syncthreads();
-    // levels kb .. nt-1 (at most kTailWarpCells cells each) go to warp 0
-    int kb = t.nt;
-    for (int k = t.nt - 1; k >= 0 && t.N[k] <= kTailWarpCells; k--) kb = k;
-    const TMap blk = tmap_block();
-    for (int k = 1; k < kb; k++) tail_eps<T>(t, P, k, blk);
-    // down through the CTA levels
-    for (int k = 0; k < kb; k++) {
-        if (k == t.nt - 1) {
-            tail_smooth<T>(g, t, E, B, P, M, k, t.coarse_sweeps, blk);
-            break;
-        }
-        tail_smooth<T>(g, t, E, B, P, M, k, nu, blk);
-        tail_restrict<T>(g, t, E, B, P, M, k, blk);
-    }
-    if (kb < t.nt) {
-        if (tid < 32) {  // warp 0: the small levels down, the coarsest, and up
-            const int lane = tid;
-            for (int k = kb > 1 ? kb : 1; k < t.nt; k++)
-                tail_eps<T>(t, P, k, tmap_warp(t.nx[k], t.ny[k], t.nz[k], lane));
-            for (int k = kb; k + 1 < t.nt; k++) {
-                tail_smooth<T>(g, t, E, B, P, M, k, nu, tmap_warp(t.nx[k], t.ny[k], t.nz[k], lane));
-                tail_restrict<T>(g, t, E, B, P, M, k, tmap_warp(t.nx[k + 1], t.ny[k + 1], t.nz[k + 1], lane));
-            }
-            const int kc = t.nt - 1;
-            tail_smooth<T>(g, t, E, B, P, M, kc, t.coarse_sweeps, tmap_warp(t.nx[kc], t.ny[kc], t.nz[kc], lane));
-            for (int k = t.nt - 2; k >= kb; k--) {
-                const TMap w = tmap_warp(t.nx[k], t.ny[k], t.nz[k], lane);
-                tail_prolong<T>(g, t, E, M, k, w);
-                tail_smooth<T>(g, t, E, B, P, M, k, nu, w);
-            }
-        }
+    for (int k = 1; k < t.nt; k++) {  // coarse permittivities: mean of 8 children
+        const int nx = t.nx[k], ny = t.ny[k], nz = t.nz[k], fx = t.nx[k - 1], fy = t.ny[k - 1];
+        const T *pf = P + t.off[k - 1];
+        for (int Z = threadIdx.z; Z < nz; Z += blockDim.z)
+            for (int Y = threadIdx.y; Y < ny; Y += blockDim.y)
+                for (int X = threadIdx.x; X < nx; X += blockDim.x) {
+                    T sum = 0;
+                    for (int c = 0; c < 8; c++)
+                        sum += pf[(2 * X + (c & 1)) + fx * ((2 * Y + ((c >> 1) & 1)) + fy * (2 * Z + (c >> 2)))];
+                    P[t.off[k] + X + nx * (Y + ny * Z)] = sum * T(0.125);
+                }
         __syncthreads();
     }
-    // up through the CTA levels
-    for (int k = (kb - 1 < t.nt - 2 ? kb - 1 : t.nt - 2); k >= 0; k--) {
-        tail_prolong<T>(g, t, E, M, k, blk);
-        tail_smooth<T>(g, t, E, B, P, M, k, nu, blk);
+    // down: smooth, restrict
+    for (int k = 0; k + 1 < t.nt; k++) {
+        tail_smooth<T>(g, t, E, B, P, M, k, nu);
+        const int nx = t.nx[k + 1], ny = t.ny[k + 1], nz = t.nz[k + 1];
+        const int fx = t.nx[k], fy = t.ny[k], fz = t.nz[k];
+        for (int Z = threadIdx.z; Z < nz; Z += blockDim.z)
+            for (int Y = threadIdx.y; Y < ny; Y += blockDim.y)
+                for (int X = threadIdx.x; X < nx; X += blockDim.x) {
+                    T sum = 0;
+                    for (int c = 0; c < 8; c++)
+                        sum += tail_resid<T>(g, E + t.off[k], B + t.off[k], P + t.off[k], M ? M + t.off[k] : nullptr,
+                                             fx, fy, fz, t.lt + k, 2 * X + (c & 1), 2 * Y + ((c >> 1) & 1),
+                                             2 * Z + (c >> 2));
+                    const int S = X + nx * (Y + ny * Z);
+                    B[t.off[k + 1] + S] = (M && M[t.off[k + 1] + S]) ? T(0) : sum;
+                    E[t.off[k + 1] + S] = T(0);
+                }
+        __syncthreads();
+    }
+    tail_smooth<T>(g, t, E, B, P, M, t.nt - 1, t.coarse_sweeps);
+    // up: prolong (trilinear), smooth
+    for (int k = t.nt - 2; k >= 0; k--) {
+        const int nx = t.nx[k], ny = t.ny[k], nz = t.nz[k];
+        const int nc[3] = {t.nx[k + 1], t.ny[k + 1], t.nz[k + 1]};
+        const T *ec = E + t.off[k + 1];
+        for (int fz_ = threadIdx.z; fz_ < nz; fz_ += blockDim.z)
+            for (int fy_ = threadIdx.y; fy_ < ny; fy_ += blockDim.y)
+                for (int fx_ = threadIdx.x; fx_ < nx; fx_ += blockDim.x) {
+                    const int fc[3] = {fx_, fy_, fz_};
+                    int i0[3], i1[3];
+                    bool z1[3];
+                    for (int a = 0; a < 3; a++) {
+                        i0[a] = fc[a] >> 1;
+                        int o = (fc[a] & 1) ? 1 : -1;
+                        int v = nbc(i0[a] + o, nc[a], g.per[a]);
+                        z1[a] = false;
+                        if (v < 0) {
+                            if (g.phi_kind[2 * a + (o > 0)] == ELBM_PHI_DIRICHLET) z1[a] = true;
+                            v = i0[a];
+                        }
+                        i1[a] = v;
+                    }
+                    T acc = 0;
+                    for (int c = 0; c < 8; c++) {
+                        int ax = c & 1, ay = (c >> 1) & 1, az = c >> 2;
+                        if ((ax && z1[0]) || (ay && z1[1]) || (az && z1[2])) continue;
+                        T w = (ax ? T(0.25) : T(0.75)) * (ay ? T(0.25) : T(0.75)) * (az ? T(0.25) : T(0.75));
+                        int X = ax ? i1[0] : i0[0], Y = ay ? i1[1] : i0[1], Z = az ? i1[2] : i0[2];
+                        acc += w * ec[X + nc[0] * (Y + nc[1] * Z)];
+                    }
+                    const int fs = fx_ + nx * (fy_ + ny * fz_);
+                    if (!(M && M[t.off[k] + fs])) E[t.off[k] + fs] += acc;
+                }
+        __syncthreads();
+        tail_smooth<T>(g, t, E, B, P, M, k, nu);
     }
     for (int s = tid; s < (int)t.N[0]; s += nthr) ((T *)t.top.e)[s] = E[s];
 }
