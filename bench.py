@@ -306,7 +306,7 @@ def run_ours(args, rank, world, local_rank):
                      "frac_of_8TBps": achieved / NOMINAL_HBM_GBS,
                      # ncu dram__bytes_read.sum + dram__bytes_write.sum of one 64^3 FP32
                      # launch of this kernel (cold caches)
-                     "traffic": 32.66e6 if args.precision == "fp32" else None,
+                     "traffic": 32.51e6 if args.precision == "fp32" else None,
                      "bytes_per_site": bytes_site, "avg_launch_ms": coll_ms,
                      "timed": "one 64^3 lattice alone, CUDA events around each collision launch"},
         "pass_share": shares,
