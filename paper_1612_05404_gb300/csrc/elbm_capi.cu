@@ -37,7 +37,9 @@ struct elbm_handle {
     Ops ops;
     cudaStream_t s;            // the caller's stream: all work runs here
     int has_dirichlet;
-    double *pin;               // pinned host scalars; [8], [9]: the step's status words (below)
+    double *pin;               // pinned host scalars; [9] Poisson no-convergence counter, [16..39] diagnostics
+    int diag_mirror;           // pin[16..39] holds the last step's diagnostics (graph steps)
+    void *arena;               // every device buffer of the handle, carved from one allocation
     long long step;
     size_t pop_bytes, g_bytes, sc_bytes;
     MGOps mg;
@@ -251,20 +253,9 @@ int validate(const elbm_params *p, const elbm_init_fields *in, int n_instances)
 
 void free_bufs(elbm_handle *h)
 {
-    void *ptrs[] = {h->b.fA, h->b.fB, h->b.gA, h->b.gB, h->b.rho, h->b.q, h->b.phi, h->b.psi, h->b.sig, h->b.ux,
-                    h->b.uy, h->b.uz, h->b.alpha, h->b.nu, h->b.mask, h->b.nh, h->b.ab,
-                    h->b.part, h->b.scal, h->b.scalf, h->b.diag, h->b.colres, h->b.ticket,
-                    const_cast<void *>(h->b.mlpimg), h->b.phi_old};
-    for (void *q : ptrs)
-        if (q) cudaFree(q);
+    if (h->arena) cudaFree(h->arena);  // every device buffer of the handle
+    h->arena = nullptr;
     if (h->pin) cudaFreeHost(h->pin);
-    for (int l = 1; l < h->nlev; l++) {
-        if (h->lev[l].e) cudaFree(h->lev[l].e);
-        if (h->lev[l].b) cudaFree(h->lev[l].b);
-        if (h->lev[l].eps) cudaFree(h->lev[l].eps);
-        if (l < h->lt && h->lev[l].m) cudaFree(const_cast<unsigned char *>(h->lev[l].m));
-    }
-    if (h->tail.m) cudaFree(const_cast<unsigned char *>(h->tail.m));
     for (int i = 0; i < 5; i++)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     for (int i = 0; i < 2; i++) {
@@ -508,13 +499,15 @@ bool enqueue_step(elbm_handle *h, int parity, cudaStream_t s, int sections, int 
     return ok;
 }
 
-// The two words elbm_step checks after a step, copied into pinned host
-// memory as the last nodes of a step graph (one wait on the stream, no
-// synchronous copies): the non-finite site count and the Poisson no-convergence
-// counter.
+// The step's diagnostics and the Poisson no-convergence counter, copied into
+// pinned host memory as the last nodes of a step graph: elbm_step checks the
+// status words there after one wait on the stream, and elbm_fields serves
+// ELBM_F_DIAG from the copy, with no synchronous copies per step.
+constexpr int kPinDiag = 16;
 bool enqueue_status(elbm_handle *h, cudaStream_t s)
 {
-    return cuda_ok(cudaMemcpyAsync(h->pin + 8, h->b.diag + 15, sizeof(double), cudaMemcpyDeviceToHost, s)) &&
+    return cuda_ok(cudaMemcpyAsync(h->pin + kPinDiag, h->b.diag, ELBM_NDIAG * sizeof(double), cudaMemcpyDeviceToHost,
+                                   s)) &&
            cuda_ok(cudaMemcpyAsync(h->pin + 9, h->b.scal + S_NOCONV, sizeof(double), cudaMemcpyDeviceToHost, s));
 }
 
@@ -808,58 +801,93 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
 
     Bufs &b = h->b;
     bool ok = true;
+    // Device memory: the buffers are laid out twice by plan(), first to size
+    // one allocation (the arena), then to hand out 256-byte aligned pieces of
+    // it; the arena is zeroed once. One cudaMalloc / cudaFree per handle
+    // instead of one per buffer.
+    char *carve_base = nullptr;
+    size_t carve_off = 0;
     auto alloc = [&](void **ptr, size_t bytes) {
-        if (!ok) return;
-        if (!cuda_ok(cudaMalloc(ptr, bytes))) { ok = false; *ptr = nullptr; return; }
-        if (!cuda_ok(cudaMemsetAsync(*ptr, 0, bytes, h->s))) ok = false;
+        const size_t at = (carve_off + 255) & ~size_t(255);
+        *ptr = carve_base ? (void *)(carve_base + at) : nullptr;
+        carve_off = at + bytes;
     };
     const bool transport = p->charge_model == ELBM_CHARGE_TRANSPORT;
-    alloc(&b.fA, (size_t)Q * N * h->pop_bytes);
-    alloc(&b.fB, (size_t)Q * N * h->pop_bytes);
-    if (transport) {
-        alloc(&b.gA, (size_t)Q7 * N * h->g_bytes);
-        alloc(&b.gB, (size_t)Q7 * N * h->g_bytes);
-    }
-    alloc(&b.rho, (size_t)N * h->sc_bytes);
-    alloc(&b.q, (size_t)N * h->sc_bytes);
-    alloc(&b.phi, (size_t)N * h->sc_bytes);
-    alloc(&b.psi, (size_t)N * h->sc_bytes);
-    if (transport) alloc(&b.sig, (size_t)N * h->sc_bytes);
-    // extrapolated warm start in reduced precision (FP64 keeps phi(t-1), the
-    // start the FP64 oracle uses, so that the two solves agree to 1e-12)
-    if (p->charge_model != ELBM_CHARGE_NONE && p->poisson_fixed_sweeps == 0 && p->precision != ELBM_PREC_FP64)
-        alloc(&b.phi_old, (size_t)N * h->sc_bytes);
-    if (p->store_macro) {
-        alloc(&b.ux, (size_t)N * h->sc_bytes);
-        alloc(&b.uy, (size_t)N * h->sc_bytes);
-        alloc(&b.uz, (size_t)N * h->sc_bytes);
-        alloc(&b.alpha, (size_t)N * h->sc_bytes);
-        alloc(&b.nu, (size_t)N * h->sc_bytes);
-    }
-    if (p->alpha_mode == ELBM_ALPHA_LEARNED) {
-        // the network output o per site passes through the alpha plane
-        if (!b.alpha) alloc(&b.alpha, (size_t)N * h->sc_bytes);
-        void *img = nullptr;
-        alloc(&img, sizeof(MlpSmem));
-        b.mlpimg = img;
-        if (ok) {
-            k_mlp_image<<<1, 128, 0, h->s>>>(p->mlp, (MlpSmem *)img);
-            ok = cuda_ok(cudaGetLastError());
+    const bool masks = h->nlev > 0 && n_solid > 0;  // coarse conductor masks
+    const long long part_blocks = p->autotune ? max_blocks_over_shapes(p) : L.nblocks;
+    auto plan = [&]() {
+        alloc(&b.fA, (size_t)Q * N * h->pop_bytes);
+        alloc(&b.fB, (size_t)Q * N * h->pop_bytes);
+        if (transport) {
+            alloc(&b.gA, (size_t)Q7 * N * h->g_bytes);
+            alloc(&b.gB, (size_t)Q7 * N * h->g_bytes);
         }
+        alloc(&b.rho, (size_t)N * h->sc_bytes);
+        alloc(&b.q, (size_t)N * h->sc_bytes);
+        alloc(&b.phi, (size_t)N * h->sc_bytes);
+        alloc(&b.psi, (size_t)N * h->sc_bytes);
+        if (transport) alloc(&b.sig, (size_t)N * h->sc_bytes);
+        // extrapolated warm start in reduced precision (FP64 keeps phi(t-1), the
+        // start the FP64 oracle uses, so that the two solves agree to 1e-12)
+        if (p->charge_model != ELBM_CHARGE_NONE && p->poisson_fixed_sweeps == 0 && p->precision != ELBM_PREC_FP64)
+            alloc(&b.phi_old, (size_t)N * h->sc_bytes);
+        if (p->store_macro) {
+            alloc(&b.ux, (size_t)N * h->sc_bytes);
+            alloc(&b.uy, (size_t)N * h->sc_bytes);
+            alloc(&b.uz, (size_t)N * h->sc_bytes);
+            alloc(&b.nu, (size_t)N * h->sc_bytes);
+        }
+        // alpha plane: stored alpha, or the network output o per site (learned)
+        if (p->store_macro || p->alpha_mode == ELBM_ALPHA_LEARNED) alloc(&b.alpha, (size_t)N * h->sc_bytes);
+        if (p->alpha_mode == ELBM_ALPHA_LEARNED) {
+            void *img = nullptr;
+            alloc(&img, sizeof(MlpSmem));
+            b.mlpimg = img;
+        }
+        if (g.has_mask) alloc((void **)&b.mask, (size_t)N);
+        if (p->charge_model == ELBM_CHARGE_CONSERVED || p->charge_model == ELBM_CHARGE_XI) {
+            alloc(&b.nh, (size_t)4 * N * h->sc_bytes);
+            alloc(&b.ab, (size_t)2 * N * h->sc_bytes);
+        }
+        for (int l = 1; l < h->nlev; l++) {
+            alloc(&h->lev[l].e, (size_t)h->lev[l].N * h->sc_bytes);
+            alloc(&h->lev[l].b, (size_t)h->lev[l].N * h->sc_bytes);
+            alloc(&h->lev[l].eps, (size_t)h->lev[l].N * h->sc_bytes);
+        }
+        if (masks) {
+            for (int l = 1; l < h->lt; l++) {
+                void *d = nullptr;
+                alloc(&d, (size_t)h->lev[l].N);
+                h->lev[l].m = (const unsigned char *)d;
+            }
+            void *dt = nullptr;
+            alloc(&dt, (size_t)h->tail.total);
+            h->tail.m = (const unsigned char *)dt;
+            h->lev[h->lt].m = (const unsigned char *)dt;  // the tail's first level is level lt
+        }
+        alloc((void **)&b.part, (size_t)part_blocks * D_NPART * sizeof(double));
+        alloc((void **)&b.scal, S_NSCAL * sizeof(double));
+        alloc((void **)&b.scalf, S_NSCAL * sizeof(float));
+        alloc((void **)&b.colres, 16 * sizeof(double));
+        alloc((void **)&b.ticket, sizeof(unsigned int));
+        alloc((void **)&b.diag, ELBM_NDIAG * sizeof(double));
+    };
+    plan();
+    const size_t arena_bytes = carve_off;
+    if (!cuda_ok(cudaMalloc(&h->arena, arena_bytes))) { h->arena = nullptr; ok = false; }
+    ok = ok && cuda_ok(cudaMemsetAsync(h->arena, 0, arena_bytes, h->s));
+    if (ok) {
+        carve_base = (char *)h->arena;
+        carve_off = 0;
+        plan();
     }
-    if (g.has_mask) alloc((void **)&b.mask, (size_t)N);
-    if (p->charge_model == ELBM_CHARGE_CONSERVED || p->charge_model == ELBM_CHARGE_XI) {
-        alloc(&b.nh, (size_t)4 * N * h->sc_bytes);
-        alloc(&b.ab, (size_t)2 * N * h->sc_bytes);
-    }
-    for (int l = 1; l < h->nlev; l++) {
-        alloc(&h->lev[l].e, (size_t)h->lev[l].N * h->sc_bytes);
-        alloc(&h->lev[l].b, (size_t)h->lev[l].N * h->sc_bytes);
-        alloc(&h->lev[l].eps, (size_t)h->lev[l].N * h->sc_bytes);
+    if (ok && p->alpha_mode == ELBM_ALPHA_LEARNED) {
+        k_mlp_image<<<1, 128, 0, h->s>>>(p->mlp, (MlpSmem *)const_cast<void *>(b.mlpimg));
+        ok = cuda_ok(cudaGetLastError());
     }
     // conductor masks of the coarse levels: a cell is a conductor (its
     // correction held at 0) when any of its 8 children is one
-    if (h->nlev > 0 && n_solid > 0 && ok) {
+    if (masks && ok) {
         std::vector<std::vector<unsigned char>> hm(h->nlev);
         hm[0].resize(N);
         for (long long i = 0; i < N; i++) hm[0][i] = in->mask[i] == ELBM_NODE_SOLID;
@@ -875,29 +903,16 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
                         hm[l][X + (long long)C.nx * (Y + (long long)C.ny * Z)] = any;
                     }
         }
-        for (int l = 1; l < h->lt && ok; l++) {
-            void *d = nullptr;
-            alloc(&d, (size_t)h->lev[l].N);
-            if (ok) ok = cuda_ok(cudaMemcpy(d, hm[l].data(), (size_t)h->lev[l].N, cudaMemcpyHostToDevice));
-            h->lev[l].m = (const unsigned char *)d;
-        }
-        void *dt = nullptr;
-        alloc(&dt, (size_t)h->tail.total);
+        for (int l = 1; l < h->lt && ok; l++)
+            ok = cuda_ok(cudaMemcpyAsync(const_cast<unsigned char *>(h->lev[l].m), hm[l].data(), (size_t)h->lev[l].N,
+                                         cudaMemcpyHostToDevice, h->s));
         for (int k = 0; k < h->tail.nt && ok; k++)
-            ok = cuda_ok(cudaMemcpy((unsigned char *)dt + h->tail.off[k], hm[h->lt + k].data(),
-                                    (size_t)h->tail.N[k], cudaMemcpyHostToDevice));
-        h->tail.m = (const unsigned char *)dt;
-        h->lev[h->lt].m = (const unsigned char *)dt;  // the tail's first level is level lt
+            ok = cuda_ok(cudaMemcpyAsync(const_cast<unsigned char *>(h->tail.m) + h->tail.off[k],
+                                         hm[h->lt + k].data(), (size_t)h->tail.N[k], cudaMemcpyHostToDevice, h->s));
+        ok = ok && cuda_ok(cudaStreamSynchronize(h->s));  // hm is freed at the end of this scope
     }
     if (h->nlev > 0) h->tail.top = h->lev[h->lt];
-    const long long part_blocks = p->autotune ? max_blocks_over_shapes(p) : L.nblocks;
-    alloc((void **)&b.part, (size_t)part_blocks * D_NPART * sizeof(double));
-    alloc((void **)&b.scal, S_NSCAL * sizeof(double));
-    alloc((void **)&b.scalf, S_NSCAL * sizeof(float));
-    alloc((void **)&b.colres, 16 * sizeof(double));
-    alloc((void **)&b.ticket, sizeof(unsigned int));
-    alloc((void **)&b.diag, ELBM_NDIAG * sizeof(double));
-    if (ok && !cuda_ok(cudaMallocHost((void **)&h->pin, 16 * sizeof(double)))) ok = false;
+    if (ok && !cuda_ok(cudaMallocHost((void **)&h->pin, (kPinDiag + ELBM_NDIAG) * sizeof(double)))) ok = false;
     if (ok && p->profile)
         for (int i = 0; i < 5; i++)
             if (!cuda_ok(cudaEventCreate(&h->ev[i]))) ok = false;
@@ -905,9 +920,15 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
 
     // upload the initial fields into temporaries and build f(r, 0)
     double *d_rho0 = nullptr, *d_u0 = nullptr, *d_f0 = nullptr, *d_uin = nullptr, *d_q0 = nullptr;
+    const size_t n_up = (in->rho0 ? N : 0) + (in->u0 ? 3 * N : 0) + (in->f0 ? (size_t)Q * N : 0) +
+                        (in->u_in ? 3 * N : 0) + (transport && in->q0 ? N : 0);
+    double *d_up = nullptr;  // one temporary for all of them
+    if (ok && n_up > 0 && !cuda_ok(cudaMalloc((void **)&d_up, n_up * sizeof(double)))) { d_up = nullptr; ok = false; }
+    size_t up_off = 0;
     auto up = [&](double **dst, const double *src, size_t n) {
         if (!ok || !src) return;
-        if (!cuda_ok(cudaMalloc((void **)dst, n * sizeof(double)))) { ok = false; return; }
+        *dst = d_up + up_off;
+        up_off += n;
         if (!cuda_ok(cudaMemcpyAsync(*dst, src, n * sizeof(double), cudaMemcpyHostToDevice, h->s))) ok = false;
     };
     up(&d_rho0, in->rho0, N);
@@ -920,9 +941,7 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
         h->ops.init_pop(g, ph, b, d_rho0, d_u0, d_f0, d_uin, d_q0, L, h->s);
         if (!cuda_ok(cudaGetLastError()) || !cuda_ok(cudaStreamSynchronize(h->s))) ok = false;
     }
-    double *tmps[] = {d_rho0, d_u0, d_f0, d_uin, d_q0};
-    for (double *t : tmps)
-        if (t) cudaFree(t);
+    if (d_up) cudaFree(d_up);
     if (!ok) { free_bufs(h); delete h; return ELBM_E_CUDA; }
 
     if (p->autotune && !autotune(h)) { free_bufs(h); delete h; return ELBM_E_CUDA; }
@@ -1016,7 +1035,8 @@ elbm_status elbm_step(elbm_handle *h, int nsteps)
         if (nsteps > 0) {
             for (int i = 0; i < h->n_sub; i++) {
                 elbm_handle *q = h->sub[i];
-                const double v[2] = {q->pin[8], q->pin[9]};  // copied by the graph's last nodes
+                const double v[2] = {q->pin[kPinDiag + 15], q->pin[9]};  // copied by the graph's last nodes
+                q->diag_mirror = 1;
                 if (v[0] != 0.0) worst = ELBM_E_NUMERIC;
                 if (v[1] > q->noconv_seen) {
                     q->noconv_seen = v[1];
@@ -1063,8 +1083,9 @@ elbm_status elbm_step(elbm_handle *h, int nsteps)
     if (!cuda_ok(cudaStreamSynchronize(h->s))) return ELBM_E_CUDA;
     if (nsteps > 0) {
         double v[2] = {0.0, 0.0};
-        if (h->use_graph && !prof) {  // copied by the step graph's last nodes
-            v[0] = h->pin[8];
+        h->diag_mirror = h->use_graph && !prof;
+        if (h->diag_mirror) {  // copied by the step graph's last nodes
+            v[0] = h->pin[kPinDiag + 15];
             v[1] = h->pin[9];
             if (v[0] != 0.0) return ELBM_E_NUMERIC;
         } else {
@@ -1155,13 +1176,12 @@ elbm_status elbm_fields(elbm_handle *h, unsigned mask, double *out, size_t out_l
         off += (size_t)Q7 * N;
     }
     if ((mask & ELBM_F_DIAG) && st == ELBM_OK) {
-        double sc[S_NSCAL];
-        if (!cuda_ok(cudaMemcpyAsync(out + off, h->b.diag, ELBM_NDIAG * sizeof(double), cudaMemcpyDeviceToHost, h->s)) ||
-            !cuda_ok(cudaMemcpyAsync(sc, h->b.scal, S_NSCAL * sizeof(double), cudaMemcpyDeviceToHost, h->s)) ||
-            !cuda_ok(cudaStreamSynchronize(h->s))) {
+        if (h->diag_mirror) {  // the last step graph copied them to pinned memory
+            std::memcpy(out + off, h->pin + kPinDiag, ELBM_NDIAG * sizeof(double));
+        } else if (!cuda_ok(cudaMemcpyAsync(out + off, h->b.diag, ELBM_NDIAG * sizeof(double), cudaMemcpyDeviceToHost,
+                                            h->s)) ||
+                   !cuda_ok(cudaStreamSynchronize(h->s))) {
             st = ELBM_E_CUDA;
-        } else {
-            (void)sc;
         }
         off += ELBM_NDIAG;
     }
