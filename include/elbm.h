@@ -178,7 +178,11 @@ elbm_status elbm_step(elbm_handle *h, int nsteps);
 /* Copy the selected fields (ELBM_F_* bits) to the caller's host buffer out of
  * out_len doubles, blocks back to back in bit order, converted to FP64.
  * U, ALPHA and NU need store_macro = 1 (else ELBM_E_STATE); GPOP needs
- * transport mode. ELBM_E_INVAL if out_len is too small. */
+ * transport mode. ELBM_E_INVAL if out_len is too small. After a step run as
+ * a CUDA graph (alone or in a batch) DIAG comes from a pinned-memory copy
+ * that the graph made, without touching the device; the FP64 conversion of
+ * the other fields goes through a device scratch buffer that the handle
+ * keeps (grown on demand, freed by elbm_free). */
 elbm_status elbm_fields(elbm_handle *h, unsigned mask, double *out, size_t out_len);
 
 /* Number of doubles elbm_fields writes for this selector (0 on error). */

@@ -39,6 +39,8 @@ struct elbm_handle {
     int has_dirichlet;
     double *pin;               // pinned host scalars; [9] Poisson no-convergence counter, [16..39] diagnostics
     int diag_mirror;           // pin[16..39] holds the last step's diagnostics (graph steps)
+    double *xtmp;              // elbm_fields' FP64 export scratch, kept for the next call
+    size_t xtmp_n;
     void *arena;               // every device buffer of the handle, carved from one allocation
     long long step;
     size_t pop_bytes, g_bytes, sc_bytes;
@@ -255,6 +257,8 @@ void free_bufs(elbm_handle *h)
 {
     if (h->arena) cudaFree(h->arena);  // every device buffer of the handle
     h->arena = nullptr;
+    if (h->xtmp) cudaFree(h->xtmp);
+    h->xtmp = nullptr;
     if (h->pin) cudaFreeHost(h->pin);
     for (int i = 0; i < 5; i++)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
@@ -1131,8 +1135,14 @@ elbm_status elbm_fields(elbm_handle *h, unsigned mask, double *out, size_t out_l
     if (mask & (ELBM_F_RHO | ELBM_F_U | ELBM_F_PHI | ELBM_F_Q | ELBM_F_ALPHA | ELBM_F_NU)) need = (size_t)N;
     if (mask & ELBM_F_POP) need = (size_t)Q * N;
     if (mask & ELBM_F_GPOP) need = need > (size_t)Q7 * N ? need : (size_t)Q7 * N;
-    double *tmp = nullptr;
-    if (need && !cuda_ok(cudaMalloc((void **)&tmp, need * sizeof(double)))) return ELBM_E_NOMEM;
+    if (need > h->xtmp_n) {  // grow the export scratch (kept: repeated reads allocate nothing)
+        if (h->xtmp) cudaFree(h->xtmp);
+        h->xtmp = nullptr;
+        h->xtmp_n = 0;
+        if (!cuda_ok(cudaMalloc((void **)&h->xtmp, need * sizeof(double)))) return ELBM_E_NOMEM;
+        h->xtmp_n = need;
+    }
+    double *tmp = need ? h->xtmp : nullptr;
     elbm_status st = ELBM_OK;
     size_t off = 0;
     auto plane = [&](const void *src) {
@@ -1185,7 +1195,6 @@ elbm_status elbm_fields(elbm_handle *h, unsigned mask, double *out, size_t out_l
         }
         off += ELBM_NDIAG;
     }
-    if (tmp) cudaFree(tmp);
     return st;
 }
 
