@@ -55,6 +55,7 @@ struct elbm_handle {
     cudaGraphExec_t gexec[2];  // one whole step for each A/B parity
     cudaGraphExec_t gsec[2][3];  // profiling: the step as three section graphs
     int use_graph;
+    int want_graph, graph_tried;  // step graphs requested; capture attempted (on the first elbm_step)
     int n_pre, n_body, n_post; // kernels per graph section (launch accounting)
     double noconv_seen;
     cudaEvent_t ev[5];         // pass boundaries when profiling
@@ -954,21 +955,10 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     h->ce = (h->nlev > 0 || p->poisson_fixed_sweeps > 0) ? 1
             : (p->poisson_check_every > 0 ? p->poisson_check_every : 8);
     h->units_max = (p->poisson_maxit + h->ce - 1) / h->ce;
-    // one CUDA graph per A/B parity; any capture failure keeps the host loop
+    // one CUDA graph per A/B parity, captured on the first elbm_step (an
+    // instance stepped only inside a batch never needs its own)
     h->use_graph = 0;
-    if (p->graph && p->diag_every == 1) {
-        bool g_ok = cuda_ok(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking)) &&
-                    cuda_ok(cudaStreamCreateWithFlags(&h->cap2, cudaStreamNonBlocking));
-        h->n_pre = h->n_body = h->n_post = 0;
-        if (p->profile) {
-            for (int par = 0; par < 2 && g_ok; par++)
-                for (int sec = 0; sec < 3 && g_ok; sec++) g_ok = capture_step(h, par, &h->gsec[par][sec], 1 << sec);
-        } else {
-            g_ok = g_ok && capture_step(h, 0, &h->gexec[0]) && capture_step(h, 1, &h->gexec[1]);
-        }
-        h->use_graph = g_ok ? 1 : 0;
-        cudaGetLastError();
-    }
+    h->want_graph = p->graph && p->diag_every == 1;
     *out = h;
     return ELBM_OK;
 }
@@ -1020,6 +1010,30 @@ elbm_status elbm_batch_create(elbm_handle *const *inst, int n, int flags, void *
     return ELBM_OK;
 }
 
+// The instance's step graphs, captured once; any capture failure keeps the
+// host loop. The graphs are laid out for the buffers of an even step, so an
+// instance already stepped an odd number of times (in a batch) is captured
+// with A and B swapped back.
+void ensure_graphs(elbm_handle *h)
+{
+    if (!h->want_graph || h->graph_tried) return;
+    h->graph_tried = 1;
+    bool g_ok = (h->cap || cuda_ok(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking))) &&
+                (h->cap2 || cuda_ok(cudaStreamCreateWithFlags(&h->cap2, cudaStreamNonBlocking)));
+    const Bufs cur = h->b;
+    if (h->step & 1) swap_ab(h->b);
+    h->n_pre = h->n_body = h->n_post = 0;
+    if (h->p.profile) {
+        for (int par = 0; par < 2 && g_ok; par++)
+            for (int sec = 0; sec < 3 && g_ok; sec++) g_ok = capture_step(h, par, &h->gsec[par][sec], 1 << sec);
+    } else {
+        g_ok = g_ok && capture_step(h, 0, &h->gexec[0]) && capture_step(h, 1, &h->gexec[1]);
+    }
+    h->b = cur;
+    h->use_graph = g_ok ? 1 : 0;
+    cudaGetLastError();
+}
+
 elbm_status elbm_step(elbm_handle *h, int nsteps)
 {
     if (!h || nsteps < 0) return ELBM_E_INVAL;
@@ -1051,6 +1065,7 @@ elbm_status elbm_step(elbm_handle *h, int nsteps)
         return worst;
     }
     const bool prof = h->p.profile != 0;
+    if (nsteps > 0) ensure_graphs(h);
     for (int i = 0; i < nsteps; i++) {
         if (h->use_graph && prof) {
             cudaGraphExec_t *gs = h->gsec[h->step & 1];
