@@ -373,6 +373,7 @@ void swap_ab(Bufs &b)
 {
     void *t = b.fA; b.fA = b.fB; b.fB = t;
     t = b.gA; b.gA = b.gB; b.gB = t;
+    float *r = b.rA; b.rA = b.rB; b.rB = r;
 }
 
 // One step issued from the host; the Poisson loop reads the device decision
@@ -823,6 +824,10 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     auto plan = [&]() {
         alloc(&b.fA, (size_t)Q * N * h->pop_bytes);
         alloc(&b.fB, (size_t)Q * N * h->pop_bytes);
+        if (p->precision == ELBM_PREC_BF16) {
+            alloc((void **)&b.rA, (size_t)N * sizeof(float));
+            alloc((void **)&b.rB, (size_t)N * sizeof(float));
+        }
         if (transport) {
             alloc(&b.gA, (size_t)Q7 * N * h->g_bytes);
             alloc(&b.gB, (size_t)Q7 * N * h->g_bytes);

@@ -37,21 +37,26 @@ constexpr double CS2Q = 0.25;
 
 // ---------------------------------------------------------------------------
 // Precision traits: storage type of the populations, arithmetic type, type
-// of the scalar planes (rho, q, phi), and whether populations are stored as
-// deviations d_p = f_p - w_p from the rest-state equilibrium.
+// of the scalar planes (rho, q, phi), and whether populations are handled as
+// deviations d_p = f_p - w_p from the rest-state equilibrium (dev). BF16
+// storage (rel) keeps f_p - w_p rho_ref instead, rho_ref the density of the
+// site that wrote the value (a plane beside the populations, A/B like them):
+// at a gas-phase site (rho ~ 0.16) f_p - w_p is about -0.84 w_p, whose 8-bit
+// significand would leave ~1 % of f_p as noise, while f_p - w_p rho is of
+// the order of the Mach number.
 // ---------------------------------------------------------------------------
 template <int PR> struct Tr;
 template <> struct Tr<ELBM_PREC_FP64> {
     typedef double st; typedef double ct; typedef double sc; typedef double gt;
-    static constexpr bool dev = false;
+    static constexpr bool dev = false, rel = false;
 };
 template <> struct Tr<ELBM_PREC_FP32> {
     typedef float st; typedef float ct; typedef float sc; typedef float gt;
-    static constexpr bool dev = true;
+    static constexpr bool dev = true, rel = false;
 };
 template <> struct Tr<ELBM_PREC_BF16> {
     typedef __nv_bfloat16 st; typedef float ct; typedef float sc; typedef float gt;
-    static constexpr bool dev = true;
+    static constexpr bool dev = true, rel = true;
 };
 
 __device__ __forceinline__ float to_ct(float v) { return v; }

@@ -41,6 +41,7 @@ template <> __host__ __device__ __forceinline__ const Cst<float> &cst<float>(con
 
 struct Bufs {
     void *fA, *fB, *gA, *gB;          // populations (current A, next B)
+    float *rA, *rB;                   // BF16 storage: reference density of each stored site (A/B)
     void *rho, *q, *phi;              // scalar planes
     void *psi, *sig;                  // psi(rho) of the Shan-Chen force; sigma(rho) (transport mode)
     void *ux, *uy, *uz, *alpha, *nu;  // optional macroscopic planes

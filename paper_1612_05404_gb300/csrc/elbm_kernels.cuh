@@ -191,22 +191,39 @@ __device__ __forceinline__ S *plane(void *A, int p, ll N)
     return (S *)A + (ll)p * N;
 }
 
+// stored value of population p at site idx as it enters the arithmetic: f_p
+// (FP64) or d_p = f_p - w_p (deviation modes; BF16 adds back w_p (rho_ref - 1))
 template <int PR>
-__device__ __forceinline__ typename Tr<PR>::ct ldp(const void *A, int p, int idx, ll N)
+__device__ __forceinline__ typename Tr<PR>::ct ldp(const void *A, int p, int idx, ll N, const float *rref)
 {
-    return to_ct(plane<typename Tr<PR>::st>(A, p, N)[idx]);
+    typedef typename Tr<PR>::ct ct;
+    const ct v = to_ct(plane<typename Tr<PR>::st>(A, p, N)[idx]);
+    if constexpr (Tr<PR>::rel) return v + ct(wq(p)) * (ct(rref[idx]) - ct(1));
+    else return v;
+}
+
+// the value to store for population p of a site whose density is rho, from
+// its FP32 deviation d = f - w (BF16: f - w rho)
+template <int PR>
+__device__ __forceinline__ typename Tr<PR>::st stp(typename Tr<PR>::ct d, int p, typename Tr<PR>::ct drho)
+{
+    typedef typename Tr<PR>::ct ct;
+    if constexpr (Tr<PR>::rel) return from_ct<typename Tr<PR>::st>(d - ct(wq(p)) * drho);
+    else return from_ct<typename Tr<PR>::st>(d);
 }
 
 // f_p(r, t): pull from r - c_p, bounce-back across walls and from solids.
-// FP64 returns f_p; the deviation modes return d_p = f_p - w_p.
+// FP64 returns f_p; the deviation modes return d_p = f_p - w_p. rref: the
+// reference-density plane of A (BF16 storage), else unused.
 template <int PR>
 __device__ __forceinline__ typename Tr<PR>::ct gather_pop(const Geom &g, const unsigned char *mask,
-                                                          const void *A, const Nbr &n, int p)
+                                                          const void *A, const Nbr &n, int p,
+                                                          const float *rref = nullptr)
 {
     const int src = nbr_idx(n, g, -cx(p), -cy(p), -cz(p));
     bool bb = src < 0;
     if (!bb && mask) bb = mask[src] == ELBM_NODE_SOLID;
-    return bb ? ldp<PR>(A, opp(p), n.s, g.N) : ldp<PR>(A, p, src, g.N);
+    return bb ? ldp<PR>(A, opp(p), n.s, g.N, rref) : ldp<PR>(A, p, src, g.N, rref);
 }
 
 template <int PR>
@@ -295,6 +312,24 @@ __global__ void k_init_pop(Geom g, Phys ph, Bufs b, const double *rho0, const do
     unsigned char kind = b.mask ? b.mask[s] : 0;
     st *A = (st *)b.fA, *B = (st *)b.fB;
     sc *rho = (sc *)b.rho;
+    // BF16 storage: the reference density of the values stored at a site is
+    // its initial density (1 where none is given); inlet and outlet nodes
+    // keep theirs
+    auto rref_of = [&](ll i) -> double {
+        if (b.mask && b.mask[i] == ELBM_NODE_INLET) return ph.rho_in;
+        if (b.mask && b.mask[i] == ELBM_NODE_OUTLET) return ph.rho_out;
+        return rho0 ? rho0[i] : 1.0;
+    };
+    auto stored = [&](double f, int p, ll at) -> st {
+        if constexpr (T::rel) return from_ct<st>((typename T::ct)(f - wq(p) * rref_of(at)));
+        else if constexpr (T::dev) return from_ct<st>((typename T::ct)(f - wq(p)));
+        else return from_ct<st>((typename T::ct)f);
+    };
+    if constexpr (T::rel) {
+        const float r0 = kind == ELBM_NODE_SOLID ? 1.f : float(rref_of(s));
+        b.rA[s] = r0;
+        b.rB[s] = r0;
+    }
     if (kind == ELBM_NODE_SOLID) { rho[s] = sc(0); return; }
     if (kind == ELBM_NODE_INLET || kind == ELBM_NODE_OUTLET) {
         double r = kind == ELBM_NODE_INLET ? ph.rho_in : ph.rho_out;
@@ -304,7 +339,7 @@ __global__ void k_init_pop(Geom g, Phys ph, Bufs b, const double *rho0, const do
 #pragma unroll
         for (int p = 0; p < Q; p++) {
             double fe = wq(p) * r * (1.0 + Ppoly<double>(p, ux, uy, uz, usq));
-            st v = T::dev ? from_ct<st>((typename T::ct)(fe - wq(p))) : from_ct<st>((typename T::ct)fe);
+            st v = stored(fe, p, s);
             A[(ll)p * g.N + s] = v;
             B[(ll)p * g.N + s] = v;
         }
@@ -319,11 +354,10 @@ __global__ void k_init_pop(Geom g, Phys ph, Bufs b, const double *rho0, const do
 #pragma unroll
     for (int p = 0; p < Q; p++) {
         double fp = f0 ? f0[(ll)p * g.N + s] : wq(p) * rho0[s] * (1.0 + Ppoly<double>(p, ux, uy, uz, usq));
-        st v = T::dev ? from_ct<st>((typename T::ct)(fp - wq(p))) : from_ct<st>((typename T::ct)fp);
         ll src = nbr_idx(n, g, -cx(p), -cy(p), -cz(p));
         unsigned char k2 = (src >= 0 && b.mask) ? b.mask[src] : 0;
-        if (src < 0 || k2 == ELBM_NODE_SOLID) A[(ll)opp(p) * g.N + s] = v;
-        else if (k2 == ELBM_NODE_FLUID) A[(ll)p * g.N + src] = v;
+        if (src < 0 || k2 == ELBM_NODE_SOLID) A[(ll)opp(p) * g.N + s] = stored(fp, p, s);
+        else if (k2 == ELBM_NODE_FLUID) A[(ll)p * g.N + src] = stored(fp, p, src);
     }
     if (b.gA) {
         gt *GA = (gt *)b.gA;
@@ -363,7 +397,7 @@ __global__ void __launch_bounds__(128) k_moments(Geom g, Phys ph, Bufs b)
         nbr_init(n, g, x, y, z, s);
         ct rs = 0;
 #pragma unroll
-        for (int p = 0; p < Q; p++) rs += gather_pop<PR>(g, b.mask, b.fA, n, p);
+        for (int p = 0; p < Q; p++) rs += gather_pop<PR>(g, b.mask, b.fA, n, p, b.rA);
         ((sc *)b.rho)[s] = sc(T::dev ? ct(1) + rs : rs);
         if (ph.charge_model == ELBM_CHARGE_TRANSPORT) {
             gt qs = 0;
@@ -674,7 +708,7 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
         nbr_init(n, g, x, y, z, s);
         const sc *phi = (const sc *)b.phi;
 #pragma unroll
-        for (int p = 0; p < Q; p++) f[p] = gather_pop<PR>(g, b.mask, b.fA, n, p);
+        for (int p = 0; p < Q; p++) f[p] = gather_pop<PR>(g, b.mask, b.fA, n, p, b.rA);
         ct rs = 0, rs_lo = 0;  // deviations: sum d_p compensated (Delta below)
 #pragma unroll
         for (int p = 0; p < Q; p++) {
@@ -850,8 +884,10 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
         for (int p = 0; p < Q; p++) {
             ct Sp = ct(wq(p)) * r * (Ppoly<ct>(p, vx, vy, vz, vsq) - Ppoly<ct>(p, ux, uy, uz, usq));
             ct fo = f[p] + ab * D[p] + Sp;
-            plane<st>(b.fB, p, g.N)[n.s] = from_ct<st>(fo);
+            // (BF16: relative to r - 1 as the reader forms it from the stored r)
+            plane<st>(b.fB, p, g.N)[n.s] = stp<PR>(fo, p, r - ct(1));
         }
+        if constexpr (T::rel) b.rB[n.s] = float(r);
 
         // half-step velocity (Sec. II): rho u = sum f c + F/2
         const ct upx = (jx + ct(0.5) * Fx) * ir, upy = (jy + ct(0.5) * Fy) * ir, upz = (jz + ct(0.5) * Fz) * ir;
@@ -984,7 +1020,7 @@ __global__ void __launch_bounds__(128) k_alpha_mlp(Geom g, Phys ph, Bufs b)
         nbr_init(n, g, x, y, z, s);
         float f[Q];
 #pragma unroll
-        for (int p = 0; p < Q; p++) f[p] = float(gather_pop<PR>(g, b.mask, b.fA, n, p));
+        for (int p = 0; p < Q; p++) f[p] = float(gather_pop<PR>(g, b.mask, b.fA, n, p, b.rA));
         float rs = 0.f, rs_lo = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
         for (int p = 0; p < Q; p++) {
@@ -1057,7 +1093,7 @@ __global__ void k_export_pop(Geom g, Bufs b, double *out)
     for (int p = 0; p < Q; p++) {
         double v = 0.0;
         if (fluid) {
-            double fv = double(gather_pop<PR>(g, b.mask, b.fA, n, p));
+            double fv = double(gather_pop<PR>(g, b.mask, b.fA, n, p, b.rA));
             v = T::dev ? wq(p) + fv : fv;
         }
         out[(ll)p * g.N + s] = v;
