@@ -291,8 +291,8 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": f"drop-in-field: {len(sims)} x 64^3 D3Q19 lattices (E0 sweep 1e-4..1e-3), "
                                "transported charge, Carreau n=0.6",
-                   "sites_per_step": len(sims) * N, "population_storage": args.precision + " deviation"
-                   if args.precision != "fp64" else "fp64",
+                   "sites_per_step": len(sims) * N, "population_storage": {"fp64": "fp64", "fp32": "fp32 deviation from w",
+                                          "bf16": "bf16, relative to the site density"}[args.precision],
                    "alpha_arithmetic": args.alpha_precision,
                    "l2": "256 MiB flush between timed steps (outside timing); state 190 MB > L2",
                    "poisson": "multigrid V(2,2), red-black Gauss-Seidel, tol 1e-6 (FP32 floor stop), warm start extrapolated from the two previous potentials",
@@ -499,7 +499,7 @@ def jet_run(args):
         guarded += d["n_guarded"]
     sim.close()
     return {"workload": "electrified jet 128x128x512, nozzle r=8, Carreau n=0.5 lambda=20, E0=5e-4, xi-form charge",
-            "storage": "bf16 deviation", "sites": N, "mlups": N * args.steps / (total * 1e-3) / 1e6,
+            "storage": "bf16, relative to the site density", "sites": N, "mlups": N * args.steps / (total * 1e-3) / 1e6,
             "ms_per_step": total / args.steps, "poisson": "multigrid, nozzle as conductor",
             "poisson_vcycles_per_step": cycles / args.steps, "max_h_error_device": herr,
             "guarded_site_fraction": guarded / (N * args.steps)}
