@@ -281,6 +281,29 @@ def test_fp32_parity_multi_step(E, aprec):
         assert max(e4.values()) < 1e-4, (t, e4)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_reduced_precision_nozzle_xi_charge(E, precision):
+    """The jet's path in reduced precision on a small nozzle: xi-form charge
+    (Eq. surface-q3, global sums), inlet and outlet nodes, the nozzle as a
+    conductor in the multigrid, Carreau. Against the FP64 oracle after
+    three steps, relative L2: density, potential and charge within 2e-6
+    (FP32; measured ~2e-7); density and potential within 3e-4 and charge
+    within 2e-3 (BF16 storage relative to the site density; measured 6e-5,
+    3e-5, 2.4e-4)."""
+    cfg, fields = W.jet(shape=(16, 16, 20), nozzle_r=3, wall=1, nozzle_len=5, precision=precision)
+    cfg["store_macro"] = 1
+    g = E.Sim(cfg, fields)
+    o = oracle.Sim(dict(cfg, poisson_tol=1e-13), fields)
+    g.step(3)
+    o.step(3)
+    fluid = o.rho > 0
+    t5, t4 = (2e-6, 2e-6) if precision == "fp32" else (3e-4, 2e-3)
+    errs = dict(rho=rel_l2(g.get("rho")[fluid], o.rho[fluid]), phi=rel_l2(g.get("phi"), o.phi))
+    errs["q"] = rel_l2(g.get("q"), o.q)
+    assert max(errs["rho"], errs["phi"]) <= t5, errs
+    assert errs["q"] <= t4, errs
+
+
 def test_bf16_single_step(E):
     """BF16 deviation storage: one rounding of d = f - w per stored value
     (unit roundoff 2^-9) bounds the single-step error on rho by
