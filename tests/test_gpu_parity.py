@@ -260,25 +260,23 @@ def test_fp32_single_step_populations_and_viscosity(E):
 @pytest.mark.parametrize("aprec", ["fp64", "fp32"])
 def test_fp32_parity_multi_step(E, aprec):
     """FP32 against the FP64 oracle over several steps from the same initial
-    fields. Density and potential stay within 1e-5 relative L2. Momentum and
-    charge are held to 1e-4: with the polynomial equilibrium, f* jumps where
-    the alpha root meets its fallbacks (h'(0) = 0: root -> 0+, fallback 2;
-    the near-equilibrium threshold), so FP32 rounding flips the branch at a
-    few sites, each carrying dalpha beta Delta, and the charge is a second
-    difference of the FP32 potential (Ohmic source)."""
+    fields, relative L2: density and potential within 1e-5 (the first,
+    cold Poisson solve stops at the FP32 floor, ~8e-6), momentum within 2e-6
+    (measured ~4e-7), charge within 5e-5 (a second difference of the FP32
+    potential through the Ohmic source; measured ~1e-5) and the alpha field
+    within 2e-5 (measured ~3e-6 with the FP32 root)."""
     cfg, fields = W.drop_in_field(E0=1e-3, n=16, radius=4.5, precision="fp32")
     cfg.update(store_macro=1, alpha_precision=aprec)
     g = E.Sim(cfg, fields)
     o = oracle.Sim(dict(cfg, poisson_tol=1e-13), fields)
-    for t in range(4):
+    for t in range(6):
         g.step(1)
         o.step(1)
         e5 = dict(rho=rel_l2(g.get("rho"), o.rho), phi=rel_l2(g.get("phi"), o.phi))
         assert max(e5.values()) < 1e-5, (t, e5)
-        e4 = dict(rho_u=rel_l2(_rho_u(g.get("rho"), g.get("u")), _rho_u(o.rho, o.u)))
-        if t >= 1:
-            e4["q"] = rel_l2(g.get("q"), o.q)
-        assert max(e4.values()) < 1e-4, (t, e4)
+        assert rel_l2(_rho_u(g.get("rho"), g.get("u")), _rho_u(o.rho, o.u)) < 2e-6, t
+        assert rel_l2(g.get("q"), o.q) < 5e-5, t
+        assert rel_l2(g.get("alpha"), o.alpha) < 2e-5, t
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
