@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="issue each step from the host (profilers see every launch)")
     ap.add_argument("--launch", default="batch", choices=["batch", "streams"],
                     help="batch: all lattices in one graph per step; streams: one graph per lattice per stream")
+    ap.add_argument("--span", type=int, default=4,
+                    help="batch: steps per graph launch (ELBM_BATCH_SPAN); timed launches cover that many steps")
     ap.add_argument("--pipeline", default="on", choices=["on", "off"],
                     help="batch: odd-position lattices run half a step ahead (ELBM_BATCH_PIPELINE)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -210,8 +212,8 @@ def run_ours(args, rank, world, local_rank):
         for c, _ in cfgs:
             c.update(autotune=1, profile=0)
         sims = [elbm.Sim(c, f) for c, f in cfgs]
-        batch = elbm.Batch(sims, pipeline=args.pipeline == "on")
-        step_all = lambda: batch.step(1)
+        batch = elbm.Batch(sims, pipeline=args.pipeline == "on", span=args.span)
+        step_all = lambda m=1: batch.step(m)
         streams = None
     else:
         # one CUDA stream per lattice, stepped from a thread pool (the library
@@ -219,7 +221,11 @@ def run_ours(args, rank, world, local_rank):
         streams = [torch.cuda.Stream() for _ in cfgs]
         sims = [elbm.Sim(c, f, stream=ctypes.c_void_p(st.cuda_stream)) for (c, f), st in zip(cfgs, streams)]
         pool = ThreadPoolExecutor(max_workers=len(sims))
-        step_all = lambda: list(pool.map(lambda s: s.step(1), sims))
+        step_all = lambda m=1: list(pool.map(lambda s: s.step(m), sims))
+    # timed launches: `span` steps per graph launch (batch), the rest one step
+    # at a time; exactly args.steps steps in all
+    span = args.span if args.launch == "batch" else 1
+    chunks = [span] * (args.steps // span) + [1] * (args.steps % span)
     for _ in range(args.warmup):
         step_all()
     torch.cuda.synchronize()
@@ -230,9 +236,9 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     torch.cuda.synchronize()
     times = []
-    sweeps = 0.0
+    sweeps0 = sum(s.diag()["poisson_sweeps_total"] for s in sims)
     with ClockSampler(local_rank) as clk:
-        for _ in range(args.steps):
+        for m in chunks:
             flush.zero_()
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -241,7 +247,7 @@ def run_ours(args, rank, world, local_rank):
             if streams:
                 for st in streams:
                     st.wait_event(e0)
-            step_all()
+            step_all(m)
             if streams:
                 cur = torch.cuda.current_stream()
                 for st in streams:
@@ -249,7 +255,7 @@ def run_ours(args, rank, world, local_rank):
             e1.record()
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
-            sweeps += sum(s.diag()["poisson_sweeps"] for s in sims)
+    sweeps = sum(s.diag()["poisson_sweeps_total"] for s in sims) - sweeps0
     torch.cuda.synchronize()
     total_ms = sum(times)
     if world > 1:
@@ -294,10 +300,13 @@ def run_ours(args, rank, world, local_rank):
                    "sites_per_step": len(sims) * N, "population_storage": {"fp64": "fp64", "fp32": "fp32 deviation from w",
                                           "bf16": "bf16, relative to the site density"}[args.precision],
                    "alpha_arithmetic": args.alpha_precision,
-                   "l2": "256 MiB flush between timed steps (outside timing); state 190 MB > L2",
+                   "l2": "256 MiB flush between timed launches (outside timing); lattice state %.0f MB > L2 (129 MB)"
+                         % (len(sims) * N * (2 * 19 * {"fp64": 8, "fp32": 4, "bf16": 2}[args.precision] + 2 * 7 * 4
+                                             + 6 * (8 if args.precision == "fp64" else 4)) / 1e6),
+                   "timed_launch_steps": span,
                    "poisson": "multigrid V(2,2), red-black Gauss-Seidel, tol 1e-6 (FP32 floor stop), warm start extrapolated from the two previous potentials",
                    "poisson_vcycles_per_step": sweeps / max(args.steps, 1) / len(sims),
-                   "launch": ("one CUDA graph per step for all lattices (batch), autotuned block shapes"
+                   "launch": ("CUDA graphs of %d step(s) for all lattices (batch), autotuned block shapes" % span
                               + (", odd lattices half a step ahead" if args.pipeline == "on" else "")
                               if args.launch == "batch" else "one graph per lattice on concurrent streams"),
                    "parallelism": f"replicas x{world}"},
@@ -522,7 +531,7 @@ def batched_compare(args):
     t_init = time.perf_counter() - t0
     sites = sum(e ** 3 for e, _, _ in params)
     t0 = time.perf_counter()
-    batch = elbm.Batch(sims, pipeline=args.pipeline == "on")
+    batch = elbm.Batch(sims, pipeline=args.pipeline == "on", span=args.span)
     t_capture = time.perf_counter() - t0
     batch.step(args.warmup)
     torch.cuda.synchronize()
@@ -551,7 +560,7 @@ def batched_compare(args):
         s.close()
     return {"boxes": len(params), "sites": sites, "edges": sorted(set(e for e, _, _ in params)),
             "batched": {"mlups": sites / (ms_b * 1e-3) / 1e6, "ms_per_step": ms_b, "max_h_error_device": hmax_b,
-                        "graph_launches_per_step": 1, "pipelined": args.pipeline == "on"},
+                        "graph_launches_per_step": 1.0 / args.span, "pipelined": args.pipeline == "on"},
             "one_at_a_time": {"mlups": sites / (single_ms * 1e-3) / 1e6, "ms_per_step": single_ms,
                               "max_h_error_device": hmax_s},
             "speedup_batched_vs_single": single_ms / ms_b,

@@ -199,6 +199,7 @@ elbm_status elbm_pass_times(const elbm_handle *h, double *out, int n);
 
 /* elbm_batch_create flags */
 #define ELBM_BATCH_PIPELINE 1 /* instances at odd positions run half a step ahead */
+#define ELBM_BATCH_SPAN(k) ((k) << 8) /* graphs of k steps (1..16) for elbm_step(batch, >= k) */
 
 /* Batched lattices (not in the paper: an execution form). One batch handle
  * advances n existing instance handles (each made by elbm_init, with
@@ -220,9 +221,18 @@ elbm_status elbm_pass_times(const elbm_handle *h, double *out, int n);
  *          (one step later than an instance not ahead). Its first moments
  *          and solve run once here. After the batch is freed, such an
  *          instance stepped alone repeats that solve (warm-started);
- *   stream cudaStream_t on which elbm_step(batch) launches the graph.
+ *          | ELBM_BATCH_SPAN(k), k in 1..16: besides the one-step graphs,
+ *          graphs of k consecutive steps, each instance's k steps one chain
+ *          of its branch: elbm_step(batch, n) launches n / k of them and the
+ *          rest one step at a time. The branches meet once per k steps
+ *          instead of every step, so one instance's latency-bound solves
+ *          overlap the others' collisions across step boundaries; every
+ *          instance runs the same kernels in the same order (bit for bit
+ *          the results of one-step launches);
+ *   stream cudaStream_t on which elbm_step(batch) launches the graphs.
  * elbm_step(batch, k) advances every instance k steps and returns the worst
- * status of the instances (non-finite state, Poisson non-convergence);
+ * status of the instances (non-finite state, Poisson non-convergence; the
+ * non-finite count is that of the last step, a NaN persisting);
  * elbm_fields and elbm_pass_times on a batch return ELBM_E_STATE (read each
  * instance); elbm_free(batch) frees the batch only. */
 elbm_status elbm_batch_create(elbm_handle *const *inst, int n, int flags, void *stream, elbm_handle **out);
@@ -233,7 +243,9 @@ elbm_status elbm_batch_create(elbm_handle *const *inst, int n, int flags, void *
  * from FP32 deviations d_p = f_p - w_p (FP32 arithmetic, in the order the
  * FP32 collision uses): rho = 1 + sum d, u = sum d c / rho,
  * Delta_p = w_p (sum d + rho P_p(u)) - d_p with P_p the velocity polynomial
- * of Eq. (2), f_p = w_p + d_p rounded to FP32.
+ * of Eq. (2) (formed so that sum_p Delta_p = 0 as for the exact Delta: sum d
+ * compensated, w_p sum d - d_p in one rounding, the residual taken off
+ * Delta_0), f_p = w_p + d_p rounded to FP32.
  *   d       device FP32 deviations, planes d[p*n + i], p = 0..18;
  *   n       number of sites (0: nothing is enqueued);
  *   aprec   ELBM_APREC_* arithmetic of the root;

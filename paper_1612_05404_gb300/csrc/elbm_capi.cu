@@ -66,6 +66,8 @@ struct elbm_handle {
     elbm_handle **sub;
     long long *sub_step0;      // each instance's step counter when the batch was made
     cudaGraphExec_t bexec[2];  // all instances' steps, one graph per A/B parity
+    cudaGraphExec_t bspan[2];  // span consecutive steps per launch (span > 1), per starting parity
+    int span;
     cudaEvent_t ev_fork;
     cudaEvent_t *ev_join;
     int pipe;                  // ELBM_BATCH_PIPELINE: odd positions run half a step ahead
@@ -544,7 +546,7 @@ bool capture_step(elbm_handle *h, int parity, cudaGraphExec_t *out, int sections
 // latency-bound solve overlaps the other instances' collisions and the
 // reverse; its prologue (prologue = true) is the first step's moments and
 // solve alone.
-bool capture_batch(elbm_handle *B, int parity, cudaGraphExec_t *out, bool prologue = false)
+bool capture_batch(elbm_handle *B, int parity, cudaGraphExec_t *out, bool prologue = false, int steps = 1)
 {
     cudaStream_t s = B->cap;
     cudaGraph_t graph = nullptr;
@@ -556,19 +558,22 @@ bool capture_batch(elbm_handle *B, int parity, cudaGraphExec_t *out, bool prolog
         const bool ahead = B->pipe && (i & 1);
         if (prologue && !ahead) continue;
         ok = cuda_ok(cudaStreamWaitEvent(h->cap, B->ev_fork, 0));
-        if (prologue) {
-            ok = ok && enqueue_step(h, parity, h->cap, 3, n_pre, n_body, n_post);
-        } else if (ahead) {
-            ok = ok && enqueue_step(h, parity, h->cap, 4, n_pre, n_body, n_post);
-            ok = ok && enqueue_step(h, parity ^ 1, h->cap, 3, n_pre, n_body, n_post);
-        } else {
-            ok = ok && enqueue_step(h, parity, h->cap, 7, n_pre, n_body, n_post);
+        for (int k = 0; k < (prologue ? 1 : steps); k++) {  // consecutive steps: one chain
+            const int par = parity ^ (k & 1);
+            if (prologue) {
+                ok = ok && enqueue_step(h, par, h->cap, 3, n_pre, n_body, n_post);
+            } else if (ahead) {
+                ok = ok && enqueue_step(h, par, h->cap, 4, n_pre, n_body, n_post);
+                ok = ok && enqueue_step(h, par ^ 1, h->cap, 3, n_pre, n_body, n_post);
+            } else {
+                ok = ok && enqueue_step(h, par, h->cap, 7, n_pre, n_body, n_post);
+            }
         }
         if (!prologue) ok = ok && enqueue_status(h, h->cap);
         ok = ok && cuda_ok(cudaEventRecord(B->ev_join[i], h->cap));
         ok = ok && cuda_ok(cudaStreamWaitEvent(s, B->ev_join[i], 0));
     }
-    if (prologue) parity = 1;  // kernel counts belong to the steady graphs
+    if (prologue || steps > 1) parity = 1;  // kernel counts belong to the one-step graphs
     ok = cuda_ok(cudaStreamEndCapture(s, &graph)) && ok;
     std::vector<const void *> heavy;
     for (int i = 0; i < B->n_sub; i++) heavy.insert(heavy.end(), B->sub[i]->ops.heavy, B->sub[i]->ops.heavy + 4);
@@ -972,7 +977,8 @@ elbm_status elbm_batch_create(elbm_handle *const *inst, int n, int flags, void *
 {
     if (!out) return ELBM_E_INVAL;
     *out = nullptr;
-    if (!inst || n < 1 || (flags & ~ELBM_BATCH_PIPELINE)) return ELBM_E_INVAL;
+    const int span = (flags >> 8) == 0 ? 1 : (flags >> 8);
+    if (!inst || n < 1 || (flags & ~(ELBM_BATCH_PIPELINE | 0xFF00)) || span > 16) return ELBM_E_INVAL;
     for (int i = 0; i < n; i++) {
         if (!inst[i] || inst[i]->n_sub > 0) return ELBM_E_INVAL;
         if (inst[i]->p.diag_every != 1 || inst[i]->p.profile) return ELBM_E_INVAL;
@@ -985,6 +991,7 @@ elbm_status elbm_batch_create(elbm_handle *const *inst, int n, int flags, void *
     B->s = (cudaStream_t)stream;
     B->n_sub = n;
     B->pipe = (flags & ELBM_BATCH_PIPELINE) && n > 1;
+    B->span = span;
     B->sub = new (std::nothrow) elbm_handle *[n];
     B->sub_step0 = new (std::nothrow) long long[n];
     B->ev_join = new (std::nothrow) cudaEvent_t[n]();
@@ -1000,6 +1007,8 @@ elbm_status elbm_batch_create(elbm_handle *const *inst, int n, int flags, void *
     ok = ok && cuda_ok(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
     ok = ok && cuda_ok(cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming));
     ok = ok && capture_batch(B, 0, &B->bexec[0]) && capture_batch(B, 1, &B->bexec[1]);
+    if (span > 1)
+        ok = ok && capture_batch(B, 0, &B->bspan[0], false, span) && capture_batch(B, 1, &B->bspan[1], false, span);
     if (ok && B->pipe) {  // the odd positions' first moments and potential solve, once
         cudaGraphExec_t pro = nullptr;
         ok = capture_batch(B, 0, &pro, true);
@@ -1045,13 +1054,18 @@ elbm_status elbm_step(elbm_handle *h, int nsteps)
     if (h->n_sub > 0) {
         for (int i = 0; i < h->n_sub; i++)
             if (h->sub[i]->step - h->sub_step0[i] != h->step) return ELBM_E_STATE;
-        for (int k = 0; k < nsteps; k++) {
-            if (!cuda_ok(cudaGraphLaunch(h->bexec[h->step & 1], h->s))) return ELBM_E_CUDA;
-            for (int i = 0; i < h->n_sub; i++) {
-                swap_ab(h->sub[i]->b);
-                h->sub[i]->step++;
+        for (int k = 0; k < nsteps;) {
+            const int m = (h->span > 1 && nsteps - k >= h->span) ? h->span : 1;  // steps in this launch
+            if (!cuda_ok(cudaGraphLaunch(m > 1 ? h->bspan[h->step & 1] : h->bexec[h->step & 1], h->s)))
+                return ELBM_E_CUDA;
+            for (int j = 0; j < m; j++) {
+                for (int i = 0; i < h->n_sub; i++) {
+                    swap_ab(h->sub[i]->b);
+                    h->sub[i]->step++;
+                }
+                h->step++;
             }
-            h->step++;
+            k += m;
         }
         if (!cuda_ok(cudaStreamSynchronize(h->s))) return ELBM_E_CUDA;
         elbm_status worst = ELBM_OK;
@@ -1234,8 +1248,10 @@ void elbm_free(elbm_handle *h)
     if (!h) return;
     cudaStreamSynchronize(h->s);
     if (h->n_sub > 0) {  // a batch: its graphs and events only, not the instances
-        for (int i = 0; i < 2; i++)
+        for (int i = 0; i < 2; i++) {
             if (h->bexec[i]) cudaGraphExecDestroy(h->bexec[i]);
+            if (h->bspan[i]) cudaGraphExecDestroy(h->bspan[i]);
+        }
         if (h->ev_join)
             for (int i = 0; i < h->n_sub; i++)
                 if (h->ev_join[i]) cudaEventDestroy(h->ev_join[i]);

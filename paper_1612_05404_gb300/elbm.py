@@ -393,11 +393,12 @@ class Batch:
     (elbm_batch_create). The batch keeps references to its Sim instances; step
     them only through the batch; read fields from each instance."""
 
-    def __init__(self, sims, pipeline=False, stream=None):
+    def __init__(self, sims, pipeline=False, span=1, stream=None):
         self.sims = list(sims)
         arr = (ctypes.c_void_p * len(self.sims))(*[s.h.value for s in self.sims])
         h = ctypes.c_void_p()
-        rc = lib().elbm_batch_create(arr, len(self.sims), 1 if pipeline else 0,
+        flags = (1 if pipeline else 0) | (int(span) << 8 if span > 1 else 0)  # ELBM_BATCH_PIPELINE, _SPAN(k)
+        rc = lib().elbm_batch_create(arr, len(self.sims), flags,
                                      stream if stream is not None else _cur_stream(), ctypes.byref(h))
         if rc != OK:
             raise ElbmError(rc, "elbm_batch_create")

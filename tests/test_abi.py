@@ -147,4 +147,5 @@ def test_batch_create_argument_checks(L):
     assert L.elbm_batch_create(arr, 0, 0, None, ctypes.byref(out)) == elbm.E_INVAL
     assert L.elbm_batch_create(arr, 1, 0, None, ctypes.byref(out)) == elbm.E_INVAL  # a NULL instance
     assert L.elbm_batch_create(arr, 1, 6, None, ctypes.byref(out)) == elbm.E_INVAL  # unknown flag
+    assert L.elbm_batch_create(arr, 1, 17 << 8, None, ctypes.byref(out)) == elbm.E_INVAL  # span above 16
     assert not out.value

@@ -132,3 +132,23 @@ def test_batch_reports_each_instance_status():
     assert batch.step(1) == elbm.W_POISSON_NOCONV
     assert capped.diag()["poisson_sweeps"] == 3
     batch.close()
+
+
+@pytest.mark.parametrize("pipeline", [False, True])
+def test_span_graphs_reproduce_one_step_launches_bitwise(pipeline):
+    """ELBM_BATCH_SPAN(4): graphs of four consecutive steps run the same
+    kernels in the same order per instance as four one-step launches; a
+    step count that is not a multiple of the span ends with one-step
+    launches."""
+    from paper_1612_05404_gb300 import elbm
+    one, spanned = _make(), _make()
+    b1 = elbm.Batch(one, pipeline=pipeline)
+    b4 = elbm.Batch(spanned, pipeline=pipeline, span=4)
+    assert b1.step(7) >= 0
+    assert b4.step(7) >= 0
+    for a, b in zip(one, spanned):
+        for name in ("rho", "phi", "q", "f"):
+            assert np.array_equal(a.get(name), b.get(name)), name
+        assert a.diag() == b.diag()
+    b1.close()
+    b4.close()
