@@ -319,7 +319,10 @@ def run_ours(args, rank, world, local_rank):
                      "bytes_per_site": bytes_site, "avg_launch_ms": coll_ms,
                      "timed": "one 64^3 lattice alone, CUDA events around each collision launch"},
         "pass_share": shares,
-        "gpu_launches": int(round(launches_per_step * len(sims) * args.steps)),
+        # kernels of the timed launches: per lattice and step those of the
+        # one-step graph, less the diagnostics finalize that a graph of m
+        # steps runs once instead of m times
+        "gpu_launches": int(round(len(sims) * sum(m * launches_per_step - (m - 1) for m in chunks))),
         "alpha": {"max_h_error_device": max(x["max_h_error"] for x in diag), "h_error_bound": 1e-10,
                   "guarded_sites_last_step": sum(x["n_guarded"] for x in diag),
                   "guard_failed_last_step": sum(x["n_guard_failed"] for x in diag),

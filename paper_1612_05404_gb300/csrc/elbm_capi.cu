@@ -97,6 +97,7 @@ struct Ctl {
     int units_max;
     int reduced;               // FP32 potential: stop at the rounding floor
     int ce;
+    int steps;                 // FIN_DIAG: time steps these diagnostics close (the step counter's increment)
 };
 
 // Sum (or min / max) each of the K columns of the per-block partials in a
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(256) k_finalize(const double *part, int nblock
         diag[14] = res[D_UMAX];
         diag[15] = res[D_NBAD];
         diag[16] = scal[S_QMEAN];
-        scal[S_STEPS] += 1.0;
+        scal[S_STEPS] += double(ctl.steps);
         diag[17] = scal[S_STEPS];
         diag[18] = scal[S_ITER_TOTAL] * ctl.ce;
         diag[19] = res[D_NGUARD];
@@ -283,14 +284,17 @@ Ctl make_ctl(const elbm_handle *h, unsigned long long cond, int use_cond)
     c.units_max = h->units_max;
     c.reduced = h->p.precision != ELBM_PREC_FP64;
     c.ce = h->ce;
+    c.steps = 1;
     return c;
 }
 
 int fin(elbm_handle *h, const Bufs &b, cudaStream_t s, int K, int mode, unsigned long long cond = 0,
-        int use_cond = 0)
+        int use_cond = 0, int steps = 1)
 {
-    k_finalize<<<K, 256, 0, s>>>(b.part, h->L.nblocks, K, mode, h->ph, make_ctl(h, cond, use_cond),
-                                 b.scal, b.scalf, b.diag, b.colres, b.ticket);
+    Ctl c = make_ctl(h, cond, use_cond);
+    c.steps = steps;
+    k_finalize<<<K, 256, 0, s>>>(b.part, h->L.nblocks, K, mode, h->ph, c, b.scal, b.scalf, b.diag, b.colres,
+                                 b.ticket);
     return 1;
 }
 
@@ -454,7 +458,11 @@ bool prioritize(cudaGraph_t graph, const std::vector<const void *> &heavy_fns)
     return true;
 }
 
-bool enqueue_step(elbm_handle *h, int parity, cudaStream_t s, int sections, int &n_pre, int &n_body, int &n_post)
+// diag_steps: the collision's diagnostics and their finalize close this
+// many steps (the step counter advances by it); 0 skips both, for a step
+// inside a multi-step graph whose diagnostics the last step supersedes.
+bool enqueue_step(elbm_handle *h, int parity, cudaStream_t s, int sections, int &n_pre, int &n_body, int &n_post,
+                  int diag_steps = 1)
 {
     Bufs b = h->b;
     if (parity) swap_ab(b);
@@ -501,8 +509,9 @@ bool enqueue_step(elbm_handle *h, int parity, cudaStream_t s, int sections, int 
             h->ops.alpha_mlp(h->g, h->ph, b, h->L, s);
             n_post += 1;
         }
-        h->ops.collide(h->g, h->ph, b, 1, h->L, s);
-        n_post += 1 + fin(h, b, s, D_NPART, FIN_DIAG);
+        h->ops.collide(h->g, h->ph, b, diag_steps > 0 ? 1 : 0, h->L, s);
+        n_post += 1;
+        if (diag_steps > 0) n_post += fin(h, b, s, D_NPART, FIN_DIAG, 0, 0, diag_steps);
     }
     return ok;
 }
@@ -560,13 +569,15 @@ bool capture_batch(elbm_handle *B, int parity, cudaGraphExec_t *out, bool prolog
         ok = cuda_ok(cudaStreamWaitEvent(h->cap, B->ev_fork, 0));
         for (int k = 0; k < (prologue ? 1 : steps); k++) {  // consecutive steps: one chain
             const int par = parity ^ (k & 1);
+            // diagnostics once, on the last step, closing all `steps` of them
+            const int dsteps = k == steps - 1 ? steps : 0;
             if (prologue) {
                 ok = ok && enqueue_step(h, par, h->cap, 3, n_pre, n_body, n_post);
             } else if (ahead) {
-                ok = ok && enqueue_step(h, par, h->cap, 4, n_pre, n_body, n_post);
+                ok = ok && enqueue_step(h, par, h->cap, 4, n_pre, n_body, n_post, dsteps);
                 ok = ok && enqueue_step(h, par ^ 1, h->cap, 3, n_pre, n_body, n_post);
             } else {
-                ok = ok && enqueue_step(h, par, h->cap, 7, n_pre, n_body, n_post);
+                ok = ok && enqueue_step(h, par, h->cap, 7, n_pre, n_body, n_post, dsteps);
             }
         }
         if (!prologue) ok = ok && enqueue_status(h, h->cap);
