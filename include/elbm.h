@@ -228,7 +228,9 @@ elbm_status elbm_pass_times(const elbm_handle *h, double *out, int n);
  *          instead of every step, so one instance's latency-bound solves
  *          overlap the others' collisions across step boundaries; every
  *          instance runs the same kernels in the same order (bit for bit
- *          the results of one-step launches);
+ *          the populations and fields of one-step launches), except that
+ *          the diagnostics (ELBM_F_DIAG) are formed on the last of the k
+ *          steps only;
  *   stream cudaStream_t on which elbm_step(batch) launches the graphs.
  * elbm_step(batch, k) advances every instance k steps and returns the worst
  * status of the instances (non-finite state, Poisson non-convergence; the
