@@ -50,8 +50,9 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="issue each step from the host (profilers see every launch)")
     ap.add_argument("--launch", default="batch", choices=["batch", "streams"],
                     help="batch: all lattices in one graph per step; streams: one graph per lattice per stream")
-    ap.add_argument("--span", type=int, default=4,
-                    help="batch: steps per graph launch (ELBM_BATCH_SPAN); timed launches cover that many steps")
+    ap.add_argument("--span", type=int, default=0,
+                    help="batch: steps per graph launch (ELBM_BATCH_SPAN, 1..16); timed launches cover that "
+                         "many steps; 0: the largest divisor of --steps up to 10")
     ap.add_argument("--pipeline", default="on", choices=["on", "off"],
                     help="batch: odd-position lattices run half a step ahead (ELBM_BATCH_PIPELINE)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -62,6 +63,14 @@ def parse():
                     help="batched-droplets comparison: number of boxes (0 skips it)")
     ap.add_argument("--no-jet", action="store_true", help="skip the electrified-jet measurement")
     return ap.parse_args()
+
+
+def span_of(args):
+    """Steps per batch graph launch: --span, or the largest divisor of the
+    timed step count up to 10 (every timed launch then a full span)."""
+    if args.span > 0:
+        return args.span
+    return max(d for d in range(1, 11) if args.steps % d == 0)
 
 
 def max_over_ranks(ms, device):
@@ -212,7 +221,7 @@ def run_ours(args, rank, world, local_rank):
         for c, _ in cfgs:
             c.update(autotune=1, profile=0)
         sims = [elbm.Sim(c, f) for c, f in cfgs]
-        batch = elbm.Batch(sims, pipeline=args.pipeline == "on", span=args.span)
+        batch = elbm.Batch(sims, pipeline=args.pipeline == "on", span=span_of(args))
         step_all = lambda m=1: batch.step(m)
         streams = None
     else:
@@ -224,7 +233,7 @@ def run_ours(args, rank, world, local_rank):
         step_all = lambda m=1: list(pool.map(lambda s: s.step(m), sims))
     # timed launches: `span` steps per graph launch (batch), the rest one step
     # at a time; exactly args.steps steps in all
-    span = args.span if args.launch == "batch" else 1
+    span = span_of(args) if args.launch == "batch" else 1
     chunks = [span] * (args.steps // span) + [1] * (args.steps % span)
     for _ in range(args.warmup):
         step_all()
@@ -534,7 +543,7 @@ def batched_compare(args):
     t_init = time.perf_counter() - t0
     sites = sum(e ** 3 for e, _, _ in params)
     t0 = time.perf_counter()
-    batch = elbm.Batch(sims, pipeline=args.pipeline == "on", span=args.span)
+    batch = elbm.Batch(sims, pipeline=args.pipeline == "on", span=span_of(args))
     t_capture = time.perf_counter() - t0
     batch.step(args.warmup)
     torch.cuda.synchronize()
@@ -563,7 +572,7 @@ def batched_compare(args):
         s.close()
     return {"boxes": len(params), "sites": sites, "edges": sorted(set(e for e, _, _ in params)),
             "batched": {"mlups": sites / (ms_b * 1e-3) / 1e6, "ms_per_step": ms_b, "max_h_error_device": hmax_b,
-                        "graph_launches_per_step": 1.0 / args.span, "pipelined": args.pipeline == "on"},
+                        "graph_launches_per_step": 1.0 / span_of(args), "pipelined": args.pipeline == "on"},
             "one_at_a_time": {"mlups": sites / (single_ms * 1e-3) / 1e6, "ms_per_step": single_ms,
                               "max_h_error_device": hmax_s},
             "speedup_batched_vs_single": single_ms / ms_b,
