@@ -52,7 +52,7 @@ def parse():
                     help="batch: all lattices in one graph per step; streams: one graph per lattice per stream")
     ap.add_argument("--span", type=int, default=0,
                     help="batch: steps per graph launch (ELBM_BATCH_SPAN, 1..16); timed launches cover that "
-                         "many steps; 0: the largest divisor of --steps up to 10")
+                         "many steps; 0: the span that covers --steps in the fewest launches")
     ap.add_argument("--pipeline", default="on", choices=["on", "off"],
                     help="batch: odd-position lattices run half a step ahead (ELBM_BATCH_PIPELINE)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -66,11 +66,13 @@ def parse():
 
 
 def span_of(args):
-    """Steps per batch graph launch: --span, or the largest divisor of the
-    timed step count up to 10 (every timed launch then a full span)."""
+    """Steps per batch graph launch: --span, or the span up to 16 that covers
+    the timed steps in the fewest launches (full spans plus single steps),
+    with the smallest remainder among those (10 for 20 steps)."""
     if args.span > 0:
         return args.span
-    return max(d for d in range(1, 11) if args.steps % d == 0)
+    n = max(args.steps, 1)
+    return min(range(1, 17), key=lambda s: (n // s + n % s, n % s, s))
 
 
 def max_over_ranks(ms, device):
