@@ -255,8 +255,6 @@ __device__ __forceinline__ double sigma_of(const Cst<double> &k, double rho)
 {
     return k.sig_g + k.dsig * 0.5 * (1.0 + tanh((rho - k.rho0) * k.itw));
 }
-template <typename T>
-__device__ __forceinline__ T theta_of(T rho, T rho0, T w) { return T(0.5) * (T(1) + tanh((rho - rho0) / w)); }
 
 __device__ __forceinline__ void site_xyz(const Geom &g, int &x, int &y, int &z, bool &inb, ll &s)
 {
