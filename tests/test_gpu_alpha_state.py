@@ -76,3 +76,44 @@ def test_fp32_collision_conserves_mass():
     m = float(np.sum(sim.get("rho")))
     # FP32 deviation storage: rounding of the stored populations only
     assert abs(m - m0) <= 1e-7 * m0, (m0, m)
+
+
+def test_benchmark_launch_configuration_at_full_size():
+    """The benchmark's workload and launch form at full size: four 64^3
+    drops (the E0 sweep) in one batch with the half-step shift and graphs
+    of ten steps, autotuned shapes. After 20 steps: the mass of every
+    lattice is kept (FP32 rounding only), no guard failed, the reported
+    H-error is within 1e-10, and the alpha of sampled sites of the last
+    lattice solves the exact entropic equation (the oracle, site by site)."""
+    from paper_1612_05404_gb300 import elbm
+    sims, m0 = [], []
+    for E0 in W.E0_SWEEP:
+        cfg, fields = W.drop_in_field(E0=E0, precision="fp32")
+        cfg.update(alpha_precision="fp32", store_macro=1, autotune=1, poisson_check_every=8)
+        m0.append(float(np.sum(fields["rho"])))
+        sims.append(elbm.Sim(cfg, fields))
+    batch = elbm.Batch(sims, pipeline=True, span=10)
+    assert batch.step(20) >= 0
+    batch.close()
+    for s, m in zip(sims, m0):
+        d = s.diag()
+        assert d["step"] == 20
+        assert d["n_guard_failed"] == 0 and d["max_h_error"] <= 1e-10, d
+        assert abs(float(np.sum(s.get("rho"))) - m) <= 1e-7 * m
+    # site-by-site alpha on the last lattice: one more step alone
+    sim = sims[-1]
+    f = sim.get("f").reshape(19, -1)
+    sim.step(1)
+    alpha = sim.get("alpha")
+    c, _, _ = oracle.lattice(3)
+    rng = np.random.default_rng(11)
+    for i in rng.choice(f.shape[1], 300, replace=False):
+        fi = f[:, i]
+        rho = fi.sum()
+        u = (c.T @ fi) / rho
+        d = oracle.feq(3, rho, u) - fi
+        if oracle.alpha(3, fi, d, 1e-12)[1] != 0:
+            continue
+        S = np.max(np.abs(d / fi))
+        herr = abs(_h_exact(fi, d, alpha[i])) / rho
+        assert herr <= (1e-10 if S < 1e-3 else 3e-8), (i, S, alpha[i], herr)
