@@ -18,9 +18,10 @@
  *    passed in are FP64 (fields) or uint8 (node kinds), owned by the caller and
  *    only read during the call. Population arrays are planes: f[p*N + site],
  *    in the velocity order reported by elbm_velocity_set().
- *  - The handle owns every byte of device memory it uses; elbm_free releases
- *    it. Work is issued on the caller's CUDA stream (params.cuda_stream,
- *    NULL = the legacy default stream).
+ *  - The handle owns every byte of device memory it uses (one arena, plus
+ *    the export scratch of elbm_fields); elbm_free releases it. Work is
+ *    issued on the caller's CUDA stream (params.cuda_stream, NULL = the
+ *    legacy default stream).
  *  - Invalid parameters return ELBM_E_INVAL and allocate nothing.
  */
 #ifndef ELBM_H
@@ -69,7 +70,9 @@ enum { ELBM_ALPHA_ENTROPIC = 0, ELBM_ALPHA_BGK = 1, ELBM_ALPHA_LEARNED = 2 };
 /* population storage / arithmetic:
  *   FP64: f stored and computed in FP64, potential in FP64;
  *   FP32: f stored as FP32 deviations d = f - w, FP32 arithmetic;
- *   BF16: f stored as BF16 deviations, FP32 arithmetic. */
+ *   BF16: f stored in BF16 as f - w rho_ref, rho_ref the density of the
+ *         site that wrote the value (kept beside the populations), FP32
+ *         arithmetic. */
 enum { ELBM_PREC_FP64 = 0, ELBM_PREC_FP32 = 1, ELBM_PREC_BF16 = 2 };
 /* arithmetic of the alpha root:
  *   FP64: Newton in FP64;
