@@ -218,3 +218,70 @@ def test_uniform_field_on_neutral_fluid_exerts_no_force():
     sim.step()
     r1, j1 = sim.moments()
     assert np.abs(j1).max() < 1e-16
+
+
+def _force_from_step(sim):
+    """Body force per site from one oracle step started at rest: the
+    reported half-step velocity is (j + F/2)/rho with j = 0."""
+    sim.step()
+    rho = sim.rho
+    return 2.0 * rho[:, None] * sim.u.reshape(-1, 3)
+
+
+def test_full_electric_force_matches_discrete_closed_form():
+    """Eq. (force_el2) on a neutral fluid of uniform density: F = (eps - 1)/2
+    grad|E|^2. With phi = A sin(kx) + B sin(ky + c) and a uniform applied
+    field E0, the central-difference field is E_x = -A sin(k) cos(kx) + E0_x
+    (E_y likewise), and the central difference of E_x^2 has the closed form
+    -A^2 sin^2(k) sin(2k) sin(2kx)/2 + 2 A E0_x sin^2(k) sin(kx): the force
+    must equal (eps - 1)/2 times it site by site. A wrong sign, a lost factor
+    1/2 or eps in place of eps - 1 fails; the q E form gives no force here."""
+    n, A, B, c, kap, r0 = 16, 0.02, -0.015, 0.3, 0.7, 1.5
+    E0 = (3e-3, -2e-3, 5e-3)
+    shape = (n, n, 4)
+    N = n * n * 4
+    x, y, z = [a.reshape(-1) for a in W._grid(shape)]
+    k = 2 * np.pi / n
+    phi = A * np.sin(k * x) + B * np.sin(k * y + c)
+    eps = 1.0 + kap * r0
+    s2 = np.sin(k) ** 2
+    d_ex2 = -0.5 * A * A * s2 * np.sin(2 * k) * np.sin(2 * k * x) + 2 * A * E0[0] * s2 * np.sin(k * x)
+    d_ey2 = -0.5 * B * B * s2 * np.sin(2 * k) * np.sin(2 * (k * y + c)) + 2 * B * E0[1] * s2 * np.sin(k * y + c)
+    expect = np.stack([0.5 * (eps - 1.0) * d_ex2, 0.5 * (eps - 1.0) * d_ey2, np.zeros(N)], 1)
+    for form in ("full", "qe"):
+        cfg = W.base_params(shape=shape, G=0.0, Gw=0.0, charge_model="none", force_el=form,
+                            eps_kappa=kap, E_ext=E0)
+        sim = oracle.Sim(cfg, dict(mask=np.zeros(N, np.uint8), rho=np.full(N, r0)))
+        sim.phi[:] = phi
+        F = _force_from_step(sim)
+        if form == "qe":
+            assert np.abs(F).max() < 1e-18
+            continue
+        scale = np.abs(expect).max()
+        assert scale > 1e-6
+        assert np.abs(F - expect).max() <= 1e-12 * scale
+        # the continuum force (eps-1)/2 d|E|^2/dx with E = -phi' + E0 agrees to O(k^2)
+        ex = -A * k * np.cos(k * x) + E0[0]
+        cont = 0.5 * (eps - 1.0) * 2 * ex * (A * k * k * np.sin(k * x))
+        assert np.abs(F[:, 0] - cont).max() <= 0.2 * np.abs(cont).max()
+
+
+def test_uniform_charge_in_uniform_field_gives_qE():
+    """A uniform free charge q in a uniform applied field (neutralised
+    background, so phi stays 0): the electric force of Eq. (force_el) is q E
+    at every site and the total momentum rises by N q E in one step."""
+    shape = (4, 6, 4)
+    N = 96
+    q0, E0 = 0.01, (0.3, -0.1, 0.2)
+    cfg = W.base_params(shape=shape, G=0.0, Gw=0.0, charge_model="transport", E_ext=E0,
+                        sigma_liq=0.02, sigma_gas=0.002)
+    sim = oracle.Sim(cfg, dict(mask=np.zeros(N, np.uint8), rho=np.full(N, 1.3), q=np.full(N, q0)))
+    r0, j0 = sim.moments()
+    assert np.abs(j0).max() == 0.0
+    F = _force_from_step(sim)
+    assert np.abs(sim.phi).max() == 0.0
+    assert np.allclose(sim.q, q0, rtol=1e-15, atol=0)
+    expect = q0 * np.asarray(E0)
+    assert np.abs(F - expect[None, :]).max() <= 1e-15 * np.abs(expect).max()
+    r1, j1 = sim.moments()
+    assert np.allclose(j1.sum(0), N * expect, rtol=1e-13, atol=0)
