@@ -340,7 +340,11 @@ elbm_status elbm_mlp_train(const float *X, const float *y, long long n, float *t
  * held by every GPU that loads it until the process exits, so
  * n_sites <= ELBM_NOALLOC_MAX_SITES (else ELBM_E_INVAL). The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress); make
- * the first call on each device before any stream capture. Every call uses
+ * the first call on each device before any stream capture. The address is
+ * kept for the life of the device's primary context: after a
+ * cudaDeviceReset the entry point must not be called again in that process.
+ * A CUDA error left pending on the calling thread by earlier work is cleared,
+ * not reported as this call's. Every call uses
  * the same scratch and leaves its contents behind (each call overwrites the
  * slots it reads, so nothing needs clearing); calls whose kernels overlap on
  * the GPU (several streams at once) race on it and must be serialised by the

@@ -213,45 +213,106 @@ __device__ __forceinline__ ffl grp_sum(const Grp &g, ffl v)
     return v;
 }
 
-// h'(0) in float-float: (1 + ln r) sum D + sum D_p ln(f_p / (w_p r)); 1/w_p is
-// the integer 3, 18 or 36, so f_p / (w_p r) = (f_p / w_p) / r exactly as pairs.
-// The guard's loops are not unrolled: compact code for a path few warps take.
-__device__ __forceinline__ ffl h0_ff(const float *f, const float *d, float r, const Grp &gp)
+// ---------------------------------------------------------------------------
+// The exact inputs of the guard. The populations are f_p = w_p + d_p with d_p
+// the FP32 deviations and w_p the weights in FP64 (1/3, 1/18, 1/36); the
+// guard forms, as float-float pairs, the site's moments drho = sum d and
+// j = sum c d, u = j / rho, and Delta_p = f^eq_p - f_p of Eq. (2) written as
+// w_p drho - d_p + w_p rho P_p(u), so that the root it certifies is the root
+// of the exact equation for those populations (not for the FP32 Delta the
+// collision applies, which carries rounding of the size of f^eq's terms).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ ffl w_ff(int p)
+{
+    constexpr float h0 = float(1.0 / 3.0), h1 = float(1.0 / 18.0), h2 = float(1.0 / 36.0);
+    constexpr float l0 = float(1.0 / 3.0 - double(h0)), l1 = float(1.0 / 18.0 - double(h1)),
+                    l2 = float(1.0 / 36.0 - double(h2));
+    return p == 0 ? ffl{h0, l0} : (p < 7 ? ffl{h1, l1} : ffl{h2, l2});
+}
+
+struct SiteFF {
+    ffl drho, rho, u[3], usq;
+};
+
+__device__ __forceinline__ void site_ff(const float *dev, SiteFF &m, const Grp &gp)
+{
+    ffl s = {0.f, 0.f}, j[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 1
+    for (int p = gp.j; p < Q; p += gp.L) {
+        const float v = dev[p];
+        s = ff_add_f(s, v);
+        const int c[3] = {cx(p), cy(p), cz(p)};
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            if (c[a]) j[a] = ff_add_f(j[a], c[a] > 0 ? v : -v);
+    }
+    m.drho = grp_sum(gp, s);
+    m.rho = ff_add_f(m.drho, 1.f);
+#pragma unroll
+    for (int a = 0; a < 3; a++) m.u[a] = ff_div(grp_sum(gp, j[a]), m.rho);
+    m.usq = ff_add(ff_add(ff_mul(m.u[0], m.u[0]), ff_mul(m.u[1], m.u[1])), ff_mul(m.u[2], m.u[2]));
+}
+
+// Delta_p with P_p(u) = c.u (3 + 4.5 c.u) - 1.5 u^2 (Eq. 2, c_s^2 = 1/3)
+__device__ __forceinline__ ffl delta_ff(int p, float devp, const SiteFF &m)
+{
+    ffl cu = {0.f, 0.f};
+    const int c[3] = {cx(p), cy(p), cz(p)};
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+        if (c[a]) cu = ff_add(cu, c[a] > 0 ? m.u[a] : ff_neg(m.u[a]));
+    const ffl P = ff_add(ff_mul(cu, ff_add_f(ff_mul_f(cu, 4.5f), 3.f)), ff_mul_f(m.usq, -1.5f));
+    const ffl w = w_ff(p);
+    return ff_add(ff_add_f(ff_mul(w, m.drho), -devp), ff_mul(ff_mul(w, m.rho), P));
+}
+
+// f_p = w_p + d_p and Delta_p of population p as pairs (Delta from the arrays
+// the guard filled)
+__device__ __forceinline__ ffl pop_ff(int p, const float *dev) { return ff_add_f(w_ff(p), dev[p]); }
+
+// h'(0) in float-float: (1 + ln rho) sum Delta + sum Delta_p ln(1 + z_p), with
+// z_p = f_p / (w_p rho) - 1 = (d_p - w_p drho) / (w_p rho) formed from small
+// terms. The guard's loops are not unrolled: compact code for a path few
+// warps take.
+__device__ __forceinline__ ffl h0_ff(const float *dev, const float *Dh, const float *Dl, const SiteFF &m,
+                                     const Grp &gp)
 {
     ffl S = {0.f, 0.f}, T = {0.f, 0.f};
 #pragma unroll 1
     for (int p = gp.j; p < Q; p += gp.L) {
-        S = ff_add_f(S, d[p]);
-        const float iw = p == 0 ? 3.f : (p < 7 ? 18.f : 36.f);
-        const ffl z = ff_add_f(ff_div(ff_prod(f[p], iw), ffl{r, 0.f}), -1.f);
+        const ffl D = {Dh[p], Dl[p]};
+        S = ff_add(S, D);
+        const ffl w = w_ff(p);
+        const ffl z = ff_div(ff_add_f(ff_neg(ff_mul(w, m.drho)), dev[p]), ff_mul(w, m.rho));
         // warp-uniform choice: a warp whose lanes disagree would run both paths
         const ffl l = __all_sync(__activemask(), fabsf(z.h) <= 0.125f) ? ff_log1p_small(z) : ff_log1p(z);
-        T = ff_add(T, ff_mul_f(l, d[p]));
+        T = ff_add(T, ff_mul(l, D));
     }
     S = grp_sum(gp, S);
     T = grp_sum(gp, T);
-    // ln r to FP32 accuracy suffices: sum D is at the rounding level of rho
-    return ff_add(ff_mul_f(S, 1.f + logf(r)), T);
+    // ln rho to FP32 accuracy suffices: sum Delta is at the rounding level of the pairs
+    return ff_add(ff_mul_f(S, 1.f + logf(m.rho.h)), T);
 }
 
 // h(a) in float-float, h'(a) and h''(a) = sum f x^2 / (1 + a x) in FP32, at a
 // float-float alpha
-__device__ __forceinline__ void h_ff(const float *f, const float *d, ffl a, ffl a0, ffl *h, float *hp,
-                                     float *hpp, const Grp &gp)
+__device__ __forceinline__ void h_ff(const float *dev, const float *Dh, const float *Dl, ffl a, ffl a0, ffl *h,
+                                     float *hp, float *hpp, const Grp &gp)
 {
     ffl acc = {0.f, 0.f};
     float g = 0.f, g2 = 0.f;
 #pragma unroll 1
     for (int p = gp.j; p < Q; p += gp.L) {
-        const ffl x = ff_div_f(d[p], f[p]);
+        const ffl F = pop_ff(p, dev), D = {Dh[p], Dl[p]};
+        const ffl x = ff_div(D, F);
         const ffl y = ff_mul(a, x);
         const ffl l = ff_log1p(y);
         // phi = (1 + y) l - y: its cancellation for small y costs relative
         // accuracy 2^-44 |y| / phi, far below the target in absolute terms
         const ffl ph = ff_add(ff_mul(ff_add_f(y, 1.f), l), ff_neg(y));
-        acc = ff_add(acc, ff_mul_f(ph, f[p]));
-        g = fmaf(d[p], l.h, g);
-        g2 = fmaf(f[p] * x.h, __fdividef(x.h, 1.f + y.h), g2);
+        acc = ff_add(acc, ff_mul(ph, F));
+        g = fmaf(D.h, l.h, g);
+        g2 = fmaf(F.h * x.h, __fdividef(x.h, 1.f + y.h), g2);
     }
     *h = ff_add(grp_sum(gp, acc), ff_mul(a, a0));
     *hp = grp_sum(gp, g) + a0.h;
@@ -271,7 +332,7 @@ struct MomFF {
     float xmax;
 };
 
-__device__ __forceinline__ void mom_ff(const float *f, const float *d, MomFF &m, const Grp &gp)
+__device__ __forceinline__ void mom_ff(const float *dev, const float *Dh, const float *Dl, MomFF &m, const Grp &gp)
 {
     m.M2 = ffl{0.f, 0.f};
     m.M3 = ffl{0.f, 0.f};
@@ -280,8 +341,9 @@ __device__ __forceinline__ void mom_ff(const float *f, const float *d, MomFF &m,
     m.xmax = 0.f;
 #pragma unroll 1
     for (int p = gp.j; p < Q; p += gp.L) {
-        const ffl x = ff_div_f(d[p], f[p]);
-        const ffl fx2 = ff_mul_f(ff_mul(x, x), f[p]);
+        const ffl F = pop_ff(p, dev), D = {Dh[p], Dl[p]};
+        const ffl x = ff_div(D, F);
+        const ffl fx2 = ff_mul(ff_mul(x, x), F);
         const ffl fx3 = ff_mul_f(fx2, x.h);
         m.M2 = ff_add(m.M2, fx2);
         m.M3 = ff_add(m.M3, fx3);
@@ -326,44 +388,86 @@ __device__ __forceinline__ ffl h_mom(ffl a, ffl a0, const MomFF &m, float *hp, f
     return h;
 }
 
-// The float-float guard from an FP32 root a: h'(0) and h(a) as pairs; accept
-// when |h| <= tol/2, else one Newton step a' = a - h/h' and accept a' when the
+// The float-float guard from an FP32 root a, for the site whose FP32
+// deviations are dev: the exact moments and Delta (Dh, Dl: the caller's
+// scratch of Q floats each, filled here), h'(0) and h as pairs. Where h'(0)
+// is small against the rounding of the FP32 Delta the exact root can lie far
+// from the FP32 one, so the iteration starts from the root of the exact
+// moment series (as the FP32 start, now from the pairs) when that differs
+// from a by more than 1e-3 a. Newton steps a' = a - h/h' inside the sign
+// bracket (0, amax) (h is convex: h < 0 left of the root), bisection when a
+// step leaves it; accept when |h| <= tol/2, or after a step when the
 // quadratic-convergence bound 3/4 h'' (a' - a)^2 plus 1e-11 rho (the pairs'
-// evaluation error) is within tol/2, else evaluate again (at most 3 steps).
-// Returns (alpha high, alpha low, H-error, accepted) on every lane of the
-// group (j its member index, L its size). Not inlined: one copy of the code,
-// entered only by warps that hold a site needing it.
-static __device__ __noinline__ float4 alpha_guard(const float *f, const float *d, float rho, float a, float S,
-                                                  int j, int L)
+// evaluation error) is within tol/2; at most 12 evaluations. Returns (alpha
+// high, alpha low, H-error, w) on every lane of the group (j its member
+// index, L its size), w = 1 accepted, 0 not certified, 2 no root (exact
+// h'(0) >= 0: alpha = 2), 3 clipped at the positivity bound. Not inlined: one copy of the code, entered only by
+// warps that hold a site needing it.
+static __device__ __noinline__ float4 alpha_guard(const float *dev, float *Dh, float *Dl, float a, float S,
+                                                  float amax, int j, int L)
 {
     const Grp gp = grp_make(j, L);
-    const float tol = 1e-10f * rho;
-    const ffl A0 = h0_ff(f, d, rho, gp);
-    // the moment series only where it holds (S = max |Delta/f| of the FP32
-    // setup, with margin), chosen for the whole warp
-    const bool use_mom = __all_sync(__activemask(), a * S <= 0.06f);
-    MomFF mom;
-    mom.xmax = 1e30f;
-    if (use_mom) mom_ff(f, d, mom, gp);
-    ffl al = {a, 0.f};
+    SiteFF m;
+    site_ff(dev, m, gp);
 #pragma unroll 1
-    for (int it = 0; it < 3; it++) {
+    for (int p = gp.j; p < Q; p += gp.L) {
+        const ffl D = delta_ff(p, dev[p], m);
+        Dh[p] = D.h;
+        Dl[p] = D.l;
+    }
+    const float rho = m.rho.h;
+    const float tol = 1e-10f * rho;
+    const ffl A0 = h0_ff(dev, Dh, Dl, m, gp);
+    // the exact h'(0) can be >= 0 where the FP32 one was < 0 (both at the
+    // rounding level): no positive root, alpha = 2 as for status 2
+    if (A0.h >= 0.f) return make_float4(2.f, 0.f, 0.f, 2.f);
+    // the exact moments: the series start below, and the series form of h
+    // wherever |a x_p| <= 1/16 (decided per evaluation for the whole warp)
+    MomFF mom;
+    mom_ff(dev, Dh, Dl, mom, gp);
+    const float hi0 = amax * (1.f - 1e-6f);
+    float lo = 0.f, hi = hi0;
+    ffl al = {a, 0.f};
+    if (a * S <= 0.06f) {
+        // root of h'(0) + a M2/2 - a^2 M3/6 + a^3 M4/12 (Newton from -2 h'(0)/M2)
+        const float a0 = A0.h, M2 = mom.M2.h, M3 = mom.M3.h, M4 = mom.Mh[4];
+        float c = -2.f * a0 / M2;
+#pragma unroll 1
+        for (int it = 0; it < 4; it++) {
+            const float gg = a0 + c * (0.5f * M2 + c * (-M3 / 6.f + c * (M4 / 12.f)));
+            const float gd = 0.5f * M2 + c * (-M3 / 3.f + c * (M4 / 4.f));
+            const float cn = c - gg / gd;
+            if (cn > 0.f && cn < hi) c = cn;
+        }
+        if (c > lo && c < hi && fabsf(c - a) > 1e-3f * a) al = ffl{c, 0.f};
+    }
+#pragma unroll 1
+    for (int it = 0; it < 12; it++) {
         ffl hf;
         float hp, hpp;
         if (__all_sync(__activemask(), al.h * mom.xmax <= 0.0625f)) hf = h_mom(al, A0, mom, &hp, &hpp);
-        else h_ff(f, d, al, A0, &hf, &hp, &hpp, gp);
+        else h_ff(dev, Dh, Dl, al, A0, &hf, &hp, &hpp, gp);
         if (fabsf(hf.h) <= 0.5f * tol) return make_float4(al.h, al.l, fabsf(hf.h) / rho, 1.f);
+        if (hf.h < 0.f) lo = fmaxf(lo, al.h); else hi = fminf(hi, al.h);
         const float delta = hf.h / hp;
-        al = ff_add_f(al, -delta);
+        const ffl an = ff_add_f(al, -delta);
+        if (!(an.h >= lo && an.h <= hi)) {  // a step within one FP32 ulp moves only the low part
+            al = ffl{0.5f * (lo + hi), 0.f};  // bisection; no convergence bound from this step
+            continue;
+        }
+        al = an;
         const float pred = 0.75f * fabsf(hpp) * delta * delta + 1e-11f * rho;
         if (pred <= 0.5f * tol) return make_float4(al.h, al.l, pred / rho, 1.f);
     }
+    // the root lies beyond the positivity bound: clipped there, as status 3
+    if (lo >= hi0 * (1.f - 1e-5f)) return make_float4(hi0, 0.f, 0.f, 3.f);
     return make_float4(al.h, al.l, 1e30f, 0.f);
 }
 
 // ---------------------------------------------------------------------------
-// FP32 root. h'(0) = (1 + ln rho) sum D + sum D_p ln(1 + z_p), z_p = f_p/(w_p
-// rho) - 1 (sum D by TwoSum), f_p the FP32 populations. Start from the root of the moment expansion
+// FP32 root. h'(0) = sum D_p ln(1 + z_p), z_p = f_p/(w_p rho) - 1 for the
+// populations f_p = w_p + d_p (the exact Delta sums to zero, so the
+// (1 + ln rho) sum D part of h'(0) vanishes). Start from the root of the moment expansion
 // h(a)/a ~ h'(0) + a M2/2 - a^2 M3/6 + a^3 M4/12 (M_k = sum f x^k), then
 // safeguarded Newton on the exact h (at most 12 steps; one or two near
 // equilibrium). A start a_start > 0 inside the bracket (a learned proposal)
@@ -372,14 +476,29 @@ static __device__ __noinline__ float4 alpha_guard(const float *f, const float *d
 // step is below 1e-6 alpha; converged lanes keep their alpha while the rest of
 // the warp iterates, and the warp leaves together.
 //
-// guard: the target is |h| <= 1e-10 rho (H-error). The FP32 rounding bound of
-// the evaluated h is 2^-21 (sum f phi + a (|h'(0)| + sum |D ln(1+z)|)) +
-// 2^-23 a |h'(a)| (the last term: alpha itself rounded to FP32). Lanes whose
-// |h| + bound stays within half the target are certified as they are; the
-// others take the float-float guard (alpha_guard) from the FP32 root and
-// report its H-error: the float-float |h|, or the quadratic-convergence bound
-// after its Newton step. Without the guard the
-// H-error reported is |h| + bound.
+// guard: the target is |h| <= 1e-10 rho (H-error) for the exact equation of
+// the site's populations f_p = w_p + d_p (FP64 weights), whose Delta differs
+// from the FP32 Delta the root is computed with. The bound on |h_exact - h|
+// at the FP32 root a has four parts:
+//  - the FP32 evaluation of h: 2^-21 (sum f phi + a (|h'(0)| + sum |D ln(1+z)|));
+//  - alpha itself rounded to FP32: 2^-23 a |h'(a)|;
+//  - the rounding of Delta (w drho - d_p is formed exactly): its final
+//    rounding, 2^-24 |Delta_p| (taken as 2^-23; Delta_0 also carries the sum
+//    of the others' through the mass correction), the rounding of w_p rho P_p
+//    (2^-24 w_p rho (36 umax + 144 umax^2)) and the error du of u (through
+//    dP_p/du), each entering h
+//    through dh/dDelta_p = a ln(f'_p / w_p) (the ln rho part cancels: both
+//    Deltas conserve mass) with |ln(f'_p/(w_p rho))| <= |ln(1+z_p)| + a |x_p| F,
+//    F = 1/(1 + a min(x, 0)) (|ln(1+y)| <= |y|/(1 + min(y, 0)));
+//  - the FP32 rounding of f_p = fl(w32_p + d_p) (at most 2^-25 w_p + 2^-24 f_p,
+//    w_p / f_p <= 1.2 / rho) in sum f phi(a x), which moves h by
+//    sum df_p (ln(1+y_p) - y_p), |ln(1+y) - y| <= y^2 F / 2:
+//    2^-24 (1 + 0.6/rho) a^2 F M2.
+// Lanes whose |h| + bound stays within half the target are certified as they
+// are; the others take the float-float guard (alpha_guard), which forms the
+// exact moments and Delta from the deviations, from the FP32 root, and report
+// its H-error: the float-float |h|, or the quadratic-convergence bound after
+// its Newton step. Without the guard the H-error reported is |h| + bound.
 // ---------------------------------------------------------------------------
 struct AlphaSetupF {
     float x[Q];      // Delta_p / f_p
@@ -388,17 +507,24 @@ struct AlphaSetupF {
     float amax;      // positivity bound min over Delta_p < 0 of -f_p/Delta_p
     float ac;        // the moment-series start
     float S;         // max |x_p|
+    float M2;        // sum f x^2
+    float Bz, Bx;    // sum E_p |ln(1+z_p)|, sum E_p |x_p|, E_p = |Delta_p| (+ the sum for p = 0)
+    float Wz, Wx;    // sum w_p |ln(1+z_p)|, sum w_p |x_p|
+    float Bu;        // rho du: the error of u scaled by the density
+    float Uz, Ux;    // 3 |sum w c ln(1+z)|_1 + 46 umax Wz; (6.1 + 46 umax) Wx
+    float Pr;        // 2^-22 rho (10 umax + 40 umax^2): rounding of w_p rho P_p over w_p
+    float xneg;      // min(0, min_p x_p)
     int status;      // 0: solve; 1 near-equilibrium shortcut; 2 no root (h'(0) >= 0)
 };
 
 __device__ __forceinline__ void alpha_fp32_setup(const float *f, const float *d, const float *fdev, float rho,
-                                                 float drho, float eq_tol, AlphaSetupF &st)
+                                                 float drho, float eq_tol, float du, float umax, AlphaSetupF &st)
 {
     float maxabs = 0.f, xneg = 0.f;
-    float s = 0.f, c = 0.f;
     float tl0 = 0.f, tl1 = 0.f, tla = 0.f;
     float M2 = 0.f, M3 = 0.f, M4 = 0.f;
-    const float lr = __logf(rho);
+    float Bz = 0.f, Bx = 0.f, Wz = 0.f, Wx = 0.f, Esum = 0.f, lz0 = 0.f, x0 = 0.f;
+    float Gx = 0.f, Gy = 0.f, Gz = 0.f;  // sum_p w_p c_p ln(1 + z_p)
     const float irho = 1.f / rho;
 #pragma unroll
     for (int p = 0; p < Q; p++) {
@@ -406,38 +532,66 @@ __device__ __forceinline__ void alpha_fp32_setup(const float *f, const float *d,
         st.x[p] = xp;
         maxabs = fmaxf(maxabs, fabsf(xp));
         xneg = fminf(xneg, xp);
-        float t = s + d[p];
-        float bp = t - s;
-        c += (s - (t - bp)) + (d[p] - bp);
-        s = t;
-        // z_p = f_p / (w_p rho) - 1 for the FP32 population f_p = fl(w_p + fdev_p):
-        // f_p = w32_p + fdev_p - e_p (e_p the exact rounding error of that sum,
-        // TwoSum), w32_p - w_p = dw a constant, so f_p - w_p rho =
-        // (fdev_p - w32_p drho) + (dw rho - e_p) is formed from small terms;
-        // the product w32_p drho is split exactly (TwoProd) because fdev_p
-        // and w32_p drho nearly cancel near equilibrium
+        // z_p = f_p / (w_p rho) - 1 for the site's population f_p = w_p + fdev_p
+        // (w_p the exact weight, not its FP32 rounding w32_p = w_p + dw_p, and
+        // not the rounded sum fl(w32_p + fdev_p): at the vapour density that
+        // rounding is a few units of 2^-24 of f_p and would move h'(0) by
+        // sum Delta_p dln_p): f_p - w_p rho = (fdev_p - w32_p drho) + dw_p drho,
+        // formed from small terms; the product w32_p drho is split exactly
+        // (TwoProd) because fdev_p and w32_p drho nearly cancel near equilibrium
         const float w32 = float(wq(p));
-        const float bb = f[p] - w32;
-        const float e = (w32 - (f[p] - bb)) + (fdev[p] - bb);
         const float dw = float(double(w32) - wq(p));
         const float iw = float(1.0 / wq(p));
         const float wd = __fmul_rn(w32, drho);   // not fused into the difference below
         const float wde = fmaf(w32, drho, -wd);  // exact error of the product (TwoProd)
-        const float z = (__fsub_rn(fdev[p], wd) + ((dw * rho - e) - wde)) * iw * irho;
-        const float dl = d[p] * l_f32(z);
+        const float z = (__fsub_rn(fdev[p], wd) + fmaf(dw, drho, -wde)) * iw * irho;
+        const float lz = l_f32(z);
+        const float dl = d[p] * lz;
         if (p & 1) tl1 += dl; else tl0 += dl;
         tla += fabsf(dl);
+        const float Ep = fabsf(d[p]);
+        Bz = fmaf(Ep, fabsf(lz), Bz);
+        Bx = fmaf(Ep, fabsf(xp), Bx);
+        Esum += Ep;
+        if (p == 0) { lz0 = fabsf(lz); x0 = fabsf(xp); }
+        Wz = fmaf(w32, fabsf(lz), Wz);
+        Wx = fmaf(w32, fabsf(xp), Wx);
+        if (cx(p)) Gx = fmaf(float(cx(p)) * w32, lz, Gx);
+        if (cy(p)) Gy = fmaf(float(cy(p)) * w32, lz, Gy);
+        if (cz(p)) Gz = fmaf(float(cz(p)) * w32, lz, Gz);
         const float fx2 = f[p] * xp * xp;
         M2 += fx2;
         M3 += fx2 * xp;
         M4 += fx2 * xp * xp;
     }
-    const float a0 = (1.f + lr) * (s + c) + (tl0 + tl1);
+    // h'(0) of the exact equation: its Delta sums to zero (f^eq has the
+    // density rho), so (1 + ln rho) sum Delta is left out (for the FP32 Delta
+    // that sum is a rounding residual)
+    const float a0 = tl0 + tl1;
     st.a0 = a0;
     st.tla = tla;
     st.S = maxabs;
     st.status = !(maxabs >= eq_tol) ? 1 : (a0 >= 0.f ? 2 : 0);
     st.amax = xneg < 0.f ? -1.f / xneg : 1e30f;
+    st.M2 = M2;
+    st.xneg = xneg;
+    // Delta_0 also takes the compensated sum of the others (mass), hence the
+    // rounding of all of them
+    st.Bz = fmaf(Esum, lz0, Bz);
+    st.Bx = fmaf(Esum, x0, Bx);
+    st.Wz = Wz;
+    st.Wx = Wx;
+    // u enters Delta through w_p rho P_p(u), dP_p/du_a = 3 c_a + 9 (c.u) c_a
+    // - 3 u_a: an error du of each component moves h'(0) = sum Delta_p
+    // ln(1+z_p) by at most rho du (3 |G|_1 + 45 umax Wz), G = sum w c ln(1+z)
+    // (sum w dP = 0: f^eq keeps the density), and sum f phi through x_p by
+    // rho du (6 + 45 umax) sum w |x| a F. The FP32 evaluation of w_p rho P_p
+    // itself rounds by at most 2^-24 w_p rho (36 umax + 144 umax^2).
+    const float usq = umax * umax;
+    st.Bu = rho * du;
+    st.Uz = fmaf(46.f * umax, Wz, 3.f * (fabsf(Gx) + fabsf(Gy) + fabsf(Gz)));
+    st.Ux = fmaf(46.f, umax, 6.1f) * Wx;
+    st.Pr = 0x1p-22f * rho * fmaf(40.f, usq, 10.f * umax);
     // start: root of a0 + a M2/2 - a^2 M3/6 + a^3 M4/12, Newton from -2 a0/M2
     float a = -2.f * a0 / M2;
     for (int it = 0; it < 3; it++) {
@@ -457,7 +611,7 @@ __device__ __forceinline__ void alpha_fp32_setup(const float *f, const float *d,
 // alpha. Converged lanes keep their alpha while the rest of the warp iterates;
 // the warp leaves together. The residual carried to the guard test is the
 // evaluated |h| or, after an accepted step, the predicted h''/2 d^2.
-__device__ __forceinline__ AlphaOutF alpha_fp32_solve(const float *f, const float *d, float rho,
+__device__ __forceinline__ AlphaOutF alpha_fp32_solve(const float *f, const float *d, const float *dev, float rho,
                                                       const AlphaSetupF &st, bool guard, float a_start,
                                                       bool defer_guard = false)
 {
@@ -522,7 +676,11 @@ __device__ __forceinline__ AlphaOutF alpha_fp32_solve(const float *f, const floa
     }
     o.alpha = a;
     o.status = a >= amax * (1.f - 2e-6f) ? 3 : 0;
-    const float bound = 0x1p-21f * (hhl + a * (fabsf(a0) + st.tla)) + 0x1p-23f * a * fabsf(hpl);
+    const float aF = __fdividef(a, fmaxf(fmaf(a, st.xneg, 1.f), 0x1p-10f));
+    const float bound = 0x1p-21f * (hhl + a * (fabsf(a0) + st.tla)) + 0x1p-23f * a * fabsf(hpl) +
+                        a * (0x1p-23f * fmaf(aF, st.Bx, st.Bz) + st.Bu * fmaf(aF, st.Ux, st.Uz) +
+                             st.Pr * fmaf(aF, st.Wx, st.Wz)) +
+                        0x1p-24f * fmaf(0.6f, irho, 1.f) * a * aF * st.M2;
     o.herr = (hres + bound) * irho;
     if (!guard || o.status == 3) return o;
     const float tol = 1e-10f * rho;
@@ -533,22 +691,24 @@ __device__ __forceinline__ AlphaOutF alpha_fp32_solve(const float *f, const floa
     }
     if (need) {
         o.guarded = 1;
-        const float4 gr = alpha_guard(f, d, rho, a, st.S, 0, 1);
+        float Dh[Q], Dl[Q];
+        const float4 gr = alpha_guard(dev, Dh, Dl, a, st.S, st.amax, 0, 1);
         o.alpha = gr.x;
         o.alpha_lo = gr.y;
         o.herr = gr.z;
         if (gr.w == 0.f) { o.status = 4; o.herr = hres * irho; }
+        else if (gr.w >= 2.f) o.status = int(gr.w);  // 2 no root, 3 clipped
     }
     return o;
 }
 
 __device__ __forceinline__ AlphaOutF alpha_fp32(const float *f, const float *d, const float *fdev,
-                                                float rho, float drho, float eq_tol, bool guard,
-                                                float a_start = -1.f)
+                                                float rho, float drho, float eq_tol, float du, float umax,
+                                                bool guard, float a_start = -1.f)
 {
     AlphaSetupF st;
-    alpha_fp32_setup(f, d, fdev, rho, drho, eq_tol, st);
-    return alpha_fp32_solve(f, d, rho, st, guard, a_start);
+    alpha_fp32_setup(f, d, fdev, rho, drho, eq_tol, du, umax, st);
+    return alpha_fp32_solve(f, d, fdev, rho, st, guard, a_start);
 }
 
 }  // namespace elbm

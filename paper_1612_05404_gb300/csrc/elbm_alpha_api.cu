@@ -22,8 +22,8 @@ k_alpha_eval(const float *__restrict__ dev, long long n, float eq_tol_f, double 
 #pragma unroll
     for (int p = 0; p < Q; p++) d[p] = dev[(long long)p * n + i];
     // moments and Eq. (2) in FP32, as the FP32 collision forms them
-    float D[Q], f[Q], drho;
-    const float r = site_delta(d, f, D, &drho);
+    float D[Q], f[Q], drho, du, umax;
+    const float r = site_delta(d, f, D, &drho, &du, &umax);
     if (delta)
         for (int p = 0; p < Q; p++) delta[(long long)p * n + i] = D[p];
     double a;
@@ -41,7 +41,7 @@ k_alpha_eval(const float *__restrict__ dev, long long n, float eq_tol_f, double 
         he = float(ao.herr);
         st = ao.status;
     } else {
-        AlphaOutF ao = alpha_fp32(f, D, d, r, drho, eq_tol_f, AP == ELBM_APREC_FP32);
+        AlphaOutF ao = alpha_fp32(f, D, d, r, drho, eq_tol_f, du, umax, AP == ELBM_APREC_FP32);
         a = double(ao.alpha) + double(ao.alpha_lo);
         he = ao.herr;
         st = (ao.status == 0 && ao.iters > 1) ? 5 : ao.status;
@@ -69,20 +69,20 @@ __global__ void __launch_bounds__(128) k_alpha_eval_learned(const float *__restr
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < n;
-    float d[Q], f[Q], D[Q], drho;
+    float d[Q], f[Q], D[Q], drho, du, umax;
 #pragma unroll
     for (int p = 0; p < Q; p++) d[p] = valid ? dev[(long long)p * n + i] : 0.f;
-    const float r = site_delta(d, f, D, &drho);
+    const float r = site_delta(d, f, D, &drho, &du, &umax);
     if (delta && valid)
         for (int p = 0; p < Q; p++) delta[(long long)p * n + i] = D[p];
     AlphaSetupF st;
-    alpha_fp32_setup(f, D, d, r, drho, eq_tol_f, st);
+    alpha_fp32_setup(f, D, d, r, drho, eq_tol_f, du, umax, st);
     mlp_site_features(st.x, st.S > 0.f ? st.S : 1.f, xs[w] + lane * MLP_XS);
     __syncwarp();
     mlp_warp_bf16(sm, xs[w], os[w]);
     const float am = st.S >= 0x1p-5f ? st.ac + st.S * st.S * st.S * os[w][lane] : st.ac;
     if (!valid) return;
-    AlphaOutF ao = alpha_fp32_solve(f, D, r, st, AP == ELBM_APREC_FP32, am);
+    AlphaOutF ao = alpha_fp32_solve(f, D, d, r, st, AP == ELBM_APREC_FP32, am);
     alpha[i] = double(ao.alpha) + double(ao.alpha_lo);
     if (herr) herr[i] = ao.herr;
     if (status) status[i] = (ao.status == 0 && ao.iters > 1) ? 5 : ao.status;
@@ -99,18 +99,18 @@ __global__ void __launch_bounds__(128) k_alpha_harvest(const float *__restrict__
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float d[Q], f[Q], D[Q], drho;
+    float d[Q], f[Q], D[Q], drho, du, umax;
 #pragma unroll
     for (int p = 0; p < Q; p++) d[p] = dev[(long long)p * n + i];
-    const float r = site_delta(d, f, D, &drho);
+    const float r = site_delta(d, f, D, &drho, &du, &umax);
     AlphaSetupF st;
-    alpha_fp32_setup(f, D, d, r, drho, eq_tol_f, st);
+    alpha_fp32_setup(f, D, d, r, drho, eq_tol_f, du, umax, st);
     const float S = st.S > 0.f ? st.S : 1.f;
     const float iS = 1.f / S;
 #pragma unroll
     for (int p = 0; p < Q; p++) X[(long long)p * n + i] = st.x[p] * iS;
     X[(long long)19 * n + i] = (__log2f(S) + 9.f) * 0.125f;
-    AlphaOutF ao = alpha_fp32_solve(f, D, r, st, true, -1.f);
+    AlphaOutF ao = alpha_fp32_solve(f, D, d, r, st, true, -1.f);
     const bool ok = ao.status == 0 && st.S >= 0x1p-5f;
     const double t = ok ? ((double(ao.alpha) - double(st.ac)) + double(ao.alpha_lo)) / (double(S) * S * S) : 0.0;
     y[i] = float(fmin(8.0, fmax(-8.0, t)));

@@ -865,6 +865,8 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
         }
         // alpha plane: stored alpha, or the network output o per site (learned)
         if (p->store_macro || p->alpha_mode == ELBM_ALPHA_LEARNED) alloc(&b.alpha, (size_t)N * h->sc_bytes);
+        // reduced precision: the low part of a root the float-float guard certified
+        if (p->store_macro && p->precision != ELBM_PREC_FP64) alloc((void **)&b.alpha_lo, (size_t)N * sizeof(float));
         if (p->alpha_mode == ELBM_ALPHA_LEARNED) {
             void *img = nullptr;
             alloc(&img, sizeof(MlpSmem));
@@ -1190,9 +1192,10 @@ elbm_status elbm_fields(elbm_handle *h, unsigned mask, double *out, size_t out_l
     double *tmp = need ? h->xtmp : nullptr;
     elbm_status st = ELBM_OK;
     size_t off = 0;
-    auto plane = [&](const void *src) {
+    auto plane = [&](const void *src, const float *lo = nullptr) {
         if (st != ELBM_OK) return;
         h->ops.export_plane(src, tmp, N, h->s);
+        if (lo) h->ops.add_plane(lo, tmp, N, h->s);
         if (!cuda_ok(cudaMemcpyAsync(out + off, tmp, N * sizeof(double), cudaMemcpyDeviceToHost, h->s)) ||
             !cuda_ok(cudaStreamSynchronize(h->s)))
             st = ELBM_E_CUDA;
@@ -1214,7 +1217,7 @@ elbm_status elbm_fields(elbm_handle *h, unsigned mask, double *out, size_t out_l
     }
     if (mask & ELBM_F_PHI) plane(h->b.phi);
     if (mask & ELBM_F_Q) plane(h->b.q);
-    if (mask & ELBM_F_ALPHA) plane(h->b.alpha);
+    if (mask & ELBM_F_ALPHA) plane(h->b.alpha, h->b.alpha_lo);
     if (mask & ELBM_F_NU) plane(h->b.nu);
     if ((mask & ELBM_F_POP) && st == ELBM_OK) {
         h->ops.export_pop(h->g, h->b, tmp, h->L, h->s);

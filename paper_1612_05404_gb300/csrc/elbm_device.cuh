@@ -153,29 +153,70 @@ __device__ __forceinline__ void delta_dev(const float *d, float drho_hi, float d
         const float w32 = float(wq(p));
         const float dw = float(wq(p) - double(w32));
         const float P = Ppoly<float>(p, ux, uy, uz, usq);
-        D[p] = fmaf(w32, drho_hi, -d[p]) + fmaf(w32, drho_lo, fmaf(dw, drho_hi, w32 * r * P));
+        // w32 drho - d_p exactly, as ah + al + pe (TwoProd of the product,
+        // TwoSum of the difference): the two nearly cancel, and their
+        // rounding would otherwise be the largest error of Delta
+        const float pr = __fmul_rn(w32, drho_hi);
+        const float pe = fmaf(w32, drho_hi, -pr);
+        const float ah = pr - d[p];
+        const float bb = ah - pr;
+        const float al = (pr - (ah - bb)) + (-d[p] - bb);
+        D[p] = ah + ((al + pe) + fmaf(w32, drho_lo, fmaf(dw, drho_hi, w32 * r * P)));
         two_sum_acc(D[p], s, c);
     }
     D[0] -= s + c;
 }
 
-// FP32 moments and Delta of a site from its deviations d (populations
-// f = w + d), as the FP32 collision forms them; returns rho
-__device__ __forceinline__ float site_delta(const float *d, float *f, float *D, float *drho_out)
+// Moments of a site from its FP32 deviations d_p = f_p - w_p: drho = sum d as
+// a compensated pair (rs, rs_lo), and the momentum j = sum_p c_p d_p formed
+// from the differences of opposite populations first. Opposite links are
+// consecutive (p = 2k-1, 2k); within a factor 2 of each other (a site near
+// equilibrium, whatever its density) their difference is exact (Sterbenz
+// 1974), so j carries rounding of the size of its own terms e_k, not of the
+// deviations, which at the vapour density are about -0.84 w_p and cancel in
+// j. esum = sum_k |e_k| bounds the rounding of j: each component's error is
+// at most 2^-21 esum.
+__device__ __forceinline__ void moments_dev(const float *d, float &rs, float &rs_lo, float &jx, float &jy, float &jz,
+                                            float &esum)
 {
-    float rs = 0.f, rs_lo = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+    rs = 0.f;
+    rs_lo = 0.f;
 #pragma unroll
-    for (int p = 0; p < Q; p++) {
-        two_sum_acc(d[p], rs, rs_lo);
-        jx += float(cx(p)) * d[p];
-        jy += float(cy(p)) * d[p];
-        jz += float(cz(p)) * d[p];
-    }
+    for (int p = 0; p < Q; p++) two_sum_acc(d[p], rs, rs_lo);
     {
         const float t = rs + rs_lo;
         rs_lo = rs_lo - (t - rs);
         rs = t;
     }
+    float e[9];
+    esum = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        e[k] = d[2 * k + 1] - d[2 * k + 2];
+        esum += fabsf(e[k]);
+    }
+    // e_0..e_8: +-x, +-y, +-z, (1,1,0), (1,-1,0), (1,0,1), (1,0,-1), (0,1,1), (0,1,-1)
+    jx = ((e[0] + e[3]) + (e[4] + e[5])) + e[6];
+    jy = ((e[1] + e[3]) - (e[4] - e[7])) + e[8];
+    jz = ((e[2] + e[5]) - (e[6] - e[7])) - e[8];
+}
+
+// Bound on the absolute FP32 error of each component of u = j (1/rho): the
+// rounding of j (2^-21 esum) over rho, plus the roundings of 1/rho, of the
+// product and of rho = 1 + drho itself (four units of 2^-24, taken as eight)
+__device__ __forceinline__ float u_err_bound(float esum, float r, float umax)
+{
+    return __fdividef(0x1p-21f * esum, r) + 0x1p-21f * umax;
+}
+
+// FP32 moments and Delta of a site from its deviations d (populations
+// f = w + d), as the FP32 collision forms them; returns rho. du: the bound
+// of u_err_bound, umax = max |u_a|.
+__device__ __forceinline__ float site_delta(const float *d, float *f, float *D, float *drho_out, float *du_out,
+                                            float *umax_out)
+{
+    float rs, rs_lo, jx, jy, jz, esum;
+    moments_dev(d, rs, rs_lo, jx, jy, jz, esum);
     const float r = 1.f + rs;
     const float ir = 1.f / r;
     const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
@@ -184,6 +225,9 @@ __device__ __forceinline__ float site_delta(const float *d, float *f, float *D, 
 #pragma unroll
     for (int p = 0; p < Q; p++) f[p] = float(wq(p)) + d[p];
     *drho_out = rs;
+    const float umax = fmaxf(fabsf(ux), fmaxf(fabsf(uy), fabsf(uz)));
+    *du_out = u_err_bound(esum, r, umax);
+    *umax_out = umax;
     return r;
 }
 

@@ -45,6 +45,7 @@ struct Bufs {
     void *rho, *q, *phi;              // scalar planes
     void *psi, *sig;                  // psi(rho) of the Shan-Chen force; sigma(rho) (transport mode)
     void *ux, *uy, *uz, *alpha, *nu;  // optional macroscopic planes
+    float *alpha_lo;                  // reduced precision: low part of a guarded alpha (with store_macro)
     unsigned char *mask;              // node kinds (NULL when all fluid)
     void *nh;                         // paper-mode charge: 4 planes n_x, n_y, n_z, |grad rho|^2
     void *ab;                         // paper-mode charge: 2 planes a, b
@@ -84,6 +85,8 @@ struct Ops {
     void (*export_pop)(const Geom &, const Bufs &, double *out, const Launch &, cudaStream_t);
     void (*export_gpop)(const Geom &, const Bufs &, double *out, const Launch &, cudaStream_t);
     void (*export_plane)(const void *plane, double *out, long long n, cudaStream_t);
+    // out[i] += lo[i] (the low part of a float-float plane)
+    void (*add_plane)(const float *lo, double *out, long long n, cudaStream_t);
     // the site-wide compute kernels (collision variants, learned-alpha pass):
     // in a batch graph every other kernel runs at a higher priority
     const void *heavy[4];

@@ -664,8 +664,9 @@ __global__ void k_phi_shift(Geom g, Bufs b)
 // thread of the block (the kernel is launched with 128 threads).
 constexpr int kGuardQ = 128;
 struct GuardEntry {
-    float f[Q], d[Q];
-    float rho, a, S;
+    float dev[Q];     // the site's FP32 deviations d_p = f_p - w_p (the exact inputs)
+    float Dh[Q], Dl[Q];  // scratch: the exact Delta as pairs (filled by the guard)
+    float a, S, amax;
     float4 res;
 };
 
@@ -698,7 +699,9 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
     ct f[Q], D[Q];
     ct r = 0, drho = 0, jx = 0, jy = 0, jz = 0, Fx = 0, Fy = 0, Fz = 0, qs = 0;
     ct ir = 0, ux = 0, uy = 0, uz = 0, usq = 0, Rq = 0;
+    float esum = 0.f;  // rounding scale of the FP32 momentum (deviation modes)
     ct alpha = ct(2);
+    float alpha_lo = 0.f;  // low part of a guarded root
     float a_herr = 0.f;
     int a_status = 0, a_guard = 0, a_lfall = 0;
     int gslot = -1;
@@ -708,18 +711,17 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
 #pragma unroll
         for (int p = 0; p < Q; p++) f[p] = gather_pop<PR>(g, b.mask, b.fA, n, p, b.rA);
         ct rs = 0, rs_lo = 0;  // deviations: sum d_p compensated (Delta below)
+        if constexpr (T::dev) {
+            // compensated density, momentum from opposite-link differences
+            moments_dev(f, rs, rs_lo, jx, jy, jz, esum);
+        } else {
 #pragma unroll
-        for (int p = 0; p < Q; p++) {
-            if constexpr (T::dev) two_sum_acc(f[p], rs, rs_lo);
-            else rs += f[p];
-            jx += ct(cx(p)) * f[p];
-            jy += ct(cy(p)) * f[p];
-            jz += ct(cz(p)) * f[p];
-        }
-        if constexpr (T::dev) {  // the pair (rs, rs_lo) normalised
-            const ct t = rs + rs_lo;
-            rs_lo = rs_lo - (t - rs);
-            rs = t;
+            for (int p = 0; p < Q; p++) {
+                rs += f[p];
+                jx += ct(cx(p)) * f[p];
+                jy += ct(cy(p)) * f[p];
+                jz += ct(cz(p)) * f[p];
+            }
         }
         r = T::dev ? ct(1) + rs : rs;
         drho = T::dev ? rs : rs - ct(1);
@@ -806,14 +808,17 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
                     fv[p] = float(f[p]);
                 }
                 AlphaSetupF ast;
-                alpha_fp32_setup(ff, dd, fv, float(r), float(drho), ph.cf.eq_tol, ast);
+                const float umax = fmaxf(fabsf(float(ux)), fmaxf(fabsf(float(uy)), fabsf(float(uz))));
+                alpha_fp32_setup(ff, dd, fv, float(r), float(drho), ph.cf.eq_tol,
+                                 u_err_bound(esum, float(r), umax), umax, ast);
                 // learned proposal: alpha_c + S^3 o, o from the network pass
                 float a_start = -1.f;
                 const bool learned = ph.alpha_mode == ELBM_ALPHA_LEARNED;
                 if (learned && ast.S >= 0x1p-5f)
                     a_start = ast.ac + ast.S * ast.S * ast.S * float(((const sc *)b.alpha)[s]);
-                AlphaOutF ao = alpha_fp32_solve(ff, dd, float(r), ast, AP == ELBM_APREC_FP32, a_start, kQueue);
+                AlphaOutF ao = alpha_fp32_solve(ff, dd, fv, float(r), ast, AP == ELBM_APREC_FP32, a_start, kQueue);
                 alpha = ct(ao.alpha);
+                alpha_lo = ao.alpha_lo;
                 a_herr = ao.herr;
                 a_status = ao.status;
                 a_guard = ao.guarded;
@@ -823,12 +828,9 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
                     gslot = atomicAdd(&gq_n, 1);  // < kGuardQ: one entry per thread
                     GuardEntry &e = gq[gslot];
 #pragma unroll
-                    for (int p = 0; p < Q; p++) {
-                        e.f[p] = ff[p];
-                        e.d[p] = dd[p];
-                    }
-                    e.rho = float(r);
+                    for (int p = 0; p < Q; p++) e.dev[p] = fv[p];
                     e.a = ao.alpha;
+                    e.amax = ast.amax;
                     e.S = ast.S;
                 }
             }
@@ -842,16 +844,18 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
         const int lg = nq <= 16 ? 3 : (nq <= 32 ? 2 : (nq <= 64 ? 1 : 0));
         const int site = tid >> lg, j = tid & ((1 << lg) - 1);
         if (site < nq) {
-            const GuardEntry &e = gq[site];
-            const float4 gr = alpha_guard(e.f, e.d, e.rho, e.a, e.S, j, 1 << lg);
+            GuardEntry &e = gq[site];
+            const float4 gr = alpha_guard(e.dev, e.Dh, e.Dl, e.a, e.S, e.amax, j, 1 << lg);
             if (j == 0) gq[site].res = gr;
         }
         __syncthreads();
         if (gslot >= 0) {
             const float4 gr = gq[gslot].res;
             alpha = ct(gr.x);
-            if (gr.w != 0.f) a_herr = gr.z;
-            else a_status = 4;  // not certified: the FP32 report stays
+            alpha_lo = gr.y;
+            if (gr.w == 0.f) a_status = 4;  // not certified: the FP32 report stays
+            else a_herr = gr.z;
+            if (gr.w >= 2.f) a_status = int(gr.w);  // no root (alpha = 2) / clipped
         }
     }
     if (active) {
@@ -908,6 +912,7 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
             ((sc *)b.uy)[s] = sc(upy);
             ((sc *)b.uz)[s] = sc(upz);
             ((sc *)b.alpha)[s] = sc(alpha);
+            if (b.alpha_lo) b.alpha_lo[s] = alpha_lo;  // the guarded root as a pair
             ((sc *)b.nu)[s] = sc(nu);
         }
         if (diag) {
@@ -1019,19 +1024,8 @@ __global__ void __launch_bounds__(128) k_alpha_mlp(Geom g, Phys ph, Bufs b)
         float f[Q];
 #pragma unroll
         for (int p = 0; p < Q; p++) f[p] = float(gather_pop<PR>(g, b.mask, b.fA, n, p, b.rA));
-        float rs = 0.f, rs_lo = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-        for (int p = 0; p < Q; p++) {
-            two_sum_acc(f[p], rs, rs_lo);
-            jx += float(cx(p)) * f[p];
-            jy += float(cy(p)) * f[p];
-            jz += float(cz(p)) * f[p];
-        }
-        {
-            const float t = rs + rs_lo;
-            rs_lo = rs_lo - (t - rs);
-            rs = t;
-        }
+        float rs, rs_lo, jx, jy, jz, esum;
+        moments_dev(f, rs, rs_lo, jx, jy, jz, esum);
         const float r = 1.f + rs;
         const float ir = 1.f / r;
         const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
@@ -1121,6 +1115,13 @@ __global__ void k_to_double(const S *in, double *out, ll n)
     if (i < n) out[i] = double(in[i]);
 }
 
+template <typename S>
+__global__ void k_add_lo(const S *lo, double *out, ll n)
+{
+    ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x;
+    if (i < n) out[i] += double(lo[i]);
+}
+
 // ---------------------------------------------------------------------------
 // Host launchers for one precision.
 // ---------------------------------------------------------------------------
@@ -1188,9 +1189,14 @@ struct Launchers {
     {
         k_to_double<sc><<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const sc *)plane, out, n);
     }
+    static void add_plane(const float *lo, double *out, ll n, cudaStream_t s)
+    {
+        k_add_lo<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(lo, out, n);
+    }
     static Ops table()
     {
         Ops o;
+        o.add_plane = add_plane;
         o.init_pop = init_pop;
         o.moments = moments;
         o.charge = charge;

@@ -234,10 +234,10 @@ __global__ void __launch_bounds__(128) k_alpha_features(const float *__restrict_
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float d[Q], f[Q], D[Q], drho;
+    float d[Q], f[Q], D[Q], drho, du, umax;
 #pragma unroll
     for (int p = 0; p < Q; p++) d[p] = dev[(long long)p * n + i];
-    site_delta(d, f, D, &drho);
+    site_delta(d, f, D, &drho, &du, &umax);
     float S = 0.f;
 #pragma unroll
     for (int p = 0; p < Q; p++) S = fmaxf(S, fabsf(D[p] / f[p]));

@@ -30,6 +30,9 @@ static __device__ __align__(256) double g_noalloc_scratch[ELBM_NOALLOC_MAX_BLOCK
 // g_noalloc_scratch is only a host-side stand-in: passing it to a kernel
 // would fault or silently touch the wrong memory, so the address is looked
 // up with cudaGetSymbolAddress, once per device, with that device current.
+// The cached address belongs to the device's primary context: it stays valid
+// as long as that context does (a cudaDeviceReset ends it; do not call this
+// entry point after one in the same process).
 constexpr int kMaxDevices = 64;
 double *g_scratch_ptr[kMaxDevices];
 std::mutex g_setup_mutex;
@@ -97,6 +100,9 @@ extern "C" elbm_status elbm_density_noalloc(const double *f, const unsigned char
     }
     const int nblocks = (int)((n_sites + kSitesPerBlock - 1) / kSitesPerBlock);
     cudaStream_t s = (cudaStream_t)stream;
+    // an error left pending by earlier, unrelated work on this thread is not
+    // this call's failure: clear it so the check below sees only these launches
+    (void)cudaGetLastError();
     k_density_noalloc<<<nblocks, kThreads, 0, s>>>(f, mask, n_sites, rho, scratch);
     k_mass_noalloc<<<1, kThreads, 0, s>>>(scratch, nblocks, mass);
     return cudaGetLastError() == cudaSuccess ? ELBM_OK : ELBM_E_CUDA;

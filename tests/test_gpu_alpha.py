@@ -1,8 +1,9 @@
 """The entropic alpha root on the GPU (elbm_alpha_eval) against the FP64 oracle.
 
 H-error := |h(alpha)| / rho with h(a) = H(f + a Delta) - H(f) of Eq. (entropic),
-evaluated by the oracle in FP64 on exactly the FP32 populations and Delta the
-GPU used. Target (reduced precision with the float-float guard): <= 1e-10.
+evaluated by the oracle in FP64 for the site's populations f = w + d (FP64
+weights, the FP32 deviations the kernel read) and their exact Delta = f^eq - f.
+Target (reduced precision with the float-float guard): <= 1e-10.
 """
 import numpy as np
 import pytest
@@ -34,7 +35,21 @@ def _run(f64, aprec):
     a, he, st, delta = elbm.alpha_eval(d, aprec=aprec, eq_tol=1e-5, with_delta=True)
     torch.cuda.synchronize()
     f32 = (W32[:, None] + d32).astype(np.float64)  # the FP32 populations the kernel used
-    return f32, delta.cpu().numpy().astype(np.float64), a.cpu().numpy(), he.cpu().numpy(), st.cpu().numpy()
+    return f32, delta.cpu().numpy().astype(np.float64), a.cpu().numpy(), he.cpu().numpy(), st.cpu().numpy(), d32
+
+
+def _exact(d32):
+    """The site's populations f = w + d (FP64 weights, the FP32 deviations the
+    kernel read) and the exact Delta = f^eq(rho, u) - f of Eq. (2) from the
+    oracle, u = sum f c / rho."""
+    f = W.D3Q19_WEIGHTS[:, None] + d32.astype(np.float64)
+    c, _, _ = oracle.lattice(3)
+    rho = f.sum(0)
+    u = (c.T.astype(np.float64) @ f) / rho
+    D = np.empty_like(f)
+    for i in range(f.shape[1]):
+        D[:, i] = oracle.feq(3, rho[i], u[:, i]) - f[:, i]
+    return f, D
 
 
 def _h_err(f, D, a):
@@ -42,7 +57,10 @@ def _h_err(f, D, a):
 
 
 def test_alpha_fp32_guard_meets_h_error():
-    f, D, a, he, st = _run(_sites(), "fp32")
+    """The guarded FP32 root solves the exact equation of the site's
+    populations (not only the FP32 Delta it iterates on) to 1e-10 rho."""
+    f32, D32, a, he, st, d32 = _run(_sites(), "fp32")
+    f, D = _exact(d32)
     assert not np.any(st == 4), "guard ended above 1e-10 rho"
     root = np.isin(st, (0, 5))  # 5: a root that took more than one FP32 evaluation
     assert root.sum() > 1000
@@ -51,7 +69,7 @@ def test_alpha_fp32_guard_meets_h_error():
     assert err.max() <= 1e-10, err.max()
     # the reported H-error is the evaluated one (guard) or an upper bound
     assert np.all(he[root] <= 1e-10)
-    # the same root as the oracle's FP64 Newton on the same inputs
+    # the same root as the oracle's FP64 Newton on the same populations
     for i in np.flatnonzero(root)[::37]:
         ar, sr = oracle.alpha(3, f[:, i], D[:, i], 1e-5)
         assert sr == 0
@@ -60,18 +78,55 @@ def test_alpha_fp32_guard_meets_h_error():
 
 
 def test_alpha_fp32_fast_bound_holds():
-    f, D, a, he, st = _run(_sites(), "fp32_fast")
+    f32, D32, a, he, st, d32 = _run(_sites(), "fp32_fast")
+    f, D = _exact(d32)
     root = np.isin(st, (0, 5))
     err = _h_err(f[:, root], D[:, root], a[root])
-    # without the guard the reported value is |h| plus the FP32 rounding bound
+    # without the guard the reported value is |h| plus a bound of every
+    # rounding between the FP32 root and the exact equation
     assert np.all(err <= he[root] * 1.0001 + 1e-15)
 
 
 def test_alpha_fp64_root():
-    f, D, a, he, st = _run(_sites(), "fp64")
+    # FP64 Newton on the FP32 populations and Delta the kernel formed
+    f, D, a, he, st, _ = _run(_sites(), "fp64")
     root = st == 0
     err = _h_err(f[:, root], D[:, root], a[root])
     assert err.max() <= 1e-13, err.max()
+
+
+def _flowing_sites(n=3072, seed=9):
+    """Sites moving at |u| up to 0.1 (the jet's liquid column), a relative
+    1e-5 .. 3e-2 from the equilibrium of their own density and velocity: the
+    FP32 rounding of u alone (2^-24 |u|) moves h'(0) by about 3 rho |u| du,
+    above 1e-10 rho once |u| > 0.02."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((19, n))
+    for i in range(n):
+        rho = (0.16, 1.0, 2.0)[i % 3]
+        u = rng.normal(size=3)
+        u *= rng.uniform(0.0, 0.1) / np.linalg.norm(u)
+        eps = 10.0 ** rng.uniform(-5, -1.5)
+        eta = rng.normal(size=19)
+        eta -= eta.mean()
+        out[:, i] = oracle.feq(3, rho, u) * (1.0 + eps * eta)
+    return out
+
+
+@pytest.mark.parametrize("aprec", ["fp32", "fp32_fast"])
+def test_alpha_flowing_sites_exact_equation(aprec):
+    f32, D32, a, he, st, d32 = _run(_flowing_sites(), aprec)
+    f, D = _exact(d32)
+    root = np.isin(st, (0, 5))
+    assert root.sum() > 2500
+    err = _h_err(f[:, root], D[:, root], a[root])
+    if aprec == "fp32":
+        assert not np.any(st == 4)
+        assert err.max() <= 1e-10, err.max()
+        assert np.all(he[root] <= 1e-10)
+    else:
+        # the reported value bounds the error against the exact equation
+        assert np.all(err <= he[root] * 1.0001 + 1e-15), err.max()
 
 
 def _near_equilibrium_sites(n=4096, seed=5):
@@ -94,7 +149,8 @@ def _near_equilibrium_sites(n=4096, seed=5):
 
 @pytest.mark.parametrize("aprec", ["fp32", "fp32_fast"])
 def test_alpha_near_equilibrium_newton_step_below_resolution(aprec):
-    f, D, a, he, st = _run(_near_equilibrium_sites(), aprec)
+    f32, D32, a, he, st, d32 = _run(_near_equilibrium_sites(), aprec)
+    f, D = _exact(d32)
     root = np.isin(st, (0, 5))
     assert root.sum() > 3000
     # one FP32 evaluation suffices: the start is the root at this precision
