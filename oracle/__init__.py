@@ -77,7 +77,7 @@ def build(force: bool = False) -> str:
         os.makedirs(_BUILD, exist_ok=True)
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-               "-fno-fast-math", "-Wall", "-o", tmp, _SRC, "-lm"]
+               "-fno-fast-math", "-fopenmp", "-Wall", "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True, capture_output=True, text=True)
         os.replace(tmp, _LIB_PATH)
         return _LIB_PATH
@@ -118,6 +118,8 @@ def lib():
         L.orc_init.argtypes = [pp, u8p, dp, dp, dp, dp, dp, dp, dp]
         L.orc_apply_io.argtypes = [pp, u8p, dp, dp]
         L.orc_step.argtypes = [pp, u8p, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
+        L.orc_set_threads.argtypes = [ctypes.c_int]
+        L.orc_set_threads.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -163,6 +165,13 @@ def make_params(cfg: dict) -> Params:
     P.alpha_eq_tol = cfg["alpha_eq_tol"]
     P.rho_in, P.rho_out = cfg["rho_in"], cfg["rho_out"]
     return P
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's site-parallel loops (n <= 0 keeps the
+    current setting); returns the number in use. Results do not depend on
+    it: every global sum is taken serially in site order."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def Q_of(dim: int) -> int:

@@ -15,7 +15,27 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include "elbm_oracle.h"
+
+/* ------------------------------------------------------------------------
+ * Threads. Loops whose sites are independent (each iteration writes only its
+ * own site's outputs) run in parallel over sites when compiled with OpenMP;
+ * every global sum is taken serially in site order afterwards, so the
+ * results are bit for bit those of one thread.
+ * ---------------------------------------------------------------------- */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------
  * Velocity sets. D2Q9 (Sec. II, Eq. 2 and the text after it): rest weight
@@ -380,6 +400,7 @@ void orc_sc_force(const orc_params *p, const unsigned char *mask,
 {
     ctx_t C;
     ctx_init(&C, p);
+#pragma omp parallel for schedule(static)
     for (long s = 0; s < C.N; s++) {
         F[3 * s] = F[3 * s + 1] = F[3 * s + 2] = 0.0;
         if (mask[s] != ORC_FLUID) continue;
@@ -417,9 +438,10 @@ void orc_charge_field(const orc_params *p, const unsigned char *mask,
     double *nh = calloc(3 * C.N, sizeof(double));
     double *a = calloc(C.N, sizeof(double));
     double *b = calloc(C.N, sizeof(double));
-    int x, y, z, face;
+#pragma omp parallel for schedule(static)
     for (long s = 0; s < C.N; s++) {
         if (mask[s] == ORC_SOLID) continue;
+        int x, y, z, face;
         coords(&C, s, &x, &y, &z);
         for (int qq = 1; qq < C.Q; qq++) {
             long nb = nbr(&C, x, y, z, C.c[qq][0], C.c[qq][1], C.c[qq][2], &face);
@@ -432,10 +454,11 @@ void orc_charge_field(const orc_params *p, const unsigned char *mask,
         if (gn < 1e-12) gn = 1e-12;
         for (int k = 0; k < 3; k++) nh[3 * s + k] = grad[3 * s + k] / gn;
     }
-    double Sa = 0.0, Sb = 0.0;
+#pragma omp parallel for schedule(static)
     for (long s = 0; s < C.N; s++) {
         if (K) K[s] = 0.0;
         if (mask[s] != ORC_FLUID) continue;
+        int x, y, z, face;
         coords(&C, s, &x, &y, &z);
         double div = 0.0;
         for (int qq = 1; qq < C.Q; qq++) {
@@ -450,9 +473,14 @@ void orc_charge_field(const orc_params *p, const unsigned char *mask,
         double kp = Kc > 0.0 ? Kc : 0.0;
         a[s] = rho[s] * theta_of(p, rho[s]);
         b[s] = g2 * (1.0 + pow(kp / p->K_d, 0.25));
+    }
+    double Sa = 0.0, Sb = 0.0;
+    for (long s = 0; s < C.N; s++) {
+        if (mask[s] != ORC_FLUID) continue;
         Sa += a[s];
         Sb += b[s];
     }
+#pragma omp parallel for schedule(static)
     for (long s = 0; s < C.N; s++) {
         q[s] = 0.0;
         if (mask[s] != ORC_FLUID) continue;
@@ -516,7 +544,8 @@ static void pois_residual(const ctx_t *C, const unsigned char *mask, const doubl
                           const double *qn, double qmean, const double *phi, double *rn,
                           double *ref)
 {
-    double r2 = 0.0, q2 = 0.0, b2 = 0.0;
+    double *t3 = calloc(3 * C->N, sizeof(double));  /* per site r^2, q^2, b^2 */
+#pragma omp parallel for schedule(static)
     for (long s = 0; s < C->N; s++) {
         if (mask[s] == ORC_SOLID) continue;
         int x, y, z;
@@ -530,10 +559,18 @@ static void pois_residual(const ctx_t *C, const unsigned char *mask, const doubl
                 if (k == PN_UNKNOWN) r += 0.5 * (eps[s] + eps[nb]) * (phi[nb] - phi[s]);
                 else if (k == PN_DIRICHLET) { r += eps[s] * (v - phi[s]); bs += eps[s] * v; }
             }
-        r2 += r * r;
-        if (mask[s] == ORC_FLUID) q2 += (qn[s] + qmean) * (qn[s] + qmean);
-        b2 += bs * bs;
+        t3[3 * s] = r * r;
+        if (mask[s] == ORC_FLUID) t3[3 * s + 1] = (qn[s] + qmean) * (qn[s] + qmean);
+        t3[3 * s + 2] = bs * bs;
     }
+    double r2 = 0.0, q2 = 0.0, b2 = 0.0;
+    for (long s = 0; s < C->N; s++) {
+        if (mask[s] == ORC_SOLID) continue;
+        r2 += t3[3 * s];
+        if (mask[s] == ORC_FLUID) q2 += t3[3 * s + 1];
+        b2 += t3[3 * s + 2];
+    }
+    free(t3);
     *rn = sqrt(r2);
     *ref = sqrt(q2) + sqrt(b2);
 }
@@ -552,6 +589,7 @@ int orc_poisson_solve(const orc_params *p, const unsigned char *mask, const doub
     ctx_t C;
     ctx_init(&C, p);
     double *eps = malloc(C.N * sizeof(double));
+#pragma omp parallel for schedule(static)
     for (long s = 0; s < C.N; s++) eps[s] = eps_of(p, rho[s]);
     double w = p->sor_omega, rn = 0.0, ref = 0.0;
     int k = 0;
@@ -562,7 +600,9 @@ int orc_poisson_solve(const orc_params *p, const unsigned char *mask, const doub
             pois_residual(&C, mask, eps, qn, qmean, phi, &rn, &ref);
             if (rn <= p->poisson_tol * ref || k >= p->poisson_maxit) break;
         }
+        /* the sites of one colour read only the other colour */
         for (int color = 0; color < 2; color++)
+#pragma omp parallel for schedule(static)
             for (long s = 0; s < C.N; s++) {
                 int x, y, z;
                 coords(&C, s, &x, &y, &z);
@@ -649,6 +689,7 @@ void orc_efield(const orc_params *p, const unsigned char *mask, const double *ph
 {
     ctx_t C;
     ctx_init(&C, p);
+#pragma omp parallel for schedule(static)
     for (long s = 0; s < C.N; s++) {
         E[3 * s] = E[3 * s + 1] = E[3 * s + 2] = 0.0;
         if (mask[s] != ORC_FLUID) continue;
@@ -711,6 +752,7 @@ void orc_apply_io(const orc_params *p, const unsigned char *mask, const double *
 {
     ctx_t C;
     ctx_init(&C, p);
+#pragma omp parallel for schedule(static)
     for (long s = 0; s < C.N; s++) {
         if (mask[s] != ORC_FLUID) continue;
         int x, y, z, face;
@@ -734,8 +776,9 @@ int orc_init(const orc_params *p, const unsigned char *mask, const double *rho0_
     if (validate(p)) return -1;
     ctx_t C;
     ctx_init(&C, p);
-    double feq[19];
+#pragma omp parallel for schedule(static)
     for (long s = 0; s < C.N; s++) {
+        double feq[19];
         double u[3] = {0, 0, 0};
         if (u0_field) { u[0] = u0_field[3 * s]; u[1] = u0_field[3 * s + 1]; u[2] = u0_field[3 * s + 2]; }
         if (mask[s] == ORC_FLUID) {
@@ -776,6 +819,10 @@ void orc_stream(const orc_params *p, const unsigned char *mask, const double *u_
     int Q = C.Q;
     double *fn = calloc((size_t)Q * N, sizeof(double));
     double *gn = gs ? calloc(7 * N, sizeof(double)) : NULL;
+    /* each destination (population, site) is written by one source site:
+     * streaming is a permutation, bounce-back writes the site's own entry,
+     * and inlet / outlet nodes do not push */
+#pragma omp parallel for schedule(static)
     for (long s = 0; s < N; s++) {
         if (mask[s] != ORC_FLUID) continue;
         int x, y, z, face;
@@ -844,11 +891,13 @@ int orc_step(const orc_params *p, const unsigned char *mask, const double *u_in,
 
     /* moments: rho = sum f, rho u = sum f c */
     long nfluid = 0;
+    for (long s = 0; s < N; s++)
+        if (mask[s] == ORC_FLUID) nfluid++;
+#pragma omp parallel for schedule(static)
     for (long s = 0; s < N; s++) {
         rho[s] = 0.0;
         q[s] = 0.0;
         if (mask[s] == ORC_FLUID) {
-            nfluid++;
             for (int k = 0; k < Q; k++) {
                 double fk = f[k * N + s];
                 rho[s] += fk;
@@ -860,6 +909,7 @@ int orc_step(const orc_params *p, const unsigned char *mask, const double *u_in,
 
     /* free charge */
     if (p->charge_model == ORC_CHARGE_TRANSPORT) {
+#pragma omp parallel for schedule(static)
         for (long s = 0; s < N; s++)
             if (mask[s] == ORC_FLUID)
                 for (int i = 0; i < 7; i++) q[s] += g[i * N + s];
@@ -885,9 +935,15 @@ int orc_step(const orc_params *p, const unsigned char *mask, const double *u_in,
         for (long s = 0; s < N; s++)
             E2[s] = E[3 * s] * E[3 * s] + E[3 * s + 1] * E[3 * s + 1] + E[3 * s + 2] * E[3 * s + 2];
 
+    /* per-site records of the collision, summed serially below: alpha
+     * status, H-error, |u|, H(f), body force */
+    int *ast = calloc(N, sizeof(int));
+    double *aherr = calloc(N, sizeof(double));
+    double *umag = calloc(N, sizeof(double));
+    double *Hs = calloc(N, sizeof(double));
+    double *Fs = calloc(3 * N, sizeof(double));
     double tau_q = 0.5 + p->Dq / CS2_Q;
-    double asum = 0.0;
-    long nroot = 0;
+#pragma omp parallel for schedule(static)
     for (long s = 0; s < N; s++) {
         alpha_out[s] = 0.0;
         nu_out[s] = 0.0;
@@ -922,14 +978,9 @@ int orc_step(const orc_params *p, const unsigned char *mask, const double *u_in,
         double alpha = 2.0;
         int st = ORC_A_ROOT;
         if (p->alpha_mode == ORC_ALPHA_ENTROPIC) st = orc_alpha(p->dim, fl, d, p->alpha_eq_tol, &alpha);
-        if (st == ORC_A_SHORTCUT) diag[8] += 1;
-        else if (st == ORC_A_NOROOT) diag[9] += 1;
-        else if (st == ORC_A_CLIPPED) diag[10] += 1;
-        if (st == ORC_A_ROOT && p->alpha_mode == ORC_ALPHA_ENTROPIC) {
-            double he = fabs(orc_h(p->dim, fl, d, alpha)) / r;
-            if (he > diag[13]) diag[13] = he;
-            nroot++;
-        }
+        ast[s] = st;
+        if (st == ORC_A_ROOT && p->alpha_mode == ORC_ALPHA_ENTROPIC)
+            aherr[s] = fabs(orc_h(p->dim, fl, d, alpha)) / r;
 
         /* Eq. (stress): Pi = sum (f - feq) c c */
         double Pi[9] = {0};
@@ -966,22 +1017,35 @@ int orc_step(const orc_params *p, const unsigned char *mask, const double *u_in,
             }
         }
 
-        diag[0] += r;
-        for (int a = 0; a < 3; a++) diag[1 + a] += j[3 * s + a] + 0.5 * F[a];
+        umag[s] = sqrt(up[0] * up[0] + up[1] * up[1] + up[2] * up[2]);
+        Hs[s] = orc_H(p->dim, fl);
+        for (int a = 0; a < 3; a++) Fs[3 * s + a] = F[a];
+    }
+    /* diagnostics: sums in site order */
+    double asum = 0.0;
+    for (long s = 0; s < N; s++) {
+        if (mask[s] != ORC_FLUID) continue;
+        int st = ast[s];
+        if (st == ORC_A_SHORTCUT) diag[8] += 1;
+        else if (st == ORC_A_NOROOT) diag[9] += 1;
+        else if (st == ORC_A_CLIPPED) diag[10] += 1;
+        if (aherr[s] > diag[13]) diag[13] = aherr[s];
+        double alpha = alpha_out[s];
+        diag[0] += rho[s];
+        for (int a = 0; a < 3; a++) diag[1 + a] += j[3 * s + a] + 0.5 * Fs[3 * s + a];
         diag[4] += q[s];
         if (alpha < diag[5]) diag[5] = alpha;
         if (alpha > diag[6]) diag[6] = alpha;
         asum += alpha;
-        double um = sqrt(up[0] * up[0] + up[1] * up[1] + up[2] * up[2]);
-        if (um > diag[14]) diag[14] = um;
-        diag[15] += orc_H(p->dim, fl);
-        for (int a = 0; a < 3; a++) diag[17 + a] += F[a];
+        if (umag[s] > diag[14]) diag[14] = umag[s];
+        diag[15] += Hs[s];
+        for (int a = 0; a < 3; a++) diag[17 + a] += Fs[3 * s + a];
     }
     diag[7] = nfluid ? asum / (double)nfluid : 0.0;
     diag[11] = iters;
     diag[12] = resid;
     diag[16] = qmean;
-    (void)nroot;
+    free(ast); free(aherr); free(umag); free(Hs); free(Fs);
 
     orc_stream(p, mask, u_in, rho, fs, gs, f, g);
 

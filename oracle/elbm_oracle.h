@@ -66,6 +66,10 @@ typedef struct orc_params {
 /* number of diagnostics written by orc_step */
 #define ORC_NDIAG 20
 
+/* threads of the site-parallel loops (OpenMP; n <= 0 keeps the setting);
+ * returns the number in use. Results are the same for any number. */
+int orc_set_threads(int n);
+
 /* ---------------- per-site building blocks ---------------- */
 int    orc_Q(int dim);
 void   orc_lattice(int dim, int *c /* Q*3 */, double *w /* Q */, double *cs2);
