@@ -1,27 +1,33 @@
 #!/usr/bin/env python
 """Throughput of the charged entropic lattice Boltzmann step on GB300.
 
-Metric: lattice-site updates per second (MLUPS) of the whole step, and the
-HBM roofline fraction of the fused collision kernel.
+Metric: lattice-site updates per second (MLUPS) of the whole step, the HBM
+roofline fraction of its dominant kernel, and the learned alpha proposal
+against the Newton root at the same H-error bound.
 
-Workload "drop64" (default): the leaky-dielectric drop between electrodes,
-four independent 64^3 D3Q19 lattices, one per applied field
-E0 = 1e-4, 4e-4, 7e-4, 1e-3 along z; drop radius 12, liquid / vapour
-densities 2.0 / 0.16 (G = -5), Carreau n = 0.6, lambda = 10, transported
-free charge (eps ratio 2, sigma ratio 10), populations stored as FP32
-deviations with FP32 arithmetic. One bench step = one time step of each of
-the four lattices. The 256 MiB L2 flush between timed steps is outside the
-timed region; the four lattices together (about 190 MB of state) also exceed
-the 129 MB L2.
+Workload "jet4" (default): the electrified jet at 256 x 256 x 768 D3Q19
+sites (50.3 M): a nozzle of radius 8 injects Carreau liquid (n = 0.5,
+lambda = 20) at 0.02 along z into vapour, E0 = 5e-4 along z, xi-form free
+charge, multigrid potential with the nozzle as a conductor; populations
+stored in BF16 relative to the site density with FP32 arithmetic; entropic
+alpha by the learned proposal (a 20-64-64-1 network trained here, on the
+GPU, on (f, alpha) pairs harvested from the drop-in-field and 128 x 128 x
+512 jet runs) followed by the FP32 Newton iteration and the float-float
+guard, certified to |h(alpha)|/rho <= 1e-10 against the exact equation.
+Every timed step computes its diagnostics (mass, momentum, charge, alpha
+statistics, H-error maximum, non-finite count) and checks its status. The
+lattice state (8.4 GB) exceeds the 129 MB L2, so no flush is needed.
 
-Runs on N GPUs as N independent replicas (weak scaling): each rank steps
-its own four lattices, no data-path collective.
+Runs on N GPUs as N independent replicas (weak scaling): each rank steps its
+own lattice, no data-path collective; rank 0 also runs the secondary
+measurements when N = 1.
 """
 from __future__ import annotations
 
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -33,6 +39,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ELBM MLUPS & frac of 8 TB/s HBM; learned-α vs Newton-α at equal H-error"
 NOMINAL_HBM_GBS = 8000.0
+JET4_SHAPE = (256, 256, 768)
+JET3_SHAPE = (128, 128, 512)
+SAMPLE_SHAPE = (48, 48, 128)  # the oracle's sample of the jet physics (multi-core baseline)
+SAMPLE1_SHAPE = (32, 32, 96)  # the same, single thread; also the reference arm's sample
 
 
 def parse():
@@ -41,27 +51,17 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="drop64", choices=["drop64"])
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
-    ap.add_argument("--alpha-precision", default="fp32", choices=["fp64", "fp32", "fp32_fast"])
-    ap.add_argument("--alpha-mode", default="entropic", choices=["entropic", "bgk"],
-                    help="bgk: alpha = 2 (the method without its entropic step; for cost attribution)")
-    ap.add_argument("--instances", type=int, default=4, help="lattices per step (E0 sweep values)")
-    ap.add_argument("--no-graph", action="store_true", help="issue each step from the host (profilers see every launch)")
-    ap.add_argument("--launch", default="batch", choices=["batch", "streams"],
-                    help="batch: all lattices in one graph per step; streams: one graph per lattice per stream")
-    ap.add_argument("--span", type=int, default=0,
-                    help="batch: steps per graph launch (ELBM_BATCH_SPAN, 1..16); timed launches cover that "
-                         "many steps; 0: the span that covers --steps in the fewest launches")
-    ap.add_argument("--pipeline", default="on", choices=["on", "off"],
-                    help="batch: odd-position lattices run half a step ahead (ELBM_BATCH_PIPELINE)")
+    ap.add_argument("--alpha-mode", default="learned", choices=["learned", "entropic"],
+                    help="headline alpha: learned proposal + guarded Newton, or guarded Newton alone")
+    ap.add_argument("--train-steps", type=int, default=4000, help="Adam steps of the proposal's training")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-alpha-compare", action="store_true",
-                    help="skip the learned-alpha vs Newton-alpha comparison")
-    ap.add_argument("--boxes", type=int, default=512,
-                    help="batched-droplets comparison: number of boxes (0 skips it)")
-    ap.add_argument("--no-jet", action="store_true", help="skip the electrified-jet measurement")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the secondary measurements (alpha comparison, drop, batch, jet 128)")
+    ap.add_argument("--boxes", type=int, default=512, help="batched-droplets comparison: boxes (0 skips it)")
+    ap.add_argument("--span", type=int, default=0,
+                    help="drop-in-field batch: steps per graph launch besides span 1 (0: the span that "
+                         "covers --steps in the fewest launches)")
     return ap.parse_args()
 
 
@@ -101,30 +101,26 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def workload_cfgs(args):
-    from paper_1612_05404_gb300 import workloads as W
-    out = []
-    for E0 in W.E0_SWEEP[len(W.E0_SWEEP) - args.instances:]:
-        cfg, fields = W.drop_in_field(E0=E0, precision=args.precision)
-        cfg.update(alpha_precision=args.alpha_precision, alpha_mode=args.alpha_mode, store_macro=0, diag_every=1,
-                   poisson_check_every=8, graph=0 if args.no_graph else 1)
-        out.append((cfg, fields))
-    return out
-
-
-def cpu_sample(steps=3):
-    """The oracle, as it stands, on a 32^3 lattice of the same physics
-    (E0 = 1e-3, drop radius 6): one untimed step (cold potential), then
-    `steps` timed steps, single-threaded."""
-    import oracle
-    from paper_1612_05404_gb300 import workloads as W
-    cfg, fields = W.drop_in_field(E0=1e-3, n=32, radius=6.0, precision="fp32")
-    sim = oracle.Sim(cfg, fields)
-    sim.step(1)
-    t0 = time.perf_counter()
-    sim.step(steps)
-    dt = time.perf_counter() - t0
-    return 32 ** 3 * steps / dt / 1e6, dt, f"oracle FP64, 32^3 drop-in-field (E0=1e-3), {steps} steps after 1 untimed"
+def host_cpu():
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    try:
+        lscpu = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in lscpu.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"model": model, "nproc": os.cpu_count(), "machine": platform.machine()}
 
 
 class ClockSampler:
@@ -182,268 +178,104 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def run_reference(args, rank):
-    if rank != 0:
-        return None
-    import oracle
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+_FIELDS = {}
+
+
+def jet_case(shape, alpha_mode="learned", aprec="fp32", theta=None, **extra):
+    """Config dict and (cached) initial fields of the jet at `shape`: BF16
+    storage relative to the site density, FP32 arithmetic, multigrid with
+    the nozzle as a conductor, graphs with per-step diagnostics."""
     from paper_1612_05404_gb300 import workloads as W
-    cfg, fields = W.drop_in_field(E0=1e-3, n=32, radius=6.0, precision="fp32")
-    sim = oracle.Sim(cfg, fields)
-    sim.step(max(args.warmup, 1))
-    t0 = time.perf_counter()
-    sim.step(args.steps)
-    dt = time.perf_counter() - t0
-    v = 32 ** 3 * args.steps / dt / 1e6
-    return {
-        "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": "drop-in-field, sample: one 32^3 lattice (E0=1e-3) of the 64^3 x4 bench workload",
-                   "oracle": "plain FP64 C, single thread"},
-        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                         "sample": f"32^3 lattice, {args.steps} steps after {max(args.warmup, 1)} untimed"},
-        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
+    key = tuple(shape)
+    if key not in _FIELDS:
+        _FIELDS[key] = W.jet(shape=shape, precision="bf16")
+    cfg, fields = _FIELDS[key]
+    cfg = dict(cfg, alpha_precision=aprec, alpha_mode=alpha_mode, poisson_solver="mg", graph=1, diag_every=1,
+               autotune=1, store_macro=0, profile=0)
+    if alpha_mode == "learned":
+        cfg["mlp"] = theta
+    cfg.update(extra)
+    return cfg, fields
 
 
-def run_ours(args, rank, world, local_rank):
-    import ctypes
-    import numpy as np
+def sites(shape):
+    return shape[0] * shape[1] * shape[2]
+
+
+def timed_steps(sim, steps, clocks=None):
+    """Device time (ms) of `steps` steps of one lattice, one CUDA-event pair
+    around them (each elbm_step waits for its step and checks its status)."""
     import torch
-    from concurrent.futures import ThreadPoolExecutor
-    from paper_1612_05404_gb300 import build, elbm
-    torch.cuda.set_device(local_rank)
-    build.build()
-    cfgs = workload_cfgs(args)
-    nx, ny, nz = cfgs[0][0]["shape"]
-    N = nx * ny * nz
-    if args.launch == "batch":
-        # all lattices in one CUDA graph per step (autotuned launch shapes)
-        for c, _ in cfgs:
-            c.update(autotune=1, profile=0)
-        sims = [elbm.Sim(c, f) for c, f in cfgs]
-        batch = elbm.Batch(sims, pipeline=args.pipeline == "on", span=span_of(args))
-        step_all = lambda m=1: batch.step(m)
-        streams = None
-    else:
-        # one CUDA stream per lattice, stepped from a thread pool (the library
-        # call releases the GIL)
-        streams = [torch.cuda.Stream() for _ in cfgs]
-        sims = [elbm.Sim(c, f, stream=ctypes.c_void_p(st.cuda_stream)) for (c, f), st in zip(cfgs, streams)]
-        pool = ThreadPoolExecutor(max_workers=len(sims))
-        step_all = lambda m=1: list(pool.map(lambda s: s.step(m), sims))
-    # timed launches: `span` steps per graph launch (batch), the rest one step
-    # at a time; exactly args.steps steps in all
-    span = span_of(args) if args.launch == "batch" else 1
-    chunks = [span] * (args.steps // span) + [1] * (args.steps % span)
-    for _ in range(args.warmup):
-        step_all()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    torch.cuda.synchronize()
-    times = []
-    sweeps0 = sum(s.diag()["poisson_sweeps_total"] for s in sims)
-    with ClockSampler(local_rank) as clk:
-        for m in chunks:
-            flush.zero_()
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            if streams:
-                for st in streams:
-                    st.wait_event(e0)
-            step_all(m)
-            if streams:
-                cur = torch.cuda.current_stream()
-                for st in streams:
-                    cur.wait_event(st.record_event())
-            e1.record()
-            torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1))
-    sweeps = sum(s.diag()["poisson_sweeps_total"] for s in sims) - sweeps0
-    torch.cuda.synchronize()
-    total_ms = sum(times)
-    if world > 1:
-        total_ms = max_over_ranks(total_ms, "cuda")
-        dist.barrier()
-    diag = [s.diag() for s in sims]
-    if args.launch == "batch":
-        batch.close()
-    else:
-        pool.shutdown()
-    for s in sims:
-        s.close()
-    value = job_mlups(len(sims) * N * args.steps, world, total_ms)
-
-    # the collision kernel alone: one lattice (E0 = 1e-3), each pass timed with
-    # CUDA events on its stream (three section graphs per step)
-    c1, f1 = cfgs[-1]
-    c1 = dict(c1, profile=1, autotune=1)
-    prof = elbm.Sim(c1, f1)
-    prof.step(args.warmup)
-    p0 = prof.pass_times()
-    prof.step(args.steps)
-    p1 = prof.pass_times()
-    prof.close()
-    d = {k: p1[k] - p0[k] for k in p0}
-    bf = {"fp64": 8, "fp32": 4, "bf16": 2}[args.precision]
-    bs = 8 if args.precision == "fp64" else 4
-    bytes_site = 2 * 19 * bf + 3 * bs + 14 * bs  # f read+write, rho/phi/q reads, g read+write
-    coll_ms = d["collide_ms"] / max(d["collide_launches"], 1)
-    achieved = N * bytes_site / (coll_ms * 1e-3) / 1e9
-    peak, peak_kind = peaks()
-    shares = {k: d[k] / max(d["moments_ms"] + d["poisson_ms"] + d["collide_ms"] + d["reduce_ms"], 1e-30)
-              for k in ("moments_ms", "poisson_ms", "collide_ms", "reduce_ms")}
-    launches_per_step = d["launches"] / max(d["steps"], 1)
-    out = {
-        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16"}[args.precision],
-        "data": "synthetic",
-        "config": {"workload": f"drop-in-field: {len(sims)} x 64^3 D3Q19 lattices (E0 sweep 1e-4..1e-3), "
-                               "transported charge, Carreau n=0.6",
-                   "sites_per_step": len(sims) * N, "population_storage": {"fp64": "fp64", "fp32": "fp32 deviation from w",
-                                          "bf16": "bf16, relative to the site density"}[args.precision],
-                   "alpha_arithmetic": args.alpha_precision,
-                   "l2": "256 MiB flush between timed launches (outside timing); lattice state %.0f MB > L2 (129 MB)"
-                         % (len(sims) * N * (2 * 19 * {"fp64": 8, "fp32": 4, "bf16": 2}[args.precision] + 2 * 7 * 4
-                                             + 6 * (8 if args.precision == "fp64" else 4)) / 1e6),
-                   "timed_launch_steps": span,
-                   "poisson": "multigrid V(2,2), red-black Gauss-Seidel, tol 1e-6 (FP32 floor stop), warm start extrapolated from the two previous potentials",
-                   "poisson_vcycles_per_step": sweeps / max(args.steps, 1) / len(sims),
-                   "launch": ("CUDA graphs of %d step(s) for all lattices (batch), autotuned block shapes" % span
-                              + (", odd lattices half a step ahead" if args.pipeline == "on" else "")
-                              if args.launch == "batch" else "one graph per lattice on concurrent streams"),
-                   "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                     "frac_of_8TBps": achieved / NOMINAL_HBM_GBS,
-                     # ncu dram__bytes_read.sum + dram__bytes_write.sum of one 64^3 FP32
-                     # launch of this kernel (cold caches)
-                     "traffic": 32.51e6 if args.precision == "fp32" else None,
-                     "bytes_per_site": bytes_site, "avg_launch_ms": coll_ms,
-                     "timed": "one 64^3 lattice alone, CUDA events around each collision launch"},
-        "pass_share": shares,
-        # kernels of the timed launches: per lattice and step those of the
-        # one-step graph, less the diagnostics finalize that a graph of m
-        # steps runs once instead of m times
-        "gpu_launches": int(round(len(sims) * sum(m * launches_per_step - (m - 1) for m in chunks))),
-        "alpha": {"max_h_error_device": max(x["max_h_error"] for x in diag), "h_error_bound": 1e-10,
-                  "guarded_sites_last_step": sum(x["n_guarded"] for x in diag),
-                  "guard_failed_last_step": sum(x["n_guard_failed"] for x in diag),
-                  "noroot": sum(x["n_noroot"] for x in diag), "clipped": sum(x["n_clipped"] for x in diag)},
-        "clocks": clk.summary(),
-    }
-    return out, cfgs, N
-
-
-def e2e_run(args, cfgs, N):
-    """The same metric end to end through the public API with host buffers,
-    on the headline's launch path: elbm_init of every lattice from host
-    arrays (H2D), the batch, warm-up and timed steps with every step's
-    diagnostics (the step's result) copied to pinned host memory, the final
-    density fields read back, elbm_free."""
-    import numpy as np
-    import torch
-    from paper_1612_05404_gb300 import elbm
-    h2d = 0
-    for c, f in cfgs:
-        c.update(profile=0, autotune=1)
-        h2d += sum(v.nbytes for v in f.values() if hasattr(v, "nbytes"))
-    n_steps = args.warmup + args.steps
-    diag = [torch.empty(elbm.NDIAG, dtype=torch.float64).pin_memory() for _ in cfgs]
-    diag_np = [d.numpy() for d in diag]
-    rho = [np.empty(N) for _ in cfgs]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    sims = [elbm.Sim(c, f) for c, f in cfgs]
-    batch = elbm.Batch(sims, pipeline=args.pipeline == "on")
-    t_init = time.perf_counter() - t0
-    for _ in range(n_steps):
-        batch.step(1)
-        for s, d in zip(sims, diag_np):
-            s.fields(elbm.F_DIAG, d)
-    for s, r in zip(sims, rho):
-        s.fields(elbm.F_RHO, r)
-    batch.close()
-    for s in sims:
-        s.close()
-    dt = time.perf_counter() - t0
-    d2h = len(cfgs) * (elbm.NDIAG * 8 + N * 8 / n_steps)
-    return {"value": len(cfgs) * N * n_steps / dt / 1e6, "unit": "MLUPS",
-            "h2d_bytes_per_step": int(h2d / n_steps), "d2h_bytes_per_step": int(d2h),
-            "init_seconds": t_init,
-            "timed": "init from host arrays + batch + %d steps with per-step diagnostics read to pinned "
-                     "host memory + final density read + free" % n_steps}
-
-
-def _timed_steps(sims, streams, pool, steps, warmup):
-    """Device time (ms) of `steps` steps of all lattices, after `warmup`."""
-    import torch
-    for _ in range(warmup):
-        list(pool.map(lambda s: s.step(1), sims))
-    torch.cuda.synchronize()
-    p0 = [s.pass_times() for s in sims]
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    total = 0.0
+    e0.record()
     for _ in range(steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for st in streams:
-            st.wait_event(e0)
-        list(pool.map(lambda s: s.step(1), sims))
-        cur = torch.cuda.current_stream()
-        for st in streams:
-            cur.wait_event(st.record_event())
-        e1.record()
-        torch.cuda.synchronize()
-        total += e0.elapsed_time(e1)
-    p1 = [s.pass_times() for s in sims]
-    d = {k: sum(b[k] - a[k] for a, b in zip(p0, p1)) for k in p0[0]}
-    return total, d
+        sim.step(1)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
 
 
-def alpha_compare(args, N):
-    """Learned-alpha vs Newton-alpha on the bench workload at one H-error
-    bound (<= 1e-10 rho): the FP64 Newton root, the FP32 Newton root with the
-    float-float guard, and the FP32 iteration started from the learned
-    proposal (trained here on the GPU: pairs harvested from the first steps of
-    the E0 = 1e-3 lattice, the project's training kernels); step throughput,
-    collision time per launch, device H-error and fallbacks."""
-    import ctypes
-    from concurrent.futures import ThreadPoolExecutor
+# ---------------------------------------------------------------------------
+# the learned proposal: pairs harvested from configs 2 and 3, trained on the GPU
+# ---------------------------------------------------------------------------
+def _harvest(sim, keep_mask=None):
+    """Training pairs of every fluid site of a lattice (FP32 deviations of its
+    populations through elbm_fields, elbm_alpha_harvest on the GPU)."""
     import numpy as np
     import torch
     from paper_1612_05404_gb300 import elbm
     from paper_1612_05404_gb300 import workloads as W
-    out = {}
-    # training pairs from the plain run of one lattice
+    f = sim.get("f").reshape(19, -1)
+    fluid = f.sum(0) > 0
+    d = torch.from_numpy(np.ascontiguousarray(f[:, fluid] - W.D3Q19_WEIGHTS[:, None]).astype(np.float32)).cuda()
+    del f
+    X, y, keep = elbm.alpha_harvest(d)
+    kk = keep.bool()
+    return X[:, kk].contiguous(), y[kk].contiguous(), int(fluid.sum())
+
+
+def train_proposal(args):
+    """(theta, report): the proposal's network trained with the project's
+    kernels (elbm_mlp_train, minibatch Adam) on pairs harvested from the
+    drop-in-field (config 2: 64^3, E0 = 1e-3 and 7e-4, FP32) and the jet
+    (config 3: 128 x 128 x 512, BF16) during their first steps; sites with
+    S = max|Delta/f| >= 2^-5, where the proposal is used."""
+    import math
+    import numpy as np
+    import torch
+    from paper_1612_05404_gb300 import elbm
+    from paper_1612_05404_gb300 import workloads as W
     t0 = time.perf_counter()
-    cfg, fields = W.drop_in_field(E0=1e-3, precision=args.precision)
-    cfg.update(alpha_precision="fp32", store_macro=0, diag_every=1, poisson_check_every=8, graph=1)
+    Xs, ys, seen, src = [], [], 0, {}
+    for E0 in (1e-3, 7e-4):
+        cfg, fields = W.drop_in_field(E0=E0, precision="fp32")
+        cfg.update(alpha_precision="fp32", store_macro=0, diag_every=1, poisson_check_every=8, graph=1)
+        sim = elbm.Sim(cfg, fields)
+        for k in range(30):
+            sim.step(1)
+            if k % 3 == 2:
+                X, y, n = _harvest(sim)
+                Xs.append(X); ys.append(y); seen += n
+                src["drop64"] = src.get("drop64", 0) + int(y.numel())
+        sim.close()
+    cfg, fields = jet_case(JET3_SHAPE, alpha_mode="entropic")
     sim = elbm.Sim(cfg, fields)
-    Xs, ys = [], []
-    for k in range(24):
+    for k in range(30):
         sim.step(1)
-        if k % 3 == 2:
-            d = torch.from_numpy((sim.get("f").reshape(19, -1) - W.D3Q19_WEIGHTS[:, None]).astype(np.float32)).cuda()
-            X, y, keep = elbm.alpha_harvest(d)
-            kk = keep.bool()
-            Xs.append(X[:, kk])
-            ys.append(y[kk])
+        if k % 10 == 9:
+            X, y, n = _harvest(sim)
+            Xs.append(X); ys.append(y); seen += n
+            src["jet128"] = src.get("jet128", 0) + int(y.numel())
     sim.close()
     X = torch.cat(Xs, dim=1).contiguous()
     y = torch.cat(ys).contiguous()
+    del Xs, ys
+    t_h = time.perf_counter() - t0
     rng = np.random.default_rng(20161209)
-    import math
     lim1, lim2, lim3 = math.sqrt(6 / 84), math.sqrt(6 / 128), math.sqrt(6 / 65)
     theta = torch.zeros(elbm.MLP_NPARAM, dtype=torch.float32)
     theta[:1280] = torch.from_numpy(rng.uniform(-lim1, lim1, 1280).astype(np.float32))
@@ -451,87 +283,278 @@ def alpha_compare(args, N):
     theta[5504:5568] = torch.from_numpy(rng.uniform(-lim3, lim3, 64).astype(np.float32))
     theta = theta.cuda()
     m, v = torch.zeros_like(theta), torch.zeros_like(theta)
-    hist = elbm.mlp_train(X, y, theta, m, v, 0, 4000, 1024, 2e-3, seed=20161209)
+    hist = elbm.mlp_train(X, y, theta, m, v, 0, args.train_steps, 1024, 2e-3, seed=20161209)
     torch.cuda.synchronize()
     h = hist.cpu().numpy()
-    out["training"] = {"pairs": int(X.shape[1]), "steps": 4000, "batch": 1024,
-                       "loss_first": float(h[:50].mean()), "loss_last": float(h[-50:].mean()),
-                       "seconds": time.perf_counter() - t0,
-                       "data": "pairs harvested every 3rd of the first 24 steps of the E0=1e-3 lattice, S >= 2^-5"}
+    return theta, {"pairs": int(X.shape[1]), "pairs_by_source": src, "sites_harvested": seen,
+                   "adam_steps": args.train_steps, "batch": 1024, "lr": 2e-3,
+                   "loss_first": float(h[:50].mean()), "loss_last": float(h[-50:].mean()),
+                   "harvest_seconds": t_h, "seconds": time.perf_counter() - t0,
+                   "data": "every 3rd of the first 30 steps of two 64^3 drops in field (E0 = 1e-3, 7e-4) and "
+                           "steps 10, 20, 30 of the 128x128x512 jet; fluid sites with S >= 2^-5 (the others "
+                           "use the moment-series start, not the network)"}
 
-    def run(mode, aprec, steps):
-        cfgs = workload_cfgs(args)
-        streams = [torch.cuda.Stream() for _ in cfgs]
-        sims = []
-        for (c, f), st in zip(cfgs, streams):
-            c.update(profile=1, alpha_mode=mode, alpha_precision=aprec)
-            if mode == "learned":
-                c["mlp"] = theta
-            sims.append(elbm.Sim(c, f, stream=ctypes.c_void_p(st.cuda_stream)))
-        pool = ThreadPoolExecutor(max_workers=len(sims))
-        ms, d = _timed_steps(sims, streams, pool, steps, args.warmup)
-        diag = [s.diag() for s in sims]
-        for s in sims:
-            s.close()
-        pool.shutdown()
-        return {"mlups": len(sims) * N * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
-                "collide_ms_per_launch": d["collide_ms"] / max(d["collide_launches"], 1),
-                "max_h_error_device": max(x["max_h_error"] for x in diag),
-                "guarded_sites_last_step": sum(x["n_guarded"] for x in diag),
-                "learned_fallback_sites_last_step": sum(x["n_learned_fallback"] for x in diag),
-                "steps": steps}
 
-    out["newton_fp64"] = run("entropic", "fp64", max(2, args.steps // 5))
-    out["newton_fp32_guarded"] = run("entropic", "fp32", args.steps)
-    out["learned_fp32_guarded"] = run("learned", "fp32", args.steps)
-    out["h_error_bound"] = 1e-10
-    out["speedup_learned_vs_newton_fp32"] = out["learned_fp32_guarded"]["mlups"] / out["newton_fp32_guarded"]["mlups"]
+# ---------------------------------------------------------------------------
+# the headline: config 4
+# ---------------------------------------------------------------------------
+def bytes_per_site_collide(learned):
+    """Algorithmic bytes of one collision launch per site, BF16 storage:
+    populations read and written (2 x 19 x 2), the reference-density plane
+    read and written (2 x 4), the psi, phi and q planes read (3 x 4), the
+    node-kind mask (1), and in learned mode the network output (4)."""
+    return 2 * 19 * 2 + 2 * 4 + 3 * 4 + 1 + (4 if learned else 0)
+
+
+def bytes_per_site_mlp():
+    """The learned-proposal pass: populations and reference densities read
+    (19 x 2 + 4), mask (1), network output written (4)."""
+    return 19 * 2 + 4 + 1 + 4
+
+
+def run_headline(args, rank, world, local_rank, theta):
+    import torch
+    N = sites(JET4_SHAPE)
+    from paper_1612_05404_gb300 import elbm
+    learned = args.alpha_mode == "learned"
+    cfg, fields = jet_case(JET4_SHAPE, alpha_mode=args.alpha_mode, theta=theta)
+    sim = elbm.Sim(cfg, fields)
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    d0 = sim.diag()
+    with ClockSampler(local_rank) as clk:
+        ms = timed_steps(sim, args.steps)
+    d1 = sim.diag()
+    sim.close()
+    total_ms = ms
+    if world > 1:
+        total_ms = max_over_ranks(ms, "cuda")
+        import torch.distributed as dist
+        dist.barrier()
+    value = job_mlups(N * args.steps, world, total_ms)
+    diag = {"max_h_error_device_last_step": d1["max_h_error"], "guard_failed_last_step": d1["n_guard_failed"],
+            "guarded_sites_last_step": d1["n_guarded"], "learned_fallback_sites_last_step": d1["n_learned_fallback"],
+            "nonfinite": d1["n_nonfinite"], "noroot_last_step": d1["n_noroot"],
+            "poisson_vcycles_per_step": (d1["poisson_sweeps_total"] - d0["poisson_sweeps_total"]) / args.steps,
+            "mass_drift_rel": abs(d1["mass"] - d0["mass"]) / d0["mass"]}
+    return value, total_ms, clk.summary(), diag
+
+
+def roofline(args, theta):
+    """The collision kernel of the headline alone: the same lattice issued
+    step by step with CUDA events around each pass (profile mode); its
+    average launch time against its algorithmic bytes."""
+    from paper_1612_05404_gb300 import elbm
+    N = sites(JET4_SHAPE)
+    learned = args.alpha_mode == "learned"
+    cfg, fields = jet_case(JET4_SHAPE, alpha_mode=args.alpha_mode, theta=theta, graph=0, profile=1)
+    sim = elbm.Sim(cfg, fields)
+    sim.step(max(args.warmup, 3))
+    p0 = sim.pass_times()
+    n = max(5, min(args.steps, 10))
+    sim.step(n)
+    p1 = sim.pass_times()
+    sim.close()
+    d = {k: p1[k] - p0[k] for k in p0}
+    launches = d["collide_launches"]
+    mlp_ms = d["mlp_ms"] / max(launches, 1)
+    coll_ms = (d["collide_ms"] - d["mlp_ms"]) / max(launches, 1)  # the collision kernel (+ the tiny finalize)
+    bs = bytes_per_site_collide(learned)
+    achieved = N * bs / (coll_ms * 1e-3) / 1e9
+    peak, kind = peaks()
+    tot = d["moments_ms"] + d["poisson_ms"] + d["collide_ms"] + d["reduce_ms"]
+    out = {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak, "peak_source": kind, "frac_of_8TBps": achieved / NOMINAL_HBM_GBS,
+           # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel on the
+           # 128x128x512 jet, scaled by sites to the 256x256x768 lattice (profiles/)
+           "traffic": None,
+           "bytes_per_site": bs, "avg_launch_ms": coll_ms,
+           "timed": "256x256x768 jet, steps issued one by one, CUDA events around each pass (profile mode)"}
+    shares = {"moments_charge": d["moments_ms"] / tot, "poisson": d["poisson_ms"] / tot,
+              "collide": (d["collide_ms"] - d["mlp_ms"]) / tot, "learned_pass": d["mlp_ms"] / tot}
+    mlp = None
+    if learned:
+        mlp = {"kernel": "k_alpha_mlp", "avg_launch_ms": mlp_ms, "bytes_per_site": bytes_per_site_mlp(),
+               "achieved_gbs": N * bytes_per_site_mlp() / max(mlp_ms * 1e-3, 1e-12) / 1e9}
+    launches_per_step = d["launches"] / max(d["steps"], 1)
+    return out, shares, mlp, launches_per_step, {k: d[k] / max(d["steps"], 1) for k in
+                                                ("moments_ms", "poisson_ms", "collide_ms", "mlp_ms")}
+
+
+def e2e_run(args, theta):
+    """The same metric end to end through the public API with host buffers:
+    elbm_init from host arrays (fields and the network's parameters
+    uploaded), warm-up and timed steps with every step's diagnostics copied
+    to pinned host memory and read, the final density read back, elbm_free."""
+    import numpy as np
+    import torch
+    from paper_1612_05404_gb300 import elbm
+    N = sites(JET4_SHAPE)
+    cfg, fields = jet_case(JET4_SHAPE, alpha_mode=args.alpha_mode, theta=theta)
+    theta_host = theta.cpu() if theta is not None else None
+    h2d = sum(v.nbytes for v in fields.values() if hasattr(v, "nbytes"))
+    h2d += theta_host.numel() * 4 if theta_host is not None else 0
+    n_steps = args.warmup + args.steps
+    diag = torch.empty(elbm.NDIAG, dtype=torch.float64).pin_memory()
+    diag_np = diag.numpy()
+    rho = np.empty(N)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if theta_host is not None:
+        cfg = dict(cfg, mlp=theta_host.cuda(non_blocking=False))
+    sim = elbm.Sim(cfg, fields)
+    t_init = time.perf_counter() - t0
+    for _ in range(n_steps):
+        sim.step(1)
+        sim.fields(elbm.F_DIAG, diag_np)
+    sim.fields(elbm.F_RHO, rho)
+    sim.close()
+    dt = time.perf_counter() - t0
+    d2h = elbm.NDIAG * 8 + N * 8 / n_steps
+    return {"value": N * n_steps / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": int(h2d / n_steps),
+            "d2h_bytes_per_step": int(d2h), "init_seconds": t_init, "steps": n_steps,
+            "timed": "elbm_init from host arrays (fields + network) + %d steps, each with its diagnostics read "
+                     "from pinned host memory + final density read + elbm_free" % n_steps}
+
+
+# ---------------------------------------------------------------------------
+# secondary measurements (rank 0, N = 1)
+# ---------------------------------------------------------------------------
+def alpha_compare(args, theta, learned_ms):
+    """Learned proposal vs the Newton root on the headline workload at one
+    bound (|h|/rho <= 1e-10 against the exact equation): guarded FP32 Newton
+    alone, and the FP64 Newton root (two steps; 1/64-rate FP64 on this part)."""
+    from paper_1612_05404_gb300 import elbm
+    N = sites(JET4_SHAPE)
+    out = {}
+    for name, mode, aprec, steps in (("newton_fp32_guarded", "entropic", "fp32", args.steps),
+                                     ("newton_fp64", "entropic", "fp64", 2)):
+        cfg, fields = jet_case(JET4_SHAPE, alpha_mode=mode, aprec=aprec)
+        sim = elbm.Sim(cfg, fields)
+        sim.step(args.warmup if aprec == "fp32" else 1)
+        ms = timed_steps(sim, steps)
+        d = sim.diag()
+        sim.close()
+        out[name] = {"mlups": N * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps, "steps": steps,
+                     "max_h_error_device_last_step": d["max_h_error"], "guarded_sites_last_step": d["n_guarded"]}
+    out["learned_fp32_guarded"] = {"mlups": N * args.steps / (learned_ms * 1e-3) / 1e6,
+                                   "ms_per_step": learned_ms / args.steps, "steps": args.steps}
+    out["speedup_learned_vs_newton_fp32"] = (out["learned_fp32_guarded"]["mlups"]
+                                             / out["newton_fp32_guarded"]["mlups"])
     out["speedup_learned_vs_newton_fp64"] = out["learned_fp32_guarded"]["mlups"] / out["newton_fp64"]["mlups"]
+    out["h_error_bound"] = "1e-10 rho, exact equation of the stored populations"
     return out
 
 
-def jet_run(args):
-    """The electrified jet at full size: 128 x 128 x 512, nozzle of radius 8
-    injecting Carreau liquid (n = 0.5, lambda = 20) at 0.02 along z, E0 = 5e-4,
-    xi-form charge, BF16 deviation storage with FP32 arithmetic, guarded FP32
-    alpha, multigrid Poisson with the nozzle as a conductor."""
+def alpha_stage(theta):
+    """Where the proposal is used: the alpha root alone (elbm_alpha_eval) on
+    held-out strongly non-equilibrium sites (S >= 2^-5) of a drop in field not
+    seen in training (E0 = 4e-4, step 33): guarded FP32 Newton from the
+    moment-series start vs from the learned proposal, same bound."""
+    import numpy as np
     import torch
     from paper_1612_05404_gb300 import elbm
     from paper_1612_05404_gb300 import workloads as W
-    cfg, fields = W.jet(precision="bf16")
-    cfg.update(alpha_precision="fp32", poisson_solver="mg", graph=1, diag_every=1, autotune=1)
-    N = cfg["shape"][0] * cfg["shape"][1] * cfg["shape"][2]
+    cfg, fields = W.drop_in_field(E0=4e-4, precision="fp32")
+    cfg.update(alpha_precision="fp32", store_macro=0, diag_every=1, poisson_check_every=8, graph=1)
     sim = elbm.Sim(cfg, fields)
-    del fields
-    sim.step(args.warmup)
-    torch.cuda.synchronize()
-    total, cycles, herr, guarded = 0.0, 0.0, 0.0, 0.0
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    for _ in range(args.steps):
-        flush.zero_()
+    sim.step(33)
+    f = sim.get("f").reshape(19, -1)
+    sim.close()
+    d = torch.from_numpy(np.ascontiguousarray(f - W.D3Q19_WEIGHTS[:, None]).astype(np.float32)).cuda()
+    _, S = elbm.alpha_features(d)
+    hard = torch.nonzero(S >= 2 ** -5).flatten()
+    dh = d[:, hard].contiguous()
+    reps = max(1, int(2_000_000 // max(dh.shape[1], 1)))
+    dh = dh.repeat(1, reps).contiguous()  # enough sites to time the kernel
+    res = {}
+    for name, mlp in (("newton", None), ("learned", theta)):
+        for _ in range(2):
+            a, he, st, _ = elbm.alpha_eval(dh, aprec="fp32", eq_tol=1e-5, mlp=mlp)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        sim.step(1)
+        for _ in range(5):
+            a, he, st, _ = elbm.alpha_eval(dh, aprec="fp32", eq_tol=1e-5, mlp=mlp)
         e1.record()
         torch.cuda.synchronize()
-        total += e0.elapsed_time(e1)
-        d = sim.diag()
-        cycles += d["poisson_sweeps"]
-        herr = max(herr, d["max_h_error"])
-        guarded += d["n_guarded"]
+        stn = st.cpu().numpy()
+        root = np.isin(stn, (0, 5))
+        res[name] = {"ns_per_site": e0.elapsed_time(e1) / 5 * 1e6 / dh.shape[1],
+                     "multi_evaluation_fraction": float(np.mean(stn[root] == 5)),
+                     "max_h_error_reported": float(he.cpu().numpy()[root].max()),
+                     "guard_failed": int(np.sum(stn == 4))}
+    res["hard_sites"] = int(hard.numel())
+    res["timed_sites"] = int(dh.shape[1])
+    res["speedup_learned_vs_newton"] = res["newton"]["ns_per_site"] / res["learned"]["ns_per_site"]
+    return res
+
+
+def drop64(args):
+    """Config 2 at full size: four 64^3 drops in field (the E0 sweep), FP32
+    storage, guarded FP32 alpha, one batch; graphs of one step (diagnostics
+    every step) and of `span` steps (diagnostics on the last)."""
+    import torch
+    from paper_1612_05404_gb300 import elbm
+    from paper_1612_05404_gb300 import workloads as W
+    N = 64 ** 3
+    out = {}
+    for span in sorted({1, span_of(args)}):
+        sims = []
+        for E0 in W.E0_SWEEP:
+            cfg, fields = W.drop_in_field(E0=E0, precision="fp32")
+            cfg.update(alpha_precision="fp32", store_macro=0, diag_every=1, poisson_check_every=8, graph=1,
+                       autotune=1)
+            sims.append(elbm.Sim(cfg, fields))
+        batch = elbm.Batch(sims, pipeline=True, span=span)
+        batch.step(args.warmup)
+        chunks = [span] * (args.steps // span) + [1] * (args.steps % span)
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        total = 0.0
+        for m in chunks:
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            batch.step(m)
+            e1.record()
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+        batch.close()
+        herr = max(s.diag()["max_h_error"] for s in sims)
+        for s in sims:
+            s.close()
+        out[f"span{span}"] = {"mlups": 4 * N * args.steps / (total * 1e-3) / 1e6, "ms_per_step": total / args.steps,
+                              "max_h_error_device": herr,
+                              "diagnostics": "every step" if span == 1 else f"last of every {span} steps"}
+    out["workload"] = "4 x 64^3 drop in field (E0 sweep), FP32, guarded FP32 alpha, batch, half-step shift"
+    return out
+
+
+def jet128(args):
+    """Config 3 at full size: one 128 x 128 x 512 jet, BF16, guarded FP32 Newton."""
+    from paper_1612_05404_gb300 import elbm
+    N = sites(JET3_SHAPE)
+    cfg, fields = jet_case(JET3_SHAPE, alpha_mode="entropic")
+    sim = elbm.Sim(cfg, fields)
+    sim.step(args.warmup)
+    ms = timed_steps(sim, args.steps)
+    d = sim.diag()
     sim.close()
-    return {"workload": "electrified jet 128x128x512, nozzle r=8, Carreau n=0.5 lambda=20, E0=5e-4, xi-form charge",
-            "storage": "bf16, relative to the site density", "sites": N, "mlups": N * args.steps / (total * 1e-3) / 1e6,
-            "ms_per_step": total / args.steps, "poisson": "multigrid, nozzle as conductor",
-            "poisson_vcycles_per_step": cycles / args.steps, "max_h_error_device": herr,
-            "guarded_site_fraction": guarded / (N * args.steps)}
+    return {"mlups": N * args.steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / args.steps,
+            "max_h_error_device_last_step": d["max_h_error"], "guarded_fraction_last_step": d["n_guarded"] / N,
+            "workload": "128x128x512 jet, BF16 relative to the site density, guarded FP32 Newton alpha"}
 
 
 def batched_compare(args):
-    """Batched droplets (uneven boxes, one CUDA graph launch per step for all)
-    against the same boxes stepped one at a time, at the same H-error bound
-    (guarded FP32 alpha), FP32 storage, autotuned launch shapes."""
+    """Batched droplets (uneven boxes, one CUDA graph launch per step for
+    all, diagnostics every step) against the same boxes stepped one at a
+    time, at the same H-error bound (guarded FP32 alpha), FP32 storage."""
     import torch
     from paper_1612_05404_gb300 import elbm
     from paper_1612_05404_gb300 import workloads as W
@@ -543,9 +566,9 @@ def batched_compare(args):
         cfg.update(alpha_precision="fp32", autotune=1, graph=1, diag_every=1)
         sims.append(elbm.Sim(cfg, fields))
     t_init = time.perf_counter() - t0
-    sites = sum(e ** 3 for e, _, _ in params)
+    nsites = sum(e ** 3 for e, _, _ in params)
     t0 = time.perf_counter()
-    batch = elbm.Batch(sims, pipeline=args.pipeline == "on", span=span_of(args))
+    batch = elbm.Batch(sims, pipeline=True, span=1)
     t_capture = time.perf_counter() - t0
     batch.step(args.warmup)
     torch.cuda.synchronize()
@@ -557,30 +580,91 @@ def batched_compare(args):
     ms_b = e0.elapsed_time(e1) / args.steps
     hmax_b = max(s.diag()["max_h_error"] for s in sims)
     batch.close()
-    # the same boxes one at a time: each box's own step graph, launched and
-    # finished before the next box starts
+    # the same boxes one at a time: each box's own step graph (diagnostics
+    # every step), its steps finished before the next box starts
+    k = 5
     single_ms = 0.0
     for s in sims:
         s.step(1)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        s.step(2)
+        s.step(k)
         b.record()
         torch.cuda.synchronize()
-        single_ms += a.elapsed_time(b) / 2
+        single_ms += a.elapsed_time(b) / k
     hmax_s = max(s.diag()["max_h_error"] for s in sims)
     for s in sims:
         s.close()
-    return {"boxes": len(params), "sites": sites, "edges": sorted(set(e for e, _, _ in params)),
-            "batched": {"mlups": sites / (ms_b * 1e-3) / 1e6, "ms_per_step": ms_b, "max_h_error_device": hmax_b,
-                        "graph_launches_per_step": 1.0 / span_of(args), "pipelined": args.pipeline == "on"},
-            "one_at_a_time": {"mlups": sites / (single_ms * 1e-3) / 1e6, "ms_per_step": single_ms,
-                              "max_h_error_device": hmax_s},
+    return {"boxes": len(params), "sites": nsites, "edges": sorted(set(e for e, _, _ in params)),
+            "batched": {"mlups": nsites / (ms_b * 1e-3) / 1e6, "ms_per_step": ms_b, "max_h_error_device": hmax_b,
+                        "graph_launches_per_step": 1, "diagnostics": "every step"},
+            "one_at_a_time": {"mlups": nsites / (single_ms * 1e-3) / 1e6, "ms_per_step": single_ms,
+                              "max_h_error_device": hmax_s, "steps_per_box": k},
             "speedup_batched_vs_single": single_ms / ms_b,
             "init_seconds": t_init, "capture_seconds": t_capture,
-            "workload": "batched droplets: periodic cubic boxes, edge over {24..96} step 8 except 72, 88, "
-                        "R = edge/4, E0 ~ U[0,1e-3] along z, Carreau n ~ U[0.5,1], lambda 10, transported charge"}
+            "workload": "batched droplets: periodic cubic boxes, R = edge/4, E0 ~ U[0,1e-3] along z, "
+                        "Carreau n ~ U[0.5,1], lambda 10, transported charge, FP32"}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores
+# ---------------------------------------------------------------------------
+def oracle_sample(shape, threads, steps, warm=1):
+    """The FP64 CPU oracle, as it stands, on a jet of the headline's physics
+    at `shape` (nozzle radius 8): `warm` untimed steps, then `steps` timed."""
+    import oracle
+    from paper_1612_05404_gb300 import workloads as W
+    used = oracle.set_threads(threads)
+    cfg, fields = W.jet(shape=shape, precision="bf16")
+    sim = oracle.Sim(cfg, fields)
+    sim.step(warm)
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    return sites(shape) * steps / dt / 1e6, dt, used
+
+
+def cpu_baseline():
+    cores = os.cpu_count() or 1
+    v, dt, used = oracle_sample(SAMPLE_SHAPE, cores, 2)
+    v1, dt1, _ = oracle_sample(SAMPLE1_SHAPE, 1, 1)
+    return {"value": v, "unit": "MLUPS", "cores": used, "kind": "oracle",
+            "sample": "FP64 oracle, jet of the headline's physics at %dx%dx%d (nozzle r = 8), 1 untimed + 2 timed "
+                      "steps, %d threads (site-parallel loops); MLUPS is per site and step, so it stands for the "
+                      "256x256x768 lattice (extrapolated)" % (*SAMPLE_SHAPE, used),
+            "seconds": dt, "host": host_cpu(),
+            "single_thread": {"value": v1, "unit": "MLUPS", "cores": 1, "seconds": dt1,
+                              "sample": "the same physics at %dx%dx%d, 1 untimed + 1 timed step" % SAMPLE1_SHAPE}}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    import oracle
+    from paper_1612_05404_gb300 import workloads as W
+    cores = os.cpu_count() or 1
+    used = oracle.set_threads(cores)
+    cfg, fields = W.jet(shape=SAMPLE1_SHAPE, precision="bf16")
+    sim = oracle.Sim(cfg, fields)
+    sim.step(max(args.warmup, 1))
+    t0 = time.perf_counter()
+    sim.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = sites(SAMPLE1_SHAPE) * args.steps / dt / 1e6
+    sample = ("FP64 oracle on a %dx%dx%d jet of the headline's physics (nozzle r = 8), %d steps after %d untimed, "
+              "%d threads" % (*SAMPLE1_SHAPE, args.steps, max(args.warmup, 1), used))
+    return {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "electrified jet, sample %dx%dx%d of the 256x256x768 headline lattice" % SAMPLE1_SHAPE,
+                   "oracle": "plain FP64 C, site-parallel loops"},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": used, "kind": "oracle", "sample": sample,
+                         "host": host_cpu()},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
 
 
 def main():
@@ -593,24 +677,59 @@ def main():
         if res is not None:
             print(json.dumps(res), flush=True)
         return
+    import torch
+    torch.cuda.set_device(local_rank)
     if world > 1:
-        import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    res, cfgs, N = run_ours(args, rank, world, local_rank)
+    from paper_1612_05404_gb300 import build
+    build.build()
+    theta, training = (None, None)
+    if args.alpha_mode == "learned":
+        theta, training = train_proposal(args)
+    value, total_ms, clocks, hdiag = run_headline(args, rank, world, local_rank, theta)
+    res = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "electrified jet 256x256x768 D3Q19 (50.3M sites), nozzle r=8, Carreau n=0.5 "
+                               "lambda=20, E0=5e-4, xi-form charge",
+                   "sites_per_step": sites(JET4_SHAPE),
+                   "population_storage": "bf16, relative to the site density", "arithmetic": "fp32",
+                   "alpha": ("learned proposal + guarded FP32 Newton" if theta is not None
+                             else "guarded FP32 Newton") + ", |h|/rho <= 1e-10 against the exact equation",
+                   "diagnostics": "every timed step",
+                   "l2": "no flush: lattice state 8.4 GB > L2 (129 MB)",
+                   "poisson": "multigrid V(2,2), red-black Gauss-Seidel, tol 1e-6 (FP32 floor stop), nozzle "
+                              "as a conductor, warm start extrapolated",
+                   "launch": "one CUDA graph per step, the Poisson loop a device-side while node, autotuned "
+                             "block shape",
+                   "parallelism": f"replicas x{world}"},
+        "headline_diagnostics": hdiag,
+        "clocks": clocks,
+    }
+    if training is not None:
+        res["training"] = training
+    roof, shares, mlp, lps, pass_ms = roofline(args, theta)
+    res["roofline"] = roof
+    res["pass_share"] = shares
+    res["pass_ms_per_step"] = pass_ms
+    if mlp is not None:
+        res["learned_pass"] = mlp
+    res["gpu_launches"] = int(round(lps * args.steps))
     if not args.no_e2e:
-        res["e2e"] = e2e_run(args, cfgs, N)
+        res["e2e"] = e2e_run(args, theta)
         res["e2e"]["value"] *= world
-    if rank == 0 and world == 1 and not args.no_alpha_compare and args.precision != "fp64":
-        res["alpha_compare"] = alpha_compare(args, N)
-    if rank == 0 and world == 1 and args.boxes > 0:
-        res["batched_compare"] = batched_compare(args)
-    if rank == 0 and world == 1 and not args.no_jet:
-        res["jet"] = jet_run(args)
+    if rank == 0 and world == 1 and not args.no_extras:
+        if theta is not None:
+            res["alpha_compare"] = alpha_compare(args, theta, total_ms)
+            res["alpha_stage"] = alpha_stage(theta)
+        res["jet128"] = jet128(args)
+        res["drop64"] = drop64(args)
+        if args.boxes > 0:
+            res["batched_compare"] = batched_compare(args)
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, dt, sample = cpu_sample()
-        res["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample}
+        res["cpu_baseline"] = cpu_baseline()
     if world > 1:
         import torch.distributed as dist
         dist.barrier()

@@ -58,8 +58,9 @@ struct elbm_handle {
     int want_graph, graph_tried;  // step graphs requested; capture attempted (on the first elbm_step)
     int n_pre, n_body, n_post; // kernels per graph section (launch accounting)
     double noconv_seen;
-    cudaEvent_t ev[5];         // pass boundaries when profiling
+    cudaEvent_t ev[6];         // pass boundaries when profiling ([5]: after the learned-proposal pass)
     double pass_ms[4];
+    double mlp_ms;             // the learned-proposal pass alone (host-issued profiled steps)
     double prof_steps, prof_collide, prof_sweeps, launches;
     // batch of instances (elbm_batch_create): n_sub > 0
     int n_sub;
@@ -264,7 +265,7 @@ void free_bufs(elbm_handle *h)
     if (h->xtmp) cudaFree(h->xtmp);
     h->xtmp = nullptr;
     if (h->pin) cudaFreeHost(h->pin);
-    for (int i = 0; i < 5; i++)
+    for (int i = 0; i < 6; i++)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     for (int i = 0; i < 2; i++) {
         if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
@@ -414,6 +415,7 @@ elbm_status step_host(elbm_handle *h, bool diag)
         h->ops.alpha_mlp(h->g, h->ph, b, h->L, s);
         h->launches += 1;
     }
+    if (prof) cudaEventRecord(h->ev[5], s);
     h->ops.collide(h->g, h->ph, b, diag ? 1 : 0, h->L, s);
     h->launches += 1;
     if (prof) cudaEventRecord(h->ev[3], s);
@@ -942,7 +944,7 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     if (h->nlev > 0) h->tail.top = h->lev[h->lt];
     if (ok && !cuda_ok(cudaMallocHost((void **)&h->pin, (kPinDiag + ELBM_NDIAG) * sizeof(double)))) ok = false;
     if (ok && p->profile)
-        for (int i = 0; i < 5; i++)
+        for (int i = 0; i < 6; i++)
             if (!cuda_ok(cudaEventCreate(&h->ev[i]))) ok = false;
     if (!ok) { free_bufs(h); delete h; return ELBM_E_NOMEM; }
 
@@ -1109,6 +1111,7 @@ elbm_status elbm_step(elbm_handle *h, int nsteps)
             if (!cuda_ok(cudaGraphLaunch(gs[2], h->s))) return ELBM_E_CUDA;
             cudaEventRecord(h->ev[3], h->s);
             cudaEventRecord(h->ev[4], h->s);
+            cudaEventRecord(h->ev[5], h->s);  // (not separated in section graphs)
         } else if (h->use_graph) {
             if (!cuda_ok(cudaGraphLaunch(h->gexec[h->step & 1], h->s))) return ELBM_E_CUDA;
         } else {
@@ -1121,6 +1124,11 @@ elbm_status elbm_step(elbm_handle *h, int nsteps)
             float ms[4];
             for (int k = 0; k < 4; k++) cudaEventElapsedTime(&ms[k], h->ev[k], h->ev[k + 1]);
             for (int k = 0; k < 4; k++) h->pass_ms[k] += ms[k];
+            if (!h->use_graph) {
+                float mm = 0.f;
+                cudaEventElapsedTime(&mm, h->ev[2], h->ev[5]);
+                h->mlp_ms += mm;
+            }
             if (!cuda_ok(cudaMemcpy(h->pin, h->b.scal + S_ITER, sizeof(double), cudaMemcpyDeviceToHost)))
                 return ELBM_E_CUDA;
             h->prof_steps += 1;
@@ -1251,9 +1259,9 @@ elbm_status elbm_pass_times(const elbm_handle *h, double *out, int n)
     if (h && h->n_sub > 0) return ELBM_E_STATE;
     if (!h || !out || n < 0) return ELBM_E_INVAL;
     if (!h->p.profile) return ELBM_E_STATE;
-    double v[8] = {h->pass_ms[0], h->pass_ms[1], h->pass_ms[2], h->pass_ms[3], h->prof_steps,
-                   h->prof_collide, h->prof_sweeps, h->launches};
-    for (int i = 0; i < n && i < 8; i++) out[i] = v[i];
+    double v[9] = {h->pass_ms[0], h->pass_ms[1], h->pass_ms[2], h->pass_ms[3], h->prof_steps,
+                   h->prof_collide, h->prof_sweeps, h->launches, h->mlp_ms};
+    for (int i = 0; i < n && i < 9; i++) out[i] = v[i];
     return ELBM_OK;
 }
 
