@@ -298,25 +298,18 @@ def train_proposal(args):
 # ---------------------------------------------------------------------------
 # the headline: config 4
 # ---------------------------------------------------------------------------
-def bytes_per_site_collide(learned):
+def bytes_per_site_collide():
     """Algorithmic bytes of one collision launch per site, BF16 storage:
     populations read and written (2 x 19 x 2), the reference-density plane
     read and written (2 x 4), the psi, phi and q planes read (3 x 4), the
-    node-kind mask (1), and in learned mode the network output (4)."""
-    return 2 * 19 * 2 + 2 * 4 + 3 * 4 + 1 + (4 if learned else 0)
-
-
-def bytes_per_site_mlp():
-    """The learned-proposal pass: populations and reference densities read
-    (19 x 2 + 4), mask (1), network output written (4)."""
-    return 19 * 2 + 4 + 1 + 4
+    node-kind mask (1). (The learned proposal runs inside this kernel.)"""
+    return 2 * 19 * 2 + 2 * 4 + 3 * 4 + 1
 
 
 def run_headline(args, rank, world, local_rank, theta):
     import torch
     N = sites(JET4_SHAPE)
     from paper_1612_05404_gb300 import elbm
-    learned = args.alpha_mode == "learned"
     cfg, fields = jet_case(JET4_SHAPE, alpha_mode=args.alpha_mode, theta=theta)
     sim = elbm.Sim(cfg, fields)
     for _ in range(args.warmup):
@@ -351,7 +344,6 @@ def roofline(args, theta):
     average launch time against its algorithmic bytes."""
     from paper_1612_05404_gb300 import elbm
     N = sites(JET4_SHAPE)
-    learned = args.alpha_mode == "learned"
     cfg, fields = jet_case(JET4_SHAPE, alpha_mode=args.alpha_mode, theta=theta, graph=0, profile=1)
     sim = elbm.Sim(cfg, fields)
     sim.step(max(args.warmup, 3))
@@ -362,9 +354,8 @@ def roofline(args, theta):
     sim.close()
     d = {k: p1[k] - p0[k] for k in p0}
     launches = d["collide_launches"]
-    mlp_ms = d["mlp_ms"] / max(launches, 1)
-    coll_ms = (d["collide_ms"] - d["mlp_ms"]) / max(launches, 1)  # the collision kernel (+ the tiny finalize)
-    bs = bytes_per_site_collide(learned)
+    coll_ms = d["collide_ms"] / max(launches, 1)  # the collision kernel (+ the tiny diagnostics finalize)
+    bs = bytes_per_site_collide()
     achieved = N * bs / (coll_ms * 1e-3) / 1e9
     peak, kind = peaks()
     tot = d["moments_ms"] + d["poisson_ms"] + d["collide_ms"] + d["reduce_ms"]
@@ -376,14 +367,10 @@ def roofline(args, theta):
            "bytes_per_site": bs, "avg_launch_ms": coll_ms,
            "timed": "256x256x768 jet, steps issued one by one, CUDA events around each pass (profile mode)"}
     shares = {"moments_charge": d["moments_ms"] / tot, "poisson": d["poisson_ms"] / tot,
-              "collide": (d["collide_ms"] - d["mlp_ms"]) / tot, "learned_pass": d["mlp_ms"] / tot}
-    mlp = None
-    if learned:
-        mlp = {"kernel": "k_alpha_mlp", "avg_launch_ms": mlp_ms, "bytes_per_site": bytes_per_site_mlp(),
-               "achieved_gbs": N * bytes_per_site_mlp() / max(mlp_ms * 1e-3, 1e-12) / 1e9}
+              "collide": d["collide_ms"] / tot}
     launches_per_step = d["launches"] / max(d["steps"], 1)
-    return out, shares, mlp, launches_per_step, {k: d[k] / max(d["steps"], 1) for k in
-                                                ("moments_ms", "poisson_ms", "collide_ms", "mlp_ms")}
+    return out, shares, launches_per_step, {k: d[k] / max(d["steps"], 1) for k in
+                                            ("moments_ms", "poisson_ms", "collide_ms")}
 
 
 def e2e_run(args, theta):
@@ -710,12 +697,10 @@ def main():
     }
     if training is not None:
         res["training"] = training
-    roof, shares, mlp, lps, pass_ms = roofline(args, theta)
+    roof, shares, lps, pass_ms = roofline(args, theta)
     res["roofline"] = roof
     res["pass_share"] = shares
     res["pass_ms_per_step"] = pass_ms
-    if mlp is not None:
-        res["learned_pass"] = mlp
     res["gpu_launches"] = int(round(lps * args.steps))
     if not args.no_e2e:
         res["e2e"] = e2e_run(args, theta)

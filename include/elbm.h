@@ -195,10 +195,8 @@ size_t elbm_fields_size(const elbm_handle *h, unsigned mask);
  * measured with CUDA events on the handle's stream around each pass:
  * out[0] moments + charge ms, out[1] Poisson ms, out[2] collision ms,
  * out[3] reductions ms, out[4] steps timed, out[5] collision launches,
- * out[6] Poisson sweeps, out[7] kernel launches of all passes, out[8] the
- * learned-proposal pass alone (part of out[2]; steps issued from the host,
- * graph = 0, only). Writes min(n, 9) values; ELBM_E_STATE when profiling is
- * off. Not part of
+ * out[6] Poisson sweeps, out[7] kernel launches of all passes.
+ * Writes min(n, 8) values; ELBM_E_STATE when profiling is off. Not part of
  * the paper's method: instrumentation for measuring the method's kernels. */
 elbm_status elbm_pass_times(const elbm_handle *h, double *out, int n);
 

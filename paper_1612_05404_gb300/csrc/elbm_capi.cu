@@ -58,9 +58,8 @@ struct elbm_handle {
     int want_graph, graph_tried;  // step graphs requested; capture attempted (on the first elbm_step)
     int n_pre, n_body, n_post; // kernels per graph section (launch accounting)
     double noconv_seen;
-    cudaEvent_t ev[6];         // pass boundaries when profiling ([5]: after the learned-proposal pass)
+    cudaEvent_t ev[5];         // pass boundaries when profiling
     double pass_ms[4];
-    double mlp_ms;             // the learned-proposal pass alone (host-issued profiled steps)
     double prof_steps, prof_collide, prof_sweeps, launches;
     // batch of instances (elbm_batch_create): n_sub > 0
     int n_sub;
@@ -265,7 +264,7 @@ void free_bufs(elbm_handle *h)
     if (h->xtmp) cudaFree(h->xtmp);
     h->xtmp = nullptr;
     if (h->pin) cudaFreeHost(h->pin);
-    for (int i = 0; i < 6; i++)
+    for (int i = 0; i < 5; i++)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     for (int i = 0; i < 2; i++) {
         if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
@@ -411,11 +410,6 @@ elbm_status step_host(elbm_handle *h, bool diag)
         h->launches += enq_shift(h, b, s);
     }
     if (prof) cudaEventRecord(h->ev[2], s);
-    if (h->ph.alpha_mode == ELBM_ALPHA_LEARNED) {
-        h->ops.alpha_mlp(h->g, h->ph, b, h->L, s);
-        h->launches += 1;
-    }
-    if (prof) cudaEventRecord(h->ev[5], s);
     h->ops.collide(h->g, h->ph, b, diag ? 1 : 0, h->L, s);
     h->launches += 1;
     if (prof) cudaEventRecord(h->ev[3], s);
@@ -499,7 +493,7 @@ bool enqueue_step(elbm_handle *h, int parity, cudaStream_t s, int sections, int 
                 n_body += enq_unit(h, b, h->cap2);
                 n_body += enq_check(h, b, h->cap2, FIN_RESID_BODY, cond, 1);
                 ok = cuda_ok(cudaStreamEndCapture(h->cap2, &body));
-                ok = ok && prioritize(body, std::vector<const void *>(h->ops.heavy, h->ops.heavy + 4));
+                ok = ok && prioritize(body, std::vector<const void *>(h->ops.heavy, h->ops.heavy + 5));
             }
             ok = ok && cuda_ok(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
                                                                    cudaStreamSetCaptureDependencies));
@@ -507,10 +501,6 @@ bool enqueue_step(elbm_handle *h, int parity, cudaStream_t s, int sections, int 
         n_post += enq_shift(h, b, s);
     }
     if (sections & 4) {
-        if (h->ph.alpha_mode == ELBM_ALPHA_LEARNED) {
-            h->ops.alpha_mlp(h->g, h->ph, b, h->L, s);
-            n_post += 1;
-        }
         h->ops.collide(h->g, h->ph, b, diag_steps > 0 ? 1 : 0, h->L, s);
         n_post += 1;
         if (diag_steps > 0) n_post += fin(h, b, s, D_NPART, FIN_DIAG, 0, 0, diag_steps);
@@ -589,7 +579,7 @@ bool capture_batch(elbm_handle *B, int parity, cudaGraphExec_t *out, bool prolog
     if (prologue || steps > 1) parity = 1;  // kernel counts belong to the one-step graphs
     ok = cuda_ok(cudaStreamEndCapture(s, &graph)) && ok;
     std::vector<const void *> heavy;
-    for (int i = 0; i < B->n_sub; i++) heavy.insert(heavy.end(), B->sub[i]->ops.heavy, B->sub[i]->ops.heavy + 4);
+    for (int i = 0; i < B->n_sub; i++) heavy.insert(heavy.end(), B->sub[i]->ops.heavy, B->sub[i]->ops.heavy + 5);
     ok = ok && prioritize(graph, heavy);
     if (ok) ok = cuda_ok(cudaGraphInstantiate(out, graph, cudaGraphInstantiateFlagUseNodePriority));
     if (graph) cudaGraphDestroy(graph);
@@ -865,8 +855,7 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
             alloc(&b.uz, (size_t)N * h->sc_bytes);
             alloc(&b.nu, (size_t)N * h->sc_bytes);
         }
-        // alpha plane: stored alpha, or the network output o per site (learned)
-        if (p->store_macro || p->alpha_mode == ELBM_ALPHA_LEARNED) alloc(&b.alpha, (size_t)N * h->sc_bytes);
+        if (p->store_macro) alloc(&b.alpha, (size_t)N * h->sc_bytes);
         // reduced precision: the low part of a root the float-float guard certified
         if (p->store_macro && p->precision != ELBM_PREC_FP64) alloc((void **)&b.alpha_lo, (size_t)N * sizeof(float));
         if (p->alpha_mode == ELBM_ALPHA_LEARNED) {
@@ -944,7 +933,7 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     if (h->nlev > 0) h->tail.top = h->lev[h->lt];
     if (ok && !cuda_ok(cudaMallocHost((void **)&h->pin, (kPinDiag + ELBM_NDIAG) * sizeof(double)))) ok = false;
     if (ok && p->profile)
-        for (int i = 0; i < 6; i++)
+        for (int i = 0; i < 5; i++)
             if (!cuda_ok(cudaEventCreate(&h->ev[i]))) ok = false;
     if (!ok) { free_bufs(h); delete h; return ELBM_E_NOMEM; }
 
@@ -1111,7 +1100,6 @@ elbm_status elbm_step(elbm_handle *h, int nsteps)
             if (!cuda_ok(cudaGraphLaunch(gs[2], h->s))) return ELBM_E_CUDA;
             cudaEventRecord(h->ev[3], h->s);
             cudaEventRecord(h->ev[4], h->s);
-            cudaEventRecord(h->ev[5], h->s);  // (not separated in section graphs)
         } else if (h->use_graph) {
             if (!cuda_ok(cudaGraphLaunch(h->gexec[h->step & 1], h->s))) return ELBM_E_CUDA;
         } else {
@@ -1124,11 +1112,6 @@ elbm_status elbm_step(elbm_handle *h, int nsteps)
             float ms[4];
             for (int k = 0; k < 4; k++) cudaEventElapsedTime(&ms[k], h->ev[k], h->ev[k + 1]);
             for (int k = 0; k < 4; k++) h->pass_ms[k] += ms[k];
-            if (!h->use_graph) {
-                float mm = 0.f;
-                cudaEventElapsedTime(&mm, h->ev[2], h->ev[5]);
-                h->mlp_ms += mm;
-            }
             if (!cuda_ok(cudaMemcpy(h->pin, h->b.scal + S_ITER, sizeof(double), cudaMemcpyDeviceToHost)))
                 return ELBM_E_CUDA;
             h->prof_steps += 1;
@@ -1259,9 +1242,9 @@ elbm_status elbm_pass_times(const elbm_handle *h, double *out, int n)
     if (h && h->n_sub > 0) return ELBM_E_STATE;
     if (!h || !out || n < 0) return ELBM_E_INVAL;
     if (!h->p.profile) return ELBM_E_STATE;
-    double v[9] = {h->pass_ms[0], h->pass_ms[1], h->pass_ms[2], h->pass_ms[3], h->prof_steps,
-                   h->prof_collide, h->prof_sweeps, h->launches, h->mlp_ms};
-    for (int i = 0; i < n && i < 9; i++) out[i] = v[i];
+    double v[8] = {h->pass_ms[0], h->pass_ms[1], h->pass_ms[2], h->pass_ms[3], h->prof_steps,
+                   h->prof_collide, h->prof_sweeps, h->launches};
+    for (int i = 0; i < n && i < 8; i++) out[i] = v[i];
     return ELBM_OK;
 }
 

@@ -80,16 +80,14 @@ struct Ops {
     void (*collide)(const Geom &, const Phys &, const Bufs &, int diag, const Launch &, cudaStream_t);
     // warm start of the Poisson solve: phi <- 2 phi - phi_old, phi_old <- phi
     void (*phi_extrap)(const Geom &, const Bufs &, cudaStream_t);
-    // learned alpha: network output o per site into the alpha plane (NULL for FP64)
-    void (*alpha_mlp)(const Geom &, const Phys &, const Bufs &, const Launch &, cudaStream_t);
     void (*export_pop)(const Geom &, const Bufs &, double *out, const Launch &, cudaStream_t);
     void (*export_gpop)(const Geom &, const Bufs &, double *out, const Launch &, cudaStream_t);
     void (*export_plane)(const void *plane, double *out, long long n, cudaStream_t);
     // out[i] += lo[i] (the low part of a float-float plane)
     void (*add_plane)(const float *lo, double *out, long long n, cudaStream_t);
-    // the site-wide compute kernels (collision variants, learned-alpha pass):
-    // in a batch graph every other kernel runs at a higher priority
-    const void *heavy[4];
+    // the site-wide compute kernels (the collision variants): in a batch
+    // graph every other kernel runs at a higher priority
+    const void *heavy[5];
 };
 
 struct MGLevel;  // elbm_kernels.cuh

@@ -670,7 +670,23 @@ struct GuardEntry {
     float4 res;
 };
 
-template <int PR, int AP>
+// Learned mode (LRN): the proposal's network runs inside the collision, only
+// in the warps that hold a site whose Newton iteration starts from it (S >=
+// 2^-5), with the weights loaded only by blocks that have one; its tiles use
+// the shared memory that the guard queue takes afterwards.
+struct MlpTiles {
+    MlpSmem sm;
+    __nv_bfloat16 xs[4][32 * MLP_XS];
+    float os[4][32];
+};
+// a call, not inlined: the network's fragments stay out of the collision's
+// register allocation, and warps without such a site never enter it
+static __device__ __noinline__ void mlp_warp_call(const MlpSmem *sm, const __nv_bfloat16 *xs, float *o)
+{
+    mlp_warp_bf16(*sm, xs, o);
+}
+
+template <int PR, int AP, bool LRN>
 __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC_FP64) ? 1 : 5) k_collide(Geom g, Phys ph, Bufs b, int diag)
 {
     typedef Tr<PR> T;
@@ -679,7 +695,11 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
     typedef typename T::st st;
     typedef typename T::gt gt;
     constexpr bool kQueue = AP == ELBM_APREC_FP32 && sizeof(ct) == 4;
-    __shared__ GuardEntry gq[kQueue ? kGuardQ : 1];
+    static_assert(!LRN || (sizeof(ct) == 4 && AP != ELBM_APREC_FP64), "the learned start needs FP32 arithmetic");
+    constexpr size_t kQBytes = sizeof(GuardEntry) * (kQueue ? kGuardQ : 1);
+    constexpr size_t kSmem = (LRN && sizeof(MlpTiles) > kQBytes) ? sizeof(MlpTiles) : kQBytes;
+    __shared__ __align__(16) unsigned char smem[kSmem];
+    GuardEntry *gq = reinterpret_cast<GuardEntry *>(smem);
     __shared__ int gq_n;
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     if (kQueue) {
@@ -702,9 +722,43 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
     float esum = 0.f;  // rounding scale of the FP32 momentum (deviation modes)
     ct alpha = ct(2);
     float alpha_lo = 0.f;  // low part of a guarded root
+    // FP32 alpha: its setup (carried across the network's barrier in learned mode)
+    AlphaSetupF ast;
+    bool need_mlp = false;
     float a_herr = 0.f;
     int a_status = 0, a_guard = 0, a_lfall = 0;
     int gslot = -1;
+    // the FP32 Newton root from a_start (< 0: the moment-series start); a
+    // lane whose root needs the float-float guard queues its inputs
+    // (deviation modes: f holds d_p, D the FP32 Delta)
+    auto solve_alpha = [&](float a_start) {
+        if constexpr (sizeof(ct) == 4) {
+            float ff[Q];  // the FP32 populations w + d
+#pragma unroll
+            for (int p = 0; p < Q; p++) ff[p] = float(wq(p)) + f[p];
+            if constexpr (LRN) {  // x_p = Delta_p / f_p again, rather than kept across the barrier
+#pragma unroll
+                for (int p = 0; p < Q; p++) ast.x[p] = __fdividef(D[p], ff[p]);
+            }
+            AlphaOutF ao = alpha_fp32_solve(ff, D, f, float(r), ast, AP == ELBM_APREC_FP32, a_start, kQueue);
+            alpha = ct(ao.alpha);
+            alpha_lo = ao.alpha_lo;
+            a_herr = ao.herr;
+            a_status = ao.status;
+            a_guard = ao.guarded;
+            a_lfall = LRN && ao.status == 0 && ao.iters > 1;
+            if (kQueue && ao.guarded == 2) {
+                a_guard = 1;
+                gslot = atomicAdd(&gq_n, 1);  // < kGuardQ: one entry per thread
+                GuardEntry &e = gq[gslot];
+#pragma unroll
+                for (int p = 0; p < Q; p++) e.dev[p] = f[p];
+                e.a = ao.alpha;
+                e.amax = ast.amax;
+                e.S = ast.S;
+            }
+        }
+    };
     if (active) {
         nbr_init(n, g, x, y, z, s);
         const sc *phi = (const sc *)b.phi;
@@ -788,7 +842,7 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
 
         // Eq. (entropic)
         if (ph.alpha_mode != ELBM_ALPHA_BGK) {
-            if (sizeof(ct) == 8 || AP == ELBM_APREC_FP64) {
+            if constexpr (sizeof(ct) == 8 || AP == ELBM_APREC_FP64) {
                 double fd[Q], dd[Q];
 #pragma unroll
                 for (int p = 0; p < Q; p++) {
@@ -800,41 +854,47 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
                 a_herr = float(ao.herr);
                 a_status = ao.status;
             } else {
-                float ff[Q], dd[Q], fv[Q];
+                float ff[Q];  // the FP32 populations w + d
 #pragma unroll
-                for (int p = 0; p < Q; p++) {
-                    ff[p] = float(wq(p)) + float(f[p]);
-                    dd[p] = float(D[p]);
-                    fv[p] = float(f[p]);
-                }
-                AlphaSetupF ast;
+                for (int p = 0; p < Q; p++) ff[p] = float(wq(p)) + f[p];
                 const float umax = fmaxf(fabsf(float(ux)), fmaxf(fabsf(float(uy)), fabsf(float(uz))));
-                alpha_fp32_setup(ff, dd, fv, float(r), float(drho), ph.cf.eq_tol,
+                alpha_fp32_setup(ff, D, f, float(r), float(drho), ph.cf.eq_tol,
                                  u_err_bound(esum, float(r), umax), umax, ast);
-                // learned proposal: alpha_c + S^3 o, o from the network pass
-                float a_start = -1.f;
-                const bool learned = ph.alpha_mode == ELBM_ALPHA_LEARNED;
-                if (learned && ast.S >= 0x1p-5f)
-                    a_start = ast.ac + ast.S * ast.S * ast.S * float(((const sc *)b.alpha)[s]);
-                AlphaOutF ao = alpha_fp32_solve(ff, dd, fv, float(r), ast, AP == ELBM_APREC_FP32, a_start, kQueue);
-                alpha = ct(ao.alpha);
-                alpha_lo = ao.alpha_lo;
-                a_herr = ao.herr;
-                a_status = ao.status;
-                a_guard = ao.guarded;
-                a_lfall = learned && ao.status == 0 && ao.iters > 1;
-                if (kQueue && ao.guarded == 2) {
-                    a_guard = 1;
-                    gslot = atomicAdd(&gq_n, 1);  // < kGuardQ: one entry per thread
-                    GuardEntry &e = gq[gslot];
-#pragma unroll
-                    for (int p = 0; p < Q; p++) e.dev[p] = fv[p];
-                    e.a = ao.alpha;
-                    e.amax = ast.amax;
-                    e.S = ast.S;
+                if constexpr (LRN) {
+                    // the proposal alpha_c + S^3 o is the start where S >= 2^-5
+                    need_mlp = ast.status == 0 && ast.S >= 0x1p-5f;
+                    if (need_mlp)
+                        mlp_site_features(ast.x, ast.S, reinterpret_cast<MlpTiles *>(smem)->xs[tid >> 5] +
+                                                            (tid & 31) * MLP_XS);
+                } else {
+                    solve_alpha(-1.f);
                 }
             }
         }
+    }
+    if constexpr (LRN) {
+        // the block's sites that start from the proposal: the network for
+        // the warps that hold one
+        MlpTiles &mt = *reinterpret_cast<MlpTiles *>(smem);
+        float o = 0.f;
+        if (__syncthreads_or(need_mlp ? 1 : 0)) {
+            const uint4 *src = (const uint4 *)b.mlpimg;
+            uint4 *dst = (uint4 *)&mt.sm;
+            for (int i = tid; i < (int)(sizeof(MlpSmem) / 16); i += blockDim.x * blockDim.y) dst[i] = src[i];
+            __syncthreads();
+            if (__any_sync(0xffffffffu, need_mlp)) {
+                __nv_bfloat16 *row = mt.xs[tid >> 5] + (tid & 31) * MLP_XS;
+                if (!need_mlp)
+#pragma unroll
+                    for (int c = 0; c < 32; c += 2) *reinterpret_cast<unsigned *>(row + c) = 0u;
+                __syncwarp();
+                mlp_warp_call(&mt.sm, mt.xs[tid >> 5], mt.os[tid >> 5]);
+                o = mt.os[tid >> 5][tid & 31];
+            }
+        }
+        __syncthreads();  // the tiles' memory becomes the guard queue
+        if (active && ph.alpha_mode != ELBM_ALPHA_BGK)
+            solve_alpha(need_mlp ? ast.ac + ast.S * ast.S * ast.S * o : -1.f);
     }
     if (kQueue) {
         static_assert(!kQueue || kGuardQ >= 128, "one guard-queue entry per thread of a 128-thread block");
@@ -988,66 +1048,6 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
     }
 }
 
-// ===========================================================================
-// Learned alpha: the network output o of every fluid site, from the same
-// pulled populations, Delta and x_p = Delta_p / f_p as the collision computes
-// (FP32 arithmetic), into the alpha plane; BF16 tensor-core inference per warp
-// (elbm_mlp.cuh). The block copies the handle's BF16 image of the network to
-// shared memory. Every lane of a warp takes part in the warp's network pass.
-// ===========================================================================
-template <int PR>
-__global__ void __launch_bounds__(128) k_alpha_mlp(Geom g, Phys ph, Bufs b)
-{
-    typedef Tr<PR> T;
-    typedef typename T::ct ct;
-    typedef typename T::sc sc;
-    __shared__ MlpSmem sm;
-    __shared__ __align__(16) __nv_bfloat16 xs[4][32 * MLP_XS];
-    __shared__ float os[4][32];
-    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-    {
-        const uint4 *src = (const uint4 *)b.mlpimg;
-        uint4 *dst = (uint4 *)&sm;
-        for (int i = tid; i < (int)(sizeof(MlpSmem) / 16); i += blockDim.x * blockDim.y) dst[i] = src[i];
-    }
-    __syncthreads();
-    const int w = tid >> 5, lane = tid & 31;
-    int x, y, z;
-    bool inb;
-    ll s;
-    site_xyz(g, x, y, z, inb, s);
-    const bool active = inb && (!b.mask || b.mask[s] == ELBM_NODE_FLUID);
-    __nv_bfloat16 *row = xs[w] + lane * MLP_XS;
-    if (active) {
-        Nbr n;
-        nbr_init(n, g, x, y, z, s);
-        float f[Q];
-#pragma unroll
-        for (int p = 0; p < Q; p++) f[p] = float(gather_pop<PR>(g, b.mask, b.fA, n, p, b.rA));
-        float rs, rs_lo, jx, jy, jz, esum;
-        moments_dev(f, rs, rs_lo, jx, jy, jz, esum);
-        const float r = 1.f + rs;
-        const float ir = 1.f / r;
-        const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
-        const float usq = ux * ux + uy * uy + uz * uz;
-        float D[Q], xv[Q];
-        delta_dev(f, rs, rs_lo, r, ux, uy, uz, usq, D);
-        float S = 0.f;
-#pragma unroll
-        for (int p = 0; p < Q; p++) {
-            xv[p] = __fdividef(D[p], float(wq(p)) + f[p]);
-            S = fmaxf(S, fabsf(xv[p]));
-        }
-        mlp_site_features(xv, S > 0.f ? S : 1.f, row);
-    } else {
-#pragma unroll
-        for (int c = 0; c < 32; c += 2) *reinterpret_cast<unsigned *>(row + c) = 0u;
-    }
-    __syncwarp();
-    mlp_warp_bf16(sm, xs[w], os[w]);
-    if (active) ((sc *)b.alpha)[s] = sc(os[w][lane]);
-}
-
 // Warm start of the Poisson solve by linear extrapolation in time,
 // phi <- 2 phi(t-1) - phi(t-2); the first call (no phi(t-2) yet, flag set by
 // the following pre-solve test) only records phi(t-1). Solid (conductor)
@@ -1162,20 +1162,25 @@ struct Launchers {
     }
     static void collide(const Geom &g, const Phys &ph, const Bufs &b, int diag, const Launch &L, cudaStream_t s)
     {
-        if (PR == ELBM_PREC_FP64 || ph.aprec == ELBM_APREC_FP64)
-            k_collide<PR, ELBM_APREC_FP64><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
-        else if (ph.aprec == ELBM_APREC_FP32_FAST)
-            k_collide<PR, ELBM_APREC_FP32_FAST><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
-        else
-            k_collide<PR, ELBM_APREC_FP32><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
+        const bool lrn = ph.alpha_mode == ELBM_ALPHA_LEARNED;
+        if constexpr (PR == ELBM_PREC_FP64) {
+            k_collide<PR, ELBM_APREC_FP64, false><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
+        } else {
+            if (ph.aprec == ELBM_APREC_FP64)
+                k_collide<PR, ELBM_APREC_FP64, false><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
+            else if (ph.aprec == ELBM_APREC_FP32_FAST && lrn)
+                k_collide<PR, ELBM_APREC_FP32_FAST, true><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
+            else if (ph.aprec == ELBM_APREC_FP32_FAST)
+                k_collide<PR, ELBM_APREC_FP32_FAST, false><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
+            else if (lrn)
+                k_collide<PR, ELBM_APREC_FP32, true><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
+            else
+                k_collide<PR, ELBM_APREC_FP32, false><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
+        }
     }
     static void phi_extrap(const Geom &g, const Bufs &b, cudaStream_t s)
     {
         k_phi_extrap<sc><<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>((sc *)b.phi, (sc *)b.phi_old, b.scal, g.N);
-    }
-    static void alpha_mlp(const Geom &g, const Phys &ph, const Bufs &b, const Launch &L, cudaStream_t s)
-    {
-        if (PR != ELBM_PREC_FP64) k_alpha_mlp<PR><<<L.grid, L.block, 0, s>>>(g, ph, b);
     }
     static void export_pop(const Geom &g, const Bufs &b, double *out, const Launch &L, cudaStream_t s)
     {
@@ -1204,15 +1209,19 @@ struct Launchers {
         o.resid = resid;
         o.phi_mean = phi_mean;
         o.collide = collide;
-        o.alpha_mlp = PR == ELBM_PREC_FP64 ? nullptr : alpha_mlp;
         o.phi_extrap = phi_extrap;
         o.export_pop = export_pop;
         o.export_gpop = export_gpop;
         o.export_plane = export_plane;
-        o.heavy[0] = (const void *)k_collide<PR, ELBM_APREC_FP64>;
-        o.heavy[1] = (const void *)k_collide<PR, ELBM_APREC_FP32>;
-        o.heavy[2] = (const void *)k_collide<PR, ELBM_APREC_FP32_FAST>;
-        o.heavy[3] = PR == ELBM_PREC_FP64 ? nullptr : (const void *)k_alpha_mlp<PR>;
+        o.heavy[0] = (const void *)k_collide<PR, ELBM_APREC_FP64, false>;
+        if constexpr (PR == ELBM_PREC_FP64) {
+            o.heavy[1] = o.heavy[2] = o.heavy[3] = o.heavy[4] = nullptr;
+        } else {
+            o.heavy[1] = (const void *)k_collide<PR, ELBM_APREC_FP32, false>;
+            o.heavy[2] = (const void *)k_collide<PR, ELBM_APREC_FP32_FAST, false>;
+            o.heavy[3] = (const void *)k_collide<PR, ELBM_APREC_FP32, true>;
+            o.heavy[4] = (const void *)k_collide<PR, ELBM_APREC_FP32_FAST, true>;
+        }
         return o;
     }
 };

@@ -98,8 +98,9 @@ __device__ __forceinline__ unsigned lds32(const __nv_bfloat16 *p)
 // outputs (shared memory). Every lane of the warp must call it.
 __device__ __forceinline__ void mlp_warp_bf16(const MlpSmem &sm, const __nv_bfloat16 *xs, float *o)
 {
-    const int lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
+    unsigned lane;  // the lane in the warp (not threadIdx.x: blocks may be two-dimensional)
+    asm("mov.u32 %0, %%laneid;" : "=r"(lane));
+    const int g = int(lane >> 2), t = int(lane & 3);
 #pragma unroll 1
     for (int mt = 0; mt < 2; mt++) {
         const __nv_bfloat16 *xr0 = xs + (mt * 16 + g) * MLP_XS;

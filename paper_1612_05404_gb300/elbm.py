@@ -365,12 +365,12 @@ class Sim:
         return self.fields(sel)
 
     def pass_times(self) -> dict:
-        out = (ctypes.c_double * 9)()
-        rc = lib().elbm_pass_times(self.h, out, 9)
+        out = (ctypes.c_double * 8)()
+        rc = lib().elbm_pass_times(self.h, out, 8)
         if rc != OK:
             raise ElbmError(rc, "elbm_pass_times")
         keys = ["moments_ms", "poisson_ms", "collide_ms", "reduce_ms", "steps", "collide_launches",
-                "sweeps", "launches", "mlp_ms"]
+                "sweeps", "launches"]
         return dict(zip(keys, list(out)))
 
     def diag(self) -> dict:

@@ -216,3 +216,45 @@ def test_learned_alpha_in_the_step_keeps_parity_and_h_error():
         assert dg["max_h_error"] <= 1e-10 and dg["n_guard_failed"] == 0, dg
         assert 0 <= dg["n_learned_fallback"] <= 16 ** 3
     g.close()
+
+
+@pytest.mark.parametrize("autotune", [0, 1])
+def test_fused_learned_start_equals_alpha_eval(autotune):
+    """The learned proposal runs inside the collision, only in warps with a
+    site that starts from it (S >= 2^-5). The alpha it gives must be the
+    alpha that elbm_alpha_eval computes with the same network on the same
+    populations (the same Delta, proposal and Newton iteration), bit for bit,
+    whatever block shape the launch uses (autotune picks among 128x1 ..
+    8x16; warps of two-dimensional blocks span several rows); only a root
+    the float-float guard took may differ in its last bits (the collision
+    sums the guard's pairs over groups of 1 to 8 lanes, elbm_alpha_eval on
+    one), and it still solves the exact equation to 1e-10 rho."""
+    torch = _torch()
+    from paper_1612_05404_gb300 import elbm
+    cfg, fields = W.drop_in_field(E0=1e-3, n=24, radius=6.5, precision="fp32")
+    cfg.update(store_macro=1, alpha_precision="fp32", autotune=autotune)
+    theta = _cuda(OM.init_params(11)) * 0.3
+    g = elbm.Sim(dict(cfg, alpha_mode="learned", mlp=theta), fields)
+    g.step(4)
+    f = g.get("f").reshape(19, -1)
+    g.step(1)
+    a_step = g.get("alpha")
+    dg = g.diag()
+    g.close()
+    d = _cuda((f - W.D3Q19_WEIGHTS[:, None]).astype(np.float32))
+    a, he, st, _ = elbm.alpha_eval(d, aprec="fp32", eq_tol=cfg["alpha_eq_tol"], mlp=theta)
+    a = a.cpu().numpy()
+    st = st.cpu().numpy()
+    _, S = elbm.alpha_features(d)
+    hard = S.cpu().numpy() >= 2 ** -5
+    assert hard.sum() > 100  # sites that start from the network
+    diff = np.flatnonzero(a_step != a)
+    assert len(diff) <= dg["n_guarded"], (len(diff), dg["n_guarded"])
+    fx = W.D3Q19_WEIGHTS[:, None] + (f - W.D3Q19_WEIGHTS[:, None]).astype(np.float32).astype(np.float64)
+    c, _, _ = oracle.lattice(3)
+    for i in diff:
+        rho = fx[:, i].sum()
+        D = oracle.feq(3, rho, (c.T @ fx[:, i]) / rho) - fx[:, i]
+        for al in (a_step[i], a[i]):
+            assert abs(oracle.h(3, fx[:, i], D, al)) / rho <= 1e-10, (i, al)
+    assert dg["max_h_error"] <= 1e-10 and dg["n_guard_failed"] == 0
