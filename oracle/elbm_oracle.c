@@ -542,11 +542,11 @@ static int has_dirichlet(const ctx_t *C, const unsigned char *mask)
  * the arithmetic mean of eps on each face) and its reference norm. */
 static void pois_residual(const ctx_t *C, const unsigned char *mask, const double *eps,
                           const double *qn, double qmean, const double *phi, double *rn,
-                          double *ref)
+                          double *ref, double *t3 /* 3N scratch: per site r^2, q^2, b^2 */)
 {
-    double *t3 = calloc(3 * C->N, sizeof(double));  /* per site r^2, q^2, b^2 */
 #pragma omp parallel for schedule(static)
     for (long s = 0; s < C->N; s++) {
+        t3[3 * s] = t3[3 * s + 1] = t3[3 * s + 2] = 0.0;
         if (mask[s] == ORC_SOLID) continue;
         int x, y, z;
         coords(C, s, &x, &y, &z);
@@ -570,7 +570,6 @@ static void pois_residual(const ctx_t *C, const unsigned char *mask, const doubl
         if (mask[s] == ORC_FLUID) q2 += t3[3 * s + 1];
         b2 += t3[3 * s + 2];
     }
-    free(t3);
     *rn = sqrt(r2);
     *ref = sqrt(q2) + sqrt(b2);
 }
@@ -589,6 +588,7 @@ int orc_poisson_solve(const orc_params *p, const unsigned char *mask, const doub
     ctx_t C;
     ctx_init(&C, p);
     double *eps = malloc(C.N * sizeof(double));
+    double *t3 = malloc(3 * C.N * sizeof(double));
 #pragma omp parallel for schedule(static)
     for (long s = 0; s < C.N; s++) eps[s] = eps_of(p, rho[s]);
     double w = p->sor_omega, rn = 0.0, ref = 0.0;
@@ -597,7 +597,7 @@ int orc_poisson_solve(const orc_params *p, const unsigned char *mask, const doub
         if (p->poisson_fixed_sweeps > 0) {
             if (k >= p->poisson_fixed_sweeps) break;
         } else {
-            pois_residual(&C, mask, eps, qn, qmean, phi, &rn, &ref);
+            pois_residual(&C, mask, eps, qn, qmean, phi, &rn, &ref, t3);
             if (rn <= p->poisson_tol * ref || k >= p->poisson_maxit) break;
         }
         /* the sites of one colour read only the other colour */
@@ -635,10 +635,11 @@ int orc_poisson_solve(const orc_params *p, const unsigned char *mask, const doub
         for (long s = 0; s < C.N; s++)
             if (mask[s] != ORC_SOLID) phi[s] -= m;
     }
-    pois_residual(&C, mask, eps, qn, qmean, phi, &rn, &ref);
+    pois_residual(&C, mask, eps, qn, qmean, phi, &rn, &ref, t3);
     if (iters) *iters = k;
     if (resid) *resid = ref > 0.0 ? rn / ref : rn;
     free(eps);
+    free(t3);
     return 0;
 }
 

@@ -75,6 +75,18 @@ struct elbm_handle {
 
 namespace {
 
+// The potential for the caller: with the deviation form the plane holds
+// psi = phi - phi_lin; add the linear electrode profile back at non-solid
+// nodes (solid nodes keep the plane's value, as without it)
+__global__ void k_add_profile(double *out, Geom g, double phi_lo, double slope, const unsigned char *mask)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    if (mask && mask[i] == ELBM_NODE_SOLID) return;
+    const long long c = g.phi_axis == 0 ? i % g.nx : (g.phi_axis == 1 ? (i / g.nx) % g.ny : i / ((long long)g.nx * g.ny));
+    out[i] += phi_lo + double(c + 1) * slope;
+}
+
 // BF16 image of the learned proposal's network (shared-memory layout of
 // elbm_mlp.cuh) from the caller's FP32 parameters, made once at elbm_init
 __global__ void k_mlp_image(const float *th, MlpSmem *img)
@@ -704,6 +716,10 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     for (int a = 0; a < 3; a++) g.per[a] = p->face_bc[2 * a] == ELBM_FACE_PERIODIC;
     for (int f = 0; f < 6; f++) g.phi_kind[f] = p->phi_bc[f];
     g.phi_axis = p->phi_axis;
+    // reduced precision: the potential plane holds its deviation from the
+    // linear profile between the electrodes (both faces of phi_axis Dirichlet)
+    g.phi_lin = p->precision != ELBM_PREC_FP64 && p->charge_model != ELBM_CHARGE_NONE &&
+                p->phi_bc[2 * p->phi_axis] == ELBM_PHI_DIRICHLET && p->phi_bc[2 * p->phi_axis + 1] == ELBM_PHI_DIRICHLET;
 
     long long n_fluid = N, n_solid = 0;
     if (in->mask) {
@@ -1183,10 +1199,13 @@ elbm_status elbm_fields(elbm_handle *h, unsigned mask, double *out, size_t out_l
     double *tmp = need ? h->xtmp : nullptr;
     elbm_status st = ELBM_OK;
     size_t off = 0;
-    auto plane = [&](const void *src, const float *lo = nullptr) {
+    auto plane = [&](const void *src, const float *lo = nullptr, bool profile = false) {
         if (st != ELBM_OK) return;
         h->ops.export_plane(src, tmp, N, h->s);
         if (lo) h->ops.add_plane(lo, tmp, N, h->s);
+        if (profile && h->g.phi_lin)
+            k_add_profile<<<(unsigned)((N + 255) / 256), 256, 0, h->s>>>(tmp, h->g, h->ph.cd.phi_lo, h->ph.cd.phi_slope,
+                                                                        h->b.mask);
         if (!cuda_ok(cudaMemcpyAsync(out + off, tmp, N * sizeof(double), cudaMemcpyDeviceToHost, h->s)) ||
             !cuda_ok(cudaStreamSynchronize(h->s)))
             st = ELBM_E_CUDA;
@@ -1206,7 +1225,7 @@ elbm_status elbm_fields(elbm_handle *h, unsigned mask, double *out, size_t out_l
         std::free(buf);
         off += 3 * N;
     }
-    if (mask & ELBM_F_PHI) plane(h->b.phi);
+    if (mask & ELBM_F_PHI) plane(h->b.phi, nullptr, true);
     if (mask & ELBM_F_Q) plane(h->b.q);
     if (mask & ELBM_F_ALPHA) plane(h->b.alpha, h->b.alpha_lo);
     if (mask & ELBM_F_NU) plane(h->b.nu);

@@ -78,6 +78,8 @@ struct Geom {
     int phi_kind[6];     // ELBM_PHI_* per face
     int phi_axis;
     int has_mask;        // any non-fluid node
+    int phi_lin;         // the potential plane holds psi = phi - phi_lin, phi_lin(c) = phi_lo + (c+1) slope
+                         // along phi_axis (reduced precision, both electrode faces Dirichlet)
 };
 
 // Constants of one step in the arithmetic type T, precomputed on the host so

@@ -268,21 +268,48 @@ __device__ __forceinline__ int block_id() { return blockIdx.x + gridDim.x * (blo
 
 // Potential of the face neighbour along +-axis (Sec. II Poisson problem):
 // kind 0 = unknown (index in *nb), 1 = Dirichlet value in *v, 2 = no term.
+// With the deviation form (g.phi_lin) the plane holds psi = phi - phi_lin,
+// phi_lin the linear electrode profile along phi_axis: a Dirichlet value is
+// returned as psi (0 on every electrode or lateral Dirichlet face, which
+// carry phi_lin; phi_solid - phi_lin at a conductor) and *dl is
+// phi_lin(neighbour) - phi_lin(site) (+-slope along phi_axis, else 0), which
+// the caller adds to the neighbour's psi: every face term c (phi_nb - phi_s)
+// is then c (psi_nb + dl - psi_s), the same difference formed from small
+// numbers. Without it *dl = 0 and the plane holds phi.
 template <typename T>
 __device__ __forceinline__ int pois_nb(const Geom &g, const Cst<T> &k, const unsigned char *mask,
-                                       const Nbr &n, int x, int y, int z, int axis, int sign, int *nb, T *v)
+                                       const Nbr &n, int x, int y, int z, int axis, int sign, int *nb, T *v, T *dl)
 {
     int o[3] = {0, 0, 0};
     o[axis] = sign;
     const int i = nbr_idx(n, g, o[0], o[1], o[2]);
+    const bool lin = g.phi_lin != 0;
+    *dl = (lin && axis == g.phi_axis) ? T(sign) * k.phi_slope : T(0);
     if (i < 0) {
         int face = 2 * axis + (sign > 0 ? 1 : 0);
-        if (g.phi_kind[face] == ELBM_PHI_DIRICHLET) { *v = phi_ghost<T>(g, k, face, x, y, z); return 1; }
+        if (g.phi_kind[face] == ELBM_PHI_DIRICHLET) { *v = lin ? T(0) : phi_ghost<T>(g, k, face, x, y, z); return 1; }
+        *dl = T(0);
         return 2;
     }
-    if (mask && mask[i] == ELBM_NODE_SOLID) { *v = k.phi_solid; return 1; }
+    if (mask && mask[i] == ELBM_NODE_SOLID) {
+        if (lin) {
+            const int c = (g.phi_axis == 0 ? x : (g.phi_axis == 1 ? y : z)) + (axis == g.phi_axis ? sign : 0);
+            *v = k.phi_solid - (k.phi_lo + T(c + 1) * k.phi_slope);
+        } else {
+            *v = k.phi_solid;
+        }
+        return 1;
+    }
     *nb = i;
     return 0;
+}
+// phi_lin at the site (0 without the deviation form)
+template <typename T>
+__device__ __forceinline__ T phi_lin_at(const Geom &g, const Cst<T> &k, int x, int y, int z)
+{
+    if (!g.phi_lin) return T(0);
+    const int c = g.phi_axis == 0 ? x : (g.phi_axis == 1 ? y : z);
+    return k.phi_lo + T(c + 1) * k.phi_slope;
 }
 
 template <typename T> __device__ __forceinline__ T scal_of(const Bufs &b, int i);
@@ -393,10 +420,16 @@ __global__ void __launch_bounds__(128) k_moments(Geom g, Phys ph, Bufs b)
     if (active) {
         Nbr n;
         nbr_init(n, g, x, y, z, s);
-        ct rs = 0;
+        ct rs = 0, rs_lo = 0;
 #pragma unroll
-        for (int p = 0; p < Q; p++) rs += gather_pop<PR>(g, b.mask, b.fA, n, p, b.rA);
-        ((sc *)b.rho)[s] = sc(T::dev ? ct(1) + rs : rs);
+        for (int p = 0; p < Q; p++) {
+            const ct v = gather_pop<PR>(g, b.mask, b.fA, n, p, b.rA);
+            // deviations: a compensated sum (at the vapour density sum d ~ -0.84
+            // and its rounding would be ~6x larger relative to rho ~ 0.16)
+            if constexpr (T::dev) two_sum_acc(v, rs, rs_lo);
+            else rs += v;
+        }
+        ((sc *)b.rho)[s] = sc(T::dev ? (ct(1) + rs) + rs_lo : rs);
         if (ph.charge_model == ELBM_CHARGE_TRANSPORT) {
             gt qs = 0;
 #pragma unroll
@@ -555,14 +588,14 @@ __global__ void __launch_bounds__(128) k_sor(Geom g, Phys ph, Bufs b, int color,
 #pragma unroll
         for (int sg = -1; sg <= 1; sg += 2) {
             int nb = 0;
-            sc v = 0;
-            int kk = pois_nb<sc>(g, k, b.mask, n, x, y, z, a, sg, &nb, &v);
+            sc v = 0, dl = 0;
+            int kk = pois_nb<sc>(g, k, b.mask, n, x, y, z, a, sg, &nb, &v, &dl);
             if (kk == 0) {
                 sc ef = sc(0.5) * (es + (sc(1) + k.kap * rho[nb]));
-                num += ef * phi[nb];
+                num += ef * (phi[nb] + dl);
                 den += ef;
             } else if (kk == 1) {
-                num += es * v;
+                num += es * (v + dl);
                 den += es;
             }
         }
@@ -597,22 +630,23 @@ __global__ void __launch_bounds__(128) k_resid(Geom g, Phys ph, Bufs b)
         sc r = kind == ELBM_NODE_FLUID ? qs - scal_of<sc>(b, S_QMEAN) : sc(0);
         sc bs = 0;
         sc ps = phi[s];
+        const sc pl = phi_lin_at<sc>(g, k, x, y, z);
         sc t = fabs(r);
 #pragma unroll
         for (int a = 0; a < 3; a++)
 #pragma unroll
             for (int sg = -1; sg <= 1; sg += 2) {
                 int nb = 0;
-                sc v = 0;
-                int kk = pois_nb<sc>(g, k, b.mask, n, x, y, z, a, sg, &nb, &v);
+                sc v = 0, dl = 0;
+                int kk = pois_nb<sc>(g, k, b.mask, n, x, y, z, a, sg, &nb, &v, &dl);
                 if (kk == 0) {
                     const sc cf = sc(0.5) * (es + (sc(1) + k.kap * rho[nb]));
-                    r += cf * (phi[nb] - ps);
-                    t += cf * (fabs(phi[nb]) + fabs(ps));
+                    r += cf * ((phi[nb] + dl) - ps);
+                    t += cf * (fabs(phi[nb]) + fabs(dl) + fabs(ps));
                 } else if (kk == 1) {
-                    r += es * (v - ps);
-                    bs += es * v;
-                    t += es * (fabs(v) + fabs(ps));
+                    r += es * ((v + dl) - ps);
+                    bs += es * (v + dl + pl);  // the Dirichlet datum itself (reference norm)
+                    t += es * (fabs(v) + fabs(dl) + fabs(ps));
                 }
             }
         r2 = r * r;
@@ -814,12 +848,12 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
 #pragma unroll
                 for (int kk = 0; kk < 2; kk++) {
                     int nb = 0;
-                    ct v = 0;
-                    int kind = pois_nb<ct>(g, k, b.mask, n, x, y, z, a, kk ? 1 : -1, &nb, &v);
-                    pv[kk] = kind == 0 ? ct(phi[nb]) : (kind == 1 ? v : phs);
+                    ct v = 0, dl = 0;
+                    int kind = pois_nb<ct>(g, k, b.mask, n, x, y, z, a, kk ? 1 : -1, &nb, &v, &dl);
+                    pv[kk] = kind == 0 ? ct(phi[nb]) + dl : (kind == 1 ? v + dl : phs);
                     if (tr) {
                         if (kind == 0) Rq += ct(0.5) * (ss + ct(sig[nb])) * (pv[kk] - phs);
-                        else if (kind == 1) Rq += ss * (v - phs);
+                        else if (kind == 1) Rq += ss * (pv[kk] - phs);
                     }
                 }
                 E[a] = -(pv[1] - pv[0]) * ct(0.5) + k.E[a];
@@ -1311,10 +1345,10 @@ __device__ __forceinline__ typename Tr<PR>::sc mg_resid_at(const Geom &g, const 
 #pragma unroll
             for (int sg = -1; sg <= 1; sg += 2) {
                 int nb = 0;
-                T v = 0;
-                const int kk = pois_nb<T>(g, k, bf.mask, n, x, y, z, a, sg, &nb, &v);
-                if (kk == 0) r += T(0.5) * (es + (T(1) + k.kap * rho[nb])) * (phi[nb] - ps);
-                else if (kk == 1) r += es * (v - ps);
+                T v = 0, dl = 0;
+                const int kk = pois_nb<T>(g, k, bf.mask, n, x, y, z, a, sg, &nb, &v, &dl);
+                if (kk == 0) r += T(0.5) * (es + (T(1) + k.kap * rho[nb])) * ((phi[nb] + dl) - ps);
+                else if (kk == 1) r += es * ((v + dl) - ps);
             }
         return r;
     }

@@ -1,0 +1,151 @@
+"""Parity at the benchmarked sizes and launch forms, element by element against
+the FP64 oracle (on all host cores). Each comparison starts the oracle from
+the GPU's own state (populations, charge populations, potential as the warm
+start), so both sides take the same steps from the same inputs:
+
+- the drop in field, four 64^3 lattices (E0 sweep) in one batch with the
+  half-step shift and graphs of ten steps, 20 steps; then three steps of two
+  of the lattices on both sides: density, momentum, potential, charge, alpha;
+- the electrified jet at 128 x 128 x 512 (BF16 storage relative to the site
+  density, multigrid with the nozzle as a conductor): one step from identical
+  populations: density, charge, potential, and the populations it writes
+  (BF16 storage: within 2^-8 of the size of f - w rho);
+- one box of every batched-droplet edge in one batch: three steps, the
+  populations of every box."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1612_05404_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def E():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1612_05404_gb300 import build, elbm
+    build.build()
+    n0 = oracle.set_threads(0)
+    oracle.set_threads(os.cpu_count() or 1)
+    yield elbm
+    oracle.set_threads(n0)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _rho_u(rho, u):
+    return u.reshape(-1, 3) * rho[:, None]
+
+
+def _oracle_from(E, g, cfg, fields, tol=1e-13):
+    """An oracle simulation holding the GPU instance's populations, charge
+    populations (transport mode) and potential. The populations are set
+    again after the oracle's set-up, which writes its own FP64 inlet and
+    outlet equilibria into the links from those nodes (the GPU's inlet nodes
+    hold theirs in the storage precision)."""
+    f = g.get("f")
+    o = oracle.Sim(dict(cfg, poisson_tol=tol), dict(fields, f=f))
+    o.f[:] = f
+    if o.g is not None:
+        o.g[:] = g.get("g")
+    o.phi[:] = g.get("phi")
+    return o
+
+
+def test_drop_in_field_batch_at_full_size(E):
+    """Four 64^3 lattices, FP32, the benchmark's batch form for 20 steps;
+    then E0 = 1e-4 and 1e-3 three steps on both sides. Relative L2: density,
+    potential and charge within 1e-5 (the potential held as its deviation from
+    the electrode profile), momentum within 2e-6, alpha within 2e-5."""
+    sims, cases = [], []
+    for E0 in W.E0_SWEEP:
+        cfg, fields = W.drop_in_field(E0=E0, precision="fp32")
+        cfg.update(alpha_precision="fp32", store_macro=1, autotune=1, poisson_check_every=8)
+        sims.append(E.Sim(cfg, fields))
+        cases.append((cfg, fields))
+    batch = E.Batch(sims, pipeline=True, span=10)
+    assert batch.step(20) >= 0
+    batch.close()
+    errs = {}
+    for i in (0, 3):
+        g, (cfg, fields) = sims[i], cases[i]
+        o = _oracle_from(E, g, cfg, fields, tol=1e-10)
+        for t in range(3):
+            g.step(1)
+            o.step(1)
+            e = dict(rho=rel_l2(g.get("rho"), o.rho), phi=rel_l2(g.get("phi"), o.phi),
+                     rho_u=rel_l2(_rho_u(g.get("rho"), g.get("u")), _rho_u(o.rho, o.u)),
+                     q=rel_l2(g.get("q"), o.q), alpha=rel_l2(g.get("alpha"), o.alpha))
+            errs[(i, t)] = e
+    print("drop 64^3 full size:", {k: {a: f"{b:.1e}" for a, b in v.items()} for k, v in errs.items()})
+    for (i, t), e in errs.items():
+        assert e["rho"] < 1e-5 and e["phi"] < 1e-5, (i, t, e)
+        assert e["rho_u"] < 2e-6 and e["q"] < 1e-5 and e["alpha"] < 2e-5, (i, t, e)
+    for g in sims:
+        d = g.diag()
+        assert d["max_h_error"] <= 1e-10 and d["n_guard_failed"] == 0
+        g.close()
+
+
+def test_jet_bf16_one_step_at_full_size(E):
+    """128 x 128 x 512 jet, BF16: three GPU steps, then one step on both
+    sides from the GPU's populations. The density of those populations within
+    1e-6 (L2, fluid sites), the xi-form charge and the potential within 1e-5
+    (FP32 multigrid stopped at its rounding floor, against SOR to 1e-9); the
+    written populations within 2^-8 of ||f - w rho|| (one BF16 rounding of
+    f - w rho_ref per stored value)."""
+    cfg, fields = W.jet(precision="bf16")
+    cfg.update(alpha_precision="fp32", poisson_solver="mg", store_macro=1)
+    g = E.Sim(cfg, fields)
+    g.step(3)
+    o = _oracle_from(E, g, cfg, fields, tol=1e-9)
+    g.step(1)
+    o.step(1)
+    fluid = o.rho > 0
+    e = dict(rho=rel_l2(g.get("rho")[fluid], o.rho[fluid]), q=rel_l2(g.get("q"), o.q),
+             phi=rel_l2(g.get("phi"), o.phi))
+    fg = g.get("f").reshape(19, -1)
+    fo = o.f.reshape(19, -1)
+    _, w = E.velocity_set()
+    dev = fo - w[:, None] * o.rho[None, :]
+    e["f_vs_dev"] = float(np.linalg.norm(fg - fo) / np.linalg.norm(dev[:, fluid]))
+    d = g.diag()
+    g.close()
+    print("jet 128x128x512 full size:", {k: f"{v:.1e}" for k, v in e.items()})
+    assert e["rho"] <= 1e-6 and e["q"] <= 1e-5 and e["phi"] <= 1e-5, e
+    assert e["f_vs_dev"] <= 2.0 ** -8, e
+    assert d["max_h_error"] <= 1e-10 and d["n_guard_failed"] == 0
+
+
+def test_every_batched_box_edge(E):
+    """One box of each batched-droplet edge (24 .. 96), FP32, one batch with
+    the half-step shift: after three batched steps each box's state goes to
+    the oracle; two more batched steps against two oracle steps: the
+    populations of every box within 3e-6 relative L2 (FP32 deviation
+    storage)."""
+    rng = np.random.default_rng(20161211)
+    sims, cases = [], []
+    for edge in W.BATCH_EDGES:
+        E0, nc = float(rng.uniform(0, 1e-3)), float(rng.uniform(0.5, 1.0))
+        cfg, fields = W.batched_droplet(edge, E0, nc, precision="fp32")
+        cfg.update(alpha_precision="fp32", autotune=1)
+        sims.append(E.Sim(cfg, fields))
+        cases.append((cfg, fields))
+    batch = E.Batch(sims, pipeline=True, span=1)
+    assert batch.step(3) >= 0
+    oracles = [_oracle_from(E, g, cfg, fields, tol=1e-10) for g, (cfg, fields) in zip(sims, cases)]
+    assert batch.step(2) >= 0
+    batch.close()
+    errs = {}
+    for g, o, (cfg, fields) in zip(sims, oracles, cases):
+        o.step(2)
+        errs[cfg["shape"][0]] = rel_l2(g.get("f"), o.f)
+        g.close()
+    print("batched boxes:", {k: f"{v:.1e}" for k, v in errs.items()})
+    assert max(errs.values()) <= 3e-6, errs

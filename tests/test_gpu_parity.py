@@ -260,11 +260,11 @@ def test_fp32_single_step_populations_and_viscosity(E):
 @pytest.mark.parametrize("aprec", ["fp64", "fp32"])
 def test_fp32_parity_multi_step(E, aprec):
     """FP32 against the FP64 oracle over several steps from the same initial
-    fields, relative L2: density and potential within 1e-5 (the first,
-    cold Poisson solve stops at the FP32 floor, ~8e-6), momentum within 2e-6
-    (measured ~4e-7), charge within 5e-5 (a second difference of the FP32
-    potential through the Ohmic source; measured ~1e-5) and the alpha field
-    within 2e-5 (measured ~3e-6 with the FP32 root)."""
+    fields, relative L2: density, potential and charge within 1e-5 (the
+    potential held as its deviation from the electrode profile, so that its
+    FP32 rounding floor and the Ohmic second difference scale with the
+    charge-driven part), momentum within 2e-6 and the alpha field within 2e-5
+    (measured ~3e-6 with the FP32 root)."""
     cfg, fields = W.drop_in_field(E0=1e-3, n=16, radius=4.5, precision="fp32")
     cfg.update(store_macro=1, alpha_precision=aprec)
     g = E.Sim(cfg, fields)
@@ -275,7 +275,7 @@ def test_fp32_parity_multi_step(E, aprec):
         e5 = dict(rho=rel_l2(g.get("rho"), o.rho), phi=rel_l2(g.get("phi"), o.phi))
         assert max(e5.values()) < 1e-5, (t, e5)
         assert rel_l2(_rho_u(g.get("rho"), g.get("u")), _rho_u(o.rho, o.u)) < 2e-6, t
-        assert rel_l2(g.get("q"), o.q) < 5e-5, t
+        assert rel_l2(g.get("q"), o.q) < 1e-5, (t, rel_l2(g.get("q"), o.q))
         assert rel_l2(g.get("alpha"), o.alpha) < 2e-5, t
 
 
