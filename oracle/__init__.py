@@ -40,6 +40,7 @@ _PHI = {"periodic": 0, "dirichlet": 1, "neumann": 2}
 _CHARGE = {"none": 0, "conserved": 1, "xi": 2, "transport": 3}
 _FEL = {"qe": 0, "full": 1}
 _ALPHA = {"entropic": 0, "bgk": 1}
+_EPS_FACE = {"arithmetic": 0, "harmonic": 1}
 
 
 class Params(ctypes.Structure):
@@ -50,7 +51,7 @@ class Params(ctypes.Structure):
         ("charge_model", ctypes.c_int), ("force_el", ctypes.c_int),
         ("neutralize", ctypes.c_int), ("poisson_maxit", ctypes.c_int),
         ("poisson_fixed_sweeps", ctypes.c_int), ("alpha_mode", ctypes.c_int),
-        ("pad0", ctypes.c_int),
+        ("eps_face", ctypes.c_int), ("carreau_lagged", ctypes.c_int), ("pad1", ctypes.c_int),
         ("phi_lo", ctypes.c_double), ("phi_hi", ctypes.c_double),
         ("phi_solid", ctypes.c_double),
         ("nu0", ctypes.c_double), ("nu_inf", ctypes.c_double),
@@ -106,6 +107,8 @@ def lib():
         L.orc_spectral_norm.argtypes = [ctypes.c_int, dp]
         L.orc_spectral_norm.restype = ctypes.c_double
         L.orc_carreau.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
+        L.orc_carreau_lagged.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, dp, dp]
         L.orc_sc_force.argtypes = [pp, u8p, dp, dp]
         L.orc_charge_field.argtypes = [pp, u8p, dp, dp, dp, dp]
         L.orc_poisson_solve.argtypes = [pp, u8p, dp, dp, ctypes.c_double, dp,
@@ -152,6 +155,8 @@ def make_params(cfg: dict) -> Params:
     P.poisson_maxit = cfg["poisson_maxit"]
     P.poisson_fixed_sweeps = cfg["poisson_fixed_sweeps"]
     P.alpha_mode = _ALPHA[cfg["alpha_mode"]]
+    P.eps_face = _EPS_FACE[cfg.get("eps_face", "arithmetic")]
+    P.carreau_lagged = int(cfg.get("carreau_lagged", 0))
     P.phi_lo, P.phi_hi, P.phi_solid = cfg["phi_lo"], cfg["phi_hi"], cfg["phi_solid"]
     P.nu0, P.nu_inf, P.lam, P.n_carreau = cfg["nu0"], cfg["nu_inf"], cfg["lambda"], cfg["n_carreau"]
     P.G, P.Gw, P.rho0 = cfg["G"], cfg["Gw"], cfg["rho0"]
@@ -235,6 +240,17 @@ def carreau(cfg, Pn, a, rho):
     dpt = ctypes.POINTER(ctypes.c_double)
     lib().orc_carreau(ctypes.byref(P), float(Pn), float(a), float(rho),
                       ctypes.cast(ctypes.pointer(g), dpt), ctypes.cast(ctypes.pointer(nu), dpt))
+    return g.value, nu.value
+
+
+def carreau_lagged(cfg, Pn, a, rho, nu_prev):
+    """gdot and nu of the lagged Carreau reading (tau from nu_prev)."""
+    P = make_params(cfg)
+    g = ctypes.c_double()
+    nu = ctypes.c_double()
+    dpt = ctypes.POINTER(ctypes.c_double)
+    lib().orc_carreau_lagged(ctypes.byref(P), float(Pn), float(a), float(rho), float(nu_prev),
+                             ctypes.cast(ctypes.pointer(g), dpt), ctypes.cast(ctypes.pointer(nu), dpt))
     return g.value, nu.value
 
 

@@ -158,6 +158,13 @@ static double sigma_of(const orc_params *p, double rho) /* conductivity per phas
 {
     return p->sigma_gas + (p->sigma_liq - p->sigma_gas) * theta_of(p, rho);
 }
+/* permittivity of the face between two sites: the arithmetic mean (the
+ * default reading), or the harmonic mean (the series value of two half-cells) */
+static double eps_face(const orc_params *p, double ea, double eb)
+{
+    if (p->eps_face == ORC_EPS_FACE_HARMONIC) return 2.0 * ea * eb / (ea + eb);
+    return 0.5 * (ea + eb);
+}
 
 /* ------------------------------------------------------------------------
  * Eq. (2): second-order Mach expansion of the equilibrium.
@@ -389,6 +396,23 @@ int orc_carreau(const orc_params *p, double Pn, double alpha, double rho,
     return it;
 }
 
+/* The lagged reading of the same passage ("a slow variation of nu over the
+ * time step"): Eq. (strain2) evaluated with tau from the previous step's
+ * viscosity, gdot = Pi alpha beta(nu_prev) / (rho c_s^2), no root; then
+ * nu = nu(gdot) by Eq. (carreau). A fixed point of this map is the root of
+ * Eq. (strain2). */
+void orc_carreau_lagged(const orc_params *p, double Pn, double alpha, double rho, double nu_prev,
+                        double *gdot, double *nu)
+{
+    if (p->n_carreau == 1.0 || p->lambda == 0.0 || p->nu0 == p->nu_inf) {
+        *nu = p->nu0;
+        *gdot = Pn * alpha * beta_of(p->nu0) / (rho * CS2);
+        return;
+    }
+    *gdot = Pn * alpha * beta_of(nu_prev) / (rho * CS2);
+    *nu = nu_carreau(p, *gdot);
+}
+
 /* ------------------------------------------------------------------------
  * Shan-Chen force, Eq. (sc). Fluid, inlet and outlet neighbours enter the
  * first sum with their own psi; solid nodes and the nodes beyond a wall face
@@ -556,7 +580,7 @@ static void pois_residual(const ctx_t *C, const unsigned char *mask, const doubl
                 long nb = 0;
                 double v = 0.0;
                 int k = pois_nb(C, mask, x, y, z, a, sg, &nb, &v);
-                if (k == PN_UNKNOWN) r += 0.5 * (eps[s] + eps[nb]) * (phi[nb] - phi[s]);
+                if (k == PN_UNKNOWN) r += eps_face(C->p, eps[s], eps[nb]) * (phi[nb] - phi[s]);
                 else if (k == PN_DIRICHLET) { r += eps[s] * (v - phi[s]); bs += eps[s] * v; }
             }
         t3[3 * s] = r * r;
@@ -614,7 +638,7 @@ int orc_poisson_solve(const orc_params *p, const unsigned char *mask, const doub
                         double v = 0.0;
                         int kk = pois_nb(&C, mask, x, y, z, a, sg, &nb, &v);
                         if (kk == PN_UNKNOWN) {
-                            double ef = 0.5 * (eps[s] + eps[nb]);
+                            double ef = eps_face(p, eps[s], eps[nb]);
                             num += ef * phi[nb];
                             den += ef;
                         } else if (kk == PN_DIRICHLET) {
@@ -668,7 +692,7 @@ int orc_poisson_system(const orc_params *p, const unsigned char *mask, const dou
                 double v = 0.0;
                 int k = pois_nb(&C, mask, x, y, z, a, sg, &nb, &v);
                 if (k == PN_UNKNOWN) {
-                    double ef = 0.5 * (es + eps_of(p, rho[nb]));
+                    double ef = eps_face(p, es, eps_of(p, rho[nb]));
                     A[i * n + i] -= ef;
                     A[i * n + index[nb]] += ef;
                 } else if (k == PN_DIRICHLET) {
@@ -946,6 +970,9 @@ int orc_step(const orc_params *p, const unsigned char *mask, const double *u_in,
     double tau_q = 0.5 + p->Dq / CS2_Q;
 #pragma omp parallel for schedule(static)
     for (long s = 0; s < N; s++) {
+        /* the lagged Carreau reading takes the previous step's viscosity (in
+         * nu_out; 0 before the first step means nu0) */
+        const double nu_prev = nu_out[s] > 0.0 ? nu_out[s] : p->nu0;
         alpha_out[s] = 0.0;
         nu_out[s] = 0.0;
         u[3 * s] = u[3 * s + 1] = u[3 * s + 2] = 0.0;
@@ -990,7 +1017,8 @@ int orc_step(const orc_params *p, const unsigned char *mask, const double *u_in,
                 for (int b2 = 0; b2 < 3; b2++) Pi[3 * a + b2] -= d[k] * C.c[k][a] * C.c[k][b2];
         double Pn = orc_spectral_norm(p->dim, Pi);
         double gdot = 0.0, nu = p->nu0;
-        orc_carreau(p, Pn, alpha, r, &gdot, &nu);
+        if (p->carreau_lagged) orc_carreau_lagged(p, Pn, alpha, r, nu_prev, &gdot, &nu);
+        else orc_carreau(p, Pn, alpha, r, &gdot, &nu);
         double beta = beta_of(nu);
 
         /* Eq. (add): S = feq(rho, u + F/rho) - feq(rho, u) */

@@ -34,6 +34,8 @@ enum { ORC_CHARGE_NONE = 0, ORC_CHARGE_CONSERVED = 1, ORC_CHARGE_XI = 2,
 enum { ORC_FEL_QE = 0, ORC_FEL_FULL = 1 };
 /* relaxation */
 enum { ORC_ALPHA_ENTROPIC = 0, ORC_ALPHA_BGK = 1 };
+/* face permittivity: arithmetic or harmonic mean of the two sites */
+enum { ORC_EPS_FACE_ARITH = 0, ORC_EPS_FACE_HARMONIC = 1 };
 /* alpha status codes */
 enum { ORC_A_ROOT = 0, ORC_A_SHORTCUT = 1, ORC_A_NOROOT = 2, ORC_A_CLIPPED = 3 };
 
@@ -49,7 +51,9 @@ typedef struct orc_params {
     int poisson_maxit;       /* cap on SOR sweeps */
     int poisson_fixed_sweeps;/* >0: run exactly this many sweeps, no test */
     int alpha_mode;          /* ORC_ALPHA_* */
-    int pad0;
+    int eps_face;            /* ORC_EPS_FACE_*: face permittivity of the Poisson operator */
+    int carreau_lagged;      /* 1: gdot from the previous step's nu (no root of Eq. strain2) */
+    int pad1;
     double phi_lo, phi_hi;   /* ghost-plane potentials at axis coord -1, n */
     double phi_solid;        /* potential of interior solid (conductor) nodes */
     double nu0, nu_inf, lambda, n_carreau;   /* Carreau law, Eq. (carreau) */
@@ -83,6 +87,8 @@ double orc_alpha_bisect(int dim, const double *f, const double *delta);
 double orc_spectral_norm(int dim, const double *Pi /* 3x3 row-major */);
 int    orc_carreau(const orc_params *p, double Pi_norm, double alpha, double rho,
                    double *gdot, double *nu);
+void   orc_carreau_lagged(const orc_params *p, double Pi_norm, double alpha, double rho,
+                          double nu_prev, double *gdot, double *nu);
 
 /* ---------------- field-level building blocks ---------------- */
 void orc_sc_force(const orc_params *p, const unsigned char *mask,

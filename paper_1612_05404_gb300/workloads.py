@@ -37,7 +37,7 @@ def base_params(**kw) -> dict:
         G=-5.0, Gw=-5.0, rho0=1.0, eps_kappa=1.0,
         sigma_liq=0.0, sigma_gas=0.0, Dq=1e-3, E_ext=(0.0, 0.0, 0.0),
         Q_b=0.0, Q_s=0.0, K_d=1.0, xi_b=0.0, xi_s=0.0, theta_width=0.1,
-        sor_omega=None, poisson_tol=1e-13, alpha_eq_tol=1e-8,
+        sor_omega=None, poisson_tol=1e-13, alpha_eq_tol=1e-8, eps_face="arithmetic", carreau_lagged=0,
         rho_in=RHO_L, rho_out=RHO_V,
         # CUDA-side choices (the oracle ignores them)
         precision="fp64", poisson_check_every=8, poisson_solver="sor", poisson_mg_cycles=50,

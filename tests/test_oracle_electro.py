@@ -285,3 +285,57 @@ def test_uniform_charge_in_uniform_field_gives_qE():
     assert np.abs(F - expect[None, :]).max() <= 1e-15 * np.abs(expect).max()
     r1, j1 = sim.moments()
     assert np.allclose(j1.sum(0), N * expect, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("face", ["harmonic", "arithmetic"])
+def test_face_permittivity_series_law(face):
+    """A slab layered along the electrode axis (eps varying with x only, no
+    charge, electrodes at x = -1 and x = n): the flux J through every face is
+    the same, so the potential drops by J times each face's resistance. With
+    the harmonic face mean a face's resistance is the sum of its two
+    half-cells' 1/(2 eps_i) + 1/(2 eps_j) (cells in series); an electrode
+    face couples with the site's own eps. The solve must reproduce that
+    series law exactly for "harmonic", and must not for "arithmetic"."""
+    n = 12
+    shape = (n, 2, 2)
+    x = np.arange(n, dtype=float)
+    kap, lo, hi = 1.0, 0.25, -0.6
+    rho1 = 1.1 + 0.9 * np.sin(2 * np.pi * x / n) ** 2 + 0.3 * (x > 6)
+    rho = np.tile(rho1, 4)
+    eps = 1.0 + kap * rho1
+    cfg = W.base_params(shape=shape, charge_model="xi", poisson_tol=1e-15, eps_kappa=kap, eps_face=face,
+                        face_bc=["wall", "wall"] + ["periodic"] * 4,
+                        phi_bc=["dirichlet", "dirichlet"] + ["periodic"] * 4,
+                        phi_axis=0, phi_lo=lo, phi_hi=hi)
+    phi, it, res = oracle.poisson_solve(cfg, np.zeros(4 * n, np.uint8), rho, np.zeros(4 * n))
+    # series law: resistances of the n + 1 faces
+    Rf = np.concatenate([[1.0 / eps[0]], 0.5 / eps[:-1] + 0.5 / eps[1:], [1.0 / eps[-1]]])
+    J = (hi - lo) / Rf.sum()
+    expect = lo + J * np.cumsum(Rf)[:-1]
+    err = np.abs(phi[:n] - expect).max() / abs(hi - lo)
+    if face == "harmonic":
+        assert err <= 1e-12, err
+    else:
+        assert err > 1e-4, err
+
+
+def test_lagged_carreau_fixed_point_is_the_root():
+    """The lagged reading of Eq. (strain2) (tau from the previous step's nu):
+    for n = 1 it is nu0 at once; otherwise iterating it from nu0 converges to
+    the root of Eq. (strain2) with Eq. (carreau), the reading the default
+    step solves for, and a single application from nu0 differs from it."""
+    cfg = W.base_params(nu0=1 / 6, nu_inf=1 / 60, n_carreau=0.5)
+    cfg["lambda"] = 10.0
+    rng = np.random.default_rng(41)
+    for _ in range(20):
+        Pn, a, rho = rng.uniform(5e-3, 5e-2), rng.uniform(1.8, 2.2), rng.uniform(0.2, 2.0)
+        g_root, nu_root = oracle.carreau(cfg, Pn, a, rho)
+        nu = cfg["nu0"]
+        _, nu1 = oracle.carreau_lagged(cfg, Pn, a, rho, nu)
+        for _ in range(400):
+            gd, nu = oracle.carreau_lagged(cfg, Pn, a, rho, nu)
+        assert nu == pytest.approx(nu_root, rel=1e-12)
+        assert gd == pytest.approx(g_root, rel=1e-12)
+        assert abs(nu1 - nu_root) > 1e-6 * nu_root
+    newt = dict(cfg, n_carreau=1.0)
+    assert oracle.carreau_lagged(newt, 2e-3, 2.0, 1.0, 0.05)[1] == newt["nu0"]
