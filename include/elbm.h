@@ -54,8 +54,13 @@ enum { ELBM_PHI_PERIODIC = 0, ELBM_PHI_DIRICHLET = 1, ELBM_PHI_NEUMANN = 2 };
 /* free-charge model: none, Eq. (surface-q2), Eq. (surface-q3), D3Q7 transport */
 enum { ELBM_CHARGE_NONE = 0, ELBM_CHARGE_CONSERVED = 1, ELBM_CHARGE_XI = 2,
        ELBM_CHARGE_TRANSPORT = 3 };
-/* electric force: q E, or Eq. (force_el2) q E + (eps-1)/2 grad|E|^2 */
+/* electric force: q E, or Eq. (force_el2) q E + (eps-1)/2 grad|E|^2 (|E|^2 of
+ * the fluid face neighbours by central differences; a neighbour that is not
+ * fluid takes the site's own |E|^2) */
 enum { ELBM_FEL_QE = 0, ELBM_FEL_FULL = 1 };
+/* face permittivity of the Poisson operator: arithmetic or harmonic mean of
+ * the two sites (a Dirichlet face couples with the site's own eps) */
+enum { ELBM_EPS_FACE_ARITH = 0, ELBM_EPS_FACE_HARMONIC = 1 };
 /* Poisson solver: red-black SOR as the paper states it, or geometric
  * multigrid (red-black Gauss-Seidel smoothing) on the same fine operator with
  * the same stopping rule; interior solid nodes are conductors held at
@@ -152,6 +157,11 @@ typedef struct elbm_params {
     const float *mlp;            /* ELBM_ALPHA_LEARNED: device FP32 parameters of the
                                     proposal (ELBM_MLP_NPARAM values), read once by
                                     elbm_init (kept as BF16 by the handle); else NULL */
+    int eps_face;                /* ELBM_EPS_FACE_*: permittivity of a face of the Poisson
+                                    operator between two sites (the paper is silent) */
+    int carreau_lagged;          /* 0: gdot as the root of Eq. (strain2) each step; 1: Eq.
+                                    (strain2) with tau from the previous step's nu ("a slow
+                                    variation of nu over the time step", Sec. II B), no root */
 } elbm_params;
 
 /* Initial state, all host arrays of N = nx*ny*nz sites (caller-owned):

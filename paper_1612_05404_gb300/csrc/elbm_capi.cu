@@ -240,7 +240,9 @@ int validate(const elbm_params *p, const elbm_init_fields *in, int n_instances)
         if ((p->face_bc[2 * a] == ELBM_FACE_PERIODIC) != (p->face_bc[2 * a + 1] == ELBM_FACE_PERIODIC)) return 1;
     if (p->phi_axis < 0 || p->phi_axis > 2) return 1;
     if (p->charge_model < ELBM_CHARGE_NONE || p->charge_model > ELBM_CHARGE_TRANSPORT) return 1;
-    if (p->force_el != ELBM_FEL_QE) return 1;
+    if (p->force_el != ELBM_FEL_QE && p->force_el != ELBM_FEL_FULL) return 1;
+    if (p->eps_face != ELBM_EPS_FACE_ARITH && p->eps_face != ELBM_EPS_FACE_HARMONIC) return 1;
+    if (p->carreau_lagged != 0 && p->carreau_lagged != 1) return 1;
     if (p->alpha_mode < ELBM_ALPHA_ENTROPIC || p->alpha_mode > ELBM_ALPHA_LEARNED) return 1;
     // the learned proposal starts the FP32 Newton iteration of FP32/BF16 storage
     if (p->alpha_mode == ELBM_ALPHA_LEARNED &&
@@ -422,6 +424,10 @@ elbm_status step_host(elbm_handle *h, bool diag)
         h->launches += enq_shift(h, b, s);
     }
     if (prof) cudaEventRecord(h->ev[2], s);
+    if (h->ph.force_el == ELBM_FEL_FULL) {
+        h->ops.efield2(h->g, h->ph, b, h->L, s);
+        h->launches += 1;
+    }
     h->ops.collide(h->g, h->ph, b, diag ? 1 : 0, h->L, s);
     h->launches += 1;
     if (prof) cudaEventRecord(h->ev[3], s);
@@ -513,6 +519,10 @@ bool enqueue_step(elbm_handle *h, int parity, cudaStream_t s, int sections, int 
         n_post += enq_shift(h, b, s);
     }
     if (sections & 4) {
+        if (h->ph.force_el == ELBM_FEL_FULL) {
+            h->ops.efield2(h->g, h->ph, b, h->L, s);
+            n_post += 1;
+        }
         h->ops.collide(h->g, h->ph, b, diag_steps > 0 ? 1 : 0, h->L, s);
         n_post += 1;
         if (diag_steps > 0) n_post += fin(h, b, s, D_NPART, FIN_DIAG, 0, 0, diag_steps);
@@ -764,6 +774,8 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     ph.aprec = p->precision == ELBM_PREC_FP64 ? ELBM_APREC_FP64 : p->alpha_precision;
     ph.store_macro = p->store_macro; ph.neutralize = p->neutralize;
     ph.newtonian = (p->n_carreau == 1.0 || p->lambda == 0.0 || p->nu0 == p->nu_inf) ? 1 : 0;
+    ph.eps_face = p->eps_face;
+    ph.carreau_lagged = p->carreau_lagged;
 
     Launch &L = h->L;
     int bx = p->nx >= 128 ? 128 : ((p->nx + 31) / 32) * 32;
@@ -869,8 +881,10 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
             alloc(&b.ux, (size_t)N * h->sc_bytes);
             alloc(&b.uy, (size_t)N * h->sc_bytes);
             alloc(&b.uz, (size_t)N * h->sc_bytes);
-            alloc(&b.nu, (size_t)N * h->sc_bytes);
         }
+        // viscosity plane: exported, or the previous step's nu of the lagged reading
+        if (p->store_macro || p->carreau_lagged) alloc(&b.nu, (size_t)N * h->sc_bytes);
+        if (p->force_el == ELBM_FEL_FULL) alloc(&b.E2, (size_t)N * h->sc_bytes);
         if (p->store_macro) alloc(&b.alpha, (size_t)N * h->sc_bytes);
         // reduced precision: the low part of a root the float-float guard certified
         if (p->store_macro && p->precision != ELBM_PREC_FP64) alloc((void **)&b.alpha_lo, (size_t)N * sizeof(float));

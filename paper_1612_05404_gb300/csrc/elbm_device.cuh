@@ -322,6 +322,25 @@ __device__ __forceinline__ T carreau_nu(const Cst<T> &k, bool newtonian, T Pn, T
     return k.nu_inf + (k.nu0 - k.nu_inf) * powT(T(1) + lg * lg, k.nexp);
 }
 
+// The lagged reading: Eq. (strain2) with tau from the previous step's
+// viscosity nu_prev, gdot = A beta(nu_prev), no root; then Eq. (carreau).
+template <typename T>
+__device__ __forceinline__ T carreau_nu_lagged(const Cst<T> &k, T Pn, T alpha, T rho, T nu_prev)
+{
+    const T cs2 = T(1.0 / 3.0);
+    const T gdot = qdiv(Pn * alpha, rho * cs2) * qdiv(cs2, T(2) * nu_prev + cs2);
+    const T lg = k.lam * gdot;
+    return k.nu_inf + (k.nu0 - k.nu_inf) * powT(T(1) + lg * lg, k.nexp);
+}
+
+// permittivity of a face of the Poisson operator: arithmetic or harmonic
+// mean of the two sites
+template <typename T>
+__device__ __forceinline__ T face_eps(T ea, T eb, int harmonic)
+{
+    return harmonic ? qdiv(T(2) * ea * eb, ea + eb) : T(0.5) * (ea + eb);
+}
+
 // ---------------------------------------------------------------------------
 // Entropic alpha, Eq. (entropic) with Eq. (H): the nontrivial root of
 //   h(a) = H(f + a D) - H(f) = sum_p [ f_p phi(a x_p) ] + a h'(0),

@@ -33,6 +33,7 @@ struct Phys {
     double tol, rho_in, rho_out;      // host / reduction-side values
     double n_fluid, n_unknown;
     int charge_model, force_el, alpha_mode, aprec, store_macro, neutralize, newtonian;
+    int eps_face, carreau_lagged;
 };
 
 template <typename T> __host__ __device__ __forceinline__ const Cst<T> &cst(const Phys &ph);
@@ -47,6 +48,7 @@ struct Bufs {
     void *ux, *uy, *uz, *alpha, *nu;  // optional macroscopic planes
     float *alpha_lo;                  // reduced precision: low part of a guarded alpha (with store_macro)
     unsigned char *mask;              // node kinds (NULL when all fluid)
+    void *E2;                         // FULL electric force: |E|^2 per site
     void *nh;                         // paper-mode charge: 4 planes n_x, n_y, n_z, |grad rho|^2
     void *ab;                         // paper-mode charge: 2 planes a, b
     double *part;                     // per-block partial sums
@@ -78,6 +80,8 @@ struct Ops {
     // stage 0: block sums of phi over non-solid nodes; stage 1: subtract S_PHIMEAN
     void (*phi_mean)(const Geom &, const Phys &, const Bufs &, int stage, const Launch &, cudaStream_t);
     void (*collide)(const Geom &, const Phys &, const Bufs &, int diag, const Launch &, cudaStream_t);
+    // FULL electric force: |E|^2 of every site into the E2 plane, before the collision
+    void (*efield2)(const Geom &, const Phys &, const Bufs &, const Launch &, cudaStream_t);
     // warm start of the Poisson solve: phi <- 2 phi - phi_old, phi_old <- phi
     void (*phi_extrap)(const Geom &, const Bufs &, cudaStream_t);
     void (*export_pop)(const Geom &, const Bufs &, double *out, const Launch &, cudaStream_t);

@@ -591,7 +591,7 @@ __global__ void __launch_bounds__(128) k_sor(Geom g, Phys ph, Bufs b, int color,
             sc v = 0, dl = 0;
             int kk = pois_nb<sc>(g, k, b.mask, n, x, y, z, a, sg, &nb, &v, &dl);
             if (kk == 0) {
-                sc ef = sc(0.5) * (es + (sc(1) + k.kap * rho[nb]));
+                sc ef = face_eps<sc>(es, sc(1) + k.kap * rho[nb], ph.eps_face);
                 num += ef * (phi[nb] + dl);
                 den += ef;
             } else if (kk == 1) {
@@ -640,7 +640,7 @@ __global__ void __launch_bounds__(128) k_resid(Geom g, Phys ph, Bufs b)
                 sc v = 0, dl = 0;
                 int kk = pois_nb<sc>(g, k, b.mask, n, x, y, z, a, sg, &nb, &v, &dl);
                 if (kk == 0) {
-                    const sc cf = sc(0.5) * (es + (sc(1) + k.kap * rho[nb]));
+                    const sc cf = face_eps<sc>(es, sc(1) + k.kap * rho[nb], ph.eps_face);
                     r += cf * ((phi[nb] + dl) - ps);
                     t += cf * (fabs(phi[nb]) + fabs(dl) + fabs(ps));
                 } else if (kk == 1) {
@@ -862,6 +862,30 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
             Fy += qs * E[1];
             Fz += qs * E[2];
         }
+        if (ph.force_el == ELBM_FEL_FULL) {
+            // Eq. (force_el2): + (eps - 1)/2 grad|E|^2, central differences of
+            // the E2 plane; a neighbour that is not fluid (or beyond a wall)
+            // takes the site's own |E|^2
+            const sc *E2 = (const sc *)b.E2;
+            const ct e2s = ct(E2[s]);
+            ct gE[3];
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                ct ev[2];
+#pragma unroll
+                for (int kk = 0; kk < 2; kk++) {
+                    const int nb = nbr_idx(n, g, a == 0 ? (kk ? 1 : -1) : 0, a == 1 ? (kk ? 1 : -1) : 0,
+                                           a == 2 ? (kk ? 1 : -1) : 0);
+                    const bool own = nb < 0 || (b.mask && b.mask[nb] != ELBM_NODE_FLUID);
+                    ev[kk] = own ? e2s : ct(E2[nb]);
+                }
+                gE[a] = (ev[1] - ev[0]) * ct(0.5);
+            }
+            const ct h = ct(0.5) * (k.kap * r);  // (eps - 1)/2, eps = 1 + kappa rho
+            Fx += h * gE[0];
+            Fy += h * gE[1];
+            Fz += h * gE[2];
+        }
 
         // Eq. (2) at the bare velocity, Delta = f^eq - f
         ir = ct(1) / r;
@@ -968,8 +992,14 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
                 pyz -= D[p] * ct(cy(p) * cz(p));
             }
             ct Pn = sym3_norm2<ct>(pxx, pyy, pzz, pxy, pxz, pyz);
-            nu = carreau_nu<ct>(k, false, Pn, alpha, r);
+            if (ph.carreau_lagged) {
+                const ct np = ct(((const sc *)b.nu)[s]);  // 0 before the first step: nu0
+                nu = carreau_nu_lagged<ct>(k, Pn, alpha, r, np > ct(0) ? np : k.nu0);
+            } else {
+                nu = carreau_nu<ct>(k, false, Pn, alpha, r);
+            }
         }
+        if (ph.carreau_lagged && !ph.store_macro) ((sc *)b.nu)[s] = sc(nu);  // for the next step
         const ct beta = ct(CS2) / (ct(2) * nu + ct(CS2));
         const ct ab = alpha * beta;
 
@@ -1080,6 +1110,43 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
             b.part[(ll)j * num_blocks() + block_id()] = val;
         }
     }
+}
+
+// |E|^2 of every site for the FULL electric force, E = -grad phi (central
+// differences, the collision's stencil) + E_ext; 0 at nodes that are not fluid
+template <int PR>
+__global__ void __launch_bounds__(128) k_efield2(Geom g, Phys ph, Bufs b)
+{
+    typedef Tr<PR> T;
+    typedef typename T::ct ct;
+    typedef typename T::sc sc;
+    int x, y, z;
+    bool inb;
+    ll s;
+    site_xyz(g, x, y, z, inb, s);
+    if (!inb) return;
+    ct e2 = 0;
+    if (!b.mask || b.mask[s] == ELBM_NODE_FLUID) {
+        const Cst<ct> &k = cst<ct>(ph);
+        Nbr n;
+        nbr_init(n, g, x, y, z, s);
+        const sc *phi = (const sc *)b.phi;
+        const ct phs = ct(phi[s]);
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            ct pv[2];
+#pragma unroll
+            for (int kk = 0; kk < 2; kk++) {
+                int nb = 0;
+                ct v = 0, dl = 0;
+                const int kind = pois_nb<ct>(g, k, b.mask, n, x, y, z, a, kk ? 1 : -1, &nb, &v, &dl);
+                pv[kk] = kind == 0 ? ct(phi[nb]) + dl : (kind == 1 ? v + dl : phs);
+            }
+            const ct E = -(pv[1] - pv[0]) * ct(0.5) + k.E[a];
+            e2 += E * E;
+        }
+    }
+    ((sc *)b.E2)[s] = sc(e2);
 }
 
 // Warm start of the Poisson solve by linear extrapolation in time,
@@ -1212,6 +1279,10 @@ struct Launchers {
                 k_collide<PR, ELBM_APREC_FP32, false><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
         }
     }
+    static void efield2(const Geom &g, const Phys &ph, const Bufs &b, const Launch &L, cudaStream_t s)
+    {
+        k_efield2<PR><<<L.grid, L.block, 0, s>>>(g, ph, b);
+    }
     static void phi_extrap(const Geom &g, const Bufs &b, cudaStream_t s)
     {
         k_phi_extrap<sc><<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>((sc *)b.phi, (sc *)b.phi_old, b.scal, g.N);
@@ -1243,6 +1314,7 @@ struct Launchers {
         o.resid = resid;
         o.phi_mean = phi_mean;
         o.collide = collide;
+        o.efield2 = efield2;
         o.phi_extrap = phi_extrap;
         o.export_pop = export_pop;
         o.export_gpop = export_gpop;
@@ -1347,7 +1419,7 @@ __device__ __forceinline__ typename Tr<PR>::sc mg_resid_at(const Geom &g, const 
                 int nb = 0;
                 T v = 0, dl = 0;
                 const int kk = pois_nb<T>(g, k, bf.mask, n, x, y, z, a, sg, &nb, &v, &dl);
-                if (kk == 0) r += T(0.5) * (es + (T(1) + k.kap * rho[nb])) * ((phi[nb] + dl) - ps);
+                if (kk == 0) r += face_eps<T>(es, T(1) + k.kap * rho[nb], ph.eps_face) * ((phi[nb] + dl) - ps);
                 else if (kk == 1) r += es * ((v + dl) - ps);
             }
         return r;

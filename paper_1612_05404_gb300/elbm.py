@@ -70,6 +70,7 @@ class Params(ctypes.Structure):
         ("alpha_eq_tol", ctypes.c_double), ("rho_in", ctypes.c_double), ("rho_out", ctypes.c_double),
         ("cuda_stream", ctypes.c_void_p),
         ("mlp", ctypes.c_void_p),
+        ("eps_face", ctypes.c_int), ("carreau_lagged", ctypes.c_int),
     ]
 
 
@@ -178,6 +179,8 @@ def make_params(cfg: dict, stream=None) -> Params:
     P.alpha_eq_tol = cfg["alpha_eq_tol"]
     P.rho_in, P.rho_out = cfg["rho_in"], cfg["rho_out"]
     P.cuda_stream = stream
+    P.eps_face = {"arithmetic": 0, "harmonic": 1}[cfg.get("eps_face", "arithmetic")]
+    P.carreau_lagged = int(cfg.get("carreau_lagged", 0))
     mlp = cfg.get("mlp")
     P.mlp = None if mlp is None else mlp.data_ptr()
     return P

@@ -77,7 +77,7 @@ def test_strerror(L):
     dict(nu0=0.0),
     dict(charge_model="transport", shape=(5, 4, 4)),   # odd periodic extent for red-black
     dict(precision="fp16"),
-    dict(force_el="full"),
+    dict(carreau_lagged=2),
 ])
 def test_invalid_parameters_rejected_without_allocation(L, bad):
     cfg = W.base_params(shape=(4, 4, 4))

@@ -387,3 +387,63 @@ def test_poisson_cap_returns_warning(E):
     g = E.Sim(cfg, fields)
     assert g.step(1) == E.W_POISSON_NOCONV
     assert g.diag()["poisson_sweeps"] == 3
+
+
+@pytest.mark.parametrize("variant", ["full", "harmonic", "harmonic_mg", "lagged"])
+def test_fp64_alternate_readings(E, variant):
+    """The paper's alternate readings on the drop in field (electrodes,
+    transported charge, Carreau n = 0.6), FP64 against the oracle at 1e-12
+    after three steps: the FULL electric force Eq. (force_el2) (|E|^2 plane,
+    central differences), the harmonic face permittivity (SOR and multigrid
+    on the same fine operator), the lagged Carreau viscosity (tau from the
+    previous step's nu)."""
+    cfg, fields = W.drop_in_field(E0=1e-3, n=16, radius=4.5, precision="fp64")
+    _tight(cfg, "mg" if variant == "harmonic_mg" else "sor")
+    if variant == "full":
+        cfg["force_el"] = "full"
+    elif variant.startswith("harmonic"):
+        cfg["eps_face"] = "harmonic"
+    else:
+        cfg["carreau_lagged"] = 1
+    g, o = run_both(E, cfg, fields, 3)
+    compare_fp64(g, o, cfg, tol=1e-10 if variant == "harmonic_mg" else 1e-12)
+    g.close()
+
+
+def test_fp64_full_force_nozzle(E):
+    """The FULL electric force on the nozzle jet: conductor (solid) nodes,
+    inlet and outlet neighbours take the site's own |E|^2; FP64 at 1e-12."""
+    cfg, fields = W.jet(shape=(16, 16, 20), nozzle_r=3, wall=1, nozzle_len=5, precision="fp64")
+    _tight(cfg)
+    cfg.update(force_el="full", eps_face="harmonic")
+    g, o = run_both(E, cfg, fields, 2)
+    compare_fp64(g, o, cfg, fields=("f", "rho", "u", "nu", "phi", "q"))
+    g.close()
+
+
+@pytest.mark.parametrize("case", ["drop", "nozzle"])
+def test_fp32_alternate_readings(E, case):
+    """All three alternate readings together in FP32 (the potential held as
+    its deviation from the electrode profile, conductors in the nozzle case):
+    density, potential and charge within 1e-5, momentum within 2e-6 relative
+    L2 over four steps, and the viscosity within 5e-5 at every fluid site."""
+    if case == "drop":
+        cfg, fields = W.drop_in_field(E0=1e-3, n=16, radius=4.5, precision="fp32")
+    else:
+        cfg, fields = W.jet(shape=(16, 16, 20), nozzle_r=3, wall=1, nozzle_len=5, precision="fp32")
+        cfg.update(n_carreau=0.6)
+    cfg.update(store_macro=1, alpha_precision="fp32", force_el="full", eps_face="harmonic", carreau_lagged=1)
+    g = E.Sim(cfg, fields)
+    o = oracle.Sim(dict(cfg, poisson_tol=1e-13), fields)
+    for t in range(4):
+        g.step(1)
+        o.step(1)
+        fl = o.rho > 0
+        e = dict(rho=rel_l2(g.get("rho")[fl], o.rho[fl]), phi=rel_l2(g.get("phi"), o.phi),
+                 q=rel_l2(g.get("q"), o.q))
+        assert max(e.values()) < 1e-5, (t, e)
+        assert rel_l2(_rho_u(g.get("rho"), g.get("u")), _rho_u(o.rho, o.u)) < 2e-6, t
+        nu_g, nu_o = g.get("nu"), o.nu
+        f = nu_o > 0
+        assert np.max(np.abs(nu_g[f] - nu_o[f]) / nu_o[f]) <= 5e-5, t
+    g.close()
