@@ -120,7 +120,7 @@ def lib():
         L.orc_stream.argtypes = [pp, u8p, dp, dp, dp, dp, dp, dp]
         L.orc_init.argtypes = [pp, u8p, dp, dp, dp, dp, dp, dp, dp]
         L.orc_apply_io.argtypes = [pp, u8p, dp, dp]
-        L.orc_step.argtypes = [pp, u8p, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
+        L.orc_step.argtypes = [pp, u8p, dp, u8p, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
         L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_set_threads.restype = ctypes.c_int
         _lib = L
@@ -335,8 +335,12 @@ class Sim:
         if mask is None:
             mask = np.zeros(self.N, np.uint8)
         self.mask = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
-        self.u_in = np.ascontiguousarray(fields.get("u_in", np.zeros((self.N, 3))),
-                                         dtype=np.float64).reshape(-1)
+        self.u_in = np.array(fields.get("u_in", np.zeros((self.N, 3))), dtype=np.float64).reshape(-1)
+        # the adaptive inlet: the nozzle sites whose mean velocity rescales
+        # the initial inlet profile each step
+        reg = fields.get("inlet_region")
+        self.region = None if reg is None else np.ascontiguousarray(reg, dtype=np.uint8).reshape(-1)
+        self.u_in0 = self.u_in.copy() if self.region is not None else None
         rho0 = np.ascontiguousarray(fields["rho"], dtype=np.float64).reshape(-1)
         u0 = fields.get("u")
         u0 = None if u0 is None else np.ascontiguousarray(u0, dtype=np.float64).reshape(-1)
@@ -364,6 +368,7 @@ class Sim:
     def step(self, n: int = 1):
         for _ in range(n):
             rc = lib().orc_step(ctypes.byref(self.P), _u8(self.mask), _dp(self.u_in),
+                                None if self.region is None else _u8(self.region), _dp(self.u_in0),
                                 _dp(self.f), _dp(self.g), _dp(self.phi), _dp(self.rho),
                                 _dp(self.u), _dp(self.q), _dp(self.alpha), _dp(self.nu),
                                 _dp(self.diag))

@@ -893,7 +893,44 @@ void orc_stream(const orc_params *p, const unsigned char *mask, const double *u_
  * populations, transport mode), phi (potential, warm start). Outputs at
  * time t: rho, u (half-step velocity), q (free charge), alpha, nu, diag.
  * ---------------------------------------------------------------------- */
-int orc_step(const orc_params *p, const unsigned char *mask, const double *u_in,
+/* The adaptive inlet of the jet (Sec. III B): at each time step the mean
+ * velocity of the fluid inside the nozzle sets the Poiseuille profile of the
+ * inlet nodes. Reading: after the collision of the step, the mean over the
+ * `region` sites of the half-step velocity along the inlet direction d (the
+ * direction of the summed initial inlet velocities), divided by the initial
+ * inlet profile's own mean along d, rescales that initial profile; the
+ * populations that the inlet nodes send in the streaming of this step (those
+ * of the next time level) carry the rescaled profile. */
+static void inlet_rescale(const ctx_t *C, const unsigned char *mask, const unsigned char *region,
+                          const double *u, const double *u_in0, double *u_in)
+{
+    double d[3] = {0, 0, 0}, mu = 0.0, m0 = 0.0;
+    long nr = 0, ni = 0;
+    for (long s = 0; s < C->N; s++)
+        if (mask[s] == ORC_INLET)
+            for (int a = 0; a < 3; a++) d[a] += u_in0[3 * s + a];
+    double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    if (dn == 0.0) return;
+    for (int a = 0; a < 3; a++) d[a] /= dn;
+    for (long s = 0; s < C->N; s++) {
+        if (mask[s] == ORC_INLET) {
+            m0 += u_in0[3 * s] * d[0] + u_in0[3 * s + 1] * d[1] + u_in0[3 * s + 2] * d[2];
+            ni++;
+        }
+        if (region[s] && mask[s] == ORC_FLUID) {
+            mu += u[3 * s] * d[0] + u[3 * s + 1] * d[1] + u[3 * s + 2] * d[2];
+            nr++;
+        }
+    }
+    if (ni == 0 || nr == 0 || m0 == 0.0) return;
+    double ratio = (mu / (double)nr) / (m0 / (double)ni);
+    for (long s = 0; s < C->N; s++)
+        if (mask[s] == ORC_INLET)
+            for (int a = 0; a < 3; a++) u_in[3 * s + a] = ratio * u_in0[3 * s + a];
+}
+
+int orc_step(const orc_params *p, const unsigned char *mask, double *u_in,
+             const unsigned char *region, const double *u_in0,
              double *f, double *g, double *phi, double *rho, double *u, double *q,
              double *alpha_out, double *nu_out, double *diag)
 {
@@ -1076,6 +1113,7 @@ int orc_step(const orc_params *p, const unsigned char *mask, const double *u_in,
     diag[16] = qmean;
     free(ast); free(aherr); free(umag); free(Hs); free(Fs);
 
+    if (region && u_in0 && u_in) inlet_rescale(&C, mask, region, u, u_in0, u_in);
     orc_stream(p, mask, u_in, rho, fs, gs, f, g);
 
     free(j); free(qn); free(Fint); free(E); free(E2); free(fs);

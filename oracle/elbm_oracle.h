@@ -115,8 +115,13 @@ int orc_init(const orc_params *p, const unsigned char *mask,
              double *phi);
 void orc_apply_io(const orc_params *p, const unsigned char *mask, const double *u_in,
                   double *f);
+/* u_in: inlet velocities (3 per site, read at inlet nodes); with region
+ * (uint8 per site: the nozzle sites whose mean velocity rescales the inlet
+ * profile) and u_in0 (the initial inlet velocities) not NULL, u_in is
+ * rewritten each step (the adaptive inlet); else it is only read. */
 int orc_step(const orc_params *p, const unsigned char *mask,
-             const double *u_in, double *f, double *g, double *phi,
+             double *u_in, const unsigned char *region, const double *u_in0,
+             double *f, double *g, double *phi,
              double *rho, double *u, double *q, double *alpha_out,
              double *nu_out, double *diag);
 

@@ -195,12 +195,15 @@ def drop_in_field(E0=1e-3, n=64, radius=12.0, precision="fp32", steps=5000,
 
 
 def jet(shape=(128, 128, 512), nozzle_r=8, wall=2, nozzle_len=16, u_mean=0.02, E0=5e-4,
-        precision="bf16", steps=20000, seed=SEED_BASE + 3, perturb=1e-3):
+        precision="bf16", steps=20000, seed=SEED_BASE + 3, perturb=1e-3, adaptive_inlet=False):
     """Electrified jet (Sec. III B, extended to 3-D): a nozzle of inner radius
     nozzle_r along z injects liquid with a Poiseuille profile; outlet nodes at
     the far z plane are a vapour reservoir; lateral faces are walls; the
     potential drops linearly from 0 (nozzle side, nozzle conductor at 0) to
-    -E0 (nz+1) (collector side). Charge is the non-conserved xi form."""
+    -E0 (nz+1) (collector side). Charge is the non-conserved xi form. With
+    adaptive_inlet the fluid sites inside the nozzle (r < nozzle_r,
+    1 <= z < nozzle_len) are the region whose mean velocity rescales the inlet
+    profile each step (fields["inlet_region"])."""
     nx, ny, nz = shape
     nu0 = 1.0 / 6.0
     cfg = base_params(
@@ -232,6 +235,8 @@ def jet(shape=(128, 128, 512), nozzle_r=8, wall=2, nozzle_len=16, u_mean=0.02, E
     pert = uniform_noise(nx * ny * nz, perturb, seed)
     u_in[inlet, 2] = prof[inlet] + pert[inlet]
     fields = dict(mask=mask, rho=rho, q=np.zeros(nx * ny * nz), u_in=u_in)
+    if adaptive_inlet:
+        fields["inlet_region"] = ((r < nozzle_r) & (zf >= 1) & (zf < nozzle_len) & (mask == FLUID)).astype(np.uint8)
     return cfg, fields
 
 

@@ -142,3 +142,28 @@ def test_sc_wall_term():
     assert F0[:, 0, :, 1] == pytest.approx(np.full((4, 4), -5.0 * psi2 * -(1 / 18 + 4 / 36)), rel=1e-14)
     assert F0[:, 5, :, 1] == pytest.approx(np.full((4, 4), -5.0 * psi2 * (1 / 18 + 4 / 36)), rel=1e-14)
     assert np.abs(F0[:, 1:5]).max() < 1e-16
+
+
+def test_adaptive_inlet_follows_the_nozzle_mean_velocity():
+    """The jet's inlet (Sec. III B): at each step the mean velocity of the
+    fluid inside the nozzle sets the Poiseuille profile of the inlet nodes.
+    After every step the inlet velocities are the initial profile times the
+    ratio of the nozzle mean (half-step velocity along z, from the step's own
+    velocity field) to the initial profile's mean: the profile keeps its shape
+    and its mean follows the nozzle, which departs from the initial mean."""
+    cfg, fields = W.jet(shape=(16, 16, 20), nozzle_r=4, wall=1, nozzle_len=8, precision="fp64",
+                        adaptive_inlet=True)
+    sim = oracle.Sim(cfg, fields)
+    inlet = sim.mask == oracle.INLET
+    region = fields["inlet_region"].astype(bool)
+    u0 = np.asarray(fields["u_in"]).reshape(-1, 3)
+    m0 = u0[inlet, 2].mean()
+    ratios = []
+    for _ in range(4):
+        sim.step()
+        u = sim.u.reshape(-1, 3)
+        ratio = u[region, 2].mean() / m0
+        uin = sim.u_in.reshape(-1, 3)
+        assert np.allclose(uin[inlet], ratio * u0[inlet], rtol=1e-12, atol=1e-15)
+        ratios.append(ratio)
+    assert abs(ratios[-1] - 1.0) > 1e-3
