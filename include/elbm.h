@@ -108,7 +108,8 @@ enum { ELBM_APREC_FP64 = 0, ELBM_APREC_FP32 = 1, ELBM_APREC_FP32_FAST = 2 };
  * 17 step counter, 18 Poisson sweeps summed over all steps, 19 sites whose
  * alpha took the float-float guard, 20 sites where the guard ended above
  * 1e-10 rho, 21 learned-alpha sites that fell back to the Newton root,
- * 22-23 reserved */
+ * 22 scale of the inlet profile set by the adaptive inlet (0 without it),
+ * 23 reserved */
 #define ELBM_NDIAG 24
 
 typedef struct elbm_params {
@@ -171,10 +172,19 @@ typedef struct elbm_params {
  *   q0    FP64 initial free charge, transport mode (NULL = 0);
  *   u_in  FP64 3N inlet velocity, read at inlet nodes (NULL = 0);
  *   f0    FP64 19N populations f(r, 0) overriding the equilibrium start
- *         (NULL = f^eq(rho0, u0), Eq. 2). */
+ *         (NULL = f^eq(rho0, u0), Eq. 2);
+ *   inlet_region  uint8 N (NULL = the inlet profile stays as given): the
+ *         adaptive inlet of the jet (Sec. III B). After the collision of each
+ *         step, the mean over the fluid sites with inlet_region != 0 of the
+ *         half-step velocity along d (the direction of the summed initial
+ *         inlet velocities), over the initial profile's own mean along d,
+ *         rescales the initial inlet velocities; the next step pulls
+ *         f^eq(rho_in, rescaled u_in) from the inlet nodes. Needs u_in with a
+ *         nonzero mean and at least one fluid region site (ELBM_E_INVAL). */
 typedef struct elbm_init_fields {
     const unsigned char *mask;
     const double *rho0, *u0, *q0, *u_in, *f0;
+    const unsigned char *inlet_region;
 } elbm_init_fields;
 
 /* Validate the parameters, allocate the device state, build f(r, 0) (and

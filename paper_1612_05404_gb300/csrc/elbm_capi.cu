@@ -98,7 +98,8 @@ __global__ void k_mlp_image(const float *th, MlpSmem *img)
     for (int i = threadIdx.x; i < (int)(sizeof(MlpSmem) / 16); i += blockDim.x) dst[i] = src[i];
 }
 
-enum { FIN_CHARGE_AB = 0, FIN_CHARGE_Q = 1, FIN_RESID_PRE = 2, FIN_PHI = 3, FIN_DIAG = 4, FIN_RESID_BODY = 5 };
+enum { FIN_CHARGE_AB = 0, FIN_CHARGE_Q = 1, FIN_RESID_PRE = 2, FIN_PHI = 3, FIN_DIAG = 4, FIN_RESID_BODY = 5,
+       FIN_INLET = 6 };
 
 // Control of the Poisson loop, evaluated on the device after each
 // convergence test (so the loop can run inside a CUDA graph).
@@ -196,6 +197,11 @@ __global__ void __launch_bounds__(256) k_finalize(const double *part, int nblock
     } else if (mode == FIN_PHI) {
         scal[S_PHISUM] = res[0];
         scal[S_PHIMEAN] = res[0] / ph.n_unknown;
+    } else if (mode == FIN_INLET) {
+        // adaptive inlet: the nozzle mean along d over the initial profile's mean
+        const double r = (ph.n_region > 0.0 && ph.in_m0 != 0.0) ? (res[0] / ph.n_region) / ph.in_m0 : 1.0;
+        scal[S_INRATIO] = r;
+        diag[22] = r;
     } else if (mode == FIN_DIAG) {
         diag[0] = res[D_MASS];
         diag[1] = res[D_MX];
@@ -310,6 +316,19 @@ int fin(elbm_handle *h, const Bufs &b, cudaStream_t s, int K, int mode, unsigned
     k_finalize<<<K, 256, 0, s>>>(b.part, h->L.nblocks, K, mode, h->ph, c, b.scal, b.scalf, b.diag, b.colres,
                                  b.ticket);
     return 1;
+}
+
+// adaptive inlet, after the collision: the profile scale from the region's
+// block sums (their own column of the partials), then the inlet equilibria
+// into the buffer of the next step
+int enq_inlet(elbm_handle *h, const Bufs &b, cudaStream_t s)
+{
+    if (!h->ph.adaptive) return 0;
+    Ctl c = make_ctl(h, 0, 0);
+    k_finalize<<<1, 256, 0, s>>>(b.part + (long long)D_UIN * h->L.nblocks, h->L.nblocks, 1, FIN_INLET, h->ph, c,
+                                 b.scal, b.scalf, b.diag, b.colres, b.ticket);
+    h->ops.inlet(h->g, h->ph, b, s);
+    return 2;
 }
 
 int vcycle(elbm_handle *h, const Bufs &b, cudaStream_t s, int l)
@@ -432,6 +451,7 @@ elbm_status step_host(elbm_handle *h, bool diag)
     h->launches += 1;
     if (prof) cudaEventRecord(h->ev[3], s);
     if (diag) h->launches += fin(h, b, s, D_NPART, FIN_DIAG);
+    h->launches += enq_inlet(h, b, s);
     if (prof) cudaEventRecord(h->ev[4], s);
     return cuda_ok(cudaGetLastError()) ? ELBM_OK : ELBM_E_CUDA;
 }
@@ -526,6 +546,7 @@ bool enqueue_step(elbm_handle *h, int parity, cudaStream_t s, int sections, int 
         h->ops.collide(h->g, h->ph, b, diag_steps > 0 ? 1 : 0, h->L, s);
         n_post += 1;
         if (diag_steps > 0) n_post += fin(h, b, s, D_NPART, FIN_DIAG, 0, 0, diag_steps);
+        n_post += enq_inlet(h, b, s);
     }
     return ok;
 }
@@ -776,6 +797,38 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     ph.newtonian = (p->n_carreau == 1.0 || p->lambda == 0.0 || p->nu0 == p->nu_inf) ? 1 : 0;
     ph.eps_face = p->eps_face;
     ph.carreau_lagged = p->carreau_lagged;
+    // adaptive inlet (Sec. III B): the inlet nodes with their initial
+    // velocities, the direction d of their sum, the profile's mean along d,
+    // and the number of fluid region sites
+    std::vector<int> in_idx;
+    std::vector<double> in_u0;
+    if (in->inlet_region) {
+        if (!in->u_in || !in->mask) { delete h; return ELBM_E_INVAL; }
+        double d[3] = {0, 0, 0};
+        long long nreg = 0;
+        for (long long i = 0; i < N; i++) {
+            if (in->mask[i] == ELBM_NODE_INLET) {
+                in_idx.push_back((int)i);
+                for (int a = 0; a < 3; a++) {
+                    in_u0.push_back(in->u_in[3 * i + a]);
+                    d[a] += in->u_in[3 * i + a];
+                }
+            }
+            if (in->inlet_region[i] && in->mask[i] == ELBM_NODE_FLUID) nreg++;
+        }
+        const double dn = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if (in_idx.empty() || nreg == 0 || !(dn > 0.0)) { delete h; return ELBM_E_INVAL; }
+        double m0 = 0.0;
+        for (int a = 0; a < 3; a++) ph.in_d[a] = d[a] / dn;
+        for (size_t t = 0; t < in_idx.size(); t++)
+            m0 += in_u0[3 * t] * ph.in_d[0] + in_u0[3 * t + 1] * ph.in_d[1] + in_u0[3 * t + 2] * ph.in_d[2];
+        m0 /= (double)in_idx.size();
+        if (m0 == 0.0) { delete h; return ELBM_E_INVAL; }
+        ph.adaptive = 1;
+        ph.n_inlet = (int)in_idx.size();
+        ph.in_m0 = m0;
+        ph.n_region = (double)nreg;
+    }
 
     Launch &L = h->L;
     int bx = p->nx >= 128 ? 128 : ((p->nx + 31) / 32) * 32;
@@ -914,7 +967,12 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
             h->tail.m = (const unsigned char *)dt;
             h->lev[h->lt].m = (const unsigned char *)dt;  // the tail's first level is level lt
         }
-        alloc((void **)&b.part, (size_t)part_blocks * D_NPART * sizeof(double));
+        alloc((void **)&b.part, (size_t)part_blocks * (D_NPART + 1) * sizeof(double));
+        if (ph.adaptive) {
+            alloc((void **)&b.region, (size_t)N);
+            alloc((void **)&b.inlet_idx, (size_t)ph.n_inlet * sizeof(int));
+            alloc((void **)&b.inlet_u0, (size_t)ph.n_inlet * 3 * sizeof(double));
+        }
         alloc((void **)&b.scal, S_NSCAL * sizeof(double));
         alloc((void **)&b.scalf, S_NSCAL * sizeof(float));
         alloc((void **)&b.colres, 16 * sizeof(double));
@@ -986,6 +1044,14 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     up(&d_uin, in->u_in, 3 * N);
     if (transport) up(&d_q0, in->q0, N);
     if (ok && b.mask && !cuda_ok(cudaMemcpyAsync(b.mask, in->mask, N, cudaMemcpyHostToDevice, h->s))) ok = false;
+    if (ok && ph.adaptive) {
+        ok = cuda_ok(cudaMemcpyAsync(const_cast<unsigned char *>(b.region), in->inlet_region, N, cudaMemcpyHostToDevice,
+                                     h->s)) &&
+             cuda_ok(cudaMemcpyAsync(const_cast<int *>(b.inlet_idx), in_idx.data(), in_idx.size() * sizeof(int),
+                                     cudaMemcpyHostToDevice, h->s)) &&
+             cuda_ok(cudaMemcpyAsync(const_cast<double *>(b.inlet_u0), in_u0.data(), in_u0.size() * sizeof(double),
+                                     cudaMemcpyHostToDevice, h->s));
+    }
     if (ok) {
         h->ops.init_pop(g, ph, b, d_rho0, d_u0, d_f0, d_uin, d_q0, L, h->s);
         if (!cuda_ok(cudaGetLastError()) || !cuda_ok(cudaStreamSynchronize(h->s))) ok = false;

@@ -19,12 +19,14 @@ enum {
     S_STEPS,       // completed steps
     S_KEEP,        // 1 while the Poisson loop must go on
     S_HAVE_OLD,    // 1 once phi(t-1) is recorded for the extrapolated warm start
+    S_INRATIO,     // adaptive inlet: scale of the initial inlet profile for the next step
     S_NSCAL = 24
 };
 // per-block partial slots of the collision diagnostics
 enum {
     D_MASS = 0, D_MX, D_MY, D_MZ, D_Q, D_AMIN, D_AMAX, D_ASUM, D_NSHORT, D_NNOROOT,
-    D_NCLIP, D_HERR, D_UMAX, D_NBAD, D_NFLUID, D_NGUARD, D_NGFAIL, D_NLFALL, D_NPART = 18
+    D_NCLIP, D_HERR, D_UMAX, D_NBAD, D_NFLUID, D_NGUARD, D_NGFAIL, D_NLFALL, D_NPART = 18,
+    D_UIN = 18     // adaptive inlet: per-block sum of u . d over the region (every step)
 };
 
 struct Phys {
@@ -34,6 +36,9 @@ struct Phys {
     double n_fluid, n_unknown;
     int charge_model, force_el, alpha_mode, aprec, store_macro, neutralize, newtonian;
     int eps_face, carreau_lagged;
+    // adaptive inlet: direction d, mean of the initial profile along d, region sites
+    int adaptive, n_inlet;
+    double in_d[3], in_m0, n_region;
 };
 
 template <typename T> __host__ __device__ __forceinline__ const Cst<T> &cst(const Phys &ph);
@@ -49,6 +54,9 @@ struct Bufs {
     float *alpha_lo;                  // reduced precision: low part of a guarded alpha (with store_macro)
     unsigned char *mask;              // node kinds (NULL when all fluid)
     void *E2;                         // FULL electric force: |E|^2 per site
+    const unsigned char *region;      // adaptive inlet: sites of the nozzle mean (NULL: fixed inlet)
+    const int *inlet_idx;             // adaptive inlet: the inlet nodes
+    const double *inlet_u0;           // adaptive inlet: their initial velocities (3 each)
     void *nh;                         // paper-mode charge: 4 planes n_x, n_y, n_z, |grad rho|^2
     void *ab;                         // paper-mode charge: 2 planes a, b
     double *part;                     // per-block partial sums
@@ -82,6 +90,8 @@ struct Ops {
     void (*collide)(const Geom &, const Phys &, const Bufs &, int diag, const Launch &, cudaStream_t);
     // FULL electric force: |E|^2 of every site into the E2 plane, before the collision
     void (*efield2)(const Geom &, const Phys &, const Bufs &, const Launch &, cudaStream_t);
+    // adaptive inlet: the rescaled inlet equilibria into the buffer of the next step
+    void (*inlet)(const Geom &, const Phys &, const Bufs &, cudaStream_t);
     // warm start of the Poisson solve: phi <- 2 phi - phi_old, phi_old <- phi
     void (*phi_extrap)(const Geom &, const Bufs &, cudaStream_t);
     void (*export_pop)(const Geom &, const Bufs &, double *out, const Launch &, cudaStream_t);

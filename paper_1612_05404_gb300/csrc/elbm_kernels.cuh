@@ -754,6 +754,7 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
     ct r = 0, drho = 0, jx = 0, jy = 0, jz = 0, Fx = 0, Fy = 0, Fz = 0, qs = 0;
     ct ir = 0, ux = 0, uy = 0, uz = 0, usq = 0, Rq = 0;
     float esum = 0.f;  // rounding scale of the FP32 momentum (deviation modes)
+    ct uin_v = 0;      // adaptive inlet: u . d at a region site
     ct alpha = ct(2);
     float alpha_lo = 0.f;  // low part of a guarded root
     // FP32 alpha: its setup (carried across the network's barrier in learned mode)
@@ -1017,6 +1018,8 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
 
         // half-step velocity (Sec. II): rho u = sum f c + F/2
         const ct upx = (jx + ct(0.5) * Fx) * ir, upy = (jy + ct(0.5) * Fy) * ir, upz = (jz + ct(0.5) * Fz) * ir;
+        if (b.region && b.region[s])  // adaptive inlet: this site's velocity along the inlet direction
+            uin_v = upx * ct(ph.in_d[0]) + upy * ct(ph.in_d[1]) + upz * ct(ph.in_d[2]);
 
         if (ph.charge_model == ELBM_CHARGE_TRANSPORT) {
             // D3Q7 advection-diffusion of q with the Ohmic source R (above)
@@ -1059,6 +1062,10 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
             dumax = um2;
             if (!(r > ct(0)) || !isfinite(float(r)) || !isfinite(um2) || !isfinite(float(alpha))) dbad = 1;
         }
+    }
+    if (b.region) {  // adaptive inlet, every step: block sums of u . d over the region
+        ct v[1] = {uin_v};
+        block_sums<1>(v, b.part + (ll)D_UIN * num_blocks() + block_id());
     }
     if (diag) {
         // sums: compensated FP32 (or FP64) block sums; the five 0/1 counts
@@ -1109,6 +1116,32 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
             }
             b.part[(ll)j * num_blocks() + block_id()] = val;
         }
+    }
+}
+
+// Adaptive inlet: f^eq(rho_in, r u0) of every inlet node, r the scale that
+// the finalize derived from the nozzle mean, stored as k_init_pop stores it,
+// into B (the buffer the next step pulls from)
+template <int PR>
+__global__ void k_inlet_update(Geom g, Phys ph, Bufs b, const double *scal)
+{
+    typedef Tr<PR> T;
+    typedef typename T::st st;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ph.n_inlet) return;
+    const ll i = b.inlet_idx[t];
+    const double r = scal[S_INRATIO];
+    const double ux = r * b.inlet_u0[3 * t], uy = r * b.inlet_u0[3 * t + 1], uz = r * b.inlet_u0[3 * t + 2];
+    const double usq = ux * ux + uy * uy + uz * uz;
+    st *B = (st *)b.fB;
+#pragma unroll
+    for (int p = 0; p < Q; p++) {
+        const double fe = wq(p) * ph.rho_in * (1.0 + Ppoly<double>(p, ux, uy, uz, usq));
+        st v;
+        if constexpr (T::rel) v = from_ct<st>((typename T::ct)(fe - wq(p) * ph.rho_in));
+        else if constexpr (T::dev) v = from_ct<st>((typename T::ct)(fe - wq(p)));
+        else v = from_ct<st>((typename T::ct)fe);
+        B[(ll)p * g.N + i] = v;
     }
 }
 
@@ -1283,6 +1316,10 @@ struct Launchers {
     {
         k_efield2<PR><<<L.grid, L.block, 0, s>>>(g, ph, b);
     }
+    static void inlet(const Geom &g, const Phys &ph, const Bufs &b, cudaStream_t s)
+    {
+        k_inlet_update<PR><<<(unsigned)((ph.n_inlet + 127) / 128), 128, 0, s>>>(g, ph, b, b.scal);
+    }
     static void phi_extrap(const Geom &g, const Bufs &b, cudaStream_t s)
     {
         k_phi_extrap<sc><<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>((sc *)b.phi, (sc *)b.phi_old, b.scal, g.N);
@@ -1315,6 +1352,7 @@ struct Launchers {
         o.phi_mean = phi_mean;
         o.collide = collide;
         o.efield2 = efield2;
+        o.inlet = inlet;
         o.phi_extrap = phi_extrap;
         o.export_pop = export_pop;
         o.export_gpop = export_gpop;

@@ -21,7 +21,7 @@ DIAG_NAMES = [
     "mass", "mom_x", "mom_y", "mom_z", "charge", "alpha_min", "alpha_max", "alpha_mean",
     "n_shortcut", "n_noroot", "n_clipped", "poisson_sweeps", "poisson_resid", "max_h_error",
     "max_u", "n_nonfinite", "q_mean", "step", "poisson_sweeps_total", "n_guarded",
-    "n_guard_failed", "n_learned_fallback", "reserved22", "reserved23",
+    "n_guard_failed", "n_learned_fallback", "inlet_scale", "reserved23",
 ]
 EXPORTS = ["elbm_init", "elbm_step", "elbm_fields", "elbm_fields_size", "elbm_free",
            "elbm_strerror", "elbm_velocity_set", "elbm_pass_times", "elbm_density_noalloc",
@@ -78,7 +78,8 @@ class InitFields(ctypes.Structure):
     _fields_ = [("mask", ctypes.POINTER(ctypes.c_ubyte)),
                 ("rho0", ctypes.POINTER(ctypes.c_double)), ("u0", ctypes.POINTER(ctypes.c_double)),
                 ("q0", ctypes.POINTER(ctypes.c_double)), ("u_in", ctypes.POINTER(ctypes.c_double)),
-                ("f0", ctypes.POINTER(ctypes.c_double))]
+                ("f0", ctypes.POINTER(ctypes.c_double)),
+                ("inlet_region", ctypes.POINTER(ctypes.c_ubyte))]
 
 
 _lib = None
@@ -327,11 +328,14 @@ class Sim:
         for k in ("rho", "u", "q", "u_in", "f"):
             if k in fields and fields[k] is not None:
                 self._keep[k] = np.ascontiguousarray(fields[k], dtype=np.float64).reshape(-1)
-        mask = fields.get("mask")
-        self._keep["mask"] = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+        for k in ("mask", "inlet_region"):
+            a = fields.get(k)
+            self._keep[k] = None if a is None else np.ascontiguousarray(a, dtype=np.uint8).reshape(-1)
         IF = InitFields()
         m = self._keep["mask"]
         IF.mask = None if m is None else m.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+        r = self._keep["inlet_region"]
+        IF.inlet_region = None if r is None else r.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
         IF.rho0 = _dptr(self._keep.get("rho"))
         IF.u0 = _dptr(self._keep.get("u"))
         IF.q0 = _dptr(self._keep.get("q"))

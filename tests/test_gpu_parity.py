@@ -447,3 +447,42 @@ def test_fp32_alternate_readings(E, case):
         f = nu_o > 0
         assert np.max(np.abs(nu_g[f] - nu_o[f]) / nu_o[f]) <= 5e-5, t
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16"])
+def test_adaptive_inlet(E, precision):
+    """The jet's adaptive inlet (Sec. III B): each step the nozzle's mean
+    velocity rescales the inlet's Poiseuille profile. Against the oracle over
+    four steps: the profile scale (diagnostic 22) and the fields, FP64 at
+    1e-12; FP32 with density, potential and charge within 2e-6, scale 1e-5;
+    BF16 with density 3e-4 and scale 1e-3 (absolute: the scale times the
+    profile's mean 0.02 is the nozzle's mean velocity, here a small
+    difference of opposite flows; the BF16 surface charge, which takes
+    |grad rho|^2 and the curvature of BF16-stored densities, is held by the
+    BF16 nozzle and full-size jet tests)."""
+    cfg, fields = W.jet(shape=(16, 16, 20), nozzle_r=3, wall=1, nozzle_len=6, precision=precision,
+                        adaptive_inlet=True)
+    if precision == "fp64":
+        _tight(cfg)
+    cfg["store_macro"] = 1
+    g = E.Sim(cfg, fields)
+    o = oracle.Sim(dict(cfg, poisson_tol=1e-13), fields)
+    inlet = o.mask == oracle.INLET
+    u0 = np.asarray(fields["u_in"]).reshape(-1, 3)[inlet, 2]
+    for t in range(4):
+        g.step(1)
+        o.step(1)
+        scale_o = float(np.mean(o.u_in.reshape(-1, 3)[inlet, 2] / u0))
+        scale_g = g.diag()["inlet_scale"]
+        if precision == "fp64":
+            assert abs(scale_g - scale_o) <= 1e-12 * abs(scale_o), (t, scale_g, scale_o)
+            compare_fp64(g, o, cfg, fields=("f", "rho", "u", "phi", "q"))
+        else:
+            t5, ts = (2e-6, 1e-5) if precision == "fp32" else (3e-4, 1e-3)
+            fl = o.rho > 0
+            assert abs(scale_g - scale_o) <= ts, (t, scale_g, scale_o)
+            assert rel_l2(g.get("rho")[fl], o.rho[fl]) <= t5, t
+            if precision == "fp32":
+                assert rel_l2(g.get("phi"), o.phi) <= t5 and rel_l2(g.get("q"), o.q) <= t5, t
+    assert abs(scale_o - 1.0) > 1e-4  # the inlet followed the nozzle
+    g.close()
