@@ -114,14 +114,23 @@ struct Ctl {
 };
 
 // Sum (or min / max) each of the K columns of the per-block partials in a
-// fixed order, then derive the scalars of `mode`. One block of 256 threads:
-// run-to-run reproducible.
-__global__ void __launch_bounds__(256) k_finalize(const double *part, int nblocks, int K, int mode, Phys ph,
-                                                  Ctl ctl, double *scal, float *scalf, double *diag,
-                                                  double *colres, unsigned int *ticket)
+// fixed order, then derive the scalars of `mode`. One block of kFinThreads
+// per column, each thread with kFinAcc independent accumulators (so that
+// that many loads are in flight: a lattice of 50 M sites has 400 k partials
+// per column): run-to-run reproducible.
+constexpr int kFinThreads = 1024, kFinAcc = 8;
+constexpr int kMaxCols = 32;  // columns a finalize reduces at most (diagnostics: D_NPART + 1)
+static_assert(D_NPART + 1 <= kMaxCols, "finalize columns");
+__device__ __forceinline__ double fin_op(int op, double a, double v)
+{
+    return op == 0 ? a + v : (op == 1 ? fmin(a, v) : fmax(a, v));
+}
+__global__ void __launch_bounds__(kFinThreads) k_finalize(const double *part, int nblocks, int K, int mode, Phys ph,
+                                                          Ctl ctl, double *scal, float *scalf, double *diag,
+                                                          double *colres, unsigned int *ticket)
 {
     // block k reduces column k of the column-major partials in a fixed order
-    __shared__ double wsum[8];
+    __shared__ double wsum[kFinThreads / 32];
     __shared__ bool last;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int k = blockIdx.x;
@@ -132,20 +141,27 @@ __global__ void __launch_bounds__(256) k_finalize(const double *part, int nblock
     }
     const double id = op == 1 ? 1e300 : (op == 2 ? -1e300 : 0.0);
     const double *col = part + (long long)k * nblocks;
-    double acc = id;
-    for (int i = t; i < nblocks; i += 256) {
-        double v = col[i];
-        acc = op == 0 ? acc + v : (op == 1 ? fmin(acc, v) : fmax(acc, v));
+    double a[kFinAcc];
+#pragma unroll
+    for (int j = 0; j < kFinAcc; j++) a[j] = id;
+    int i = t;
+    for (; i + (kFinAcc - 1) * kFinThreads < nblocks; i += kFinAcc * kFinThreads) {
+        double v[kFinAcc];
+#pragma unroll
+        for (int j = 0; j < kFinAcc; j++) v[j] = col[i + j * kFinThreads];
+#pragma unroll
+        for (int j = 0; j < kFinAcc; j++) a[j] = fin_op(op, a[j], v[j]);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        double c = __shfl_down_sync(0xffffffffu, acc, o);
-        acc = op == 0 ? acc + c : (op == 1 ? fmin(acc, c) : fmax(acc, c));
-    }
+    for (; i < nblocks; i += kFinThreads) a[0] = fin_op(op, a[0], col[i]);
+    double acc = a[0];
+#pragma unroll
+    for (int j = 1; j < kFinAcc; j++) acc = fin_op(op, acc, a[j]);
+    for (int o = 16; o > 0; o >>= 1) acc = fin_op(op, acc, __shfl_down_sync(0xffffffffu, acc, o));
     if (lane == 0) wsum[warp] = acc;
     __syncthreads();
     if (t == 0) {
         double r = wsum[0];
-        for (int w = 1; w < 8; w++) r = op == 0 ? r + wsum[w] : (op == 1 ? fmin(r, wsum[w]) : fmax(r, wsum[w]));
+        for (int w = 1; w < kFinThreads / 32; w++) r = fin_op(op, r, wsum[w]);
         colres[k] = r;
         __threadfence();
         unsigned int tk = atomicAdd(ticket, 1u);
@@ -156,8 +172,8 @@ __global__ void __launch_bounds__(256) k_finalize(const double *part, int nblock
     // the last block to finish derives the scalars of `mode`
     __threadfence();
     *ticket = 0u;
-    double res[16];
-    for (int c = 0; c < K; c++) res[c] = ((volatile double *)colres)[c];
+    double res[kMaxCols];
+    for (int c = 0; c < K && c < kMaxCols; c++) res[c] = ((volatile double *)colres)[c];
     if (mode == FIN_CHARGE_AB) {
         // the factors of Eq. (surface-q2): Q_b / sum(rho theta), Q_s / sum(|grad rho|^2 (1 + ...))
         scal[S_SA] = res[0] > 0.0 ? ph.cd.Qb / res[0] : 0.0;
@@ -313,7 +329,7 @@ int fin(elbm_handle *h, const Bufs &b, cudaStream_t s, int K, int mode, unsigned
 {
     Ctl c = make_ctl(h, cond, use_cond);
     c.steps = steps;
-    k_finalize<<<K, 256, 0, s>>>(b.part, h->L.nblocks, K, mode, h->ph, c, b.scal, b.scalf, b.diag, b.colres,
+    k_finalize<<<K, kFinThreads, 0, s>>>(b.part, h->L.nblocks, K, mode, h->ph, c, b.scal, b.scalf, b.diag, b.colres,
                                  b.ticket);
     return 1;
 }
@@ -325,7 +341,7 @@ int enq_inlet(elbm_handle *h, const Bufs &b, cudaStream_t s)
 {
     if (!h->ph.adaptive) return 0;
     Ctl c = make_ctl(h, 0, 0);
-    k_finalize<<<1, 256, 0, s>>>(b.part + (long long)D_UIN * h->L.nblocks, h->L.nblocks, 1, FIN_INLET, h->ph, c,
+    k_finalize<<<1, kFinThreads, 0, s>>>(b.part + (long long)D_UIN * h->L.nblocks, h->L.nblocks, 1, FIN_INLET, h->ph, c,
                                  b.scal, b.scalf, b.diag, b.colres, b.ticket);
     h->ops.inlet(h->g, h->ph, b, s);
     return 2;
@@ -975,7 +991,7 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
         }
         alloc((void **)&b.scal, S_NSCAL * sizeof(double));
         alloc((void **)&b.scalf, S_NSCAL * sizeof(float));
-        alloc((void **)&b.colres, 16 * sizeof(double));
+        alloc((void **)&b.colres, kMaxCols * sizeof(double));
         alloc((void **)&b.ticket, sizeof(unsigned int));
         alloc((void **)&b.diag, ELBM_NDIAG * sizeof(double));
     };
