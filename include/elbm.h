@@ -109,7 +109,13 @@ enum { ELBM_APREC_FP64 = 0, ELBM_APREC_FP32 = 1, ELBM_APREC_FP32_FAST = 2 };
  * alpha took the float-float guard, 20 sites where the guard ended above
  * 1e-10 rho, 21 learned-alpha sites that fell back to the Newton root,
  * 22 scale of the inlet profile set by the adaptive inlet (0 without it),
- * 23 reserved */
+ * 23 flags of the steps without diagnostics since the previous ones (the
+ * earlier steps of a k-step batch graph, or of diag_every > 1): bit 0 a
+ * non-finite value or non-positive density, bit 1 a guard failure.
+ * 5-12, 14, 16, 19 and 21 are those of the last step; 13 is the maximum
+ * over the last step and those steps; 15 and 20 add 1 when bit 0 resp.
+ * bit 1 of 23 is set, so that a failure on any step reaches the status
+ * elbm_step returns. */
 #define ELBM_NDIAG 24
 
 typedef struct elbm_params {
@@ -163,6 +169,10 @@ typedef struct elbm_params {
     int carreau_lagged;          /* 0: gdot as the root of Eq. (strain2) each step; 1: Eq.
                                     (strain2) with tau from the previous step's nu ("a slow
                                     variation of nu over the time step", Sec. II B), no root */
+    double alpha_h_tol;          /* H-error target |h(alpha)|/rho that the FP32 root
+                                    certifies (float-float guard), 0 = 1e-10; below
+                                    the guard's resolution (~1e-11) sites end as
+                                    guard failures (diag 20); ignored in FP64 */
 } elbm_params;
 
 /* Initial state, all host arrays of N = nx*ny*nz sites (caller-owned):

@@ -404,7 +404,7 @@ __device__ __forceinline__ ffl h_mom(ffl a, ffl a0, const MomFF &m, float *hp, f
 // h'(0) >= 0: alpha = 2), 3 clipped at the positivity bound. Not inlined: one copy of the code, entered only by
 // warps that hold a site needing it.
 static __device__ __noinline__ float4 alpha_guard(const float *dev, float *Dh, float *Dl, float a, float S,
-                                                  float amax, int j, int L)
+                                                  float amax, float htol, int j, int L)
 {
     const Grp gp = grp_make(j, L);
     SiteFF m;
@@ -416,7 +416,7 @@ static __device__ __noinline__ float4 alpha_guard(const float *dev, float *Dh, f
         Dl[p] = D.l;
     }
     const float rho = m.rho.h;
-    const float tol = 1e-10f * rho;
+    const float tol = htol * rho;
     const ffl A0 = h0_ff(dev, Dh, Dl, m, gp);
     // the exact h'(0) can be >= 0 where the FP32 one was < 0 (both at the
     // rounding level): no positive root, alpha = 2 as for status 2
@@ -613,7 +613,7 @@ __device__ __forceinline__ void alpha_fp32_setup(const float *f, const float *d,
 // evaluated |h| or, after an accepted step, the predicted h''/2 d^2.
 __device__ __forceinline__ AlphaOutF alpha_fp32_solve(const float *f, const float *d, const float *dev, float rho,
                                                       const AlphaSetupF &st, bool guard, float a_start,
-                                                      bool defer_guard = false)
+                                                      bool defer_guard = false, float htol = 1e-10f)
 {
     AlphaOutF o;
     o.alpha = 2.f; o.alpha_lo = 0.f; o.herr = 0.f; o.status = st.status; o.guarded = 0; o.iters = 0;
@@ -683,7 +683,7 @@ __device__ __forceinline__ AlphaOutF alpha_fp32_solve(const float *f, const floa
                         0x1p-24f * fmaf(0.6f, irho, 1.f) * a * aF * st.M2;
     o.herr = (hres + bound) * irho;
     if (!guard || o.status == 3) return o;
-    const float tol = 1e-10f * rho;
+    const float tol = htol * rho;
     const bool need = !(hres + bound <= 0.5f * tol);
     if (need && defer_guard) {  // the caller runs alpha_guard (compacted) and fills in the result
         o.guarded = 2;
@@ -692,7 +692,7 @@ __device__ __forceinline__ AlphaOutF alpha_fp32_solve(const float *f, const floa
     if (need) {
         o.guarded = 1;
         float Dh[Q], Dl[Q];
-        const float4 gr = alpha_guard(dev, Dh, Dl, a, st.S, st.amax, 0, 1);
+        const float4 gr = alpha_guard(dev, Dh, Dl, a, st.S, st.amax, htol, 0, 1);
         o.alpha = gr.x;
         o.alpha_lo = gr.y;
         o.herr = gr.z;

@@ -232,16 +232,23 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const double *part, in
         diag[10] = res[D_NCLIP];
         diag[11] = scal[S_ITER] * ctl.ce;
         diag[12] = scal[S_RESID];
-        diag[13] = res[D_HERR];
+        // the sticky record of the steps without diagnostics since the
+        // last ones (k-step graphs, diag_every > 1) folds in, then restarts
+        volatile unsigned int *sk = ticket + 2;
+        const unsigned int sflags = sk[1];
+        diag[13] = fmax(res[D_HERR], (double)__uint_as_float(sk[0]));
         diag[14] = res[D_UMAX];
-        diag[15] = res[D_NBAD];
+        diag[15] = res[D_NBAD] + ((sflags & 1u) ? 1.0 : 0.0);
         diag[16] = scal[S_QMEAN];
         scal[S_STEPS] += double(ctl.steps);
         diag[17] = scal[S_STEPS];
         diag[18] = scal[S_ITER_TOTAL] * ctl.ce;
         diag[19] = res[D_NGUARD];
-        diag[20] = res[D_NGFAIL];
+        diag[20] = res[D_NGFAIL] + ((sflags & 2u) ? 1.0 : 0.0);
         diag[21] = res[D_NLFALL];
+        diag[23] = (double)sflags;
+        sk[0] = 0u;
+        sk[1] = 0u;
     }
     for (int i = 0; i < S_NSCAL; i++) scalf[i] = (float)scal[i];
 }
@@ -277,6 +284,7 @@ int validate(const elbm_params *p, const elbm_init_fields *in, int n_instances)
     // FP32 arithmetic leaves about 3e-7 of noise in Delta_p/f_p; an alpha root
     // sought below a few times that is a root of rounding noise
     if (p->precision != ELBM_PREC_FP64 && !(p->alpha_eq_tol >= 0x1p-18)) return 1;
+    if (!(p->alpha_h_tol >= 0.0) || !(p->alpha_h_tol < 1.0)) return 1;
     if (p->charge_model != ELBM_CHARGE_NONE) {
         if (!(p->theta_width > 0.0) || !(p->K_d > 0.0)) return 1;
         if (!(p->sor_omega > 0.0 && p->sor_omega < 2.0)) return 1;
@@ -793,6 +801,7 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     k.Qb = p->Q_b; k.Qs = p->Q_s; k.iKd = 1.0 / p->K_d; k.xib = p->xi_b; k.xis = p->xi_s;
     k.omega = p->sor_omega;
     k.eq_tol = p->alpha_eq_tol;
+    k.htol = p->alpha_h_tol > 0.0 ? p->alpha_h_tol : 1e-10;
     const int nax[3] = {p->nx, p->ny, p->nz};
     k.phi_lo = p->phi_lo; k.phi_hi = p->phi_hi; k.phi_solid = p->phi_solid;
     k.phi_slope = (p->phi_hi - p->phi_lo) / (nax[p->phi_axis] + 1.0);
@@ -992,7 +1001,8 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
         alloc((void **)&b.scal, S_NSCAL * sizeof(double));
         alloc((void **)&b.scalf, S_NSCAL * sizeof(float));
         alloc((void **)&b.colres, kMaxCols * sizeof(double));
-        alloc((void **)&b.ticket, sizeof(unsigned int));
+        alloc((void **)&b.ticket, 4 * sizeof(unsigned int));  // the ticket; [2..3] the sticky record
+        b.sticky = b.ticket + 2;
         alloc((void **)&b.diag, ELBM_NDIAG * sizeof(double));
     };
     plan();

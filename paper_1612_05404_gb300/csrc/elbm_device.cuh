@@ -93,6 +93,7 @@ struct Cst {
     T Qb, Qs, iKd, xib, xis;         // charge models
     T omega;                         // SOR relaxation
     T eq_tol;                        // alpha near-equilibrium threshold
+    T htol;                          // H-error target per unit density of the FP32 alpha root
     T phi_lo, phi_hi, phi_solid, phi_slope;  // potential data; slope = (hi - lo)/(n_axis + 1)
     T nu0, nu_inf, lam, nexp;        // Carreau: nexp = (n - 1)/2
 };

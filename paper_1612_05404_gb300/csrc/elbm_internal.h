@@ -64,6 +64,10 @@ struct Bufs {
     float *scalf;                     // the same scalars rounded to FP32
     double *colres;                   // per-column results of the finalize kernel
     unsigned int *ticket;             // last-block-done counter of the finalize kernel
+    // sticky record of the steps without diagnostics since the last ones:
+    // [0] their max H-error (order-preserving bits of a float >= 0),
+    // [1] their flags (1 non-finite or non-positive density, 2 guard failure)
+    unsigned int *sticky;
     double *diag;                     // ELBM_NDIAG diagnostics
     const void *mlpimg;               // learned alpha: BF16 shared-memory image of the network
     void *phi_old;                    // potential of the previous step (extrapolated warm start)

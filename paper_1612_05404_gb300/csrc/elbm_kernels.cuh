@@ -303,6 +303,26 @@ __device__ __forceinline__ int pois_nb(const Geom &g, const Cst<T> &k, const uns
     *nb = i;
     return 0;
 }
+// A site whose six face neighbours lie inside the domain without a periodic
+// wrap and none of them solid: every face of the Poisson stencil is an
+// unknown neighbour at s +- off[a] (off = 1, nx, nx ny), its profile
+// difference dl being +-slope along phi_axis in the deviation form. The
+// stencil kernels take this path there, with the same operations in the
+// same order as the general one (pois_nb), free of its face and mask logic.
+__device__ __forceinline__ bool pois_interior(const Geom &g, const unsigned char *mask, int x, int y, int z, ll s)
+{
+    if (x <= 0 || x >= g.nx - 1 || y <= 0 || y >= g.ny - 1 || z <= 0 || z >= g.nz - 1) return false;
+    if (!mask) return true;
+    const int nx = g.nx, nxy = g.nx * g.ny;
+    return mask[s - 1] != ELBM_NODE_SOLID && mask[s + 1] != ELBM_NODE_SOLID && mask[s - nx] != ELBM_NODE_SOLID &&
+           mask[s + nx] != ELBM_NODE_SOLID && mask[s - nxy] != ELBM_NODE_SOLID && mask[s + nxy] != ELBM_NODE_SOLID;
+}
+template <typename T>
+__device__ __forceinline__ T interior_dl(const Geom &g, const Cst<T> &k, int a, int sg)
+{
+    return (g.phi_lin && a == g.phi_axis) ? T(sg) * k.phi_slope : T(0);
+}
+
 // phi_lin at the site (0 without the deviation form)
 template <typename T>
 __device__ __forceinline__ T phi_lin_at(const Geom &g, const Cst<T> &k, int x, int y, int z)
@@ -576,29 +596,42 @@ __global__ void __launch_bounds__(128) k_sor(Geom g, Phys ph, Bufs b, int color,
     unsigned char kind = b.mask ? b.mask[s] : 0;
     if (kind == ELBM_NODE_SOLID) return;
     const Cst<sc> &k = cst<sc>(ph);
-    Nbr n;
-    nbr_init(n, g, x, y, z, s);
     sc *phi = (sc *)b.phi;
     const sc *rho = (const sc *)b.rho;
     sc es = sc(1) + k.kap * rho[s];
     sc num = kind == ELBM_NODE_FLUID ? ((const sc *)b.q)[s] - scal_of<sc>(b, S_QMEAN) : sc(0);
     sc den = 0;
+    if (pois_interior(g, b.mask, x, y, z, s)) {
+        const int off[3] = {1, g.nx, g.nx * g.ny};
 #pragma unroll
-    for (int a = 0; a < 3; a++)
+        for (int a = 0; a < 3; a++)
 #pragma unroll
-        for (int sg = -1; sg <= 1; sg += 2) {
-            int nb = 0;
-            sc v = 0, dl = 0;
-            int kk = pois_nb<sc>(g, k, b.mask, n, x, y, z, a, sg, &nb, &v, &dl);
-            if (kk == 0) {
-                sc ef = face_eps<sc>(es, sc(1) + k.kap * rho[nb], ph.eps_face);
-                num += ef * (phi[nb] + dl);
+            for (int sg = -1; sg <= 1; sg += 2) {
+                const ll nb = s + sg * off[a];
+                const sc ef = face_eps<sc>(es, sc(1) + k.kap * rho[nb], ph.eps_face);
+                num += ef * (phi[nb] + interior_dl<sc>(g, k, a, sg));
                 den += ef;
-            } else if (kk == 1) {
-                num += es * (v + dl);
-                den += es;
             }
-        }
+    } else {
+        Nbr n;
+        nbr_init(n, g, x, y, z, s);
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int sg = -1; sg <= 1; sg += 2) {
+                int nb = 0;
+                sc v = 0, dl = 0;
+                int kk = pois_nb<sc>(g, k, b.mask, n, x, y, z, a, sg, &nb, &v, &dl);
+                if (kk == 0) {
+                    sc ef = face_eps<sc>(es, sc(1) + k.kap * rho[nb], ph.eps_face);
+                    num += ef * (phi[nb] + dl);
+                    den += ef;
+                } else if (kk == 1) {
+                    num += es * (v + dl);
+                    den += es;
+                }
+            }
+    }
     const sc w = gauss_seidel ? sc(1) : k.omega;
     if (den > sc(0)) phi[s] = (sc(1) - w) * phi[s] + w * num / den;
 }
@@ -620,8 +653,6 @@ __global__ void __launch_bounds__(128) k_resid(Geom g, Phys ph, Bufs b)
     // a potential stored in FP32 cannot fall much below 2^-24 |t|
     sc r2 = 0, q2 = 0, b2 = 0, t2 = 0;
     if (active) {
-        Nbr n;
-        nbr_init(n, g, x, y, z, s);
         const sc *phi = (const sc *)b.phi;
         const sc *rho = (const sc *)b.rho;
         const Cst<sc> &k = cst<sc>(ph);
@@ -630,25 +661,41 @@ __global__ void __launch_bounds__(128) k_resid(Geom g, Phys ph, Bufs b)
         sc r = kind == ELBM_NODE_FLUID ? qs - scal_of<sc>(b, S_QMEAN) : sc(0);
         sc bs = 0;
         sc ps = phi[s];
-        const sc pl = phi_lin_at<sc>(g, k, x, y, z);
         sc t = fabs(r);
+        if (pois_interior(g, b.mask, x, y, z, s)) {
+            const int off[3] = {1, g.nx, g.nx * g.ny};
 #pragma unroll
-        for (int a = 0; a < 3; a++)
+            for (int a = 0; a < 3; a++)
 #pragma unroll
-            for (int sg = -1; sg <= 1; sg += 2) {
-                int nb = 0;
-                sc v = 0, dl = 0;
-                int kk = pois_nb<sc>(g, k, b.mask, n, x, y, z, a, sg, &nb, &v, &dl);
-                if (kk == 0) {
+                for (int sg = -1; sg <= 1; sg += 2) {
+                    const ll nb = s + sg * off[a];
+                    const sc dl = interior_dl<sc>(g, k, a, sg);
                     const sc cf = face_eps<sc>(es, sc(1) + k.kap * rho[nb], ph.eps_face);
                     r += cf * ((phi[nb] + dl) - ps);
                     t += cf * (fabs(phi[nb]) + fabs(dl) + fabs(ps));
-                } else if (kk == 1) {
-                    r += es * ((v + dl) - ps);
-                    bs += es * (v + dl + pl);  // the Dirichlet datum itself (reference norm)
-                    t += es * (fabs(v) + fabs(dl) + fabs(ps));
                 }
-            }
+        } else {
+            Nbr n;
+            nbr_init(n, g, x, y, z, s);
+            const sc pl = phi_lin_at<sc>(g, k, x, y, z);
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+#pragma unroll
+                for (int sg = -1; sg <= 1; sg += 2) {
+                    int nb = 0;
+                    sc v = 0, dl = 0;
+                    int kk = pois_nb<sc>(g, k, b.mask, n, x, y, z, a, sg, &nb, &v, &dl);
+                    if (kk == 0) {
+                        const sc cf = face_eps<sc>(es, sc(1) + k.kap * rho[nb], ph.eps_face);
+                        r += cf * ((phi[nb] + dl) - ps);
+                        t += cf * (fabs(phi[nb]) + fabs(dl) + fabs(ps));
+                    } else if (kk == 1) {
+                        r += es * ((v + dl) - ps);
+                        bs += es * (v + dl + pl);  // the Dirichlet datum itself (reference norm)
+                        t += es * (fabs(v) + fabs(dl) + fabs(ps));
+                    }
+                }
+        }
         r2 = r * r;
         q2 = qs * qs;
         b2 = bs * bs;
@@ -748,6 +795,8 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
     ct dm = 0, dmx = 0, dmy = 0, dmz = 0, dq = 0, dasum = 0;
     unsigned dnfl = 0, dsh = 0, dnr = 0, dcl = 0, dbad = 0, dgd = 0, dgf = 0, dlf = 0;
     float damin = 1e30f, damax = -1e30f, dherr = 0.f, dumax = 0.f;
+    float sherr = 0.f;   // a step without diagnostics: the site's H-error and
+    unsigned sflag = 0;  // flags (1 non-finite or non-positive density, 2 guard failure)
     // the first part's results, carried across the block-level guard section
     Nbr n;
     ct f[Q], D[Q];
@@ -775,7 +824,7 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
 #pragma unroll
                 for (int p = 0; p < Q; p++) ast.x[p] = __fdividef(D[p], ff[p]);
             }
-            AlphaOutF ao = alpha_fp32_solve(ff, D, f, float(r), ast, AP == ELBM_APREC_FP32, a_start, kQueue);
+            AlphaOutF ao = alpha_fp32_solve(ff, D, f, float(r), ast, AP == ELBM_APREC_FP32, a_start, kQueue, ph.cf.htol);
             alpha = ct(ao.alpha);
             alpha_lo = ao.alpha_lo;
             a_herr = ao.herr;
@@ -964,7 +1013,7 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
         const int site = tid >> lg, j = tid & ((1 << lg) - 1);
         if (site < nq) {
             GuardEntry &e = gq[site];
-            const float4 gr = alpha_guard(e.dev, e.Dh, e.Dl, e.a, e.S, e.amax, j, 1 << lg);
+            const float4 gr = alpha_guard(e.dev, e.Dh, e.Dl, e.a, e.S, e.amax, ph.cf.htol, j, 1 << lg);
             if (j == 0) gq[site].res = gr;
         }
         __syncthreads();
@@ -1061,6 +1110,23 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
             const float um2 = float(upx * upx + upy * upy + upz * upz);  // |u|^2; the root once per block
             dumax = um2;
             if (!(r > ct(0)) || !isfinite(float(r)) || !isfinite(um2) || !isfinite(float(alpha))) dbad = 1;
+        } else {
+            sherr = a_herr;
+            const float um2 = float(upx * upx + upy * upy + upz * upz);
+            if (!(r > ct(0)) || !isfinite(float(r)) || !isfinite(um2) || !isfinite(float(alpha))) sflag = 1u;
+            if (a_status == 4) sflag |= 2u;
+        }
+    }
+    if (!diag) {
+        // a step without diagnostics still keeps the sticky record that the
+        // next diagnostics fold in: one warp-wide maximum of the H-error (as
+        // its order-preserving integer) and one OR of the flags, each a
+        // single reduction into the record per warp
+        const int hw = __reduce_max_sync(0xffffffffu, float_ord(sherr, 0.f));
+        const unsigned fw = __reduce_or_sync(0xffffffffu, sflag);
+        if ((tid & 31) == 0) {
+            if (hw > 0) atomicMax(reinterpret_cast<int *>(b.sticky), hw);
+            if (fw) atomicOr(b.sticky + 1, fw);
         }
     }
     if (b.region) {  // adaptive inlet, every step: block sums of u . d over the region
@@ -1448,6 +1514,18 @@ __device__ __forceinline__ typename Tr<PR>::sc mg_resid_at(const Geom &g, const 
         const T es = T(1) + k.kap * rho[s];
         const T ps = phi[s];
         T r = kind == ELBM_NODE_FLUID ? ((const T *)bf.q)[s] - scal_of<T>(bf, S_QMEAN) : T(0);
+        if (pois_interior(g, bf.mask, x, y, z, s)) {
+            const int off[3] = {1, g.nx, g.nx * g.ny};
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+#pragma unroll
+                for (int sg = -1; sg <= 1; sg += 2) {
+                    const ll nb = s + sg * off[a];
+                    r += face_eps<T>(es, T(1) + k.kap * rho[nb], ph.eps_face) *
+                         ((phi[nb] + interior_dl<T>(g, k, a, sg)) - ps);
+                }
+            return r;
+        }
         Nbr n;
         nbr_init(n, g, x, y, z, s);
 #pragma unroll

@@ -21,7 +21,7 @@ DIAG_NAMES = [
     "mass", "mom_x", "mom_y", "mom_z", "charge", "alpha_min", "alpha_max", "alpha_mean",
     "n_shortcut", "n_noroot", "n_clipped", "poisson_sweeps", "poisson_resid", "max_h_error",
     "max_u", "n_nonfinite", "q_mean", "step", "poisson_sweeps_total", "n_guarded",
-    "n_guard_failed", "n_learned_fallback", "inlet_scale", "reserved23",
+    "n_guard_failed", "n_learned_fallback", "inlet_scale", "flags_undiagnosed",
 ]
 EXPORTS = ["elbm_init", "elbm_step", "elbm_fields", "elbm_fields_size", "elbm_free",
            "elbm_strerror", "elbm_velocity_set", "elbm_pass_times", "elbm_density_noalloc",
@@ -71,6 +71,7 @@ class Params(ctypes.Structure):
         ("cuda_stream", ctypes.c_void_p),
         ("mlp", ctypes.c_void_p),
         ("eps_face", ctypes.c_int), ("carreau_lagged", ctypes.c_int),
+        ("alpha_h_tol", ctypes.c_double),
     ]
 
 
@@ -182,6 +183,7 @@ def make_params(cfg: dict, stream=None) -> Params:
     P.cuda_stream = stream
     P.eps_face = {"arithmetic": 0, "harmonic": 1}[cfg.get("eps_face", "arithmetic")]
     P.carreau_lagged = int(cfg.get("carreau_lagged", 0))
+    P.alpha_h_tol = float(cfg.get("alpha_h_tol", 0.0))
     mlp = cfg.get("mlp")
     P.mlp = None if mlp is None else mlp.data_ptr()
     return P

@@ -78,6 +78,8 @@ def test_strerror(L):
     dict(charge_model="transport", shape=(5, 4, 4)),   # odd periodic extent for red-black
     dict(precision="fp16"),
     dict(carreau_lagged=2),
+    dict(alpha_h_tol=-1e-10),
+    dict(alpha_h_tol=float("nan")),
 ])
 def test_invalid_parameters_rejected_without_allocation(L, bad):
     cfg = W.base_params(shape=(4, 4, 4))

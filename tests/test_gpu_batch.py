@@ -152,3 +152,81 @@ def test_span_graphs_reproduce_one_step_launches_bitwise(pipeline):
         assert a.diag() == b.diag()
     b1.close()
     b4.close()
+
+
+def _uniform_kick(**extra):
+    """A periodic 16^3 lattice in one uniform state far from equilibrium
+    (f_p = w_p (1 + e_p), e_p ~ U(-0.1, 0.1), the same at every site; no
+    Shan-Chen coupling): the first collision takes the entropic root at every
+    site (S = 0.14), after it the lattice sits within S < 1e-3 of equilibrium,
+    below the near-equilibrium shortcut of 0.05, so every later step takes
+    alpha = 2 without a root (the oracle: 4096 shortcuts from the second
+    step on)."""
+    from paper_1612_05404_gb300 import elbm
+    cfg = W.base_params(shape=(16, 16, 16), G=0.0, Gw=0.0, precision="fp32", alpha_precision="fp32",
+                        alpha_eq_tol=0.05)
+    cfg.update(extra)
+    _, w = elbm.velocity_set()
+    e = np.random.default_rng(5).uniform(-0.1, 0.1, 19)
+    fs = w * (1.0 + e)
+    N = 16 ** 3
+    fields = dict(rho=np.full(N, fs.sum()), f=np.repeat(fs[:, None], N, axis=1).reshape(-1))
+    return elbm.Sim(cfg, fields)
+
+
+def test_span_graph_reports_the_guard_failures_of_its_first_step():
+    """A graph of four steps forms the full diagnostics on its last step
+    only; the sticky record of the steps before it must carry their guard
+    failures and H-error into those diagnostics. With an H-error target of
+    1e-30 (below what the float-float guard resolves) every root of the
+    first step ends as a guard failure; steps 2-4 take no root."""
+    from paper_1612_05404_gb300 import elbm
+    one = _uniform_kick(alpha_h_tol=1e-30)
+    b1 = elbm.Batch([one], span=1)
+    assert b1.step(1) >= 0
+    d1 = one.diag()
+    assert d1["n_guard_failed"] == 16 ** 3 and d1["n_shortcut"] == 0
+    assert d1["flags_undiagnosed"] == 0
+    assert b1.step(1) >= 0
+    d2 = one.diag()
+    assert d2["n_guard_failed"] == 0 and d2["n_shortcut"] == 16 ** 3 and d2["max_h_error"] == 0.0
+    b1.close()
+
+    four = _uniform_kick(alpha_h_tol=1e-30)
+    b4 = elbm.Batch([four], span=4)
+    assert b4.step(4) >= 0
+    d = four.diag()
+    assert d["step"] == 4 and d["n_shortcut"] == 16 ** 3
+    assert d["flags_undiagnosed"] == 2.0          # bit 1: a guard failure on an earlier step
+    assert d["n_guard_failed"] == 1.0             # none on the last step, plus the flag
+    assert d["max_h_error"] == d1["max_h_error"]  # the first step's, carried over
+    # the record restarts with the diagnostics that folded it in
+    assert b4.step(4) >= 0
+    d = four.diag()
+    assert d["flags_undiagnosed"] == 0.0 and d["n_guard_failed"] == 0.0 and d["max_h_error"] == 0.0
+    b4.close()
+
+
+def test_span_graph_max_h_error_covers_every_step():
+    """At the default target (1e-10) the H-error maximum that a four-step
+    graph reports equals the maximum of the four steps' own diagnostics in
+    one-step launches, bit for bit (here the first step's: the others take
+    no root); the host-issued path with diagnostics every fourth step
+    reports the same."""
+    from paper_1612_05404_gb300 import elbm
+    one = _uniform_kick()
+    b1 = elbm.Batch([one], span=1)
+    herr = []
+    for _ in range(4):
+        assert b1.step(1) >= 0
+        herr.append(one.diag()["max_h_error"])
+    b1.close()
+    assert herr[0] > 0.0 and herr[0] <= 1e-10 and max(herr[1:]) == 0.0
+    four = _uniform_kick()
+    b4 = elbm.Batch([four], span=4)
+    assert b4.step(4) >= 0
+    assert four.diag()["max_h_error"] == max(herr) and four.diag()["flags_undiagnosed"] == 0.0
+    b4.close()
+    host = _uniform_kick(graph=0, diag_every=4)
+    assert host.step(4) == elbm.OK
+    assert host.diag()["max_h_error"] == max(herr)
