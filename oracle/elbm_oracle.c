@@ -598,8 +598,39 @@ static void pois_residual(const ctx_t *C, const unsigned char *mask, const doubl
     *ref = sqrt(q2) + sqrt(b2);
 }
 
-/* Poisson equation div(eps grad phi) = -qn (Sec. II) by red-black SOR,
- * warm-started from phi. Colour of a site = (x+y+z) mod 2. qn is the charge
+/* Colour of a site in the SOR sweep. (x + y + z) mod 2 (red-black) colours
+ * every face neighbour differently unless a periodic extent is odd: there
+ * the two sites across the wrap, x = 0 and x = n - 1, have the same parity.
+ * With an odd periodic extent the sweep takes three colours, (c(x) + c(y) +
+ * c(z)) mod 3 with c(i) = i mod 2 except c = 2 at i = n - 1 on an odd
+ * periodic axis: c differs by 1 or 2 between face neighbours on every axis
+ * (the wrap included), so the sum mod 3 does too. The sweep order is the
+ * paper's free choice (it states SOR, not an ordering); the converged
+ * potential is the solution of the same discrete system. */
+static int odd_periodic(const ctx_t *C, int a)
+{
+    const int n = a == 0 ? C->nx : (a == 1 ? C->ny : C->nz);
+    return C->p->face_bc[2 * a] == ORC_FACE_PERIODIC && (n & 1) && n > 1;
+}
+static int sor_ncolors(const ctx_t *C)
+{
+    for (int a = 0; a < C->dim; a++)
+        if (odd_periodic(C, a)) return 3;
+    return 2;
+}
+static int col3_axis(const ctx_t *C, int a, int i)
+{
+    const int n = a == 0 ? C->nx : (a == 1 ? C->ny : C->nz);
+    return (odd_periodic(C, a) && i == n - 1) ? 2 : (i & 1);
+}
+static int sor_color(const ctx_t *C, int ncol, int x, int y, int z)
+{
+    if (ncol == 2) return (x + y + z) & 1;
+    return (col3_axis(C, 0, x) + col3_axis(C, 1, y) + (C->dim == 3 ? col3_axis(C, 2, z) : 0)) % 3;
+}
+
+/* Poisson equation div(eps grad phi) = -qn (Sec. II) by SOR with the site
+ * ordering of sor_color, warm-started from phi. qn is the charge
  * after neutralisation, qmean the uniform charge that was subtracted. The
  * iteration stops when ||r||_2 <= tol (||q||_2 + ||b||_2), q = qn + qmean the
  * free charge on fluid nodes and b the Dirichlet data, or after a fixed
@@ -616,6 +647,7 @@ int orc_poisson_solve(const orc_params *p, const unsigned char *mask, const doub
 #pragma omp parallel for schedule(static)
     for (long s = 0; s < C.N; s++) eps[s] = eps_of(p, rho[s]);
     double w = p->sor_omega, rn = 0.0, ref = 0.0;
+    const int ncol = sor_ncolors(&C);
     int k = 0;
     for (;;) {
         if (p->poisson_fixed_sweeps > 0) {
@@ -624,13 +656,13 @@ int orc_poisson_solve(const orc_params *p, const unsigned char *mask, const doub
             pois_residual(&C, mask, eps, qn, qmean, phi, &rn, &ref, t3);
             if (rn <= p->poisson_tol * ref || k >= p->poisson_maxit) break;
         }
-        /* the sites of one colour read only the other colour */
-        for (int color = 0; color < 2; color++)
+        /* the sites of one colour read only the other colours */
+        for (int color = 0; color < ncol; color++)
 #pragma omp parallel for schedule(static)
             for (long s = 0; s < C.N; s++) {
                 int x, y, z;
                 coords(&C, s, &x, &y, &z);
-                if (((x + y + z) & 1) != color || mask[s] == ORC_SOLID) continue;
+                if (sor_color(&C, ncol, x, y, z) != color || mask[s] == ORC_SOLID) continue;
                 double num = qn[s], den = 0.0;
                 for (int a = 0; a < C.dim; a++)
                     for (int sg = -1; sg <= 1; sg += 2) {
@@ -761,12 +793,6 @@ static int validate(const orc_params *p)
     for (int f = 0; f < 2 * p->dim; f++)
         if ((p->face_bc[f] == ORC_FACE_PERIODIC) != (p->phi_bc[f] == ORC_PHI_PERIODIC)) return -1;
     if (p->nu0 <= 0.0 || p->nu_inf <= 0.0 || p->rho0 <= 0.0) return -1;
-    if (p->charge_model != ORC_CHARGE_NONE) {
-        int n[3] = {p->nx, p->ny, p->nz};
-        /* red-black ordering needs even periodic extents */
-        for (int a = 0; a < p->dim; a++)
-            if (p->face_bc[2 * a] == ORC_FACE_PERIODIC && (n[a] & 1) && n[a] > 1) return -2;
-    }
     return 0;
 }
 

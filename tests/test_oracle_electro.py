@@ -32,6 +32,67 @@ def test_poisson_periodic_matches_direct_solve():
     assert np.allclose(phi, ref - ref.mean(), rtol=0, atol=1e-11 * np.abs(ref).max())
 
 
+def test_poisson_odd_periodic_extents_match_direct_solve():
+    """Odd periodic extents (5 x 7 x 3, every axis periodic): red-black cannot
+    colour them (the two sites across the wrap share a parity), the sweep takes
+    the three-colour ordering; its converged potential is the direct solution
+    of the same discrete system."""
+    shape = (5, 7, 3)
+    N = 105
+    cfg = W.base_params(shape=shape, charge_model="xi", poisson_tol=1e-14, eps_kappa=0.7)
+    rng = np.random.default_rng(82)
+    rho = rng.uniform(0.16, 2.0, N)
+    q = rng.standard_normal(N)
+    qn = q - q.mean()
+    phi, ref, it, res = _dense_vs_sor(cfg, np.zeros(N, np.uint8), rho, qn)
+    assert res <= 1e-14 and it > 0
+    assert np.allclose(phi, ref - ref.mean(), rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+def test_poisson_odd_periodic_with_electrodes_matches_direct_solve():
+    """An odd periodic extent beside even ones and Dirichlet electrodes (7 x 4
+    x 5, periodic in x and y, electrodes on the z faces, one conductor node)."""
+    shape = (7, 4, 5)
+    N = 140
+    cfg = W.base_params(shape=shape, charge_model="xi", poisson_tol=1e-14,
+                        face_bc=["periodic"] * 4 + ["wall", "wall"],
+                        phi_bc=["periodic"] * 4 + ["dirichlet", "dirichlet"],
+                        phi_lo=0.1, phi_hi=-0.4, phi_solid=0.05)
+    rng = np.random.default_rng(83)
+    mask = np.zeros(N, np.uint8)
+    mask[61] = oracle.SOLID
+    rho = rng.uniform(0.16, 2.0, N)
+    qn = rng.standard_normal(N) * (mask == 0)
+    phi, ref, it, res = _dense_vs_sor(cfg, mask, rho, qn)
+    fl = mask == 0
+    assert np.allclose(phi[fl], ref[fl], rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+def test_three_colour_sweep_is_independent_of_the_thread_count():
+    """A site updates from sites of other colours only, so the result of a
+    sweep does not depend on how the sites of a colour are split over
+    threads: two fixed sweeps on 1 and 4 threads agree bit for bit (with two
+    colours on an odd periodic extent, the two sites across the wrap would
+    read each other while being written)."""
+    shape = (9, 5, 7)
+    N = 315
+    cfg = W.base_params(shape=shape, charge_model="xi", poisson_fixed_sweeps=2, eps_kappa=0.7)
+    rng = np.random.default_rng(84)
+    rho = rng.uniform(0.16, 2.0, N)
+    q = rng.standard_normal(N)
+    qn = q - q.mean()
+    mask = np.zeros(N, np.uint8)
+    n0 = oracle.set_threads(0)
+    try:
+        out = []
+        for t in (1, 4):
+            oracle.set_threads(t)
+            out.append(oracle.poisson_solve(cfg, mask, rho, qn)[0])
+    finally:
+        oracle.set_threads(n0)
+    assert np.array_equal(out[0], out[1])
+
+
 def test_poisson_dirichlet_and_conductors_match_direct_solve():
     shape = (6, 4, 5)
     N = 120
