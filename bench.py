@@ -59,6 +59,11 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary measurements (alpha comparison, drop, batch, jet 128)")
     ap.add_argument("--boxes", type=int, default=512, help="batched-droplets comparison: boxes (0 skips it)")
+    ap.add_argument("--batched-steps", type=int, default=40, help="batched-droplets comparison: timed steps")
+    ap.add_argument("--ncu-case", default="", choices=["", "jet128", "jet4"],
+                    help="profiling run for ncu: the 128x128x512 (or 256x256x768) jet with learned alpha, "
+                         "steps issued from the host (every kernel a separate launch), fixed block shape; "
+                         "--warmup + --steps steps, no timing")
     ap.add_argument("--span", type=int, default=0,
                     help="drop-in-field batch: steps per graph launch besides span 1 (0: the span that "
                          "covers --steps in the fewest launches)")
@@ -538,60 +543,96 @@ def jet128(args):
             "workload": "128x128x512 jet, BF16 relative to the site density, guarded FP32 Newton alpha"}
 
 
-def batched_compare(args):
-    """Batched droplets (uneven boxes, one CUDA graph launch per step for
-    all, diagnostics every step) against the same boxes stepped one at a
-    time, at the same H-error bound (guarded FP32 alpha), FP32 storage."""
+def batched_compare(args, theta):
+    """Config 5: batched droplets (boxes of every integer edge in [24, 96],
+    learned alpha when a network is given), all boxes one CUDA graph launch
+    per step (diagnostics every step) and graphs of 10 steps (diagnostics on
+    the last, the sticky record of H-error and failures on every step),
+    against the same boxes stepped one at a time with plain guarded Newton
+    alpha (and, to isolate the batching, with the same alpha as the batch).
+    FP32 storage; the H-error maximum covers every timed step."""
     import torch
     from paper_1612_05404_gb300 import elbm
     from paper_1612_05404_gb300 import workloads as W
     params = W.batched_droplet_params(n_boxes=args.boxes)
-    t0 = time.perf_counter()
-    sims = []
-    for edge, E0, nc in params:
-        cfg, fields = W.batched_droplet(edge, E0, nc, precision="fp32")
-        cfg.update(alpha_precision="fp32", autotune=1, graph=1, diag_every=1)
-        sims.append(elbm.Sim(cfg, fields))
-    t_init = time.perf_counter() - t0
     nsites = sum(e ** 3 for e, _, _ in params)
+    steps = args.batched_steps
+
+    def make(learned):
+        out = []
+        for edge, E0, nc in params:
+            cfg, fields = W.batched_droplet(edge, E0, nc, precision="fp32")
+            cfg.update(alpha_precision="fp32", autotune=1, graph=1, diag_every=1)
+            if learned:
+                cfg.update(alpha_mode="learned", mlp=theta)
+            out.append(elbm.Sim(cfg, fields))
+        return out
+
+    def timed_batch(sims, span):
+        t0 = time.perf_counter()
+        batch = elbm.Batch(sims, pipeline=True, span=span)
+        t_cap = time.perf_counter() - t0
+        assert batch.step(args.warmup) >= 0
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st = batch.step(steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        ds = [s.diag() for s in sims]
+        batch.close()
+        return {"mlups": nsites / (ms * 1e-3) / 1e6, "ms_per_step": ms, "steps": steps, "status": st,
+                "max_h_error_device": max(d["max_h_error"] for d in ds),
+                "guard_failed": sum(d["n_guard_failed"] for d in ds),
+                "learned_fallback_sites_last_step": sum(d["n_learned_fallback"] for d in ds),
+                "graph_launches_per_step": 1.0 / span if steps % span == 0 else None,
+                "diagnostics": "every step" if span == 1 else f"last of every {span} steps, sticky record on every step",
+                "capture_seconds": t_cap}
+
+    def one_at_a_time(sims, k=5):
+        total = 0.0
+        for s in sims:
+            s.step(1)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            s.step(k)
+            b.record()
+            torch.cuda.synchronize()
+            total += a.elapsed_time(b) / k
+        return {"mlups": nsites / (total * 1e-3) / 1e6, "ms_per_step": total, "steps_per_box": k,
+                "max_h_error_device": max(s.diag()["max_h_error"] for s in sims),
+                "diagnostics": "every step"}
+
+    learned = theta is not None
     t0 = time.perf_counter()
-    batch = elbm.Batch(sims, pipeline=True, span=1)
-    t_capture = time.perf_counter() - t0
-    batch.step(args.warmup)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    batch.step(args.steps)
-    e1.record()
-    torch.cuda.synchronize()
-    ms_b = e0.elapsed_time(e1) / args.steps
-    hmax_b = max(s.diag()["max_h_error"] for s in sims)
-    batch.close()
-    # the same boxes one at a time: each box's own step graph (diagnostics
-    # every step), its steps finished before the next box starts
-    k = 5
-    single_ms = 0.0
-    for s in sims:
-        s.step(1)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        s.step(k)
-        b.record()
-        torch.cuda.synchronize()
-        single_ms += a.elapsed_time(b) / k
-    hmax_s = max(s.diag()["max_h_error"] for s in sims)
+    sims = make(learned)
+    t_init = time.perf_counter() - t0
+    res = {"boxes": len(params), "sites": nsites, "edges": sorted(set(e for e, _, _ in params)),
+           "odd_edge_boxes": sum(1 for e, _, _ in params if e & 1),
+           "alpha": "learned proposal + guarded FP32 Newton" if learned else "guarded FP32 Newton",
+           "init_seconds": t_init}
+    res["batched_span1"] = timed_batch(sims, 1)
+    res["batched_span10"] = timed_batch(sims, 10)
+    res["one_at_a_time_same_alpha"] = one_at_a_time(sims)
     for s in sims:
         s.close()
-    return {"boxes": len(params), "sites": nsites, "edges": sorted(set(e for e, _, _ in params)),
-            "batched": {"mlups": nsites / (ms_b * 1e-3) / 1e6, "ms_per_step": ms_b, "max_h_error_device": hmax_b,
-                        "graph_launches_per_step": 1, "diagnostics": "every step"},
-            "one_at_a_time": {"mlups": nsites / (single_ms * 1e-3) / 1e6, "ms_per_step": single_ms,
-                              "max_h_error_device": hmax_s, "steps_per_box": k},
-            "speedup_batched_vs_single": single_ms / ms_b,
-            "init_seconds": t_init, "capture_seconds": t_capture,
-            "workload": "batched droplets: periodic cubic boxes, R = edge/4, E0 ~ U[0,1e-3] along z, "
-                        "Carreau n ~ U[0.5,1], lambda 10, transported charge, FP32"}
+    if learned:
+        sims = make(False)
+        res["one_at_a_time_newton"] = one_at_a_time(sims)
+        for s in sims:
+            s.close()
+    else:
+        res["one_at_a_time_newton"] = res["one_at_a_time_same_alpha"]
+    base = res["one_at_a_time_newton"]["ms_per_step"]
+    res["speedup_batched_vs_single_newton"] = base / res["batched_span1"]["ms_per_step"]
+    res["speedup_batched_span10_vs_single_newton"] = base / res["batched_span10"]["ms_per_step"]
+    res["speedup_batched_vs_single_same_alpha"] = (res["one_at_a_time_same_alpha"]["ms_per_step"]
+                                                   / res["batched_span1"]["ms_per_step"])
+    res["workload"] = ("batched droplets: periodic cubic boxes, edge uniform over the integers 24..96, R = edge/4, "
+                       "E0 ~ U[0,1e-3] along z, Carreau n ~ U[0.5,1], lambda 10, transported charge, FP32")
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -654,8 +695,43 @@ def run_reference(args, rank):
     }
 
 
+def ncu_case(args):
+    """The kernels of the headline step as separate launches for ncu: the jet
+    at 128x128x512 (or the headline's 256x256x768), BF16 storage, learned
+    alpha with a seeded Glorot-initialised network scaled by 0.01 (the
+    kernels' cost does not depend on the weights' values; the proposal only
+    starts the certified Newton iteration), multigrid, graph = 0 (the
+    Poisson loop from the host: a graph with a conditional node hides its
+    kernels from ncu), fixed block shape (no autotuner launches)."""
+    import math
+    import numpy as np
+    import torch
+    from paper_1612_05404_gb300 import build, elbm
+    build.build()
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(1)
+    theta = torch.zeros(elbm.MLP_NPARAM, dtype=torch.float32)
+    theta[:1280] = torch.from_numpy(rng.uniform(-math.sqrt(6 / 84), math.sqrt(6 / 84), 1280).astype(np.float32))
+    theta[1344:5440] = torch.from_numpy(rng.uniform(-math.sqrt(6 / 128), math.sqrt(6 / 128), 4096).astype(np.float32))
+    theta[5504:5568] = torch.from_numpy(rng.uniform(-math.sqrt(6 / 65), math.sqrt(6 / 65), 64).astype(np.float32))
+    theta = theta.cuda() * 0.01
+    shape = (128, 128, 512) if args.ncu_case == "jet128" else JET4_SHAPE
+    cfg, fields = jet_case(shape, alpha_mode="learned", theta=theta, graph=0, autotune=0)
+    sim = elbm.Sim(cfg, fields)
+    sim.step(args.warmup + args.steps)
+    torch.cuda.synchronize()
+    d = sim.diag()
+    sim.close()
+    print(json.dumps({"ncu_case": args.ncu_case, "steps": args.warmup + args.steps,
+                      "max_h_error": d["max_h_error"], "guarded": d["n_guarded"],
+                      "poisson_vcycles_total": d["poisson_sweeps_total"]}), flush=True)
+
+
 def main():
     args = parse()
+    if args.ncu_case:
+        ncu_case(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -712,7 +788,7 @@ def main():
         res["jet128"] = jet128(args)
         res["drop64"] = drop64(args)
         if args.boxes > 0:
-            res["batched_compare"] = batched_compare(args)
+            res["batched_compare"] = batched_compare(args, theta)
     if rank == 0 and world == 1 and not args.no_cpu:
         res["cpu_baseline"] = cpu_baseline()
     if world > 1:

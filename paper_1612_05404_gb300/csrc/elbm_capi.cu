@@ -25,6 +25,7 @@ constexpr int kNu = 2;             // pre- and post-smoothing sweeps
 constexpr int kNuTail = 1;         // the same on the levels of the one-CTA tail (reduced precision;
                                    // FP64 solves to 1e-13 keep kNu)
 constexpr int kCoarseSweeps = 8;   // red-black sweeps on the coarsest level (<= 8 cells per axis pair)
+constexpr int kCoarseCells = 512;  // a coarsest level above this size coarsens further, odd extents included
 }
 
 struct elbm_handle {
@@ -289,10 +290,6 @@ int validate(const elbm_params *p, const elbm_init_fields *in, int n_instances)
         if (!(p->theta_width > 0.0) || !(p->K_d > 0.0)) return 1;
         if (!(p->sor_omega > 0.0 && p->sor_omega < 2.0)) return 1;
         if (!(p->poisson_tol >= 0.0) || p->poisson_maxit < 0 || p->poisson_fixed_sweeps < 0) return 1;
-        // red-black ordering needs even periodic extents
-        int n[3] = {p->nx, p->ny, p->nz};
-        for (int a = 0; a < 3; a++)
-            if (p->face_bc[2 * a] == ELBM_FACE_PERIODIC && (n[a] & 1) && n[a] > 1) return 1;
     }
     if (p->charge_model == ELBM_CHARGE_TRANSPORT && !(p->Dq >= 0.0)) return 1;
     if (p->diag_every < 0) return 1;
@@ -362,18 +359,15 @@ int vcycle(elbm_handle *h, const Bufs &b, cudaStream_t s, int l)
         m.tail(h->g, h->tail, h->p.precision == ELBM_PREC_FP64 ? kNu : kNuTail, s);
         return 1;
     }
-    for (int i = 0; i < kNu; i++) {
-        m.smooth(h->g, h->ph, b, h->lev[l], l, 0, h->Lh, s);
-        m.smooth(h->g, h->ph, b, h->lev[l], l, 1, h->Lh, s);
-    }
+    const int nc = h->lev[l].ncol;
+    for (int i = 0; i < kNu; i++)
+        for (int c = 0; c < nc; c++) m.smooth(h->g, h->ph, b, h->lev[l], l, c, h->Lh, s);
     m.restrict_(h->g, h->ph, b, h->lev[l], h->lev[l + 1], l, s);
     int n = vcycle(h, b, s, l + 1);
     m.prolong(h->g, b, h->lev[l], h->lev[l + 1], l, s);
-    for (int i = 0; i < kNu; i++) {
-        m.smooth(h->g, h->ph, b, h->lev[l], l, 0, h->Lh, s);
-        m.smooth(h->g, h->ph, b, h->lev[l], l, 1, h->Lh, s);
-    }
-    return n + 4 * kNu + 2;
+    for (int i = 0; i < kNu; i++)
+        for (int c = 0; c < nc; c++) m.smooth(h->g, h->ph, b, h->lev[l], l, c, h->Lh, s);
+    return n + 2 * nc * kNu + 2;
 }
 
 // moments, and the free charge with its global sums (Sec. II C, item 3)
@@ -415,11 +409,9 @@ int enq_check(elbm_handle *h, const Bufs &b, cudaStream_t s, int mode, unsigned 
 int enq_unit(elbm_handle *h, const Bufs &b, cudaStream_t s)
 {
     if (h->nlev > 0) return vcycle(h, b, s, 0);
-    for (int i = 0; i < h->ce; i++) {
-        h->ops.sor(h->g, h->ph, b, 0, h->Lh, s);
-        h->ops.sor(h->g, h->ph, b, 1, h->Lh, s);
-    }
-    return 2 * h->ce;
+    for (int i = 0; i < h->ce; i++)
+        for (int c = 0; c < h->g.ncol; c++) h->ops.sor(h->g, h->ph, b, c, h->Lh, s);
+    return h->g.ncol * h->ce;
 }
 
 // zero-mean potential when nothing pins its constant
@@ -769,6 +761,7 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     Geom &g = h->g;
     g.nx = p->nx; g.ny = p->ny; g.nz = p->nz; g.N = N;
     for (int a = 0; a < 3; a++) g.per[a] = p->face_bc[2 * a] == ELBM_FACE_PERIODIC;
+    g.ncol = ncolors_of(g.per, p->nx, p->ny, p->nz);
     for (int f = 0; f < 6; f++) g.phi_kind[f] = p->phi_bc[f];
     g.phi_axis = p->phi_axis;
     // reduced precision: the potential plane holds its deviation from the
@@ -864,7 +857,7 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     if (L.grid.y > 65535 || L.grid.z > 65535) { delete h; return ELBM_E_INVAL; }
     {
         Launch &H = h->Lh;
-        const int nh = (p->nx + 1) / 2;
+        const int nh = g.ncol == 3 ? p->nx : (p->nx + 1) / 2;  // three colours: one thread per site
         int hx = nh >= 128 ? 128 : ((nh + 31) / 32) * 32;
         int hy = 128 / hx;
         H.block = dim3(hx, hy, 1);
@@ -873,11 +866,24 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     }
 
     // multigrid hierarchy: halve while every extent is even (and stays even on
-    // periodic axes, for the red-black colouring) and the level has > 64 cells
+    // periodic axes) and at least 4; then, while the coarsest level has more
+    // than kCoarseCells cells, halve to (n + 1)/2 cells per axis, the last
+    // cell of an odd extent a single child (its span kept in last[])
     h->nlev = 0;
     if (p->charge_model != ELBM_CHARGE_NONE && p->poisson_solver == ELBM_POISSON_MG) {
-        int n[3] = {p->nx, p->ny, p->nz};
-        h->lev[0].nx = n[0]; h->lev[0].ny = n[1]; h->lev[0].nz = n[2]; h->lev[0].N = N;
+        int n[3] = {p->nx, p->ny, p->nz}, last[3] = {1, 1, 1};
+        auto set_level = [&](int l) {
+            MGLevel &v = h->lev[l];
+            v.nx = n[0]; v.ny = n[1]; v.nz = n[2];
+            v.N = (long long)n[0] * n[1] * n[2];
+            v.irr = 0;
+            for (int a = 0; a < 3; a++) {
+                v.last[a] = last[a];
+                if (last[a] != (1 << l)) v.irr = 1;
+            }
+            v.ncol = ncolors_of(g.per, n[0], n[1], n[2]);
+        };
+        set_level(0);
         int L = 1;
         while (L < kMaxLevels) {
             bool ok = true;
@@ -886,9 +892,21 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
                 if (g.per[a] && ((n[a] / 2) & 1)) ok = false;
             }
             if (!ok) break;
-            for (int a = 0; a < 3; a++) n[a] /= 2;
-            h->lev[L].nx = n[0]; h->lev[L].ny = n[1]; h->lev[L].nz = n[2];
-            h->lev[L].N = (long long)n[0] * n[1] * n[2];
+            for (int a = 0; a < 3; a++) { n[a] /= 2; last[a] *= 2; }
+            set_level(L);
+            L++;
+        }
+        while (L < kMaxLevels && h->lev[L - 1].N > kCoarseCells) {
+            bool ok = true;
+            for (int a = 0; a < 3; a++)
+                if (n[a] < 4) ok = false;
+            if (!ok) break;
+            const int S = 1 << (L - 1);  // span of the regular cells of level L - 1
+            for (int a = 0; a < 3; a++) {
+                if (!(n[a] & 1)) last[a] += S;  // the last pair: a regular cell and the last one
+                n[a] = (n[a] + 1) / 2;
+            }
+            set_level(L);
             L++;
         }
         if (L < 2) { delete h; return ELBM_E_INVAL; }
@@ -905,6 +923,9 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
         for (int k = 0; k < t.nt; k++) {
             t.nx[k] = h->lev[lt + k].nx; t.ny[k] = h->lev[lt + k].ny; t.nz[k] = h->lev[lt + k].nz;
             t.N[k] = h->lev[lt + k].N;
+            for (int a = 0; a < 3; a++) t.last[k][a] = h->lev[lt + k].last[a];
+            t.irr[k] = h->lev[lt + k].irr;
+            t.ncol[k] = h->lev[lt + k].ncol;
             t.off[k] = t.total;
             t.total += t.N[k];
         }
@@ -1031,8 +1052,11 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
                 for (int Y = 0; Y < C.ny; Y++)
                     for (int X = 0; X < C.nx; X++) {
                         unsigned char any = 0;
-                        for (int c = 0; c < 8; c++)
-                            any |= hm[l - 1][(2 * X + (c & 1)) + (long long)F.nx * ((2 * Y + ((c >> 1) & 1)) + (long long)F.ny * (2 * Z + (c >> 2)))];
+                        for (int c = 0; c < 8; c++) {
+                            const int cx = 2 * X + (c & 1), cy = 2 * Y + ((c >> 1) & 1), cz = 2 * Z + (c >> 2);
+                            if (cx < F.nx && cy < F.ny && cz < F.nz)
+                                any |= hm[l - 1][cx + (long long)F.nx * (cy + (long long)F.ny * cz)];
+                        }
                         hm[l][X + (long long)C.nx * (Y + (long long)C.ny * Z)] = any;
                     }
         }

@@ -80,7 +80,30 @@ struct Geom {
     int has_mask;        // any non-fluid node
     int phi_lin;         // the potential plane holds psi = phi - phi_lin, phi_lin(c) = phi_lo + (c+1) slope
                          // along phi_axis (reduced precision, both electrode faces Dirichlet)
+    int ncol;            // colours of the Poisson sweep ordering: 2 (red-black) or 3 (an odd periodic extent)
 };
+
+// Colour of a cell in the Poisson sweep ordering. Red-black, (x + y + z) mod
+// 2, gives every face neighbour the other colour unless a periodic extent is
+// odd: the two cells across the wrap then share a parity. There the ordering
+// takes three colours, (c(x) + c(y) + c(z)) mod 3 with c(i) = i mod 2 except
+// c = 2 on the last cell of an odd periodic axis; c differs by 1 or 2 between
+// face neighbours on every axis (the wrap included), so the sum mod 3 does.
+__host__ __device__ __forceinline__ int col3_axis(int i, int n, int per)
+{
+    return (per && (n & 1) && n > 1 && i == n - 1) ? 2 : (i & 1);
+}
+__host__ __device__ __forceinline__ int color3(const int per[3], int x, int y, int z, int nx, int ny, int nz)
+{
+    return (col3_axis(x, nx, per[0]) + col3_axis(y, ny, per[1]) + col3_axis(z, nz, per[2])) % 3;
+}
+__host__ __device__ __forceinline__ int ncolors_of(const int per[3], int nx, int ny, int nz)
+{
+    const int n[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; a++)
+        if (per[a] && (n[a] & 1) && n[a] > 1) return 3;
+    return 2;
+}
 
 // Constants of one step in the arithmetic type T, precomputed on the host so
 // FP32 kernels never touch GB300's slow FP64 pipe.

@@ -120,7 +120,6 @@ struct MGOps {
     void (*eps)(const Geom &, const Phys &, const Bufs &, const MGLevel &F, const MGLevel &C, int level,
                 cudaStream_t);
     void (*prolong)(const Geom &, const Bufs &, const MGLevel &F, const MGLevel &C, int level, cudaStream_t);
-    void (*coarse)(const Geom &, const MGLevel &, int level, int sweeps, cudaStream_t);
 };
 
 Ops ops_fp64();

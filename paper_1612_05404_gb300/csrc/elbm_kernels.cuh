@@ -586,12 +586,14 @@ template <int PR>
 __global__ void __launch_bounds__(128) k_sor(Geom g, Phys ph, Bufs b, int color, int gauss_seidel)
 {
     typedef typename Tr<PR>::sc sc;
-    // one thread per site of the colour: x = 2 i + ((y + z + color) & 1)
+    // red-black: one thread per site of the colour, x = 2 i + ((y + z +
+    // color) & 1); three colours: one thread per site, those of the colour work
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    const int x = 2 * i + ((y + z + color) & 1);
+    const int x = g.ncol == 3 ? i : 2 * i + ((y + z + color) & 1);
     if (x >= g.nx || y >= g.ny) return;
+    if (g.ncol == 3 && color3(g.per, x, y, z, g.nx, g.ny, g.nz) != color) return;
     const ll s = x + (ll)g.nx * (y + (ll)g.ny * z);
     unsigned char kind = b.mask ? b.mask[s] : 0;
     if (kind == ELBM_NODE_SOLID) return;
@@ -1008,8 +1010,11 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
         static_assert(!kQueue || kGuardQ >= 128, "one guard-queue entry per thread of a 128-thread block");
         __syncthreads();
         const int nq = gq_n;
-        // L lanes per queued site (the fewer the sites, the more lanes each)
-        const int lg = nq <= 16 ? 3 : (nq <= 32 ? 2 : (nq <= 64 ? 1 : 0));
+        // L lanes per queued site (the fewer the sites, the more lanes each),
+        // as many as the block's threads cover (blocks of 96 threads when a
+        // row of 65..96 sites is one block row)
+        const int nthr = blockDim.x * blockDim.y;
+        const int lg = 8 * nq <= nthr ? 3 : (4 * nq <= nthr ? 2 : (2 * nq <= nthr ? 1 : 0));
         const int site = tid >> lg, j = tid & ((1 << lg) - 1);
         if (site < nq) {
             GuardEntry &e = gq[site];
@@ -1446,53 +1451,161 @@ struct Launchers {
 // Dirichlet face couples with 2 4^l/(2^l + 1) eps_I, which places the
 // boundary where the fine problem has it; restriction sums the 8 child
 // residuals; trilinear (cell-centred) prolongation; red-black Gauss-Seidel
-// smoothing. Level 0 works on phi, q and rho directly; level l >= 1 on the
-// correction e_l, right side b_l and permittivity eps_l.
+// smoothing (three colours on a level with an odd periodic extent). An odd
+// extent coarsens to (n + 1)/2 cells, the last of one child: such a level
+// re-discretises the operator on its cell sizes (mg_face) and interpolates
+// by the cell centres (mg_pweights). Level 0 works on phi, q and rho
+// directly; level l >= 1 on the correction e_l, right side b_l and
+// permittivity eps_l.
 // ===========================================================================
 struct MGLevel {
     int nx, ny, nz;
     long long N;
-    void *e, *b, *eps;     // level >= 1
+    void *e, *b, *eps;       // level >= 1
     const unsigned char *m;  // level >= 1: 1 = conductor cell (correction held at 0), or NULL
+    int last[3];             // fine (level-0) cells spanned by the last cell along each axis
+    int irr;                 // 1 when a last[a] differs from 2^level (coarsened from an odd extent)
+    int ncol;                // colours of its sweep ordering: 2 (red-black) or 3 (an odd periodic extent)
 };
 
+// Coarse-level geometry. The cells of level l span S = 2^l fine (level-0)
+// cells along each axis, except where an axis was coarsened from an odd
+// extent: its last cell, a single child, spans last[a] < S. The coarse
+// operator is the fine one re-discretised on these cells: a face couples its
+// two cells with eps_face A / d (A the face area, d the distance of the two
+// centres, in fine cells), a Dirichlet face couples the cell with eps_s A /
+// d_D, d_D = (s_a + 1)/2 the distance to the fine ghost plane. On a regular
+// level A / d = 2^l and A / d_D = 2 4^l / (2^l + 1) (kap, kb below).
 template <typename T>
-__device__ __forceinline__ int mg_nbr(int v, int n, int per) { return nbc(v, n, per); }
+__device__ __forceinline__ T mg_span(int i, int n, int last, int S) { return T(i == n - 1 ? last : S); }
+template <typename T>
+__device__ __forceinline__ T mg_face(const int n[3], const int last[3], int S, const int c[3], int a, int v)
+{
+    const int b = a == 0 ? 1 : 0, e = a == 2 ? 1 : 2;
+    const T A = mg_span<T>(c[b], n[b], last[b], S) * mg_span<T>(c[e], n[e], last[e], S);
+    return A / (T(0.5) * (mg_span<T>(c[a], n[a], last[a], S) + mg_span<T>(v, n[a], last[a], S)));
+}
+template <typename T>
+__device__ __forceinline__ T mg_dface(const int n[3], const int last[3], int S, const int c[3], int a)
+{
+    const int b = a == 0 ? 1 : 0, e = a == 2 ? 1 : 2;
+    const T A = mg_span<T>(c[b], n[b], last[b], S) * mg_span<T>(c[e], n[e], last[e], S);
+    return A / (T(0.5) * (mg_span<T>(c[a], n[a], last[a], S) + T(1)));
+}
 
-// red-black Gauss-Seidel half sweep on a coarse level (homogeneous Dirichlet)
+// Gauss-Seidel update of coarse cell (x, y, z) of level `level` (the
+// correction equation: homogeneous Dirichlet data)
+template <typename T>
+__device__ __forceinline__ void mg_gs_cell(const Geom &g, T *e, const T *b, const T *ep, const int n[3],
+                                           const int last[3], int level, int irr, int x, int y, int z)
+{
+    const ll s = x + (ll)n[0] * (y + (ll)n[1] * z);
+    const int S = 1 << level;
+    const T kap = T(S), kb = T(2 * (1 << (2 * level))) / T(S + 1);
+    const T es = ep[s];
+    T num = b[s], den = 0;
+    const int cc[3] = {x, y, z};
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int sg = -1; sg <= 1; sg += 2) {
+            int c[3] = {cc[0], cc[1], cc[2]};
+            const int v = nbc(c[a] + sg, n[a], g.per[a]);
+            if (v < 0) {
+                if (g.phi_kind[2 * a + (sg > 0)] == ELBM_PHI_DIRICHLET)
+                    den += (irr ? mg_dface<T>(n, last, S, cc, a) : kb) * es;
+                continue;
+            }
+            c[a] = v;
+            const ll nb = c[0] + (ll)n[0] * (c[1] + (ll)n[1] * c[2]);
+            const T cf = (irr ? mg_face<T>(n, last, S, cc, a, v) : kap) * T(0.5) * (es + ep[nb]);
+            num += cf * e[nb];
+            den += cf;
+        }
+    if (den > T(0)) e[s] = num / den;
+}
+
+// residual of the correction equation at coarse cell (x, y, z)
+template <typename T>
+__device__ __forceinline__ T mg_res_cell(const Geom &g, const T *e, const T *b, const T *ep, const int n[3],
+                                         const int last[3], int level, int irr, int x, int y, int z)
+{
+    const ll s = x + (ll)n[0] * (y + (ll)n[1] * z);
+    const int S = 1 << level;
+    const T kap = T(S), kb = T(2 * (1 << (2 * level))) / T(S + 1);
+    const T es = ep[s], xs = e[s];
+    T r = b[s];
+    const int cc[3] = {x, y, z};
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int sg = -1; sg <= 1; sg += 2) {
+            int c[3] = {cc[0], cc[1], cc[2]};
+            const int v = nbc(c[a] + sg, n[a], g.per[a]);
+            if (v < 0) {
+                if (g.phi_kind[2 * a + (sg > 0)] == ELBM_PHI_DIRICHLET)
+                    r -= (irr ? mg_dface<T>(n, last, S, cc, a) : kb) * es * xs;
+                continue;
+            }
+            c[a] = v;
+            const ll nb = c[0] + (ll)n[0] * (c[1] + (ll)n[1] * c[2]);
+            r += (irr ? mg_face<T>(n, last, S, cc, a, v) : kap) * T(0.5) * (es + ep[nb]) * (e[nb] - xs);
+        }
+    return r;
+}
+
+// Prolongation along one axis: fine cell i of a level whose cells span Sf
+// fine (level-0) cells (its last one lastf) from the coarse level above
+// (spans 2 Sf, its last one lastc). i0 is the parent, i1 the other coarse
+// cell of the pair and w1 its weight (the parent's 1 - w1), linear in the
+// positions of the cell centres: 1/4 on a regular pair, 0 for a single child
+// (its centre is the parent's). Beyond a Neumann face the edge value (w1 =
+// 0); beyond a Dirichlet face the correction is 0 (skip: the i1 term drops,
+// its weight taken as for a regular ghost cell).
+template <typename T>
+__device__ __forceinline__ void mg_pweights(const Geom &g, int a, int i, int nf, int lastf, int Sf, int nc,
+                                            int lastc, int &i0, int &i1, T &w1, bool &skip)
+{
+    const int Sc = 2 * Sf;
+    i0 = i >> 1;
+    i1 = i0;
+    w1 = T(0);
+    skip = false;
+    const T xf = T(i) * T(Sf) + T(0.5) * mg_span<T>(i, nf, lastf, Sf);
+    const T xp = T(i0) * T(Sc) + T(0.5) * mg_span<T>(i0, nc, lastc, Sc);
+    if (xf == xp) return;
+    const int o = xf > xp ? 1 : -1;
+    const int v = nbc(i0 + o, nc, g.per[a]);
+    T dist;
+    if (v < 0) {
+        if (g.phi_kind[2 * a + (o > 0)] != ELBM_PHI_DIRICHLET) return;
+        skip = true;
+        dist = T(0.5) * (mg_span<T>(i0, nc, lastc, Sc) + T(Sc));
+    } else {
+        T xn = T(v) * T(Sc) + T(0.5) * mg_span<T>(v, nc, lastc, Sc);
+        const T len = T(nc - 1) * T(Sc) + T(lastc);  // the axis in fine cells (periodic wrap)
+        if (o > 0 && v < i0) xn += len;
+        if (o < 0 && v > i0) xn -= len;
+        dist = xn > xp ? xn - xp : xp - xn;
+        i1 = v;
+    }
+    w1 = (xf > xp ? xf - xp : xp - xf) / dist;
+}
+
+// Gauss-Seidel sweep of one colour on a coarse level
 template <typename T>
 __global__ void __launch_bounds__(128) k_mg_smooth(Geom g, MGLevel L, int level, int color)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    const int x = 2 * i + ((y + z + color) & 1);
+    const int x = L.ncol == 3 ? i : 2 * i + ((y + z + color) & 1);
     if (x >= L.nx || y >= L.ny) return;
+    if (L.ncol == 3 && color3(g.per, x, y, z, L.nx, L.ny, L.nz) != color) return;
     const ll s = x + (ll)L.nx * (y + (ll)L.ny * z);
     if (L.m && L.m[s]) return;  // conductor cell: correction stays 0
-    T *e = (T *)L.e;
-    const T *b = (const T *)L.b, *ep = (const T *)L.eps;
-    const T kap = T(1 << level), kb = T(2 * (1 << (2 * level))) / T((1 << level) + 1);
-    const T es = ep[s];
-    T num = b[s], den = 0;
-    const int cx_[3] = {x, y, z}, n_[3] = {L.nx, L.ny, L.nz};
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-        for (int sg = -1; sg <= 1; sg += 2) {
-            int c[3] = {cx_[0], cx_[1], cx_[2]};
-            int v = nbc(c[a] + sg, n_[a], g.per[a]);
-            if (v < 0) {
-                if (g.phi_kind[2 * a + (sg > 0)] == ELBM_PHI_DIRICHLET) den += kb * es;
-                continue;
-            }
-            c[a] = v;
-            ll nb = c[0] + (ll)L.nx * (c[1] + (ll)L.ny * c[2]);
-            T cf = kap * T(0.5) * (es + ep[nb]);
-            num += cf * e[nb];
-            den += cf;
-        }
-    if (den > T(0)) e[s] = num / den;
+    const int n[3] = {L.nx, L.ny, L.nz};
+    mg_gs_cell<T>(g, (T *)L.e, (const T *)L.b, (const T *)L.eps, n, L.last, level, L.irr, x, y, z);
 }
 
 // residual of level l at one cell (level 0: phi / q / rho and the Dirichlet data)
@@ -1502,7 +1615,6 @@ __device__ __forceinline__ typename Tr<PR>::sc mg_resid_at(const Geom &g, const 
 {
     typedef typename Tr<PR>::sc T;
     const ll s = x + (ll)L.nx * (y + (ll)L.ny * z);
-    const int cx_[3] = {x, y, z}, n_[3] = {L.nx, L.ny, L.nz};
     if (level == 0) {
         // the fine operator exactly as the fine smoother and residual use it
         // (pois_nb): solid (conductor) nodes are fixed, with residual 0, and a
@@ -1541,30 +1653,14 @@ __device__ __forceinline__ typename Tr<PR>::sc mg_resid_at(const Geom &g, const 
         return r;
     }
     if (L.m && L.m[s]) return T(0);
-    const T *e = (const T *)L.e, *b = (const T *)L.b, *ep = (const T *)L.eps;
-    const T kap = T(1 << level), kb = T(2 * (1 << (2 * level))) / T((1 << level) + 1);
-    const T es = ep[s], xs = e[s];
-    T r = b[s];
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-        for (int sg = -1; sg <= 1; sg += 2) {
-            int c[3] = {cx_[0], cx_[1], cx_[2]};
-            int v = nbc(c[a] + sg, n_[a], g.per[a]);
-            if (v < 0) {
-                if (g.phi_kind[2 * a + (sg > 0)] == ELBM_PHI_DIRICHLET) r -= kb * es * xs;
-                continue;
-            }
-            c[a] = v;
-            ll nb = c[0] + (ll)L.nx * (c[1] + (ll)L.ny * c[2]);
-            r += kap * T(0.5) * (es + ep[nb]) * (e[nb] - xs);
-        }
-    return r;
+    const int n[3] = {L.nx, L.ny, L.nz};
+    return mg_res_cell<T>(g, (const T *)L.e, (const T *)L.b, (const T *)L.eps, n, L.last, level, L.irr, x, y, z);
 }
 
-// b_{l+1} = sum of the 8 child residuals of level l; e_{l+1} = 0. Eight
-// consecutive lanes handle the 8 children of one coarse cell and sum them
-// with a fixed shuffle tree.
+// b_{l+1} = sum of the child residuals of level l (8, or fewer in the last
+// cell of an axis coarsened from an odd extent); e_{l+1} = 0. Eight
+// consecutive lanes handle the children of one coarse cell and sum them with
+// a fixed shuffle tree.
 template <int PR>
 __global__ void __launch_bounds__(128) k_mg_restrict(Geom g, Phys ph, Bufs bf, MGLevel F, MGLevel C, int level)
 {
@@ -1582,11 +1678,13 @@ __global__ void __launch_bounds__(128) k_mg_restrict(Geom g, Phys ph, Bufs bf, M
         Y = (int)(rem / (unsigned)C.nx);
         X = (int)(rem - (unsigned)Y * (unsigned)C.nx);
         const int fx = 2 * X + (c & 1), fy = 2 * Y + ((c >> 1) & 1), fz = 2 * Z + (c >> 2);
-        r = mg_resid_at<PR>(g, ph, bf, F, level, fx, fy, fz);
-        // the coarse permittivity (mean of the 8 children) comes with the
-        // restriction: the coarse level's smoothing and residual read it next
-        const ll fs = fx + (ll)F.nx * (fy + (ll)F.ny * fz);
-        ep = level == 0 ? T(1) + cst<T>(ph).kap * ((const T *)bf.rho)[fs] : ((const T *)F.eps)[fs];
+        if (fx < F.nx && fy < F.ny && fz < F.nz) {
+            r = mg_resid_at<PR>(g, ph, bf, F, level, fx, fy, fz);
+            // the coarse permittivity (mean of the children) comes with the
+            // restriction: the coarse level's smoothing and residual read it next
+            const ll fs = fx + (ll)F.nx * (fy + (ll)F.ny * fz);
+            ep = level == 0 ? T(1) + cst<T>(ph).kap * ((const T *)bf.rho)[fs] : ((const T *)F.eps)[fs];
+        }
     }
     r += __shfl_down_sync(0xffffffffu, r, 4, 8);
     r += __shfl_down_sync(0xffffffffu, r, 2, 8);
@@ -1595,13 +1693,14 @@ __global__ void __launch_bounds__(128) k_mg_restrict(Geom g, Phys ph, Bufs bf, M
     ep += __shfl_down_sync(0xffffffffu, ep, 2, 8);
     ep += __shfl_down_sync(0xffffffffu, ep, 1, 8);
     if (act && c == 0) {
+        const int nch = (2 * X + 1 < F.nx ? 2 : 1) * (2 * Y + 1 < F.ny ? 2 : 1) * (2 * Z + 1 < F.nz ? 2 : 1);
         ((T *)C.b)[S] = (C.m && C.m[S]) ? T(0) : r;
         ((T *)C.e)[S] = T(0);
-        ((T *)C.eps)[S] = ep * T(0.125);
+        ((T *)C.eps)[S] = ep * (T(1) / T(nch));
     }
 }
 
-// coarse permittivity: mean of the 8 children (level 0 children from rho)
+// coarse permittivity: mean of the children (level 0 children from rho)
 template <int PR>
 __global__ void __launch_bounds__(128) k_mg_eps(Geom g, Phys ph, Bufs bf, MGLevel F, MGLevel C, int level)
 {
@@ -1612,17 +1711,22 @@ __global__ void __launch_bounds__(128) k_mg_eps(Geom g, Phys ph, Bufs bf, MGLeve
     if (X >= C.nx || Y >= C.ny) return;
     const Cst<T> &k = cst<T>(ph);
     T sum = 0;
+    int nch = 0;
 #pragma unroll
     for (int c = 0; c < 8; c++) {
-        ll s = (2 * X + (c & 1)) + (ll)F.nx * ((2 * Y + ((c >> 1) & 1)) + (ll)F.ny * (2 * Z + (c >> 2)));
+        const int fx = 2 * X + (c & 1), fy = 2 * Y + ((c >> 1) & 1), fz = 2 * Z + (c >> 2);
+        if (fx >= F.nx || fy >= F.ny || fz >= F.nz) continue;
+        const ll s = fx + (ll)F.nx * (fy + (ll)F.ny * fz);
         sum += level == 0 ? T(1) + k.kap * ((const T *)bf.rho)[s] : ((const T *)F.eps)[s];
+        nch++;
     }
-    ((T *)C.eps)[X + (ll)C.nx * (Y + (ll)C.ny * Z)] = sum * T(0.125);
+    ((T *)C.eps)[X + (ll)C.nx * (Y + (ll)C.ny * Z)] = sum * (T(1) / T(nch));
 }
 
 // trilinear prolongation of e_{l+1} added to level l (phi at level 0).
 // Beyond a Dirichlet face the coarse error is 0, beyond a Neumann face the
-// edge value.
+// edge value. A coarse level with a smaller last cell (odd extent) takes the
+// weights from the positions of the cell centres (mg_pweights).
 template <int PR>
 __global__ void __launch_bounds__(128) k_mg_prolong(Geom g, Bufs bf, MGLevel F, MGLevel C, int level)
 {
@@ -1632,30 +1736,46 @@ __global__ void __launch_bounds__(128) k_mg_prolong(Geom g, Bufs bf, MGLevel F, 
     const int z = blockIdx.z;
     if (x >= F.nx || y >= F.ny) return;
     const T *ec = (const T *)C.e;
-    const int fc[3] = {x, y, z}, nc[3] = {C.nx, C.ny, C.nz};
+    const int fc[3] = {x, y, z}, nc[3] = {C.nx, C.ny, C.nz}, nf[3] = {F.nx, F.ny, F.nz};
     int i0[3], i1[3];
     bool z1[3];
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        i0[a] = fc[a] >> 1;
-        int o = (fc[a] & 1) ? 1 : -1;  // the other coarse cell of the 3/4 - 1/4 pair
-        int v = nbc(i0[a] + o, nc[a], g.per[a]);
-        z1[a] = false;
-        if (v < 0) {
-            int face = 2 * a + (o > 0);
-            if (g.phi_kind[face] == ELBM_PHI_DIRICHLET) { z1[a] = true; v = i0[a]; }
-            else v = i0[a];
-        }
-        i1[a] = v;
-    }
     T acc = 0;
+    if (C.irr) {
+        T w1[3];
 #pragma unroll
-    for (int c = 0; c < 8; c++) {
-        int ax = c & 1, ay = (c >> 1) & 1, az = c >> 2;
-        if ((ax && z1[0]) || (ay && z1[1]) || (az && z1[2])) continue;
-        T w = (ax ? T(0.25) : T(0.75)) * (ay ? T(0.25) : T(0.75)) * (az ? T(0.25) : T(0.75));
-        int X = ax ? i1[0] : i0[0], Y = ay ? i1[1] : i0[1], Z = az ? i1[2] : i0[2];
-        acc += w * ec[X + (ll)C.nx * (Y + (ll)C.ny * Z)];
+        for (int a = 0; a < 3; a++)
+            mg_pweights<T>(g, a, fc[a], nf[a], level == 0 ? 1 : F.last[a], 1 << level, nc[a], C.last[a], i0[a],
+                           i1[a], w1[a], z1[a]);
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            int ax = c & 1, ay = (c >> 1) & 1, az = c >> 2;
+            if ((ax && z1[0]) || (ay && z1[1]) || (az && z1[2])) continue;
+            T w = (ax ? w1[0] : T(1) - w1[0]) * (ay ? w1[1] : T(1) - w1[1]) * (az ? w1[2] : T(1) - w1[2]);
+            int X = ax ? i1[0] : i0[0], Y = ay ? i1[1] : i0[1], Z = az ? i1[2] : i0[2];
+            acc += w * ec[X + (ll)C.nx * (Y + (ll)C.ny * Z)];
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            i0[a] = fc[a] >> 1;
+            int o = (fc[a] & 1) ? 1 : -1;  // the other coarse cell of the 3/4 - 1/4 pair
+            int v = nbc(i0[a] + o, nc[a], g.per[a]);
+            z1[a] = false;
+            if (v < 0) {
+                int face = 2 * a + (o > 0);
+                if (g.phi_kind[face] == ELBM_PHI_DIRICHLET) { z1[a] = true; v = i0[a]; }
+                else v = i0[a];
+            }
+            i1[a] = v;
+        }
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            int ax = c & 1, ay = (c >> 1) & 1, az = c >> 2;
+            if ((ax && z1[0]) || (ay && z1[1]) || (az && z1[2])) continue;
+            T w = (ax ? T(0.25) : T(0.75)) * (ay ? T(0.25) : T(0.75)) * (az ? T(0.25) : T(0.75));
+            int X = ax ? i1[0] : i0[0], Y = ay ? i1[1] : i0[1], Z = az ? i1[2] : i0[2];
+            acc += w * ec[X + (ll)C.nx * (Y + (ll)C.ny * Z)];
+        }
     }
     const ll s = x + (ll)F.nx * (y + (ll)F.ny * z);
     if (level == 0) {
@@ -1666,51 +1786,6 @@ __global__ void __launch_bounds__(128) k_mg_prolong(Geom g, Bufs bf, MGLevel F, 
         ((T *)F.e)[s] += acc;
     }
 }
-
-// coarsest level: red-black Gauss-Seidel sweeps by one block in shared memory
-template <typename T>
-__global__ void __launch_bounds__(1024) k_mg_coarse(Geom g, MGLevel L, int level, int sweeps)
-{
-    extern __shared__ unsigned char smem_raw[];
-    T *e = (T *)smem_raw;
-    T *b = e + L.N;
-    T *ep = b + L.N;
-    for (ll s = threadIdx.x; s < L.N; s += blockDim.x) {
-        e[s] = ((const T *)L.e)[s];
-        b[s] = ((const T *)L.b)[s];
-        ep[s] = ((const T *)L.eps)[s];
-    }
-    __syncthreads();
-    const T kap = T(1 << level), kb = T(2 * (1 << (2 * level))) / T((1 << level) + 1);
-    const int n_[3] = {L.nx, L.ny, L.nz};
-    for (int it = 0; it < 2 * sweeps; it++) {
-        const int color = it & 1;
-        for (ll s = threadIdx.x; s < L.N; s += blockDim.x) {
-            int si = (int)s, x = si % L.nx, y = (si / L.nx) % L.ny, z = si / (L.nx * L.ny);
-            if (((x + y + z) & 1) != color) continue;
-            const int cx_[3] = {x, y, z};
-            T es = ep[s], num = b[s], den = 0;
-            for (int a = 0; a < 3; a++)
-                for (int sg = -1; sg <= 1; sg += 2) {
-                    int c[3] = {cx_[0], cx_[1], cx_[2]};
-                    int v = nbc(c[a] + sg, n_[a], g.per[a]);
-                    if (v < 0) {
-                        if (g.phi_kind[2 * a + (sg > 0)] == ELBM_PHI_DIRICHLET) den += kb * es;
-                        continue;
-                    }
-                    c[a] = v;
-                    ll nb = c[0] + (ll)L.nx * (c[1] + (ll)L.ny * c[2]);
-                    T cf = kap * T(0.5) * (es + ep[nb]);
-                    num += cf * e[nb];
-                    den += cf;
-                }
-            if (den > T(0)) e[s] = num / den;
-        }
-        __syncthreads();
-    }
-    for (ll s = threadIdx.x; s < L.N; s += blockDim.x) ((T *)L.e)[s] = e[s];
-}
-
 
 // ---------------------------------------------------------------------------
 // The bottom of the V-cycle in one CTA: every level from `lt` down (at most
@@ -1726,43 +1801,19 @@ struct MGTail {
     int lt;                       // global index of the first tail level
     int nx[kTailMaxLevels], ny[kTailMaxLevels], nz[kTailMaxLevels];
     long long N[kTailMaxLevels], off[kTailMaxLevels];  // cells, offset in each smem array
+    int last[kTailMaxLevels][3];  // fine cells spanned by the last cell along each axis (MGLevel::last)
+    int irr[kTailMaxLevels];      // MGLevel::irr
+    int ncol[kTailMaxLevels];     // MGLevel::ncol
     long long total;              // cells over all tail levels
     int coarse_sweeps;
     MGLevel top;                  // global arrays of level lt
     const unsigned char *m;       // conductor masks of the tail levels (offsets off[k]), or NULL
 };
 
-template <typename T>
-__device__ __forceinline__ T tail_resid(const Geom &g, const T *e, const T *b, const T *ep, const unsigned char *m,
-                                        int nx, int ny, int nz, int level, int x, int y, int z)
-{
-    const int s = x + nx * (y + ny * z);
-    if (m && m[s]) return T(0);
-    const T kap = T(1 << level), kb = T(2 * (1 << (2 * level))) / T((1 << level) + 1);
-    const T es = ep[s], xs = e[s];
-    T r = b[s];
-    const int cc[3] = {x, y, z}, n_[3] = {nx, ny, nz};
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-        for (int sg = -1; sg <= 1; sg += 2) {
-            int c[3] = {cc[0], cc[1], cc[2]};
-            int v = nbc(c[a] + sg, n_[a], g.per[a]);
-            if (v < 0) {
-                if (g.phi_kind[2 * a + (sg > 0)] == ELBM_PHI_DIRICHLET) r -= kb * es * xs;
-                continue;
-            }
-            c[a] = v;
-            int nb = c[0] + nx * (c[1] + ny * c[2]);
-            r += kap * T(0.5) * (es + ep[nb]) * (e[nb] - xs);
-        }
-    return r;
-}
-
 // The tail runs as one CTA of (BX, BY, BZ) threads: a level is swept with
 // x = tx + BX i (or, in a red-black pass, x = 2 (tx + BX i) + parity so that
 // every thread owns cells of the active colour), y = ty + BY j, z = tz + BZ k;
-// no integer division, no idle half in a colour pass.
+// no integer division, no idle half in a red-black pass.
 template <typename T>
 __device__ void tail_smooth(const Geom &g, const MGTail &t, T *E, T *B, T *P, const unsigned char *M, int k,
                             int sweeps)
@@ -1772,36 +1823,18 @@ __device__ void tail_smooth(const Geom &g, const MGTail &t, T *E, T *B, T *P, co
     T *e = E + t.off[k];
     const T *b = B + t.off[k], *ep = P + t.off[k];
     const int level = t.lt + k;
-    const T kap = T(1 << level), kb = T(2 * (1 << (2 * level))) / T((1 << level) + 1);
     const int n_[3] = {nx, ny, nz};
-    for (int it = 0; it < 2 * sweeps; it++) {
-        const int color = it & 1;
+    const int nc = t.ncol[k];
+    for (int it = 0; it < nc * sweeps; it++) {
+        const int color = it % nc;
         for (int z = threadIdx.z; z < nz; z += blockDim.z)
             for (int y = threadIdx.y; y < ny; y += blockDim.y)
                 for (int xi = threadIdx.x;; xi += blockDim.x) {
-                    const int x = 2 * xi + ((y + z + color) & 1);
+                    const int x = nc == 3 ? xi : 2 * xi + ((y + z + color) & 1);
                     if (x >= nx) break;
-                    const int s = x + nx * (y + ny * z);
-                    if (m && m[s]) continue;  // conductor cell: correction stays 0
-                    const int cc[3] = {x, y, z};
-                    T es = ep[s], num = b[s], den = 0;
-#pragma unroll
-                    for (int a = 0; a < 3; a++)
-#pragma unroll
-                        for (int sg = -1; sg <= 1; sg += 2) {
-                            int c[3] = {cc[0], cc[1], cc[2]};
-                            int v = nbc(c[a] + sg, n_[a], g.per[a]);
-                            if (v < 0) {
-                                if (g.phi_kind[2 * a + (sg > 0)] == ELBM_PHI_DIRICHLET) den += kb * es;
-                                continue;
-                            }
-                            c[a] = v;
-                            int nb = c[0] + nx * (c[1] + ny * c[2]);
-                            T cf = kap * T(0.5) * (es + ep[nb]);
-                            num += cf * e[nb];
-                            den += cf;
-                        }
-                    if (den > T(0)) e[s] = num / den;
+                    if (nc == 3 && color3(g.per, x, y, z, nx, ny, nz) != color) continue;
+                    if (m && m[x + nx * (y + ny * z)]) continue;  // conductor cell: correction stays 0
+                    mg_gs_cell<T>(g, e, b, ep, n_, t.last[k], level, t.irr[k], x, y, z);
                 }
         __syncthreads();
     }
@@ -1825,16 +1858,21 @@ __global__ void __launch_bounds__(1024) k_mg_tail(Geom g, MGTail t, int nu)
     if (M)
         for (int s = tid; s < (int)t.total; s += nthr) M[s] = t.m[s];
     __syncthreads();
-    for (int k = 1; k < t.nt; k++) {  // coarse permittivities: mean of 8 children
-        const int nx = t.nx[k], ny = t.ny[k], nz = t.nz[k], fx = t.nx[k - 1], fy = t.ny[k - 1];
+    for (int k = 1; k < t.nt; k++) {  // coarse permittivities: mean of the children
+        const int nx = t.nx[k], ny = t.ny[k], nz = t.nz[k], fx = t.nx[k - 1], fy = t.ny[k - 1], fz = t.nz[k - 1];
         const T *pf = P + t.off[k - 1];
         for (int Z = threadIdx.z; Z < nz; Z += blockDim.z)
             for (int Y = threadIdx.y; Y < ny; Y += blockDim.y)
                 for (int X = threadIdx.x; X < nx; X += blockDim.x) {
                     T sum = 0;
-                    for (int c = 0; c < 8; c++)
-                        sum += pf[(2 * X + (c & 1)) + fx * ((2 * Y + ((c >> 1) & 1)) + fy * (2 * Z + (c >> 2)))];
-                    P[t.off[k] + X + nx * (Y + ny * Z)] = sum * T(0.125);
+                    int nch = 0;
+                    for (int c = 0; c < 8; c++) {
+                        const int cx_ = 2 * X + (c & 1), cy_ = 2 * Y + ((c >> 1) & 1), cz_ = 2 * Z + (c >> 2);
+                        if (cx_ >= fx || cy_ >= fy || cz_ >= fz) continue;
+                        sum += pf[cx_ + fx * (cy_ + fy * cz_)];
+                        nch++;
+                    }
+                    P[t.off[k] + X + nx * (Y + ny * Z)] = sum * (T(1) / T(nch));
                 }
         __syncthreads();
     }
@@ -1843,14 +1881,19 @@ __global__ void __launch_bounds__(1024) k_mg_tail(Geom g, MGTail t, int nu)
         tail_smooth<T>(g, t, E, B, P, M, k, nu);
         const int nx = t.nx[k + 1], ny = t.ny[k + 1], nz = t.nz[k + 1];
         const int fx = t.nx[k], fy = t.ny[k], fz = t.nz[k];
+        const int nf[3] = {fx, fy, fz};
+        const unsigned char *mf = M ? M + t.off[k] : nullptr;
         for (int Z = threadIdx.z; Z < nz; Z += blockDim.z)
             for (int Y = threadIdx.y; Y < ny; Y += blockDim.y)
                 for (int X = threadIdx.x; X < nx; X += blockDim.x) {
                     T sum = 0;
-                    for (int c = 0; c < 8; c++)
-                        sum += tail_resid<T>(g, E + t.off[k], B + t.off[k], P + t.off[k], M ? M + t.off[k] : nullptr,
-                                             fx, fy, fz, t.lt + k, 2 * X + (c & 1), 2 * Y + ((c >> 1) & 1),
-                                             2 * Z + (c >> 2));
+                    for (int c = 0; c < 8; c++) {
+                        const int cx_ = 2 * X + (c & 1), cy_ = 2 * Y + ((c >> 1) & 1), cz_ = 2 * Z + (c >> 2);
+                        if (cx_ >= fx || cy_ >= fy || cz_ >= fz) continue;
+                        if (mf && mf[cx_ + fx * (cy_ + fy * cz_)]) continue;  // a conductor's residual is 0
+                        sum += mg_res_cell<T>(g, E + t.off[k], B + t.off[k], P + t.off[k], nf, t.last[k], t.lt + k,
+                                              t.irr[k], cx_, cy_, cz_);
+                    }
                     const int S = X + nx * (Y + ny * Z);
                     B[t.off[k + 1] + S] = (M && M[t.off[k + 1] + S]) ? T(0) : sum;
                     E[t.off[k + 1] + S] = T(0);
@@ -1861,15 +1904,24 @@ __global__ void __launch_bounds__(1024) k_mg_tail(Geom g, MGTail t, int nu)
     // up: prolong (trilinear), smooth
     for (int k = t.nt - 2; k >= 0; k--) {
         const int nx = t.nx[k], ny = t.ny[k], nz = t.nz[k];
-        const int nc[3] = {t.nx[k + 1], t.ny[k + 1], t.nz[k + 1]};
+        const int nc[3] = {t.nx[k + 1], t.ny[k + 1], t.nz[k + 1]}, nf[3] = {nx, ny, nz};
         const T *ec = E + t.off[k + 1];
+        const bool irr = t.irr[k + 1] != 0;
+        const int Sf = 1 << (t.lt + k);
         for (int fz_ = threadIdx.z; fz_ < nz; fz_ += blockDim.z)
             for (int fy_ = threadIdx.y; fy_ < ny; fy_ += blockDim.y)
                 for (int fx_ = threadIdx.x; fx_ < nx; fx_ += blockDim.x) {
                     const int fc[3] = {fx_, fy_, fz_};
                     int i0[3], i1[3];
                     bool z1[3];
+                    T w1[3];
                     for (int a = 0; a < 3; a++) {
+                        if (irr) {
+                            mg_pweights<T>(g, a, fc[a], nf[a], t.last[k][a], Sf, nc[a], t.last[k + 1][a], i0[a], i1[a],
+                                           w1[a], z1[a]);
+                            continue;
+                        }
+                        w1[a] = T(0.25);
                         i0[a] = fc[a] >> 1;
                         int o = (fc[a] & 1) ? 1 : -1;
                         int v = nbc(i0[a] + o, nc[a], g.per[a]);
@@ -1884,7 +1936,9 @@ __global__ void __launch_bounds__(1024) k_mg_tail(Geom g, MGTail t, int nu)
                     for (int c = 0; c < 8; c++) {
                         int ax = c & 1, ay = (c >> 1) & 1, az = c >> 2;
                         if ((ax && z1[0]) || (ay && z1[1]) || (az && z1[2])) continue;
-                        T w = (ax ? T(0.25) : T(0.75)) * (ay ? T(0.25) : T(0.75)) * (az ? T(0.25) : T(0.75));
+                        T w = irr ? (ax ? w1[0] : T(1) - w1[0]) * (ay ? w1[1] : T(1) - w1[1]) *
+                                        (az ? w1[2] : T(1) - w1[2])
+                                  : (ax ? T(0.25) : T(0.75)) * (ay ? T(0.25) : T(0.75)) * (az ? T(0.25) : T(0.75));
                         int X = ax ? i1[0] : i0[0], Y = ay ? i1[1] : i0[1], Z = az ? i1[2] : i0[2];
                         acc += w * ec[X + nc[0] * (Y + nc[1] * Z)];
                     }
@@ -1922,7 +1976,7 @@ struct MGLaunchers {
         if (level == 0) {
             k_sor<PR><<<fine_half.grid, fine_half.block, 0, s>>>(g, ph, b, color, 1);
         } else {
-            const int nh = (L.nx + 1) / 2;
+            const int nh = L.ncol == 3 ? L.nx : (L.nx + 1) / 2;
             dim3 blk = blk_of(nh);
             k_mg_smooth<sc><<<grid_of(nh, L.ny, L.nz, blk), blk, 0, s>>>(g, L, level, color);
         }
@@ -1944,12 +1998,6 @@ struct MGLaunchers {
         dim3 blk = blk_of(F.nx);
         k_mg_prolong<PR><<<grid_of(F.nx, F.ny, F.nz, blk), blk, 0, s>>>(g, b, F, C, level);
     }
-    static void coarse(const Geom &g, const MGLevel &L, int level, int sweeps, cudaStream_t s)
-    {
-        size_t sm = 3 * (size_t)L.N * sizeof(sc);
-        int thr = L.N >= 1024 ? 1024 : (int)(((L.N + 31) / 32) * 32);
-        k_mg_coarse<sc><<<1, thr, sm, s>>>(g, L, level, sweeps);
-    }
     static void prepare()
     {
         cudaFuncSetAttribute(k_mg_tail<sc>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -1968,7 +2016,6 @@ struct MGLaunchers {
         o.restrict_ = restrict_;
         o.eps = eps;
         o.prolong = prolong;
-        o.coarse = coarse;
         return o;
     }
 };

@@ -125,10 +125,10 @@ def charged_drop_at_rest(n=32, radius=8.0, precision="fp64", steps=500, seed=SEE
     return cfg, fields
 
 
-# Box edges for batched droplets: the multiples of 8 in [24, 96] whose
-# multigrid halving chain (periodic axes stay even) reaches <= 16^3 cells for
-# the one-CTA coarse tail; 72 and 88 stop at 18^3 and 22^3 and are left out.
-BATCH_EDGES = (24, 32, 40, 48, 56, 64, 80, 96)
+# Box edges for batched droplets: every integer in [24, 96], odd ones
+# included (periodic boxes of odd edge take the three-colour sweep and a
+# multigrid hierarchy that coarsens odd extents).
+BATCH_EDGES = tuple(range(24, 97))
 
 
 def batched_droplet_params(n_boxes=512, seed=SEED_BASE + 5):

@@ -117,3 +117,24 @@ def test_benchmark_launch_configuration_at_full_size():
         S = np.max(np.abs(d / fi))
         herr = abs(_h_exact(fi, d, alpha[i])) / rho
         assert herr <= 1e-10, (i, S, alpha[i], herr)
+
+
+def test_guard_queue_with_blocks_of_96_threads():
+    """An 80^3 box launched with the default block shape, one row of 80
+    sites per block (96 threads): in the start-up transient of a large drop
+    (|u| ~ 0.1) about an eighth of the sites take the float-float guard,
+    queued per block. Every queued site must be solved, whatever the block's
+    thread count: no guard failure, the H-error within 1e-10, alpha inside
+    (0, 2.5) at every site."""
+    from paper_1612_05404_gb300 import elbm
+    cfg, fields = W.batched_droplet(80, 1e-3, 0.7, precision="fp32")
+    cfg.update(alpha_precision="fp32", store_macro=1, autotune=0)
+    sim = elbm.Sim(cfg, fields)
+    for _ in range(4):
+        assert sim.step(1) == elbm.OK
+        d = sim.diag()
+        assert d["n_guard_failed"] == 0 and d["max_h_error"] <= 1e-10, d
+        a = sim.get("alpha")
+        assert np.all(a > 0.0) and np.all(a < 2.5), (a.min(), a.max())
+    assert d["n_guarded"] > 1000, d
+    sim.close()
