@@ -303,6 +303,13 @@ def train_proposal(args):
 # ---------------------------------------------------------------------------
 # the headline: config 4
 # ---------------------------------------------------------------------------
+# DRAM bytes (read + write) per site of one collision launch, measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the 128x128x512 jet with
+# the learned proposal: 814.066688 MB over 8,388,608 sites. Valid for the
+# collision kernel as it stood for that capture.
+COLLIDE_DRAM_BYTES_PER_SITE = 814.066688e6 / 8388608
+
+
 def bytes_per_site_collide():
     """Algorithmic bytes of one collision launch per site, BF16 storage:
     populations read and written (2 x 19 x 2), the reference-density plane
@@ -367,8 +374,10 @@ def roofline(args, theta):
     out = {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak, "unit": "GB/s",
            "frac": achieved / peak, "peak_source": kind, "frac_of_8TBps": achieved / NOMINAL_HBM_GBS,
            # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel on the
-           # 128x128x512 jet, scaled by sites to the 256x256x768 lattice (profiles/)
-           "traffic": None,
+           # 128x128x512 jet, scaled by sites to this lattice (the traffic is per site)
+           "traffic": COLLIDE_DRAM_BYTES_PER_SITE * N,
+           "traffic_source": "ncu, one k_collide launch on the 128x128x512 jet (462.44 + 351.63 MB over "
+                             "8,388,608 sites), scaled by the site count",
            "bytes_per_site": bs, "avg_launch_ms": coll_ms,
            "timed": "256x256x768 jet, steps issued one by one, CUDA events around each pass (profile mode)"}
     shares = {"moments_charge": d["moments_ms"] / tot, "poisson": d["poisson_ms"] / tot,
@@ -485,6 +494,31 @@ def alpha_stage(theta):
     res["timed_sites"] = int(dh.shape[1])
     res["speedup_learned_vs_newton"] = res["newton"]["ns_per_site"] / res["learned"]["ns_per_site"]
     return res
+
+
+def fp64_configs(args):
+    """Configs 1 and 2 in FP64 (storage, arithmetic and the alpha root, FP64
+    Newton): the charged drop at rest (32^3 periodic, transported charge,
+    Newtonian) and one 64^3 drop in field (E0 = 1e-3, Carreau n = 0.6), each
+    alone, one CUDA graph per step, diagnostics every step."""
+    import torch
+    from paper_1612_05404_gb300 import elbm
+    from paper_1612_05404_gb300 import workloads as W
+    out = {}
+    cases = (("config1_drop_at_rest_32", W.charged_drop_at_rest(precision="fp64")),
+             ("config2_drop_in_field_64", W.drop_in_field(E0=1e-3, precision="fp64")))
+    for name, (cfg, fields) in cases:
+        cfg = dict(cfg, alpha_precision="fp64", graph=1, diag_every=1, autotune=1)
+        sim = elbm.Sim(cfg, fields)
+        sim.step(args.warmup)
+        ms = timed_steps(sim, args.steps)
+        d = sim.diag()
+        n = sites(cfg["shape"])
+        sim.close()
+        out[name] = {"mlups": n * args.steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / args.steps, "sites": n,
+                     "max_h_error_device": d["max_h_error"], "poisson_resid": d["poisson_resid"]}
+    out["workload"] = "FP64 storage, arithmetic and alpha (Newton), multigrid to 1e-13"
+    return out
 
 
 def drop64(args):
@@ -787,6 +821,7 @@ def main():
             res["alpha_stage"] = alpha_stage(theta)
         res["jet128"] = jet128(args)
         res["drop64"] = drop64(args)
+        res["fp64_configs"] = fp64_configs(args)
         if args.boxes > 0:
             res["batched_compare"] = batched_compare(args, theta)
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -21,7 +21,8 @@ using namespace elbm;
 
 namespace {
 constexpr int kMaxLevels = 10;
-constexpr int kNu = 2;             // pre- and post-smoothing sweeps
+constexpr int kNu = 2;             // pre- and post-smoothing sweeps (FP64; the tail in FP64)
+constexpr int kNuPre = 2, kNuPost = 2;  // the same on the launched levels in reduced precision
 constexpr int kNuTail = 1;         // the same on the levels of the one-CTA tail (reduced precision;
                                    // FP64 solves to 1e-13 keep kNu)
 constexpr int kCoarseSweeps = 8;   // red-black sweeps on the coarsest level (<= 8 cells per axis pair)
@@ -360,14 +361,16 @@ int vcycle(elbm_handle *h, const Bufs &b, cudaStream_t s, int l)
         return 1;
     }
     const int nc = h->lev[l].ncol;
-    for (int i = 0; i < kNu; i++)
+    const bool fp64 = h->p.precision == ELBM_PREC_FP64;
+    const int pre = fp64 ? kNu : kNuPre, post = fp64 ? kNu : kNuPost;
+    for (int i = 0; i < pre; i++)
         for (int c = 0; c < nc; c++) m.smooth(h->g, h->ph, b, h->lev[l], l, c, h->Lh, s);
     m.restrict_(h->g, h->ph, b, h->lev[l], h->lev[l + 1], l, s);
     int n = vcycle(h, b, s, l + 1);
     m.prolong(h->g, b, h->lev[l], h->lev[l + 1], l, s);
-    for (int i = 0; i < kNu; i++)
+    for (int i = 0; i < post; i++)
         for (int c = 0; c < nc; c++) m.smooth(h->g, h->ph, b, h->lev[l], l, c, h->Lh, s);
-    return n + 2 * nc * kNu + 2;
+    return n + nc * (pre + post) + 2;
 }
 
 // moments, and the free charge with its global sums (Sec. II C, item 3)
@@ -993,6 +996,11 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
             b.mlpimg = img;
         }
         if (g.has_mask) alloc((void **)&b.mask, (size_t)N);
+        if (g.has_mask || !g.per[0] || !g.per[1] || !g.per[2]) {
+            void *bb = nullptr;
+            alloc(&bb, (size_t)N * sizeof(unsigned));
+            b.bbits = (const unsigned *)bb;
+        }
         if (p->charge_model == ELBM_CHARGE_CONSERVED || p->charge_model == ELBM_CHARGE_XI) {
             alloc(&b.nh, (size_t)4 * N * h->sc_bytes);
             alloc(&b.ab, (size_t)2 * N * h->sc_bytes);
@@ -1094,6 +1102,10 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     up(&d_uin, in->u_in, 3 * N);
     if (transport) up(&d_q0, in->q0, N);
     if (ok && b.mask && !cuda_ok(cudaMemcpyAsync(b.mask, in->mask, N, cudaMemcpyHostToDevice, h->s))) ok = false;
+    if (ok && b.bbits) {
+        k_bounce_bits<<<L.grid, L.block, 0, h->s>>>(g, b.mask, const_cast<unsigned *>(b.bbits));
+        ok = cuda_ok(cudaGetLastError());
+    }
     if (ok && ph.adaptive) {
         ok = cuda_ok(cudaMemcpyAsync(const_cast<unsigned char *>(b.region), in->inlet_region, N, cudaMemcpyHostToDevice,
                                      h->s)) &&

@@ -53,6 +53,11 @@ struct Bufs {
     void *ux, *uy, *uz, *alpha, *nu;  // optional macroscopic planes
     float *alpha_lo;                  // reduced precision: low part of a guarded alpha (with store_macro)
     unsigned char *mask;              // node kinds (NULL when all fluid)
+    // per site, bit p set when the pull of population p comes back from a
+    // wall face or a solid node (bits 0..6 also serve the D3Q7 pull, whose
+    // directions are D3Q19's first seven); NULL when every pull is a plain
+    // gather (all faces periodic, no solid node)
+    const unsigned *bbits;
     void *E2;                         // FULL electric force: |E|^2 per site
     const unsigned char *region;      // adaptive inlet: sites of the nozzle mean (NULL: fixed inlet)
     const int *inlet_idx;             // adaptive inlet: the inlet nodes

@@ -226,6 +226,29 @@ __device__ __forceinline__ typename Tr<PR>::ct gather_pop(const Geom &g, const u
     return bb ? ldp<PR>(A, opp(p), n.s, g.N, rref) : ldp<PR>(A, p, src, g.N, rref);
 }
 
+// The same pulls from a site's precomputed bounce bits (Bufs::bbits): the
+// plane and index follow from one word loaded per site, so the 19 (or 7)
+// loads do not wait for the node kinds of their sources (the moments pass,
+// latency-bound; the collision reads the node kinds for its wall terms
+// anyway and keeps the plain pulls).
+template <int PR>
+__device__ __forceinline__ typename Tr<PR>::ct gather_pop_b(const Geom &g, const void *A, const Nbr &n, int p,
+                                                            unsigned bits, const float *rref = nullptr)
+{
+    const bool bb = (bits >> p) & 1u;
+    const int src = bb ? n.s : nbr_idx(n, g, -cx(p), -cy(p), -cz(p));
+    return ldp<PR>(A, bb ? opp(p) : p, src, g.N, rref);
+}
+template <int PR>
+__device__ __forceinline__ typename Tr<PR>::gt gather_g_b(const Geom &g, const void *A, const Nbr &n, int i,
+                                                          unsigned bits)
+{
+    typedef typename Tr<PR>::gt gt;
+    const bool bb = (bits >> i) & 1u;
+    const int src = bb ? n.s : nbr_idx(n, g, -c7x(i), -c7y(i), -c7z(i));
+    const int io = i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+    return plane<gt>(A, bb ? io : i, g.N)[src];
+}
 template <int PR>
 __device__ __forceinline__ typename Tr<PR>::gt gather_g(const Geom &g, const unsigned char *mask,
                                                         const void *A, const Nbr &n, int i)
@@ -266,6 +289,26 @@ __device__ __forceinline__ void site_xyz(const Geom &g, int &x, int &y, int &z, 
 }
 __device__ __forceinline__ int block_id() { return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); }
 
+// the bounce bits of every site (once, at initialisation)
+static __global__ void __launch_bounds__(128) k_bounce_bits(Geom g, const unsigned char *mask, unsigned *bits)
+{
+    int x, y, z;
+    bool inb;
+    ll s;
+    site_xyz(g, x, y, z, inb, s);
+    if (!inb) return;
+    Nbr n;
+    nbr_init(n, g, x, y, z, s);
+    unsigned w = 0;
+#pragma unroll
+    for (int p = 0; p < Q; p++) {
+        const int src = nbr_idx(n, g, -cx(p), -cy(p), -cz(p));
+        if (src < 0 || (mask && mask[src] == ELBM_NODE_SOLID)) w |= 1u << p;
+    }
+    bits[s] = w;
+}
+
+
 // Potential of the face neighbour along +-axis (Sec. II Poisson problem):
 // kind 0 = unknown (index in *nb), 1 = Dirichlet value in *v, 2 = no term.
 // With the deviation form (g.phi_lin) the plane holds psi = phi - phi_lin,
@@ -303,6 +346,13 @@ __device__ __forceinline__ int pois_nb(const Geom &g, const Cst<T> &k, const uns
     *nb = i;
     return 0;
 }
+// The quotient of a Gauss-Seidel / SOR update: in FP32 the fast reciprocal
+// quotient (2 ulp; the sweep is an iteration towards the discrete solution,
+// whose accuracy the residual test decides), in FP64 the exact one (the FP64
+// path follows the oracle's sweeps)
+__device__ __forceinline__ float pois_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double pois_div(double a, double b) { return a / b; }
+
 // A site whose six face neighbours lie inside the domain without a periodic
 // wrap and none of them solid: every face of the Poisson stencil is an
 // unknown neighbour at s +- off[a] (off = 1, nx, nx ny), its profile
@@ -440,10 +490,11 @@ __global__ void __launch_bounds__(128) k_moments(Geom g, Phys ph, Bufs b)
     if (active) {
         Nbr n;
         nbr_init(n, g, x, y, z, s);
+        const unsigned bits = b.bbits ? b.bbits[s] : 0u;
         ct rs = 0, rs_lo = 0;
 #pragma unroll
         for (int p = 0; p < Q; p++) {
-            const ct v = gather_pop<PR>(g, b.mask, b.fA, n, p, b.rA);
+            const ct v = gather_pop_b<PR>(g, b.fA, n, p, bits, b.rA);
             // deviations: a compensated sum (at the vapour density sum d ~ -0.84
             // and its rounding would be ~6x larger relative to rho ~ 0.16)
             if constexpr (T::dev) two_sum_acc(v, rs, rs_lo);
@@ -453,7 +504,7 @@ __global__ void __launch_bounds__(128) k_moments(Geom g, Phys ph, Bufs b)
         if (ph.charge_model == ELBM_CHARGE_TRANSPORT) {
             gt qs = 0;
 #pragma unroll
-            for (int i = 0; i < Q7; i++) qs += gather_g<PR>(g, b.mask, b.gA, n, i);
+            for (int i = 0; i < Q7; i++) qs += gather_g_b<PR>(g, b.gA, n, i, bits);
             ((sc *)b.q)[s] = sc(qs);
             qv = qs;
             q2 = qs * qs;
@@ -582,18 +633,18 @@ __global__ void __launch_bounds__(128) k_charge_q(Geom g, Phys ph, Bufs b)
 // kappa rho/rho0, face permittivity the mean of the two sites: red-black SOR
 // half-sweep over the sites of one colour, (x+y+z) mod 2 = color.
 // ===========================================================================
-template <int PR>
+template <int PR, int NC>
 __global__ void __launch_bounds__(128) k_sor(Geom g, Phys ph, Bufs b, int color, int gauss_seidel)
 {
     typedef typename Tr<PR>::sc sc;
-    // red-black: one thread per site of the colour, x = 2 i + ((y + z +
-    // color) & 1); three colours: one thread per site, those of the colour work
+    // red-black (NC = 2): one thread per site of the colour, x = 2 i + ((y +
+    // z + color) & 1); three colours: one thread per site, those of the colour work
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    const int x = g.ncol == 3 ? i : 2 * i + ((y + z + color) & 1);
+    const int x = NC == 3 ? i : 2 * i + ((y + z + color) & 1);
     if (x >= g.nx || y >= g.ny) return;
-    if (g.ncol == 3 && color3(g.per, x, y, z, g.nx, g.ny, g.nz) != color) return;
+    if (NC == 3 && color3(g.per, x, y, z, g.nx, g.ny, g.nz) != color) return;
     const ll s = x + (ll)g.nx * (y + (ll)g.ny * z);
     unsigned char kind = b.mask ? b.mask[s] : 0;
     if (kind == ELBM_NODE_SOLID) return;
@@ -609,7 +660,7 @@ __global__ void __launch_bounds__(128) k_sor(Geom g, Phys ph, Bufs b, int color,
         for (int a = 0; a < 3; a++)
 #pragma unroll
             for (int sg = -1; sg <= 1; sg += 2) {
-                const ll nb = s + sg * off[a];
+                const int nb = (int)s + sg * off[a];  // 32-bit site index (N < 2^31)
                 const sc ef = face_eps<sc>(es, sc(1) + k.kap * rho[nb], ph.eps_face);
                 num += ef * (phi[nb] + interior_dl<sc>(g, k, a, sg));
                 den += ef;
@@ -634,8 +685,9 @@ __global__ void __launch_bounds__(128) k_sor(Geom g, Phys ph, Bufs b, int color,
                 }
             }
     }
-    const sc w = gauss_seidel ? sc(1) : k.omega;
-    if (den > sc(0)) phi[s] = (sc(1) - w) * phi[s] + w * num / den;
+    if (!(den > sc(0))) return;
+    if (gauss_seidel) phi[s] = pois_div(num, den);
+    else phi[s] = (sc(1) - k.omega) * phi[s] + pois_div(k.omega * num, den);
 }
 
 // residual r = div(eps grad phi) + q - qmean with the reference norms:
@@ -670,7 +722,7 @@ __global__ void __launch_bounds__(128) k_resid(Geom g, Phys ph, Bufs b)
             for (int a = 0; a < 3; a++)
 #pragma unroll
                 for (int sg = -1; sg <= 1; sg += 2) {
-                    const ll nb = s + sg * off[a];
+                    const int nb = (int)s + sg * off[a];
                     const sc dl = interior_dl<sc>(g, k, a, sg);
                     const sc cf = face_eps<sc>(es, sc(1) + k.kap * rho[nb], ph.eps_face);
                     r += cf * ((phi[nb] + dl) - ps);
@@ -1354,7 +1406,8 @@ struct Launchers {
     }
     static void sor(const Geom &g, const Phys &ph, const Bufs &b, int color, const Launch &L, cudaStream_t s)
     {
-        k_sor<PR><<<L.grid, L.block, 0, s>>>(g, ph, b, color, 0);
+        if (g.ncol == 3) k_sor<PR, 3><<<L.grid, L.block, 0, s>>>(g, ph, b, color, 0);
+        else k_sor<PR, 2><<<L.grid, L.block, 0, s>>>(g, ph, b, color, 0);
     }
     static void resid(const Geom &g, const Phys &ph, const Bufs &b, const Launch &L, cudaStream_t s)
     {
@@ -1495,9 +1548,9 @@ __device__ __forceinline__ T mg_dface(const int n[3], const int last[3], int S, 
 
 // Gauss-Seidel update of coarse cell (x, y, z) of level `level` (the
 // correction equation: homogeneous Dirichlet data)
-template <typename T>
+template <typename T, bool IRR>
 __device__ __forceinline__ void mg_gs_cell(const Geom &g, T *e, const T *b, const T *ep, const int n[3],
-                                           const int last[3], int level, int irr, int x, int y, int z)
+                                           const int last[3], int level, int x, int y, int z)
 {
     const ll s = x + (ll)n[0] * (y + (ll)n[1] * z);
     const int S = 1 << level;
@@ -1513,12 +1566,12 @@ __device__ __forceinline__ void mg_gs_cell(const Geom &g, T *e, const T *b, cons
             const int v = nbc(c[a] + sg, n[a], g.per[a]);
             if (v < 0) {
                 if (g.phi_kind[2 * a + (sg > 0)] == ELBM_PHI_DIRICHLET)
-                    den += (irr ? mg_dface<T>(n, last, S, cc, a) : kb) * es;
+                    den += (IRR ? mg_dface<T>(n, last, S, cc, a) : kb) * es;
                 continue;
             }
             c[a] = v;
             const ll nb = c[0] + (ll)n[0] * (c[1] + (ll)n[1] * c[2]);
-            const T cf = (irr ? mg_face<T>(n, last, S, cc, a, v) : kap) * T(0.5) * (es + ep[nb]);
+            const T cf = (IRR ? mg_face<T>(n, last, S, cc, a, v) : kap) * T(0.5) * (es + ep[nb]);
             num += cf * e[nb];
             den += cf;
         }
@@ -1526,9 +1579,9 @@ __device__ __forceinline__ void mg_gs_cell(const Geom &g, T *e, const T *b, cons
 }
 
 // residual of the correction equation at coarse cell (x, y, z)
-template <typename T>
+template <typename T, bool IRR>
 __device__ __forceinline__ T mg_res_cell(const Geom &g, const T *e, const T *b, const T *ep, const int n[3],
-                                         const int last[3], int level, int irr, int x, int y, int z)
+                                         const int last[3], int level, int x, int y, int z)
 {
     const ll s = x + (ll)n[0] * (y + (ll)n[1] * z);
     const int S = 1 << level;
@@ -1544,12 +1597,12 @@ __device__ __forceinline__ T mg_res_cell(const Geom &g, const T *e, const T *b, 
             const int v = nbc(c[a] + sg, n[a], g.per[a]);
             if (v < 0) {
                 if (g.phi_kind[2 * a + (sg > 0)] == ELBM_PHI_DIRICHLET)
-                    r -= (irr ? mg_dface<T>(n, last, S, cc, a) : kb) * es * xs;
+                    r -= (IRR ? mg_dface<T>(n, last, S, cc, a) : kb) * es * xs;
                 continue;
             }
             c[a] = v;
             const ll nb = c[0] + (ll)n[0] * (c[1] + (ll)n[1] * c[2]);
-            r += (irr ? mg_face<T>(n, last, S, cc, a, v) : kap) * T(0.5) * (es + ep[nb]) * (e[nb] - xs);
+            r += (IRR ? mg_face<T>(n, last, S, cc, a, v) : kap) * T(0.5) * (es + ep[nb]) * (e[nb] - xs);
         }
     return r;
 }
@@ -1593,19 +1646,19 @@ __device__ __forceinline__ void mg_pweights(const Geom &g, int a, int i, int nf,
 }
 
 // Gauss-Seidel sweep of one colour on a coarse level
-template <typename T>
+template <typename T, bool IRR, int NC>
 __global__ void __launch_bounds__(128) k_mg_smooth(Geom g, MGLevel L, int level, int color)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    const int x = L.ncol == 3 ? i : 2 * i + ((y + z + color) & 1);
+    const int x = NC == 3 ? i : 2 * i + ((y + z + color) & 1);
     if (x >= L.nx || y >= L.ny) return;
-    if (L.ncol == 3 && color3(g.per, x, y, z, L.nx, L.ny, L.nz) != color) return;
+    if (NC == 3 && color3(g.per, x, y, z, L.nx, L.ny, L.nz) != color) return;
     const ll s = x + (ll)L.nx * (y + (ll)L.ny * z);
     if (L.m && L.m[s]) return;  // conductor cell: correction stays 0
     const int n[3] = {L.nx, L.ny, L.nz};
-    mg_gs_cell<T>(g, (T *)L.e, (const T *)L.b, (const T *)L.eps, n, L.last, level, L.irr, x, y, z);
+    mg_gs_cell<T, IRR>(g, (T *)L.e, (const T *)L.b, (const T *)L.eps, n, L.last, level, x, y, z);
 }
 
 // residual of level l at one cell (level 0: phi / q / rho and the Dirichlet data)
@@ -1632,7 +1685,7 @@ __device__ __forceinline__ typename Tr<PR>::sc mg_resid_at(const Geom &g, const 
             for (int a = 0; a < 3; a++)
 #pragma unroll
                 for (int sg = -1; sg <= 1; sg += 2) {
-                    const ll nb = s + sg * off[a];
+                    const int nb = (int)s + sg * off[a];
                     r += face_eps<T>(es, T(1) + k.kap * rho[nb], ph.eps_face) *
                          ((phi[nb] + interior_dl<T>(g, k, a, sg)) - ps);
                 }
@@ -1654,14 +1707,15 @@ __device__ __forceinline__ typename Tr<PR>::sc mg_resid_at(const Geom &g, const 
     }
     if (L.m && L.m[s]) return T(0);
     const int n[3] = {L.nx, L.ny, L.nz};
-    return mg_res_cell<T>(g, (const T *)L.e, (const T *)L.b, (const T *)L.eps, n, L.last, level, L.irr, x, y, z);
+    if (L.irr) return mg_res_cell<T, true>(g, (const T *)L.e, (const T *)L.b, (const T *)L.eps, n, L.last, level, x, y, z);
+    return mg_res_cell<T, false>(g, (const T *)L.e, (const T *)L.b, (const T *)L.eps, n, L.last, level, x, y, z);
 }
 
 // b_{l+1} = sum of the child residuals of level l (8, or fewer in the last
 // cell of an axis coarsened from an odd extent); e_{l+1} = 0. Eight
 // consecutive lanes handle the children of one coarse cell and sum them with
 // a fixed shuffle tree.
-template <int PR>
+template <int PR, bool ODD>
 __global__ void __launch_bounds__(128) k_mg_restrict(Geom g, Phys ph, Bufs bf, MGLevel F, MGLevel C, int level)
 {
     typedef typename Tr<PR>::sc T;
@@ -1678,7 +1732,7 @@ __global__ void __launch_bounds__(128) k_mg_restrict(Geom g, Phys ph, Bufs bf, M
         Y = (int)(rem / (unsigned)C.nx);
         X = (int)(rem - (unsigned)Y * (unsigned)C.nx);
         const int fx = 2 * X + (c & 1), fy = 2 * Y + ((c >> 1) & 1), fz = 2 * Z + (c >> 2);
-        if (fx < F.nx && fy < F.ny && fz < F.nz) {
+        if (!ODD || (fx < F.nx && fy < F.ny && fz < F.nz)) {
             r = mg_resid_at<PR>(g, ph, bf, F, level, fx, fy, fz);
             // the coarse permittivity (mean of the children) comes with the
             // restriction: the coarse level's smoothing and residual read it next
@@ -1693,7 +1747,7 @@ __global__ void __launch_bounds__(128) k_mg_restrict(Geom g, Phys ph, Bufs bf, M
     ep += __shfl_down_sync(0xffffffffu, ep, 2, 8);
     ep += __shfl_down_sync(0xffffffffu, ep, 1, 8);
     if (act && c == 0) {
-        const int nch = (2 * X + 1 < F.nx ? 2 : 1) * (2 * Y + 1 < F.ny ? 2 : 1) * (2 * Z + 1 < F.nz ? 2 : 1);
+        const int nch = ODD ? (2 * X + 1 < F.nx ? 2 : 1) * (2 * Y + 1 < F.ny ? 2 : 1) * (2 * Z + 1 < F.nz ? 2 : 1) : 8;
         ((T *)C.b)[S] = (C.m && C.m[S]) ? T(0) : r;
         ((T *)C.e)[S] = T(0);
         ((T *)C.eps)[S] = ep * (T(1) / T(nch));
@@ -1727,7 +1781,7 @@ __global__ void __launch_bounds__(128) k_mg_eps(Geom g, Phys ph, Bufs bf, MGLeve
 // Beyond a Dirichlet face the coarse error is 0, beyond a Neumann face the
 // edge value. A coarse level with a smaller last cell (odd extent) takes the
 // weights from the positions of the cell centres (mg_pweights).
-template <int PR>
+template <int PR, bool IRR>
 __global__ void __launch_bounds__(128) k_mg_prolong(Geom g, Bufs bf, MGLevel F, MGLevel C, int level)
 {
     typedef typename Tr<PR>::sc T;
@@ -1740,7 +1794,7 @@ __global__ void __launch_bounds__(128) k_mg_prolong(Geom g, Bufs bf, MGLevel F, 
     int i0[3], i1[3];
     bool z1[3];
     T acc = 0;
-    if (C.irr) {
+    if (IRR) {
         T w1[3];
 #pragma unroll
         for (int a = 0; a < 3; a++)
@@ -1825,6 +1879,21 @@ __device__ void tail_smooth(const Geom &g, const MGTail &t, T *E, T *B, T *P, co
     const int level = t.lt + k;
     const int n_[3] = {nx, ny, nz};
     const int nc = t.ncol[k];
+    if (nc == 2 && !t.irr[k]) {  // red-black on a regular level
+        for (int it = 0; it < 2 * sweeps; it++) {
+            const int color = it & 1;
+            for (int z = threadIdx.z; z < nz; z += blockDim.z)
+                for (int y = threadIdx.y; y < ny; y += blockDim.y)
+                    for (int xi = threadIdx.x;; xi += blockDim.x) {
+                        const int x = 2 * xi + ((y + z + color) & 1);
+                        if (x >= nx) break;
+                        if (m && m[x + nx * (y + ny * z)]) continue;  // conductor cell: correction stays 0
+                        mg_gs_cell<T, false>(g, e, b, ep, n_, t.last[k], level, x, y, z);
+                    }
+            __syncthreads();
+        }
+        return;
+    }
     for (int it = 0; it < nc * sweeps; it++) {
         const int color = it % nc;
         for (int z = threadIdx.z; z < nz; z += blockDim.z)
@@ -1833,8 +1902,8 @@ __device__ void tail_smooth(const Geom &g, const MGTail &t, T *E, T *B, T *P, co
                     const int x = nc == 3 ? xi : 2 * xi + ((y + z + color) & 1);
                     if (x >= nx) break;
                     if (nc == 3 && color3(g.per, x, y, z, nx, ny, nz) != color) continue;
-                    if (m && m[x + nx * (y + ny * z)]) continue;  // conductor cell: correction stays 0
-                    mg_gs_cell<T>(g, e, b, ep, n_, t.last[k], level, t.irr[k], x, y, z);
+                    if (m && m[x + nx * (y + ny * z)]) continue;
+                    mg_gs_cell<T, true>(g, e, b, ep, n_, t.last[k], level, x, y, z);
                 }
         __syncthreads();
     }
@@ -1891,8 +1960,12 @@ __global__ void __launch_bounds__(1024) k_mg_tail(Geom g, MGTail t, int nu)
                         const int cx_ = 2 * X + (c & 1), cy_ = 2 * Y + ((c >> 1) & 1), cz_ = 2 * Z + (c >> 2);
                         if (cx_ >= fx || cy_ >= fy || cz_ >= fz) continue;
                         if (mf && mf[cx_ + fx * (cy_ + fy * cz_)]) continue;  // a conductor's residual is 0
-                        sum += mg_res_cell<T>(g, E + t.off[k], B + t.off[k], P + t.off[k], nf, t.last[k], t.lt + k,
-                                              t.irr[k], cx_, cy_, cz_);
+                        if (t.irr[k])
+                            sum += mg_res_cell<T, true>(g, E + t.off[k], B + t.off[k], P + t.off[k], nf, t.last[k],
+                                                        t.lt + k, cx_, cy_, cz_);
+                        else
+                            sum += mg_res_cell<T, false>(g, E + t.off[k], B + t.off[k], P + t.off[k], nf, t.last[k],
+                                                         t.lt + k, cx_, cy_, cz_);
                     }
                     const int S = X + nx * (Y + ny * Z);
                     B[t.off[k + 1] + S] = (M && M[t.off[k + 1] + S]) ? T(0) : sum;
@@ -1974,18 +2047,24 @@ struct MGLaunchers {
                        const Launch &fine_half, cudaStream_t s)
     {
         if (level == 0) {
-            k_sor<PR><<<fine_half.grid, fine_half.block, 0, s>>>(g, ph, b, color, 1);
+            if (g.ncol == 3) k_sor<PR, 3><<<fine_half.grid, fine_half.block, 0, s>>>(g, ph, b, color, 1);
+            else k_sor<PR, 2><<<fine_half.grid, fine_half.block, 0, s>>>(g, ph, b, color, 1);
         } else {
             const int nh = L.ncol == 3 ? L.nx : (L.nx + 1) / 2;
             dim3 blk = blk_of(nh);
-            k_mg_smooth<sc><<<grid_of(nh, L.ny, L.nz, blk), blk, 0, s>>>(g, L, level, color);
+            const dim3 gr = grid_of(nh, L.ny, L.nz, blk);
+            if (L.ncol == 3) k_mg_smooth<sc, true, 3><<<gr, blk, 0, s>>>(g, L, level, color);
+            else if (L.irr) k_mg_smooth<sc, true, 2><<<gr, blk, 0, s>>>(g, L, level, color);
+            else k_mg_smooth<sc, false, 2><<<gr, blk, 0, s>>>(g, L, level, color);
         }
     }
     static void restrict_(const Geom &g, const Phys &ph, const Bufs &b, const MGLevel &F, const MGLevel &C,
                           int level, cudaStream_t s)
     {
         long long thr = 8 * C.N;
-        k_mg_restrict<PR><<<(unsigned)((thr + 127) / 128), 128, 0, s>>>(g, ph, b, F, C, level);
+        const unsigned nb = (unsigned)((thr + 127) / 128);
+        if ((F.nx | F.ny | F.nz) & 1) k_mg_restrict<PR, true><<<nb, 128, 0, s>>>(g, ph, b, F, C, level);
+        else k_mg_restrict<PR, false><<<nb, 128, 0, s>>>(g, ph, b, F, C, level);
     }
     static void eps(const Geom &g, const Phys &ph, const Bufs &b, const MGLevel &F, const MGLevel &C, int level,
                     cudaStream_t s)
@@ -1996,7 +2075,8 @@ struct MGLaunchers {
     static void prolong(const Geom &g, const Bufs &b, const MGLevel &F, const MGLevel &C, int level, cudaStream_t s)
     {
         dim3 blk = blk_of(F.nx);
-        k_mg_prolong<PR><<<grid_of(F.nx, F.ny, F.nz, blk), blk, 0, s>>>(g, b, F, C, level);
+        if (C.irr) k_mg_prolong<PR, true><<<grid_of(F.nx, F.ny, F.nz, blk), blk, 0, s>>>(g, b, F, C, level);
+        else k_mg_prolong<PR, false><<<grid_of(F.nx, F.ny, F.nz, blk), blk, 0, s>>>(g, b, F, C, level);
     }
     static void prepare()
     {
