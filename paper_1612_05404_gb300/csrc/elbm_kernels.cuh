@@ -353,24 +353,43 @@ __device__ __forceinline__ int pois_nb(const Geom &g, const Cst<T> &k, const uns
 __device__ __forceinline__ float pois_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double pois_div(double a, double b) { return a / b; }
 
-// A site whose six face neighbours lie inside the domain without a periodic
-// wrap and none of them solid: every face of the Poisson stencil is an
-// unknown neighbour at s +- off[a] (off = 1, nx, nx ny), its profile
-// difference dl being +-slope along phi_axis in the deviation form. The
-// stencil kernels take this path there, with the same operations in the
-// same order as the general one (pois_nb), free of its face and mask logic.
-__device__ __forceinline__ bool pois_interior(const Geom &g, const unsigned char *mask, int x, int y, int z, ll s)
+// The fast path of the Poisson stencil: a site inside the lattice along y
+// and z, none of its face neighbours solid. Its y and z neighbours are at
+// s +- nx and s +- nx ny; its x neighbours xn[0] (x - 1) and xn[1] (x + 1),
+// wrapped on a periodic axis, or -1 beyond a boundary face of the lattice
+// (then the face's own term, as pois_nb gives it). The profile difference dl
+// is +-slope along phi_axis in the deviation form. A row's first and last
+// sites then cost their warp a few instructions instead of the general path
+// (pois_nb), with the same operations in the same order.
+__device__ __forceinline__ bool pois_fast(const Geom &g, const unsigned char *mask, int x, int y, int z, int si,
+                                          int xn[2])
 {
-    if (x <= 0 || x >= g.nx - 1 || y <= 0 || y >= g.ny - 1 || z <= 0 || z >= g.nz - 1) return false;
+    if (y <= 0 || y >= g.ny - 1 || z <= 0 || z >= g.nz - 1) return false;
+    xn[0] = x > 0 ? si - 1 : (g.per[0] ? si + g.nx - 1 : -1);
+    xn[1] = x < g.nx - 1 ? si + 1 : (g.per[0] ? si - (g.nx - 1) : -1);
     if (!mask) return true;
+    // six independent loads (the site itself stands in for a missing x
+    // neighbour: the callers have returned at solid sites)
     const int nx = g.nx, nxy = g.nx * g.ny;
-    return mask[s - 1] != ELBM_NODE_SOLID && mask[s + 1] != ELBM_NODE_SOLID && mask[s - nx] != ELBM_NODE_SOLID &&
-           mask[s + nx] != ELBM_NODE_SOLID && mask[s - nxy] != ELBM_NODE_SOLID && mask[s + nxy] != ELBM_NODE_SOLID;
+    const unsigned char m0 = mask[xn[0] >= 0 ? xn[0] : si], m1 = mask[xn[1] >= 0 ? xn[1] : si];
+    const unsigned char m2 = mask[si - nx], m3 = mask[si + nx], m4 = mask[si - nxy], m5 = mask[si + nxy];
+    return (m0 != ELBM_NODE_SOLID) & (m1 != ELBM_NODE_SOLID) & (m2 != ELBM_NODE_SOLID) & (m3 != ELBM_NODE_SOLID) &
+           (m4 != ELBM_NODE_SOLID) & (m5 != ELBM_NODE_SOLID);
 }
 template <typename T>
 __device__ __forceinline__ T interior_dl(const Geom &g, const Cst<T> &k, int a, int sg)
 {
     return (g.phi_lin && a == g.phi_axis) ? T(sg) * k.phi_slope : T(0);
+}
+// a boundary x face of the fast path: 1 with its Dirichlet value in *v (as
+// pois_nb), 0 for a face with no term
+template <typename T>
+__device__ __forceinline__ int pois_xface(const Geom &g, const Cst<T> &k, int x, int y, int z, int sg, T *v)
+{
+    const int face = sg > 0 ? 1 : 0;
+    if (g.phi_kind[face] != ELBM_PHI_DIRICHLET) return 0;
+    *v = g.phi_lin ? T(0) : phi_ghost<T>(g, k, face, x, y, z);
+    return 1;
 }
 
 // phi_lin at the site (0 without the deviation form)
@@ -544,12 +563,14 @@ __global__ void __launch_bounds__(128) k_charge_grad(Geom g, Phys ph, Bufs b)
     Nbr n;
     nbr_init(n, g, x, y, z, s);
     const sc *rho = (const sc *)b.rho;
-    sc rs = rho[s];
+    // the neighbour r + c_p is beyond a wall face or solid exactly when the
+    // pull of the opposite population bounces (bit opp(p) of the bounce bits)
+    const unsigned bits = b.bbits ? b.bbits[s] : 0u;
     sc gx = 0, gy = 0, gz = 0;
 #pragma unroll
     for (int p = 1; p < Q; p++) {
         const int nb = nbr_idx(n, g, cx(p), cy(p), cz(p));
-        sc v = (nb < 0 || (b.mask && b.mask[nb] == ELBM_NODE_SOLID)) ? rs : rho[nb];
+        sc v = rho[((bits >> opp(p)) & 1u) ? n.s : nb];
         sc wv = sc(wq(p)) * v / sc(CS2);
         gx += wv * sc(cx(p));
         gy += wv * sc(cy(p));
@@ -579,11 +600,12 @@ __global__ void __launch_bounds__(128) k_charge_ab(Geom g, Phys ph, Bufs b)
         Nbr n;
         nbr_init(n, g, x, y, z, s);
         const sc *nh = (const sc *)b.nh;
+        const unsigned bits = b.bbits ? b.bbits[s] : 0u;  // as in k_charge_grad
         sc div = 0;
 #pragma unroll
         for (int p = 1; p < Q; p++) {
             const int nb = nbr_idx(n, g, cx(p), cy(p), cz(p));
-            const int src = (nb < 0 || (b.mask && b.mask[nb] == ELBM_NODE_SOLID)) ? n.s : nb;
+            const int src = ((bits >> opp(p)) & 1u) ? n.s : nb;
             sc wv = sc(wq(p)) / sc(CS2);
             div += wv * (nh[src] * sc(cx(p)) + nh[g.N + src] * sc(cy(p)) + nh[2 * g.N + src] * sc(cz(p)));
         }
@@ -654,16 +676,30 @@ __global__ void __launch_bounds__(128) k_sor(Geom g, Phys ph, Bufs b, int color,
     sc es = sc(1) + k.kap * rho[s];
     sc num = kind == ELBM_NODE_FLUID ? ((const sc *)b.q)[s] - scal_of<sc>(b, S_QMEAN) : sc(0);
     sc den = 0;
-    if (pois_interior(g, b.mask, x, y, z, s)) {
+    int xn[2];
+    if (pois_fast(g, b.mask, x, y, z, (int)s, xn)) {
         const int off[3] = {1, g.nx, g.nx * g.ny};
 #pragma unroll
         for (int a = 0; a < 3; a++)
 #pragma unroll
             for (int sg = -1; sg <= 1; sg += 2) {
-                const int nb = (int)s + sg * off[a];  // 32-bit site index (N < 2^31)
-                const sc ef = face_eps<sc>(es, sc(1) + k.kap * rho[nb], ph.eps_face);
-                num += ef * (phi[nb] + interior_dl<sc>(g, k, a, sg));
-                den += ef;
+                const int nb = a == 0 ? xn[sg > 0] : (int)s + sg * off[a];  // 32-bit site index (N < 2^31)
+                // loads from a valid index whatever the face (the site itself
+                // beyond a boundary x face), so none waits on the face test
+                const int li = nb >= 0 ? nb : (int)s;
+                const sc rn = rho[li], pn = phi[li];
+                const sc dl = interior_dl<sc>(g, k, a, sg);
+                if (nb >= 0) {
+                    const sc ef = face_eps<sc>(es, sc(1) + k.kap * rn, ph.eps_face);
+                    num += ef * (pn + dl);
+                    den += ef;
+                } else {
+                    sc v = 0;
+                    if (pois_xface<sc>(g, k, x, y, z, sg, &v)) {
+                        num += es * (v + dl);
+                        den += es;
+                    }
+                }
             }
     } else {
         Nbr n;
@@ -716,17 +752,29 @@ __global__ void __launch_bounds__(128) k_resid(Geom g, Phys ph, Bufs b)
         sc bs = 0;
         sc ps = phi[s];
         sc t = fabs(r);
-        if (pois_interior(g, b.mask, x, y, z, s)) {
+        int xn[2];
+        if (pois_fast(g, b.mask, x, y, z, (int)s, xn)) {
             const int off[3] = {1, g.nx, g.nx * g.ny};
 #pragma unroll
             for (int a = 0; a < 3; a++)
 #pragma unroll
                 for (int sg = -1; sg <= 1; sg += 2) {
-                    const int nb = (int)s + sg * off[a];
+                    const int nb = a == 0 ? xn[sg > 0] : (int)s + sg * off[a];
+                    const int li = nb >= 0 ? nb : (int)s;  // loads independent of the face test
+                    const sc rn = rho[li], pn = phi[li];
                     const sc dl = interior_dl<sc>(g, k, a, sg);
-                    const sc cf = face_eps<sc>(es, sc(1) + k.kap * rho[nb], ph.eps_face);
-                    r += cf * ((phi[nb] + dl) - ps);
-                    t += cf * (fabs(phi[nb]) + fabs(dl) + fabs(ps));
+                    if (nb >= 0) {
+                        const sc cf = face_eps<sc>(es, sc(1) + k.kap * rn, ph.eps_face);
+                        r += cf * ((pn + dl) - ps);
+                        t += cf * (fabs(pn) + fabs(dl) + fabs(ps));
+                    } else {
+                        sc v = 0;
+                        if (pois_xface<sc>(g, k, x, y, z, sg, &v)) {
+                            r += es * ((v + dl) - ps);
+                            bs += es * (v + dl + phi_lin_at<sc>(g, k, x, y, z));  // the Dirichlet datum itself
+                            t += es * (fabs(v) + fabs(dl) + fabs(ps));
+                        }
+                    }
                 }
         } else {
             Nbr n;
@@ -1679,15 +1727,23 @@ __device__ __forceinline__ typename Tr<PR>::sc mg_resid_at(const Geom &g, const 
         const T es = T(1) + k.kap * rho[s];
         const T ps = phi[s];
         T r = kind == ELBM_NODE_FLUID ? ((const T *)bf.q)[s] - scal_of<T>(bf, S_QMEAN) : T(0);
-        if (pois_interior(g, bf.mask, x, y, z, s)) {
+        int xn[2];
+        if (pois_fast(g, bf.mask, x, y, z, (int)s, xn)) {
             const int off[3] = {1, g.nx, g.nx * g.ny};
 #pragma unroll
             for (int a = 0; a < 3; a++)
 #pragma unroll
                 for (int sg = -1; sg <= 1; sg += 2) {
-                    const int nb = (int)s + sg * off[a];
-                    r += face_eps<T>(es, T(1) + k.kap * rho[nb], ph.eps_face) *
-                         ((phi[nb] + interior_dl<T>(g, k, a, sg)) - ps);
+                    const int nb = a == 0 ? xn[sg > 0] : (int)s + sg * off[a];
+                    const int li = nb >= 0 ? nb : (int)s;  // loads independent of the face test
+                    const T rn = rho[li], pn = phi[li];
+                    const T dl = interior_dl<T>(g, k, a, sg);
+                    if (nb >= 0) {
+                        r += face_eps<T>(es, T(1) + k.kap * rn, ph.eps_face) * ((pn + dl) - ps);
+                    } else {
+                        T v = 0;
+                        if (pois_xface<T>(g, k, x, y, z, sg, &v)) r += es * ((v + dl) - ps);
+                    }
                 }
             return r;
         }
