@@ -353,6 +353,16 @@ int enq_inlet(elbm_handle *h, const Bufs &b, cudaStream_t s)
     return 2;
 }
 
+// The colour of the fine level that the multigrid's red-black Gauss-Seidel
+// smoothing updates last, whose residual (the rounding of that update) the
+// residual passes take as 0 in reduced precision; -1 where they take every
+// site (FP64, which follows the oracle's procedure; SOR, whose over-relaxed
+// update leaves (1 - omega) of the residual; three-colour orderings).
+int gs_settled(const elbm_handle *h)
+{
+    return (h->nlev > 0 && h->p.precision != ELBM_PREC_FP64 && h->g.ncol == 2) ? 1 : -1;
+}
+
 int vcycle(elbm_handle *h, const Bufs &b, cudaStream_t s, int l)
 {
     const MGOps &m = h->mg;
@@ -365,7 +375,7 @@ int vcycle(elbm_handle *h, const Bufs &b, cudaStream_t s, int l)
     const int pre = fp64 ? kNu : kNuPre, post = fp64 ? kNu : kNuPost;
     for (int i = 0; i < pre; i++)
         for (int c = 0; c < nc; c++) m.smooth(h->g, h->ph, b, h->lev[l], l, c, h->Lh, s);
-    m.restrict_(h->g, h->ph, b, h->lev[l], h->lev[l + 1], l, s);
+    m.restrict_(h->g, h->ph, b, h->lev[l], h->lev[l + 1], l, l == 0 ? gs_settled(h) : -1, s);
     int n = vcycle(h, b, s, l + 1);
     m.prolong(h->g, b, h->lev[l], h->lev[l + 1], l, s);
     for (int i = 0; i < post; i++)
@@ -404,7 +414,7 @@ int enq_eps(elbm_handle *h, const Bufs &b, cudaStream_t s)
 // convergence test: residual sums, then the device-side decision
 int enq_check(elbm_handle *h, const Bufs &b, cudaStream_t s, int mode, unsigned long long cond, int use_cond)
 {
-    h->ops.resid(h->g, h->ph, b, h->L, s);
+    h->ops.resid(h->g, h->ph, b, mode == FIN_RESID_BODY ? gs_settled(h) : -1, h->L, s);
     return 1 + fin(h, b, s, 4, mode, cond, use_cond);
 }
 

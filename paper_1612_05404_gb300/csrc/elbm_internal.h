@@ -93,7 +93,9 @@ struct Ops {
     // stage 1: q from the finalised sums, with block sums of q and q^2
     void (*charge)(const Geom &, const Phys &, const Bufs &, int stage, const Launch &, cudaStream_t);
     void (*sor)(const Geom &, const Phys &, const Bufs &, int color, const Launch &, cudaStream_t);
-    void (*resid)(const Geom &, const Phys &, const Bufs &, const Launch &, cudaStream_t);
+    // zc: the colour whose residual is taken as 0 (the one a Gauss-Seidel
+    // sweep updated last), or -1
+    void (*resid)(const Geom &, const Phys &, const Bufs &, int zc, const Launch &, cudaStream_t);
     // stage 0: block sums of phi over non-solid nodes; stage 1: subtract S_PHIMEAN
     void (*phi_mean)(const Geom &, const Phys &, const Bufs &, int stage, const Launch &, cudaStream_t);
     void (*collide)(const Geom &, const Phys &, const Bufs &, int diag, const Launch &, cudaStream_t);
@@ -121,7 +123,7 @@ struct MGOps {
     void (*smooth)(const Geom &, const Phys &, const Bufs &, const MGLevel &, int level, int color,
                    const Launch &fine_half, cudaStream_t);
     void (*restrict_)(const Geom &, const Phys &, const Bufs &, const MGLevel &F, const MGLevel &C, int level,
-                      cudaStream_t);
+                      int zc, cudaStream_t);
     void (*eps)(const Geom &, const Phys &, const Bufs &, const MGLevel &F, const MGLevel &C, int level,
                 cudaStream_t);
     void (*prolong)(const Geom &, const Bufs &, const MGLevel &F, const MGLevel &C, int level, cudaStream_t);

@@ -729,7 +729,7 @@ __global__ void __launch_bounds__(128) k_sor(Geom g, Phys ph, Bufs b, int color,
 // residual r = div(eps grad phi) + q - qmean with the reference norms:
 // per-block sums of r^2, q^2 (fluid) and b^2 (Dirichlet data)
 template <int PR>
-__global__ void __launch_bounds__(128) k_resid(Geom g, Phys ph, Bufs b)
+__global__ void __launch_bounds__(128) k_resid(Geom g, Phys ph, Bufs b, int zc)
 {
     typedef typename Tr<PR>::sc sc;
     int x, y, z;
@@ -753,7 +753,23 @@ __global__ void __launch_bounds__(128) k_resid(Geom g, Phys ph, Bufs b)
         sc ps = phi[s];
         sc t = fabs(r);
         int xn[2];
-        if (pois_fast(g, b.mask, x, y, z, (int)s, xn)) {
+        sc tw = 1;  // weight of t^2 (see below)
+        if (zc >= 0 && ((x + y + z) & 1) == zc && pois_fast(g, b.mask, x, y, z, (int)s, xn)) {
+            // a site of the colour a Gauss-Seidel sweep has just updated: its
+            // residual is the rounding of that update (the level the FP32
+            // floor stop tolerates), taken as 0; only the Dirichlet data of a
+            // row's end faces enter (the reference norm), and its |t| is
+            // counted by the sites of the other colour (tw = 2 there)
+            r = 0;
+            t = 0;
+#pragma unroll
+            for (int sg = -1; sg <= 1; sg += 2) {
+                sc v = 0;
+                if (xn[sg > 0] < 0 && pois_xface<sc>(g, k, x, y, z, sg, &v))
+                    bs += es * (v + interior_dl<sc>(g, k, 0, sg) + phi_lin_at<sc>(g, k, x, y, z));
+            }
+        } else if (pois_fast(g, b.mask, x, y, z, (int)s, xn)) {
+            if (zc >= 0) tw = 2;
             const int off[3] = {1, g.nx, g.nx * g.ny};
 #pragma unroll
             for (int a = 0; a < 3; a++)
@@ -801,7 +817,7 @@ __global__ void __launch_bounds__(128) k_resid(Geom g, Phys ph, Bufs b)
         r2 = r * r;
         q2 = qs * qs;
         b2 = bs * bs;
-        t2 = t * t;
+        t2 = tw * t * t;
     }
     sc v[4] = {r2, q2, b2, t2};
     block_sums<4>(v, b.part + block_id(), num_blocks());
@@ -1457,9 +1473,9 @@ struct Launchers {
         if (g.ncol == 3) k_sor<PR, 3><<<L.grid, L.block, 0, s>>>(g, ph, b, color, 0);
         else k_sor<PR, 2><<<L.grid, L.block, 0, s>>>(g, ph, b, color, 0);
     }
-    static void resid(const Geom &g, const Phys &ph, const Bufs &b, const Launch &L, cudaStream_t s)
+    static void resid(const Geom &g, const Phys &ph, const Bufs &b, int zc, const Launch &L, cudaStream_t s)
     {
-        k_resid<PR><<<L.grid, L.block, 0, s>>>(g, ph, b);
+        k_resid<PR><<<L.grid, L.block, 0, s>>>(g, ph, b, zc);
     }
     static void phi_mean(const Geom &g, const Phys &ph, const Bufs &b, int stage, const Launch &L, cudaStream_t s)
     {
@@ -1772,7 +1788,8 @@ __device__ __forceinline__ typename Tr<PR>::sc mg_resid_at(const Geom &g, const 
 // consecutive lanes handle the children of one coarse cell and sum them with
 // a fixed shuffle tree.
 template <int PR, bool ODD>
-__global__ void __launch_bounds__(128) k_mg_restrict(Geom g, Phys ph, Bufs bf, MGLevel F, MGLevel C, int level)
+__global__ void __launch_bounds__(128) k_mg_restrict(Geom g, Phys ph, Bufs bf, MGLevel F, MGLevel C, int level,
+                                                     int zc)
 {
     typedef typename Tr<PR>::sc T;
     const unsigned gid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1789,7 +1806,9 @@ __global__ void __launch_bounds__(128) k_mg_restrict(Geom g, Phys ph, Bufs bf, M
         X = (int)(rem - (unsigned)Y * (unsigned)C.nx);
         const int fx = 2 * X + (c & 1), fy = 2 * Y + ((c >> 1) & 1), fz = 2 * Z + (c >> 2);
         if (!ODD || (fx < F.nx && fy < F.ny && fz < F.nz)) {
-            r = mg_resid_at<PR>(g, ph, bf, F, level, fx, fy, fz);
+            // zc: the colour the fine Gauss-Seidel sweep updated last, whose
+            // residual is the rounding of that update, taken as 0 (-1: none)
+            if (zc < 0 || ((fx + fy + fz) & 1) != zc) r = mg_resid_at<PR>(g, ph, bf, F, level, fx, fy, fz);
             // the coarse permittivity (mean of the children) comes with the
             // restriction: the coarse level's smoothing and residual read it next
             const ll fs = fx + (ll)F.nx * (fy + (ll)F.ny * fz);
@@ -2115,12 +2134,12 @@ struct MGLaunchers {
         }
     }
     static void restrict_(const Geom &g, const Phys &ph, const Bufs &b, const MGLevel &F, const MGLevel &C,
-                          int level, cudaStream_t s)
+                          int level, int zc, cudaStream_t s)
     {
         long long thr = 8 * C.N;
         const unsigned nb = (unsigned)((thr + 127) / 128);
-        if ((F.nx | F.ny | F.nz) & 1) k_mg_restrict<PR, true><<<nb, 128, 0, s>>>(g, ph, b, F, C, level);
-        else k_mg_restrict<PR, false><<<nb, 128, 0, s>>>(g, ph, b, F, C, level);
+        if ((F.nx | F.ny | F.nz) & 1) k_mg_restrict<PR, true><<<nb, 128, 0, s>>>(g, ph, b, F, C, level, zc);
+        else k_mg_restrict<PR, false><<<nb, 128, 0, s>>>(g, ph, b, F, C, level, zc);
     }
     static void eps(const Geom &g, const Phys &ph, const Bufs &b, const MGLevel &F, const MGLevel &C, int level,
                     cudaStream_t s)
