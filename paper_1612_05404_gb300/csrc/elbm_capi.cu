@@ -331,12 +331,14 @@ Ctl make_ctl(const elbm_handle *h, unsigned long long cond, int use_cond)
 }
 
 int fin(elbm_handle *h, const Bufs &b, cudaStream_t s, int K, int mode, unsigned long long cond = 0,
-        int use_cond = 0, int steps = 1)
+        int use_cond = 0, int steps = 1, int nblocks = 0)
 {
     Ctl c = make_ctl(h, cond, use_cond);
     c.steps = steps;
-    k_finalize<<<K, kFinThreads, 0, s>>>(b.part, h->L.nblocks, K, mode, h->ph, c, b.scal, b.scalf, b.diag, b.colres,
-                                 b.ticket);
+    // nblocks: the block count of the kernel that wrote the partials (its
+    // own column stride); 0 = the site kernels' shape
+    k_finalize<<<K, kFinThreads, 0, s>>>(b.part, nblocks > 0 ? nblocks : h->L.nblocks, K, mode, h->ph, c, b.scal,
+                                         b.scalf, b.diag, b.colres, b.ticket);
     return 1;
 }
 
@@ -414,8 +416,12 @@ int enq_eps(elbm_handle *h, const Bufs &b, cudaStream_t s)
 // convergence test: residual sums, then the device-side decision
 int enq_check(elbm_handle *h, const Bufs &b, cudaStream_t s, int mode, unsigned long long cond, int use_cond)
 {
-    h->ops.resid(h->g, h->ph, b, mode == FIN_RESID_BODY ? gs_settled(h) : -1, h->L, s);
-    return 1 + fin(h, b, s, 4, mode, cond, use_cond);
+    // with a settled colour the residual runs one thread per pair of x
+    // (the half-row shape of the red-black sweeps)
+    const int zc = mode == FIN_RESID_BODY ? gs_settled(h) : -1;
+    const Launch &L = zc >= 0 ? h->Lh : h->L;
+    h->ops.resid(h->g, h->ph, b, zc, L, s);
+    return 1 + fin(h, b, s, 4, mode, cond, use_cond, 1, L.nblocks);
 }
 
 // one Poisson unit: a V-cycle, or ce red-black SOR sweeps
@@ -968,7 +974,8 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     };
     const bool transport = p->charge_model == ELBM_CHARGE_TRANSPORT;
     const bool masks = h->nlev > 0 && n_solid > 0;  // coarse conductor masks
-    const long long part_blocks = p->autotune ? max_blocks_over_shapes(p) : L.nblocks;
+    long long part_blocks = p->autotune ? max_blocks_over_shapes(p) : L.nblocks;
+    if (h->Lh.nblocks > part_blocks) part_blocks = h->Lh.nblocks;  // the pair-wise residual's partials
     auto plan = [&]() {
         alloc(&b.fA, (size_t)Q * N * h->pop_bytes);
         alloc(&b.fB, (size_t)Q * N * h->pop_bytes);

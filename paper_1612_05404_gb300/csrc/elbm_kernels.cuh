@@ -728,21 +728,18 @@ __global__ void __launch_bounds__(128) k_sor(Geom g, Phys ph, Bufs b, int color,
 
 // residual r = div(eps grad phi) + q - qmean with the reference norms:
 // per-block sums of r^2, q^2 (fluid) and b^2 (Dirichlet data)
+// The stop rule's sums at site (x, y, z), added to acc: r^2, q^2, b^2 and
+// t^2, t = the magnitude of the terms of r (source and every face term with
+// |phi| in place of its difference): the residual of a potential stored in
+// FP32 cannot fall much below 2^-24 |t|
 template <int PR>
-__global__ void __launch_bounds__(128) k_resid(Geom g, Phys ph, Bufs b, int zc)
+__device__ __forceinline__ void resid_site(const Geom &g, const Phys &ph, const Bufs &b, int zc, int x, int y, int z,
+                                           typename Tr<PR>::sc (&acc)[4])
 {
     typedef typename Tr<PR>::sc sc;
-    int x, y, z;
-    bool inb;
-    ll s;
-    site_xyz(g, x, y, z, inb, s);
-    unsigned char kind = (inb && b.mask) ? b.mask[s] : 0;
-    bool active = inb && kind != ELBM_NODE_SOLID;
-    // r^2, q^2, b^2 and t^2, t = the magnitude of the terms of r (source and
-    // every face term with |phi| in place of its difference): the residual of
-    // a potential stored in FP32 cannot fall much below 2^-24 |t|
-    sc r2 = 0, q2 = 0, b2 = 0, t2 = 0;
-    if (active) {
+    const ll s = x + (ll)g.nx * (y + (ll)g.ny * z);
+    unsigned char kind = b.mask ? b.mask[s] : 0;
+    if (kind != ELBM_NODE_SOLID) {
         const sc *phi = (const sc *)b.phi;
         const sc *rho = (const sc *)b.rho;
         const Cst<sc> &k = cst<sc>(ph);
@@ -814,13 +811,47 @@ __global__ void __launch_bounds__(128) k_resid(Geom g, Phys ph, Bufs b, int zc)
                     }
                 }
         }
-        r2 = r * r;
-        q2 = qs * qs;
-        b2 = bs * bs;
-        t2 = tw * t * t;
+        acc[0] += r * r;
+        acc[1] += qs * qs;
+        acc[2] += bs * bs;
+        acc[3] += tw * t * t;
     }
-    sc v[4] = {r2, q2, b2, t2};
-    block_sums<4>(v, b.part + block_id(), num_blocks());
+}
+
+// per-block sums of r^2, q^2 (fluid), b^2 (Dirichlet data) and t^2, one
+// thread per site
+template <int PR>
+__global__ void __launch_bounds__(128) k_resid(Geom g, Phys ph, Bufs b, int zc)
+{
+    typedef typename Tr<PR>::sc sc;
+    int x, y, z;
+    bool inb;
+    ll s;
+    site_xyz(g, x, y, z, inb, s);
+    sc acc[4] = {0, 0, 0, 0};
+    if (inb) resid_site<PR>(g, ph, b, zc, x, y, z, acc);
+    block_sums<4>(acc, b.part + block_id(), num_blocks());
+}
+
+// The same sums with the colour zc settled (red-black, reduced precision):
+// one thread per site of the other colour, x = 2 i + ((y + z + 1 - zc) & 1),
+// which also takes its partner of colour zc in the same pair of x (the
+// settled site costs its own q and the Dirichlet data of a row's end), so
+// that no warp splits between the full and the settled sites.
+template <int PR>
+__global__ void __launch_bounds__(128) k_resid_pairs(Geom g, Phys ph, Bufs b, int zc)
+{
+    typedef typename Tr<PR>::sc sc;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    sc acc[4] = {0, 0, 0, 0};
+    if (y < g.ny) {
+        const int xa = 2 * i + ((y + z + 1 - zc) & 1), xb = 2 * i + ((y + z + zc) & 1);
+        if (xa < g.nx) resid_site<PR>(g, ph, b, zc, xa, y, z, acc);
+        if (xb < g.nx) resid_site<PR>(g, ph, b, zc, xb, y, z, acc);
+    }
+    block_sums<4>(acc, b.part + block_id(), num_blocks());
 }
 
 template <int PR>
@@ -1475,7 +1506,8 @@ struct Launchers {
     }
     static void resid(const Geom &g, const Phys &ph, const Bufs &b, int zc, const Launch &L, cudaStream_t s)
     {
-        k_resid<PR><<<L.grid, L.block, 0, s>>>(g, ph, b, zc);
+        if (zc >= 0) k_resid_pairs<PR><<<L.grid, L.block, 0, s>>>(g, ph, b, zc);  // L: the half-row shape
+        else k_resid<PR><<<L.grid, L.block, 0, s>>>(g, ph, b, zc);
     }
     static void phi_mean(const Geom &g, const Phys &ph, const Bufs &b, int stage, const Launch &L, cudaStream_t s)
     {
