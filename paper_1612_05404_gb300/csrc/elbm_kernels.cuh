@@ -1861,6 +1861,44 @@ __global__ void __launch_bounds__(128) k_mg_restrict(Geom g, Phys ph, Bufs bf, M
     }
 }
 
+// Level 0 -> 1 with the colour zc settled (red-black, reduced precision,
+// even extents): four lanes per coarse cell, each taking one pair of x
+// children: the residual of its unsettled child (the settled child's is the
+// rounding of its update, taken as 0) and the permittivity of both; so no
+// warp splits between full and settled children.
+template <int PR>
+__global__ void __launch_bounds__(128) k_mg_restrict_pairs(Geom g, Phys ph, Bufs bf, MGLevel F, MGLevel C, int zc)
+{
+    typedef typename Tr<PR>::sc T;
+    const unsigned gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned S = gid >> 2;
+    const int c = (int)(gid & 3);
+    const bool act = S < (unsigned)C.N;
+    T r = 0, ep = 0;
+    if (act) {
+        const unsigned nxy = (unsigned)C.nx * (unsigned)C.ny;
+        const int Z = (int)(S / nxy);
+        const unsigned rem = S - (unsigned)Z * nxy;
+        const int Y = (int)(rem / (unsigned)C.nx);
+        const int X = (int)(rem - (unsigned)Y * (unsigned)C.nx);
+        const int fy = 2 * Y + (c & 1), fz = 2 * Z + (c >> 1);
+        r = mg_resid_at<PR>(g, ph, bf, F, 0, 2 * X + ((fy + fz + 1 - zc) & 1), fy, fz);
+        const ll f0 = 2 * X + (ll)F.nx * (fy + (ll)F.ny * fz);
+        const T kap = cst<T>(ph).kap;
+        const T *rho = (const T *)bf.rho;
+        ep = (T(1) + kap * rho[f0]) + (T(1) + kap * rho[f0 + 1]);
+    }
+    r += __shfl_down_sync(0xffffffffu, r, 2, 4);
+    r += __shfl_down_sync(0xffffffffu, r, 1, 4);
+    ep += __shfl_down_sync(0xffffffffu, ep, 2, 4);
+    ep += __shfl_down_sync(0xffffffffu, ep, 1, 4);
+    if (act && c == 0) {
+        ((T *)C.b)[S] = (C.m && C.m[S]) ? T(0) : r;
+        ((T *)C.e)[S] = T(0);
+        ((T *)C.eps)[S] = ep * T(0.125);
+    }
+}
+
 // coarse permittivity: mean of the children (level 0 children from rho)
 template <int PR>
 __global__ void __launch_bounds__(128) k_mg_eps(Geom g, Phys ph, Bufs bf, MGLevel F, MGLevel C, int level)
@@ -2170,7 +2208,10 @@ struct MGLaunchers {
     {
         long long thr = 8 * C.N;
         const unsigned nb = (unsigned)((thr + 127) / 128);
-        if ((F.nx | F.ny | F.nz) & 1) k_mg_restrict<PR, true><<<nb, 128, 0, s>>>(g, ph, b, F, C, level, zc);
+        const bool odd = ((F.nx | F.ny | F.nz) & 1) != 0;
+        if (level == 0 && zc >= 0 && !odd)
+            k_mg_restrict_pairs<PR><<<(unsigned)((4 * C.N + 127) / 128), 128, 0, s>>>(g, ph, b, F, C, zc);
+        else if (odd) k_mg_restrict<PR, true><<<nb, 128, 0, s>>>(g, ph, b, F, C, level, zc);
         else k_mg_restrict<PR, false><<<nb, 128, 0, s>>>(g, ph, b, F, C, level, zc);
     }
     static void eps(const Geom &g, const Phys &ph, const Bufs &b, const MGLevel &F, const MGLevel &C, int level,
