@@ -525,6 +525,32 @@ def fp64_configs(args):
     return out
 
 
+def poisson64(args):
+    """The Poisson chain of one lone 64^3 drop in field (E0 = 1e-3, FP32,
+    multigrid, warm), as the step runs it: CUDA events around each pass
+    (section graphs), V-cycles per step, device time per V-cycle (the
+    warm-start extrapolation and the stop tests included) and kernel
+    launches per step."""
+    from paper_1612_05404_gb300 import elbm
+    from paper_1612_05404_gb300 import workloads as W
+    cfg, fields = W.drop_in_field(E0=1e-3, precision="fp32")
+    cfg.update(alpha_precision="fp32", store_macro=0, diag_every=1, poisson_check_every=8, graph=1, autotune=1,
+               profile=1)
+    sim = elbm.Sim(cfg, fields)
+    sim.step(args.warmup)
+    p0 = sim.pass_times()
+    sim.step(args.steps)
+    p1 = sim.pass_times()
+    sim.close()
+    d = {k: p1[k] - p0[k] for k in p0}
+    n = max(d["steps"], 1)
+    cyc = d["sweeps"] / n
+    return {"poisson_ms_per_step": d["poisson_ms"] / n, "vcycles_per_step": cyc,
+            "ms_per_vcycle": d["poisson_ms"] / n / max(cyc, 1e-30), "launches_per_step": d["launches"] / n,
+            "step_ms": (d["moments_ms"] + d["poisson_ms"] + d["collide_ms"] + d["reduce_ms"]) / n,
+            "workload": "one 64^3 drop in field, E0 = 1e-3, FP32, multigrid V(2,2), tail of <= 4096 cells in one CTA"}
+
+
 def drop64(args):
     """Config 2 at full size: four 64^3 drops in field (the E0 sweep), FP32
     storage, guarded FP32 alpha, one batch; graphs of one step (diagnostics
@@ -825,6 +851,7 @@ def main():
             res["alpha_stage"] = alpha_stage(theta)
         res["jet128"] = jet128(args)
         res["drop64"] = drop64(args)
+        res["poisson64"] = poisson64(args)
         res["fp64_configs"] = fp64_configs(args)
         if args.boxes > 0:
             res["batched_compare"] = batched_compare(args, theta)

@@ -2055,6 +2055,36 @@ __device__ void tail_smooth(const Geom &g, const MGTail &t, T *E, T *B, T *P, co
     }
 }
 
+// The coarsest level when it has at most 32 cells: one warp, a cell per
+// lane, warp-level synchronisation between colours instead of the block's
+// barriers; the same updates in the same colour order as tail_smooth.
+template <typename T>
+__device__ void tail_smooth_warp(const Geom &g, const MGTail &t, T *E, T *B, T *P, const unsigned char *M, int k,
+                                 int sweeps)
+{
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    if (tid < 32) {
+        const int nx = t.nx[k], ny = t.ny[k], nz = t.nz[k];
+        const int n_[3] = {nx, ny, nz};
+        const unsigned char *m = M ? M + t.off[k] : nullptr;
+        T *e = E + t.off[k];
+        const T *b = B + t.off[k], *ep = P + t.off[k];
+        const int level = t.lt + k, nc = t.ncol[k];
+        const bool live = tid < (int)t.N[k];
+        const int x = tid % nx, y = (tid / nx) % ny, z = tid / (nx * ny);
+        const int col = live ? (nc == 3 ? color3(g.per, x, y, z, nx, ny, nz) : ((x + y + z) & 1)) : -1;
+        const bool work = live && !(m && m[tid]);  // conductor cell: correction stays 0
+        for (int it = 0; it < nc * sweeps; it++) {
+            if (work && col == it % nc) {
+                if (t.irr[k]) mg_gs_cell<T, true>(g, e, b, ep, n_, t.last[k], level, x, y, z);
+                else mg_gs_cell<T, false>(g, e, b, ep, n_, t.last[k], level, x, y, z);
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(1024) k_mg_tail(Geom g, MGTail t, int nu)
 {
@@ -2119,7 +2149,8 @@ __global__ void __launch_bounds__(1024) k_mg_tail(Geom g, MGTail t, int nu)
                 }
         __syncthreads();
     }
-    tail_smooth<T>(g, t, E, B, P, M, t.nt - 1, t.coarse_sweeps);
+    if (t.N[t.nt - 1] <= 32 && nthr >= 32) tail_smooth_warp<T>(g, t, E, B, P, M, t.nt - 1, t.coarse_sweeps);
+    else tail_smooth<T>(g, t, E, B, P, M, t.nt - 1, t.coarse_sweeps);
     // up: prolong (trilinear), smooth
     for (int k = t.nt - 2; k >= 0; k--) {
         const int nx = t.nx[k], ny = t.ny[k], nz = t.nz[k];
