@@ -394,11 +394,16 @@ int enq_pre(elbm_handle *h, const Bufs &b, cudaStream_t s)
     const int cm = h->p.charge_model;
     if (cm == ELBM_CHARGE_TRANSPORT) {
         n += fin(h, b, s, 2, FIN_CHARGE_Q);
-    } else if (cm == ELBM_CHARGE_CONSERVED || cm == ELBM_CHARGE_XI) {
+    } else if (cm == ELBM_CHARGE_CONSERVED) {
         o.charge(h->g, h->ph, b, 0, h->L, s);
         n += 2 + fin(h, b, s, 2, FIN_CHARGE_AB);
         o.charge(h->g, h->ph, b, 1, h->L, s);
         n += 1 + fin(h, b, s, 2, FIN_CHARGE_Q);
+    } else if (cm == ELBM_CHARGE_XI) {
+        // Eq. (surface-q3) needs no global sum: the second charge kernel
+        // writes q with its sums (q, q^2)
+        o.charge(h->g, h->ph, b, 0, h->L, s);
+        n += 2 + fin(h, b, s, 2, FIN_CHARGE_Q);
     }
     return n;
 }
@@ -1020,7 +1025,7 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
         }
         if (p->charge_model == ELBM_CHARGE_CONSERVED || p->charge_model == ELBM_CHARGE_XI) {
             alloc(&b.nh, (size_t)4 * N * h->sc_bytes);
-            alloc(&b.ab, (size_t)2 * N * h->sc_bytes);
+            if (p->charge_model == ELBM_CHARGE_CONSERVED) alloc(&b.ab, (size_t)2 * N * h->sc_bytes);
         }
         for (int l = 1; l < h->nlev; l++) {
             alloc(&h->lev[l].e, (size_t)h->lev[l].N * h->sc_bytes);

@@ -63,7 +63,7 @@ struct Bufs {
     const int *inlet_idx;             // adaptive inlet: the inlet nodes
     const double *inlet_u0;           // adaptive inlet: their initial velocities (3 each)
     void *nh;                         // paper-mode charge: 4 planes n_x, n_y, n_z, |grad rho|^2
-    void *ab;                         // paper-mode charge: 2 planes a, b
+    void *ab;                         // conserved paper-mode charge: 2 planes a, b (NULL otherwise)
     double *part;                     // per-block partial sums
     double *scal;                     // device scalars (S_*)
     float *scalf;                     // the same scalars rounded to FP32

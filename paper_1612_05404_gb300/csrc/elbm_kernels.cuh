@@ -590,6 +590,10 @@ __global__ void __launch_bounds__(128) k_charge_grad(Geom g, Phys ph, Bufs b)
 template <int PR>
 __global__ void __launch_bounds__(128) k_charge_ab(Geom g, Phys ph, Bufs b)
 {
+    // the xi form, Eq. (surface-q3), needs no global sum: the free charge
+    // q = xi_b a + xi_s b is written here with its block sums (q, q^2), the
+    // same values k_charge_q would form from the stored a and b
+    const bool xi = ph.charge_model == ELBM_CHARGE_XI;
     typedef typename Tr<PR>::sc sc;
     int x, y, z;
     bool inb;
@@ -616,9 +620,18 @@ __global__ void __launch_bounds__(128) k_charge_ab(Geom g, Phys ph, Bufs b)
         const Cst<sc> &k = cst<sc>(ph);
         av = r * sc(0.5) * (sc(1) + tanh((r - k.rho0) * k.itw));
         bv = nh[3 * g.N + s] * (sc(1) + sqrt(sqrt(kp * k.iKd)));
-        sc *ab = (sc *)b.ab;
-        ab[s] = av;
-        ab[g.N + s] = bv;
+        if (!xi) {  // the conserved form scales a and b by global sums first (k_charge_q)
+            sc *ab = (sc *)b.ab;
+            ab[s] = av;
+            ab[g.N + s] = bv;
+        } else {
+            const sc qv = k.xib * av + k.xis * bv;
+            ((sc *)b.q)[s] = qv;
+            av = qv;
+            bv = qv * qv;
+        }
+    } else if (xi && inb) {
+        ((sc *)b.q)[s] = sc(0);
     }
     sc v[2] = {av, bv};
     block_sums<2>(v, b.part + block_id(), num_blocks());
