@@ -361,21 +361,21 @@ __device__ __forceinline__ double pois_div(double a, double b) { return a / b; }
 // is +-slope along phi_axis in the deviation form. A row's first and last
 // sites then cost their warp a few instructions instead of the general path
 // (pois_nb), with the same operations in the same order.
-__device__ __forceinline__ bool pois_fast(const Geom &g, const unsigned *bbits, int x, int y, int z, int si,
+__device__ __forceinline__ bool pois_fast(const Geom &g, const unsigned char *mask, int x, int y, int z, int si,
                                           int xn[2])
 {
     if (y <= 0 || y >= g.ny - 1 || z <= 0 || z >= g.nz - 1) return false;
     xn[0] = x > 0 ? si - 1 : (g.per[0] ? si + g.nx - 1 : -1);
     xn[1] = x < g.nx - 1 ? si + 1 : (g.per[0] ? si - (g.nx - 1) : -1);
-    if (!bbits) return true;  // no solid node and no wall face
-    // the face neighbour r + c_p is solid or beyond a wall face exactly when
-    // the pull of the opposite population bounces: bit opp(p) of the site's
-    // bounce bits (p = 1..6: +x, -x, +y, -y, +z, -z); inside along y and z
-    // a set bit there means a solid node, along x only where the neighbour
-    // exists (xn >= 0)
-    const unsigned w = bbits[si];
-    if (w & (0xFu << 3)) return false;  // bits 3..6: the y and z neighbours
-    return !((xn[0] >= 0 && (w & 2u)) || (xn[1] >= 0 && (w & 4u)));
+    if (!mask) return true;
+    // six independent loads of one byte each (the site itself stands in for
+    // a missing x neighbour: the callers have returned at solid sites); the
+    // 4-byte bounce word would answer the same question with more traffic
+    const int nx = g.nx, nxy = g.nx * g.ny;
+    const unsigned char m0 = mask[xn[0] >= 0 ? xn[0] : si], m1 = mask[xn[1] >= 0 ? xn[1] : si];
+    const unsigned char m2 = mask[si - nx], m3 = mask[si + nx], m4 = mask[si - nxy], m5 = mask[si + nxy];
+    return (m0 != ELBM_NODE_SOLID) & (m1 != ELBM_NODE_SOLID) & (m2 != ELBM_NODE_SOLID) & (m3 != ELBM_NODE_SOLID) &
+           (m4 != ELBM_NODE_SOLID) & (m5 != ELBM_NODE_SOLID);
 }
 template <typename T>
 __device__ __forceinline__ T interior_dl(const Geom &g, const Cst<T> &k, int a, int sg)
@@ -691,7 +691,7 @@ __global__ void __launch_bounds__(128) k_sor(Geom g, Phys ph, Bufs b, int color,
     sc num = kind == ELBM_NODE_FLUID ? ((const sc *)b.q)[s] - scal_of<sc>(b, S_QMEAN) : sc(0);
     sc den = 0;
     int xn[2];
-    if (pois_fast(g, b.bbits, x, y, z, (int)s, xn)) {
+    if (pois_fast(g, b.mask, x, y, z, (int)s, xn)) {
         const int off[3] = {1, g.nx, g.nx * g.ny};
 #pragma unroll
         for (int a = 0; a < 3; a++)
@@ -765,7 +765,7 @@ __device__ __forceinline__ void resid_site(const Geom &g, const Phys &ph, const 
         sc t = fabs(r);
         int xn[2];
         sc tw = 1;  // weight of t^2 (see below)
-        if (zc >= 0 && ((x + y + z) & 1) == zc && pois_fast(g, b.bbits, x, y, z, (int)s, xn)) {
+        if (zc >= 0 && ((x + y + z) & 1) == zc && pois_fast(g, b.mask, x, y, z, (int)s, xn)) {
             // a site of the colour a Gauss-Seidel sweep has just updated: its
             // residual is the rounding of that update (the level the FP32
             // floor stop tolerates), taken as 0; only the Dirichlet data of a
@@ -779,7 +779,7 @@ __device__ __forceinline__ void resid_site(const Geom &g, const Phys &ph, const 
                 if (xn[sg > 0] < 0 && pois_xface<sc>(g, k, x, y, z, sg, &v))
                     bs += es * (v + interior_dl<sc>(g, k, 0, sg) + phi_lin_at<sc>(g, k, x, y, z));
             }
-        } else if (pois_fast(g, b.bbits, x, y, z, (int)s, xn)) {
+        } else if (pois_fast(g, b.mask, x, y, z, (int)s, xn)) {
             if (zc >= 0) tw = 2;
             const int off[3] = {1, g.nx, g.nx * g.ny};
 #pragma unroll
@@ -1790,7 +1790,7 @@ __device__ __forceinline__ typename Tr<PR>::sc mg_resid_at(const Geom &g, const 
         const T ps = phi[s];
         T r = kind == ELBM_NODE_FLUID ? ((const T *)bf.q)[s] - scal_of<T>(bf, S_QMEAN) : T(0);
         int xn[2];
-        if (pois_fast(g, bf.bbits, x, y, z, (int)s, xn)) {
+        if (pois_fast(g, bf.mask, x, y, z, (int)s, xn)) {
             const int off[3] = {1, g.nx, g.nx * g.ny};
 #pragma unroll
             for (int a = 0; a < 3; a++)
