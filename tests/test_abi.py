@@ -151,3 +151,32 @@ def test_batch_create_argument_checks(L):
     assert L.elbm_batch_create(arr, 1, 6, None, ctypes.byref(out)) == elbm.E_INVAL  # unknown flag
     assert L.elbm_batch_create(arr, 1, 17 << 8, None, ctypes.byref(out)) == elbm.E_INVAL  # span above 16
     assert not out.value
+
+
+def test_every_box_edge_passes_the_multigrid_checks(L):
+    """The batched-droplet boxes (periodic, FP32, multigrid) of every integer
+    edge 24..96, odd ones included: elbm_init's host checks (parameters, the
+    multigrid hierarchy with odd extents coarsened to (n + 1)/2 cells, the
+    one-CTA tail of at most 4096 cells) accept each; only the device
+    allocation can then fail (no GPU here). A lattice whose extents cannot
+    coarsen at all is refused before that."""
+    for edge in W.BATCH_EDGES:
+        cfg, fields = W.batched_droplet(edge, 5e-4, 0.7, precision="fp32")
+        P = elbm.make_params(cfg)
+        IF = elbm.InitFields()
+        rho = np.ascontiguousarray(fields["rho"], dtype=np.float64)
+        IF.rho0 = rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        h = ctypes.c_void_p()
+        rc = L.elbm_init(ctypes.byref(P), ctypes.byref(IF), 1, ctypes.byref(h))
+        assert rc != elbm.E_INVAL, edge
+        if h.value:
+            L.elbm_free(h)
+    cfg = W.base_params(shape=(3, 4, 4), charge_model="transport", poisson_solver="mg", precision="fp32",
+                        alpha_eq_tol=1e-5)
+    P = elbm.make_params(cfg)
+    IF = elbm.InitFields()
+    rho = np.ones(48)
+    IF.rho0 = rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    h = ctypes.c_void_p()
+    assert L.elbm_init(ctypes.byref(P), ctypes.byref(IF), 1, ctypes.byref(h)) == elbm.E_INVAL
+    assert not h.value
