@@ -93,6 +93,36 @@ def test_three_colour_sweep_is_independent_of_the_thread_count():
     assert np.array_equal(out[0], out[1])
 
 
+def test_poisson_point_charge_matches_fourier_green_function():
+    """Uniform permittivity on a periodic 12 x 10 x 8 lattice (eps = 1 +
+    kappa rho with rho uniform): the 7-point operator is diagonal in Fourier
+    space, eigenvalue
+    -eps lambda(k), lambda(k) = sum_a 2 (1 - cos(2 pi k_a / n_a)). A point
+    charge with its neutralising background then has the potential
+    phi_hat(k) = q_hat(k) / (eps lambda(k)) (k != 0, zero mean), computed
+    here by numpy's FFT: the oracle's SOR potential matches it."""
+    nx, ny, nz = 12, 10, 8
+    N = nx * ny * nz
+    kap = 0.7
+    cfg = W.base_params(shape=(nx, ny, nz), charge_model="xi", poisson_tol=1e-14, eps_kappa=kap)
+    rho = np.full(N, 1.3)
+    eps = 1.0 + kap * 1.3
+    q = np.zeros(N)
+    q[3 + nx * (4 + ny * 2)] = 1.0
+    qn = q - q.mean()
+    phi, it, res = oracle.poisson_solve(cfg, np.zeros(N, np.uint8), rho, qn)
+    assert res <= 1e-14 and it > 0
+    kz, ky, kx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    lam = (2 * (1 - np.cos(2 * np.pi * kx / nx)) + 2 * (1 - np.cos(2 * np.pi * ky / ny))
+           + 2 * (1 - np.cos(2 * np.pi * kz / nz)))
+    qh = np.fft.fftn(qn.reshape(nz, ny, nx))
+    ph = np.zeros_like(qh)
+    nzk = lam > 0
+    ph[nzk] = qh[nzk] / (eps * lam[nzk])  # div(eps grad phi) = -q  =>  eps lambda phi_hat = q_hat
+    ref = np.real(np.fft.ifftn(ph)).reshape(-1)
+    assert np.allclose(phi, ref - ref.mean(), rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
 def test_poisson_dirichlet_and_conductors_match_direct_solve():
     shape = (6, 4, 5)
     N = 120
@@ -268,6 +298,41 @@ def test_transport_relaxation_time_constant():
         eps = 1.0 + 2.0 * kappa
         expect = sigma / eps + 0.25 * (4e-3) * (2 * np.pi / n) ** 2
         assert rate == pytest.approx(-np.log(1 - expect), rel=0.02)
+
+
+def test_transport_advects_charge_with_the_flow():
+    """A Gaussian of transported charge in a uniform flow u (no conduction,
+    no Shan-Chen coupling): the equilibrium w q (1 + c.u/c_s,q^2) carries the
+    flux q u, and the global flux is conserved by streaming and kept by the
+    relaxation, so the charge's first moment advances by exactly Q u per step
+    (the centroid moves at u; diffusion only widens it). A wrong sign or
+    factor in the c.u/c_s,q^2 term fails. The charge is small (1e-6), so its
+    electric force leaves the flow uniform to O(1e-12). The Gaussian starts
+    at the middle of a 64-site periodic axis so that nothing of it (nor of
+    the scheme's ripples near tau_q = 1/2) crosses the wrap, where a
+    population would move the first moment by the axis length."""
+    n, steps, ux = 64, 60, 0.05
+    shape = (n, 4, 4)
+    N = n * 16
+    # (one SOR sweep per step: with no conduction the potential enters only
+    # through the force q E, negligible at this charge)
+    cfg = W.base_params(shape=shape, G=0.0, Gw=0.0, charge_model="transport", sigma_liq=0.0,
+                        sigma_gas=0.0, Dq=1e-2, poisson_fixed_sweeps=1)
+    x = np.tile(np.arange(n), 16).astype(float)
+    q0 = 1e-6 * np.exp(-0.5 * ((x - 32.0) / 2.0) ** 2)
+    u0 = np.zeros((N, 3))
+    u0[:, 0] = ux
+    sim = oracle.Sim(cfg, dict(mask=np.zeros(N, np.uint8), rho=np.full(N, 2.0), q=q0, u=u0.reshape(-1)))
+
+    def moments():
+        q = sim.g.reshape(7, N).sum(0)
+        return q.sum(), (q * x).sum()
+
+    Q0, M0 = moments()
+    sim.step(steps)
+    Q1, M1 = moments()
+    assert abs(Q1 - Q0) <= 1e-14 * Q0
+    assert abs(M1 - M0 - steps * ux * Q0) <= 1e-6 * steps * ux * Q0, (M1 - M0, steps * ux * Q0)
 
 
 def test_uniform_field_on_neutral_fluid_exerts_no_force():
