@@ -2,7 +2,8 @@
  * elbm.h -- C ABI of the GB300 (sm_103a) charged entropic lattice Boltzmann
  * library: one time step of Lauricella et al., "Entropic Lattice Boltzmann
  * Model for Charged Leaky Dielectric Multiphase Fluids in Electrified Jets"
- * (arXiv:1612.05404), Sec. II, on a 3-D D3Q19 lattice.
+ * (arXiv:1612.05404), Sec. II, on a 3-D D3Q19 lattice, or on the paper's own
+ * 2-D D2Q9 lattice (params.velset; the paper's experiments, Sec. III, are 2-D).
  *
  * One step (Sec. II C) is: moments; free charge (Eqs. surface-q2 / surface-q3,
  * or the transported D3Q7 charge); neutralisation and the variable-permittivity
@@ -17,7 +18,7 @@
  *  - Lattice arrays are flat, x fastest: site = x + nx*(y + ny*z). Host arrays
  *    passed in are FP64 (fields) or uint8 (node kinds), owned by the caller and
  *    only read during the call. Population arrays are planes: f[p*N + site],
- *    in the velocity order reported by elbm_velocity_set().
+ *    in the velocity order reported by elbm_velocity_set_of(params.velset).
  *  - The handle owns every byte of device memory it uses (one arena, plus
  *    the export scratch of elbm_fields); elbm_free releases it. Work is
  *    issued on the caller's CUDA stream (params.cuda_stream, NULL = the
@@ -58,6 +59,9 @@ enum { ELBM_CHARGE_NONE = 0, ELBM_CHARGE_CONSERVED = 1, ELBM_CHARGE_XI = 2,
  * the fluid face neighbours by central differences; a neighbour that is not
  * fluid takes the site's own |E|^2) */
 enum { ELBM_FEL_QE = 0, ELBM_FEL_FULL = 1 };
+/* velocity set of the populations: D3Q19 (3-D), or the paper's D2Q9 (Sec. II:
+ * rest 4/9, axis 1/9, diagonals 1/36) on a lattice one site thick (nz = 1) */
+enum { ELBM_VSET_D3Q19 = 0, ELBM_VSET_D2Q9 = 1 };
 /* face permittivity of the Poisson operator: arithmetic or harmonic mean of
  * the two sites (a Dirichlet face couples with the site's own eps) */
 enum { ELBM_EPS_FACE_ARITH = 0, ELBM_EPS_FACE_HARMONIC = 1 };
@@ -119,7 +123,7 @@ enum { ELBM_APREC_FP64 = 0, ELBM_APREC_FP32 = 1, ELBM_APREC_FP32_FAST = 2 };
 #define ELBM_NDIAG 24
 
 typedef struct elbm_params {
-    int nx, ny, nz;              /* lattice (3-D, D3Q19); nx*ny*nz < 2^31 (ELBM_E_INVAL otherwise) */
+    int nx, ny, nz;              /* lattice; nz = 1 for D2Q9; nx*ny*nz < 2^31 (ELBM_E_INVAL otherwise) */
     int face_bc[6];              /* ELBM_FACE_* ; opposite faces must agree when periodic */
     int phi_bc[6];               /* ELBM_PHI_* ; PERIODIC exactly where face_bc is */
     int phi_axis;                /* axis normal to the electrode planes (0,1,2) */
@@ -173,6 +177,13 @@ typedef struct elbm_params {
                                     certifies (float-float guard), 0 = 1e-10; below
                                     the guard's resolution (~1e-11) sites end as
                                     guard failures (diag 20); ignored in FP64 */
+    int velset;                  /* ELBM_VSET_* (0 = D3Q19). D2Q9 needs nz = 1 and phi_axis
+                                    0 or 1; the z faces take no part (no link crosses them,
+                                    the potential has no z flux: face_bc[4..5] and
+                                    phi_bc[4..5] are ignored, E_ext[2] must be 0). It runs
+                                    FP64 or FP32 populations with the FP64 or the guarded
+                                    FP32 root, the paper's charge models (not transport) and
+                                    SOR; other choices return ELBM_E_INVAL */
 } elbm_params;
 
 /* Initial state, all host arrays of N = nx*ny*nz sites (caller-owned):
@@ -393,6 +404,11 @@ const char *elbm_strerror(int status);
 /* The D3Q19 velocity set of the library (host call, no GPU needed):
  * c[3*p + a] and w[p] for p = 0..18; returns 19. */
 int elbm_velocity_set(int *c, double *w);
+
+/* The velocity set `velset` (ELBM_VSET_*; host call, no GPU needed): c[3*p + a]
+ * and w[p] for p = 0..Q-1 (either pointer may be NULL); returns Q (19 or 9),
+ * or ELBM_E_INVAL for an unknown set. */
+int elbm_velocity_set_of(int velset, int *c, double *w);
 
 #ifdef __cplusplus
 }

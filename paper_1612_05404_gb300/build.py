@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libelbm.so")
-SOURCES = ["elbm_capi.cu", "k_fp64.cu", "k_fp32.cu", "k_bf16.cu", "elbm_noalloc.cu", "elbm_alpha_api.cu", "elbm_mlp.cu"]
+SOURCES = ["elbm_capi.cu", "k_fp64.cu", "k_fp32.cu", "k_bf16.cu", "k_fp64_d2q9.cu", "k_fp32_d2q9.cu", "elbm_noalloc.cu", "elbm_alpha_api.cu", "elbm_mlp.cu"]
 HEADERS = ["elbm_device.cuh", "elbm_alpha.cuh", "elbm_mlp.cuh", "elbm_internal.h", "elbm_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -16,6 +16,7 @@
 #pragma once
 
 namespace elbm {
+ELBM_VS_BEGIN
 
 struct AlphaOutF {
     float alpha;    // the root (high part)
@@ -215,7 +216,7 @@ __device__ __forceinline__ ffl grp_sum(const Grp &g, ffl v)
 
 // ---------------------------------------------------------------------------
 // The exact inputs of the guard. The populations are f_p = w_p + d_p with d_p
-// the FP32 deviations and w_p the weights in FP64 (1/3, 1/18, 1/36); the
+// the FP32 deviations and w_p the weights of the set in FP64; the
 // guard forms, as float-float pairs, the site's moments drho = sum d and
 // j = sum c d, u = j / rho, and Delta_p = f^eq_p - f_p of Eq. (2) written as
 // w_p drho - d_p + w_p rho P_p(u), so that the root it certifies is the root
@@ -224,10 +225,10 @@ __device__ __forceinline__ ffl grp_sum(const Grp &g, ffl v)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ ffl w_ff(int p)
 {
-    constexpr float h0 = float(1.0 / 3.0), h1 = float(1.0 / 18.0), h2 = float(1.0 / 36.0);
-    constexpr float l0 = float(1.0 / 3.0 - double(h0)), l1 = float(1.0 / 18.0 - double(h1)),
-                    l2 = float(1.0 / 36.0 - double(h2));
-    return p == 0 ? ffl{h0, l0} : (p < 7 ? ffl{h1, l1} : ffl{h2, l2});
+    constexpr double W0 = wq(0), W1 = wq(1), W2 = wq(Q - 1);  // rest, axis, diagonal
+    constexpr float h0 = float(W0), h1 = float(W1), h2 = float(W2);
+    constexpr float l0 = float(W0 - double(h0)), l1 = float(W1 - double(h1)), l2 = float(W2 - double(h2));
+    return p == 0 ? ffl{h0, l0} : (p <= NAX ? ffl{h1, l1} : ffl{h2, l2});
 }
 
 struct SiteFF {
@@ -711,4 +712,5 @@ __device__ __forceinline__ AlphaOutF alpha_fp32(const float *f, const float *d, 
     return alpha_fp32_solve(f, d, fdev, rho, st, guard, a_start);
 }
 
+ELBM_VS_END
 }  // namespace elbm

@@ -38,6 +38,7 @@ struct elbm_handle {
     Launch Lh;                 // one thread per site of one red-black colour
     Ops ops;
     cudaStream_t s;            // the caller's stream: all work runs here
+    int Q;                     // populations per site of the velocity set (19 or 9)
     int has_dirichlet;
     double *pin;               // pinned host scalars; [9] Poisson no-convergence counter, [16..39] diagnostics
     int diag_mirror;           // pin[16..39] holds the last step's diagnostics (graph steps)
@@ -296,6 +297,16 @@ int validate(const elbm_params *p, const elbm_init_fields *in, int n_instances)
     if (p->diag_every < 0) return 1;
     if (p->poisson_solver != ELBM_POISSON_SOR && p->poisson_solver != ELBM_POISSON_MG) return 1;
     if (p->autotune != 0 && p->autotune != 1) return 1;
+    if (p->velset != ELBM_VSET_D3Q19 && p->velset != ELBM_VSET_D2Q9) return 1;
+    if (p->velset == ELBM_VSET_D2Q9) {
+        // one site thick, potential data in the plane
+        if (p->nz != 1 || p->phi_axis > 1 || p->E_ext[2] != 0.0) return 1;
+        // the kernels built for D2Q9: FP64 / FP32 populations, FP64 or guarded FP32 root, SOR
+        if (p->precision == ELBM_PREC_BF16 || p->alpha_mode == ELBM_ALPHA_LEARNED ||
+            p->alpha_precision == ELBM_APREC_FP32_FAST)
+            return 1;
+        if (p->charge_model == ELBM_CHARGE_TRANSPORT || p->poisson_solver != ELBM_POISSON_SOR) return 1;
+    }
     return 0;
 }
 
@@ -769,6 +780,13 @@ int elbm_velocity_set(int *c, double *w)
     return Q;
 }
 
+int elbm_velocity_set_of(int velset, int *c, double *w)
+{
+    if (velset == ELBM_VSET_D3Q19) return elbm_velocity_set(c, w);
+    if (velset == ELBM_VSET_D2Q9) return vset_d2q9(c, w);
+    return ELBM_E_INVAL;
+}
+
 elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_instances,
                       elbm_handle **out)
 {
@@ -785,8 +803,15 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     Geom &g = h->g;
     g.nx = p->nx; g.ny = p->ny; g.nz = p->nz; g.N = N;
     for (int a = 0; a < 3; a++) g.per[a] = p->face_bc[2 * a] == ELBM_FACE_PERIODIC;
-    g.ncol = ncolors_of(g.per, p->nx, p->ny, p->nz);
     for (int f = 0; f < 6; f++) g.phi_kind[f] = p->phi_bc[f];
+    h->Q = p->velset == ELBM_VSET_D2Q9 ? vset_d2q9(nullptr, nullptr) : Q;
+    if (p->velset == ELBM_VSET_D2Q9) {
+        // the one-site-thick z axis: no population crosses it (c_z = 0) and
+        // the potential has no flux through its faces
+        g.per[2] = 0;
+        g.phi_kind[4] = g.phi_kind[5] = ELBM_PHI_NEUMANN;
+    }
+    g.ncol = ncolors_of(g.per, p->nx, p->ny, p->nz);
     g.phi_axis = p->phi_axis;
     // reduced precision: the potential plane holds its deviation from the
     // linear profile between the electrodes (both faces of phi_axis Dirichlet)
@@ -805,7 +830,7 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     }
     h->has_dirichlet = n_solid > 0;
     for (int f = 0; f < 6; f++)
-        if (p->phi_bc[f] == ELBM_PHI_DIRICHLET) h->has_dirichlet = 1;
+        if (g.phi_kind[f] == ELBM_PHI_DIRICHLET) h->has_dirichlet = 1;  // the faces that take part
 
     Phys &ph = h->ph;
     Cst<double> &k = ph.cd;
@@ -958,9 +983,10 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
         h->mg.prepare();
     }
 
+    const bool d2 = p->velset == ELBM_VSET_D2Q9;
     switch (p->precision) {
-    case ELBM_PREC_FP64: h->ops = ops_fp64(); h->pop_bytes = 8; h->sc_bytes = 8; h->g_bytes = 8; break;
-    case ELBM_PREC_FP32: h->ops = ops_fp32(); h->pop_bytes = 4; h->sc_bytes = 4; h->g_bytes = 4; break;
+    case ELBM_PREC_FP64: h->ops = d2 ? ops_fp64_d2q9() : ops_fp64(); h->pop_bytes = 8; h->sc_bytes = 8; h->g_bytes = 8; break;
+    case ELBM_PREC_FP32: h->ops = d2 ? ops_fp32_d2q9() : ops_fp32(); h->pop_bytes = 4; h->sc_bytes = 4; h->g_bytes = 4; break;
     default: h->ops = ops_bf16(); h->pop_bytes = 2; h->sc_bytes = 4; h->g_bytes = 4; break;
     }
 
@@ -982,8 +1008,8 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     long long part_blocks = p->autotune ? max_blocks_over_shapes(p) : L.nblocks;
     if (h->Lh.nblocks > part_blocks) part_blocks = h->Lh.nblocks;  // the pair-wise residual's partials
     auto plan = [&]() {
-        alloc(&b.fA, (size_t)Q * N * h->pop_bytes);
-        alloc(&b.fB, (size_t)Q * N * h->pop_bytes);
+        alloc(&b.fA, (size_t)h->Q * N * h->pop_bytes);
+        alloc(&b.fB, (size_t)h->Q * N * h->pop_bytes);
         if (p->precision == ELBM_PREC_BF16) {
             alloc((void **)&b.rA, (size_t)N * sizeof(float));
             alloc((void **)&b.rB, (size_t)N * sizeof(float));
@@ -1107,7 +1133,7 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
 
     // upload the initial fields into temporaries and build f(r, 0)
     double *d_rho0 = nullptr, *d_u0 = nullptr, *d_f0 = nullptr, *d_uin = nullptr, *d_q0 = nullptr;
-    const size_t n_up = (in->rho0 ? N : 0) + (in->u0 ? 3 * N : 0) + (in->f0 ? (size_t)Q * N : 0) +
+    const size_t n_up = (in->rho0 ? N : 0) + (in->u0 ? 3 * N : 0) + (in->f0 ? (size_t)h->Q * N : 0) +
                         (in->u_in ? 3 * N : 0) + (transport && in->q0 ? N : 0);
     double *d_up = nullptr;  // one temporary for all of them
     if (ok && n_up > 0 && !cuda_ok(cudaMalloc((void **)&d_up, n_up * sizeof(double)))) { d_up = nullptr; ok = false; }
@@ -1120,12 +1146,12 @@ elbm_status elbm_init(const elbm_params *p, const elbm_init_fields *in, int n_in
     };
     up(&d_rho0, in->rho0, N);
     up(&d_u0, in->u0, 3 * N);
-    up(&d_f0, in->f0, (size_t)Q * N);
+    up(&d_f0, in->f0, (size_t)h->Q * N);
     up(&d_uin, in->u_in, 3 * N);
     if (transport) up(&d_q0, in->q0, N);
     if (ok && b.mask && !cuda_ok(cudaMemcpyAsync(b.mask, in->mask, N, cudaMemcpyHostToDevice, h->s))) ok = false;
     if (ok && b.bbits) {
-        k_bounce_bits<<<L.grid, L.block, 0, h->s>>>(g, b.mask, const_cast<unsigned *>(b.bbits));
+        h->ops.bounce_bits(g, b, L, h->s);
         ok = cuda_ok(cudaGetLastError());
     }
     if (ok && ph.adaptive) {
@@ -1334,7 +1360,7 @@ size_t elbm_fields_size(const elbm_handle *h, unsigned mask)
     if (mask & ELBM_F_Q) n += N;
     if (mask & ELBM_F_ALPHA) n += N;
     if (mask & ELBM_F_NU) n += N;
-    if (mask & ELBM_F_POP) n += (size_t)Q * N;
+    if (mask & ELBM_F_POP) n += (size_t)h->Q * N;
     if (mask & ELBM_F_GPOP) n += (size_t)Q7 * N;
     if (mask & ELBM_F_DIAG) n += ELBM_NDIAG;
     return n;
@@ -1351,7 +1377,7 @@ elbm_status elbm_fields(elbm_handle *h, unsigned mask, double *out, size_t out_l
     const long long N = h->g.N;
     size_t need = 0;
     if (mask & (ELBM_F_RHO | ELBM_F_U | ELBM_F_PHI | ELBM_F_Q | ELBM_F_ALPHA | ELBM_F_NU)) need = (size_t)N;
-    if (mask & ELBM_F_POP) need = (size_t)Q * N;
+    if (mask & ELBM_F_POP) need = (size_t)h->Q * N;
     if (mask & ELBM_F_GPOP) need = need > (size_t)Q7 * N ? need : (size_t)Q7 * N;
     if (need > h->xtmp_n) {  // grow the export scratch (kept: repeated reads allocate nothing)
         if (h->xtmp) cudaFree(h->xtmp);
@@ -1395,10 +1421,10 @@ elbm_status elbm_fields(elbm_handle *h, unsigned mask, double *out, size_t out_l
     if (mask & ELBM_F_NU) plane(h->b.nu);
     if ((mask & ELBM_F_POP) && st == ELBM_OK) {
         h->ops.export_pop(h->g, h->b, tmp, h->L, h->s);
-        if (!cuda_ok(cudaMemcpyAsync(out + off, tmp, (size_t)Q * N * sizeof(double), cudaMemcpyDeviceToHost, h->s)) ||
+        if (!cuda_ok(cudaMemcpyAsync(out + off, tmp, (size_t)h->Q * N * sizeof(double), cudaMemcpyDeviceToHost, h->s)) ||
             !cuda_ok(cudaStreamSynchronize(h->s)))
             st = ELBM_E_CUDA;
-        off += (size_t)Q * N;
+        off += (size_t)h->Q * N;
     }
     if ((mask & ELBM_F_GPOP) && st == ELBM_OK) {
         h->ops.export_gpop(h->g, h->b, tmp, h->L, h->s);

@@ -14,18 +14,48 @@
 namespace elbm {
 
 // ---------------------------------------------------------------------------
-// D3Q19 (the 3-D set with c_s^2 = 1/3 of the paper's D2Q9): rest, 6 axis
-// links, 12 face diagonals. The order is the library's public population
-// order (elbm_velocity_set). Components are encoded as characters '0'/'1'/'2'
-// for -1/0/+1 so that an unrolled loop folds them to constants.
+// Velocity set of the populations. A translation unit compiles the kernels
+// for one set: D3Q19 by default, the paper's D2Q9 (Sec. II, the set its
+// Eq. 2 is written for) where ELBM_D2Q9 is defined. Everything that depends
+// on the set (the tables, the per-site physics, the kernels and their
+// launchers) sits in an inline namespace named after it, so that the two
+// builds link into one library side by side; the problem description, the
+// constants and the buffer tables below are common to both. Components are
+// encoded as characters '0'/'1'/'2' for -1/0/+1 so that an unrolled loop
+// folds them to constants; opposite links are consecutive (p = 2k-1, 2k) in
+// both orders, which are the library's public population orders
+// (elbm_velocity_set_of).
 // ---------------------------------------------------------------------------
+#ifdef ELBM_D2Q9
+#define ELBM_VS_BEGIN inline namespace d2q9 {
+#else
+#define ELBM_VS_BEGIN inline namespace d3q19 {
+#endif
+#define ELBM_VS_END }
+
+ELBM_VS_BEGIN
+#ifdef ELBM_D2Q9
+// D2Q9: rest 4/9, the 4 axis links 1/9, the 4 diagonals 1/36, c_s^2 = 1/3;
+// lattices of this set are one site thick in z (nz = 1).
+constexpr int Q = 9;
+__host__ __device__ constexpr int cx(int p) { return "120112020"[p] - '1'; }
+__host__ __device__ constexpr int cy(int p) { return "111202002"[p] - '1'; }
+__host__ __device__ constexpr int cz(int p) { return "111111111"[p] - '1'; }
+__host__ __device__ constexpr double wq(int p) { return p == 0 ? 4.0 / 9.0 : (p < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
+#else
+// D3Q19 (the 3-D set with the c_s^2 = 1/3 of the paper's D2Q9): rest 1/3, the
+// 6 axis links 1/18, the 12 face diagonals 1/36.
 constexpr int Q = 19;
 __host__ __device__ constexpr int cx(int p) { return "1201111202020201111"[p] - '1'; }
 __host__ __device__ constexpr int cy(int p) { return "1112011200211112020"[p] - '1'; }
 __host__ __device__ constexpr int cz(int p) { return "1111120111120022002"[p] - '1'; }
-__host__ __device__ constexpr int opp(int p) { return p == 0 ? 0 : ((p & 1) ? p + 1 : p - 1); }
 __host__ __device__ constexpr double wq(int p) { return p == 0 ? 1.0 / 3.0 : (p < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
+#endif
+// number of the axis links (the rest population is 0, they are 1..NAX)
+constexpr int NAX = Q == 9 ? 4 : 6;
+__host__ __device__ constexpr int opp(int p) { return p == 0 ? 0 : ((p & 1) ? p + 1 : p - 1); }
 constexpr double CS2 = 1.0 / 3.0;
+ELBM_VS_END
 
 // D3Q7 for the charge advection-diffusion: rest 1/4, axis links 1/8, c_s^2 = 1/4.
 constexpr int Q7 = 7;
@@ -141,6 +171,7 @@ __device__ __forceinline__ T phi_ghost(const Geom &g, const Cst<T> &k, int face,
     return k.phi_lo + T(c + 1) * k.phi_slope;
 }
 
+ELBM_VS_BEGIN
 // ---------------------------------------------------------------------------
 // Eq. (2): f^eq_p = w_p rho (1 + P_p(u)), P_p(u) = c.u/c_s^2 + ((c.u)^2 - c_s^2 u^2)/(2 c_s^4)
 // ---------------------------------------------------------------------------
@@ -214,17 +245,25 @@ __device__ __forceinline__ void moments_dev(const float *d, float &rs, float &rs
         rs_lo = rs_lo - (t - rs);
         rs = t;
     }
-    float e[9];
+    constexpr int NP = (Q - 1) / 2;
+    float e[NP];
     esum = 0.f;
 #pragma unroll
-    for (int k = 0; k < 9; k++) {
+    for (int k = 0; k < NP; k++) {
         e[k] = d[2 * k + 1] - d[2 * k + 2];
         esum += fabsf(e[k]);
     }
+#ifdef ELBM_D2Q9
+    // e_0..e_3: +-x, +-y, (1,1), (1,-1)
+    jx = (e[0] + e[2]) + e[3];
+    jy = (e[1] + e[2]) - e[3];
+    jz = 0.f;
+#else
     // e_0..e_8: +-x, +-y, +-z, (1,1,0), (1,-1,0), (1,0,1), (1,0,-1), (0,1,1), (0,1,-1)
     jx = ((e[0] + e[3]) + (e[4] + e[5])) + e[6];
     jy = ((e[1] + e[3]) - (e[4] - e[7])) + e[8];
     jz = ((e[2] + e[5]) - (e[6] - e[7])) - e[8];
+#endif
 }
 
 // Bound on the absolute FP32 error of each component of u = j (1/rho): the
@@ -433,6 +472,7 @@ __device__ __forceinline__ AlphaOut alpha_fp64(const double *f, const double *d,
     return o;
 }
 
+ELBM_VS_END
 }  // namespace elbm
 
 #include "elbm_alpha.cuh"

@@ -1,5 +1,6 @@
 // elbm_internal.h -- host-side state of a handle and the per-precision kernel
-// launchers (implemented in k_fp64.cu / k_fp32.cu / k_bf16.cu).
+// launchers (implemented in k_fp64.cu / k_fp32.cu / k_bf16.cu, and for the
+// D2Q9 set in k_fp64_d2q9.cu / k_fp32_d2q9.cu).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -110,6 +111,8 @@ struct Ops {
     void (*export_plane)(const void *plane, double *out, long long n, cudaStream_t);
     // out[i] += lo[i] (the low part of a float-float plane)
     void (*add_plane)(const float *lo, double *out, long long n, cudaStream_t);
+    // the bounce bits of every site (Bufs.bbits), once at elbm_init
+    void (*bounce_bits)(const Geom &, const Bufs &, const Launch &, cudaStream_t);
     // the site-wide compute kernels (the collision variants): in a batch
     // graph every other kernel runs at a higher priority
     const void *heavy[5];
@@ -132,6 +135,11 @@ struct MGOps {
 Ops ops_fp64();
 Ops ops_fp32();
 Ops ops_bf16();
+// the same kernels for the D2Q9 set (k_fp64_d2q9.cu / k_fp32_d2q9.cu)
+Ops ops_fp64_d2q9();
+Ops ops_fp32_d2q9();
+// public population order and weights of D2Q9 (c: 3 per population)
+int vset_d2q9(int *c, double *w);
 MGOps mgops_fp64();
 MGOps mgops_fp32();
 

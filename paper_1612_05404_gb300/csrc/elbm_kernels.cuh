@@ -20,6 +20,8 @@ namespace elbm {
 
 typedef long long ll;
 
+ELBM_VS_BEGIN
+
 // ---------------------------------------------------------------------------
 // Block reductions. FP64 precision reduces in FP64. The FP32 modes reduce
 // within a warp in FP32 with an error-free transformation (TwoSum, Knuth) so
@@ -1207,7 +1209,14 @@ __global__ void __launch_bounds__(128, (PR == ELBM_PREC_FP64 || AP == ELBM_APREC
                 pxz -= D[p] * ct(cx(p) * cz(p));
                 pyz -= D[p] * ct(cy(p) * cz(p));
             }
+#ifdef ELBM_D2Q9
+            // a set without z links leaves the stress 2x2: max |eigenvalue| = |mean| + radius
+            (void)pzz; (void)pxz; (void)pyz;
+            const ct hm = ct(0.5) * (pxx + pyy), hd = ct(0.5) * (pxx - pyy);
+            ct Pn = fabs(hm) + sqrt(hd * hd + pxy * pxy);
+#else
             ct Pn = sym3_norm2<ct>(pxx, pyy, pzz, pxy, pxz, pyz);
+#endif
             if (ph.carreau_lagged) {
                 const ct np = ct(((const sc *)b.nu)[s]);  // 0 before the first step: nu0
                 nu = carreau_nu_lagged<ct>(k, Pn, alpha, r, np > ct(0) ? np : k.nu0);
@@ -1533,6 +1542,15 @@ struct Launchers {
         const bool lrn = ph.alpha_mode == ELBM_ALPHA_LEARNED;
         if constexpr (PR == ELBM_PREC_FP64) {
             k_collide<PR, ELBM_APREC_FP64, false><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
+        } else if constexpr (Q != 19) {
+            // other sets: the FP64 root or the guarded FP32 one (elbm_init
+            // refuses the learned proposal, whose features are D3Q19's, and
+            // the unguarded root)
+            (void)lrn;
+            if (ph.aprec == ELBM_APREC_FP64)
+                k_collide<PR, ELBM_APREC_FP64, false><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
+            else
+                k_collide<PR, ELBM_APREC_FP32, false><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
         } else {
             if (ph.aprec == ELBM_APREC_FP64)
                 k_collide<PR, ELBM_APREC_FP64, false><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
@@ -1545,6 +1563,10 @@ struct Launchers {
             else
                 k_collide<PR, ELBM_APREC_FP32, false><<<L.grid, L.block, 0, s>>>(g, ph, b, diag);
         }
+    }
+    static void bounce_bits(const Geom &g, const Bufs &b, const Launch &L, cudaStream_t s)
+    {
+        k_bounce_bits<<<L.grid, L.block, 0, s>>>(g, b.mask, const_cast<unsigned *>(b.bbits));
     }
     static void efield2(const Geom &g, const Phys &ph, const Bufs &b, const Launch &L, cudaStream_t s)
     {
@@ -1591,9 +1613,13 @@ struct Launchers {
         o.export_pop = export_pop;
         o.export_gpop = export_gpop;
         o.export_plane = export_plane;
+        o.bounce_bits = bounce_bits;
         o.heavy[0] = (const void *)k_collide<PR, ELBM_APREC_FP64, false>;
         if constexpr (PR == ELBM_PREC_FP64) {
             o.heavy[1] = o.heavy[2] = o.heavy[3] = o.heavy[4] = nullptr;
+        } else if constexpr (Q != 19) {
+            o.heavy[1] = (const void *)k_collide<PR, ELBM_APREC_FP32, false>;
+            o.heavy[2] = o.heavy[3] = o.heavy[4] = nullptr;
         } else {
             o.heavy[1] = (const void *)k_collide<PR, ELBM_APREC_FP32, false>;
             o.heavy[2] = (const void *)k_collide<PR, ELBM_APREC_FP32_FAST, false>;
@@ -1604,6 +1630,8 @@ struct Launchers {
     }
 };
 
+
+ELBM_VS_END  // the multigrid below is the same for every velocity set
 
 // ===========================================================================
 // Geometric multigrid for the same fine-level Poisson operator (an

@@ -25,7 +25,10 @@
 
 #include <cuda_bf16.h>
 
+#include "elbm_device.cuh"
+
 namespace elbm {
+ELBM_VS_BEGIN
 
 constexpr int MLP_NIN = 20, MLP_NH = 64;
 constexpr int MLP_OFF_W1 = 0, MLP_OFF_B1 = MLP_NH * MLP_NIN, MLP_OFF_W2 = MLP_OFF_B1 + MLP_NH,
@@ -180,4 +183,5 @@ __device__ __forceinline__ void mlp_site_features(const float *x, float S, __nv_
     for (int c = 20; c < 32; c += 2) *reinterpret_cast<unsigned *>(xrow + c) = 0u;
 }
 
+ELBM_VS_END
 }  // namespace elbm

@@ -24,7 +24,7 @@ DIAG_NAMES = [
     "n_guard_failed", "n_learned_fallback", "inlet_scale", "flags_undiagnosed",
 ]
 EXPORTS = ["elbm_init", "elbm_step", "elbm_fields", "elbm_fields_size", "elbm_free",
-           "elbm_strerror", "elbm_velocity_set", "elbm_pass_times", "elbm_density_noalloc",
+           "elbm_strerror", "elbm_velocity_set", "elbm_velocity_set_of", "elbm_pass_times", "elbm_density_noalloc",
            "elbm_alpha_eval", "elbm_alpha_features", "elbm_alpha_harvest", "elbm_mlp_forward",
            "elbm_mlp_workspace_floats", "elbm_mlp_grad", "elbm_mlp_adam", "elbm_mlp_train",
            "elbm_batch_create"]
@@ -72,6 +72,7 @@ class Params(ctypes.Structure):
         ("mlp", ctypes.c_void_p),
         ("eps_face", ctypes.c_int), ("carreau_lagged", ctypes.c_int),
         ("alpha_h_tol", ctypes.c_double),
+        ("velset", ctypes.c_int),
     ]
 
 
@@ -109,6 +110,8 @@ def lib():
         L.elbm_strerror.restype = ctypes.c_char_p
         L.elbm_velocity_set.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
         L.elbm_velocity_set.restype = ctypes.c_int
+        L.elbm_velocity_set_of.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+        L.elbm_velocity_set_of.restype = ctypes.c_int
         L.elbm_pass_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
         L.elbm_pass_times.restype = ctypes.c_int
         L.elbm_density_noalloc.argtypes = [vp, vp, ctypes.c_longlong, vp, vp, vp]
@@ -138,11 +141,17 @@ def strerror(code: int) -> str:
     return lib().elbm_strerror(int(code)).decode()
 
 
-def velocity_set():
+VSET = {3: 0, 2: 1}  # lattice dimension -> ELBM_VSET_D3Q19 / ELBM_VSET_D2Q9
+
+
+def velocity_set(dim: int = 3):
+    """(c (Q, 3), w (Q,)) of the D3Q19 set (dim 3) or the D2Q9 set (dim 2)."""
     c = (ctypes.c_int * 57)()
     w = (ctypes.c_double * 19)()
-    lib().elbm_velocity_set(c, w)
-    return np.array(list(c)).reshape(19, 3), np.array(list(w))
+    Q = lib().elbm_velocity_set_of(VSET[dim], c, w)
+    if Q < 0:
+        raise ElbmError(Q, "elbm_velocity_set_of")
+    return np.array(list(c)[:3 * Q]).reshape(Q, 3), np.array(list(w)[:Q])
 
 
 def make_params(cfg: dict, stream=None) -> Params:
@@ -184,6 +193,7 @@ def make_params(cfg: dict, stream=None) -> Params:
     P.eps_face = {"arithmetic": 0, "harmonic": 1}[cfg.get("eps_face", "arithmetic")]
     P.carreau_lagged = int(cfg.get("carreau_lagged", 0))
     P.alpha_h_tol = float(cfg.get("alpha_h_tol", 0.0))
+    P.velset = VSET[int(cfg.get("dim", 3))]
     mlp = cfg.get("mlp")
     P.mlp = None if mlp is None else mlp.data_ptr()
     return P

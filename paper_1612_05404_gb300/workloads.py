@@ -256,6 +256,65 @@ def paper_drop_2d(n=320, radius=40.0, Q=2.13, qs_over_qb=10.0, steps=1000,
     return cfg, fields
 
 
+JET2D_CASES = {  # Sec. III B: Newtonian, then Carreau with flow index 0.75 and 0.5
+    "a": dict(n_carreau=1.0, nu_inf=1.0 / 6.0, lam=0.0),
+    "b": dict(n_carreau=0.75, nu_inf=1e-3, lam=1000.0),
+    "c": dict(n_carreau=0.5, nu_inf=1e-3, lam=1000.0),
+}
+
+
+def jet_2d(n=320, D=40, case="a", nozzle_len=40, wall=5, u_mean=0.02, E0=0.1,
+           precision="fp64", steps=20000, seed=SEED_BASE + 7, perturb=0.0):
+    """The paper's 2-D electrified jet (Sec. III B) on D2Q9: an n x n lattice,
+    x along the jet. A nozzle of inner diameter D on the left (bore
+    |y - c| < D/2, walls `wall` sites thick, x < nozzle_len; a conductor at
+    the potential of the left side) holds the inlet nodes at x = 0; outlet
+    nodes at x = n - 1 are a vapour reservoir (rho 0.16); every face is a
+    bounce-back wall. The potential is 0 on the left ghost plane and
+    -E0 (n + 1) on the right one, linear along the upper and lower sides (a
+    field E0 along x); the charge is the xi form (1e-4, 6e-2), neutralised;
+    G = Gw = -5, eps = 1 + rho. The inlet profile is Poiseuille, rescaled
+    each step to the mean velocity measured inside the nozzle
+    (fields["inlet_region"]). Liquid fills the nozzle with a drop just
+    outside it. `case` picks the rheology (JET2D_CASES)."""
+    rh = JET2D_CASES[case]
+    shape = (n, n, 1)
+    nu0 = 1.0 / 6.0
+    cfg = base_params(
+        dim=2, shape=shape, charge_model="xi", xi_b=1e-4, xi_s=6e-2, K_d=1.0,
+        face_bc=["wall"] * 6, phi_bc=["dirichlet"] * 4 + ["neumann"] * 2, phi_axis=0,
+        phi_lo=0.0, phi_hi=-E0 * (n + 1), phi_solid=0.0,
+        nu0=nu0, nu_inf=rh["nu_inf"], n_carreau=rh["n_carreau"], eps_kappa=1.0,
+        precision=precision, poisson_tol=1e-13)
+    reduced_precision(cfg)
+    cfg["lambda"] = rh["lam"]
+    cfg["steps"] = steps
+    N = n * n
+    x = np.tile(np.arange(n), n).astype(float)
+    y = np.repeat(np.arange(n), n).astype(float)
+    yc = (n - 1) / 2.0
+    a0 = D / 2.0
+    ry = np.abs(y - yc)
+    mask = np.zeros(N, np.uint8)
+    mask[(ry >= a0) & (ry < a0 + wall) & (x < nozzle_len)] = SOLID
+    inlet = (ry < a0) & (x == 0)
+    mask[inlet] = INLET
+    mask[x == n - 1] = OUTLET
+    rho = np.full(N, RHO_V)
+    rho[(ry < a0) & (x < nozzle_len)] = RHO_L
+    d = np.sqrt((x - nozzle_len) ** 2 + (y - yc) ** 2)
+    rho = np.maximum(rho, 0.5 * (RHO_L + RHO_V) - 0.5 * (RHO_L - RHO_V) * np.tanh(2.0 * (d - a0) / 5.0))
+    rho[mask == SOLID] = 0.0
+    u_in = np.zeros((N, 3))
+    prof = 1.5 * u_mean * (1.0 - (ry / a0) ** 2)  # 2-D Poiseuille: peak 3/2 of the mean
+    u_in[inlet, 0] = prof[inlet]
+    if perturb:
+        u_in[inlet, 0] += uniform_noise(N, perturb, seed)[inlet]
+    fields = dict(mask=mask, rho=rho, q=np.zeros(N), u_in=u_in,
+                  inlet_region=((ry < a0) & (x >= 1) & (x < nozzle_len) & (mask == FLUID)).astype(np.uint8))
+    return cfg, fields
+
+
 def as_float64_fields(fields: dict) -> dict:
     out = {}
     for k, v in fields.items():

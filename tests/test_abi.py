@@ -45,6 +45,7 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(elbm_params), offsetof(elbm_params, phi_lo),
          offsetof(elbm_params, nu0), offsetof(elbm_params, E_ext), offsetof(elbm_params, rho_out),
          offsetof(elbm_params, cuda_stream), sizeof(elbm_init_fields));
+  printf("%zu\n", offsetof(elbm_params, velset));
   return 0; }
 '''
     with tempfile.TemporaryDirectory() as d:
@@ -55,7 +56,7 @@ int main(void) {
         got = list(map(int, subprocess.run([exe], capture_output=True, text=True).stdout.split()))
     P = elbm.Params
     want = [ctypes.sizeof(P), P.phi_lo.offset, P.nu0.offset, P.E_ext.offset, P.rho_out.offset,
-            P.cuda_stream.offset, ctypes.sizeof(elbm.InitFields)]
+            P.cuda_stream.offset, ctypes.sizeof(elbm.InitFields), P.velset.offset]
     assert got == want
 
 
@@ -63,6 +64,14 @@ def test_velocity_set_matches_oracle_table(L):
     c, w = elbm.velocity_set()
     co, wo, _ = oracle.lattice(3)
     assert np.array_equal(c, co) and np.array_equal(w, wo)
+
+
+def test_d2q9_velocity_set_matches_oracle_table(L):
+    """The CUDA path's D2Q9 order and weights (Sec. II) are the oracle's."""
+    c, w = elbm.velocity_set(2)
+    co, wo, _ = oracle.lattice(2)
+    assert c.shape == (9, 3) and np.array_equal(c, co) and np.array_equal(w, wo)
+    assert L.elbm_velocity_set_of(7, None, None) == elbm.E_INVAL
 
 
 def test_strerror(L):
@@ -80,6 +89,15 @@ def test_strerror(L):
     dict(carreau_lagged=2),
     dict(alpha_h_tol=-1e-10),
     dict(alpha_h_tol=float("nan")),
+    # D2Q9: one site thick, in-plane potential data, and the kernels it is built for
+    dict(dim=2),                                                  # nz = 4
+    dict(dim=2, shape=(4, 4, 1), precision="bf16"),
+    dict(dim=2, shape=(4, 4, 1), precision="fp32", alpha_precision="fp32_fast"),
+    dict(dim=2, shape=(4, 4, 1), charge_model="transport"),
+    dict(dim=2, shape=(4, 4, 1), charge_model="conserved", poisson_solver="mg"),
+    dict(dim=2, shape=(4, 4, 1), phi_axis=2),
+    dict(dim=2, shape=(4, 4, 1), E_ext=(0.0, 0.0, 1e-3)),
+    dict(dim=4, shape=(4, 4, 1)),                                 # no such set
 ])
 def test_invalid_parameters_rejected_without_allocation(L, bad):
     cfg = W.base_params(shape=(4, 4, 4))
