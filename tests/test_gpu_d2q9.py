@@ -299,3 +299,42 @@ def test_d2q9_paper_charged_drop_at_rest_full_size(E, paper):
     Eb = paper["E_boundary"]["value"]
     assert Em[band].min() < Eb < Em[band].max()
     g.close()
+
+
+def _aspect(rho, n, rho_v=0.16):
+    """sqrt(I_xx / I_yy) of the liquid's excess density (x: the field's axis)."""
+    w = np.clip(rho.reshape(n, n) - rho_v, 0.0, None)
+    y, x = np.mgrid[0:n, 0:n]
+    m = w.sum()
+    cx, cy = (w * x).sum() / m, (w * y).sum() / m
+    return float(np.sqrt((w * (x - cx) ** 2).sum() / (w * (y - cy) ** 2).sum()))
+
+
+def test_d2q9_paper_drop_in_applied_field_full_size(E, paper):
+    """The paper's charged drop in an applied field at its own size (320^2,
+    R = 40, E_ext = 0.1 and 0.5 along x, t = 1250, FP64; Sec. III A): the
+    drop stays finite and stretches along the field, more at 0.5 than at
+    0.1, and its interface curvature K (the oracle's K of the GPU's density,
+    maximum over 0.6 < rho < 1.6) grows from about 1/R. Measured: aspect
+    1.015 and 1.41, K_max 0.028 and 0.113; the paper prints K_max = 5.17e-2
+    at 0.5 (a measure of its own: held here only as an order of magnitude)."""
+    n = 320
+    res = {}
+    for e_ext in (0.1, 0.5):
+        cfg, fl = W.paper_drop_2d()
+        cfg.update(E_ext=(e_ext, 0.0, 0.0), poisson_tol=1e-10, store_macro=1)
+        g = E.Sim(cfg, fl)
+        for _ in range(5):
+            g.step(250)
+        assert g.diag()["n_nonfinite"] == 0
+        rho = g.get("rho")
+        _, K, _ = oracle.charge_field(cfg, fl["mask"], rho)
+        band = (rho > 0.6) & (rho < 1.6)
+        res[e_ext] = (_aspect(rho, n), float(K[band].max()))
+        g.close()
+    (a1, k1), (a5, k5) = res[0.1], res[0.5]
+    assert 1.0 < a1 < 1.05 and 1.2 < a5 < 1.6, res
+    assert 0.9 / 40.0 < k1 < 1.25 / 40.0, res
+    assert k5 > 2.0 * k1, res
+    kp = paper["K_max"]["value"]
+    assert 0.5 * kp < k5 < 4.0 * kp, res
