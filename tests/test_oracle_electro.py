@@ -123,6 +123,35 @@ def test_poisson_point_charge_matches_fourier_green_function():
     assert np.allclose(phi, ref - ref.mean(), rtol=0, atol=1e-11 * np.abs(ref).max())
 
 
+def test_poisson_2d_point_charge_matches_fourier_green_function():
+    """The same pin for the paper's 2-D lattice (nz = 1, dim 2; the odd
+    periodic extent 13 puts the sweep on three colours): the 5-point
+    operator, eigenvalue -eps lambda(k) with lambda(k) = 2 (1 - cos(2 pi
+    k_x / n_x)) + 2 (1 - cos(2 pi k_y / n_y)), two charges of unequal sign
+    and size with their neutralising background."""
+    nx, ny = 13, 10
+    N = nx * ny
+    kap = 1.0
+    cfg = W.base_params(dim=2, shape=(nx, ny, 1), phi_axis=0, charge_model="xi", poisson_tol=1e-14,
+                        eps_kappa=kap)
+    rho = np.full(N, 0.4)
+    eps = 1.0 + kap * 0.4
+    q = np.zeros(N)
+    q[5 + nx * 3] = 1.0
+    q[9 + nx * 7] = -0.4
+    qn = q - q.mean()
+    phi, it, res = oracle.poisson_solve(cfg, np.zeros(N, np.uint8), rho, qn)
+    assert res <= 1e-14 and it > 0
+    ky, kx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    lam = 2 * (1 - np.cos(2 * np.pi * kx / nx)) + 2 * (1 - np.cos(2 * np.pi * ky / ny))
+    qh = np.fft.fft2(qn.reshape(ny, nx))
+    ph = np.zeros_like(qh)
+    nzk = lam > 0
+    ph[nzk] = qh[nzk] / (eps * lam[nzk])
+    ref = np.real(np.fft.ifft2(ph)).reshape(-1)
+    assert np.allclose(phi, ref - ref.mean(), rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
 def test_poisson_dirichlet_and_conductors_match_direct_solve():
     shape = (6, 4, 5)
     N = 120
