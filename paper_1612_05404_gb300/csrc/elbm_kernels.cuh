@@ -1,7 +1,8 @@
 // elbm_kernels.cuh -- the kernels of one time step of the charged entropic
 // lattice Boltzmann method (arXiv:1612.05404, Sec. II C), templated on the
 // population precision. Each k_*.cu translation unit instantiates them for
-// one precision.
+// one precision and one velocity set (D3Q19, or D2Q9 where it defines
+// ELBM_D2Q9; see elbm_device.cuh).
 //
 // Data layout: populations are planes [p][site] (site = x + nx (y + ny z)) in
 // two buffers A (read) and B (write); streaming is done by "pull": the step
