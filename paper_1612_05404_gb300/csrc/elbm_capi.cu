@@ -1,7 +1,8 @@
 // elbm_capi.cu -- the C ABI declared in include/elbm.h: parameter checks,
 // device state, the order of the passes of one step (Sec. II C of
 // arXiv:1612.05404) and field export. Every pass runs in the kernels of
-// k_fp64.cu / k_fp32.cu / k_bf16.cu; this file only sequences them, plus the
+// k_fp64.cu / k_fp32.cu / k_bf16.cu (D3Q19) or k_fp64_d2q9.cu /
+// k_fp32_d2q9.cu (D2Q9); this file only sequences them, plus the
 // small deterministic reductions that turn per-block partial sums into the
 // global sums the step needs (mean charge, Poisson residual, diagnostics).
 #include <cmath>
