@@ -36,6 +36,21 @@ def test_exports_every_declared_symbol(L):
         assert getattr(L, name)
 
 
+def test_velocity_sets_link_side_by_side(L):
+    """The step's kernels are compiled once per velocity set into one
+    library (D3Q19, and the paper's D2Q9 in k_*_d2q9.cu) under distinct
+    names, so that a launch for one set can never reach the other's code;
+    the D2Q9 build holds only the variants elbm_init accepts for it (no BF16
+    storage, no learned proposal)."""
+    out = subprocess.run(["nm", "-C", elbm.LIB_PATH], capture_output=True, text=True, check=True).stdout
+    for ns in ("elbm::d3q19::", "elbm::d2q9::"):
+        for k in ("k_collide<", "k_moments<", "k_charge_ab<", "k_sor<", "k_init_pop<", "k_bounce_bits("):
+            assert ns + k in out, ns + k
+    assert "elbm::d3q19::k_collide<2," in out and "elbm::d3q19::k_collide<1, 1, true>" in out
+    assert "elbm::d2q9::k_collide<2," not in out and "elbm::d2q9::k_collide<1, 1, true>" not in out
+    assert "elbm::d2q9::k_mg_" not in out  # multigrid is shared and D3Q19-instantiated only
+
+
 def test_struct_layout_matches_c(L):
     src = r'''
 #include <stdio.h>
@@ -169,6 +184,26 @@ def test_batch_create_argument_checks(L):
     assert L.elbm_batch_create(arr, 1, 6, None, ctypes.byref(out)) == elbm.E_INVAL  # unknown flag
     assert L.elbm_batch_create(arr, 1, 17 << 8, None, ctypes.byref(out)) == elbm.E_INVAL  # span above 16
     assert not out.value
+
+
+def test_paper_2d_workloads_pass_the_host_checks(L):
+    """The paper's 2-D runs on D2Q9 (the drop at rest and in a field, the jet
+    cases a/b/c with the adaptive inlet, FP64 and FP32): elbm_init's host
+    checks accept each, inlet region and all; only the device allocation can
+    then fail (no GPU here)."""
+    runs = [W.paper_drop_2d(n=40, radius=8.0)]
+    cfg, fl = W.paper_drop_2d(n=40, radius=8.0)
+    cfg.update(E_ext=(0.5, 0.0, 0.0), force_el="full", precision="fp32", alpha_precision="fp32")
+    W.reduced_precision(cfg)
+    runs.append((cfg, fl))
+    for case in "abc":
+        for prec in ("fp64", "fp32"):
+            runs.append(W.jet_2d(n=48, D=12, nozzle_len=10, wall=2, case=case, precision=prec))
+    for cfg, fl in runs:
+        try:
+            elbm.Sim(cfg, fl).close()
+        except elbm.ElbmError as e:
+            assert e.code != elbm.E_INVAL, (cfg["charge_model"], cfg["precision"], e)
 
 
 def test_every_box_edge_passes_the_multigrid_checks(L):
