@@ -264,7 +264,8 @@ JET2D_CASES = {  # Sec. III B: Newtonian, then Carreau with flow index 0.75 and 
 
 
 def jet_2d(n=320, D=40, case="a", nozzle_len=40, wall=5, u_mean=0.02, E0=0.1,
-           precision="fp64", steps=20000, seed=SEED_BASE + 7, perturb=0.0):
+           precision="fp64", steps=20000, seed=SEED_BASE + 7, perturb=0.0,
+           rho_in=RHO_L, rho_out=RHO_V):
     """The paper's 2-D electrified jet (Sec. III B) on D2Q9: an n x n lattice,
     x along the jet. A nozzle of inner diameter D on the left (bore
     |y - c| < D/2, walls `wall` sites thick, x < nozzle_len; a conductor at
@@ -276,7 +277,9 @@ def jet_2d(n=320, D=40, case="a", nozzle_len=40, wall=5, u_mean=0.02, E0=0.1,
     G = Gw = -5, eps = 1 + rho. The inlet profile is Poiseuille, rescaled
     each step to the mean velocity measured inside the nozzle
     (fields["inlet_region"]). Liquid fills the nozzle with a drop just
-    outside it. `case` picks the rheology (JET2D_CASES)."""
+    outside it. `case` picks the rheology (JET2D_CASES). rho_in / rho_out:
+    the densities held by the inlet and outlet nodes (the paper's printed
+    2.0 / 0.16 by default)."""
     rh = JET2D_CASES[case]
     shape = (n, n, 1)
     nu0 = 1.0 / 6.0
@@ -285,7 +288,7 @@ def jet_2d(n=320, D=40, case="a", nozzle_len=40, wall=5, u_mean=0.02, E0=0.1,
         face_bc=["wall"] * 6, phi_bc=["dirichlet"] * 4 + ["neumann"] * 2, phi_axis=0,
         phi_lo=0.0, phi_hi=-E0 * (n + 1), phi_solid=0.0,
         nu0=nu0, nu_inf=rh["nu_inf"], n_carreau=rh["n_carreau"], eps_kappa=1.0,
-        precision=precision, poisson_tol=1e-13)
+        precision=precision, poisson_tol=1e-13, rho_in=rho_in, rho_out=rho_out)
     reduced_precision(cfg)
     cfg["lambda"] = rh["lam"]
     cfg["steps"] = steps
