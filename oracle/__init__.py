@@ -12,6 +12,7 @@ passage of Lauricella et al. (arXiv:1612.05404) it follows in the C source.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -87,44 +88,61 @@ def build(force: bool = False) -> str:
 def lib():
     global _lib
     if _lib is None:
-        path = build()
-        L = ctypes.CDLL(path)
-        dp = ctypes.POINTER(ctypes.c_double)
-        u8p = ctypes.POINTER(ctypes.c_ubyte)
-        pp = ctypes.POINTER(Params)
-        L.orc_Q.argtypes = [ctypes.c_int]
-        L.orc_lattice.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp, dp]
-        L.orc_feq.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp]
-        L.orc_H.argtypes = [ctypes.c_int, dp]
-        L.orc_H.restype = ctypes.c_double
-        L.orc_h.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double]
-        L.orc_h.restype = ctypes.c_double
-        L.orc_h_prime0.argtypes = [ctypes.c_int, dp, dp]
-        L.orc_h_prime0.restype = ctypes.c_double
-        L.orc_alpha.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp]
-        L.orc_alpha_bisect.argtypes = [ctypes.c_int, dp, dp]
-        L.orc_alpha_bisect.restype = ctypes.c_double
-        L.orc_spectral_norm.argtypes = [ctypes.c_int, dp]
-        L.orc_spectral_norm.restype = ctypes.c_double
-        L.orc_carreau.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
-        L.orc_carreau_lagged.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                         ctypes.c_double, dp, dp]
-        L.orc_sc_force.argtypes = [pp, u8p, dp, dp]
-        L.orc_charge_field.argtypes = [pp, u8p, dp, dp, dp, dp]
-        L.orc_poisson_solve.argtypes = [pp, u8p, dp, dp, ctypes.c_double, dp,
-                                        ctypes.POINTER(ctypes.c_int), dp]
-        L.orc_poisson_system.argtypes = [pp, u8p, dp, dp, dp, dp,
-                                         ctypes.POINTER(ctypes.c_long),
-                                         ctypes.POINTER(ctypes.c_int)]
-        L.orc_efield.argtypes = [pp, u8p, dp, dp]
-        L.orc_stream.argtypes = [pp, u8p, dp, dp, dp, dp, dp, dp]
-        L.orc_init.argtypes = [pp, u8p, dp, dp, dp, dp, dp, dp, dp]
-        L.orc_apply_io.argtypes = [pp, u8p, dp, dp]
-        L.orc_step.argtypes = [pp, u8p, dp, u8p, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
-        L.orc_set_threads.argtypes = [ctypes.c_int]
-        L.orc_set_threads.restype = ctypes.c_int
-        _lib = L
+        _lib = _configure(ctypes.CDLL(build()))
     return _lib
+
+
+@contextlib.contextmanager
+def substituted(path: str):
+    """Test infrastructure: inside the block every function of this module
+    runs from the library at `path`, another build of elbm_oracle.c (a copy
+    with a planted mistake, to show that the pins catch it)."""
+    global _lib
+    old = lib()
+    _lib = _configure(ctypes.CDLL(path))
+    try:
+        yield
+    finally:
+        _lib = old
+
+
+def _configure(L):
+    """Argument and result types of the oracle's C entry points."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    u8p = ctypes.POINTER(ctypes.c_ubyte)
+    pp = ctypes.POINTER(Params)
+    L.orc_Q.argtypes = [ctypes.c_int]
+    L.orc_lattice.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp, dp]
+    L.orc_feq.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp]
+    L.orc_H.argtypes = [ctypes.c_int, dp]
+    L.orc_H.restype = ctypes.c_double
+    L.orc_h.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double]
+    L.orc_h.restype = ctypes.c_double
+    L.orc_h_prime0.argtypes = [ctypes.c_int, dp, dp]
+    L.orc_h_prime0.restype = ctypes.c_double
+    L.orc_alpha.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp]
+    L.orc_alpha_bisect.argtypes = [ctypes.c_int, dp, dp]
+    L.orc_alpha_bisect.restype = ctypes.c_double
+    L.orc_spectral_norm.argtypes = [ctypes.c_int, dp]
+    L.orc_spectral_norm.restype = ctypes.c_double
+    L.orc_carreau.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
+    L.orc_carreau_lagged.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, dp, dp]
+    L.orc_sc_force.argtypes = [pp, u8p, dp, dp]
+    L.orc_charge_field.argtypes = [pp, u8p, dp, dp, dp, dp]
+    L.orc_poisson_solve.argtypes = [pp, u8p, dp, dp, ctypes.c_double, dp,
+                                    ctypes.POINTER(ctypes.c_int), dp]
+    L.orc_poisson_system.argtypes = [pp, u8p, dp, dp, dp, dp,
+                                     ctypes.POINTER(ctypes.c_long),
+                                     ctypes.POINTER(ctypes.c_int)]
+    L.orc_efield.argtypes = [pp, u8p, dp, dp]
+    L.orc_stream.argtypes = [pp, u8p, dp, dp, dp, dp, dp, dp]
+    L.orc_init.argtypes = [pp, u8p, dp, dp, dp, dp, dp, dp, dp]
+    L.orc_apply_io.argtypes = [pp, u8p, dp, dp]
+    L.orc_step.argtypes = [pp, u8p, dp, u8p, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
+    L.orc_set_threads.argtypes = [ctypes.c_int]
+    L.orc_set_threads.restype = ctypes.c_int
+    return L
 
 
 def _dp(a):
