@@ -152,6 +152,29 @@ def test_poisson_2d_point_charge_matches_fourier_green_function():
     assert np.allclose(phi, ref - ref.mean(), rtol=0, atol=1e-11 * np.abs(ref).max())
 
 
+def test_step_potential_solves_the_neutralised_problem():
+    """Inside a time step (Sec. II C) the potential solves div(eps grad phi) =
+    -(q - <q>): the free charge of the step less its mean (the uniform
+    background of reading 17). With uniform eps on a periodic lattice that
+    solution is the Fourier one, phi_hat = q_hat / (eps lambda(k)), k != 0,
+    taken here from the step's own charge."""
+    nx, ny = 20, 16
+    cfg = W.base_params(dim=2, shape=(nx, ny, 1), phi_axis=0, charge_model="conserved", Q_b=0.3, Q_s=0.9,
+                        eps_kappa=0.0, poisson_tol=1e-13, poisson_check_every=1)
+    rho = W.drop_profile((nx, ny, 1), 5.0, dim=2)
+    sim = oracle.Sim(cfg, dict(mask=np.zeros(nx * ny, np.uint8), rho=rho))
+    sim.step(1)
+    q = sim.q
+    assert abs(q.sum() - 1.2) < 1e-12 and q.min() >= 0.0
+    ky, kx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    lam = 2 * (1 - np.cos(2 * np.pi * kx / nx)) + 2 * (1 - np.cos(2 * np.pi * ky / ny))
+    qh = np.fft.fft2((q - q.mean()).reshape(ny, nx))
+    ph = np.zeros_like(qh)
+    ph[lam > 0] = qh[lam > 0] / lam[lam > 0]
+    ref = np.real(np.fft.ifft2(ph)).reshape(-1)
+    assert np.allclose(sim.phi, ref - ref.mean(), rtol=0, atol=1e-10 * np.abs(ref).max())
+
+
 def test_poisson_dirichlet_and_conductors_match_direct_solve():
     shape = (6, 4, 5)
     N = 120

@@ -16,19 +16,20 @@ def _eos(rho, G):
 def test_sc_force_continuum_limit():
     """On a long-wave profile Eq. (sc) tends to -G c_s^2 psi grad psi (the
     gradient of the non-ideal pressure), with an O(k^2) error that drops by
-    about 4 when the wavelength doubles."""
-    for dim in (2, 3):
+    about 4 when the wavelength doubles; psi = rho0 (1 - exp(-rho/rho0)),
+    checked at rho0 = 1 and 1.5."""
+    for dim, rho0 in ((2, 1.0), (3, 1.0), (2, 1.5)):
         errs = []
         for nx in (64, 128):
             shape = (nx, 4, 1) if dim == 2 else (nx, 4, 4)
-            cfg = W.base_params(dim=dim, shape=shape, G=-5.0, phi_axis=0)
+            cfg = W.base_params(dim=dim, shape=shape, G=-5.0, phi_axis=0, rho0=rho0)
             x = np.arange(nx, dtype=float)
             k = 2 * np.pi / nx
             rho1 = 1.0 + 0.5 * np.sin(k * x)
             rho = np.broadcast_to(rho1, shape[::-1]).reshape(-1).copy()
             F = oracle.sc_force(cfg, np.zeros(rho.size, np.uint8), rho)
-            psi = 1 - np.exp(-rho1)
-            dpsi = np.exp(-rho1) * 0.5 * k * np.cos(k * x)
+            psi = rho0 * (1 - np.exp(-rho1 / rho0))
+            dpsi = np.exp(-rho1 / rho0) * 0.5 * k * np.cos(k * x)
             ref = 5.0 / 3.0 * psi * dpsi
             Fx = F[:nx, 0]
             assert np.abs(F[:, 1:]).max() < 1e-15

@@ -118,6 +118,36 @@ MUTANTS = {
         "double tau_q = 0.5 + p->Dq / CS2_Q;",
         "double tau_q = 0.5 + p->Dq / CS2;",
         [("test_oracle_electro", "test_transport_mode_matches_linear_mode_dynamics", {})]),
+    # Eq. (sc): psi without rho0 (1 - exp(-rho) for rho0 (1 - exp(-rho/rho0)))
+    "psi_without_rho0": (
+        "return p->rho0 * (1.0 - exp(-rho / p->rho0));",
+        "return 1.0 - exp(-rho);",
+        [("test_oracle_forces", "test_sc_force_continuum_limit", {})]),
+    # Eq. (sc) wall sum without the site's psi
+    "sc_wall_psi": (
+        "F[3 * s + a] = -p->G * ps * sf[a] - p->Gw * ps * sw[a];",
+        "F[3 * s + a] = -p->G * ps * sf[a] - p->Gw * sw[a];",
+        [("test_oracle_forces", "test_sc_wall_term", {})]),
+    # the smoothed Heaviside of the bulk charge turned over (gas side)
+    "theta_turned_over": (
+        "return 0.5 * (1.0 + tanh((rho - p->rho0) / p->theta_width));",
+        "return 0.5 * (1.0 - tanh((rho - p->rho0) / p->theta_width));",
+        [("test_oracle_electro", "test_conserved_charge_totals", {})]),
+    # E = -grad phi without the 1/2 of the central difference
+    "efield_difference_factor": (
+        "E[3 * s + a] = -(pv[1] - pv[0]) / 2.0 + p->E_ext[a];",
+        "E[3 * s + a] = -(pv[1] - pv[0]) + p->E_ext[a];",
+        [("test_oracle_electro", "test_full_electric_force_matches_discrete_closed_form", {})]),
+    # D3Q7 charge populations pushed along -c
+    "charge_push_opposite": (
+        "else if (mask[nb] == ORC_FLUID) gn[i * N + nb] = gs[i * N + s];",
+        "else if (mask[nb] == ORC_FLUID) gn[opp * N + nb] = gs[i * N + s];",
+        [("test_oracle_electro", "test_transport_advects_charge_with_the_flow", {})]),
+    # the step's Poisson source without the neutralising background
+    "no_neutralisation": (
+        "for (long s = 0; s < N; s++) qn[s] = (mask[s] == ORC_FLUID) ? q[s] - qmean : 0.0;",
+        "for (long s = 0; s < N; s++) qn[s] = (mask[s] == ORC_FLUID) ? q[s] : 0.0;",
+        [("test_oracle_electro", "test_step_potential_solves_the_neutralised_problem", {})]),
     # adaptive inlet: the nozzle mean divided by the inlet count
     "inlet_mean_count": (
         "double ratio = (mu / (double)nr) / (m0 / (double)ni);",
