@@ -175,3 +175,55 @@ def test_planted_mistake_fails_its_pins(name, tmp_path, paper):
                 args["paper"] = paper
             with pytest.raises(AssertionError):
                 pin(**args)
+
+
+# The learned-alpha oracle (oracle/mlp.py, Python): the same check, the
+# mutant's functions swapped into the module for the duration of its pins.
+MLP_SRC = os.path.join(ROOT, "oracle", "mlp.py")
+MLP_MUTANTS = {
+    # gelu'(z) without the 3 of d(z + K z^3)/dz
+    "gelu_prime_cubic_term": (
+        "0.5 * z * (1.0 - t * t) * _C * (1.0 + 3.0 * _K * z * z)",
+        "0.5 * z * (1.0 - t * t) * _C * (1.0 + _K * z * z)",
+        [("test_oracle_mlp", "test_gradient_matches_central_differences")]),
+    # back-propagation through the first layer with the second layer's gelu'
+    "backprop_wrong_layer": (
+        'dz1 = (dz2 @ P["W2"]) * gelu_prime(z1)',
+        'dz1 = (dz2 @ P["W2"]) * gelu_prime(z2)',
+        [("test_oracle_mlp", "test_gradient_matches_central_differences")]),
+    # Adam without the second moment's bias correction
+    "adam_second_moment_uncorrected": (
+        "vh = v / (1.0 - beta2 ** t)",
+        "vh = v",
+        [("test_oracle_mlp", "test_adam_first_step_is_lr_times_sign")]),
+    # the network's output without its bias
+    "output_bias_dropped": (
+        'o = h2 @ P["W3"] + P["b3"][0]',
+        'o = h2 @ P["W3"]',
+        [("test_oracle_mlp", "test_zero_weights_give_the_output_bias")]),
+    # the series start of Eq. (entropic) with the a^3 M4 term's coefficient halved
+    "series_fourth_moment": (
+        "g = h0 + a * (0.5 * M2 + a * (-M3 / 6.0 + a * (M4 / 12.0)))",
+        "g = h0 + a * (0.5 * M2 + a * (-M3 / 6.0 + a * (M4 / 24.0)))",
+        [("test_oracle_mlp", "test_series_start_error_is_third_order")]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MLP_MUTANTS))
+def test_planted_mistake_in_the_mlp_oracle_fails_its_pins(name):
+    from oracle import mlp
+    old, new, pins = MLP_MUTANTS[name]
+    src = open(MLP_SRC).read()
+    assert src.count(old) == 1, f"{name}: the planted text must occur once in the MLP oracle"
+    ns = {"__name__": "oracle.mlp_planted"}
+    exec(compile(src.replace(old, new), MLP_SRC + " (planted)", "exec"), ns)
+    saved = {k: v for k, v in vars(mlp).items() if inspect.isfunction(v)}
+    try:
+        for k in saved:
+            setattr(mlp, k, ns[k])
+        for mod, fn in pins:
+            with pytest.raises(AssertionError):
+                getattr(importlib.import_module(mod), fn)()
+    finally:
+        for k, v in saved.items():
+            setattr(mlp, k, v)
