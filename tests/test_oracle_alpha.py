@@ -21,6 +21,22 @@ def _state(dim, rng, amp, umax=0.1):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
+def test_H_closed_forms(dim):
+    """Eq. (H), H(f) = sum_p f_p ln(f_p / w_p): zero at the weights, rho ln rho
+    at the rest equilibrium f = rho w, and H(f + a D) - H(f) equal to the
+    h of Eq. (entropic) (pinned on its own in 50-digit arithmetic)."""
+    _, w, _ = oracle.lattice(dim)
+    assert abs(oracle.H(dim, w)) < 1e-16
+    for rho in (0.16, 1.0, 2.0):
+        assert oracle.H(dim, rho * w) == pytest.approx(rho * np.log(rho), rel=1e-14, abs=1e-16)
+    rng = np.random.default_rng(60 + dim)
+    f, d, _ = _state(dim, rng, 0.05)
+    for a in (0.5, 1.7):
+        dH = oracle.H(dim, f + a * d) - oracle.H(dim, f)
+        assert dH == pytest.approx(oracle.h(dim, f, d, a), rel=1e-9, abs=1e-15)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
 def test_h_log1p_form_equals_H_difference(dim):
     """The oracle's rearranged h(alpha) is H(f + alpha D) - H(f) exactly."""
     rng = np.random.default_rng(10 + dim)

@@ -148,6 +148,26 @@ MUTANTS = {
         "for (long s = 0; s < N; s++) qn[s] = (mask[s] == ORC_FLUID) ? q[s] - qmean : 0.0;",
         "for (long s = 0; s < N; s++) qn[s] = (mask[s] == ORC_FLUID) ? q[s] : 0.0;",
         [("test_oracle_electro", "test_step_potential_solves_the_neutralised_problem", {})]),
+    # Eq. (H) with ln f in place of ln(f / w)
+    "H_without_weights": (
+        "for (int p = 0; p < orc_Q(dim); p++) s += f[p] * log(f[p] / w[p]);",
+        "for (int p = 0; p < orc_Q(dim); p++) s += f[p] * log(f[p]);",
+        [("test_oracle_alpha", "test_H_closed_forms", dict(dim=3))]),
+    # the Jacobi rotation of the stress norm with its sine on the wrong side
+    "jacobi_rotation_sign": (
+        "J[p][p] = cth; J[q][q] = cth; J[p][q] = sth; J[q][p] = -sth;",
+        "J[p][p] = cth; J[q][q] = cth; J[p][q] = -sth; J[q][p] = sth;",
+        [("test_oracle_rheology", "test_spectral_norm_matches_eigvalsh", {})]),
+    # the lagged Carreau reading using nu0 in place of the previous step's nu
+    "lagged_carreau_nu0": (
+        "*gdot = Pn * alpha * beta_of(nu_prev) / (rho * CS2);\n    *nu = nu_carreau(p, *gdot);",
+        "*gdot = Pn * alpha * beta_of(p->nu0) / (rho * CS2);\n    *nu = nu_carreau(p, *gdot);",
+        [("test_oracle_electro", "test_lagged_carreau_fixed_point_is_the_root", {})]),
+    # the Ohmic source of the transported charge without its face mean's 1/2
+    "ohmic_face_mean": (
+        "if (k == PN_UNKNOWN) R += 0.5 * (ss + sigma_of(C->p, rho[nb])) * (phi[nb] - phi[s]);",
+        "if (k == PN_UNKNOWN) R += (ss + sigma_of(C->p, rho[nb])) * (phi[nb] - phi[s]);",
+        [("test_oracle_electro", "test_transport_relaxation_time_constant", {})]),
     # adaptive inlet: the nozzle mean divided by the inlet count
     "inlet_mean_count": (
         "double ratio = (mu / (double)nr) / (m0 / (double)ni);",
