@@ -168,6 +168,21 @@ MUTANTS = {
         "if (k == PN_UNKNOWN) R += 0.5 * (ss + sigma_of(C->p, rho[nb])) * (phi[nb] - phi[s]);",
         "if (k == PN_UNKNOWN) R += (ss + sigma_of(C->p, rho[nb])) * (phi[nb] - phi[s]);",
         [("test_oracle_electro", "test_transport_relaxation_time_constant", {})]),
+    # initial populations at rest whatever the initial velocity
+    "init_ignores_velocity": (
+        "            orc_feq(p->dim, rho0_field[s], u, feq);",
+        "            { const double u00[3] = {0, 0, 0}; orc_feq(p->dim, rho0_field[s], u00, feq); }",
+        [("test_oracle_electro", "test_transport_advects_charge_with_the_flow", {})]),
+    # initial charge populations without their advective part
+    "charge_init_at_rest": (
+        "g[i * C.N + s] = (mask[s] == ORC_FLUID) ? W7[i] * q0 * (1.0 + cu / CS2_Q) : 0.0;",
+        "g[i * C.N + s] = (mask[s] == ORC_FLUID) ? W7[i] * q0 : 0.0;",
+        [("test_oracle_electro", "test_transport_advects_charge_with_the_flow", {})]),
+    # links from inlet nodes carrying the reservoir density during streaming
+    "stream_inlet_density": (
+        "orc_feq(p->dim, mask[src] == ORC_INLET ? p->rho_in : p->rho_out, uio, fe);\n                fn[k * N + s] = fe[k];",
+        "orc_feq(p->dim, p->rho_out, uio, fe);\n                fn[k * N + s] = fe[k];",
+        [("test_oracle_lattice", "test_inlet_and_outlet_populations", {})]),
     # adaptive inlet: the nozzle mean divided by the inlet count
     "inlet_mean_count": (
         "double ratio = (mu / (double)nr) / (m0 / (double)ni);",
