@@ -312,12 +312,14 @@ def _aspect(rho, n, rho_v=0.16):
 
 def test_d2q9_paper_drop_in_applied_field_full_size(E, paper):
     """The paper's charged drop in an applied field at its own size (320^2,
-    R = 40, E_ext = 0.1 and 0.5 along x, t = 1250, FP64; Sec. III A): the
-    drop stays finite and stretches along the field, more at 0.5 than at
-    0.1, and its interface curvature K (the oracle's K of the GPU's density,
-    maximum over 0.6 < rho < 1.6) grows from about 1/R. Measured: aspect
-    1.015 and 1.41, K_max 0.028 and 0.113; the paper prints K_max = 5.17e-2
-    at 0.5 (a measure of its own: held here only as an order of magnitude)."""
+    R = 40, E_ext = 0.1 and 0.5 along x, t = 1250, FP64; Sec. III A), here
+    started from the initial tanh profile (the paper starts from the drop
+    equilibrated at rest): the drop stays finite and stretches along the
+    field, more at 0.5 than at 0.1, and its interface curvature K (the
+    oracle's K of the GPU's density, maximum over 0.6 < rho < 1.6) grows
+    from about 1/R. Measured: aspect 1.015 and 1.41, K_max 0.028 and 0.113;
+    the paper prints K_max = 5.17e-2 at 0.5 for its protocol and measure
+    (held here only as an order of magnitude)."""
     n = 320
     res = {}
     for e_ext in (0.1, 0.5):
