@@ -180,7 +180,8 @@ typedef struct elbm_params {
     int velset;                  /* ELBM_VSET_* (0 = D3Q19). D2Q9 needs nz = 1 and phi_axis
                                     0 or 1; the z faces take no part (no link crosses them,
                                     the potential has no z flux: face_bc[4..5] and
-                                    phi_bc[4..5] are ignored, E_ext[2] must be 0). It runs
+                                    phi_bc[4..5] only pass the checks every set makes,
+                                    E_ext[2] must be 0). It runs
                                     FP64 or FP32 populations with the FP64 or the guarded
                                     FP32 root, the paper's charge models (not transport) and
                                     SOR; other choices return ELBM_E_INVAL */
